@@ -1,0 +1,175 @@
+"""FP64 CPU oracle for the skeletal-density energy / force / torque fields.
+
+TEST INFRASTRUCTURE ONLY: imported by the test-suite, by the package smoke
+check and by the benchmark's CPU-baseline leg, never by the product path.
+It shares no code with the CUDA library; the only module both sides use is
+the seeded input generator package ``synth``.
+
+Each function wraps one routine of ``hf_oracle.c`` (plain C, double
+precision) and cites the passage of Behandish & Ilies (2016) it follows.
+Arrays are numpy float64, grids are (N, N, N) indexed [z, y, x].
+
+Parity status: every function here is pinned by a ``-m "not gpu"`` test
+against something other than itself (brute force, closed forms, numpy's
+pocketfft, scipy's rotation routines, exact invariants); see tests/.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from .build import build_oracle
+
+_lib = None
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build_oracle())
+        d = ctypes.POINTER(ctypes.c_double)
+        i = ctypes.c_int
+        ip = ctypes.POINTER(ctypes.c_int)
+        _lib.or_splat.argtypes = [i, i, d, d, d, ctypes.c_double, d]
+        _lib.or_quat_to_rot.argtypes = [d, d]
+        _lib.or_resample.argtypes = [i, d, d, d]
+        _lib.or_fft1d.argtypes = [i, d, d, i]
+        _lib.or_fft3d.argtypes = [i, d, i]
+        _lib.or_correlate_direct.argtypes = [i, d, d, d]
+        _lib.or_fields.argtypes = [i, d, d, d, d, d, d]
+        _lib.or_torque.argtypes = [i, i, d, d, i, d, ip]
+        _lib.or_query.argtypes = [i, i, d, d, i, d, d, i, d]
+        _lib.or_nearest.argtypes = [i, d, d, i, i, ip, d]
+        _lib.or_so3_log.argtypes = [d, d]
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def splat(n, pts, sigma, amp=None, cutoff=6.0):
+    """Skeletal density on the N^3 grid: sum of peak-normalised Gaussians
+    exp(-r^2 / 2 sigma_i^2), truncated at r <= cutoff*sigma_i, minimum-image
+    distance on the period-2 torus.  Stand-in for the skeletal density of
+    Section 2.3 (the Gaussian kernel g_sigma highlighting skeleton branches)."""
+    pts, sigma = _f64(pts).reshape(-1, 3), _f64(sigma).reshape(-1)
+    a = None if amp is None else _f64(amp).reshape(-1)
+    out = np.empty((n, n, n))
+    _L().or_splat(n, len(sigma), _p(pts), _p(sigma), None if a is None else _p(a), float(cutoff), _p(out))
+    return out
+
+
+def quat_to_rot(q):
+    """Unit quaternion (w, x, y, z) -> rotation matrix R in SO(3) (Section 2.2)."""
+    q = _f64(q).reshape(4)
+    R = np.empty((3, 3))
+    _L().or_quat_to_rot(_p(q), _p(R))
+    return R
+
+
+def resample(rho, R):
+    """rho^R[n] = rho(R^T x_n) by periodic trilinear interpolation
+    (Section 2.4, motion decomposition feeding Eq. 3)."""
+    rho = _f64(rho)
+    n = rho.shape[0]
+    R = _f64(R).reshape(3, 3)
+    out = np.empty_like(rho)
+    _L().or_resample(n, _p(rho), _p(R), _p(out))
+    return out
+
+
+def fft1d(x, sign=-1):
+    """Unscaled 1D DFT (Eq. 7a for sign=-1, Eq. 7b without 1/N for +1)."""
+    x = np.ascontiguousarray(x, dtype=np.complex128)
+    out = np.empty_like(x)
+    _L().or_fft1d(len(x), x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                  out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(sign))
+    return out
+
+
+def fft3d(x, sign=-1):
+    """Unscaled 3D DFT over all three axes (Eqs. 7a/7b)."""
+    a = np.array(x, dtype=np.complex128, order="C", copy=True)
+    _L().or_fft3d(a.shape[0], a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(sign))
+    return a
+
+
+def correlate_direct(rho1, rho2r):
+    """E[j] = h^3 sum_n rho1[n] rho2r[(n - j) mod N] -- Eqs. 1/3 as a direct
+    Riemann sum over the periodic grid, O(N^6)."""
+    rho1, rho2r = _f64(rho1), _f64(rho2r)
+    n = rho1.shape[0]
+    E = np.empty_like(rho1)
+    _L().or_correlate_direct(n, _p(rho1), _p(rho2r), _p(E))
+    return E
+
+
+def fields(rho1, rho2r):
+    """(E, Fx, Fy, Fz) over all lags by the convolution theorem, Eq. 5, and
+    the gradient multiplier 2 pi i omega of Eq. 6a (Nyquist multiplier 0);
+    F = -grad_t E."""
+    rho1, rho2r = _f64(rho1), _f64(rho2r)
+    n = rho1.shape[0]
+    outs = [np.empty_like(rho1) for _ in range(4)]
+    _L().or_fields(n, _p(rho1), _p(rho2r), *[_p(o) for o in outs])
+    return tuple(outs)
+
+
+def torque(quats, E, knn=6):
+    """T = -dE/dtheta per rotation by least squares over the knn nearest
+    sampled rotations (left perturbations), the finite-difference stand-in
+    for Eq. 6b.  E: (R, N, N, N).  Returns (T (R, 3, N, N, N), status (R,))."""
+    quats = _f64(quats).reshape(-1, 4)
+    E = _f64(E)
+    nrot, n = E.shape[0], E.shape[1]
+    T = np.empty((nrot, 3, n, n, n))
+    st = np.zeros(nrot, dtype=np.int32)
+    _L().or_torque(n, nrot, _p(quats), _p(E), int(knn), _p(T),
+                   st.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    return T, st
+
+
+def query(quats, fields_, t, q, k=4):
+    """Pose query (Section 4.2, restricted motion DOF): blend of the k nearest
+    sampled rotations (weights 1/theta) of periodic trilinear samples at
+    u = t/h.  fields_: (R, F, N, N, N).  Returns (F,) values."""
+    quats = _f64(quats).reshape(-1, 4)
+    fl = _f64(fields_)
+    nrot, nf, n = fl.shape[0], fl.shape[1], fl.shape[2]
+    t, q = _f64(t).reshape(3), _f64(q).reshape(4)
+    out = np.empty(nf)
+    _L().or_query(n, nrot, _p(quats), _p(fl), nf, _p(t), _p(q), int(k), _p(out))
+    return out
+
+
+def nearest(quats, q, k, skip=-1):
+    """k nearest sampled rotations to q by geodesic angle, ties to lower index."""
+    quats = _f64(quats).reshape(-1, 4)
+    q = _f64(q).reshape(4)
+    idx = np.empty(k, dtype=np.int32)
+    ang = np.empty(k)
+    _L().or_nearest(len(quats), _p(quats), _p(q), int(skip), int(k),
+                    idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _p(ang))
+    return idx, ang
+
+
+def so3_log(M):
+    """Axis-angle vector of a rotation matrix."""
+    M = _f64(M).reshape(3, 3)
+    v = np.empty(3)
+    _L().or_so3_log(_p(M), _p(v))
+    return v
+
+
+def pose_fields(rho1, rho2, quats):
+    """Convenience: for each quaternion, resample rho2 and return the stacked
+    (R, 4, N, N, N) array of (E, Fx, Fy, Fz)."""
+    out = []
+    for q in _f64(quats).reshape(-1, 4):
+        out.append(np.stack(fields(rho1, resample(rho2, quat_to_rot(q)))))
+    return np.stack(out)

@@ -1,0 +1,461 @@
+/*
+ * hf_oracle.c -- plain FP64 CPU oracle for the skeletal-density correlation
+ * path of Behandish & Ilies, "Haptic Assembly Using Skeletal Densities and
+ * Fourier Transforms" (ASME JCISE 16(2), 2016).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may link, call or
+ * execute this file; only the test-suite, the package smoke check and the
+ * benchmark's CPU-baseline leg use it.  It shares no code, header, table or
+ * constant with the CUDA library.
+ *
+ * Every routine is the plain definition written out, in double precision,
+ * with at most an OpenMP "parallel for" over independent outer iterations.
+ * There is no blocking, fusion or reordering beyond what the definition
+ * states.
+ *
+ * Conventions (readings of passages the paper leaves open):
+ *   grid      N^3 nodes on the periodic box [-1,1)^3, h = 2/N,
+ *             node x_n = -1 + n*h, arrays indexed [z][y][x] (x fastest).
+ *   lags      translation t_j = j*h, j wrapped to the torus; lag 0 at index 0.
+ *   DFT       unscaled forward sum with e^{-2 pi i k n / N}; inverse carries
+ *             1/N^3 (Eqs. 7a/7b up to their "constant factor").
+ *   energy    E = +f_SC, the Riemann sum of Eq. 1 with volume element h^3.
+ *   force     F = -grad_t E via the multiplier 2 pi i omega of Eq. 6a,
+ *             omega = k~/(N h), k~ signed, Nyquist multiplier set to 0.
+ *   torque    T = -grad_theta E by least squares over the 6 nearest sampled
+ *             rotations (left perturbation R_j = exp([d theta]x) R_i).
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+static const double PI = 3.14159265358979323846264338327950288;
+
+static int wrap(long i, int n) {
+    long r = i % n;
+    return (int)(r < 0 ? r + n : r);
+}
+
+static long idx3(int n, int z, int y, int x) {
+    return ((long)z * n + y) * n + x;
+}
+
+/* ------------------------------------------------------------------ */
+/* Skeletal density (stand-in for the SDF of Eq. 2, Section 2.3):       */
+/* a sum of isotropic Gaussian kernels centred on skeleton samples,     */
+/* peak amplitude a_i, truncated at |r| <= cutoff*sigma_i, distances    */
+/* measured by the minimum image on the torus of period 2.             */
+/* ------------------------------------------------------------------ */
+void or_splat(int n, int npts, const double *pts, const double *sigma,
+              const double *amp, double cutoff, double *rho)
+{
+    const double h = 2.0 / n;
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < n; ++z) {
+        for (int y = 0; y < n; ++y) {
+            for (int x = 0; x < n; ++x) {
+                const double p[3] = {-1.0 + x * h, -1.0 + y * h, -1.0 + z * h};
+                double acc = 0.0;
+                for (int i = 0; i < npts; ++i) {
+                    double r2 = 0.0;
+                    for (int a = 0; a < 3; ++a) {
+                        double d = p[a] - pts[3 * i + a];
+                        d -= 2.0 * nearbyint(d / 2.0); /* minimum image */
+                        r2 += d * d;
+                    }
+                    const double s = sigma[i];
+                    if (r2 <= cutoff * cutoff * s * s)
+                        acc += (amp ? amp[i] : 1.0) * exp(-r2 / (2.0 * s * s));
+                }
+                rho[idx3(n, z, y, x)] = acc;
+            }
+        }
+    }
+}
+
+/* Unit quaternion (w,x,y,z) -> proper orthogonal 3x3 matrix, row-major. */
+void or_quat_to_rot(const double *q_in, double *R)
+{
+    double nrm = sqrt(q_in[0] * q_in[0] + q_in[1] * q_in[1] +
+                      q_in[2] * q_in[2] + q_in[3] * q_in[3]);
+    double w = q_in[0] / nrm, x = q_in[1] / nrm, y = q_in[2] / nrm, z = q_in[3] / nrm;
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+/* Periodic trilinear sample of a grid at continuous index coordinates u. */
+static double trilinear(int n, const double *g, const double u[3])
+{
+    long i0[3];
+    double f[3];
+    for (int a = 0; a < 3; ++a) {
+        double fl = floor(u[a]);
+        i0[a] = (long)fl;
+        f[a] = u[a] - fl;
+    }
+    double acc = 0.0;
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+                double w = (dx ? f[0] : 1 - f[0]) * (dy ? f[1] : 1 - f[1]) *
+                           (dz ? f[2] : 1 - f[2]);
+                acc += w * g[idx3(n, wrap(i0[2] + dz, n), wrap(i0[1] + dy, n),
+                                  wrap(i0[0] + dx, n))];
+            }
+    return acc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Rotated moving density, Section 2.4 "Motion Decomposition":          */
+/*   rho2^R(p) = rho2(R^T p), sampled at the nodes by periodic          */
+/*   trilinear interpolation of the rho2 grid.                          */
+/* ------------------------------------------------------------------ */
+void or_resample(int n, const double *rho, const double *R, double *out)
+{
+    const double h = 2.0 / n;
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < n; ++z)
+        for (int y = 0; y < n; ++y)
+            for (int x = 0; x < n; ++x) {
+                const double p[3] = {-1.0 + x * h, -1.0 + y * h, -1.0 + z * h};
+                double u[3];
+                for (int a = 0; a < 3; ++a) {
+                    /* (R^T p)_a = sum_b R[b][a] p_b, then to index units */
+                    double q = R[0 * 3 + a] * p[0] + R[1 * 3 + a] * p[1] + R[2 * 3 + a] * p[2];
+                    u[a] = (q + 1.0) / h;
+                }
+                out[idx3(n, z, y, x)] = trilinear(n, rho, u);
+            }
+}
+
+/* ------------------------------------------------------------------ */
+/* Discrete Fourier transform, Eqs. 7a/7b and Section 3.2:              */
+/* recursive mixed-radix Cooley-Tukey, decimation in time.  A length    */
+/* n = p*m splits into p interleaved subsequences of length m whose     */
+/* transforms Y_r combine as X[k + s*m] = sum_r W_n^{r(k+s*m)} Y_r[k].  */
+/* A prime length falls back to the direct DFT sum.                     */
+/* sign = -1 forward, +1 inverse (unscaled both ways).                  */
+/* ------------------------------------------------------------------ */
+static int smallest_factor(int n)
+{
+    for (int p = 2; p * p <= n; ++p)
+        if (n % p == 0) return p;
+    return n;
+}
+
+static void fft_rec(int n, const cplx *in, long stride, cplx *out, int sign)
+{
+    if (n == 1) { out[0] = in[0]; return; }
+    int p = smallest_factor(n);
+    if (p == n) { /* direct DFT of a prime length */
+        for (int k = 0; k < n; ++k) {
+            cplx acc = 0;
+            for (int j = 0; j < n; ++j)
+                acc += in[j * stride] * cexp(sign * 2.0 * PI * I * (double)((long)j * k % n) / n);
+            out[k] = acc;
+        }
+        return;
+    }
+    int m = n / p;
+    cplx *sub = malloc(sizeof(cplx) * n);
+    for (int r = 0; r < p; ++r)
+        fft_rec(m, in + r * stride, stride * p, sub + r * m, sign);
+    for (int k = 0; k < m; ++k)
+        for (int s = 0; s < p; ++s) {
+            int kk = k + s * m;
+            cplx acc = 0;
+            for (int r = 0; r < p; ++r)
+                acc += sub[r * m + k] * cexp(sign * 2.0 * PI * I * (double)((long)r * kk % n) / n);
+            out[kk] = acc;
+        }
+    free(sub);
+}
+
+void or_fft1d(int n, const double *in_ri, double *out_ri, int sign)
+{
+    fft_rec(n, (const cplx *)in_ri, 1, (cplx *)out_ri, sign);
+}
+
+/* Full complex 3D DFT of an n^3 array ([z][y][x]), one axis at a time. */
+void or_fft3d(int n, double *data_ri, int sign)
+{
+    cplx *a = (cplx *)data_ri;
+    for (int axis = 0; axis < 3; ++axis) {
+        long st = axis == 0 ? 1 : axis == 1 ? n : (long)n * n;
+#pragma omp parallel
+        {
+            cplx *line = malloc(sizeof(cplx) * n), *res = malloc(sizeof(cplx) * n);
+#pragma omp for schedule(static)
+            for (long l = 0; l < (long)n * n; ++l) {
+                int u = (int)(l % n), v = (int)(l / n);
+                long base = axis == 0 ? idx3(n, v, u, 0)
+                          : axis == 1 ? idx3(n, v, 0, u)
+                                      : idx3(n, 0, v, u);
+                for (int i = 0; i < n; ++i) line[i] = a[base + i * st];
+                fft_rec(n, line, 1, res, sign);
+                for (int i = 0; i < n; ++i) a[base + i * st] = res[i];
+            }
+            free(line);
+            free(res);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Direct translational cross-correlation, Eqs. 1 and 3 as a Riemann    */
+/* sum over the periodic grid:                                          */
+/*   E[j] = h^3 sum_n rho1[n] rho2R[(n - j) mod N]                       */
+/* O(N^6); only for small grids.                                        */
+/* ------------------------------------------------------------------ */
+void or_correlate_direct(int n, const double *rho1, const double *rho2r, double *E)
+{
+    const double h = 2.0 / n, dv = h * h * h;
+#pragma omp parallel for schedule(dynamic)
+    for (int jz = 0; jz < n; ++jz)
+        for (int jy = 0; jy < n; ++jy)
+            for (int jx = 0; jx < n; ++jx) {
+                double acc = 0.0;
+                for (int z = 0; z < n; ++z)
+                    for (int y = 0; y < n; ++y)
+                        for (int x = 0; x < n; ++x)
+                            acc += rho1[idx3(n, z, y, x)] *
+                                   rho2r[idx3(n, wrap(z - jz, n), wrap(y - jy, n), wrap(x - jx, n))];
+                E[idx3(n, jz, jy, jx)] = dv * acc;
+            }
+}
+
+/* signed frequency index in [-N/2, N/2) */
+static int signed_k(int k, int n) { return k < (n + 1) / 2 ? k : k - n; }
+
+/* ------------------------------------------------------------------ */
+/* Energy and force over all lags through the convolution theorem,      */
+/* Eqs. 5 and 6a (Section 2.4) discretised per Section 3.2:             */
+/*   S_k   = h^3 * rho1^_k * conj(rho2R^_k)     (reflection = conj for   */
+/*                                               real densities)         */
+/*   E     = IDFT(S) / N^3                                               */
+/*   F_d   = -IDFT(2 pi i omega_d S) / N^3,  omega_d = k~_d / (N h),     */
+/*           multiplier 0 on each axis' Nyquist index (even N).          */
+/* Outputs are real parts; E and F are real for real densities.         */
+/* ------------------------------------------------------------------ */
+void or_fields(int n, const double *rho1, const double *rho2r,
+               double *E, double *Fx, double *Fy, double *Fz)
+{
+    const long m = (long)n * n * n;
+    const double h = 2.0 / n, dv = h * h * h;
+    cplx *A = malloc(sizeof(cplx) * m), *B = malloc(sizeof(cplx) * m);
+    cplx *S = malloc(sizeof(cplx) * m), *G = malloc(sizeof(cplx) * m);
+    for (long i = 0; i < m; ++i) { A[i] = rho1[i]; B[i] = rho2r[i]; }
+    or_fft3d(n, (double *)A, -1);
+    or_fft3d(n, (double *)B, -1);
+    for (long i = 0; i < m; ++i) S[i] = dv * A[i] * conj(B[i]);
+
+    memcpy(G, S, sizeof(cplx) * m);
+    or_fft3d(n, (double *)G, +1);
+    for (long i = 0; i < m; ++i) E[i] = creal(G[i]) / (double)m;
+
+    double *outs[3] = {Fx, Fy, Fz};
+    for (int d = 0; d < 3; ++d) {
+        for (int kz = 0; kz < n; ++kz)
+            for (int ky = 0; ky < n; ++ky)
+                for (int kx = 0; kx < n; ++kx) {
+                    int kd = d == 0 ? kx : d == 1 ? ky : kz;
+                    double kt = (n % 2 == 0 && kd == n / 2) ? 0.0 : (double)signed_k(kd, n);
+                    double omega = kt / (n * h);
+                    long i = idx3(n, kz, ky, kx);
+                    G[i] = 2.0 * PI * I * omega * S[i];
+                }
+        or_fft3d(n, (double *)G, +1);
+        for (long i = 0; i < m; ++i) outs[d][i] = -creal(G[i]) / (double)m;
+    }
+    free(A); free(B); free(S); free(G);
+}
+
+/* Geodesic angle between two unit quaternions (double cover aware). */
+static double quat_angle(const double *a, const double *b)
+{
+    double d = fabs(a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + a[3] * b[3]);
+    if (d > 1.0) d = 1.0;
+    return 2.0 * acos(d);
+}
+
+/* indices of the k smallest angles (ties to the lower index), excluding `skip` */
+static void k_nearest(int nrot, const double *quats, const double *q, int skip,
+                      int k, int *out_idx, double *out_ang)
+{
+    for (int s = 0; s < k; ++s) { out_idx[s] = -1; out_ang[s] = INFINITY; }
+    for (int j = 0; j < nrot; ++j) {
+        if (j == skip) continue;
+        double th = quat_angle(q, quats + 4 * j);
+        /* insertion into the sorted k-list; strict '<' keeps lower index on ties */
+        int pos = k;
+        while (pos > 0 && th < out_ang[pos - 1]) --pos;
+        if (pos < k) {
+            for (int s = k - 1; s > pos; --s) { out_ang[s] = out_ang[s - 1]; out_idx[s] = out_idx[s - 1]; }
+            out_ang[pos] = th;
+            out_idx[pos] = j;
+        }
+    }
+}
+
+/* Matrix logarithm on SO(3): the axis-angle vector of M. */
+static void so3_log(const double *M, double *v)
+{
+    double c = (M[0] + M[4] + M[8] - 1.0) / 2.0;
+    if (c > 1.0) c = 1.0;
+    if (c < -1.0) c = -1.0;
+    double th = acos(c);
+    double w[3] = {M[7] - M[5], M[2] - M[6], M[3] - M[1]}; /* 2 sin(th) * axis */
+    if (th < 1e-6) { /* th/(2 sin th) -> 1/2 */
+        for (int a = 0; a < 3; ++a) v[a] = 0.5 * w[a];
+        return;
+    }
+    if (PI - th < 1e-6) { /* axis from the symmetric part: M + I = 2 a a^T */
+        int best = 0;
+        for (int a = 1; a < 3; ++a) if (M[4 * a] > M[4 * best]) best = a;
+        double ax[3];
+        double d = sqrt((M[4 * best] + 1.0) / 2.0);
+        for (int a = 0; a < 3; ++a) ax[a] = (a == best) ? d : (M[3 * a + best] + M[3 * best + a]) / (4.0 * d);
+        for (int a = 0; a < 3; ++a) v[a] = th * ax[a];
+        return;
+    }
+    double s = th / (2.0 * sin(th));
+    for (int a = 0; a < 3; ++a) v[a] = s * w[a];
+}
+
+/* ------------------------------------------------------------------ */
+/* Torque field by least-squares finite differences across rotations.   */
+/* The paper's rotational gradient is Eq. 6b; this path estimates the   */
+/* same quantity, T = -dE/d(theta) for world-frame perturbations        */
+/* R_j = exp([theta]x) R_i, from the energy fields of the k nearest     */
+/* sampled rotations:                                                   */
+/*   A (k x 3) rows = Log(R_j R_i^T),  b_j = E_j - E_i per cell,        */
+/*   g = (A^T A)^{-1} A^T b,  T = -g.                                   */
+/* E is nrot consecutive n^3 fields; T is nrot x 3 consecutive fields. */
+/* status[i] = 0 on success, 1 when A^T A is singular (cond > 1e16),   */
+/* in which case rotation i's torque is NaN.                            */
+/* ------------------------------------------------------------------ */
+void or_torque(int n, int nrot, const double *quats, const double *E, int knn,
+               double *T, int *status)
+{
+    const long m = (long)n * n * n;
+    for (int i = 0; i < nrot; ++i) {
+        int *nb = malloc(sizeof(int) * knn);
+        double *ang = malloc(sizeof(double) * knn);
+        double *A = malloc(sizeof(double) * 3 * knn);
+        k_nearest(nrot, quats, quats + 4 * i, i, knn, nb, ang);
+        double Ri[9], Rj[9], M[9];
+        or_quat_to_rot(quats + 4 * i, Ri);
+        int ok = 1;
+        for (int s = 0; s < knn; ++s) {
+            if (nb[s] < 0) { ok = 0; break; }
+            or_quat_to_rot(quats + 4 * nb[s], Rj);
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 3; ++c)
+                    M[3 * r + c] = Rj[3 * r + 0] * Ri[3 * c + 0] + Rj[3 * r + 1] * Ri[3 * c + 1] +
+                                   Rj[3 * r + 2] * Ri[3 * c + 2];
+            so3_log(M, A + 3 * s);
+        }
+        /* normal matrix and its inverse by the adjugate */
+        double N3[9] = {0}, Ninv[9];
+        for (int s = 0; s < knn && ok; ++s)
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 3; ++c) N3[3 * r + c] += A[3 * s + r] * A[3 * s + c];
+        double det = N3[0] * (N3[4] * N3[8] - N3[5] * N3[7]) - N3[1] * (N3[3] * N3[8] - N3[5] * N3[6]) +
+                     N3[2] * (N3[3] * N3[7] - N3[4] * N3[6]);
+        double fro = 0;
+        for (int e = 0; e < 9; ++e) fro += N3[e] * N3[e];
+        if (ok) {
+            Ninv[0] = (N3[4] * N3[8] - N3[5] * N3[7]) / det;
+            Ninv[1] = (N3[2] * N3[7] - N3[1] * N3[8]) / det;
+            Ninv[2] = (N3[1] * N3[5] - N3[2] * N3[4]) / det;
+            Ninv[3] = (N3[5] * N3[6] - N3[3] * N3[8]) / det;
+            Ninv[4] = (N3[0] * N3[8] - N3[2] * N3[6]) / det;
+            Ninv[5] = (N3[2] * N3[3] - N3[0] * N3[5]) / det;
+            Ninv[6] = (N3[3] * N3[7] - N3[4] * N3[6]) / det;
+            Ninv[7] = (N3[1] * N3[6] - N3[0] * N3[7]) / det;
+            Ninv[8] = (N3[0] * N3[4] - N3[1] * N3[3]) / det;
+            double finv = 0;
+            for (int e = 0; e < 9; ++e) finv += Ninv[e] * Ninv[e];
+            /* Frobenius condition number of the normal matrix */
+            if (!(det != 0.0) || !isfinite(finv) || sqrt(fro) * sqrt(finv) > 1e16) ok = 0;
+        }
+        status[i] = ok ? 0 : 1;
+        double *Ti = T + (long)i * 3 * m;
+        if (!ok) {
+            for (long c = 0; c < 3 * m; ++c) Ti[c] = NAN;
+        } else {
+            /* P = (A^T A)^{-1} A^T, 3 x k */
+            double *P = malloc(sizeof(double) * 3 * knn);
+            for (int r = 0; r < 3; ++r)
+                for (int s = 0; s < knn; ++s)
+                    P[r * knn + s] = Ninv[3 * r + 0] * A[3 * s + 0] + Ninv[3 * r + 1] * A[3 * s + 1] +
+                                     Ninv[3 * r + 2] * A[3 * s + 2];
+            const double *Ei = E + (long)i * m;
+#pragma omp parallel for schedule(static)
+            for (long c = 0; c < m; ++c) {
+                double g[3] = {0, 0, 0};
+                for (int s = 0; s < knn; ++s) {
+                    double b = E[(long)nb[s] * m + c] - Ei[c];
+                    for (int r = 0; r < 3; ++r) g[r] += P[r * knn + s] * b;
+                }
+                for (int r = 0; r < 3; ++r) Ti[r * m + c] = -g[r];
+            }
+            free(P);
+        }
+        free(nb); free(ang); free(A);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Pose query for the restricted-orientation mode (Section 4.2,         */
+/* "Restricted Motion DOF"): fields precomputed per sampled rotation    */
+/* are read at an arbitrary pose (t, q).                                */
+/*   rotation: the k sampled rotations nearest to q (geodesic angle),   */
+/*             weights proportional to 1/theta_j and normalised; an     */
+/*             exact hit (theta < 1e-12) returns that rotation alone.   */
+/*   translation: periodic trilinear interpolation over the lag grid at */
+/*             u = t/h (lag index j <-> translation j*h).               */
+/* fields: nrot x nf consecutive n^3 arrays; out: nf values.            */
+/* ------------------------------------------------------------------ */
+void or_query(int n, int nrot, const double *quats, const double *fields, int nf,
+              const double *t, const double *q, int k, double *out)
+{
+    const long m = (long)n * n * n;
+    const double h = 2.0 / n;
+    int *nb = malloc(sizeof(int) * k);
+    double *ang = malloc(sizeof(double) * k), *w = malloc(sizeof(double) * k);
+    double qn[4];
+    double nrm = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    for (int a = 0; a < 4; ++a) qn[a] = q[a] / nrm;
+    k_nearest(nrot, quats, qn, -1, k, nb, ang);
+    int used = k;
+    if (ang[0] < 1e-12) {
+        used = 1;
+        w[0] = 1.0;
+    } else {
+        double sw = 0;
+        for (int s = 0; s < k; ++s) { w[s] = 1.0 / ang[s]; sw += w[s]; }
+        for (int s = 0; s < k; ++s) w[s] /= sw;
+    }
+    double u[3] = {t[0] / h, t[1] / h, t[2] / h};
+    for (int f = 0; f < nf; ++f) {
+        double acc = 0;
+        for (int s = 0; s < used; ++s)
+            acc += w[s] * trilinear(n, fields + ((long)nb[s] * nf + f) * m, u);
+        out[f] = acc;
+    }
+    free(nb); free(ang); free(w);
+}
+
+/* k nearest sampled rotations to q (exposed for tests). */
+void or_nearest(int nrot, const double *quats, const double *q, int skip, int k,
+                int *idx, double *ang)
+{
+    k_nearest(nrot, quats, q, skip, k, idx, ang);
+}
+
+void or_so3_log(const double *M, double *v) { so3_log(M, v); }
