@@ -1,0 +1,205 @@
+/*
+ * hf.h -- C ABI of the B300 geometric-energy field library.
+ *
+ * Computes, for two rigid parts given as skeletal densities on a periodic
+ * N^3 grid, the geometric energy field over all translations for each
+ * sampled rotation of the moving part, together with the force field (its
+ * translational gradient) and the torque field (its rotational gradient),
+ * and answers pose queries against the precomputed fields.  The method is
+ * Behandish & Ilies, "Haptic Assembly Using Skeletal Densities and Fourier
+ * Transforms" (ASME JCISE 16(2), 2016):
+ *
+ *   energy   f(R, t) = integral rho1(p) rho2(R^T (p - t)) dV       Eqs. 1, 3
+ *            = F^-1{ F{rho1} . (F{rho2~} o R^T) }                   Eq. 5
+ *   force    <df/dt, e> = 2 pi i F^-1{ (e . w) ... }                 Eq. 6a
+ *   torque   rotational gradient (the paper's Eq. 6b), here by least
+ *            squares over the nearest sampled rotations
+ *   query    fields precomputed per permitted orientation, read at a
+ *            pose during motion (Section 4.2, "Restricted Motion DOF")
+ *
+ * Conventions shared by every call:
+ *   grid     N^3 nodes on the periodic box [-1,1)^3, spacing h = 2/N, node
+ *            index n <-> position -1 + n h, arrays [z][y][x], x fastest,
+ *            float32.  Supported N: 32, 64, 96, 128.
+ *   lags     field index j <-> translation t = j h (periodic), lag 0 at 0.
+ *   E        = +f (the Riemann sum of Eq. 1 with volume element h^3).
+ *   F        = -grad_t E (spectral; the Nyquist multiplier on each axis is 0).
+ *   T        = -grad_theta E for world-frame perturbations R -> exp([d]x) R,
+ *            about the moving part's reference point.
+ *   rotation unit quaternion (w, x, y, z); the moving part's density at pose
+ *            (R, t) is rho2(R^T (p - t)), sampled by periodic trilinear
+ *            interpolation of its grid.
+ *
+ * Memory: pointers named d_* are device pointers owned by the caller (the
+ * library never frees them); h_* are host pointers.  Handles (hf_ctx,
+ * hf_part, hf_fieldset) are owned by the library, allocated on the context's
+ * device and charged against the context's HBM budget.
+ *
+ * Streams: every call taking an hf_stream enqueues asynchronous work on it
+ * (NULL = the legacy default stream).  Outputs are valid after the stream is
+ * synchronised.  A handle produced by a call may be used by later work on
+ * the same stream at once.
+ *
+ * Errors: every call returns an hf_status; no exception or abort crosses the
+ * ABI.  On failure the call has written no output handle, and hf_last_error()
+ * returns a message for the calling thread.
+ */
+#ifndef HF_H
+#define HF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HF_OK = 0,
+    HF_EINVAL = 1,       /* bad argument (size, pointer, flag, rank-deficient rotation set) */
+    HF_ENOMEM = 2,       /* device allocation failed */
+    HF_EBUDGET = 3,      /* the allocation would exceed the context's HBM budget */
+    HF_ECUDA = 4,        /* a CUDA runtime call failed (message has the CUDA error) */
+    HF_ETIMEOUT = 5,     /* a bounded device-side wait gave up */
+    HF_ENOTREADY = 6,    /* the field set has not been computed */
+    HF_EUNSUPPORTED = 7  /* grid size or flag combination not built */
+} hf_status;
+
+typedef struct hf_ctx hf_ctx;
+typedef struct hf_part hf_part;
+typedef struct hf_fieldset hf_fieldset;
+typedef void *hf_stream; /* a cudaStream_t */
+
+/* Part roles for hf_part_create. */
+#define HF_STATIONARY 0 /* keeps the scaled half spectrum of rho1 (Section 3.2: precomputed once) */
+#define HF_MOVING 1     /* keeps the rho2 grid, resampled per rotation */
+
+/* Field-set flags. */
+#define HF_E 0x1u           /* energy field per rotation (always held) */
+#define HF_F 0x2u           /* force field (3 components) per rotation (always held) */
+#define HF_T 0x4u           /* torque field (3 components) per rotation */
+#define HF_TORQUE_F64 0x10u /* torque differences and products in float64 on the device */
+
+/* Field indices for hf_fieldset_get / hf_fieldset_field_ptr and query outputs. */
+#define HF_FIELD_E 0
+#define HF_FIELD_FX 1
+#define HF_FIELD_FY 2
+#define HF_FIELD_FZ 3
+#define HF_FIELD_TX 4
+#define HF_FIELD_TY 5
+#define HF_FIELD_TZ 6
+
+/* Library version, e.g. "hf 1.0 sm_103a". Static storage. */
+const char *hf_version(void);
+
+/* Thread-local message describing the calling thread's last failure. */
+const char *hf_last_error(void);
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the
+ * device memory the context's handles may hold (0 = no bound).
+ * Errors: HF_EINVAL (null out, bad device), HF_ECUDA. */
+hf_status hf_ctx_create(int device, size_t hbm_budget_bytes, hf_ctx **out);
+void hf_ctx_destroy(hf_ctx *ctx);
+/* Bytes currently charged against the budget. */
+size_t hf_ctx_reserved_bytes(const hf_ctx *ctx);
+
+/* Skeletal density on the N^3 grid (the stand-in for the paper's skeletal
+ * density, Section 2.3): rho[n] = sum_i a_i exp(-|x_n - c_i|^2 / (2 sigma_i^2))
+ * over points with |x_n - c_i| <= 6 sigma_i, distances by the minimum image
+ * on the period-2 torus.  d_pts: P x 3 (x, y, z); d_sigma: P (> 0, 6 sigma < 1);
+ * d_amp: P or NULL (all 1); d_grid_out: N^3, overwritten.  Deterministic.
+ * Errors: HF_EINVAL (P < 0, null pointers), HF_EUNSUPPORTED (N), HF_ECUDA. */
+hf_status hf_density_build(hf_ctx *ctx, int n, const float *d_pts, const float *d_sigma,
+                           const float *d_amp, int P, float *d_grid_out, hf_stream stream);
+
+/* Make a part from an N^3 density grid (caller-owned, read by the call's
+ * stream work).  HF_STATIONARY parts keep (h^3/N^3) F{rho1} (Eq. 7a with the
+ * volume element and the inverse's normalisation folded in); HF_MOVING parts
+ * keep a copy of the grid.  Errors: HF_EINVAL, HF_EBUDGET, HF_ENOMEM, HF_ECUDA. */
+hf_status hf_part_create(hf_ctx *ctx, int n, const float *d_grid, int role, hf_part **out,
+                         hf_stream stream);
+void hf_part_release(hf_part *part);
+
+/* Allocate a field set for R rotations at grid size n holding the fields
+ * selected by `flags` (energy and force always; HF_T adds torque).  Bytes: R * N^3 * 4 * (#fields)
+ * plus per-set scratch.  Errors: HF_EINVAL, HF_EBUDGET, HF_ENOMEM. */
+hf_status hf_fieldset_create(hf_ctx *ctx, int n, int R, unsigned flags, hf_fieldset **out);
+
+/* Compute the fields of `fs` for the rotations h_quat (R x 4, w x y z, host,
+ * normalised by the library) of the moving part s2 against the stationary
+ * part s1 (Eqs. 3, 5, 6a per rotation; the torque by least squares over the
+ * 6 nearest rotations of the set).  R must equal the set's size; with HF_T,
+ * R >= 7.  Rotations whose neighbourhood is rank deficient get NaN torque and
+ * the call returns HF_EINVAL after enqueueing everything else.
+ * Errors: HF_EINVAL, HF_ECUDA. */
+hf_status hf_fieldset_compute(hf_ctx *ctx, const hf_part *s1, const hf_part *s2,
+                              const float *h_quat, int R, hf_fieldset *fs, hf_stream stream);
+
+/* hf_fieldset_create followed by hf_fieldset_compute. */
+hf_status hf_fieldset_build(hf_ctx *ctx, const hf_part *s1, const hf_part *s2,
+                            const float *h_quat, int R, unsigned flags, hf_fieldset **out,
+                            hf_stream stream);
+
+/* Copy field `field` (HF_FIELD_*) of rotation `rot` (N^3 floats) to d_dst.
+ * Errors: HF_EINVAL (index out of range or field not held), HF_ENOTREADY, HF_ECUDA. */
+hf_status hf_fieldset_get(const hf_fieldset *fs, int rot, int field, float *d_dst, hf_stream stream);
+
+/* Device pointer to field `field` of rotation `rot` inside the set (valid until
+ * the set is released).  Errors as hf_fieldset_get. */
+hf_status hf_fieldset_field_ptr(const hf_fieldset *fs, int rot, int field, const float **d_ptr);
+
+/* Field-set geometry. */
+int hf_fieldset_n(const hf_fieldset *fs);
+int hf_fieldset_rotations(const hf_fieldset *fs);
+unsigned hf_fieldset_flags(const hf_fieldset *fs);
+void hf_fieldset_release(hf_fieldset *fs);
+
+/* Pose query (Section 4.2): the k_blend sampled rotations nearest to q by
+ * geodesic angle (ties to the lower index), weights 1/theta normalised (an
+ * exact hit, theta < 1e-12, returns that rotation alone); per rotation,
+ * periodic trilinear interpolation of each held field at lag u = t/h.
+ * out7 = (E, Fx, Fy, Fz, Tx, Ty, Tz); fields not held read 0.  Host in/out;
+ * synchronous (runs on an internal high-priority stream).
+ * Errors: HF_EINVAL (k_blend outside 1..8 or > R), HF_ENOTREADY, HF_ECUDA. */
+hf_status hf_query(const hf_fieldset *fs, const float t[3], const float q[4], int k_blend,
+                   float out7[7]);
+
+/* Batched pose query on the caller's stream: d_tq is Q x 7 floats
+ * (tx, ty, tz, qw, qx, qy, qz); d_out is Q x 7 floats as in hf_query. */
+hf_status hf_query_batch(const hf_fieldset *fs, const float *d_tq, int Q, int k_blend,
+                         float *d_out, hf_stream stream);
+
+/* ---- single-step entry points (each step of the path on its own) ---- */
+
+/* Rotated resample (Section 2.4, motion decomposition):
+ * d_out[n] = trilinear_periodic(d_rho, R^T x_n) for the 3x3 row-major h_R. */
+hf_status hf_resample(int n, const float *d_rho, const float h_R[9], float *d_out, hf_stream stream);
+
+/* Forward 3D real-to-complex DFT (Eq. 7a, unscaled, e^{-2 pi i k n / N}) of
+ * d_in (N^3 floats).  d_out: N x N x (N/2+1) complex64 as interleaved floats,
+ * [kz][ky][kx] in natural frequency order.  d_scratch: at least
+ * hf_rfft3d_scratch_bytes(n) bytes of device memory, 16-byte aligned. */
+size_t hf_rfft3d_scratch_bytes(int n);
+hf_status hf_rfft3d(int n, const float *d_in, float *d_out, void *d_scratch, hf_stream stream);
+
+/* Energy and force for one rotation into explicit buffers (Eqs. 3, 5, 6a):
+ * d_E, d_Fx, d_Fy, d_Fz are N^3 floats each (the force pointers may be NULL);
+ * d_scratch: at least hf_fields_scratch_bytes(n) bytes, 16-byte aligned. */
+size_t hf_fields_scratch_bytes(int n);
+hf_status hf_fields(hf_ctx *ctx, const hf_part *s1, const hf_part *s2, const float h_quat[4],
+                    float *d_E, float *d_Fx, float *d_Fy, float *d_Fz, void *d_scratch,
+                    hf_stream stream);
+
+/* Torque by least squares over the 6 nearest rotations for explicit
+ * buffers: d_E is R x N^3, d_T is R x 3 x N^3, h_quat R x 4.  flags may hold
+ * HF_TORQUE_F64.  h_status (R ints, may be NULL) receives 0 or 1 (rank
+ * deficient: NaN torque).  Errors: HF_EINVAL (R < 7 or a rank-deficient
+ * rotation), HF_ENOMEM, HF_ECUDA. */
+hf_status hf_torque(hf_ctx *ctx, int n, int R, const float *h_quat, const float *d_E, float *d_T,
+                    unsigned flags, int *h_status, hf_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HF_H */

@@ -1,0 +1,703 @@
+// hf_api.cu -- the C ABI declared in include/hf.h: contexts, parts, field
+// sets, budget accounting, the float64 host set-up of the rotation
+// neighbourhoods for the torque, and the pose-query entry points.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "hf.h"
+#include "hf_internal.h"
+
+using hf::FieldPtrs;
+
+// ------------------------------------------------------------------ errors
+static thread_local char g_err[512] = "";
+
+static hf_status fail(hf_status s, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+#define CU(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(e_ == cudaErrorMemoryAllocation ? HF_ENOMEM : HF_ECUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                        \
+    } while (0)
+
+// ------------------------------------------------------------------ handles
+struct hf_ctx {
+    int device = 0;
+    size_t budget = 0, reserved = 0;
+    std::mutex mu;
+    cudaStream_t qstream = nullptr;             // high-priority stream for hf_query
+    float *h_qin = nullptr, *h_qout = nullptr;  // pinned 7-float mailboxes
+    float *d_qin = nullptr, *d_qout = nullptr;
+    std::mutex qmu;
+};
+
+struct hf_part {
+    hf_ctx *ctx;
+    int n, role;
+    float *grid;   // HF_MOVING: N^3
+    float2 *spec;  // HF_STATIONARY: (h^3/N^3) rho1^ in [ky*][kz*][kx*] slot order
+    size_t bytes;
+};
+
+struct hf_fieldset {
+    hf_ctx *ctx = nullptr;
+    int n = 0, R = 0;
+    unsigned flags = 0;
+    int nf = 0;                  // fields held per rotation
+    int slot[7];                 // field index -> slot within a rotation block, -1 if not held
+    float *data = nullptr;       // R x nf x N^3
+    float2 *scratch = nullptr;   // 3 x chunk x N*N*(N/2+1): X1, Y1, Y2
+    float *d_rot9 = nullptr;     // R x 9
+    double *d_quat = nullptr;    // R x 4 (normalised)
+    int *d_nbr = nullptr;        // R x 6
+    float *d_P = nullptr;        // R x 18
+    double *d_P64 = nullptr;     // R x 18
+    int chunk = 1;
+    bool ready = false;
+    size_t bytes = 0;
+    void *h_stage = nullptr;     // pinned staging for the per-call uploads
+    size_t stage_bytes = 0;
+    cudaEvent_t stage_done = nullptr;  // the last uploads from h_stage have been consumed
+};
+
+static bool charge(hf_ctx *c, size_t b) {
+    std::lock_guard<std::mutex> g(c->mu);
+    if (c->budget && c->reserved + b > c->budget) return false;
+    c->reserved += b;
+    return true;
+}
+static void uncharge(hf_ctx *c, size_t b) {
+    std::lock_guard<std::mutex> g(c->mu);
+    c->reserved -= std::min(b, c->reserved);
+}
+
+extern "C" const char *hf_version(void) { return "hf 1.0 sm_103a"; }
+extern "C" const char *hf_last_error(void) { return g_err; }
+
+extern "C" hf_status hf_ctx_create(int device, size_t budget, hf_ctx **out) {
+    if (!out) return fail(HF_EINVAL, "hf_ctx_create: out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    CU(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(HF_EINVAL, "hf_ctx_create: device %d of %d", device, ndev);
+    CU(cudaSetDevice(device));
+    hf_ctx *c = new (std::nothrow) hf_ctx();
+    if (!c) return fail(HF_ENOMEM, "hf_ctx_create: host allocation");
+    c->device = device;
+    c->budget = budget;
+    int lo = 0, hi = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->qstream, cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_qin, 8 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_qout, 8 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_qin, 8 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_qout, 8 * sizeof(float));
+    for (int n : {32, 64, 96, 128})
+        if (e == cudaSuccess) e = hf::fft_init_attrs(n);
+    if (e != cudaSuccess) {
+        hf_ctx_destroy(c);
+        return fail(HF_ECUDA, "hf_ctx_create: %s", cudaGetErrorString(e));
+    }
+    *out = c;
+    return HF_OK;
+}
+
+extern "C" void hf_ctx_destroy(hf_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->qstream) cudaStreamDestroy(c->qstream);
+    if (c->h_qin) cudaFreeHost(c->h_qin);
+    if (c->h_qout) cudaFreeHost(c->h_qout);
+    if (c->d_qin) cudaFree(c->d_qin);
+    if (c->d_qout) cudaFree(c->d_qout);
+    delete c;
+}
+
+extern "C" size_t hf_ctx_reserved_bytes(const hf_ctx *c) {
+    if (!c) return 0;
+    std::lock_guard<std::mutex> g(const_cast<hf_ctx *>(c)->mu);
+    return c->reserved;
+}
+
+// ------------------------------------------------------------------ density
+extern "C" hf_status hf_density_build(hf_ctx *ctx, int n, const float *d_pts, const float *d_sigma,
+                                      const float *d_amp, int P, float *d_grid_out, hf_stream stream) {
+    if (!ctx) return fail(HF_EINVAL, "hf_density_build: ctx is NULL");
+    if (!hf::supported_n(n)) return fail(HF_EUNSUPPORTED, "hf_density_build: N=%d not supported", n);
+    if (P < 0 || !d_grid_out || (P > 0 && (!d_pts || !d_sigma)))
+        return fail(HF_EINVAL, "hf_density_build: bad arguments (P=%d)", P);
+    CU(cudaSetDevice(ctx->device));
+    CU(hf::run_splat(n, d_pts, d_sigma, d_amp, P, d_grid_out, (cudaStream_t)stream));
+    return HF_OK;
+}
+
+// --------------------------------------------------------------------- parts
+static const float kIdentity9[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};  // static: outlives async copies
+
+static hf_status stationary_spectrum(int n, const float *d_grid, float2 *spec, float scale, cudaStream_t st) {
+    // identity "rotation": pass A's resample is then an exact copy
+    const size_t he = hf::half_spec_elems(n);
+    float2 *X1 = nullptr;
+    float *rot = nullptr;
+    CU(cudaMallocAsync(&X1, he * sizeof(float2), st));
+    CU(cudaMallocAsync(&rot, 9 * sizeof(float), st));
+    CU(cudaMemcpyAsync(rot, kIdentity9, sizeof kIdentity9, cudaMemcpyHostToDevice, st));
+    CU(hf::run_passA(n, d_grid, rot, X1, 1, st));
+    CU(hf::run_passB_forward(n, X1, spec, scale, st));
+    CU(cudaFreeAsync(X1, st));
+    CU(cudaFreeAsync(rot, st));
+    return HF_OK;
+}
+
+extern "C" hf_status hf_part_create(hf_ctx *ctx, int n, const float *d_grid, int role, hf_part **out,
+                                    hf_stream stream) {
+    if (!ctx || !out || !d_grid) return fail(HF_EINVAL, "hf_part_create: NULL argument");
+    *out = nullptr;
+    if (!hf::supported_n(n)) return fail(HF_EUNSUPPORTED, "hf_part_create: N=%d not supported", n);
+    if (role != HF_STATIONARY && role != HF_MOVING) return fail(HF_EINVAL, "hf_part_create: role %d", role);
+    CU(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n3 = (size_t)n * n * n;
+    const size_t bytes = role == HF_MOVING ? n3 * sizeof(float) : hf::half_spec_elems(n) * sizeof(float2);
+    if (!charge(ctx, bytes)) return fail(HF_EBUDGET, "hf_part_create: %zu bytes exceed the budget", bytes);
+    hf_part *p = new (std::nothrow) hf_part{ctx, n, role, nullptr, nullptr, bytes};
+    if (!p) {
+        uncharge(ctx, bytes);
+        return fail(HF_ENOMEM, "hf_part_create: host allocation");
+    }
+    void *mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, bytes);
+    if (e != cudaSuccess) {
+        delete p;
+        uncharge(ctx, bytes);
+        return fail(HF_ENOMEM, "hf_part_create: cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    hf_status s = HF_OK;
+    if (role == HF_MOVING) {
+        p->grid = (float *)mem;
+        e = cudaMemcpyAsync(p->grid, d_grid, bytes, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) s = fail(HF_ECUDA, "hf_part_create: %s", cudaGetErrorString(e));
+    } else {
+        p->spec = (float2 *)mem;
+        // h^3 / N^3 in float64: the Riemann-sum volume element of Eq. 1 and
+        // the inverse transform's normalisation, rounded once
+        const double h = 2.0 / n;
+        const double scale = h * h * h / ((double)n * n * n);
+        s = stationary_spectrum(n, d_grid, p->spec, (float)scale, st);
+    }
+    if (s != HF_OK) {
+        cudaFree(mem);
+        delete p;
+        uncharge(ctx, bytes);
+        return s;
+    }
+    *out = p;
+    return HF_OK;
+}
+
+extern "C" void hf_part_release(hf_part *p) {
+    if (!p) return;
+    cudaSetDevice(p->ctx->device);
+    cudaFree(p->grid ? (void *)p->grid : (void *)p->spec);
+    uncharge(p->ctx, p->bytes);
+    delete p;
+}
+
+// ---------------------------------------------- rotation set-up (float64)
+namespace {
+
+struct Quat {
+    double w, x, y, z;
+};
+
+Quat qnorm(const float *q) {
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    const double n = sqrt(w * w + x * x + y * y + z * z);
+    return {w / n, x / n, y / n, z / n};
+}
+
+bool qfinite(const Quat &q) { return isfinite(q.w) && isfinite(q.x) && isfinite(q.y) && isfinite(q.z); }
+
+void rot_from_quat(const Quat &q, double R[9]) {
+    const double w = q.w, x = q.x, y = q.y, z = q.z;
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+// axis-angle vector of R_j R_i^T, from the relative quaternion q_j * conj(q_i)
+void rel_log(const Quat &qi, const Quat &qj, double v[3]) {
+    const double w = qj.w * qi.w + qj.x * qi.x + qj.y * qi.y + qj.z * qi.z;
+    double x = -qj.w * qi.x + qj.x * qi.w - qj.y * qi.z + qj.z * qi.y;
+    double y = -qj.w * qi.y + qj.x * qi.z + qj.y * qi.w - qj.z * qi.x;
+    double z = -qj.w * qi.z - qj.x * qi.y + qj.y * qi.x + qj.z * qi.w;
+    double ww = w;
+    if (ww < 0) { ww = -ww; x = -x; y = -y; z = -z; }
+    const double s = sqrt(x * x + y * y + z * z);
+    if (s < 1e-300) { v[0] = v[1] = v[2] = 0; return; }
+    const double th = 2.0 * atan2(s, ww);
+    v[0] = th * x / s;
+    v[1] = th * y / s;
+    v[2] = th * z / s;
+}
+
+// 6 nearest rotations by |q_i . q_j| (i.e. geodesic angle), ties to the lower index
+void nearest6(const std::vector<Quat> &Q, int i, int nb[6]) {
+    double bd[6];
+    for (int s = 0; s < 6; ++s) { bd[s] = -1.0; nb[s] = -1; }
+    const Quat &a = Q[i];
+    for (int j = 0; j < (int)Q.size(); ++j) {
+        if (j == i) continue;
+        double d = fabs(a.w * Q[j].w + a.x * Q[j].x + a.y * Q[j].y + a.z * Q[j].z);
+        if (d > 1.0) d = 1.0;
+        if (d <= bd[5]) continue;
+        int pos = 5;
+        while (pos > 0 && d > bd[pos - 1]) --pos;
+        for (int s = 5; s > pos; --s) { bd[s] = bd[s - 1]; nb[s] = nb[s - 1]; }
+        bd[pos] = d;
+        nb[pos] = j;
+    }
+}
+
+// P = (A^T A)^{-1} A^T for the 6 x 3 A; false when A^T A is numerically singular
+bool ls_pinv(const double A[6][3], double P[3][6]) {
+    double N[3][3] = {};
+    for (int s = 0; s < 6; ++s)
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) N[r][c] += A[s][r] * A[s][c];
+    double inv[3][3];
+    inv[0][0] = N[1][1] * N[2][2] - N[1][2] * N[2][1];
+    inv[0][1] = N[0][2] * N[2][1] - N[0][1] * N[2][2];
+    inv[0][2] = N[0][1] * N[1][2] - N[0][2] * N[1][1];
+    inv[1][0] = N[1][2] * N[2][0] - N[1][0] * N[2][2];
+    inv[1][1] = N[0][0] * N[2][2] - N[0][2] * N[2][0];
+    inv[1][2] = N[0][2] * N[1][0] - N[0][0] * N[1][2];
+    inv[2][0] = N[1][0] * N[2][1] - N[1][1] * N[2][0];
+    inv[2][1] = N[0][1] * N[2][0] - N[0][0] * N[2][1];
+    inv[2][2] = N[0][0] * N[1][1] - N[0][1] * N[1][0];
+    const double det = N[0][0] * inv[0][0] + N[0][1] * inv[1][0] + N[0][2] * inv[2][0];
+    if (!(det != 0.0) || !isfinite(det)) return false;
+    double fn = 0, fi = 0;
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            inv[r][c] /= det;
+            fn += N[r][c] * N[r][c];
+            fi += inv[r][c] * inv[r][c];
+        }
+    if (!isfinite(fi) || sqrt(fn) * sqrt(fi) > 1e16) return false;  // Frobenius condition of A^T A
+    for (int r = 0; r < 3; ++r)
+        for (int s = 0; s < 6; ++s) P[r][s] = inv[r][0] * A[s][0] + inv[r][1] * A[s][1] + inv[r][2] * A[s][2];
+    return true;
+}
+
+// neighbour indices and least-squares operators for every rotation; returns
+// the number of rank-deficient rotations (their operator entries are NaN)
+int torque_setup(const std::vector<Quat> &Q, std::vector<int> &nbr, std::vector<float> &P32,
+                 std::vector<double> &P64, int *h_status) {
+    const int R = (int)Q.size();
+    nbr.assign((size_t)R * 6, 0);
+    P32.assign((size_t)R * 18, 0.f);
+    P64.assign((size_t)R * 18, 0.0);
+    int bad = 0;
+    for (int i = 0; i < R; ++i) {
+        int nb[6];
+        nearest6(Q, i, nb);
+        double A[6][3], P[3][6];
+        bool ok = true;
+        for (int s = 0; s < 6; ++s) {
+            if (nb[s] < 0) { ok = false; break; }
+            rel_log(Q[i], Q[nb[s]], A[s]);
+        }
+        ok = ok && ls_pinv(A, P);
+        for (int s = 0; s < 6; ++s) nbr[(size_t)6 * i + s] = nb[s] < 0 ? i : nb[s];
+        for (int r = 0; r < 3; ++r)
+            for (int s = 0; s < 6; ++s) {
+                const double v = ok ? P[r][s] : NAN;
+                P64[(size_t)18 * i + 6 * r + s] = v;
+                P32[(size_t)18 * i + 6 * r + s] = (float)v;
+            }
+        if (h_status) h_status[i] = ok ? 0 : 1;
+        bad += ok ? 0 : 1;
+    }
+    return bad;
+}
+
+int default_chunk(int n) {
+    const char *env = getenv("HF_ROT_CHUNK");
+    if (env && atoi(env) > 0) return atoi(env);
+    switch (n) {
+        case 32: return 64;
+        case 64: return 32;
+        case 96: return 12;
+        default: return 8;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- fieldsets
+extern "C" hf_status hf_fieldset_create(hf_ctx *ctx, int n, int R, unsigned flags, hf_fieldset **out) {
+    if (!ctx || !out) return fail(HF_EINVAL, "hf_fieldset_create: NULL argument");
+    *out = nullptr;
+    if (!hf::supported_n(n)) return fail(HF_EUNSUPPORTED, "hf_fieldset_create: N=%d not supported", n);
+    if (R <= 0) return fail(HF_EINVAL, "hf_fieldset_create: R=%d", R);
+    flags |= HF_E | HF_F;  // energy and force are always held
+    if ((flags & HF_T) && R < 7) return fail(HF_EINVAL, "hf_fieldset_create: torque needs R >= 7 (R=%d)", R);
+    CU(cudaSetDevice(ctx->device));
+    hf_fieldset *fs = new (std::nothrow) hf_fieldset();
+    if (!fs) return fail(HF_ENOMEM, "hf_fieldset_create: host allocation");
+    fs->ctx = ctx;
+    fs->n = n;
+    fs->R = R;
+    fs->flags = flags;
+    int nf = 0;
+    for (int f = 0; f < 7; ++f) fs->slot[f] = -1;
+    fs->slot[0] = nf++;
+    if (flags & HF_F)
+        for (int f = 1; f <= 3; ++f) fs->slot[f] = nf++;
+    if (flags & HF_T)
+        for (int f = 4; f <= 6; ++f) fs->slot[f] = nf++;
+    fs->nf = nf;
+    fs->chunk = std::min(default_chunk(n), R);
+    const size_t n3 = (size_t)n * n * n;
+    const size_t data_b = (size_t)R * nf * n3 * sizeof(float);
+    const size_t scr_b = 3 * (size_t)fs->chunk * hf::half_spec_elems(n) * sizeof(float2);
+    fs->stage_bytes = (size_t)R * (9 * sizeof(float) + 4 * sizeof(double) + 6 * sizeof(int) + 18 * sizeof(float) +
+                                   18 * sizeof(double));
+    fs->bytes = data_b + scr_b + fs->stage_bytes;
+    if (!charge(ctx, fs->bytes)) {
+        const size_t b = fs->bytes;
+        delete fs;
+        return fail(HF_EBUDGET, "hf_fieldset_create: %zu bytes exceed the budget", b);
+    }
+    cudaError_t e = cudaMalloc(&fs->data, data_b);
+    if (e == cudaSuccess) e = cudaMalloc(&fs->scratch, scr_b);
+    if (e == cudaSuccess) e = cudaMalloc(&fs->d_rot9, (size_t)R * 9 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&fs->d_quat, (size_t)R * 4 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&fs->d_nbr, (size_t)R * 6 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&fs->d_P, (size_t)R * 18 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&fs->d_P64, (size_t)R * 18 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&fs->h_stage, fs->stage_bytes);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fs->stage_done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        hf_fieldset_release(fs);
+        return fail(e == cudaErrorMemoryAllocation ? HF_ENOMEM : HF_ECUDA, "hf_fieldset_create: %s",
+                    cudaGetErrorString(e));
+    }
+    *out = fs;
+    return HF_OK;
+}
+
+extern "C" void hf_fieldset_release(hf_fieldset *fs) {
+    if (!fs) return;
+    cudaSetDevice(fs->ctx->device);
+    cudaFree(fs->data);
+    cudaFree(fs->scratch);
+    cudaFree(fs->d_rot9);
+    cudaFree(fs->d_quat);
+    cudaFree(fs->d_nbr);
+    cudaFree(fs->d_P);
+    cudaFree(fs->d_P64);
+    if (fs->h_stage) cudaFreeHost(fs->h_stage);
+    if (fs->stage_done) cudaEventDestroy(fs->stage_done);
+    uncharge(fs->ctx, fs->bytes);
+    delete fs;
+}
+
+extern "C" int hf_fieldset_n(const hf_fieldset *fs) { return fs ? fs->n : 0; }
+extern "C" int hf_fieldset_rotations(const hf_fieldset *fs) { return fs ? fs->R : 0; }
+extern "C" unsigned hf_fieldset_flags(const hf_fieldset *fs) { return fs ? fs->flags : 0u; }
+
+// the energy/force passes for `cnt` rotations whose float matrices are at
+// rot9 (cnt x 9, device); outputs through `out` (first rotation at out.E)
+static hf_status run_fields(int n, const hf_part *s1, const hf_part *s2, const float *rot9, int cnt,
+                            float2 *scratch, size_t scratch_rot, FieldPtrs out, cudaStream_t st) {
+    float2 *X1 = scratch, *Y1 = scratch + scratch_rot, *Y2 = scratch + 2 * scratch_rot;
+    CU(hf::run_passA(n, s2->grid, rot9, X1, cnt, st));
+    CU(hf::run_passB(n, X1, s1->spec, Y1, Y2, cnt, st));
+    CU(hf::run_passC(n, Y1, Y2, out, cnt, st));
+    return HF_OK;
+}
+
+static hf_status check_pair(const hf_part *s1, const hf_part *s2, int n, const char *who) {
+    if (!s1 || !s2) return fail(HF_EINVAL, "%s: NULL part", who);
+    if (s1->role != HF_STATIONARY || s2->role != HF_MOVING)
+        return fail(HF_EINVAL, "%s: s1 must be HF_STATIONARY and s2 HF_MOVING", who);
+    if (s1->n != n || s2->n != n) return fail(HF_EINVAL, "%s: grid sizes differ (%d, %d, %d)", who, s1->n, s2->n, n);
+    return HF_OK;
+}
+
+extern "C" hf_status hf_fieldset_compute(hf_ctx *ctx, const hf_part *s1, const hf_part *s2, const float *h_quat,
+                                         int R, hf_fieldset *fs, hf_stream stream) {
+    if (!ctx || !fs || !h_quat) return fail(HF_EINVAL, "hf_fieldset_compute: NULL argument");
+    if (R != fs->R) return fail(HF_EINVAL, "hf_fieldset_compute: R=%d but the set holds %d", R, fs->R);
+    hf_status s = check_pair(s1, s2, fs->n, "hf_fieldset_compute");
+    if (s != HF_OK) return s;
+    CU(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = fs->n;
+    std::vector<Quat> Q(R);
+    for (int r = 0; r < R; ++r) {
+        Q[r] = qnorm(h_quat + 4 * (size_t)r);
+        if (!qfinite(Q[r])) return fail(HF_EINVAL, "hf_fieldset_compute: quaternion %d is zero or not finite", r);
+    }
+    int bad = 0;
+    std::vector<int> nbr;
+    std::vector<float> P32;
+    std::vector<double> P64;
+    if (fs->flags & HF_T) bad = torque_setup(Q, nbr, P32, P64, nullptr);
+    // stage through pinned memory once the previous call's uploads are done
+    CU(cudaEventSynchronize(fs->stage_done));
+    float *s_rot = (float *)fs->h_stage;
+    double *s_q = (double *)(s_rot + (size_t)9 * R);
+    int *s_nbr = (int *)(s_q + (size_t)4 * R);
+    float *s_P = (float *)(s_nbr + (size_t)6 * R);
+    double *s_P64 = (double *)(s_P + (size_t)18 * R);
+    for (int r = 0; r < R; ++r) {
+        double M[9];
+        rot_from_quat(Q[r], M);
+        for (int k = 0; k < 9; ++k) s_rot[(size_t)9 * r + k] = (float)M[k];
+        s_q[4 * (size_t)r + 0] = Q[r].w;
+        s_q[4 * (size_t)r + 1] = Q[r].x;
+        s_q[4 * (size_t)r + 2] = Q[r].y;
+        s_q[4 * (size_t)r + 3] = Q[r].z;
+    }
+    fs->ready = false;
+    CU(cudaMemcpyAsync(fs->d_rot9, s_rot, (size_t)R * 9 * sizeof(float), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(fs->d_quat, s_q, (size_t)R * 4 * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (fs->flags & HF_T) {
+        memcpy(s_nbr, nbr.data(), nbr.size() * sizeof(int));
+        memcpy(s_P, P32.data(), P32.size() * sizeof(float));
+        memcpy(s_P64, P64.data(), P64.size() * sizeof(double));
+        CU(cudaMemcpyAsync(fs->d_nbr, s_nbr, nbr.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        CU(cudaMemcpyAsync(fs->d_P, s_P, P32.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+        CU(cudaMemcpyAsync(fs->d_P64, s_P64, P64.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    }
+    CU(cudaEventRecord(fs->stage_done, st));
+    const size_t n3 = (size_t)n * n * n;
+    const size_t rs = (size_t)fs->nf * n3;
+    const size_t scr_rot = (size_t)fs->chunk * hf::half_spec_elems(n);
+    for (int r0 = 0; r0 < R; r0 += fs->chunk) {
+        const int cnt = std::min(fs->chunk, R - r0);
+        FieldPtrs out;
+        float *base = fs->data + (size_t)r0 * rs;
+        out.E = base;
+        out.rot_stride = rs;
+        out.Fx = base + n3;
+        out.Fy = base + 2 * n3;
+        out.Fz = base + 3 * n3;
+        s = run_fields(n, s1, s2, fs->d_rot9 + (size_t)9 * r0, cnt, fs->scratch, scr_rot, out, st);
+        if (s != HF_OK) return s;
+    }
+    if (fs->flags & HF_T) {
+        CU(hf::run_torque(n, R, fs->data, rs, fs->data + (size_t)fs->slot[4] * n3, rs, fs->d_nbr, fs->d_P,
+                          fs->d_P64, (fs->flags & HF_TORQUE_F64) != 0, st));
+    }
+    fs->ready = true;
+    if (bad) return fail(HF_EINVAL, "hf_fieldset_compute: %d rotation(s) with a rank-deficient neighbourhood", bad);
+    return HF_OK;
+}
+
+extern "C" hf_status hf_fieldset_build(hf_ctx *ctx, const hf_part *s1, const hf_part *s2, const float *h_quat,
+                                       int R, unsigned flags, hf_fieldset **out, hf_stream stream) {
+    if (!out) return fail(HF_EINVAL, "hf_fieldset_build: out is NULL");
+    *out = nullptr;
+    if (!s2) return fail(HF_EINVAL, "hf_fieldset_build: NULL part");
+    hf_fieldset *fs = nullptr;
+    hf_status s = hf_fieldset_create(ctx, s2->n, R, flags, &fs);
+    if (s != HF_OK) return s;
+    s = hf_fieldset_compute(ctx, s1, s2, h_quat, R, fs, stream);
+    if (s != HF_OK && !fs->ready) {
+        const hf_status keep = s;
+        char msg[sizeof g_err];
+        memcpy(msg, g_err, sizeof msg);
+        hf_fieldset_release(fs);
+        memcpy(g_err, msg, sizeof msg);
+        return keep;
+    }
+    *out = fs;
+    return s;
+}
+
+static hf_status field_check(const hf_fieldset *fs, int rot, int field, const char *who) {
+    if (!fs) return fail(HF_EINVAL, "%s: NULL field set", who);
+    if (rot < 0 || rot >= fs->R) return fail(HF_EINVAL, "%s: rotation %d of %d", who, rot, fs->R);
+    if (field < 0 || field > 6 || fs->slot[field] < 0) return fail(HF_EINVAL, "%s: field %d not held", who, field);
+    if (!fs->ready) return fail(HF_ENOTREADY, "%s: field set not computed", who);
+    return HF_OK;
+}
+
+extern "C" hf_status hf_fieldset_field_ptr(const hf_fieldset *fs, int rot, int field, const float **d_ptr) {
+    hf_status s = field_check(fs, rot, field, "hf_fieldset_field_ptr");
+    if (s != HF_OK) return s;
+    if (!d_ptr) return fail(HF_EINVAL, "hf_fieldset_field_ptr: d_ptr is NULL");
+    const size_t n3 = (size_t)fs->n * fs->n * fs->n;
+    *d_ptr = fs->data + ((size_t)rot * fs->nf + fs->slot[field]) * n3;
+    return HF_OK;
+}
+
+extern "C" hf_status hf_fieldset_get(const hf_fieldset *fs, int rot, int field, float *d_dst, hf_stream stream) {
+    const float *src = nullptr;
+    hf_status s = hf_fieldset_field_ptr(fs, rot, field, &src);
+    if (s != HF_OK) return s;
+    if (!d_dst) return fail(HF_EINVAL, "hf_fieldset_get: d_dst is NULL");
+    CU(cudaSetDevice(fs->ctx->device));
+    const size_t n3 = (size_t)fs->n * fs->n * fs->n;
+    CU(cudaMemcpyAsync(d_dst, src, n3 * sizeof(float), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return HF_OK;
+}
+
+// -------------------------------------------------------------------- query
+static hf::QueryGeom query_geom(const hf_fieldset *fs) {
+    hf::QueryGeom g;
+    g.base = fs->data;
+    g.rot_stride = (size_t)fs->nf * fs->n * fs->n * fs->n;
+    for (int f = 0; f < 7; ++f) g.field_slot[f] = fs->slot[f];
+    g.n = fs->n;
+    g.R = fs->R;
+    g.quats = fs->d_quat;
+    return g;
+}
+
+extern "C" hf_status hf_query_batch(const hf_fieldset *fs, const float *d_tq, int Q, int k, float *d_out,
+                                    hf_stream stream) {
+    if (!fs) return fail(HF_EINVAL, "hf_query_batch: NULL field set");
+    if (Q < 0 || (Q > 0 && (!d_tq || !d_out))) return fail(HF_EINVAL, "hf_query_batch: bad buffers");
+    if (k < 1 || k > 8 || k > fs->R) return fail(HF_EINVAL, "hf_query_batch: k_blend=%d", k);
+    if (!fs->ready) return fail(HF_ENOTREADY, "hf_query_batch: field set not computed");
+    CU(cudaSetDevice(fs->ctx->device));
+    CU(hf::run_query(query_geom(fs), d_tq, Q, k, d_out, (cudaStream_t)stream));
+    return HF_OK;
+}
+
+extern "C" hf_status hf_query(const hf_fieldset *fs, const float t[3], const float q[4], int k, float out7[7]) {
+    if (!fs || !t || !q || !out7) return fail(HF_EINVAL, "hf_query: NULL argument");
+    if (k < 1 || k > 8 || k > fs->R) return fail(HF_EINVAL, "hf_query: k_blend=%d", k);
+    if (!fs->ready) return fail(HF_ENOTREADY, "hf_query: field set not computed");
+    hf_ctx *c = fs->ctx;
+    std::lock_guard<std::mutex> g(c->qmu);
+    CU(cudaSetDevice(c->device));
+    for (int a = 0; a < 3; ++a) c->h_qin[a] = t[a];
+    for (int a = 0; a < 4; ++a) c->h_qin[3 + a] = q[a];
+    CU(cudaMemcpyAsync(c->d_qin, c->h_qin, 7 * sizeof(float), cudaMemcpyHostToDevice, c->qstream));
+    CU(hf::run_query(query_geom(fs), c->d_qin, 1, k, c->d_qout, c->qstream));
+    CU(cudaMemcpyAsync(c->h_qout, c->d_qout, 7 * sizeof(float), cudaMemcpyDeviceToHost, c->qstream));
+    CU(cudaStreamSynchronize(c->qstream));
+    for (int a = 0; a < 7; ++a) out7[a] = c->h_qout[a];
+    return HF_OK;
+}
+
+// ----------------------------------------------------- single-step entries
+extern "C" hf_status hf_resample(int n, const float *d_rho, const float h_R[9], float *d_out, hf_stream stream) {
+    if (!hf::supported_n(n)) return fail(HF_EUNSUPPORTED, "hf_resample: N=%d not supported", n);
+    if (!d_rho || !h_R || !d_out) return fail(HF_EINVAL, "hf_resample: NULL argument");
+    hf::Rot9 r;
+    for (int k = 0; k < 9; ++k) r.r[k] = h_R[k];
+    CU(hf::run_resample(n, d_rho, r, d_out, (cudaStream_t)stream));
+    return HF_OK;
+}
+
+extern "C" size_t hf_rfft3d_scratch_bytes(int n) {
+    if (!hf::supported_n(n)) return 0;
+    return 2 * hf::half_spec_elems(n) * sizeof(float2) + 256;
+}
+
+extern "C" hf_status hf_rfft3d(int n, const float *d_in, float *d_out, void *d_scratch, hf_stream stream) {
+    if (!hf::supported_n(n)) return fail(HF_EUNSUPPORTED, "hf_rfft3d: N=%d not supported", n);
+    if (!d_in || !d_out || !d_scratch) return fail(HF_EINVAL, "hf_rfft3d: NULL argument");
+    if ((uintptr_t)d_scratch % 16) return fail(HF_EINVAL, "hf_rfft3d: scratch must be 16-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t he = hf::half_spec_elems(n);
+    float2 *X1 = (float2 *)d_scratch, *spec = X1 + he;
+    float *rot = (float *)(spec + he);
+    CU(cudaMemcpyAsync(rot, kIdentity9, sizeof kIdentity9, cudaMemcpyHostToDevice, st));
+    CU(hf::run_passA(n, d_in, rot, X1, 1, st));
+    CU(hf::run_passB_forward(n, X1, spec, 1.0f, st));
+    CU(hf::run_unpermute(n, spec, (float2 *)d_out, st));
+    return HF_OK;
+}
+
+extern "C" size_t hf_fields_scratch_bytes(int n) {
+    if (!hf::supported_n(n)) return 0;
+    const size_t n3 = (size_t)n * n * n;
+    return 3 * hf::half_spec_elems(n) * sizeof(float2) + 3 * n3 * sizeof(float) + 256;
+}
+
+extern "C" hf_status hf_fields(hf_ctx *ctx, const hf_part *s1, const hf_part *s2, const float h_quat[4], float *d_E,
+                               float *d_Fx, float *d_Fy, float *d_Fz, void *d_scratch, hf_stream stream) {
+    if (!ctx || !h_quat || !d_E || !d_scratch) return fail(HF_EINVAL, "hf_fields: NULL argument");
+    if ((uintptr_t)d_scratch % 16) return fail(HF_EINVAL, "hf_fields: scratch must be 16-byte aligned");
+    hf_status s = check_pair(s1, s2, s1 ? s1->n : 0, "hf_fields");
+    if (s != HF_OK) return s;
+    const int n = s1->n;
+    CU(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t he = hf::half_spec_elems(n), n3 = (size_t)n * n * n;
+    float2 *scr = (float2 *)d_scratch;
+    float *dummy = (float *)(scr + 3 * he);
+    float *rot = dummy + 3 * n3;
+    const Quat q = qnorm(h_quat);
+    if (!qfinite(q)) return fail(HF_EINVAL, "hf_fields: quaternion is zero or not finite");
+    double M[9];
+    rot_from_quat(q, M);
+    float m9[9];
+    for (int k = 0; k < 9; ++k) m9[k] = (float)M[k];
+    CU(cudaMemcpyAsync(rot, m9, sizeof m9, cudaMemcpyHostToDevice, st));
+    FieldPtrs out{d_E, d_Fx ? d_Fx : dummy, d_Fy ? d_Fy : dummy + n3, d_Fz ? d_Fz : dummy + 2 * n3, 0};
+    s = run_fields(n, s1, s2, rot, 1, scr, he, out, st);
+    if (s != HF_OK) return s;
+    CU(cudaStreamSynchronize(st));  // m9 lives on this stack frame
+    return HF_OK;
+}
+
+extern "C" hf_status hf_torque(hf_ctx *ctx, int n, int R, const float *h_quat, const float *d_E, float *d_T,
+                               unsigned flags, int *h_status, hf_stream stream) {
+    if (!ctx || !h_quat || !d_E || !d_T) return fail(HF_EINVAL, "hf_torque: NULL argument");
+    if (!hf::supported_n(n)) return fail(HF_EUNSUPPORTED, "hf_torque: N=%d not supported", n);
+    if (R < 7) return fail(HF_EINVAL, "hf_torque: R=%d < 7", R);
+    CU(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<Quat> Q(R);
+    for (int r = 0; r < R; ++r) {
+        Q[r] = qnorm(h_quat + 4 * (size_t)r);
+        if (!qfinite(Q[r])) return fail(HF_EINVAL, "hf_torque: quaternion %d is zero or not finite", r);
+    }
+    std::vector<int> nbr;
+    std::vector<float> P32;
+    std::vector<double> P64;
+    const int bad = torque_setup(Q, nbr, P32, P64, h_status);
+    int *d_nbr = nullptr;
+    float *d_P = nullptr;
+    double *d_P64 = nullptr;
+    CU(cudaMallocAsync(&d_nbr, nbr.size() * sizeof(int), st));
+    CU(cudaMallocAsync(&d_P, P32.size() * sizeof(float), st));
+    CU(cudaMallocAsync(&d_P64, P64.size() * sizeof(double), st));
+    CU(cudaMemcpyAsync(d_nbr, nbr.data(), nbr.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(d_P, P32.data(), P32.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(d_P64, P64.data(), P64.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    const size_t n3 = (size_t)n * n * n;
+    CU(hf::run_torque(n, R, d_E, n3, d_T, 3 * n3, d_nbr, d_P, d_P64, (flags & HF_TORQUE_F64) != 0, st));
+    CU(cudaFreeAsync(d_nbr, st));
+    CU(cudaFreeAsync(d_P, st));
+    CU(cudaFreeAsync(d_P64, st));
+    CU(cudaStreamSynchronize(st));  // the host vectors are freed on return
+    if (bad) return fail(HF_EINVAL, "hf_torque: %d rotation(s) with a rank-deficient neighbourhood", bad);
+    return HF_OK;
+}

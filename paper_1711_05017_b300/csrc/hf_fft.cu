@@ -1,0 +1,391 @@
+// hf_fft.cu -- the per-rotation energy/force pipeline as three slab/pencil
+// passes over an N^3 grid (Section 3.2: interpolate, multiply, inverse FFT;
+// with the forward transform of the rotated density added because the
+// resample is done in the spatial domain).
+//
+//   pass A  (one CTA per z-plane and rotation)
+//           rho2^R = trilinear(rho2, R^T x_n)             Section 2.4
+//           x: real-to-complex DFT of every row            Eq. 7a
+//           y: complex DFT of every kx column              Eq. 7a
+//           -> X1[r][z][ky*][kx*]     (* = digit-permuted slot order)
+//   pass B  (one CTA per ky slot, kx chunk and rotation)
+//           z: complex DFT of every (ky, kx) pencil        Eq. 7a
+//           S  = (h^3/N^3) rho1^ . conj(rho2^R^)            Eqs. 3, 5
+//           Gz = i pi kz~ S                                 Eq. 6a (2 pi w = pi k~)
+//           z: inverse DFT of S and of Gz                   Eq. 7b
+//           -> Y1 = S', Y2 = Gz'      [r][z][ky*][kx*]
+//   pass C  (one CTA per z-plane and rotation)
+//           Gy = i pi ky~ S'; y: inverse DFT of S', Gy, Gz' Eq. 7b
+//           x: one complex inverse DFT per row gives two real fields:
+//              IDFT(S (1 + pi kx~))  = E + i Fx   (Gx = i pi kx~ S)
+//              IDFT(-(Gy + i Gz))    = Fy + i Fz
+//           -> E, Fx, Fy, Fz (float, [z][y][x])
+//
+// The multipliers of Gx and Gy are constant along the pencils transformed
+// before they are applied, so Gx needs no transform of its own until the
+// last (x) stage and Gy none before pass C: 2 z-, 3 y- and 2 full x-
+// transforms per rotation instead of the 4 of each that a field-by-field
+// inverse takes.  Nyquist multipliers are 0 on every axis.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "hf_dft.cuh"
+#include "hf_internal.h"
+#include "hf_sample.cuh"
+
+namespace hf {
+
+// ---------------------------------------------------------------- twiddles
+struct cf2 {
+    float x, y;
+};
+template <int L>
+struct TwTab {
+    cf2 v[L];
+};
+template <int L>
+constexpr TwTab<L> make_tw() {
+    TwTab<L> t{};
+    for (int j = 0; j < L; ++j) {
+        t.v[j].x = (float)ct::trig(j, L, 0);
+        t.v[j].y = (float)(-ct::trig(j, L, 1));  // exp(-2 pi i j / L)
+    }
+    return t;
+}
+template <int L>
+__device__ const TwTab<L> g_tw = make_tw<L>();
+
+template <int L>
+__device__ __forceinline__ void load_tw(float2 *dst) {
+    for (int i = threadIdx.x; i < L; i += blockDim.x) dst[i] = make_float2(g_tw<L>.v[i].x, g_tw<L>.v[i].y);
+}
+
+constexpr float kPi = 3.14159265358979323846f;
+
+template <int N>
+__device__ __forceinline__ float signed_k_mult(int k) {
+    // pi * k~ with k~ the signed index, 0 at the Nyquist index
+    return (2 * k == N) ? 0.0f : kPi * (float)(k < N / 2 ? k : k - N);
+}
+
+// ------------------------------------------------------------------ pass A
+template <int N>
+struct PassA {
+    static constexpr int H = N / 2 + 1, HALF = N / 2;
+    static constexpr int NT = (N >= 128) ? 544 : (N >= 64 ? 288 : 160);
+    static constexpr size_t smem = sizeof(float2) * ((size_t)N * H + N + HALF);
+};
+
+template <int N>
+__global__ void __launch_bounds__(PassA<N>::NT) passA_kernel(const float *__restrict__ rho,
+                                                              const float *__restrict__ rot9,
+                                                              float2 *__restrict__ X1) {
+    constexpr int H = PassA<N>::H, HALF = PassA<N>::HALF;
+    extern __shared__ float2 sm[];
+    float2 *P = sm;            // [N rows y][H]  (row = N reals = N/2 complex + Nyquist slot)
+    float2 *twN = P + N * H;   // exp(-2 pi i j / N)
+    float2 *twH = twN + N;     // exp(-2 pi i j / (N/2))
+    const int z = blockIdx.x, r = blockIdx.y;
+    load_tw<N>(twN);
+    load_tw<HALF>(twH);
+
+    // rotated resample of the moving density into the plane, as reals
+    float R[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) R[k] = __ldg(rot9 + 9 * r + k);
+    const float cz = (float)(z - N / 2);
+    const float bx = R[6] * cz, by = R[7] * cz, bz = R[8] * cz;
+    float *Pf = reinterpret_cast<float *>(P);
+    for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+        const int x = i % N, y = i / N;
+        const float cx = (float)(x - N / 2), cy = (float)(y - N / 2);
+        // (R^T c)_a = R[0][a] cx + R[1][a] cy + R[2][a] cz
+        const float vx = fmaf(R[0], cx, fmaf(R[3], cy, bx));
+        const float vy = fmaf(R[1], cx, fmaf(R[4], cy, by));
+        const float vz = fmaf(R[2], cx, fmaf(R[5], cy, bz));
+        Pf[(size_t)y * 2 * H + x] = trilinear_c<N>(rho, vx, vy, vz);
+    }
+    __syncthreads();
+
+    // x: rows as N/2-point complex sequences z[m] = x[2m] + i x[2m+1]
+    fft_lines<HALF, -1>(P, N, 1, H, twH);
+    // split into the half spectrum X[k], k = 0..N/2:
+    //   E_k = (Z[k] + conj Z[N/2-k]) / 2,  O_k = (Z[k] - conj Z[N/2-k]) / 2i
+    //   X[k] = E_k + W^k O_k,  X[N/2-k] = conj(E_k - W^k O_k),  W = exp(-2 pi i / N)
+    for (int i = threadIdx.x; i < N * (N / 4 + 1); i += blockDim.x) {
+        const int y = i % N, k = i / N;
+        float2 *row = P + y * H;
+        if (k == 0) {
+            const float2 z0 = row[0];
+            row[0] = make_float2(z0.x + z0.y, 0.f);
+            row[HALF] = make_float2(z0.x - z0.y, 0.f);
+        } else if (4 * k == N) {
+            const int s = perm_slot<HALF>(k);
+            row[s] = cconj(row[s]);
+        } else {
+            const int s1 = perm_slot<HALF>(k), s2 = perm_slot<HALF>(HALF - k);
+            const float2 a = row[s1], b = row[s2];
+            const float2 Ek = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+            const float2 Ok = make_float2(0.5f * (a.y + b.y), -0.5f * (a.x - b.x));
+            const float2 WO = cmul(twN[k], Ok);
+            row[s1] = cadd(Ek, WO);
+            row[s2] = cconj(csub(Ek, WO));
+        }
+    }
+    __syncthreads();
+    // y: H columns of length N
+    fft_lines<N, -1>(P, H, H, 1, twN);
+    float2 *dst = X1 + ((size_t)r * N + z) * N * H;
+    for (int i = threadIdx.x; i < N * H; i += blockDim.x) dst[i] = P[i];
+}
+
+// ------------------------------------------------------------------ pass B
+template <int N>
+struct PassB {
+    static constexpr int H = N / 2 + 1;
+    static constexpr int C = (H + 1) / 2;  // kx chunk width (2 chunks)
+    static constexpr int NCH = 2;
+    static constexpr int NT = (N >= 128) ? 544 : (N >= 64 ? 288 : 160);
+    static constexpr size_t smem = sizeof(float2) * ((size_t)N * 2 * C + N);
+};
+
+// MODE 0: full middle pass (product, gradient, inverse z) -> Y1, Y2
+// MODE 1: forward only, spectrum * scale -> spec[ky*][kz*][kx*]  (stationary part)
+template <int N, int MODE>
+__global__ void __launch_bounds__(PassB<N>::NT) passB_kernel(const float2 *__restrict__ X1,
+                                                              const float2 *__restrict__ R1hat,
+                                                              float2 *__restrict__ Y1,
+                                                              float2 *__restrict__ Y2, float scale) {
+    constexpr int H = PassB<N>::H, C = PassB<N>::C, W2 = 2 * C;
+    extern __shared__ float2 sm[];
+    float2 *T = sm;            // [N][2C]: columns [0,C) = S, [C,2C) = Gz
+    float2 *twN = T + N * W2;
+    const int ky = blockIdx.x, c0 = blockIdx.y * C, r = blockIdx.z;
+    const int cw = min(C, H - c0);
+    load_tw<N>(twN);
+    const float2 *src = X1 + (size_t)r * N * N * H + (size_t)ky * H + c0;
+    for (int i = threadIdx.x; i < N * C; i += blockDim.x) {
+        const int z = i / C, c = i % C;
+        T[z * W2 + c] = c < cw ? src[(size_t)z * N * H + c] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    fft_lines<N, -1>(T, C, W2, 1, twN);
+    if constexpr (MODE == 1) {
+        float2 *dst = Y1 + (size_t)ky * N * H + c0;
+        for (int i = threadIdx.x; i < N * cw; i += blockDim.x) {
+            const int s = i / cw, c = i % cw;
+            dst[(size_t)s * H + c] = cscale(T[s * W2 + c], scale);
+        }
+    } else {
+        const float2 *rh = R1hat + (size_t)ky * N * H + c0;
+        for (int i = threadIdx.x; i < N * C; i += blockDim.x) {
+            const int s = i / C, c = i % C;
+            float2 S = make_float2(0.f, 0.f);
+            if (c < cw) S = cmulc(__ldg(rh + (size_t)s * H + c), T[s * W2 + c]);
+            T[s * W2 + c] = S;
+            T[s * W2 + C + c] = cmul_is(S, signed_k_mult<N>(slot_freq<N>(s)));
+        }
+        __syncthreads();
+        fft_lines<N, +1>(T, W2, W2, 1, twN);
+        float2 *d1 = Y1 + (size_t)r * N * N * H + (size_t)ky * H + c0;
+        float2 *d2 = Y2 + (size_t)r * N * N * H + (size_t)ky * H + c0;
+        for (int i = threadIdx.x; i < N * cw; i += blockDim.x) {
+            const int z = i / cw, c = i % cw;
+            d1[(size_t)z * N * H + c] = T[z * W2 + c];
+            d2[(size_t)z * N * H + c] = T[z * W2 + C + c];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ pass C
+template <int N>
+struct PassC {
+    static constexpr int H = N / 2 + 1, HALF = N / 2;
+    static constexpr int PW = 2 * H + 1;  // plane pitch: S' at [0,H), Gy at [H,2H)
+    static constexpr int RB = (N >= 128) ? 32 : N / 2;  // rows per x batch
+    static constexpr int TP = N + 1;                    // row-buffer pitch
+    static constexpr int NT = (N >= 128) ? 512 : (N >= 64 ? 256 : 128);
+    static constexpr size_t smem = sizeof(float2) * ((size_t)N * PW + (size_t)RB * TP + N);
+};
+
+// x slot of half-spectrum index k in [0, N/2]
+template <int N>
+__device__ __forceinline__ int xslot(int k) {
+    return k == N / 2 ? N / 2 : perm_slot<N / 2>(k);
+}
+
+// One complex inverse DFT of length N per row, input built from the
+// half-spectrum columns of the plane; real part -> out0, imaginary -> out1.
+// PAIR 0: Z[k] = S(k) (1 + pi kx~)              -> (E, Fx)
+// PAIR 1: Z[k] = -(Gy(k) + i Gz(k))             -> (Fy, Fz)
+template <int N, int PAIR>
+__device__ __forceinline__ void x_pass(const float2 *plane, int colA, int colB, float2 *Tb,
+                                       const float2 *twN, float *__restrict__ out0,
+                                       float *__restrict__ out1) {
+    constexpr int R1 = Fact<N>::R1, R2 = Fact<N>::R2, PW = PassC<N>::PW, RB = PassC<N>::RB,
+                  TP = PassC<N>::TP;
+    for (int y0 = 0; y0 < N; y0 += RB) {
+        // stage 1 (inverse), items (row, k1): slots R2*k1 + k2 <- Z[k1 + R1*k2]
+        for (int w = threadIdx.x; w < RB * R1; w += blockDim.x) {
+            const int row = w % RB, k1 = w / RB;
+            const float2 *pr = plane + (size_t)(y0 + row) * PW;
+            float2 v[R2];
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2) {
+                const int k = k1 + R1 * k2;
+                const bool neg = 2 * k > N;
+                const int m = neg ? N - k : k;
+                const int s = xslot<N>(m);
+                float2 z;
+                if constexpr (PAIR == 0) {
+                    float2 a = pr[colA + s];
+                    if (neg) a = cconj(a);
+                    const float mult = (2 * k == N) ? 1.0f : 1.0f + (neg ? -kPi * (float)m : kPi * (float)m);
+                    z = cscale(a, mult);
+                } else {
+                    float2 gy = pr[colB + s], gz = pr[colA + s];
+                    if (neg) { gy = cconj(gy); gz = cconj(gz); }
+                    z = make_float2(gz.y - gy.x, -gy.y - gz.x);  // -(gy + i gz)
+                }
+                v[k2] = z;
+            }
+            RegDFT<R2, +1>::run(v);
+            float2 *tr = Tb + row * TP + R2 * k1;
+#pragma unroll
+            for (int n2 = 0; n2 < R2; ++n2) tr[n2] = n2 ? cmulc(v[n2], twN[n2 * k1]) : v[n2];
+        }
+        __syncthreads();
+        // stage 2 (inverse), items (row, n2): natural order back into the row buffer
+        for (int w = threadIdx.x; w < RB * R2; w += blockDim.x) {
+            const int row = w % RB, n2 = w / RB;
+            float2 *tr = Tb + row * TP + n2;
+            float2 v[R1];
+#pragma unroll
+            for (int k1 = 0; k1 < R1; ++k1) v[k1] = tr[R2 * k1];
+            RegDFT<R1, +1>::run(v);
+#pragma unroll
+            for (int n1 = 0; n1 < R1; ++n1) tr[R2 * n1] = v[n1];
+        }
+        __syncthreads();
+        // coalesced store of the RB rows
+        for (int i = threadIdx.x; i < RB * N; i += blockDim.x) {
+            const int row = i / N, x = i % N;
+            const float2 v = Tb[row * TP + x];
+            const size_t o = (size_t)(y0 + row) * N + x;
+            out0[o] = v.x;
+            out1[o] = v.y;
+        }
+        __syncthreads();
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(PassC<N>::NT) passC_kernel(const float2 *__restrict__ Y1,
+                                                              const float2 *__restrict__ Y2,
+                                                              FieldPtrs out) {
+    constexpr int H = PassC<N>::H, PW = PassC<N>::PW, RB = PassC<N>::RB, TP = PassC<N>::TP;
+    extern __shared__ float2 sm[];
+    float2 *plane = sm;                       // [N][PW]
+    float2 *Tb = plane + (size_t)N * PW;      // [RB][TP]
+    float2 *twN = Tb + (size_t)RB * TP;
+    const int z = blockIdx.x, r = blockIdx.y;
+    load_tw<N>(twN);
+    const float2 *s1 = Y1 + ((size_t)r * N + z) * N * H;
+    for (int i = threadIdx.x; i < N * H; i += blockDim.x) {
+        const int y = i / H, c = i % H;  // y is the ky slot
+        const float2 v = s1[i];
+        plane[y * PW + c] = v;
+        plane[y * PW + H + c] = cmul_is(v, signed_k_mult<N>(slot_freq<N>(y)));
+    }
+    __syncthreads();
+    fft_lines<N, +1>(plane, 2 * H, PW, 1, twN);
+    const size_t fo = (size_t)r * out.rot_stride + (size_t)z * N * N;
+    x_pass<N, 0>(plane, 0, H, Tb, twN, out.E + fo, out.Fx + fo);
+    const float2 *s2 = Y2 + ((size_t)r * N + z) * N * H;
+    for (int i = threadIdx.x; i < N * H; i += blockDim.x) {
+        const int y = i / H, c = i % H;
+        plane[y * PW + c] = s2[i];
+    }
+    __syncthreads();
+    fft_lines<N, +1>(plane, H, PW, 1, twN);
+    x_pass<N, 1>(plane, 0, H, Tb, twN, out.Fy + fo, out.Fz + fo);
+}
+
+// -------------------------------------------- natural-order spectrum copy
+// spec[ky*][kz*][kx*] (slot order, as left by pass B mode 1) -> out[kz][ky][kx]
+template <int N>
+__global__ void unpermute_spectrum_kernel(const float2 *__restrict__ spec, float2 *__restrict__ out) {
+    constexpr int H = N / 2 + 1;
+    const size_t total = (size_t)N * N * H;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int kx = (int)(i % H), ky = (int)((i / H) % N), kz = (int)(i / ((size_t)H * N));
+        out[i] = spec[((size_t)perm_slot<N>(ky) * N + perm_slot<N>(kz)) * H + xslot<N>(kx)];
+    }
+}
+
+// ------------------------------------------------------------- launchers
+template <int N>
+static cudaError_t set_smem_attrs() {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(passA_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassA<N>::smem))) return e;
+    if ((e = cudaFuncSetAttribute(passB_kernel<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N>::smem))) return e;
+    if ((e = cudaFuncSetAttribute(passB_kernel<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N>::smem))) return e;
+    if ((e = cudaFuncSetAttribute(passC_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassC<N>::smem))) return e;
+    return cudaSuccess;
+}
+
+template <int N>
+static cudaError_t launch_passA(const float *rho, const float *rot9, float2 *X1, int nrot, cudaStream_t st) {
+    passA_kernel<N><<<dim3(N, nrot), PassA<N>::NT, PassA<N>::smem, st>>>(rho, rot9, X1);
+    return cudaGetLastError();
+}
+template <int N>
+static cudaError_t launch_passB(const float2 *X1, const float2 *R1hat, float2 *Y1, float2 *Y2, int nrot,
+                                cudaStream_t st) {
+    passB_kernel<N, 0><<<dim3(N, PassB<N>::NCH, nrot), PassB<N>::NT, PassB<N>::smem, st>>>(X1, R1hat, Y1, Y2, 0.f);
+    return cudaGetLastError();
+}
+template <int N>
+static cudaError_t launch_passB_fwd(const float2 *X1, float2 *spec, float scale, cudaStream_t st) {
+    passB_kernel<N, 1><<<dim3(N, PassB<N>::NCH, 1), PassB<N>::NT, PassB<N>::smem, st>>>(X1, nullptr, spec, nullptr, scale);
+    return cudaGetLastError();
+}
+template <int N>
+static cudaError_t launch_passC(const float2 *Y1, const float2 *Y2, FieldPtrs out, int nrot, cudaStream_t st) {
+    passC_kernel<N><<<dim3(N, nrot), PassC<N>::NT, PassC<N>::smem, st>>>(Y1, Y2, out);
+    return cudaGetLastError();
+}
+template <int N>
+static cudaError_t launch_unpermute(const float2 *spec, float2 *out, cudaStream_t st) {
+    unpermute_spectrum_kernel<N><<<148, 256, 0, st>>>(spec, out);
+    return cudaGetLastError();
+}
+
+#define HF_DISPATCH(n, call)                                \
+    switch (n) {                                            \
+        case 32: { constexpr int NN = 32; return call; }    \
+        case 64: { constexpr int NN = 64; return call; }    \
+        case 96: { constexpr int NN = 96; return call; }    \
+        case 128: { constexpr int NN = 128; return call; }  \
+        default: return cudaErrorInvalidValue;              \
+    }
+
+cudaError_t fft_init_attrs(int n) { HF_DISPATCH(n, set_smem_attrs<NN>()); }
+cudaError_t run_passA(int n, const float *rho, const float *rot9, float2 *X1, int nrot, cudaStream_t st) {
+    HF_DISPATCH(n, launch_passA<NN>(rho, rot9, X1, nrot, st));
+}
+cudaError_t run_passB(int n, const float2 *X1, const float2 *R1hat, float2 *Y1, float2 *Y2, int nrot, cudaStream_t st) {
+    HF_DISPATCH(n, launch_passB<NN>(X1, R1hat, Y1, Y2, nrot, st));
+}
+cudaError_t run_passB_forward(int n, const float2 *X1, float2 *spec, float scale, cudaStream_t st) {
+    HF_DISPATCH(n, launch_passB_fwd<NN>(X1, spec, scale, st));
+}
+cudaError_t run_passC(int n, const float2 *Y1, const float2 *Y2, FieldPtrs out, int nrot, cudaStream_t st) {
+    HF_DISPATCH(n, launch_passC<NN>(Y1, Y2, out, nrot, st));
+}
+cudaError_t run_unpermute(int n, const float2 *spec, float2 *out, cudaStream_t st) {
+    HF_DISPATCH(n, launch_unpermute<NN>(spec, out, st));
+}
+
+}  // namespace hf

@@ -1,0 +1,51 @@
+// hf_internal.h -- declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace hf {
+
+// Output pointers of one field-build launch; fields of rotation r start at
+// ptr + r * rot_stride (floats).
+struct FieldPtrs {
+    float *E, *Fx, *Fy, *Fz;
+    size_t rot_stride;
+};
+
+struct Rot9 {
+    float r[9];  // row-major rotation matrix
+};
+
+inline bool supported_n(int n) { return n == 32 || n == 64 || n == 96 || n == 128; }
+
+// elements of one half-spectrum intermediate (complex): N * N * (N/2 + 1)
+inline size_t half_spec_elems(int n) { return (size_t)n * n * (n / 2 + 1); }
+
+// hf_fft.cu
+cudaError_t fft_init_attrs(int n);
+cudaError_t run_passA(int n, const float *rho, const float *rot9, float2 *X1, int nrot, cudaStream_t st);
+cudaError_t run_passB(int n, const float2 *X1, const float2 *R1hat, float2 *Y1, float2 *Y2, int nrot,
+                      cudaStream_t st);
+cudaError_t run_passB_forward(int n, const float2 *X1, float2 *spec, float scale, cudaStream_t st);
+cudaError_t run_passC(int n, const float2 *Y1, const float2 *Y2, FieldPtrs out, int nrot, cudaStream_t st);
+cudaError_t run_unpermute(int n, const float2 *spec, float2 *out, cudaStream_t st);
+
+// hf_kernels.cu
+cudaError_t run_splat(int n, const float *pts, const float *sigma, const float *amp, int P, float *grid,
+                      cudaStream_t st);
+cudaError_t run_resample(int n, const float *rho, Rot9 rot, float *out, cudaStream_t st);
+cudaError_t run_torque(int n, int R, const float *E, size_t e_rot_stride, float *T, size_t t_rot_stride,
+                       const int *nbr, const float *P, const double *P64, bool f64, cudaStream_t st);
+// query: field f of rotation r at base + r*rot_stride + field_slot[f]*n^3 when
+// field_slot[f] >= 0, else the field reads 0
+struct QueryGeom {
+    const float *base;
+    size_t rot_stride;
+    int field_slot[7];
+    int n, R;
+    const double *quats;  // R x 4, normalised, on device
+};
+cudaError_t run_query(const QueryGeom &g, const float *tq, int Q, int k, float *out, cudaStream_t st);
+
+}  // namespace hf

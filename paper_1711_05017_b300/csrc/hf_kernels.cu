@@ -1,0 +1,325 @@
+// hf_kernels.cu -- the non-FFT steps of the path:
+//   splat    skeletal density from skeleton samples (stand-in for the
+//            skeletal density of Section 2.3, Gaussian kernel)
+//   resample rotated density on the grid (Section 2.4)
+//   torque   rotational gradient of the energy by least squares over the
+//            nearest sampled rotations (the quantity of Eq. 6b)
+//   query    fields at a pose from the per-orientation precompute
+//            (Section 4.2, restricted motion DOF)
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "hf_internal.h"
+#include "hf_sample.cuh"
+
+namespace hf {
+
+// ------------------------------------------------------------------ splat
+// One CTA per 8x8x8 tile of nodes, one thread per node.  The CTA walks the
+// point list in chunks, keeps (in point order) the points whose cutoff
+// sphere reaches the tile's box, and every thread adds their Gaussians to
+// its node.  Gather form: deterministic, no atomics.
+constexpr int kSplatTile = 8;
+constexpr int kSplatThreads = kSplatTile * kSplatTile * kSplatTile;
+
+__device__ __forceinline__ float min_image(float d) { return d - 2.0f * rintf(0.5f * d); }
+
+template <int N>
+__global__ void __launch_bounds__(kSplatThreads) splat_kernel(const float *__restrict__ pts,
+                                                              const float *__restrict__ sigma,
+                                                              const float *__restrict__ amp, int P,
+                                                              float *__restrict__ grid) {
+    __shared__ float4 cand[kSplatThreads];  // x, y, z, a
+    __shared__ float2 cpar[kSplatThreads];  // cutoff^2, 1/(2 sigma^2)
+    __shared__ int warp_cnt[kSplatThreads / 32];
+    constexpr int TPA = N / kSplatTile;  // tiles per axis
+    const int t = blockIdx.x;
+    const int tx = t % TPA, ty = (t / TPA) % TPA, tz = t / (TPA * TPA);
+    const float h = 2.0f / N;
+    const int lx = threadIdx.x % kSplatTile, ly = (threadIdx.x / kSplatTile) % kSplatTile,
+              lz = threadIdx.x / (kSplatTile * kSplatTile);
+    const int nx = tx * kSplatTile + lx, ny = ty * kSplatTile + ly, nz = tz * kSplatTile + lz;
+    const float px = (float)(nx - N / 2) * h, py = (float)(ny - N / 2) * h, pz = (float)(nz - N / 2) * h;
+    // tile box: centre and half-width per axis
+    const float half = 0.5f * (kSplatTile - 1) * h;
+    const float bx = (float)(tx * kSplatTile - N / 2) * h + half;
+    const float by = (float)(ty * kSplatTile - N / 2) * h + half;
+    const float bz = (float)(tz * kSplatTile - N / 2) * h + half;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float acc = 0.0f;
+    for (int base = 0; base < P; base += kSplatThreads) {
+        const int i = base + threadIdx.x;
+        bool keep = false;
+        float4 c = make_float4(0, 0, 0, 0);
+        float2 cp = make_float2(0, 0);
+        if (i < P) {
+            c = make_float4(__ldg(pts + 3 * i), __ldg(pts + 3 * i + 1), __ldg(pts + 3 * i + 2),
+                            amp ? __ldg(amp + i) : 1.0f);
+            const float s = __ldg(sigma + i);
+            const float cut = 6.0f * s;
+            // distance from the point to the tile box on the torus, per axis
+            const float dx = fmaxf(fabsf(min_image(c.x - bx)) - half, 0.f);
+            const float dy = fmaxf(fabsf(min_image(c.y - by)) - half, 0.f);
+            const float dz = fmaxf(fabsf(min_image(c.z - bz)) - half, 0.f);
+            keep = dx * dx + dy * dy + dz * dz <= cut * cut * 1.0001f + 1e-12f;
+            cp = make_float2(36.0f * s * s, 1.0f / (2.0f * s * s));
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) warp_cnt[warp] = __popc(m);
+        __syncthreads();
+        int off = 0, total = 0;
+        for (int wv = 0; wv < kSplatThreads / 32; ++wv) {
+            const int cnt = warp_cnt[wv];
+            off += (wv < warp) ? cnt : 0;
+            total += cnt;
+        }
+        if (keep) {
+            const int pos = off + __popc(m & ((1u << lane) - 1u));
+            cand[pos] = c;
+            cpar[pos] = cp;
+        }
+        __syncthreads();
+        for (int j = 0; j < total; ++j) {
+            const float4 cj = cand[j];
+            const float2 pj = cpar[j];
+            const float dx = min_image(px - cj.x), dy = min_image(py - cj.y), dz = min_image(pz - cj.z);
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (r2 <= pj.x) acc = fmaf(cj.w, expf(-r2 * pj.y), acc);
+        }
+        __syncthreads();
+    }
+    grid[((size_t)nz * N + ny) * N + nx] = acc;
+}
+
+// --------------------------------------------------------------- resample
+template <int N>
+__global__ void resample_kernel(const float *__restrict__ rho, Rot9 rot, float *__restrict__ out) {
+    const size_t total = (size_t)N * N * N;
+    const float *R = rot.r;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % N), y = (int)((i / N) % N), z = (int)(i / ((size_t)N * N));
+        const float cx = (float)(x - N / 2), cy = (float)(y - N / 2), cz = (float)(z - N / 2);
+        const float vx = fmaf(R[0], cx, fmaf(R[3], cy, R[6] * cz));
+        const float vy = fmaf(R[1], cx, fmaf(R[4], cy, R[7] * cz));
+        const float vz = fmaf(R[2], cx, fmaf(R[5], cy, R[8] * cz));
+        out[i] = trilinear_c<N>(rho, vx, vy, vz);
+    }
+}
+
+// ----------------------------------------------------------------- torque
+// T_i = -P_i (E_nb - E_i) per cell, P_i = (A^T A)^{-1} A^T (3 x 6, from the
+// host in float64), A rows = Log(R_j R_i^T).  Blocks are ordered rotation-
+// fastest over cell tiles so that one tile of every rotation's energy stays
+// in L2 while all rotations that use it run.
+constexpr int kTorqueThreads = 256;
+constexpr int kTorqueVec = 4;  // cells per thread (one float4)
+constexpr int kTorqueTile = kTorqueThreads * kTorqueVec;
+
+template <bool F64>
+__global__ void __launch_bounds__(kTorqueThreads) torque_kernel(const float *__restrict__ E, size_t es,
+                                                                float *__restrict__ T, size_t ts,
+                                                                const int *__restrict__ nbr,
+                                                                const float *__restrict__ P,
+                                                                const double *__restrict__ P64, int R,
+                                                                size_t n3) {
+    const int r = blockIdx.x % R;
+    const size_t tile = blockIdx.x / R;
+    const size_t c0 = tile * kTorqueTile + (size_t)threadIdx.x * kTorqueVec;
+    if (c0 >= n3) return;
+    int nb[6];
+#pragma unroll
+    for (int s = 0; s < 6; ++s) nb[s] = __ldg(nbr + 6 * r + s);
+    const float4 ei = __ldg(reinterpret_cast<const float4 *>(E + (size_t)r * es + c0));
+    float4 g[3];
+    if constexpr (!F64) {
+        float p[18];
+#pragma unroll
+        for (int k = 0; k < 18; ++k) p[k] = __ldg(P + 18 * r + k);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) g[d] = make_float4(0, 0, 0, 0);
+#pragma unroll
+        for (int s = 0; s < 6; ++s) {
+            const float4 ej = __ldg(reinterpret_cast<const float4 *>(E + (size_t)nb[s] * es + c0));
+            const float4 b = make_float4(ej.x - ei.x, ej.y - ei.y, ej.z - ei.z, ej.w - ei.w);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const float w = p[6 * d + s];
+                g[d].x = fmaf(w, b.x, g[d].x);
+                g[d].y = fmaf(w, b.y, g[d].y);
+                g[d].z = fmaf(w, b.z, g[d].z);
+                g[d].w = fmaf(w, b.w, g[d].w);
+            }
+        }
+    } else {
+        double gd[3][4] = {};
+#pragma unroll
+        for (int s = 0; s < 6; ++s) {
+            const float4 ej = __ldg(reinterpret_cast<const float4 *>(E + (size_t)nb[s] * es + c0));
+            const double b[4] = {(double)ej.x - ei.x, (double)ej.y - ei.y, (double)ej.z - ei.z,
+                                 (double)ej.w - ei.w};
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const double w = __ldg(P64 + 18 * r + 6 * d + s);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) gd[d][c] = fma(w, b[c], gd[d][c]);
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            g[d] = make_float4((float)gd[d][0], (float)gd[d][1], (float)gd[d][2], (float)gd[d][3]);
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        *reinterpret_cast<float4 *>(T + (size_t)r * ts + (size_t)d * n3 + c0) =
+            make_float4(-g[d].x, -g[d].y, -g[d].z, -g[d].w);
+}
+
+// ------------------------------------------------------------------ query
+// One warp per query.  Rotation search in float64 (ordering by |q . q_j|,
+// which orders the geodesic angle; ties to the lower index), weights
+// 1/theta in float64, trilinear sampling in float32.
+constexpr int kQueryMaxK = 8;
+constexpr int kQueryWarps = 8;
+
+__device__ __forceinline__ bool better(double da, int ia, double db, int ib) {
+    return da > db || (da == db && ia < ib);
+}
+
+template <int N>
+__global__ void query_kernel(QueryGeom g, const float *__restrict__ tq, int Q, int k, float *__restrict__ out) {
+    __shared__ float part[kQueryWarps][7 * kQueryMaxK];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int qi = blockIdx.x * kQueryWarps + warp;
+    if (qi >= Q) return;  // warp-uniform
+    const float *in = tq + 7 * (size_t)qi;
+    double q[4] = {in[3], in[4], in[5], in[6]};
+    const double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) q[a] /= qn;
+    // per-lane sorted top-k of (|dot|, index); lanes visit indices in ascending order
+    double bd[kQueryMaxK];
+    int bi[kQueryMaxK];
+#pragma unroll
+    for (int s = 0; s < kQueryMaxK; ++s) { bd[s] = -1.0; bi[s] = 0x7fffffff; }
+    for (int j = lane; j < g.R; j += 32) {
+        const double *qj = g.quats + 4 * (size_t)j;
+        double d = fabs(q[0] * qj[0] + q[1] * qj[1] + q[2] * qj[2] + q[3] * qj[3]);
+        d = fmin(d, 1.0);
+        int ij = j;
+#pragma unroll
+        for (int s = 0; s < kQueryMaxK; ++s) {
+            if (s < k && better(d, ij, bd[s], bi[s])) {
+                const double td = bd[s];
+                const int ti = bi[s];
+                bd[s] = d; bi[s] = ij; d = td; ij = ti;
+            }
+        }
+    }
+    // warp merge: k rounds of arg-best over the lanes' list heads
+    double sel_d[kQueryMaxK];
+    int sel_i[kQueryMaxK];
+    for (int s = 0; s < k; ++s) {
+        double d = bd[0];
+        int i = bi[0];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double od = __shfl_xor_sync(0xffffffffu, d, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+            if (better(od, oi, d, i)) { d = od; i = oi; }
+        }
+        sel_d[s] = d;
+        sel_i[s] = i;
+        if (bi[0] == i) {  // this lane owned the winner: pop its head
+#pragma unroll
+            for (int t = 0; t < kQueryMaxK - 1; ++t) { bd[t] = bd[t + 1]; bi[t] = bi[t + 1]; }
+            bd[kQueryMaxK - 1] = -1.0;
+            bi[kQueryMaxK - 1] = 0x7fffffff;
+        }
+    }
+    // weights 1/theta, theta = 2 acos(|dot|)
+    double w[kQueryMaxK];
+    int used = k;
+    if (2.0 * acos(sel_d[0]) < 1e-12) {
+        used = 1;
+        w[0] = 1.0;
+    } else {
+        double sw = 0.0;
+        for (int s = 0; s < k; ++s) { w[s] = 1.0 / (2.0 * acos(sel_d[s])); sw += w[s]; }
+        for (int s = 0; s < k; ++s) w[s] /= sw;
+    }
+    // trilinear per (field, rotation) pair at lag u = t / h
+    const float hinv = 0.5f * N;
+    const float ux = in[0] * hinv, uy = in[1] * hinv, uz = in[2] * hinv;
+    const float fx = floorf(ux), fy = floorf(uy), fz = floorf(uz);
+    const float ax = ux - fx, ay = uy - fy, az = uz - fz;
+    const int x0 = wrapN<N>((int)fx), y0 = wrapN<N>((int)fy), z0 = wrapN<N>((int)fz);
+    const int x1 = wrapN<N>(x0 + 1), y1 = wrapN<N>(y0 + 1), z1 = wrapN<N>(z0 + 1);
+    const size_t n3 = (size_t)N * N * N;
+    for (int pidx = lane; pidx < 7 * used; pidx += 32) {
+        const int f = pidx % 7, s = pidx / 7;
+        float v = 0.f;
+        if (g.field_slot[f] >= 0) {
+            const float *fb = g.base + (size_t)sel_i[s] * g.rot_stride + (size_t)g.field_slot[f] * n3;
+            const float *r00 = fb + ((size_t)z0 * N + y0) * N, *r01 = fb + ((size_t)z0 * N + y1) * N;
+            const float *r10 = fb + ((size_t)z1 * N + y0) * N, *r11 = fb + ((size_t)z1 * N + y1) * N;
+            const float c00 = fmaf(ax, r00[x1] - r00[x0], r00[x0]);
+            const float c01 = fmaf(ax, r01[x1] - r01[x0], r01[x0]);
+            const float c10 = fmaf(ax, r10[x1] - r10[x0], r10[x0]);
+            const float c11 = fmaf(ax, r11[x1] - r11[x0], r11[x0]);
+            const float c0 = fmaf(ay, c01 - c00, c00), c1 = fmaf(ay, c11 - c10, c10);
+            v = fmaf(az, c1 - c0, c0);
+        }
+        part[warp][pidx] = v * (float)w[s];
+    }
+    __syncwarp();
+    if (lane < 7) {
+        float acc = 0.f;
+        for (int s = 0; s < used; ++s) acc += part[warp][7 * s + lane];
+        out[7 * (size_t)qi + lane] = acc;
+    }
+}
+
+// ------------------------------------------------------------- launchers
+#define HF_DISPATCH_K(n, call)                              \
+    switch (n) {                                            \
+        case 32: { constexpr int NN = 32; call; break; }    \
+        case 64: { constexpr int NN = 64; call; break; }    \
+        case 96: { constexpr int NN = 96; call; break; }    \
+        case 128: { constexpr int NN = 128; call; break; }  \
+        default: return cudaErrorInvalidValue;              \
+    }
+
+cudaError_t run_splat(int n, const float *pts, const float *sigma, const float *amp, int P, float *grid,
+                      cudaStream_t st) {
+    const int tiles = (n / kSplatTile) * (n / kSplatTile) * (n / kSplatTile);
+    HF_DISPATCH_K(n, (splat_kernel<NN><<<tiles, kSplatThreads, 0, st>>>(pts, sigma, amp, P, grid)));
+    return cudaGetLastError();
+}
+
+cudaError_t run_resample(int n, const float *rho, Rot9 rot, float *out, cudaStream_t st) {
+    HF_DISPATCH_K(n, (resample_kernel<NN><<<4 * 148, 256, 0, st>>>(rho, rot, out)));
+    return cudaGetLastError();
+}
+
+cudaError_t run_torque(int n, int R, const float *E, size_t e_rot_stride, float *T, size_t t_rot_stride,
+                       const int *nbr, const float *P, const double *P64, bool f64, cudaStream_t st) {
+    const size_t n3 = (size_t)n * n * n;
+    const size_t tiles = (n3 + kTorqueTile - 1) / kTorqueTile;
+    const size_t blocks = tiles * (size_t)R;
+    if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
+    if (f64)
+        torque_kernel<true><<<(unsigned)blocks, kTorqueThreads, 0, st>>>(E, e_rot_stride, T, t_rot_stride, nbr, P, P64, R, n3);
+    else
+        torque_kernel<false><<<(unsigned)blocks, kTorqueThreads, 0, st>>>(E, e_rot_stride, T, t_rot_stride, nbr, P, P64, R, n3);
+    return cudaGetLastError();
+}
+
+cudaError_t run_query(const QueryGeom &g, const float *tq, int Q, int k, float *out, cudaStream_t st) {
+    if (Q <= 0) return cudaSuccess;
+    const int blocks = (Q + kQueryWarps - 1) / kQueryWarps;
+    HF_DISPATCH_K(g.n, (query_kernel<NN><<<blocks, 32 * kQueryWarps, 0, st>>>(g, tq, Q, k, out)));
+    return cudaGetLastError();
+}
+
+}  // namespace hf
