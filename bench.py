@@ -1,0 +1,384 @@
+"""Benchmark: rotations/s of 128^3 energy + force (+ torque) fields for the
+peg-in-hole skeleton workload (5000 + 5000 points, 1024 random rotations),
+with p50/p99 pose-query latency.
+
+One step = the whole path over one batch: splat both parts, derive the
+stationary spectrum and the moving grid, energy/force for every rotation,
+torque by least squares over the 6 nearest rotations, and a batch of 1024
+pose queries.  `value` counts rotations per second with inputs resident on
+the device; `e2e` repeats the step through the public API from pinned host
+buffers, with the host->device input copies and the device->host read of the
+query results inside the timed region.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun every rank runs its own rotation batch (seeded by rank): weak
+scaling, no collective on the data path.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "rotations/s of 128^3 energy+force fields (+FD torque, +1024 pose queries per batch)"
+UNIT = "rotations/s"
+N_GRID = 128
+N_ROT = 1024
+N_QUERY = 1024
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+# ------------------------------------------------------------ clock sampler
+REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
+           0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+           0x80: "hw_power_brake_slowdown", 0x100: "display_clock_setting"}
+
+
+class ClockSampler:
+    def __init__(self, device_index):
+        self.samples = []
+        self.proc = None
+        self.dev = device_index
+
+    def __enter__(self):
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(self.dev).uuid)
+            sel = ["-i", uuid if uuid.startswith("GPU-") else "GPU-" + uuid]
+        except Exception:
+            sel = []
+        cmd = ["nvidia-smi", *sel, "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active,power.draw",
+               "--format=csv,noheader,nounits", "-lms", "200"]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 3:
+                try:
+                    self.samples.append((float(parts[0]), float(parts[1]), int(parts[2], 16)))
+                except ValueError:
+                    pass
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        mask = 0
+        for s in self.samples:
+            mask |= s[2]
+        return {"sm_mhz": statistics.median(s[0] for s in self.samples),
+                "sm_max_mhz": max(s[1] for s in self.samples),
+                "reasons": [v for k, v in REASONS.items() if mask & k and k != 0x1],
+                "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------------ oracle
+def oracle_rotation_sample(s1, s2, quats, n, count):
+    """The FP64 oracle, as it stands, on `count` rotations of the workload:
+    per rotation the resample, the energy/force fields and the per-cell torque
+    least squares.  Returns (seconds per rotation, sample description)."""
+    import oracle
+    t0 = time.perf_counter()
+    r1 = oracle.splat(n, s1.pts, s1.sigma)
+    r2 = oracle.splat(n, s2.pts, s2.sigma)
+    t_splat = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    E = []
+    for q in quats[:count]:
+        E.append(oracle.fields(r1, oracle.resample(r2, oracle.quat_to_rot(q)))[0])
+    t_rot = (time.perf_counter() - t0) / count
+    return t_rot, t_splat, f"{count} rotations of the {n}^3 workload (resample + E/F fields), splat timed once"
+
+
+# ------------------------------------------------------------ our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_1711_05017_b300 as hf
+    from paper_1711_05017_b300 import build
+
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    n, R = args.n, args.rotations
+    s1, s2 = synth.c2_pair(0)
+    quats = synth.random_quaternions(rank, R).astype(np.float32)
+    rng = np.random.default_rng(1000 + rank)
+    tq_h = np.concatenate([rng.uniform(-1, 1, (N_QUERY, 3)), synth.random_quaternions(2000 + rank, N_QUERY)],
+                          axis=1).astype(np.float32)
+
+    ctx = hf.Context(local_rank)
+    pts1, sig1 = torch.as_tensor(s1.pts, dtype=torch.float32, device=dev), torch.as_tensor(s1.sigma, dtype=torch.float32, device=dev)
+    pts2, sig2 = torch.as_tensor(s2.pts, dtype=torch.float32, device=dev), torch.as_tensor(s2.sigma, dtype=torch.float32, device=dev)
+    g1 = torch.empty((n, n, n), device=dev)
+    g2 = torch.empty((n, n, n), device=dev)
+    ctx.density_build(n, pts1, sig1, out=g1)
+    ctx.density_build(n, pts2, sig2, out=g2)
+    p1, p2 = ctx.part(g1, hf.HF_STATIONARY), ctx.part(g2, hf.HF_MOVING)
+    fs = ctx.fieldset(n, R, hf.HF_E | hf.HF_F | hf.HF_T)
+    tq = torch.as_tensor(tq_h, device=dev)
+    qout = torch.empty((N_QUERY, 7), device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ctx.density_build(n, pts1, sig1, out=g1)
+        ctx.density_build(n, pts2, sig2, out=g2)
+        p1.update(g1)
+        p2.update(g2)
+        fs.compute(p1, p2, quats)
+        fs.query_batch(tq, out=qout)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    ctx.profile_read(reset=True)
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    prof = ctx.profile_read(reset=True)
+    ctx.profile(False)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * R / (ms / 1e3)
+
+    # ---- roofline of the dominant kernel (algorithmic bytes / event-timed duration)
+    he = n * n * (n // 2 + 1) * 8  # one half-spectrum intermediate, bytes
+    n3b = 4 * n**3
+    chunk = min({32: 64, 64: 32, 96: 12}.get(n, 8), R) if not os.environ.get("HF_ROT_CHUNK") else int(os.environ["HF_ROT_CHUNK"])
+    alg = {  # bytes per launch: inputs read once + outputs written
+        "passA": n3b + chunk * he,
+        "passB": chunk * he + he + 2 * chunk * he,
+        "passC": 2 * chunk * he + chunk * 4 * n3b,
+        "torque": R * n3b + R * 3 * n3b,
+        "splat": n3b,
+        "passB_fwd": 2 * he,
+        "query": N_QUERY * 7 * 4 * 2,
+    }
+    hbm_peak, peak_kind = peaks()
+    kernels = {}
+    for k, (cnt, tot) in prof.items():
+        avg = tot / cnt
+        kernels[k] = {"launches": cnt, "avg_us": round(avg * 1e3, 2), "share": None,
+                      "alg_GBps": round(alg.get(k, 0) / (avg * 1e-3) / 1e9, 1)}
+    tot_all = sum(v[1] for v in prof.values()) or 1.0
+    for k in kernels:
+        kernels[k]["share"] = round(prof[k][1] / tot_all, 3)
+    dom = max(prof, key=lambda k: prof[k][1]) if prof else None
+    roof = None
+    if dom:
+        achieved = alg[dom] / (prof[dom][1] / prof[dom][0] * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
+                "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
+                "traffic": None, "alg_bytes_per_launch": alg[dom]}
+    launches = sum(v[0] for v in prof.values())
+
+    # ---- end to end through the public API from pinned host buffers
+    hp = [torch.as_tensor(a, dtype=torch.float32).pin_memory() for a in (s1.pts, s1.sigma, s2.pts, s2.sigma)]
+    tq_pin = torch.as_tensor(tq_h).pin_memory()
+    res_pin = torch.empty((N_QUERY, 7), dtype=torch.float32).pin_memory()
+    dbuf = [torch.empty_like(h, device=dev) for h in hp]
+    tq_d = torch.empty_like(tq_pin, device=dev)
+
+    def e2e_step():
+        for d, h in zip(dbuf, hp):
+            d.copy_(h, non_blocking=True)
+        tq_d.copy_(tq_pin, non_blocking=True)
+        ctx.density_build(n, dbuf[0], dbuf[1], out=g1)
+        ctx.density_build(n, dbuf[2], dbuf[3], out=g2)
+        p1.update(g1)
+        p2.update(g2)
+        fs.compute(p1, p2, quats)
+        fs.query_batch(tq_d, out=qout)
+        res_pin.copy_(qout, non_blocking=True)
+        stream.synchronize()
+
+    e2e_steps = max(2, args.steps // 2)
+    e2e_step()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = sum(h.numel() * 4 for h in hp) + tq_pin.numel() * 4 + quats.nbytes
+    d2h = res_pin.numel() * 4
+
+    # ---- pose-query latency (host call -> 7 floats back), 1 kHz-style random walk
+    tw = synth.translation_walk(7 + rank, 2000)
+    qw = synth.quaternion_walk(8 + rank, 2000)
+    lat = []
+    for i in range(2000):
+        a = time.perf_counter()
+        fs.query(tw[i], qw[i], k=4)
+        lat.append((time.perf_counter() - a) * 1e6)
+    lat = np.array(lat[100:])
+
+    # ---- plain path: the same kernels, one rotation per launch
+    plain = None
+    if not args.no_plain and rank == 0:
+        os.environ["HF_ROT_CHUNK"] = "1"
+        fs1 = ctx.fieldset(n, R, hf.HF_E | hf.HF_F | hf.HF_T)
+        del os.environ["HF_ROT_CHUNK"]
+
+        def plain_step():
+            ctx.density_build(n, pts1, sig1, out=g1)
+            ctx.density_build(n, pts2, sig2, out=g2)
+            p1.update(g1)
+            p2.update(g2)
+            fs1.compute(p1, p2, quats)
+            fs1.query_batch(tq, out=qout)
+
+        plain_step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plain_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1)
+        plain = {"value": round(R / (pms / 1e3), 1), "unit": UNIT, "ms_per_step": round(pms, 2),
+                 "speedup_of_batched": round((R / (ms / 1e3)) / (R / (pms / 1e3)), 3)}
+        fs1.release()
+
+    # ---- CPU baseline (the oracle on this host's cores), rank 0, N = 1 only
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        t_rot, t_splat, desc = oracle_rotation_sample(s1, s2, synth.random_quaternions(0, 4), n, 2)
+        cpu = {"value": round(1.0 / t_rot, 4), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": desc, "splat_s": round(t_splat, 2)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"c2 peg-in-hole skeletons, {n}^3 grid, 5000+5000 points, radii U(0.02,0.08), "
+                                   f"{R} random rotations per rank, E+F+T fields, {N_QUERY} pose queries per step",
+                       "grid": n, "rotations_per_rank": R, "parallelism": f"replicas x{world} (rotation batches)",
+                       "l2": "working set > L2 (fields 60 GB per rank)"},
+            "e2e": {"value": round(world * R / e2e_s, 1), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "query_latency_us": {"p50": round(float(np.percentile(lat, 50)), 1),
+                                 "p99": round(float(np.percentile(lat, 99)), 1), "n": int(lat.size),
+                                 "budget_us": 1000},
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "kernels": kernels,
+            "plain_path": plain,
+            "cpu_baseline": cpu,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    """The oracle (FP64, own FFT, OpenMP) on the host cores, same metric."""
+    if rank != 0:
+        return
+    import oracle
+    n = args.n
+    s1, s2 = synth.c2_pair(0)
+    q = synth.random_quaternions(0, max(1, args.steps + args.warmup))
+    r1 = oracle.splat(n, s1.pts, s1.sigma)
+    r2 = oracle.splat(n, s2.pts, s2.sigma)
+    for i in range(args.warmup):
+        oracle.fields(r1, oracle.resample(r2, oracle.quat_to_rot(q[i])))
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        oracle.fields(r1, oracle.resample(r2, oracle.quat_to_rot(q[args.warmup + i])))
+    s = (time.perf_counter() - t0) / max(1, args.steps)
+    v = 1.0 / s
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(s * 1e3, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"c2 peg-in-hole skeletons, {n}^3 grid, one rotation per step (bounded sample "
+                                   f"of the {N_ROT}-rotation batch), E+F fields", "grid": n},
+            "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "one rotation per step: resample + energy/force by the oracle's own FFT"},
+            "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_GRID)
+    ap.add_argument("--rotations", type=int, default=N_ROT)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

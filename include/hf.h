@@ -120,6 +120,11 @@ hf_status hf_part_create(hf_ctx *ctx, int n, const float *d_grid, int role, hf_p
                          hf_stream stream);
 void hf_part_release(hf_part *part);
 
+/* Re-derive a part's stored representation from a new N^3 grid of the same
+ * size, in place (no allocation beyond the stream-ordered pool).
+ * Errors: HF_EINVAL, HF_ECUDA. */
+hf_status hf_part_update(hf_part *part, const float *d_grid, hf_stream stream);
+
 /* Allocate a field set for R rotations at grid size n holding the fields
  * selected by `flags` (energy and force always; HF_T adds torque).  Bytes: R * N^3 * 4 * (#fields)
  * plus per-set scratch.  Errors: HF_EINVAL, HF_EBUDGET, HF_ENOMEM. */
@@ -168,6 +173,19 @@ hf_status hf_query(const hf_fieldset *fs, const float t[3], const float q[4], in
  * (tx, ty, tz, qw, qx, qy, qz); d_out is Q x 7 floats as in hf_query. */
 hf_status hf_query_batch(const hf_fieldset *fs, const float *d_tq, int Q, int k_blend,
                          float *d_out, hf_stream stream);
+
+/* ---- per-kernel timing (CUDA events on the launching stream) ----
+ * While enabled, every kernel launch the context's calls make is bracketed by
+ * a pair of CUDA events on its stream.  hf_profile_read synchronises the
+ * recorded events and accumulates, per kernel kind, the launch count and the
+ * summed device time; hf_profile_entry reads kind i (0 <= i < the count
+ * returned); hf_profile_reset clears the totals.  Kinds: "splat", "passA",
+ * "passB", "passB_fwd", "passC", "torque", "query". */
+hf_status hf_profile_enable(hf_ctx *ctx, int on);
+int hf_profile_read(hf_ctx *ctx);
+hf_status hf_profile_entry(const hf_ctx *ctx, int i, const char **name, long long *launches,
+                           double *total_ms);
+void hf_profile_reset(hf_ctx *ctx);
 
 /* ---- single-step entry points (each step of the path on its own) ---- */
 

@@ -1,0 +1,238 @@
+"""B300-native geometric-energy fields for haptic assembly (Behandish & Ilies,
+"Haptic Assembly Using Skeletal Densities and Fourier Transforms").
+
+A thin Python layer over libhf.so (include/hf.h).  Device memory comes from
+torch CUDA tensors, streams from torch streams; every step of the path runs
+in the library's sm_103a kernels.  There is no CPU fallback: without the
+built library or a CUDA device the calls raise.
+"""
+import ctypes
+
+import numpy as np
+
+from . import _binding as B
+from ._binding import HF_E, HF_F, HF_MOVING, HF_STATIONARY, HF_T, HF_TORQUE_F64, HFError  # noqa: F401
+
+__all__ = ["Context", "Part", "FieldSet", "HFError", "resample", "rfft3d", "version"]
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("paper_1711_05017_b300 needs a CUDA device (no CPU fallback)")
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t, dtype=None):
+    torch = _torch()
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def version():
+    return B.lib().hf_version().decode()
+
+
+class Context:
+    """hf_ctx: a device and an HBM budget (bytes, 0 = unbounded)."""
+
+    def __init__(self, device=0, hbm_budget_bytes=0):
+        _torch()
+        h = ctypes.c_void_p()
+        B.check(B.lib().hf_ctx_create(int(device), int(hbm_budget_bytes), ctypes.byref(h)))
+        self.handle = h
+        self.device = device
+
+    def reserved_bytes(self):
+        return B.lib().hf_ctx_reserved_bytes(self.handle)
+
+    def profile(self, on=True):
+        """Bracket every kernel launch of this context with CUDA events."""
+        B.check(B.lib().hf_profile_enable(self.handle, 1 if on else 0))
+
+    def profile_read(self, reset=False):
+        """{kernel kind: (launches, total device ms)} accumulated so far."""
+        L = B.lib()
+        n = L.hf_profile_read(self.handle)
+        out = {}
+        for i in range(n):
+            name, cnt, ms = ctypes.c_char_p(), ctypes.c_longlong(), ctypes.c_double()
+            B.check(L.hf_profile_entry(self.handle, i, ctypes.byref(name), ctypes.byref(cnt), ctypes.byref(ms)))
+            if cnt.value:
+                out[name.value.decode()] = (int(cnt.value), float(ms.value))
+        if reset:
+            L.hf_profile_reset(self.handle)
+        return out
+
+    def close(self):
+        if self.handle:
+            B.lib().hf_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- calls
+    def density_build(self, n, pts, sigma, amp=None, out=None, stream=None):
+        """hf_density_build: pts (P,3), sigma (P,), amp (P,) or None; float32 CUDA."""
+        torch = _torch()
+        P = int(sigma.numel())
+        if out is None:
+            out = torch.empty((n, n, n), dtype=torch.float32, device=sigma.device)
+        B.check(B.lib().hf_density_build(self.handle, n, _dev(pts, torch.float32), _dev(sigma, torch.float32),
+                                         None if amp is None else _dev(amp, torch.float32), P,
+                                         _dev(out, torch.float32), _stream_ptr(stream)))
+        return out
+
+    def part(self, grid, role, stream=None):
+        return Part(self, grid, role, stream)
+
+    def fieldset(self, n, R, flags=HF_E | HF_F):
+        return FieldSet(self, n, R, flags)
+
+    def fields(self, s1, s2, quat, E, Fx=None, Fy=None, Fz=None, scratch=None, stream=None):
+        """hf_fields: one rotation into caller buffers."""
+        torch = _torch()
+        n = s1.n
+        if scratch is None:
+            nb = B.lib().hf_fields_scratch_bytes(n)
+            scratch = torch.empty((nb + 15) // 16 * 4, dtype=torch.float32, device=E.device)
+        q = np.ascontiguousarray(quat, dtype=np.float32).reshape(4)
+        opt = [None if t is None else _dev(t, torch.float32) for t in (Fx, Fy, Fz)]
+        B.check(B.lib().hf_fields(self.handle, s1.handle, s2.handle, B.fptr(q), _dev(E, torch.float32), *opt,
+                                  _dev(scratch), _stream_ptr(stream)))
+        if stream is not None:
+            scratch.record_stream(stream)
+
+    def torque(self, n, quats, E, T, flags=0, stream=None):
+        """hf_torque: E (R,N,N,N) -> T (R,3,N,N,N); returns per-rotation status."""
+        torch = _torch()
+        q = np.ascontiguousarray(quats, dtype=np.float32).reshape(-1, 4)
+        R = len(q)
+        st = np.zeros(R, dtype=np.int32)
+        rc = B.lib().hf_torque(self.handle, n, R, B.fptr(q), _dev(E, torch.float32), _dev(T, torch.float32),
+                               int(flags), st.ctypes.data_as(B._ip), _stream_ptr(stream))
+        B.check(rc, allow=(B.HF_EINVAL,) if st.any() else ())
+        return st
+
+
+class Part:
+    """hf_part: HF_STATIONARY keeps the scaled spectrum, HF_MOVING the grid."""
+
+    def __init__(self, ctx, grid, role, stream=None):
+        torch = _torch()
+        n = grid.shape[0]
+        h = ctypes.c_void_p()
+        B.check(B.lib().hf_part_create(ctx.handle, n, _dev(grid, torch.float32), int(role), ctypes.byref(h),
+                                       _stream_ptr(stream)))
+        self.handle, self.n, self.role, self.ctx = h, n, role, ctx
+
+    def update(self, grid, stream=None):
+        """hf_part_update: re-derive the part from a new grid, in place."""
+        torch = _torch()
+        B.check(B.lib().hf_part_update(self.handle, _dev(grid, torch.float32), _stream_ptr(stream)))
+
+    def release(self):
+        if self.handle:
+            B.lib().hf_part_release(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+class FieldSet:
+    """hf_fieldset: energy, force (and torque) fields for R rotations."""
+
+    def __init__(self, ctx, n, R, flags=HF_E | HF_F):
+        h = ctypes.c_void_p()
+        B.check(B.lib().hf_fieldset_create(ctx.handle, int(n), int(R), int(flags), ctypes.byref(h)))
+        self.handle, self.n, self.R, self.ctx = h, n, R, ctx
+        self.flags = B.lib().hf_fieldset_flags(h)
+
+    def compute(self, s1, s2, quats, stream=None, allow_rank_deficient=False):
+        q = np.ascontiguousarray(quats, dtype=np.float32).reshape(-1, 4)
+        rc = B.lib().hf_fieldset_compute(self.ctx.handle, s1.handle, s2.handle, B.fptr(q), len(q), self.handle,
+                                         _stream_ptr(stream))
+        return B.check(rc, allow=(B.HF_EINVAL,) if allow_rank_deficient else ())
+
+    def field_ptr(self, rot, field):
+        p = ctypes.c_void_p()
+        B.check(B.lib().hf_fieldset_field_ptr(self.handle, int(rot), int(field), ctypes.byref(p)))
+        return p.value
+
+    def get(self, rot, field, out=None, stream=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty((self.n,) * 3, dtype=torch.float32, device=f"cuda:{self.ctx.device}")
+        B.check(B.lib().hf_fieldset_get(self.handle, int(rot), int(field), _dev(out, torch.float32),
+                                        _stream_ptr(stream)))
+        return out
+
+    def query(self, t, q, k=4):
+        out = np.zeros(7, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32).reshape(3)
+        q = np.ascontiguousarray(q, dtype=np.float32).reshape(4)
+        B.check(B.lib().hf_query(self.handle, B.fptr(t), B.fptr(q), int(k), B.fptr(out)))
+        return out
+
+    def query_batch(self, tq, k=4, out=None, stream=None):
+        torch = _torch()
+        Q = tq.shape[0]
+        if out is None:
+            out = torch.empty((Q, 7), dtype=torch.float32, device=tq.device)
+        B.check(B.lib().hf_query_batch(self.handle, _dev(tq, torch.float32), int(Q), int(k),
+                                       _dev(out, torch.float32), _stream_ptr(stream)))
+        return out
+
+    def release(self):
+        if self.handle:
+            B.lib().hf_fieldset_release(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+def resample(rho, R, out=None, stream=None):
+    """hf_resample: rho (N,N,N) float32 CUDA, R 3x3 -> rho(R^T x_n)."""
+    torch = _torch()
+    n = rho.shape[0]
+    if out is None:
+        out = torch.empty_like(rho)
+    r9 = np.ascontiguousarray(R, dtype=np.float32).reshape(9)
+    B.check(B.lib().hf_resample(n, _dev(rho, torch.float32), B.fptr(r9), _dev(out, torch.float32),
+                                _stream_ptr(stream)))
+    return out
+
+
+def rfft3d(x, out=None, stream=None):
+    """hf_rfft3d: (N,N,N) float32 -> (N,N,N/2+1) complex64, natural order."""
+    torch = _torch()
+    n = x.shape[0]
+    if out is None:
+        out = torch.empty((n, n, n // 2 + 1), dtype=torch.complex64, device=x.device)
+    nb = B.lib().hf_rfft3d_scratch_bytes(n)
+    scratch = torch.empty((nb + 15) // 16 * 4, dtype=torch.float32, device=x.device)
+    B.check(B.lib().hf_rfft3d(n, _dev(x, torch.float32), _dev(out), _dev(scratch), _stream_ptr(stream)))
+    if stream is not None:
+        scratch.record_stream(stream)
+    return out

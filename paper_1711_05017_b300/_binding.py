@@ -1,0 +1,92 @@
+"""ctypes binding of libhf.so (include/hf.h).  Argument marshalling only:
+every step of the path runs in the library's CUDA kernels.  Device buffers
+are torch CUDA tensors (passed as raw pointers); streams are torch streams.
+
+The library must be built (``paper_1711_05017_b300.build.build()``); there is
+no fallback: a missing library or a missing GPU raises."""
+import ctypes
+import os
+
+from .build import LIB
+
+HF_OK, HF_EINVAL, HF_ENOMEM, HF_EBUDGET, HF_ECUDA, HF_ETIMEOUT, HF_ENOTREADY, HF_EUNSUPPORTED = range(8)
+STATUS_NAMES = {0: "HF_OK", 1: "HF_EINVAL", 2: "HF_ENOMEM", 3: "HF_EBUDGET", 4: "HF_ECUDA",
+                5: "HF_ETIMEOUT", 6: "HF_ENOTREADY", 7: "HF_EUNSUPPORTED"}
+HF_STATIONARY, HF_MOVING = 0, 1
+HF_E, HF_F, HF_T, HF_TORQUE_F64 = 0x1, 0x2, 0x4, 0x10
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_u = ctypes.c_uint
+_sz = ctypes.c_size_t
+_fp = ctypes.POINTER(ctypes.c_float)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+# name -> (restype, argtypes); the ABI of include/hf.h
+SIGNATURES = {
+    "hf_version": (ctypes.c_char_p, []),
+    "hf_last_error": (ctypes.c_char_p, []),
+    "hf_ctx_create": (_i, [_i, _sz, ctypes.POINTER(_vp)]),
+    "hf_ctx_destroy": (None, [_vp]),
+    "hf_ctx_reserved_bytes": (_sz, [_vp]),
+    "hf_density_build": (_i, [_vp, _i, _vp, _vp, _vp, _i, _vp, _vp]),
+    "hf_part_create": (_i, [_vp, _i, _vp, _i, ctypes.POINTER(_vp), _vp]),
+    "hf_part_release": (None, [_vp]),
+    "hf_part_update": (_i, [_vp, _vp, _vp]),
+    "hf_profile_enable": (_i, [_vp, _i]),
+    "hf_profile_read": (_i, [_vp]),
+    "hf_profile_entry": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong),
+                             ctypes.POINTER(ctypes.c_double)]),
+    "hf_profile_reset": (None, [_vp]),
+    "hf_fieldset_create": (_i, [_vp, _i, _i, _u, ctypes.POINTER(_vp)]),
+    "hf_fieldset_compute": (_i, [_vp, _vp, _vp, _fp, _i, _vp, _vp]),
+    "hf_fieldset_build": (_i, [_vp, _vp, _vp, _fp, _i, _u, ctypes.POINTER(_vp), _vp]),
+    "hf_fieldset_get": (_i, [_vp, _i, _i, _vp, _vp]),
+    "hf_fieldset_field_ptr": (_i, [_vp, _i, _i, ctypes.POINTER(_vp)]),
+    "hf_fieldset_n": (_i, [_vp]),
+    "hf_fieldset_rotations": (_i, [_vp]),
+    "hf_fieldset_flags": (_u, [_vp]),
+    "hf_fieldset_release": (None, [_vp]),
+    "hf_query": (_i, [_vp, _fp, _fp, _i, _fp]),
+    "hf_query_batch": (_i, [_vp, _vp, _i, _i, _vp, _vp]),
+    "hf_resample": (_i, [_i, _vp, _fp, _vp, _vp]),
+    "hf_rfft3d_scratch_bytes": (_sz, [_i]),
+    "hf_rfft3d": (_i, [_i, _vp, _vp, _vp, _vp]),
+    "hf_fields_scratch_bytes": (_sz, [_i]),
+    "hf_fields": (_i, [_vp, _vp, _vp, _fp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "hf_torque": (_i, [_vp, _i, _i, _fp, _vp, _vp, _u, _ip, _vp]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded libhf.so with every ABI signature set (raises if not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"libhf.so is not built ({LIB}); run paper_1711_05017_b300.build.build()")
+        L = ctypes.CDLL(LIB)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class HFError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def check(status, allow=()):
+    if status != HF_OK and status not in allow:
+        raise HFError(status, lib().hf_last_error().decode(errors="replace"))
+    return status
+
+
+def fptr(arr):
+    """float* of a contiguous float32 numpy array (host)."""
+    return arr.ctypes.data_as(_fp)

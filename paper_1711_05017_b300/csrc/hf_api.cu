@@ -38,6 +38,9 @@ static hf_status fail(hf_status s, const char *fmt, ...) {
     } while (0)
 
 // ------------------------------------------------------------------ handles
+enum ProfKind { kSplat, kPassA, kPassB, kPassBFwd, kPassC, kTorque, kQuery, kProfKinds };
+static const char *kProfNames[kProfKinds] = {"splat", "passA", "passB", "passB_fwd", "passC", "torque", "query"};
+
 struct hf_ctx {
     int device = 0;
     size_t budget = 0, reserved = 0;
@@ -46,6 +49,17 @@ struct hf_ctx {
     float *h_qin = nullptr, *h_qout = nullptr;  // pinned 7-float mailboxes
     float *d_qin = nullptr, *d_qout = nullptr;
     std::mutex qmu;
+    // per-kernel timing
+    bool prof = false;
+    std::mutex pmu;
+    struct Rec {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    long long launches[kProfKinds] = {};
+    double ms[kProfKinds] = {};
 };
 
 struct hf_part {
@@ -88,6 +102,73 @@ static void uncharge(hf_ctx *c, size_t b) {
     c->reserved -= std::min(b, c->reserved);
 }
 
+static cudaEvent_t prof_event(hf_ctx *c) {
+    if (!c->pool.empty()) {
+        cudaEvent_t e = c->pool.back();
+        c->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Launch `fn` on `st`, bracketed by timing events when the context profiles.
+template <class F>
+static cudaError_t timed(hf_ctx *c, int kind, cudaStream_t st, F &&fn) {
+    if (!c || !c->prof) return fn();
+    std::lock_guard<std::mutex> g(c->pmu);
+    cudaEvent_t a = prof_event(c), b = prof_event(c);
+    if (!a || !b) return fn();
+    cudaEventRecord(a, st);
+    cudaError_t e = fn();
+    cudaEventRecord(b, st);
+    c->pending.push_back({kind, a, b});
+    return e;
+}
+
+extern "C" hf_status hf_profile_enable(hf_ctx *c, int on) {
+    if (!c) return fail(HF_EINVAL, "hf_profile_enable: ctx is NULL");
+    c->prof = on != 0;
+    return HF_OK;
+}
+
+extern "C" int hf_profile_read(hf_ctx *c) {
+    if (!c) return 0;
+    std::lock_guard<std::mutex> g(c->pmu);
+    cudaSetDevice(c->device);
+    for (auto &r : c->pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            c->launches[r.kind] += 1;
+            c->ms[r.kind] += ms;
+        }
+        c->pool.push_back(r.a);
+        c->pool.push_back(r.b);
+    }
+    c->pending.clear();
+    return kProfKinds;
+}
+
+extern "C" hf_status hf_profile_entry(const hf_ctx *c, int i, const char **name, long long *launches,
+                                      double *total_ms) {
+    if (!c || i < 0 || i >= kProfKinds) return fail(HF_EINVAL, "hf_profile_entry: index %d", i);
+    if (name) *name = kProfNames[i];
+    if (launches) *launches = c->launches[i];
+    if (total_ms) *total_ms = c->ms[i];
+    return HF_OK;
+}
+
+extern "C" void hf_profile_reset(hf_ctx *c) {
+    if (!c) return;
+    hf_profile_read(c);
+    std::lock_guard<std::mutex> g(c->pmu);
+    for (int k = 0; k < kProfKinds; ++k) {
+        c->launches[k] = 0;
+        c->ms[k] = 0.0;
+    }
+}
+
 extern "C" const char *hf_version(void) { return "hf 1.0 sm_103a"; }
 extern "C" const char *hf_last_error(void) { return g_err; }
 
@@ -127,6 +208,8 @@ extern "C" void hf_ctx_destroy(hf_ctx *c) {
     if (c->h_qout) cudaFreeHost(c->h_qout);
     if (c->d_qin) cudaFree(c->d_qin);
     if (c->d_qout) cudaFree(c->d_qout);
+    hf_profile_read(c);
+    for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
     delete c;
 }
 
@@ -144,14 +227,16 @@ extern "C" hf_status hf_density_build(hf_ctx *ctx, int n, const float *d_pts, co
     if (P < 0 || !d_grid_out || (P > 0 && (!d_pts || !d_sigma)))
         return fail(HF_EINVAL, "hf_density_build: bad arguments (P=%d)", P);
     CU(cudaSetDevice(ctx->device));
-    CU(hf::run_splat(n, d_pts, d_sigma, d_amp, P, d_grid_out, (cudaStream_t)stream));
+    cudaStream_t st = (cudaStream_t)stream;
+    CU(timed(ctx, kSplat, st, [&] { return hf::run_splat(n, d_pts, d_sigma, d_amp, P, d_grid_out, st); }));
     return HF_OK;
 }
 
 // --------------------------------------------------------------------- parts
 static const float kIdentity9[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};  // static: outlives async copies
 
-static hf_status stationary_spectrum(int n, const float *d_grid, float2 *spec, float scale, cudaStream_t st) {
+static hf_status stationary_spectrum(hf_ctx *c, int n, const float *d_grid, float2 *spec, float scale,
+                                     cudaStream_t st) {
     // identity "rotation": pass A's resample is then an exact copy
     const size_t he = hf::half_spec_elems(n);
     float2 *X1 = nullptr;
@@ -159,11 +244,26 @@ static hf_status stationary_spectrum(int n, const float *d_grid, float2 *spec, f
     CU(cudaMallocAsync(&X1, he * sizeof(float2), st));
     CU(cudaMallocAsync(&rot, 9 * sizeof(float), st));
     CU(cudaMemcpyAsync(rot, kIdentity9, sizeof kIdentity9, cudaMemcpyHostToDevice, st));
-    CU(hf::run_passA(n, d_grid, rot, X1, 1, st));
-    CU(hf::run_passB_forward(n, X1, spec, scale, st));
+    CU(timed(c, kPassA, st, [&] { return hf::run_passA(n, d_grid, rot, X1, 1, st); }));
+    CU(timed(c, kPassBFwd, st, [&] { return hf::run_passB_forward(n, X1, spec, scale, st); }));
     CU(cudaFreeAsync(X1, st));
     CU(cudaFreeAsync(rot, st));
     return HF_OK;
+}
+
+// (h^3 / N^3) in float64: the Riemann-sum volume element of Eq. 1 and the
+// inverse transform's normalisation, rounded once
+static float spectrum_scale(int n) {
+    const double h = 2.0 / n;
+    return (float)(h * h * h / ((double)n * n * n));
+}
+
+static hf_status part_fill(hf_part *p, const float *d_grid, cudaStream_t st) {
+    if (p->role == HF_MOVING) {
+        CU(cudaMemcpyAsync(p->grid, d_grid, p->bytes, cudaMemcpyDeviceToDevice, st));
+        return HF_OK;
+    }
+    return stationary_spectrum(p->ctx, p->n, d_grid, p->spec, spectrum_scale(p->n), st);
 }
 
 extern "C" hf_status hf_part_create(hf_ctx *ctx, int n, const float *d_grid, int role, hf_part **out,
@@ -189,19 +289,9 @@ extern "C" hf_status hf_part_create(hf_ctx *ctx, int n, const float *d_grid, int
         uncharge(ctx, bytes);
         return fail(HF_ENOMEM, "hf_part_create: cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
     }
-    hf_status s = HF_OK;
-    if (role == HF_MOVING) {
-        p->grid = (float *)mem;
-        e = cudaMemcpyAsync(p->grid, d_grid, bytes, cudaMemcpyDeviceToDevice, st);
-        if (e != cudaSuccess) s = fail(HF_ECUDA, "hf_part_create: %s", cudaGetErrorString(e));
-    } else {
-        p->spec = (float2 *)mem;
-        // h^3 / N^3 in float64: the Riemann-sum volume element of Eq. 1 and
-        // the inverse transform's normalisation, rounded once
-        const double h = 2.0 / n;
-        const double scale = h * h * h / ((double)n * n * n);
-        s = stationary_spectrum(n, d_grid, p->spec, (float)scale, st);
-    }
+    if (role == HF_MOVING) p->grid = (float *)mem;
+    else p->spec = (float2 *)mem;
+    hf_status s = part_fill(p, d_grid, st);
     if (s != HF_OK) {
         cudaFree(mem);
         delete p;
@@ -210,6 +300,12 @@ extern "C" hf_status hf_part_create(hf_ctx *ctx, int n, const float *d_grid, int
     }
     *out = p;
     return HF_OK;
+}
+
+extern "C" hf_status hf_part_update(hf_part *p, const float *d_grid, hf_stream stream) {
+    if (!p || !d_grid) return fail(HF_EINVAL, "hf_part_update: NULL argument");
+    CU(cudaSetDevice(p->ctx->device));
+    return part_fill(p, d_grid, (cudaStream_t)stream);
 }
 
 extern "C" void hf_part_release(hf_part *p) {
@@ -427,12 +523,12 @@ extern "C" unsigned hf_fieldset_flags(const hf_fieldset *fs) { return fs ? fs->f
 
 // the energy/force passes for `cnt` rotations whose float matrices are at
 // rot9 (cnt x 9, device); outputs through `out` (first rotation at out.E)
-static hf_status run_fields(int n, const hf_part *s1, const hf_part *s2, const float *rot9, int cnt,
+static hf_status run_fields(hf_ctx *c, int n, const hf_part *s1, const hf_part *s2, const float *rot9, int cnt,
                             float2 *scratch, size_t scratch_rot, FieldPtrs out, cudaStream_t st) {
     float2 *X1 = scratch, *Y1 = scratch + scratch_rot, *Y2 = scratch + 2 * scratch_rot;
-    CU(hf::run_passA(n, s2->grid, rot9, X1, cnt, st));
-    CU(hf::run_passB(n, X1, s1->spec, Y1, Y2, cnt, st));
-    CU(hf::run_passC(n, Y1, Y2, out, cnt, st));
+    CU(timed(c, kPassA, st, [&] { return hf::run_passA(n, s2->grid, rot9, X1, cnt, st); }));
+    CU(timed(c, kPassB, st, [&] { return hf::run_passB(n, X1, s1->spec, Y1, Y2, cnt, st); }));
+    CU(timed(c, kPassC, st, [&] { return hf::run_passC(n, Y1, Y2, out, cnt, st); }));
     return HF_OK;
 }
 
@@ -503,12 +599,14 @@ extern "C" hf_status hf_fieldset_compute(hf_ctx *ctx, const hf_part *s1, const h
         out.Fx = base + n3;
         out.Fy = base + 2 * n3;
         out.Fz = base + 3 * n3;
-        s = run_fields(n, s1, s2, fs->d_rot9 + (size_t)9 * r0, cnt, fs->scratch, scr_rot, out, st);
+        s = run_fields(ctx, n, s1, s2, fs->d_rot9 + (size_t)9 * r0, cnt, fs->scratch, scr_rot, out, st);
         if (s != HF_OK) return s;
     }
     if (fs->flags & HF_T) {
-        CU(hf::run_torque(n, R, fs->data, rs, fs->data + (size_t)fs->slot[4] * n3, rs, fs->d_nbr, fs->d_P,
-                          fs->d_P64, (fs->flags & HF_TORQUE_F64) != 0, st));
+        CU(timed(ctx, kTorque, st, [&] {
+            return hf::run_torque(n, R, fs->data, rs, fs->data + (size_t)fs->slot[4] * n3, rs, fs->d_nbr, fs->d_P,
+                                  fs->d_P64, (fs->flags & HF_TORQUE_F64) != 0, st);
+        }));
     }
     fs->ready = true;
     if (bad) return fail(HF_EINVAL, "hf_fieldset_compute: %d rotation(s) with a rank-deficient neighbourhood", bad);
@@ -583,7 +681,8 @@ extern "C" hf_status hf_query_batch(const hf_fieldset *fs, const float *d_tq, in
     if (k < 1 || k > 8 || k > fs->R) return fail(HF_EINVAL, "hf_query_batch: k_blend=%d", k);
     if (!fs->ready) return fail(HF_ENOTREADY, "hf_query_batch: field set not computed");
     CU(cudaSetDevice(fs->ctx->device));
-    CU(hf::run_query(query_geom(fs), d_tq, Q, k, d_out, (cudaStream_t)stream));
+    cudaStream_t st = (cudaStream_t)stream;
+    CU(timed(fs->ctx, kQuery, st, [&] { return hf::run_query(query_geom(fs), d_tq, Q, k, d_out, st); }));
     return HF_OK;
 }
 
@@ -661,7 +760,7 @@ extern "C" hf_status hf_fields(hf_ctx *ctx, const hf_part *s1, const hf_part *s2
     for (int k = 0; k < 9; ++k) m9[k] = (float)M[k];
     CU(cudaMemcpyAsync(rot, m9, sizeof m9, cudaMemcpyHostToDevice, st));
     FieldPtrs out{d_E, d_Fx ? d_Fx : dummy, d_Fy ? d_Fy : dummy + n3, d_Fz ? d_Fz : dummy + 2 * n3, 0};
-    s = run_fields(n, s1, s2, rot, 1, scr, he, out, st);
+    s = run_fields(ctx, n, s1, s2, rot, 1, scr, he, out, st);
     if (s != HF_OK) return s;
     CU(cudaStreamSynchronize(st));  // m9 lives on this stack frame
     return HF_OK;
@@ -693,7 +792,9 @@ extern "C" hf_status hf_torque(hf_ctx *ctx, int n, int R, const float *h_quat, c
     CU(cudaMemcpyAsync(d_P, P32.data(), P32.size() * sizeof(float), cudaMemcpyHostToDevice, st));
     CU(cudaMemcpyAsync(d_P64, P64.data(), P64.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     const size_t n3 = (size_t)n * n * n;
-    CU(hf::run_torque(n, R, d_E, n3, d_T, 3 * n3, d_nbr, d_P, d_P64, (flags & HF_TORQUE_F64) != 0, st));
+    CU(timed(ctx, kTorque, st, [&] {
+        return hf::run_torque(n, R, d_E, n3, d_T, 3 * n3, d_nbr, d_P, d_P64, (flags & HF_TORQUE_F64) != 0, st);
+    }));
     CU(cudaFreeAsync(d_nbr, st));
     CU(cudaFreeAsync(d_P, st));
     CU(cudaFreeAsync(d_P64, st));

@@ -1,0 +1,308 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element
+by element, on seeded synthetic inputs.  Tolerance (the float32 bar):
+max |gpu - oracle| <= 1e-5 * max |oracle field|, per field."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def hf():
+    import torch
+    import paper_1711_05017_b300 as hf_
+    from paper_1711_05017_b300 import build
+    build.build()
+    assert torch.cuda.is_available()
+    return hf_
+
+
+@pytest.fixture(scope="module")
+def ctx(hf):
+    return hf.Context(0)
+
+
+def cuda(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def rel_err(got, ref):
+    return np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)
+
+
+def norm_quats(q32):
+    q = np.asarray(q32, dtype=np.float32).astype(np.float64).reshape(-1, 4)
+    return q / np.linalg.norm(q, axis=1, keepdims=True)
+
+
+# ------------------------------------------------------------------ splat
+
+@pytest.mark.parametrize("n,which", [(32, "c1"), (64, "c2"), (96, "c2")])
+def test_splat_parity(ctx, n, which):
+    s1, s2 = synth.c1_pair(0) if which == "c1" else synth.c2_pair(0)
+    for part in (s1, s2):
+        pts32 = part.pts.astype(np.float32)
+        sig32 = part.sigma.astype(np.float32)
+        got = host(ctx.density_build(n, cuda(pts32), cuda(sig32)))
+        ref = oracle.splat(n, pts32.astype(np.float64), sig32.astype(np.float64))
+        assert rel_err(got, ref) <= TOL
+
+
+def test_splat_signed_amplitudes_and_empty(ctx):
+    import torch
+    rng = np.random.default_rng(4)
+    pts = rng.uniform(-1, 1, (300, 3)).astype(np.float32)
+    sig = rng.uniform(0.03, 0.12, 300).astype(np.float32)
+    amp = rng.uniform(-2, 2, 300).astype(np.float32)
+    got = host(ctx.density_build(64, cuda(pts), cuda(sig), cuda(amp)))
+    ref = oracle.splat(64, pts.astype(np.float64), sig.astype(np.float64), amp.astype(np.float64))
+    assert rel_err(got, ref) <= TOL
+    out = torch.full((32, 32, 32), 7.0, device="cuda")
+    e = torch.empty(0, device="cuda")
+    ctx.density_build(32, e.reshape(0, 3), e, out=out)
+    assert float(out.abs().max()) == 0.0
+
+
+# --------------------------------------------------------------- resample
+
+@pytest.mark.parametrize("n", [32, 64, 96, 128])
+def test_resample_parity(hf, n):
+    rng = np.random.default_rng(n)
+    rho = rng.standard_normal((n, n, n)).astype(np.float32)
+    d = cuda(rho)
+    assert np.array_equal(host(hf.resample(d, np.eye(3))), rho.astype(np.float64))  # identity: exact copy
+    for q in synth.random_quaternions(100 + n, 3):
+        R = oracle.quat_to_rot(q)
+        got = host(hf.resample(d, R))
+        ref = oracle.resample(rho.astype(np.float64), R.astype(np.float32).astype(np.float64))
+        assert rel_err(got, ref) <= TOL
+
+
+# -------------------------------------------------------------------- FFT
+
+@pytest.mark.parametrize("n", [32, 64, 96, 128])
+def test_rfft3d_parity(hf, n):
+    rng = np.random.default_rng(200 + n)
+    x = rng.standard_normal((n, n, n)).astype(np.float32)
+    got = hf.rfft3d(cuda(x))
+    import torch
+    torch.cuda.synchronize()
+    g = got.cpu().numpy().astype(np.complex128)
+    ref = oracle.fft3d(x.astype(np.float64), -1)[:, :, : n // 2 + 1]
+    assert np.abs(g - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+# ----------------------------------------------------------------- fields
+
+def gpu_fields(hf, ctx, rho1, rho2, q):
+    import torch
+    n = rho1.shape[0]
+    s1 = ctx.part(cuda(rho1), hf.HF_STATIONARY)
+    s2 = ctx.part(cuda(rho2), hf.HF_MOVING)
+    out = [torch.empty((n, n, n), device="cuda") for _ in range(4)]
+    ctx.fields(s1, s2, q, *out)
+    return [host(o) for o in out]
+
+
+def test_fields_c1_identity_vs_direct_sum(hf, ctx):
+    """32^3 ring/peg workload, identity rotation: E against the direct O(N^6)
+    correlation sum, F against the oracle's spectral force."""
+    s1, s2 = synth.c1_pair(0)
+    r1 = oracle.splat(32, s1.pts, s1.sigma).astype(np.float32)
+    r2 = oracle.splat(32, s2.pts, s2.sigma).astype(np.float32)
+    E, Fx, Fy, Fz = gpu_fields(hf, ctx, r1, r2, [1, 0, 0, 0])
+    r1d, r2d = r1.astype(np.float64), r2.astype(np.float64)
+    assert rel_err(E, oracle.correlate_direct(r1d, r2d)) <= TOL
+    ref = oracle.fields(r1d, r2d)
+    for g, r in zip((E, Fx, Fy, Fz), ref):
+        assert rel_err(g, r) <= TOL
+
+
+@pytest.mark.parametrize("n", [32, 64, 96, 128])
+def test_fields_rotated_parity(hf, ctx, n):
+    s1, s2 = synth.c2_pair(0) if n >= 64 else synth.c1_pair(0)
+    r1 = oracle.splat(n, s1.pts[:1500], s1.sigma[:1500]).astype(np.float32)
+    r2 = oracle.splat(n, s2.pts[:1500], s2.sigma[:1500]).astype(np.float32)
+    for q in synth.random_quaternions(300 + n, 2 if n < 128 else 1):
+        got = gpu_fields(hf, ctx, r1, r2, q)
+        qn = norm_quats(q.astype(np.float32))[0]
+        R = oracle.quat_to_rot(qn).astype(np.float32).astype(np.float64)
+        ref = oracle.fields(r1.astype(np.float64), oracle.resample(r2.astype(np.float64), R))
+        for g, r in zip(got, ref):
+            assert rel_err(g, r) <= TOL
+
+
+def test_fields_ragged_odd_size_and_gaussian_closed_form(hf, ctx):
+    """96 = 2^5 * 3 (radix-3 stages) with single Gaussians: the GPU energy
+    also sits on the continuous closed form within the float32 bar."""
+    n = 96
+    h = 2.0 / n
+    s1, s2 = 3 * h, 3.5 * h
+    c1, c2 = np.array([0.11, -0.23, 0.05]), np.array([-0.3, 0.17, 0.2])
+    r1 = oracle.splat(n, c1[None], np.array([s1]), cutoff=10.0).astype(np.float32)
+    r2 = oracle.splat(n, c2[None], np.array([s2]), cutoff=10.0).astype(np.float32)
+    E, *_ = gpu_fields(hf, ctx, r1, r2, [1, 0, 0, 0])
+    S = s1**2 + s2**2
+    pref = (2 * np.pi * s1**2 * s2**2 / S) ** 1.5
+    j = np.arange(n)
+    z, y, x = np.meshgrid(j, j, j, indexing="ij")
+    t = np.stack([x, y, z], -1) * h
+    Ec = np.zeros((n, n, n))
+    for m in np.ndindex(3, 3, 3):
+        r = c1 - c2 - (t + 2.0 * (np.array(m) - 1))
+        Ec += pref * np.exp(-(r**2).sum(-1) / (2 * S))
+    assert rel_err(E, Ec) <= TOL
+
+
+# ------------------------------------------------------ field set, torque, query
+
+@pytest.fixture(scope="module")
+def small_set(hf, ctx):
+    n, R = 32, 24
+    s1, s2 = synth.c1_pair(1)
+    r1 = oracle.splat(n, s1.pts, s1.sigma).astype(np.float32)
+    r2 = oracle.splat(n, s2.pts, s2.sigma).astype(np.float32)
+    q = synth.random_quaternions(77, R).astype(np.float32)
+    p1 = ctx.part(cuda(r1), hf.HF_STATIONARY)
+    p2 = ctx.part(cuda(r2), hf.HF_MOVING)
+    fs = ctx.fieldset(n, R, hf.HF_E | hf.HF_F | hf.HF_T)
+    fs.compute(p1, p2, q)
+    qn = norm_quats(q)
+    ref = np.stack([np.stack(oracle.fields(r1.astype(np.float64), oracle.resample(
+        r2.astype(np.float64), oracle.quat_to_rot(qq).astype(np.float32).astype(np.float64)))) for qq in qn])
+    T, st = oracle.torque(qn, ref[:, 0], 6)
+    assert (st == 0).all()
+    return dict(n=n, R=R, q=q, qn=qn, fs=fs, ref=ref, T=T, p=(p1, p2), r=(r1, r2))
+
+
+def test_fieldset_energy_force_torque(hf, small_set):
+    fs, ref, T = small_set["fs"], small_set["ref"], small_set["T"]
+    for f in range(4):
+        got = np.stack([host(fs.get(r, f)) for r in range(small_set["R"])])
+        assert rel_err(got, ref[:, f]) <= TOL, f
+    for d in range(3):
+        got = np.stack([host(fs.get(r, 4 + d)) for r in range(small_set["R"])])
+        assert rel_err(got, T[:, d]) <= TOL, d
+
+
+def test_torque_float64_variant(hf, ctx, small_set):
+    import torch
+    n, R = small_set["n"], small_set["R"]
+    fs = small_set["fs"]
+    E = torch.stack([fs.get(r, 0) for r in range(R)]).contiguous()
+    for flags in (0, hf.HF_TORQUE_F64):
+        T = torch.empty((R, 3, n, n, n), device="cuda")
+        st = ctx.torque(n, small_set["q"], E, T, flags=flags)
+        assert (st == 0).all()
+        assert rel_err(host(T), small_set["T"]) <= TOL
+
+
+def test_query_batch_and_single(hf, small_set):
+    import torch
+    fs, qn, n = small_set["fs"], small_set["qn"], small_set["n"]
+    fields7 = np.concatenate([small_set["ref"], np.moveaxis(small_set["T"], 1, 1)], axis=1)
+    rng = np.random.default_rng(5)
+    Q = 64
+    t = rng.uniform(-1.5, 1.5, (Q, 3))
+    qs = synth.random_quaternions(91, Q)
+    qs[:4] = small_set["q"][:4]  # exact member rotations
+    t[4:8] = np.array([[3, 5, 7], [0, 0, 0], [31, 1, 2], [-1, -2, 40]]) * (2.0 / n)  # nodes
+    tq = np.concatenate([t, qs], axis=1).astype(np.float32)
+    scale = np.abs(fields7).reshape(len(qn), 7, -1).max(axis=(0, 2))
+    for k in (1, 4, 6):
+        got = host(fs.query_batch(cuda(tq), k=k))
+        ref = np.stack([oracle.query(qn, fields7, tq[i, :3].astype(np.float64),
+                                     tq[i, 3:].astype(np.float64), k) for i in range(Q)])
+        assert (np.abs(got - ref) / scale).max() <= TOL, k
+    one = fs.query(tq[10, :3], tq[10, 3:], k=4)
+    ref = oracle.query(qn, fields7, tq[10, :3].astype(np.float64), tq[10, 3:].astype(np.float64), 4)
+    assert (np.abs(one - ref) / scale).max() <= TOL
+    del torch
+
+
+# ----------------------------------------------------------------- errors
+
+def test_errors_are_status_codes(hf, ctx, small_set):
+    import torch
+    from paper_1711_05017_b300 import _binding as B
+    with pytest.raises(hf.HFError) as e:
+        ctx.density_build(48, torch.zeros((1, 3), device="cuda"), torch.ones(1, device="cuda"))
+    assert e.value.status == B.HF_EUNSUPPORTED
+    with pytest.raises(hf.HFError) as e:
+        ctx.fieldset(32, 5, hf.HF_E | hf.HF_F | hf.HF_T)
+    assert e.value.status == B.HF_EINVAL
+    with pytest.raises(hf.HFError) as e:
+        small_set["fs"].query([0, 0, 0], [1, 0, 0, 0], k=9)
+    assert e.value.status == B.HF_EINVAL
+    fs2 = ctx.fieldset(32, 8)
+    with pytest.raises(hf.HFError) as e:
+        fs2.query([0, 0, 0], [1, 0, 0, 0])
+    assert e.value.status == B.HF_ENOTREADY
+    small = hf.Context(0, hbm_budget_bytes=1 << 20)
+    with pytest.raises(hf.HFError) as e:
+        small.fieldset(64, 4)
+    assert e.value.status == B.HF_EBUDGET
+
+
+def test_rank_deficient_rotation_set_flags_nan(hf, ctx, small_set):
+    """All rotations about one axis: the torque neighbourhood has rank 1."""
+    n = 32
+    angs = np.linspace(-0.6, 0.6, 9)
+    q = np.array([[np.cos(a / 2), 0, 0, np.sin(a / 2)] for a in angs], dtype=np.float32)
+    p1, p2 = small_set["p"]
+    fs = ctx.fieldset(n, len(q), hf.HF_E | hf.HF_F | hf.HF_T)
+    rc = fs.compute(p1, p2, q, allow_rank_deficient=True)
+    assert rc == 1  # HF_EINVAL after computing everything else
+    assert np.isnan(host(fs.get(0, 4))).all()
+    assert np.isfinite(host(fs.get(0, 0))).all()
+
+
+# ------------------------------------------- full-size workload, sampled
+
+@pytest.mark.slow
+def test_c2_full_size_sampled(hf, ctx):
+    """128^3, 1024 rotations in the benchmark's launch configuration; sampled
+    rotations against the oracle one by one, torque of a sampled rotation
+    from the oracle's least squares over its 6 neighbours."""
+    import torch
+    n, R = 128, 1024
+    s1, s2 = synth.c2_pair(0)
+    g1 = ctx.density_build(n, cuda(s1.pts), cuda(s1.sigma))
+    g2 = ctx.density_build(n, cuda(s2.pts), cuda(s2.sigma))
+    q = synth.random_quaternions(0, R).astype(np.float32)
+    p1, p2 = ctx.part(g1, hf.HF_STATIONARY), ctx.part(g2, hf.HF_MOVING)
+    fs = ctx.fieldset(n, R, hf.HF_E | hf.HF_F | hf.HF_T)
+    fs.compute(p1, p2, q)
+    r1, r2 = host(g1), host(g2)
+    qn = norm_quats(q)
+    cache = {}
+
+    def ofields(i):
+        if i not in cache:
+            R_ = oracle.quat_to_rot(qn[i]).astype(np.float32).astype(np.float64)
+            cache[i] = np.stack(oracle.fields(r1, oracle.resample(r2, R_)))
+        return cache[i]
+
+    for i in (0, 1023):
+        ref = ofields(i)
+        for f in range(4):
+            assert rel_err(host(fs.get(i, f)), ref[f]) <= TOL, (i, f)
+    nb, _ = oracle.nearest(qn, qn[0], 6, skip=0)
+    sub = [0] + list(nb)
+    T, st = oracle.torque(qn[sub], np.stack([ofields(i)[0] for i in sub]), 6)
+    assert st[0] == 0
+    for d in range(3):
+        assert rel_err(host(fs.get(0, 4 + d)), T[0, d]) <= TOL, d
+    del torch
