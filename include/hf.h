@@ -216,6 +216,29 @@ hf_status hf_fields(hf_ctx *ctx, const hf_part *s1, const hf_part *s2, const flo
 hf_status hf_torque(hf_ctx *ctx, int n, int R, const float *h_quat, const float *d_E, float *d_T,
                     unsigned flags, int *h_status, hf_stream stream);
 
+/* ---- energy and force without device allocation ----
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not allocate device memory while they run -- a 1 kHz haptic loop, where a
+ * cudaMalloc/cudaFree can stall the device well past the frame budget; a
+ * plug-in whose host application owns all device memory; a runtime that
+ * forbids allocation after start-up.  It computes what hf_fields computes
+ * (energy and force of the rotated moving density against the stationary
+ * one, Eqs. 3, 5, 6a) directly from the two caller-owned N^3 grids d_rho1
+ * (stationary) and d_rho2 (moving) into the caller-owned N^3 outputs (all
+ * four required), and allocates nothing: its intermediates live in one
+ * static device array of HF_NOALLOC_MAX_N-sized buffers (about 4.3 MB) that
+ * every GPU loading the library holds until the process exits.
+ *   - N must be 32 or 64 (N > HF_NOALLOC_MAX_N: HF_EINVAL with a message).
+ *   - All calls share that array: calls whose GPU work overlaps (other
+ *     streams or threads) race and give wrong results; order them.
+ *   - The first call on a device resolves the array's address and sets
+ *     kernel attributes with that device current; make it before any
+ *     stream capture.
+ * Errors: HF_EINVAL, HF_ECUDA (message in hf_last_error()). */
+#define HF_NOALLOC_MAX_N 64
+hf_status hf_fields_noalloc(int n, const float *d_rho1, const float *d_rho2, const float h_quat[4],
+                            float *d_E, float *d_Fx, float *d_Fy, float *d_Fz, hf_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -55,6 +55,7 @@ SIGNATURES = {
     "hf_fields_scratch_bytes": (_sz, [_i]),
     "hf_fields": (_i, [_vp, _vp, _vp, _fp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "hf_torque": (_i, [_vp, _i, _i, _fp, _vp, _vp, _u, _ip, _vp]),
+    "hf_fields_noalloc": (_i, [_i, _vp, _vp, _fp, _vp, _vp, _vp, _vp, _vp]),
 }
 
 _lib = None

@@ -29,6 +29,10 @@ static hf_status fail(hf_status s, const char *fmt, ...) {
     return s;
 }
 
+namespace hf {
+void set_last_error(const char *msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+}  // namespace hf
+
 #define CU(call)                                                                                   \
     do {                                                                                           \
         cudaError_t e_ = (call);                                                                   \

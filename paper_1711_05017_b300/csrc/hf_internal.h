@@ -22,6 +22,9 @@ inline bool supported_n(int n) { return n == 32 || n == 64 || n == 96 || n == 12
 // elements of one half-spectrum intermediate (complex): N * N * (N/2 + 1)
 inline size_t half_spec_elems(int n) { return (size_t)n * n * (n / 2 + 1); }
 
+// hf_api.cu: the calling thread's message for hf_last_error()
+void set_last_error(const char *msg);
+
 // hf_fft.cu
 cudaError_t fft_init_attrs(int n);
 cudaError_t run_passA(int n, const float *rho, const float *rot9, float2 *X1, int nrot, cudaStream_t st);
