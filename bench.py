@@ -191,7 +191,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- roofline of the dominant kernel (algorithmic bytes / event-timed duration)
     he = n * n * (n // 2 + 1) * 8  # one half-spectrum intermediate, bytes
     n3b = 4 * n**3
-    chunk = min({32: 64, 64: 32, 96: 12}.get(n, 8), R) if not os.environ.get("HF_ROT_CHUNK") else int(os.environ["HF_ROT_CHUNK"])
+    chunk = min({32: 256, 64: 128, 96: 48}.get(n, 32), R) if not os.environ.get("HF_ROT_CHUNK") else int(os.environ["HF_ROT_CHUNK"])
     alg = {  # bytes per launch: inputs read once + outputs written
         "passA": n3b + chunk * he,
         "passB": chunk * he + he + 2 * chunk * he,
@@ -354,7 +354,7 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_GRID)

@@ -112,8 +112,8 @@ size_t hf_ctx_reserved_bytes(const hf_ctx *ctx);
 hf_status hf_density_build(hf_ctx *ctx, int n, const float *d_pts, const float *d_sigma,
                            const float *d_amp, int P, float *d_grid_out, hf_stream stream);
 
-/* Make a part from an N^3 density grid (caller-owned, read by the call's
- * stream work).  HF_STATIONARY parts keep (h^3/N^3) F{rho1} (Eq. 7a with the
+/* Make a part from an N^3 density grid (caller-owned, 8-byte aligned, read by
+ * the call's stream work).  HF_STATIONARY parts keep (h^3/N^3) F{rho1} (Eq. 7a with the
  * volume element and the inverse's normalisation folded in); HF_MOVING parts
  * keep a copy of the grid.  Errors: HF_EINVAL, HF_EBUDGET, HF_ENOMEM, HF_ECUDA. */
 hf_status hf_part_create(hf_ctx *ctx, int n, const float *d_grid, int role, hf_part **out,
@@ -180,7 +180,7 @@ hf_status hf_query_batch(const hf_fieldset *fs, const float *d_tq, int Q, int k_
  * recorded events and accumulates, per kernel kind, the launch count and the
  * summed device time; hf_profile_entry reads kind i (0 <= i < the count
  * returned); hf_profile_reset clears the totals.  Kinds: "splat", "passA",
- * "passB", "passB_fwd", "passC", "torque", "query". */
+ * "passB", "passB_fwd", "passC", "torque", "query", "resample". */
 hf_status hf_profile_enable(hf_ctx *ctx, int on);
 int hf_profile_read(hf_ctx *ctx);
 hf_status hf_profile_entry(const hf_ctx *ctx, int i, const char **name, long long *launches,
@@ -194,7 +194,7 @@ void hf_profile_reset(hf_ctx *ctx);
 hf_status hf_resample(int n, const float *d_rho, const float h_R[9], float *d_out, hf_stream stream);
 
 /* Forward 3D real-to-complex DFT (Eq. 7a, unscaled, e^{-2 pi i k n / N}) of
- * d_in (N^3 floats).  d_out: N x N x (N/2+1) complex64 as interleaved floats,
+ * d_in (N^3 floats, 8-byte aligned).  d_out: N x N x (N/2+1) complex64 as interleaved floats,
  * [kz][ky][kx] in natural frequency order.  d_scratch: at least
  * hf_rfft3d_scratch_bytes(n) bytes of device memory, 16-byte aligned. */
 size_t hf_rfft3d_scratch_bytes(int n);

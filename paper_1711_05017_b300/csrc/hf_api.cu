@@ -42,8 +42,9 @@ void set_last_error(const char *msg) { snprintf(g_err, sizeof g_err, "%s", msg);
     } while (0)
 
 // ------------------------------------------------------------------ handles
-enum ProfKind { kSplat, kPassA, kPassB, kPassBFwd, kPassC, kTorque, kQuery, kProfKinds };
-static const char *kProfNames[kProfKinds] = {"splat", "passA", "passB", "passB_fwd", "passC", "torque", "query"};
+enum ProfKind { kSplat, kPassA, kPassB, kPassBFwd, kPassC, kTorque, kQuery, kResample, kProfKinds };
+static const char *kProfNames[kProfKinds] = {"splat",  "passA", "passB", "passB_fwd",
+                                             "passC",  "torque", "query", "resample"};
 
 struct hf_ctx {
     int device = 0;
@@ -72,6 +73,12 @@ struct hf_part {
     float *grid;   // HF_MOVING: N^3
     float2 *spec;  // HF_STATIONARY: (h^3/N^3) rho1^ in [ky*][kz*][kx*] slot order
     size_t bytes;
+    // HF_MOVING: the grid as stacked padded z-slices in a gather-capable 2D
+    // array, (N+1) wide and N(N+1) high, sampled by 2x2 texture gathers
+    float *slab = nullptr;
+    size_t slab_pitch = 0;  // bytes
+    cudaArray_t arr = nullptr;
+    cudaTextureObject_t tex = 0;
 };
 
 struct hf_fieldset {
@@ -82,6 +89,7 @@ struct hf_fieldset {
     int slot[7];                 // field index -> slot within a rotation block, -1 if not held
     float *data = nullptr;       // R x nf x N^3
     float2 *scratch = nullptr;   // 3 x chunk x N*N*(N/2+1): X1, Y1, Y2
+    float *planes = nullptr;     // chunk x N^3: the chunk's resampled moving densities
     float *d_rot9 = nullptr;     // R x 9
     double *d_quat = nullptr;    // R x 4 (normalised)
     int *d_nbr = nullptr;        // R x 6
@@ -237,21 +245,15 @@ extern "C" hf_status hf_density_build(hf_ctx *ctx, int n, const float *d_pts, co
 }
 
 // --------------------------------------------------------------------- parts
-static const float kIdentity9[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};  // static: outlives async copies
-
 static hf_status stationary_spectrum(hf_ctx *c, int n, const float *d_grid, float2 *spec, float scale,
                                      cudaStream_t st) {
-    // identity "rotation": pass A's resample is then an exact copy
+    // pass A with the identity: a plain copy of each plane into the transform
     const size_t he = hf::half_spec_elems(n);
     float2 *X1 = nullptr;
-    float *rot = nullptr;
     CU(cudaMallocAsync(&X1, he * sizeof(float2), st));
-    CU(cudaMallocAsync(&rot, 9 * sizeof(float), st));
-    CU(cudaMemcpyAsync(rot, kIdentity9, sizeof kIdentity9, cudaMemcpyHostToDevice, st));
-    CU(timed(c, kPassA, st, [&] { return hf::run_passA(n, d_grid, rot, X1, 1, st); }));
+    CU(timed(c, kPassA, st, [&] { return hf::run_passA_planes(n, d_grid, X1, 1, st); }));
     CU(timed(c, kPassBFwd, st, [&] { return hf::run_passB_forward(n, X1, spec, scale, st); }));
     CU(cudaFreeAsync(X1, st));
-    CU(cudaFreeAsync(rot, st));
     return HF_OK;
 }
 
@@ -264,10 +266,59 @@ static float spectrum_scale(int n) {
 
 static hf_status part_fill(hf_part *p, const float *d_grid, cudaStream_t st) {
     if (p->role == HF_MOVING) {
-        CU(cudaMemcpyAsync(p->grid, d_grid, p->bytes, cudaMemcpyDeviceToDevice, st));
+        const int n = p->n;
+        CU(cudaMemcpyAsync(p->grid, d_grid, (size_t)n * n * n * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        if (p->arr) {
+            CU(hf::run_pad_slices(n, d_grid, p->slab, p->slab_pitch / sizeof(float), st));
+            CU(cudaMemcpy2DToArrayAsync(p->arr, 0, 0, p->slab, p->slab_pitch, (size_t)(n + 1) * sizeof(float),
+                                        (size_t)n * (n + 1), cudaMemcpyDeviceToDevice, st));
+        }
         return HF_OK;
     }
     return stationary_spectrum(p->ctx, p->n, d_grid, p->spec, spectrum_scale(p->n), st);
+}
+
+static void moving_texture_free(hf_part *p) {
+    if (p->tex) cudaDestroyTextureObject(p->tex);
+    if (p->arr) cudaFreeArray(p->arr);
+    if (p->slab) cudaFree(p->slab);
+    p->tex = 0;
+    p->arr = nullptr;
+    p->slab = nullptr;
+}
+
+// the gather-capable array + texture object of a moving part; when the device
+// cannot hold the stacked slices in one gather array, the part keeps only the
+// plain grid and the resample reads it with ordinary loads
+static hf_status moving_texture_alloc(hf_part *p) {
+    const int n = p->n;
+    int maxw = 0, maxh = 0;
+    if (cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxTexture2DGatherWidth, p->ctx->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&maxh, cudaDevAttrMaxTexture2DGatherHeight, p->ctx->device) != cudaSuccess ||
+        n + 1 > maxw || (long)n * (n + 1) > maxh)
+        return HF_OK;
+    const size_t w = (size_t)(n + 1), h = (size_t)n * (n + 1);
+    cudaChannelFormatDesc fd = cudaCreateChannelDesc<float>();
+    CU(cudaMallocPitch(&p->slab, &p->slab_pitch, w * sizeof(float), h));
+    cudaError_t e = cudaMallocArray(&p->arr, &fd, w, h, cudaArrayTextureGather);
+    if (e == cudaSuccess) {
+        cudaResourceDesc rd = {};
+        rd.resType = cudaResourceTypeArray;
+        rd.res.array.array = p->arr;
+        cudaTextureDesc td = {};
+        td.addressMode[0] = cudaAddressModeClamp;
+        td.addressMode[1] = cudaAddressModeClamp;
+        td.filterMode = cudaFilterModePoint;
+        td.readMode = cudaReadModeElementType;
+        td.normalizedCoords = 0;
+        e = cudaCreateTextureObject(&p->tex, &rd, &td, nullptr);
+    }
+    if (e != cudaSuccess) {
+        moving_texture_free(p);
+        return fail(e == cudaErrorMemoryAllocation ? HF_ENOMEM : HF_ECUDA, "hf_part_create: texture: %s",
+                    cudaGetErrorString(e));
+    }
+    return HF_OK;
 }
 
 extern "C" hf_status hf_part_create(hf_ctx *ctx, int n, const float *d_grid, int role, hf_part **out,
@@ -276,10 +327,13 @@ extern "C" hf_status hf_part_create(hf_ctx *ctx, int n, const float *d_grid, int
     *out = nullptr;
     if (!hf::supported_n(n)) return fail(HF_EUNSUPPORTED, "hf_part_create: N=%d not supported", n);
     if (role != HF_STATIONARY && role != HF_MOVING) return fail(HF_EINVAL, "hf_part_create: role %d", role);
+    if ((uintptr_t)d_grid % 8) return fail(HF_EINVAL, "hf_part_create: d_grid must be 8-byte aligned");
     CU(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n3 = (size_t)n * n * n;
-    const size_t bytes = role == HF_MOVING ? n3 * sizeof(float) : hf::half_spec_elems(n) * sizeof(float2);
+    // moving: the grid plus the padded slices (pitched buffer and array)
+    const size_t bytes = role == HF_MOVING ? n3 * sizeof(float) + 2 * (size_t)(n + 2) * n * (n + 1) * sizeof(float)
+                                           : hf::half_spec_elems(n) * sizeof(float2);
     if (!charge(ctx, bytes)) return fail(HF_EBUDGET, "hf_part_create: %zu bytes exceed the budget", bytes);
     hf_part *p = new (std::nothrow) hf_part{ctx, n, role, nullptr, nullptr, bytes};
     if (!p) {
@@ -287,7 +341,7 @@ extern "C" hf_status hf_part_create(hf_ctx *ctx, int n, const float *d_grid, int
         return fail(HF_ENOMEM, "hf_part_create: host allocation");
     }
     void *mem = nullptr;
-    cudaError_t e = cudaMalloc(&mem, bytes);
+    cudaError_t e = cudaMalloc(&mem, role == HF_MOVING ? n3 * sizeof(float) : bytes);
     if (e != cudaSuccess) {
         delete p;
         uncharge(ctx, bytes);
@@ -295,8 +349,11 @@ extern "C" hf_status hf_part_create(hf_ctx *ctx, int n, const float *d_grid, int
     }
     if (role == HF_MOVING) p->grid = (float *)mem;
     else p->spec = (float2 *)mem;
-    hf_status s = part_fill(p, d_grid, st);
+    hf_status s = HF_OK;
+    if (role == HF_MOVING) s = moving_texture_alloc(p);
+    if (s == HF_OK) s = part_fill(p, d_grid, st);
     if (s != HF_OK) {
+        moving_texture_free(p);
         cudaFree(mem);
         delete p;
         uncharge(ctx, bytes);
@@ -308,6 +365,7 @@ extern "C" hf_status hf_part_create(hf_ctx *ctx, int n, const float *d_grid, int
 
 extern "C" hf_status hf_part_update(hf_part *p, const float *d_grid, hf_stream stream) {
     if (!p || !d_grid) return fail(HF_EINVAL, "hf_part_update: NULL argument");
+    if ((uintptr_t)d_grid % 8) return fail(HF_EINVAL, "hf_part_update: d_grid must be 8-byte aligned");
     CU(cudaSetDevice(p->ctx->device));
     return part_fill(p, d_grid, (cudaStream_t)stream);
 }
@@ -315,6 +373,7 @@ extern "C" hf_status hf_part_update(hf_part *p, const float *d_grid, hf_stream s
 extern "C" void hf_part_release(hf_part *p) {
     if (!p) return;
     cudaSetDevice(p->ctx->device);
+    moving_texture_free(p);
     cudaFree(p->grid ? (void *)p->grid : (void *)p->spec);
     uncharge(p->ctx, p->bytes);
     delete p;
@@ -442,11 +501,11 @@ int torque_setup(const std::vector<Quat> &Q, std::vector<int> &nbr, std::vector<
 int default_chunk(int n) {
     const char *env = getenv("HF_ROT_CHUNK");
     if (env && atoi(env) > 0) return atoi(env);
-    switch (n) {
-        case 32: return 64;
-        case 64: return 32;
-        case 96: return 12;
-        default: return 8;
+    switch (n) {  // rotations per launch: enough CTAs for several waves on 148 SMs
+        case 32: return 256;
+        case 64: return 128;
+        case 96: return 48;
+        default: return 32;
     }
 }
 
@@ -479,9 +538,10 @@ extern "C" hf_status hf_fieldset_create(hf_ctx *ctx, int n, int R, unsigned flag
     const size_t n3 = (size_t)n * n * n;
     const size_t data_b = (size_t)R * nf * n3 * sizeof(float);
     const size_t scr_b = 3 * (size_t)fs->chunk * hf::half_spec_elems(n) * sizeof(float2);
+    const size_t planes_b = (size_t)fs->chunk * n3 * sizeof(float);
     fs->stage_bytes = (size_t)R * (9 * sizeof(float) + 4 * sizeof(double) + 6 * sizeof(int) + 18 * sizeof(float) +
                                    18 * sizeof(double));
-    fs->bytes = data_b + scr_b + fs->stage_bytes;
+    fs->bytes = data_b + scr_b + planes_b + fs->stage_bytes;
     if (!charge(ctx, fs->bytes)) {
         const size_t b = fs->bytes;
         delete fs;
@@ -489,6 +549,7 @@ extern "C" hf_status hf_fieldset_create(hf_ctx *ctx, int n, int R, unsigned flag
     }
     cudaError_t e = cudaMalloc(&fs->data, data_b);
     if (e == cudaSuccess) e = cudaMalloc(&fs->scratch, scr_b);
+    if (e == cudaSuccess) e = cudaMalloc(&fs->planes, planes_b);
     if (e == cudaSuccess) e = cudaMalloc(&fs->d_rot9, (size_t)R * 9 * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&fs->d_quat, (size_t)R * 4 * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&fs->d_nbr, (size_t)R * 6 * sizeof(int));
@@ -510,6 +571,7 @@ extern "C" void hf_fieldset_release(hf_fieldset *fs) {
     cudaSetDevice(fs->ctx->device);
     cudaFree(fs->data);
     cudaFree(fs->scratch);
+    cudaFree(fs->planes);
     cudaFree(fs->d_rot9);
     cudaFree(fs->d_quat);
     cudaFree(fs->d_nbr);
@@ -528,9 +590,13 @@ extern "C" unsigned hf_fieldset_flags(const hf_fieldset *fs) { return fs ? fs->f
 // the energy/force passes for `cnt` rotations whose float matrices are at
 // rot9 (cnt x 9, device); outputs through `out` (first rotation at out.E)
 static hf_status run_fields(hf_ctx *c, int n, const hf_part *s1, const hf_part *s2, const float *rot9, int cnt,
-                            float2 *scratch, size_t scratch_rot, FieldPtrs out, cudaStream_t st) {
+                            float2 *scratch, size_t scratch_rot, float *planes, FieldPtrs out, cudaStream_t st) {
     float2 *X1 = scratch, *Y1 = scratch + scratch_rot, *Y2 = scratch + 2 * scratch_rot;
-    CU(timed(c, kPassA, st, [&] { return hf::run_passA(n, s2->grid, rot9, X1, cnt, st); }));
+    if (s2->tex)
+        CU(timed(c, kResample, st, [&] { return hf::run_resample_tex(n, s2->tex, rot9, planes, cnt, st); }));
+    else
+        CU(timed(c, kResample, st, [&] { return hf::run_resample_chunk(n, s2->grid, rot9, planes, cnt, st); }));
+    CU(timed(c, kPassA, st, [&] { return hf::run_passA_planes(n, planes, X1, cnt, st); }));
     CU(timed(c, kPassB, st, [&] { return hf::run_passB(n, X1, s1->spec, Y1, Y2, cnt, st); }));
     CU(timed(c, kPassC, st, [&] { return hf::run_passC(n, Y1, Y2, out, cnt, st); }));
     return HF_OK;
@@ -603,7 +669,7 @@ extern "C" hf_status hf_fieldset_compute(hf_ctx *ctx, const hf_part *s1, const h
         out.Fx = base + n3;
         out.Fy = base + 2 * n3;
         out.Fz = base + 3 * n3;
-        s = run_fields(ctx, n, s1, s2, fs->d_rot9 + (size_t)9 * r0, cnt, fs->scratch, scr_rot, out, st);
+        s = run_fields(ctx, n, s1, s2, fs->d_rot9 + (size_t)9 * r0, cnt, fs->scratch, scr_rot, fs->planes, out, st);
         if (s != HF_OK) return s;
     }
     if (fs->flags & HF_T) {
@@ -726,12 +792,11 @@ extern "C" hf_status hf_rfft3d(int n, const float *d_in, float *d_out, void *d_s
     if (!hf::supported_n(n)) return fail(HF_EUNSUPPORTED, "hf_rfft3d: N=%d not supported", n);
     if (!d_in || !d_out || !d_scratch) return fail(HF_EINVAL, "hf_rfft3d: NULL argument");
     if ((uintptr_t)d_scratch % 16) return fail(HF_EINVAL, "hf_rfft3d: scratch must be 16-byte aligned");
+    if ((uintptr_t)d_in % 8) return fail(HF_EINVAL, "hf_rfft3d: d_in must be 8-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t he = hf::half_spec_elems(n);
     float2 *X1 = (float2 *)d_scratch, *spec = X1 + he;
-    float *rot = (float *)(spec + he);
-    CU(cudaMemcpyAsync(rot, kIdentity9, sizeof kIdentity9, cudaMemcpyHostToDevice, st));
-    CU(hf::run_passA(n, d_in, rot, X1, 1, st));
+    CU(hf::run_passA_planes(n, d_in, X1, 1, st));
     CU(hf::run_passB_forward(n, X1, spec, 1.0f, st));
     CU(hf::run_unpermute(n, spec, (float2 *)d_out, st));
     return HF_OK;
@@ -740,7 +805,7 @@ extern "C" hf_status hf_rfft3d(int n, const float *d_in, float *d_out, void *d_s
 extern "C" size_t hf_fields_scratch_bytes(int n) {
     if (!hf::supported_n(n)) return 0;
     const size_t n3 = (size_t)n * n * n;
-    return 3 * hf::half_spec_elems(n) * sizeof(float2) + 3 * n3 * sizeof(float) + 256;
+    return 3 * hf::half_spec_elems(n) * sizeof(float2) + 4 * n3 * sizeof(float) + 256;
 }
 
 extern "C" hf_status hf_fields(hf_ctx *ctx, const hf_part *s1, const hf_part *s2, const float h_quat[4], float *d_E,
@@ -755,7 +820,8 @@ extern "C" hf_status hf_fields(hf_ctx *ctx, const hf_part *s1, const hf_part *s2
     const size_t he = hf::half_spec_elems(n), n3 = (size_t)n * n * n;
     float2 *scr = (float2 *)d_scratch;
     float *dummy = (float *)(scr + 3 * he);
-    float *rot = dummy + 3 * n3;
+    float *planes = dummy + 3 * n3;
+    float *rot = planes + n3;
     const Quat q = qnorm(h_quat);
     if (!qfinite(q)) return fail(HF_EINVAL, "hf_fields: quaternion is zero or not finite");
     double M[9];
@@ -764,7 +830,7 @@ extern "C" hf_status hf_fields(hf_ctx *ctx, const hf_part *s1, const hf_part *s2
     for (int k = 0; k < 9; ++k) m9[k] = (float)M[k];
     CU(cudaMemcpyAsync(rot, m9, sizeof m9, cudaMemcpyHostToDevice, st));
     FieldPtrs out{d_E, d_Fx ? d_Fx : dummy, d_Fy ? d_Fy : dummy + n3, d_Fz ? d_Fz : dummy + 2 * n3, 0};
-    s = run_fields(ctx, n, s1, s2, rot, 1, scr, he, out, st);
+    s = run_fields(ctx, n, s1, s2, rot, 1, scr, he, planes, out, st);
     if (s != HF_OK) return s;
     CU(cudaStreamSynchronize(st));  // m9 lives on this stack frame
     return HF_OK;

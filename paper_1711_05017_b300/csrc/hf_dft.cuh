@@ -211,64 +211,68 @@ __device__ __forceinline__ int slot_freq(int s) {
 
 // ------------------------------------------------ two-stage batched FFT
 // tw[j] = exp(-2 pi i j / L), j < L (forward sign), in shared memory.
-// Lines f in [0, M); element j of line f at base[f * ls + j * es].
-// All threads of the block must call; ends with __syncthreads.
-template <int L, int DIR>
-__device__ __forceinline__ void fft_lines(float2 *base, int M, int es, int ls, const float2 *tw) {
+// M lines; element j of line f at base[f * LS + j * ES]; NT threads.  All
+// sizes are compile-time so every index is a multiply-shift.  All threads of
+// the block must call; ends with __syncthreads.
+template <int L, int DIR, int M, int ES, int LS, int NT>
+__device__ __forceinline__ void fft_lines(float2 *base, const float2 *tw) {
     constexpr int R1 = Fact<L>::R1, R2 = Fact<L>::R2;
-    const int nthr = blockDim.x;
     if constexpr (DIR < 0) {
         // stage 1: items (f, n2)
-        for (int w = threadIdx.x; w < M * R2; w += nthr) {
+#pragma unroll 1
+        for (int w = threadIdx.x; w < M * R2; w += NT) {
             const int f = w % M, n2 = w / M;
-            float2 *p = base + f * ls + n2 * es;
+            float2 *p = base + f * LS + n2 * ES;
             float2 v[R1];
 #pragma unroll
-            for (int n1 = 0; n1 < R1; ++n1) v[n1] = p[n1 * R2 * es];
+            for (int n1 = 0; n1 < R1; ++n1) v[n1] = p[n1 * R2 * ES];
             RegDFT<R1, -1>::run(v);
 #pragma unroll
             for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmul(v[k1], tw[n2 * k1]);
 #pragma unroll
-            for (int k1 = 0; k1 < R1; ++k1) p[k1 * R2 * es] = v[k1];
+            for (int k1 = 0; k1 < R1; ++k1) p[k1 * R2 * ES] = v[k1];
         }
         __syncthreads();
         // stage 2: items (f, k1)
-        for (int w = threadIdx.x; w < M * R1; w += nthr) {
+#pragma unroll 1
+        for (int w = threadIdx.x; w < M * R1; w += NT) {
             const int f = w % M, k1 = w / M;
-            float2 *p = base + f * ls + (R2 * k1) * es;
+            float2 *p = base + f * LS + (R2 * k1) * ES;
             float2 v[R2];
 #pragma unroll
-            for (int n2 = 0; n2 < R2; ++n2) v[n2] = p[n2 * es];
+            for (int n2 = 0; n2 < R2; ++n2) v[n2] = p[n2 * ES];
             RegDFT<R2, -1>::run(v);
 #pragma unroll
-            for (int k2 = 0; k2 < R2; ++k2) p[k2 * es] = v[k2];
+            for (int k2 = 0; k2 < R2; ++k2) p[k2 * ES] = v[k2];
         }
         __syncthreads();
     } else {
         // stage 1: items (f, k1): slots R2*k1 + k2 hold X[k1 + R1*k2]
-        for (int w = threadIdx.x; w < M * R1; w += nthr) {
+#pragma unroll 1
+        for (int w = threadIdx.x; w < M * R1; w += NT) {
             const int f = w % M, k1 = w / M;
-            float2 *p = base + f * ls + (R2 * k1) * es;
+            float2 *p = base + f * LS + (R2 * k1) * ES;
             float2 v[R2];
 #pragma unroll
-            for (int k2 = 0; k2 < R2; ++k2) v[k2] = p[k2 * es];
+            for (int k2 = 0; k2 < R2; ++k2) v[k2] = p[k2 * ES];
             RegDFT<R2, +1>::run(v);
 #pragma unroll
             for (int n2 = 1; n2 < R2; ++n2) v[n2] = cmulc(v[n2], tw[n2 * k1]);
 #pragma unroll
-            for (int n2 = 0; n2 < R2; ++n2) p[n2 * es] = v[n2];
+            for (int n2 = 0; n2 < R2; ++n2) p[n2 * ES] = v[n2];
         }
         __syncthreads();
         // stage 2: items (f, n2)
-        for (int w = threadIdx.x; w < M * R2; w += nthr) {
+#pragma unroll 1
+        for (int w = threadIdx.x; w < M * R2; w += NT) {
             const int f = w % M, n2 = w / M;
-            float2 *p = base + f * ls + n2 * es;
+            float2 *p = base + f * LS + n2 * ES;
             float2 v[R1];
 #pragma unroll
-            for (int k1 = 0; k1 < R1; ++k1) v[k1] = p[k1 * R2 * es];
+            for (int k1 = 0; k1 < R1; ++k1) v[k1] = p[k1 * R2 * ES];
             RegDFT<R1, +1>::run(v);
 #pragma unroll
-            for (int n1 = 0; n1 < R1; ++n1) p[n1 * R2 * es] = v[n1];
+            for (int n1 = 0; n1 < R1; ++n1) p[n1 * R2 * ES] = v[n1];
         }
         __syncthreads();
     }

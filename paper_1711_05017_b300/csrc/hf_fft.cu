@@ -70,50 +70,76 @@ __device__ __forceinline__ float signed_k_mult(int k) {
 }
 
 // ------------------------------------------------------------------ pass A
+// Source of the plane: SRC_RAW samples a plain [z][y][x] grid at the rotated
+// node positions (8 loads per trilinear sample); SRC_PLANES reads plane z of
+// rotation r of an already resampled chunk rho2^R[r][z][y][x] (the identity
+// rotation is this mode with r = 0) by asynchronous 8-byte copies.
+enum { SRC_RAW = 0, SRC_PLANES = 1 };
+
 template <int N>
 struct PassA {
     static constexpr int H = N / 2 + 1, HALF = N / 2;
-    static constexpr int NT = (N >= 128) ? 544 : (N >= 64 ? 288 : 160);
+    static constexpr int NT = (N >= 64) ? 256 : 128;
+    static constexpr int MINB = (N >= 128) ? 3 : 4;
     static constexpr size_t smem = sizeof(float2) * ((size_t)N * H + N + HALF);
 };
 
-template <int N>
-__global__ void __launch_bounds__(PassA<N>::NT) passA_kernel(const float *__restrict__ rho,
-                                                              const float *__restrict__ rot9,
-                                                              float2 *__restrict__ X1) {
-    constexpr int H = PassA<N>::H, HALF = PassA<N>::HALF;
+__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+template <int N, int SRC>
+__global__ void __launch_bounds__(PassA<N>::NT, PassA<N>::MINB) passA_kernel(const float *__restrict__ rho,
+                                                                              const float *__restrict__ rot9,
+                                                                              float2 *__restrict__ X1) {
+    constexpr int H = PassA<N>::H, HALF = PassA<N>::HALF, NT = PassA<N>::NT;
     extern __shared__ float2 sm[];
     float2 *P = sm;            // [N rows y][H]  (row = N reals = N/2 complex + Nyquist slot)
     float2 *twN = P + N * H;   // exp(-2 pi i j / N)
     float2 *twH = twN + N;     // exp(-2 pi i j / (N/2))
     const int z = blockIdx.x, r = blockIdx.y;
-    load_tw<N>(twN);
-    load_tw<HALF>(twH);
-
-    // rotated resample of the moving density into the plane, as reals
-    float R[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) R[k] = __ldg(rot9 + 9 * r + k);
-    const float cz = (float)(z - N / 2);
-    const float bx = R[6] * cz, by = R[7] * cz, bz = R[8] * cz;
     float *Pf = reinterpret_cast<float *>(P);
-    for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
-        const int x = i % N, y = i / N;
-        const float cx = (float)(x - N / 2), cy = (float)(y - N / 2);
-        // (R^T c)_a = R[0][a] cx + R[1][a] cy + R[2][a] cz
-        const float vx = fmaf(R[0], cx, fmaf(R[3], cy, bx));
-        const float vy = fmaf(R[1], cx, fmaf(R[4], cy, by));
-        const float vz = fmaf(R[2], cx, fmaf(R[5], cy, bz));
-        Pf[(size_t)y * 2 * H + x] = trilinear_c<N>(rho, vx, vy, vz);
+
+    if constexpr (SRC == SRC_PLANES) {
+        const float2 *src = reinterpret_cast<const float2 *>(rho + ((size_t)r * N + z) * N * N);
+        for (int i = threadIdx.x; i < N * N / 2; i += NT) {
+            const int y = i / (N / 2), x2 = i % (N / 2);
+            cp_async8(P + (size_t)y * H + x2, src + i);
+        }
+        load_tw<N>(twN);
+        load_tw<HALF>(twH);
+        cp_async_wait_all();
+    } else {
+        load_tw<N>(twN);
+        load_tw<HALF>(twH);
+        // rotated resample of the moving density into the plane, as reals
+        float R[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) R[k] = __ldg(rot9 + 9 * r + k);
+        const float cz = (float)(z - N / 2);
+        const float bx = R[6] * cz, by = R[7] * cz, bz = R[8] * cz;
+        for (int i = threadIdx.x; i < N * N; i += NT) {
+            const int x = i % N, y = i / N;
+            const float cx = (float)(x - N / 2), cy = (float)(y - N / 2);
+            // (R^T c)_a = R[0][a] cx + R[1][a] cy + R[2][a] cz
+            const float vx = fmaf(R[0], cx, fmaf(R[3], cy, bx));
+            const float vy = fmaf(R[1], cx, fmaf(R[4], cy, by));
+            const float vz = fmaf(R[2], cx, fmaf(R[5], cy, bz));
+            Pf[(size_t)y * 2 * H + x] = trilinear_c<N>(rho, vx, vy, vz);
+        }
     }
     __syncthreads();
 
     // x: rows as N/2-point complex sequences z[m] = x[2m] + i x[2m+1]
-    fft_lines<HALF, -1>(P, N, 1, H, twH);
+    fft_lines<HALF, -1, N, 1, H, NT>(P, twH);
     // split into the half spectrum X[k], k = 0..N/2:
     //   E_k = (Z[k] + conj Z[N/2-k]) / 2,  O_k = (Z[k] - conj Z[N/2-k]) / 2i
     //   X[k] = E_k + W^k O_k,  X[N/2-k] = conj(E_k - W^k O_k),  W = exp(-2 pi i / N)
-    for (int i = threadIdx.x; i < N * (N / 4 + 1); i += blockDim.x) {
+    for (int i = threadIdx.x; i < N * (N / 4 + 1); i += NT) {
         const int y = i % N, k = i / N;
         float2 *row = P + y * H;
         if (k == 0) {
@@ -135,9 +161,104 @@ __global__ void __launch_bounds__(PassA<N>::NT) passA_kernel(const float *__rest
     }
     __syncthreads();
     // y: H columns of length N
-    fft_lines<N, -1>(P, H, H, 1, twN);
+    fft_lines<N, -1, H, H, 1, NT>(P, twN);
     float2 *dst = X1 + ((size_t)r * N + z) * N * H;
-    for (int i = threadIdx.x; i < N * H; i += blockDim.x) dst[i] = P[i];
+    for (int i = threadIdx.x; i < N * H; i += NT) dst[i] = P[i];
+}
+
+// ------------------------------------------------------- rotated resample
+// rho2^R[r][z][y][x] = trilinear_periodic(rho2, R_r^T x_n) for a chunk of
+// rotations.  No shared memory, so the whole L1 serves the gathers; each
+// thread samples kZ nodes along z so that their loads are in flight together.
+constexpr int kRsX = 32, kRsY = 8, kRsZ = 4;
+
+// The same resample through the texture units.  The moving grid is held as a
+// 2D float array of stacked z-slices, each (N+1) x (N+1) with the wrapped
+// row y = N and column x = N appended, so slice z spans rows
+// [z(N+1), z(N+1)+N].  One 2x2 gather at the corner (x0 + 1, row0 + 1)
+// returns texels (x0, x0+1) x (row0, row0+1) exactly (the footprint of an
+// integer corner does not depend on the unit's coordinate rounding), so a
+// trilinear sample is two gathers; the weights stay in float32 software.
+template <int N>
+__device__ __forceinline__ float trilinear_tex(cudaTextureObject_t t, float vx, float vy, float vz) {
+    const float fx = floorf(vx), fy = floorf(vy), fz = floorf(vz);
+    const float ax = vx - fx, ay = vy - fy, az = vz - fz;
+    const int x0 = wrapN<N>((int)fx + N / 2), y0 = wrapN<N>((int)fy + N / 2), z0 = wrapN<N>((int)fz + N / 2);
+    const int z1 = wrapN<N>(z0 + 1);
+    const float u = (float)x0 + 1.0f;
+    // gather components: w = (x0, y0), z = (x0+1, y0), x = (x0, y0+1), y = (x0+1, y0+1)
+    const float4 a = tex2Dgather<float4>(t, u, (float)(z0 * (N + 1) + y0) + 1.0f, 0);
+    const float4 b = tex2Dgather<float4>(t, u, (float)(z1 * (N + 1) + y0) + 1.0f, 0);
+    const float a0 = fmaf(ax, a.z - a.w, a.w), a1 = fmaf(ax, a.y - a.x, a.x);
+    const float b0 = fmaf(ax, b.z - b.w, b.w), b1 = fmaf(ax, b.y - b.x, b.x);
+    const float c0 = fmaf(ay, a1 - a0, a0), c1 = fmaf(ay, b1 - b0, b0);
+    return fmaf(az, c1 - c0, c0);
+}
+
+template <int N>
+__global__ void __launch_bounds__(kRsX * kRsY) resample_tex_kernel(cudaTextureObject_t tex,
+                                                                 const float *__restrict__ rot9,
+                                                                 float *__restrict__ out) {
+    const int tiles_x = N / kRsX, tiles_y = N / kRsY;
+    int t = blockIdx.x;
+    const int tx = t % tiles_x; t /= tiles_x;
+    const int ty = t % tiles_y; t /= tiles_y;
+    const int tz = t;
+    const int r = blockIdx.y;
+    float R[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) R[k] = __ldg(rot9 + 9 * r + k);
+    const int x = tx * kRsX + (threadIdx.x % kRsX), y = ty * kRsY + (threadIdx.x / kRsX);
+    const float cx = (float)(x - N / 2), cy = (float)(y - N / 2);
+    const float ax = fmaf(R[0], cx, R[3] * cy), ay = fmaf(R[1], cx, R[4] * cy), az = fmaf(R[2], cx, R[5] * cy);
+    float v[kRsZ];
+#pragma unroll
+    for (int j = 0; j < kRsZ; ++j) {
+        const float cz = (float)(tz * kRsZ + j - N / 2);
+        v[j] = trilinear_tex<N>(tex, fmaf(R[6], cz, ax), fmaf(R[7], cz, ay), fmaf(R[8], cz, az));
+    }
+    float *o = out + (size_t)r * N * N * N + (size_t)y * N + x;
+#pragma unroll
+    for (int j = 0; j < kRsZ; ++j) o[(size_t)(tz * kRsZ + j) * N * N] = v[j];
+}
+
+// stacked padded slices for the texture: slab[row][x], row = z(N+1) + y, x, y in [0, N]
+template <int N>
+__global__ void pad_slices_kernel(const float *__restrict__ g, float *__restrict__ slab, size_t pitch_floats) {
+    const size_t total = (size_t)N * (N + 1) * (N + 1);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % (N + 1));
+        const size_t row = i / (N + 1);
+        const int y = (int)(row % (N + 1)), z = (int)(row / (N + 1));
+        slab[row * pitch_floats + x] = __ldg(g + ((size_t)z * N + wrapN<N>(y)) * N + wrapN<N>(x));
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kRsX * kRsY) resample_chunk_kernel(const float *__restrict__ rho,
+                                                                   const float *__restrict__ rot9,
+                                                                   float *__restrict__ out) {
+    const int tiles_x = N / kRsX, tiles_y = N / kRsY;
+    int t = blockIdx.x;
+    const int tx = t % tiles_x; t /= tiles_x;
+    const int ty = t % tiles_y; t /= tiles_y;
+    const int tz = t;
+    const int r = blockIdx.y;
+    float R[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) R[k] = __ldg(rot9 + 9 * r + k);
+    const int x = tx * kRsX + (threadIdx.x % kRsX), y = ty * kRsY + (threadIdx.x / kRsX);
+    const float cx = (float)(x - N / 2), cy = (float)(y - N / 2);
+    const float ax = fmaf(R[0], cx, R[3] * cy), ay = fmaf(R[1], cx, R[4] * cy), az = fmaf(R[2], cx, R[5] * cy);
+    float v[kRsZ];
+#pragma unroll
+    for (int j = 0; j < kRsZ; ++j) {
+        const float cz = (float)(tz * kRsZ + j - N / 2);
+        v[j] = trilinear_c<N>(rho, fmaf(R[6], cz, ax), fmaf(R[7], cz, ay), fmaf(R[8], cz, az));
+    }
+    float *o = out + (size_t)r * N * N * N + (size_t)y * N + x;
+#pragma unroll
+    for (int j = 0; j < kRsZ; ++j) o[(size_t)(tz * kRsZ + j) * N * N] = v[j];
 }
 
 // ------------------------------------------------------------------ pass B
@@ -146,51 +267,63 @@ struct PassB {
     static constexpr int H = N / 2 + 1;
     static constexpr int C = (H + 1) / 2;  // kx chunk width (2 chunks)
     static constexpr int NCH = 2;
-    static constexpr int NT = (N >= 128) ? 544 : (N >= 64 ? 288 : 160);
+    static constexpr int NT = (N >= 64) ? 256 : 128;
+    static constexpr int MINB = (N >= 128) ? 3 : 4;
     static constexpr size_t smem = sizeof(float2) * ((size_t)N * 2 * C + N);
 };
 
 // MODE 0: full middle pass (product, gradient, inverse z) -> Y1, Y2
 // MODE 1: forward only, spectrum * scale -> spec[ky*][kz*][kx*]  (stationary part)
 template <int N, int MODE>
-__global__ void __launch_bounds__(PassB<N>::NT) passB_kernel(const float2 *__restrict__ X1,
+__global__ void __launch_bounds__(PassB<N>::NT, PassB<N>::MINB) passB_kernel(const float2 *__restrict__ X1,
                                                               const float2 *__restrict__ R1hat,
                                                               float2 *__restrict__ Y1,
                                                               float2 *__restrict__ Y2, float scale) {
-    constexpr int H = PassB<N>::H, C = PassB<N>::C, W2 = 2 * C;
+    constexpr int H = PassB<N>::H, C = PassB<N>::C, W2 = 2 * C, NT = PassB<N>::NT;
     extern __shared__ float2 sm[];
     float2 *T = sm;            // [N][2C]: columns [0,C) = S, [C,2C) = Gz
     float2 *twN = T + N * W2;
     const int ky = blockIdx.x, c0 = blockIdx.y * C, r = blockIdx.z;
     const int cw = min(C, H - c0);
-    load_tw<N>(twN);
+    // asynchronous loads: the X1 tile into columns [0, C); for the full pass
+    // the matching tile of the stationary spectrum into columns [C, 2C),
+    // which hold Gz only after the product has consumed it
     const float2 *src = X1 + (size_t)r * N * N * H + (size_t)ky * H + c0;
-    for (int i = threadIdx.x; i < N * C; i += blockDim.x) {
+    for (int i = threadIdx.x; i < N * C; i += NT) {
         const int z = i / C, c = i % C;
-        T[z * W2 + c] = c < cw ? src[(size_t)z * N * H + c] : make_float2(0.f, 0.f);
+        if (c < cw) cp_async8(T + z * W2 + c, src + (size_t)z * N * H + c);
+        else T[z * W2 + c] = make_float2(0.f, 0.f);
     }
+    if constexpr (MODE == 0) {
+        const float2 *rh = R1hat + (size_t)ky * N * H + c0;
+        for (int i = threadIdx.x; i < N * C; i += NT) {
+            const int s = i / C, c = i % C;
+            if (c < cw) cp_async8(T + s * W2 + C + c, rh + (size_t)s * H + c);
+            else T[s * W2 + C + c] = make_float2(0.f, 0.f);
+        }
+    }
+    load_tw<N>(twN);
+    cp_async_wait_all();
     __syncthreads();
-    fft_lines<N, -1>(T, C, W2, 1, twN);
+    fft_lines<N, -1, C, W2, 1, NT>(T, twN);
     if constexpr (MODE == 1) {
         float2 *dst = Y1 + (size_t)ky * N * H + c0;
-        for (int i = threadIdx.x; i < N * cw; i += blockDim.x) {
+        for (int i = threadIdx.x; i < N * cw; i += NT) {
             const int s = i / cw, c = i % cw;
             dst[(size_t)s * H + c] = cscale(T[s * W2 + c], scale);
         }
     } else {
-        const float2 *rh = R1hat + (size_t)ky * N * H + c0;
-        for (int i = threadIdx.x; i < N * C; i += blockDim.x) {
+        for (int i = threadIdx.x; i < N * C; i += NT) {
             const int s = i / C, c = i % C;
-            float2 S = make_float2(0.f, 0.f);
-            if (c < cw) S = cmulc(__ldg(rh + (size_t)s * H + c), T[s * W2 + c]);
+            const float2 S = cmulc(T[s * W2 + C + c], T[s * W2 + c]);  // (h^3/N^3) rho1^ conj(rho2^R^)
             T[s * W2 + c] = S;
             T[s * W2 + C + c] = cmul_is(S, signed_k_mult<N>(slot_freq<N>(s)));
         }
         __syncthreads();
-        fft_lines<N, +1>(T, W2, W2, 1, twN);
+        fft_lines<N, +1, W2, W2, 1, NT>(T, twN);
         float2 *d1 = Y1 + (size_t)r * N * N * H + (size_t)ky * H + c0;
         float2 *d2 = Y2 + (size_t)r * N * N * H + (size_t)ky * H + c0;
-        for (int i = threadIdx.x; i < N * cw; i += blockDim.x) {
+        for (int i = threadIdx.x; i < N * cw; i += NT) {
             const int z = i / cw, c = i % cw;
             d1[(size_t)z * N * H + c] = T[z * W2 + c];
             d2[(size_t)z * N * H + c] = T[z * W2 + C + c];
@@ -227,7 +360,7 @@ __device__ __forceinline__ void x_pass(const float2 *plane, int colA, int colB, 
                   TP = PassC<N>::TP;
     for (int y0 = 0; y0 < N; y0 += RB) {
         // stage 1 (inverse), items (row, k1): slots R2*k1 + k2 <- Z[k1 + R1*k2]
-        for (int w = threadIdx.x; w < RB * R1; w += blockDim.x) {
+        for (int w = threadIdx.x; w < RB * R1; w += PassC<N>::NT) {
             const int row = w % RB, k1 = w / RB;
             const float2 *pr = plane + (size_t)(y0 + row) * PW;
             float2 v[R2];
@@ -257,7 +390,7 @@ __device__ __forceinline__ void x_pass(const float2 *plane, int colA, int colB, 
         }
         __syncthreads();
         // stage 2 (inverse), items (row, n2): natural order back into the row buffer
-        for (int w = threadIdx.x; w < RB * R2; w += blockDim.x) {
+        for (int w = threadIdx.x; w < RB * R2; w += PassC<N>::NT) {
             const int row = w % RB, n2 = w / RB;
             float2 *tr = Tb + row * TP + n2;
             float2 v[R1];
@@ -269,7 +402,7 @@ __device__ __forceinline__ void x_pass(const float2 *plane, int colA, int colB, 
         }
         __syncthreads();
         // coalesced store of the RB rows
-        for (int i = threadIdx.x; i < RB * N; i += blockDim.x) {
+        for (int i = threadIdx.x; i < RB * N; i += PassC<N>::NT) {
             const int row = i / N, x = i % N;
             const float2 v = Tb[row * TP + x];
             const size_t o = (size_t)(y0 + row) * N + x;
@@ -290,25 +423,31 @@ __global__ void __launch_bounds__(PassC<N>::NT) passC_kernel(const float2 *__res
     float2 *Tb = plane + (size_t)N * PW;      // [RB][TP]
     float2 *twN = Tb + (size_t)RB * TP;
     const int z = blockIdx.x, r = blockIdx.y;
-    load_tw<N>(twN);
+    constexpr int NT = PassC<N>::NT;
     const float2 *s1 = Y1 + ((size_t)r * N + z) * N * H;
-    for (int i = threadIdx.x; i < N * H; i += blockDim.x) {
+    for (int i = threadIdx.x; i < N * H; i += NT) {
         const int y = i / H, c = i % H;  // y is the ky slot
-        const float2 v = s1[i];
-        plane[y * PW + c] = v;
-        plane[y * PW + H + c] = cmul_is(v, signed_k_mult<N>(slot_freq<N>(y)));
+        cp_async8(plane + y * PW + c, s1 + i);
+    }
+    load_tw<N>(twN);
+    cp_async_wait_all();
+    __syncthreads();
+    for (int i = threadIdx.x; i < N * H; i += NT) {
+        const int y = i / H, c = i % H;
+        plane[y * PW + H + c] = cmul_is(plane[y * PW + c], signed_k_mult<N>(slot_freq<N>(y)));
     }
     __syncthreads();
-    fft_lines<N, +1>(plane, 2 * H, PW, 1, twN);
+    fft_lines<N, +1, 2 * H, PW, 1, PassC<N>::NT>(plane, twN);
     const size_t fo = (size_t)r * out.rot_stride + (size_t)z * N * N;
     x_pass<N, 0>(plane, 0, H, Tb, twN, out.E + fo, out.Fx + fo);
     const float2 *s2 = Y2 + ((size_t)r * N + z) * N * H;
-    for (int i = threadIdx.x; i < N * H; i += blockDim.x) {
+    for (int i = threadIdx.x; i < N * H; i += NT) {
         const int y = i / H, c = i % H;
-        plane[y * PW + c] = s2[i];
+        cp_async8(plane + y * PW + c, s2 + i);
     }
+    cp_async_wait_all();
     __syncthreads();
-    fft_lines<N, +1>(plane, H, PW, 1, twN);
+    fft_lines<N, +1, H, PW, 1, PassC<N>::NT>(plane, twN);
     x_pass<N, 1>(plane, 0, H, Tb, twN, out.Fy + fo, out.Fz + fo);
 }
 
@@ -328,16 +467,32 @@ __global__ void unpermute_spectrum_kernel(const float2 *__restrict__ spec, float
 template <int N>
 static cudaError_t set_smem_attrs() {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(passA_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassA<N>::smem))) return e;
+    if ((e = cudaFuncSetAttribute(passA_kernel<N, SRC_RAW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassA<N>::smem))) return e;
+    if ((e = cudaFuncSetAttribute(passA_kernel<N, SRC_PLANES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassA<N>::smem))) return e;
     if ((e = cudaFuncSetAttribute(passB_kernel<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N>::smem))) return e;
     if ((e = cudaFuncSetAttribute(passB_kernel<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N>::smem))) return e;
     if ((e = cudaFuncSetAttribute(passC_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassC<N>::smem))) return e;
     return cudaSuccess;
 }
 
-template <int N>
+template <int N, int SRC>
 static cudaError_t launch_passA(const float *rho, const float *rot9, float2 *X1, int nrot, cudaStream_t st) {
-    passA_kernel<N><<<dim3(N, nrot), PassA<N>::NT, PassA<N>::smem, st>>>(rho, rot9, X1);
+    passA_kernel<N, SRC><<<dim3(N, nrot), PassA<N>::NT, PassA<N>::smem, st>>>(rho, rot9, X1);
+    return cudaGetLastError();
+}
+template <int N>
+static cudaError_t launch_resample_tex(cudaTextureObject_t tex, const float *rot9, float *out, int nrot, cudaStream_t st) {
+    resample_tex_kernel<N><<<dim3((N / kRsX) * (N / kRsY) * (N / kRsZ), nrot), kRsX * kRsY, 0, st>>>(tex, rot9, out);
+    return cudaGetLastError();
+}
+template <int N>
+static cudaError_t launch_pad_slices(const float *g, float *slab, size_t pitch_floats, cudaStream_t st) {
+    pad_slices_kernel<N><<<4 * 148, 256, 0, st>>>(g, slab, pitch_floats);
+    return cudaGetLastError();
+}
+template <int N>
+static cudaError_t launch_resample_chunk(const float *rho, const float *rot9, float *out, int nrot, cudaStream_t st) {
+    resample_chunk_kernel<N><<<dim3((N / kRsX) * (N / kRsY) * (N / kRsZ), nrot), kRsX * kRsY, 0, st>>>(rho, rot9, out);
     return cudaGetLastError();
 }
 template <int N>
@@ -373,7 +528,19 @@ static cudaError_t launch_unpermute(const float2 *spec, float2 *out, cudaStream_
 
 cudaError_t fft_init_attrs(int n) { HF_DISPATCH(n, set_smem_attrs<NN>()); }
 cudaError_t run_passA(int n, const float *rho, const float *rot9, float2 *X1, int nrot, cudaStream_t st) {
-    HF_DISPATCH(n, launch_passA<NN>(rho, rot9, X1, nrot, st));
+    HF_DISPATCH(n, (launch_passA<NN, SRC_RAW>(rho, rot9, X1, nrot, st)));
+}
+cudaError_t run_passA_planes(int n, const float *planes, float2 *X1, int nrot, cudaStream_t st) {
+    HF_DISPATCH(n, (launch_passA<NN, SRC_PLANES>(planes, nullptr, X1, nrot, st)));
+}
+cudaError_t run_resample_chunk(int n, const float *rho, const float *rot9, float *out, int nrot, cudaStream_t st) {
+    HF_DISPATCH(n, launch_resample_chunk<NN>(rho, rot9, out, nrot, st));
+}
+cudaError_t run_resample_tex(int n, cudaTextureObject_t tex, const float *rot9, float *out, int nrot, cudaStream_t st) {
+    HF_DISPATCH(n, launch_resample_tex<NN>(tex, rot9, out, nrot, st));
+}
+cudaError_t run_pad_slices(int n, const float *g, float *slab, size_t pitch_floats, cudaStream_t st) {
+    HF_DISPATCH(n, launch_pad_slices<NN>(g, slab, pitch_floats, st));
 }
 cudaError_t run_passB(int n, const float2 *X1, const float2 *R1hat, float2 *Y1, float2 *Y2, int nrot, cudaStream_t st) {
     HF_DISPATCH(n, launch_passB<NN>(X1, R1hat, Y1, Y2, nrot, st));
