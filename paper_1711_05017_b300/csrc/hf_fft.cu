@@ -29,6 +29,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include "hf_dft.cuh"
 #include "hf_internal.h"
@@ -331,21 +332,40 @@ __global__ void __launch_bounds__(PassB<N>::NT, PassB<N>::MINB) passB_kernel(con
     }
 }
 
-// ------------------------------------------------------------------ pass C
-template <int N>
-struct PassC {
-    static constexpr int H = N / 2 + 1, HALF = N / 2;
-    static constexpr int PW = 2 * H + 1;  // plane pitch: S' at [0,H), Gy at [H,2H)
-    static constexpr int RB = (N >= 128) ? 32 : N / 2;  // rows per x batch
-    static constexpr int TP = N + 1;                    // row-buffer pitch
-    static constexpr int NT = (N >= 128) ? 512 : (N >= 64 ? 256 : 128);
-    static constexpr size_t smem = sizeof(float2) * ((size_t)N * PW + (size_t)RB * TP + N);
-};
-
 // x slot of half-spectrum index k in [0, N/2]
 template <int N>
 __device__ __forceinline__ int xslot(int k) {
     return k == N / 2 ? N / 2 : perm_slot<N / 2>(k);
+}
+
+// ------------------------------------------------------------------ pass C
+// One CTA per (z-plane, rotation) holding S'' and Gy'' side by side (pitch
+// 2H+1), then Gz'' in place of S''.
+template <int N>
+struct PassC {
+    static constexpr int H = N / 2 + 1, HALF = N / 2;
+    static constexpr int PW = 2 * H + 1;  // plane pitch: S' at [0,H), Gy at [H,2H)
+    static constexpr int RB = (N >= 128) ? 64 : N / 2;  // rows per x batch
+    static constexpr int TP = N + 1;                    // row-buffer pitch
+    static constexpr int NT = (N >= 128) ? 512 : (N >= 64 ? 256 : 128);
+    static constexpr size_t smem = sizeof(float2) * ((size_t)N * PW + (size_t)RB * TP + N) +
+                                   sizeof(float4) * (size_t)N;
+};
+
+// Per frequency k of the full x row: where its half-spectrum value sits and
+// how it enters the row:  k <= N/2 reads slot(k) as is, k > N/2 reads
+// slot(N-k) conjugated (Hermitian symmetry); for the (E, Fx) row the value is
+// also scaled by 1 + pi kx~ (kx~ signed, Nyquist 0).
+//   entry = (slot as float bits, conj sign, scale, scale * conj sign)
+template <int N>
+__device__ __forceinline__ void build_xtable(float4 *xt) {
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const bool neg = 2 * k > N;
+        const int m = neg ? N - k : k;
+        const float cs = neg ? -1.0f : 1.0f;
+        const float mult = (2 * k == N) ? 1.0f : 1.0f + (neg ? -kPi * (float)m : kPi * (float)m);
+        xt[k] = make_float4(__int_as_float(xslot<N>(m)), cs, mult, mult * cs);
+    }
 }
 
 // One complex inverse DFT of length N per row, input built from the
@@ -354,34 +374,29 @@ __device__ __forceinline__ int xslot(int k) {
 // PAIR 1: Z[k] = -(Gy(k) + i Gz(k))             -> (Fy, Fz)
 template <int N, int PAIR>
 __device__ __forceinline__ void x_pass(const float2 *plane, int colA, int colB, float2 *Tb,
-                                       const float2 *twN, float *__restrict__ out0,
+                                       const float2 *twN, const float4 *xt, float *__restrict__ out0,
                                        float *__restrict__ out1) {
     constexpr int R1 = Fact<N>::R1, R2 = Fact<N>::R2, PW = PassC<N>::PW, RB = PassC<N>::RB,
-                  TP = PassC<N>::TP;
+                  TP = PassC<N>::TP, NT = PassC<N>::NT;
+#pragma unroll 1
     for (int y0 = 0; y0 < N; y0 += RB) {
         // stage 1 (inverse), items (row, k1): slots R2*k1 + k2 <- Z[k1 + R1*k2]
-        for (int w = threadIdx.x; w < RB * R1; w += PassC<N>::NT) {
+#pragma unroll 1
+        for (int w = threadIdx.x; w < RB * R1; w += NT) {
             const int row = w % RB, k1 = w / RB;
             const float2 *pr = plane + (size_t)(y0 + row) * PW;
             float2 v[R2];
 #pragma unroll
             for (int k2 = 0; k2 < R2; ++k2) {
-                const int k = k1 + R1 * k2;
-                const bool neg = 2 * k > N;
-                const int m = neg ? N - k : k;
-                const int s = xslot<N>(m);
-                float2 z;
+                const float4 e = xt[k1 + R1 * k2];
+                const int sl = __float_as_int(e.x);
                 if constexpr (PAIR == 0) {
-                    float2 a = pr[colA + s];
-                    if (neg) a = cconj(a);
-                    const float mult = (2 * k == N) ? 1.0f : 1.0f + (neg ? -kPi * (float)m : kPi * (float)m);
-                    z = cscale(a, mult);
+                    const float2 a = pr[colA + sl];
+                    v[k2] = make_float2(e.z * a.x, e.w * a.y);
                 } else {
-                    float2 gy = pr[colB + s], gz = pr[colA + s];
-                    if (neg) { gy = cconj(gy); gz = cconj(gz); }
-                    z = make_float2(gz.y - gy.x, -gy.y - gz.x);  // -(gy + i gz)
+                    const float2 gy = pr[colB + sl], gz = pr[colA + sl];
+                    v[k2] = make_float2(fmaf(e.y, gz.y, -gy.x), fmaf(-e.y, gy.y, -gz.x));  // -(gy + i gz)
                 }
-                v[k2] = z;
             }
             RegDFT<R2, +1>::run(v);
             float2 *tr = Tb + row * TP + R2 * k1;
@@ -390,7 +405,8 @@ __device__ __forceinline__ void x_pass(const float2 *plane, int colA, int colB, 
         }
         __syncthreads();
         // stage 2 (inverse), items (row, n2): natural order back into the row buffer
-        for (int w = threadIdx.x; w < RB * R2; w += PassC<N>::NT) {
+#pragma unroll 1
+        for (int w = threadIdx.x; w < RB * R2; w += NT) {
             const int row = w % RB, n2 = w / RB;
             float2 *tr = Tb + row * TP + n2;
             float2 v[R1];
@@ -402,7 +418,7 @@ __device__ __forceinline__ void x_pass(const float2 *plane, int colA, int colB, 
         }
         __syncthreads();
         // coalesced store of the RB rows
-        for (int i = threadIdx.x; i < RB * N; i += PassC<N>::NT) {
+        for (int i = threadIdx.x; i < RB * N; i += NT) {
             const int row = i / N, x = i % N;
             const float2 v = Tb[row * TP + x];
             const size_t o = (size_t)(y0 + row) * N + x;
@@ -417,19 +433,21 @@ template <int N>
 __global__ void __launch_bounds__(PassC<N>::NT) passC_kernel(const float2 *__restrict__ Y1,
                                                               const float2 *__restrict__ Y2,
                                                               FieldPtrs out) {
-    constexpr int H = PassC<N>::H, PW = PassC<N>::PW, RB = PassC<N>::RB, TP = PassC<N>::TP;
+    constexpr int H = PassC<N>::H, PW = PassC<N>::PW, RB = PassC<N>::RB, TP = PassC<N>::TP,
+                  NT = PassC<N>::NT;
     extern __shared__ float2 sm[];
     float2 *plane = sm;                       // [N][PW]
     float2 *Tb = plane + (size_t)N * PW;      // [RB][TP]
     float2 *twN = Tb + (size_t)RB * TP;
+    float4 *xt = reinterpret_cast<float4 *>(twN + N);
     const int z = blockIdx.x, r = blockIdx.y;
-    constexpr int NT = PassC<N>::NT;
     const float2 *s1 = Y1 + ((size_t)r * N + z) * N * H;
     for (int i = threadIdx.x; i < N * H; i += NT) {
         const int y = i / H, c = i % H;  // y is the ky slot
         cp_async8(plane + y * PW + c, s1 + i);
     }
     load_tw<N>(twN);
+    build_xtable<N>(xt);
     cp_async_wait_all();
     __syncthreads();
     for (int i = threadIdx.x; i < N * H; i += NT) {
@@ -437,9 +455,9 @@ __global__ void __launch_bounds__(PassC<N>::NT) passC_kernel(const float2 *__res
         plane[y * PW + H + c] = cmul_is(plane[y * PW + c], signed_k_mult<N>(slot_freq<N>(y)));
     }
     __syncthreads();
-    fft_lines<N, +1, 2 * H, PW, 1, PassC<N>::NT>(plane, twN);
+    fft_lines<N, +1, 2 * H, PW, 1, NT>(plane, twN);
     const size_t fo = (size_t)r * out.rot_stride + (size_t)z * N * N;
-    x_pass<N, 0>(plane, 0, H, Tb, twN, out.E + fo, out.Fx + fo);
+    x_pass<N, 0>(plane, 0, H, Tb, twN, xt, out.E + fo, out.Fx + fo);
     const float2 *s2 = Y2 + ((size_t)r * N + z) * N * H;
     for (int i = threadIdx.x; i < N * H; i += NT) {
         const int y = i / H, c = i % H;
@@ -447,8 +465,10 @@ __global__ void __launch_bounds__(PassC<N>::NT) passC_kernel(const float2 *__res
     }
     cp_async_wait_all();
     __syncthreads();
-    fft_lines<N, +1, H, PW, 1, PassC<N>::NT>(plane, twN);
-    x_pass<N, 1>(plane, 0, H, Tb, twN, out.Fy + fo, out.Fz + fo);
+    fft_lines<N, +1, H, PW, 1, NT>(plane, twN);
+    x_pass<N, 1>(plane, 0, H, Tb, twN, xt, out.Fy + fo, out.Fz + fo);
+    (void)RB;
+    (void)TP;
 }
 
 // -------------------------------------------- natural-order spectrum copy
