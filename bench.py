@@ -200,7 +200,11 @@ def run_ours(args, rank, world, local_rank):
         "splat": n3b,
         "passB_fwd": 2 * he,
         "query": N_QUERY * 7 * 4 * 2,
+        "resample": n3b + chunk * n3b,
     }
+    # dram__bytes_read.sum + dram__bytes_write.sum per launch of the current
+    # kernels, 32 rotations per launch (profiles/passC_c2_128.md)
+    traffic = {"passC": 1.5625e9} if (n == 128 and chunk == 32) else {}
     hbm_peak, peak_kind = peaks()
     kernels = {}
     for k, (cnt, tot) in prof.items():
@@ -213,10 +217,10 @@ def run_ours(args, rank, world, local_rank):
     dom = max(prof, key=lambda k: prof[k][1]) if prof else None
     roof = None
     if dom:
-        achieved = alg[dom] / (prof[dom][1] / prof[dom][0] * 1e-3) / 1e9
+        achieved = alg.get(dom, 0) / (prof[dom][1] / prof[dom][0] * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
                 "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
-                "traffic": None, "alg_bytes_per_launch": alg[dom]}
+                "traffic": traffic.get(dom), "alg_bytes_per_launch": alg.get(dom, 0)}
     launches = sum(v[0] for v in prof.values())
 
     # ---- end to end through the public API from pinned host buffers
@@ -268,8 +272,10 @@ def run_ours(args, rank, world, local_rank):
     plain = None
     if not args.no_plain and rank == 0:
         os.environ["HF_ROT_CHUNK"] = "1"
+        os.environ["HF_LANES"] = "1"
         fs1 = ctx.fieldset(n, R, hf.HF_E | hf.HF_F | hf.HF_T)
         del os.environ["HF_ROT_CHUNK"]
+        del os.environ["HF_LANES"]
 
         def plain_step():
             ctx.density_build(n, pts1, sig1, out=g1)

@@ -88,14 +88,20 @@ struct hf_fieldset {
     int nf = 0;                  // fields held per rotation
     int slot[7];                 // field index -> slot within a rotation block, -1 if not held
     float *data = nullptr;       // R x nf x N^3
-    float2 *scratch = nullptr;   // 3 x chunk x N*N*(N/2+1): X1, Y1, Y2
-    float *planes = nullptr;     // chunk x N^3: the chunk's resampled moving densities
+    // two pipelines, each with its own intermediates, run alternate chunks on
+    // two internal streams so that one chunk's texture-bound resample can
+    // overlap the other's shared-memory-bound passes
+    float2 *scratch[2] = {};     // 3 x chunk x N*N*(N/2+1): X1, Y1, Y2
+    float *planes[2] = {};       // chunk x N^3: the chunk's resampled moving densities
+    cudaStream_t lane[2] = {};
+    cudaEvent_t fork = nullptr, join[2] = {};
     float *d_rot9 = nullptr;     // R x 9
     double *d_quat = nullptr;    // R x 4 (normalised)
     int *d_nbr = nullptr;        // R x 6
     float *d_P = nullptr;        // R x 18
     double *d_P64 = nullptr;     // R x 18
     int chunk = 1;
+    int lanes = 1;  // pipelines used by compute (HF_LANES=2 alternates chunks over two)
     bool ready = false;
     size_t bytes = 0;
     void *h_stage = nullptr;     // pinned staging for the per-call uploads
@@ -535,21 +541,30 @@ extern "C" hf_status hf_fieldset_create(hf_ctx *ctx, int n, int R, unsigned flag
         for (int f = 4; f <= 6; ++f) fs->slot[f] = nf++;
     fs->nf = nf;
     fs->chunk = std::min(default_chunk(n), R);
+    {
+        const char *ev = getenv("HF_LANES");
+        fs->lanes = (ev && atoi(ev) == 2) ? 2 : 1;
+    }
     const size_t n3 = (size_t)n * n * n;
     const size_t data_b = (size_t)R * nf * n3 * sizeof(float);
     const size_t scr_b = 3 * (size_t)fs->chunk * hf::half_spec_elems(n) * sizeof(float2);
     const size_t planes_b = (size_t)fs->chunk * n3 * sizeof(float);
     fs->stage_bytes = (size_t)R * (9 * sizeof(float) + 4 * sizeof(double) + 6 * sizeof(int) + 18 * sizeof(float) +
                                    18 * sizeof(double));
-    fs->bytes = data_b + scr_b + planes_b + fs->stage_bytes;
+    fs->bytes = data_b + fs->lanes * (scr_b + planes_b) + fs->stage_bytes;
     if (!charge(ctx, fs->bytes)) {
         const size_t b = fs->bytes;
         delete fs;
         return fail(HF_EBUDGET, "hf_fieldset_create: %zu bytes exceed the budget", b);
     }
     cudaError_t e = cudaMalloc(&fs->data, data_b);
-    if (e == cudaSuccess) e = cudaMalloc(&fs->scratch, scr_b);
-    if (e == cudaSuccess) e = cudaMalloc(&fs->planes, planes_b);
+    for (int l = 0; l < 2; ++l) {
+        if (e == cudaSuccess && l < fs->lanes) e = cudaMalloc(&fs->scratch[l], scr_b);
+        if (e == cudaSuccess && l < fs->lanes) e = cudaMalloc(&fs->planes[l], planes_b);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&fs->lane[l], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fs->join[l], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fs->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&fs->d_rot9, (size_t)R * 9 * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&fs->d_quat, (size_t)R * 4 * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&fs->d_nbr, (size_t)R * 6 * sizeof(int));
@@ -570,8 +585,13 @@ extern "C" void hf_fieldset_release(hf_fieldset *fs) {
     if (!fs) return;
     cudaSetDevice(fs->ctx->device);
     cudaFree(fs->data);
-    cudaFree(fs->scratch);
-    cudaFree(fs->planes);
+    for (int l = 0; l < 2; ++l) {
+        cudaFree(fs->scratch[l]);
+        cudaFree(fs->planes[l]);
+        if (fs->lane[l]) cudaStreamDestroy(fs->lane[l]);
+        if (fs->join[l]) cudaEventDestroy(fs->join[l]);
+    }
+    if (fs->fork) cudaEventDestroy(fs->fork);
     cudaFree(fs->d_rot9);
     cudaFree(fs->d_quat);
     cudaFree(fs->d_nbr);
@@ -660,8 +680,16 @@ extern "C" hf_status hf_fieldset_compute(hf_ctx *ctx, const hf_part *s1, const h
     const size_t n3 = (size_t)n * n * n;
     const size_t rs = (size_t)fs->nf * n3;
     const size_t scr_rot = (size_t)fs->chunk * hf::half_spec_elems(n);
-    for (int r0 = 0; r0 < R; r0 += fs->chunk) {
+    // with two pipelines: fork them off the caller's stream, alternate
+    // chunks, join; with one: run on the caller's stream
+    if (fs->lanes == 2) {
+        CU(cudaEventRecord(fs->fork, st));
+        CU(cudaStreamWaitEvent(fs->lane[0], fs->fork, 0));
+        CU(cudaStreamWaitEvent(fs->lane[1], fs->fork, 0));
+    }
+    for (int r0 = 0, c = 0; r0 < R; r0 += fs->chunk, ++c) {
         const int cnt = std::min(fs->chunk, R - r0);
+        const int l = fs->lanes == 2 ? (c & 1) : 0;
         FieldPtrs out;
         float *base = fs->data + (size_t)r0 * rs;
         out.E = base;
@@ -669,8 +697,13 @@ extern "C" hf_status hf_fieldset_compute(hf_ctx *ctx, const hf_part *s1, const h
         out.Fx = base + n3;
         out.Fy = base + 2 * n3;
         out.Fz = base + 3 * n3;
-        s = run_fields(ctx, n, s1, s2, fs->d_rot9 + (size_t)9 * r0, cnt, fs->scratch, scr_rot, fs->planes, out, st);
+        s = run_fields(ctx, n, s1, s2, fs->d_rot9 + (size_t)9 * r0, cnt, fs->scratch[l], scr_rot, fs->planes[l], out,
+                       fs->lanes == 2 ? fs->lane[l] : st);
         if (s != HF_OK) return s;
+    }
+    for (int l = 0; l < 2 && fs->lanes == 2; ++l) {
+        CU(cudaEventRecord(fs->join[l], fs->lane[l]));
+        CU(cudaStreamWaitEvent(st, fs->join[l], 0));
     }
     if (fs->flags & HF_T) {
         CU(timed(ctx, kTorque, st, [&] {
