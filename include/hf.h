@@ -20,7 +20,7 @@
  * Conventions shared by every call:
  *   grid     N^3 nodes on the periodic box [-1,1)^3, spacing h = 2/N, node
  *            index n <-> position -1 + n h, arrays [z][y][x], x fastest,
- *            float32.  Supported N: 32, 64, 96, 128.
+ *            float32.  Supported N: 32, 64, 96, 128, 256.
  *   lags     field index j <-> translation t = j h (periodic), lag 0 at 0.
  *   E        = +f (the Riemann sum of Eq. 1 with volume element h^3).
  *   F        = -grad_t E (spectral; the Nyquist multiplier on each axis is 0).

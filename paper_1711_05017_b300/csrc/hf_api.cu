@@ -31,6 +31,14 @@ static hf_status fail(hf_status s, const char *fmt, ...) {
 
 namespace hf {
 void set_last_error(const char *msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+bool pencil_n(int n) {
+    static int forced = -1;
+    if (forced < 0) {
+        const char *e = getenv("HF_PIPELINE");
+        forced = (e && e[0] == 'p') ? 1 : 0;
+    }
+    return n >= 256 || forced == 1;
+}
 }  // namespace hf
 
 #define CU(call)                                                                                   \
@@ -187,6 +195,22 @@ extern "C" void hf_profile_reset(hf_ctx *c) {
     }
 }
 
+// kernel shared-memory limits for entry points that take no context: once per device
+static cudaError_t ensure_kernel_attrs() {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> g(mu);
+    if (done[dev]) return cudaSuccess;
+    for (int n : {32, 64, 96, 128, 256})
+        if ((e = hf::fft_init_attrs(n)) != cudaSuccess) return e;
+    done[dev] = true;
+    return cudaSuccess;
+}
+
 extern "C" const char *hf_version(void) { return "hf 1.0 sm_103a"; }
 extern "C" const char *hf_last_error(void) { return g_err; }
 
@@ -208,7 +232,7 @@ extern "C" hf_status hf_ctx_create(int device, size_t budget, hf_ctx **out) {
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_qout, 8 * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_qin, 8 * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_qout, 8 * sizeof(float));
-    for (int n : {32, 64, 96, 128})
+    for (int n : {32, 64, 96, 128, 256})
         if (e == cudaSuccess) e = hf::fft_init_attrs(n);
     if (e != cudaSuccess) {
         hf_ctx_destroy(c);
@@ -256,8 +280,13 @@ static hf_status stationary_spectrum(hf_ctx *c, int n, const float *d_grid, floa
     // pass A with the identity: a plain copy of each plane into the transform
     const size_t he = hf::half_spec_elems(n);
     float2 *X1 = nullptr;
-    CU(cudaMallocAsync(&X1, he * sizeof(float2), st));
-    CU(timed(c, kPassA, st, [&] { return hf::run_passA_planes(n, d_grid, X1, 1, st); }));
+    CU(cudaMallocAsync(&X1, 2 * he * sizeof(float2), st));
+    if (hf::pencil_n(n)) {
+        CU(timed(c, kPassA, st, [&] { return hf::run_xfwd(n, d_grid, X1 + he, 1, st); }));
+        CU(timed(c, kPassA, st, [&] { return hf::run_yfwd(n, X1 + he, X1, 1, st); }));
+    } else {
+        CU(timed(c, kPassA, st, [&] { return hf::run_passA_planes(n, d_grid, X1, 1, st); }));
+    }
     CU(timed(c, kPassBFwd, st, [&] { return hf::run_passB_forward(n, X1, spec, scale, st); }));
     CU(cudaFreeAsync(X1, st));
     return HF_OK;
@@ -275,9 +304,11 @@ static hf_status part_fill(hf_part *p, const float *d_grid, cudaStream_t st) {
         const int n = p->n;
         CU(cudaMemcpyAsync(p->grid, d_grid, (size_t)n * n * n * sizeof(float), cudaMemcpyDeviceToDevice, st));
         if (p->arr) {
+            int tw = 0, th = 0;
+            hf::tex_layout(n, &tw, &th);
             CU(hf::run_pad_slices(n, d_grid, p->slab, p->slab_pitch / sizeof(float), st));
-            CU(cudaMemcpy2DToArrayAsync(p->arr, 0, 0, p->slab, p->slab_pitch, (size_t)(n + 1) * sizeof(float),
-                                        (size_t)n * (n + 1), cudaMemcpyDeviceToDevice, st));
+            CU(cudaMemcpy2DToArrayAsync(p->arr, 0, 0, p->slab, p->slab_pitch, (size_t)tw * sizeof(float), (size_t)th,
+                                        cudaMemcpyDeviceToDevice, st));
         }
         return HF_OK;
     }
@@ -298,12 +329,13 @@ static void moving_texture_free(hf_part *p) {
 // plain grid and the resample reads it with ordinary loads
 static hf_status moving_texture_alloc(hf_part *p) {
     const int n = p->n;
-    int maxw = 0, maxh = 0;
+    int maxw = 0, maxh = 0, tw = 0, th = 0;
+    hf::tex_layout(n, &tw, &th);
     if (cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxTexture2DGatherWidth, p->ctx->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&maxh, cudaDevAttrMaxTexture2DGatherHeight, p->ctx->device) != cudaSuccess ||
-        n + 1 > maxw || (long)n * (n + 1) > maxh)
+        tw > maxw || th > maxh)
         return HF_OK;
-    const size_t w = (size_t)(n + 1), h = (size_t)n * (n + 1);
+    const size_t w = (size_t)tw, h = (size_t)th;
     cudaChannelFormatDesc fd = cudaCreateChannelDesc<float>();
     CU(cudaMallocPitch(&p->slab, &p->slab_pitch, w * sizeof(float), h));
     cudaError_t e = cudaMallocArray(&p->arr, &fd, w, h, cudaArrayTextureGather);
@@ -338,7 +370,9 @@ extern "C" hf_status hf_part_create(hf_ctx *ctx, int n, const float *d_grid, int
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n3 = (size_t)n * n * n;
     // moving: the grid plus the padded slices (pitched buffer and array)
-    const size_t bytes = role == HF_MOVING ? n3 * sizeof(float) + 2 * (size_t)(n + 2) * n * (n + 1) * sizeof(float)
+    int tw = 0, th = 0;
+    hf::tex_layout(n, &tw, &th);
+    const size_t bytes = role == HF_MOVING ? n3 * sizeof(float) + 2 * ((size_t)tw + 32) * th * sizeof(float)
                                            : hf::half_spec_elems(n) * sizeof(float2);
     if (!charge(ctx, bytes)) return fail(HF_EBUDGET, "hf_part_create: %zu bytes exceed the budget", bytes);
     hf_part *p = new (std::nothrow) hf_part{ctx, n, role, nullptr, nullptr, bytes};
@@ -511,6 +545,7 @@ int default_chunk(int n) {
         case 32: return 256;
         case 64: return 128;
         case 96: return 48;
+        case 256: return 4;
         default: return 32;
     }
 }
@@ -518,6 +553,9 @@ int default_chunk(int n) {
 }  // namespace
 
 // ---------------------------------------------------------------- fieldsets
+// intermediates per rotation: 3 half spectra for the slab passes, 5 for the pencil pipeline
+static size_t fields_spectra(int n) { return hf::pencil_n(n) ? 5 : 3; }
+
 extern "C" hf_status hf_fieldset_create(hf_ctx *ctx, int n, int R, unsigned flags, hf_fieldset **out) {
     if (!ctx || !out) return fail(HF_EINVAL, "hf_fieldset_create: NULL argument");
     *out = nullptr;
@@ -547,7 +585,7 @@ extern "C" hf_status hf_fieldset_create(hf_ctx *ctx, int n, int R, unsigned flag
     }
     const size_t n3 = (size_t)n * n * n;
     const size_t data_b = (size_t)R * nf * n3 * sizeof(float);
-    const size_t scr_b = 3 * (size_t)fs->chunk * hf::half_spec_elems(n) * sizeof(float2);
+    const size_t scr_b = fields_spectra(n) * (size_t)fs->chunk * hf::half_spec_elems(n) * sizeof(float2);
     const size_t planes_b = (size_t)fs->chunk * n3 * sizeof(float);
     fs->stage_bytes = (size_t)R * (9 * sizeof(float) + 4 * sizeof(double) + 6 * sizeof(int) + 18 * sizeof(float) +
                                    18 * sizeof(double));
@@ -612,6 +650,19 @@ extern "C" unsigned hf_fieldset_flags(const hf_fieldset *fs) { return fs ? fs->f
 static hf_status run_fields(hf_ctx *c, int n, const hf_part *s1, const hf_part *s2, const float *rot9, int cnt,
                             float2 *scratch, size_t scratch_rot, float *planes, FieldPtrs out, cudaStream_t st) {
     float2 *X1 = scratch, *Y1 = scratch + scratch_rot, *Y2 = scratch + 2 * scratch_rot;
+    if (hf::pencil_n(n)) {
+        float2 *A = scratch + 3 * scratch_rot, *B = scratch + 4 * scratch_rot;
+        if (s2->tex)
+            CU(timed(c, kResample, st, [&] { return hf::run_resample_tex(n, s2->tex, rot9, planes, cnt, st); }));
+        else
+            CU(timed(c, kResample, st, [&] { return hf::run_resample_chunk(n, s2->grid, rot9, planes, cnt, st); }));
+        CU(timed(c, kPassA, st, [&] { return hf::run_xfwd(n, planes, A, cnt, st); }));
+        CU(timed(c, kPassA, st, [&] { return hf::run_yfwd(n, A, X1, cnt, st); }));
+        CU(timed(c, kPassB, st, [&] { return hf::run_passB(n, X1, s1->spec, Y1, Y2, cnt, st); }));
+        CU(timed(c, kPassC, st, [&] { return hf::run_yinv(n, Y1, Y2, A, X1, B, cnt, st); }));
+        CU(timed(c, kPassC, st, [&] { return hf::run_xinv(n, A, X1, B, out, cnt, st); }));
+        return HF_OK;
+    }
     if (s2->tex)
         CU(timed(c, kResample, st, [&] { return hf::run_resample_tex(n, s2->tex, rot9, planes, cnt, st); }));
     else
@@ -818,7 +869,7 @@ extern "C" hf_status hf_resample(int n, const float *d_rho, const float h_R[9], 
 
 extern "C" size_t hf_rfft3d_scratch_bytes(int n) {
     if (!hf::supported_n(n)) return 0;
-    return 2 * hf::half_spec_elems(n) * sizeof(float2) + 256;
+    return 3 * hf::half_spec_elems(n) * sizeof(float2) + 256;
 }
 
 extern "C" hf_status hf_rfft3d(int n, const float *d_in, float *d_out, void *d_scratch, hf_stream stream) {
@@ -826,10 +877,16 @@ extern "C" hf_status hf_rfft3d(int n, const float *d_in, float *d_out, void *d_s
     if (!d_in || !d_out || !d_scratch) return fail(HF_EINVAL, "hf_rfft3d: NULL argument");
     if ((uintptr_t)d_scratch % 16) return fail(HF_EINVAL, "hf_rfft3d: scratch must be 16-byte aligned");
     if ((uintptr_t)d_in % 8) return fail(HF_EINVAL, "hf_rfft3d: d_in must be 8-byte aligned");
+    CU(ensure_kernel_attrs());
     cudaStream_t st = (cudaStream_t)stream;
     const size_t he = hf::half_spec_elems(n);
     float2 *X1 = (float2 *)d_scratch, *spec = X1 + he;
-    CU(hf::run_passA_planes(n, d_in, X1, 1, st));
+    if (hf::pencil_n(n)) {
+        CU(hf::run_xfwd(n, d_in, spec + he, 1, st));
+        CU(hf::run_yfwd(n, spec + he, X1, 1, st));
+    } else {
+        CU(hf::run_passA_planes(n, d_in, X1, 1, st));
+    }
     CU(hf::run_passB_forward(n, X1, spec, 1.0f, st));
     CU(hf::run_unpermute(n, spec, (float2 *)d_out, st));
     return HF_OK;
@@ -838,7 +895,7 @@ extern "C" hf_status hf_rfft3d(int n, const float *d_in, float *d_out, void *d_s
 extern "C" size_t hf_fields_scratch_bytes(int n) {
     if (!hf::supported_n(n)) return 0;
     const size_t n3 = (size_t)n * n * n;
-    return 3 * hf::half_spec_elems(n) * sizeof(float2) + 4 * n3 * sizeof(float) + 256;
+    return fields_spectra(n) * hf::half_spec_elems(n) * sizeof(float2) + 4 * n3 * sizeof(float) + 256;
 }
 
 extern "C" hf_status hf_fields(hf_ctx *ctx, const hf_part *s1, const hf_part *s2, const float h_quat[4], float *d_E,
@@ -852,7 +909,7 @@ extern "C" hf_status hf_fields(hf_ctx *ctx, const hf_part *s1, const hf_part *s2
     cudaStream_t st = (cudaStream_t)stream;
     const size_t he = hf::half_spec_elems(n), n3 = (size_t)n * n * n;
     float2 *scr = (float2 *)d_scratch;
-    float *dummy = (float *)(scr + 3 * he);
+    float *dummy = (float *)(scr + fields_spectra(n) * he);
     float *planes = dummy + 3 * n3;
     float *rot = planes + n3;
     const Quat q = qnorm(h_quat);

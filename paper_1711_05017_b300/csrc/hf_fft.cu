@@ -182,14 +182,17 @@ constexpr int kRsX = 32, kRsY = 8, kRsZ = 4;
 // trilinear sample is two gathers; the weights stay in float32 software.
 template <int N>
 __device__ __forceinline__ float trilinear_tex(cudaTextureObject_t t, float vx, float vy, float vz) {
+    constexpr int SC = TexLayout<N>::SC;
     const float fx = floorf(vx), fy = floorf(vy), fz = floorf(vz);
     const float ax = vx - fx, ay = vy - fy, az = vz - fz;
     const int x0 = wrapN<N>((int)fx + N / 2), y0 = wrapN<N>((int)fy + N / 2), z0 = wrapN<N>((int)fz + N / 2);
     const int z1 = wrapN<N>(z0 + 1);
-    const float u = (float)x0 + 1.0f;
+    // slice z sits at texel origin ((z % SC)(N+1), (z / SC)(N+1))
     // gather components: w = (x0, y0), z = (x0+1, y0), x = (x0, y0+1), y = (x0+1, y0+1)
-    const float4 a = tex2Dgather<float4>(t, u, (float)(z0 * (N + 1) + y0) + 1.0f, 0);
-    const float4 b = tex2Dgather<float4>(t, u, (float)(z1 * (N + 1) + y0) + 1.0f, 0);
+    const float4 a = tex2Dgather<float4>(t, (float)((z0 % SC) * (N + 1) + x0) + 1.0f,
+                                         (float)((z0 / SC) * (N + 1) + y0) + 1.0f, 0);
+    const float4 b = tex2Dgather<float4>(t, (float)((z1 % SC) * (N + 1) + x0) + 1.0f,
+                                         (float)((z1 / SC) * (N + 1) + y0) + 1.0f, 0);
     const float a0 = fmaf(ax, a.z - a.w, a.w), a1 = fmaf(ax, a.y - a.x, a.x);
     const float b0 = fmaf(ax, b.z - b.w, b.w), b1 = fmaf(ax, b.y - b.x, b.x);
     const float c0 = fmaf(ay, a1 - a0, a0), c1 = fmaf(ay, b1 - b0, b0);
@@ -223,15 +226,18 @@ __global__ void __launch_bounds__(kRsX * kRsY) resample_tex_kernel(cudaTextureOb
     for (int j = 0; j < kRsZ; ++j) o[(size_t)(tz * kRsZ + j) * N * N] = v[j];
 }
 
-// stacked padded slices for the texture: slab[row][x], row = z(N+1) + y, x, y in [0, N]
+// padded slices for the texture: slice z, local (x, y) in [0, N]^2, at
+// slab[((z / SC)(N+1) + y) * pitch + (z % SC)(N+1) + x]
 template <int N>
 __global__ void pad_slices_kernel(const float *__restrict__ g, float *__restrict__ slab, size_t pitch_floats) {
+    constexpr int SC = TexLayout<N>::SC;
     const size_t total = (size_t)N * (N + 1) * (N + 1);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const int x = (int)(i % (N + 1));
-        const size_t row = i / (N + 1);
-        const int y = (int)(row % (N + 1)), z = (int)(row / (N + 1));
-        slab[row * pitch_floats + x] = __ldg(g + ((size_t)z * N + wrapN<N>(y)) * N + wrapN<N>(x));
+        const size_t rest = i / (N + 1);
+        const int y = (int)(rest % (N + 1)), z = (int)(rest / (N + 1));
+        const size_t row = (size_t)(z / SC) * (N + 1) + y, col = (size_t)(z % SC) * (N + 1) + x;
+        slab[row * pitch_floats + col] = __ldg(g + ((size_t)z * N + wrapN<N>(y)) * N + wrapN<N>(x));
     }
 }
 
@@ -266,8 +272,8 @@ __global__ void __launch_bounds__(kRsX * kRsY) resample_chunk_kernel(const float
 template <int N>
 struct PassB {
     static constexpr int H = N / 2 + 1;
-    static constexpr int C = (H + 1) / 2;  // kx chunk width (2 chunks)
-    static constexpr int NCH = 2;
+    static constexpr int C = N <= 128 ? (H + 1) / 2 : 17;  // kx chunk width
+    static constexpr int NCH = (H + C - 1) / C;
     static constexpr int NT = (N >= 64) ? 256 : 128;
     static constexpr int MINB = (N >= 128) ? 3 : 4;
     static constexpr size_t smem = sizeof(float2) * ((size_t)N * 2 * C + N);
@@ -372,14 +378,15 @@ __device__ __forceinline__ void build_xtable(float4 *xt) {
 // half-spectrum columns of the plane; real part -> out0, imaginary -> out1.
 // PAIR 0: Z[k] = S(k) (1 + pi kx~)              -> (E, Fx)
 // PAIR 1: Z[k] = -(Gy(k) + i Gz(k))             -> (Fy, Fz)
-template <int N, int PAIR>
+// Rows [0, ROWS) of `plane` (pitch PW) go to output rows [0, ROWS), RB rows
+// per batch through the row buffer Tb (pitch TP).
+template <int N, int PAIR, int PW, int RB, int TP, int NT, int ROWS>
 __device__ __forceinline__ void x_pass(const float2 *plane, int colA, int colB, float2 *Tb,
                                        const float2 *twN, const float4 *xt, float *__restrict__ out0,
                                        float *__restrict__ out1) {
-    constexpr int R1 = Fact<N>::R1, R2 = Fact<N>::R2, PW = PassC<N>::PW, RB = PassC<N>::RB,
-                  TP = PassC<N>::TP, NT = PassC<N>::NT;
+    constexpr int R1 = Fact<N>::R1, R2 = Fact<N>::R2;
 #pragma unroll 1
-    for (int y0 = 0; y0 < N; y0 += RB) {
+    for (int y0 = 0; y0 < ROWS; y0 += RB) {
         // stage 1 (inverse), items (row, k1): slots R2*k1 + k2 <- Z[k1 + R1*k2]
 #pragma unroll 1
         for (int w = threadIdx.x; w < RB * R1; w += NT) {
@@ -457,7 +464,7 @@ __global__ void __launch_bounds__(PassC<N>::NT) passC_kernel(const float2 *__res
     __syncthreads();
     fft_lines<N, +1, 2 * H, PW, 1, NT>(plane, twN);
     const size_t fo = (size_t)r * out.rot_stride + (size_t)z * N * N;
-    x_pass<N, 0>(plane, 0, H, Tb, twN, xt, out.E + fo, out.Fx + fo);
+    x_pass<N, 0, PW, RB, TP, NT, N>(plane, 0, H, Tb, twN, xt, out.E + fo, out.Fx + fo);
     const float2 *s2 = Y2 + ((size_t)r * N + z) * N * H;
     for (int i = threadIdx.x; i < N * H; i += NT) {
         const int y = i / H, c = i % H;
@@ -466,9 +473,175 @@ __global__ void __launch_bounds__(PassC<N>::NT) passC_kernel(const float2 *__res
     cp_async_wait_all();
     __syncthreads();
     fft_lines<N, +1, H, PW, 1, NT>(plane, twN);
-    x_pass<N, 1>(plane, 0, H, Tb, twN, xt, out.Fy + fo, out.Fz + fo);
-    (void)RB;
-    (void)TP;
+    x_pass<N, 1, PW, RB, TP, NT, N>(plane, 0, H, Tb, twN, xt, out.Fy + fo, out.Fz + fo);
+}
+
+// ------------------------------------------------------- pencil pipeline
+// For grids whose planes do not fit one CTA's shared memory (N = 256): the
+// x and y stages of passes A and C run as separate row-batch and column-chunk
+// kernels with the intermediates in global memory (same layouts and slot
+// orders as the slab passes, so pass B is shared).
+template <int N>
+struct Pencil {
+    static constexpr int H = N / 2 + 1, HALF = N / 2;
+    static constexpr int RBX = 16;                      // rows per CTA, x stages
+    static constexpr int CY = 16;                       // kx columns per CTA, y stages
+    static constexpr int NCY = (H + CY - 1) / CY;
+    static constexpr int NT = 256;
+    static constexpr int PW = 3 * H;                    // x-inverse row pitch: S | Gy | Gz (odd)
+    static constexpr int TP = N + 1;
+    static constexpr size_t smem_xfwd = sizeof(float2) * ((size_t)RBX * H + N + HALF);
+    static constexpr size_t smem_yfwd = sizeof(float2) * ((size_t)N * CY + N);
+    static constexpr size_t smem_yinv = sizeof(float2) * ((size_t)N * 3 * CY + N);
+    static constexpr size_t smem_xinv =
+        sizeof(float2) * ((size_t)RBX * PW + (size_t)RBX * TP + N) + sizeof(float4) * (size_t)N;
+};
+
+// x forward: RBX rows (q = z N + y) of rotation r -> half-spectrum rows Xa[r][q][kx*]
+template <int N>
+__global__ void __launch_bounds__(Pencil<N>::NT) xfwd_kernel(const float *__restrict__ planes,
+                                                             float2 *__restrict__ Xa) {
+    constexpr int H = Pencil<N>::H, HALF = Pencil<N>::HALF, RBX = Pencil<N>::RBX, NT = Pencil<N>::NT;
+    extern __shared__ float2 sm[];
+    float2 *P = sm;               // [RBX][H]
+    float2 *twN = P + RBX * H;
+    float2 *twH = twN + N;
+    const size_t q0 = (size_t)blockIdx.x * RBX;
+    const int r = blockIdx.y;
+    const float2 *src = reinterpret_cast<const float2 *>(planes + ((size_t)r * N * N + q0) * N);
+    for (int i = threadIdx.x; i < RBX * HALF; i += NT) {
+        const int row = i / HALF, x2 = i % HALF;
+        cp_async8(P + row * H + x2, src + i);
+    }
+    load_tw<N>(twN);
+    load_tw<HALF>(twH);
+    cp_async_wait_all();
+    __syncthreads();
+    fft_lines<HALF, -1, RBX, 1, H, NT>(P, twH);
+    for (int i = threadIdx.x; i < RBX * (N / 4 + 1); i += NT) {
+        const int y = i % RBX, k = i / RBX;
+        float2 *row = P + y * H;
+        if (k == 0) {
+            const float2 z0 = row[0];
+            row[0] = make_float2(z0.x + z0.y, 0.f);
+            row[HALF] = make_float2(z0.x - z0.y, 0.f);
+        } else if (4 * k == N) {
+            const int sl = perm_slot<HALF>(k);
+            row[sl] = cconj(row[sl]);
+        } else {
+            const int s1 = perm_slot<HALF>(k), s2 = perm_slot<HALF>(HALF - k);
+            const float2 a = row[s1], b = row[s2];
+            const float2 Ek = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+            const float2 Ok = make_float2(0.5f * (a.y + b.y), -0.5f * (a.x - b.x));
+            const float2 WO = cmul(twN[k], Ok);
+            row[s1] = cadd(Ek, WO);
+            row[s2] = cconj(csub(Ek, WO));
+        }
+    }
+    __syncthreads();
+    float2 *dst = Xa + ((size_t)r * N * N + q0) * H;
+    for (int i = threadIdx.x; i < RBX * H; i += NT) dst[i] = P[i];
+}
+
+// y forward: kx columns [c0, c0 + CY) of plane z -> X1[r][z][ky*][kx*]
+template <int N>
+__global__ void __launch_bounds__(Pencil<N>::NT) yfwd_kernel(const float2 *__restrict__ Xa,
+                                                             float2 *__restrict__ X1) {
+    constexpr int H = Pencil<N>::H, CY = Pencil<N>::CY, NCY = Pencil<N>::NCY, NT = Pencil<N>::NT;
+    extern __shared__ float2 sm[];
+    float2 *T = sm;               // [N][CY]
+    float2 *twN = T + N * CY;
+    const int z = blockIdx.x / NCY, c0 = (blockIdx.x % NCY) * CY, r = blockIdx.y;
+    const int cw = min(CY, H - c0);
+    const float2 *src = Xa + ((size_t)r * N + z) * N * H + c0;
+    for (int i = threadIdx.x; i < N * CY; i += NT) {
+        const int y = i / CY, c = i % CY;
+        if (c < cw) cp_async8(T + i, src + (size_t)y * H + c);
+        else T[i] = make_float2(0.f, 0.f);
+    }
+    load_tw<N>(twN);
+    cp_async_wait_all();
+    __syncthreads();
+    fft_lines<N, -1, CY, CY, 1, NT>(T, twN);
+    float2 *dst = X1 + ((size_t)r * N + z) * N * H + c0;
+    for (int i = threadIdx.x; i < N * CY; i += NT) {
+        const int sl = i / CY, c = i % CY;
+        if (c < cw) dst[(size_t)sl * H + c] = T[i];
+    }
+}
+
+// y inverse of S', Gy = i pi ky~ S' and Gz' for kx columns [c0, c0 + CY) of plane z
+template <int N>
+__global__ void __launch_bounds__(Pencil<N>::NT) yinv_kernel(const float2 *__restrict__ Y1,
+                                                             const float2 *__restrict__ Y2,
+                                                             float2 *__restrict__ ZS, float2 *__restrict__ ZGy,
+                                                             float2 *__restrict__ ZGz) {
+    constexpr int H = Pencil<N>::H, CY = Pencil<N>::CY, NCY = Pencil<N>::NCY, NT = Pencil<N>::NT,
+                  W3 = 3 * CY;
+    extern __shared__ float2 sm[];
+    float2 *T = sm;               // [N][3 CY]: S | Gy | Gz
+    float2 *twN = T + N * W3;
+    const int z = blockIdx.x / NCY, c0 = (blockIdx.x % NCY) * CY, r = blockIdx.y;
+    const int cw = min(CY, H - c0);
+    const size_t base = ((size_t)r * N + z) * N * H + c0;
+    for (int i = threadIdx.x; i < N * CY; i += NT) {
+        const int sl = i / CY, c = i % CY;
+        if (c < cw) {
+            cp_async8(T + sl * W3 + c, Y1 + base + (size_t)sl * H + c);
+            cp_async8(T + sl * W3 + 2 * CY + c, Y2 + base + (size_t)sl * H + c);
+        } else {
+            T[sl * W3 + c] = make_float2(0.f, 0.f);
+            T[sl * W3 + 2 * CY + c] = make_float2(0.f, 0.f);
+        }
+    }
+    load_tw<N>(twN);
+    cp_async_wait_all();
+    __syncthreads();
+    for (int i = threadIdx.x; i < N * CY; i += NT) {
+        const int sl = i / CY, c = i % CY;
+        T[sl * W3 + CY + c] = cmul_is(T[sl * W3 + c], signed_k_mult<N>(slot_freq<N>(sl)));
+    }
+    __syncthreads();
+    fft_lines<N, +1, W3, W3, 1, NT>(T, twN);
+    for (int i = threadIdx.x; i < N * CY; i += NT) {
+        const int y = i / CY, c = i % CY;
+        if (c < cw) {
+            const size_t o = base + (size_t)y * H + c;
+            ZS[o] = T[y * W3 + c];
+            ZGy[o] = T[y * W3 + CY + c];
+            ZGz[o] = T[y * W3 + 2 * CY + c];
+        }
+    }
+}
+
+// x inverse: RBX rows (q = z N + y): (E, Fx) from S'', (Fy, Fz) from Gy'', Gz''
+template <int N>
+__global__ void __launch_bounds__(Pencil<N>::NT) xinv_kernel(const float2 *__restrict__ ZS,
+                                                             const float2 *__restrict__ ZGy,
+                                                             const float2 *__restrict__ ZGz, FieldPtrs out) {
+    constexpr int H = Pencil<N>::H, RBX = Pencil<N>::RBX, NT = Pencil<N>::NT, PW = Pencil<N>::PW,
+                  TP = Pencil<N>::TP;
+    extern __shared__ float2 sm[];
+    float2 *plane = sm;                    // [RBX][PW]
+    float2 *Tb = plane + RBX * PW;         // [RBX][TP]
+    float2 *twN = Tb + RBX * TP;
+    float4 *xt = reinterpret_cast<float4 *>(twN + N);
+    const size_t q0 = (size_t)blockIdx.x * RBX;
+    const int r = blockIdx.y;
+    const size_t in = ((size_t)r * N * N + q0) * H;
+    for (int i = threadIdx.x; i < RBX * H; i += NT) {
+        const int row = i / H, c = i % H;
+        cp_async8(plane + row * PW + c, ZS + in + i);
+        cp_async8(plane + row * PW + H + c, ZGy + in + i);
+        cp_async8(plane + row * PW + 2 * H + c, ZGz + in + i);
+    }
+    load_tw<N>(twN);
+    build_xtable<N>(xt);
+    cp_async_wait_all();
+    __syncthreads();
+    const size_t fo = (size_t)r * out.rot_stride + q0 * N;
+    x_pass<N, 0, PW, RBX, TP, NT, RBX>(plane, 0, H, Tb, twN, xt, out.E + fo, out.Fx + fo);
+    x_pass<N, 1, PW, RBX, TP, NT, RBX>(plane, 2 * H, H, Tb, twN, xt, out.Fy + fo, out.Fz + fo);
 }
 
 // -------------------------------------------- natural-order spectrum copy
@@ -485,8 +658,21 @@ __global__ void unpermute_spectrum_kernel(const float2 *__restrict__ spec, float
 
 // ------------------------------------------------------------- launchers
 template <int N>
+static cudaError_t set_pencil_attrs() {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(xfwd_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Pencil<N>::smem_xfwd))) return e;
+    if ((e = cudaFuncSetAttribute(yfwd_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Pencil<N>::smem_yfwd))) return e;
+    if ((e = cudaFuncSetAttribute(yinv_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Pencil<N>::smem_yinv))) return e;
+    if ((e = cudaFuncSetAttribute(xinv_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Pencil<N>::smem_xinv))) return e;
+    if ((e = cudaFuncSetAttribute(passB_kernel<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N>::smem))) return e;
+    if ((e = cudaFuncSetAttribute(passB_kernel<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N>::smem))) return e;
+    return cudaSuccess;
+}
+
+template <int N>
 static cudaError_t set_smem_attrs() {
     cudaError_t e;
+    if ((e = set_pencil_attrs<N>())) return e;
     if ((e = cudaFuncSetAttribute(passA_kernel<N, SRC_RAW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassA<N>::smem))) return e;
     if ((e = cudaFuncSetAttribute(passA_kernel<N, SRC_PLANES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassA<N>::smem))) return e;
     if ((e = cudaFuncSetAttribute(passB_kernel<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N>::smem))) return e;
@@ -532,6 +718,28 @@ static cudaError_t launch_passC(const float2 *Y1, const float2 *Y2, FieldPtrs ou
     return cudaGetLastError();
 }
 template <int N>
+static cudaError_t launch_xfwd(const float *planes, float2 *Xa, int nrot, cudaStream_t st) {
+    xfwd_kernel<N><<<dim3(N * N / Pencil<N>::RBX, nrot), Pencil<N>::NT, Pencil<N>::smem_xfwd, st>>>(planes, Xa);
+    return cudaGetLastError();
+}
+template <int N>
+static cudaError_t launch_yfwd(const float2 *Xa, float2 *X1, int nrot, cudaStream_t st) {
+    yfwd_kernel<N><<<dim3(N * Pencil<N>::NCY, nrot), Pencil<N>::NT, Pencil<N>::smem_yfwd, st>>>(Xa, X1);
+    return cudaGetLastError();
+}
+template <int N>
+static cudaError_t launch_yinv(const float2 *Y1, const float2 *Y2, float2 *ZS, float2 *ZGy, float2 *ZGz, int nrot,
+                               cudaStream_t st) {
+    yinv_kernel<N><<<dim3(N * Pencil<N>::NCY, nrot), Pencil<N>::NT, Pencil<N>::smem_yinv, st>>>(Y1, Y2, ZS, ZGy, ZGz);
+    return cudaGetLastError();
+}
+template <int N>
+static cudaError_t launch_xinv(const float2 *ZS, const float2 *ZGy, const float2 *ZGz, FieldPtrs out, int nrot,
+                               cudaStream_t st) {
+    xinv_kernel<N><<<dim3(N * N / Pencil<N>::RBX, nrot), Pencil<N>::NT, Pencil<N>::smem_xinv, st>>>(ZS, ZGy, ZGz, out);
+    return cudaGetLastError();
+}
+template <int N>
 static cudaError_t launch_unpermute(const float2 *spec, float2 *out, cudaStream_t st) {
     unpermute_spectrum_kernel<N><<<148, 256, 0, st>>>(spec, out);
     return cudaGetLastError();
@@ -545,8 +753,35 @@ static cudaError_t launch_unpermute(const float2 *spec, float2 *out, cudaStream_
         case 128: { constexpr int NN = 128; return call; }  \
         default: return cudaErrorInvalidValue;              \
     }
+// kernels built for every size, the pencil pipeline's 256 included
+#define HF_DISPATCH_ALL(n, call)                            \
+    switch (n) {                                            \
+        case 32: { constexpr int NN = 32; return call; }    \
+        case 64: { constexpr int NN = 64; return call; }    \
+        case 96: { constexpr int NN = 96; return call; }    \
+        case 128: { constexpr int NN = 128; return call; }  \
+        case 256: { constexpr int NN = 256; return call; }  \
+        default: return cudaErrorInvalidValue;              \
+    }
 
-cudaError_t fft_init_attrs(int n) { HF_DISPATCH(n, set_smem_attrs<NN>()); }
+cudaError_t fft_init_attrs(int n) {
+    if (n == 256) return set_pencil_attrs<256>();
+    HF_DISPATCH(n, set_smem_attrs<NN>());
+}
+cudaError_t run_xfwd(int n, const float *planes, float2 *Xa, int nrot, cudaStream_t st) {
+    HF_DISPATCH_ALL(n, launch_xfwd<NN>(planes, Xa, nrot, st));
+}
+cudaError_t run_yfwd(int n, const float2 *Xa, float2 *X1, int nrot, cudaStream_t st) {
+    HF_DISPATCH_ALL(n, launch_yfwd<NN>(Xa, X1, nrot, st));
+}
+cudaError_t run_yinv(int n, const float2 *Y1, const float2 *Y2, float2 *ZS, float2 *ZGy, float2 *ZGz, int nrot,
+                     cudaStream_t st) {
+    HF_DISPATCH_ALL(n, launch_yinv<NN>(Y1, Y2, ZS, ZGy, ZGz, nrot, st));
+}
+cudaError_t run_xinv(int n, const float2 *ZS, const float2 *ZGy, const float2 *ZGz, FieldPtrs out, int nrot,
+                     cudaStream_t st) {
+    HF_DISPATCH_ALL(n, launch_xinv<NN>(ZS, ZGy, ZGz, out, nrot, st));
+}
 cudaError_t run_passA(int n, const float *rho, const float *rot9, float2 *X1, int nrot, cudaStream_t st) {
     HF_DISPATCH(n, (launch_passA<NN, SRC_RAW>(rho, rot9, X1, nrot, st)));
 }
@@ -554,25 +789,25 @@ cudaError_t run_passA_planes(int n, const float *planes, float2 *X1, int nrot, c
     HF_DISPATCH(n, (launch_passA<NN, SRC_PLANES>(planes, nullptr, X1, nrot, st)));
 }
 cudaError_t run_resample_chunk(int n, const float *rho, const float *rot9, float *out, int nrot, cudaStream_t st) {
-    HF_DISPATCH(n, launch_resample_chunk<NN>(rho, rot9, out, nrot, st));
+    HF_DISPATCH_ALL(n, launch_resample_chunk<NN>(rho, rot9, out, nrot, st));
 }
 cudaError_t run_resample_tex(int n, cudaTextureObject_t tex, const float *rot9, float *out, int nrot, cudaStream_t st) {
-    HF_DISPATCH(n, launch_resample_tex<NN>(tex, rot9, out, nrot, st));
+    HF_DISPATCH_ALL(n, launch_resample_tex<NN>(tex, rot9, out, nrot, st));
 }
 cudaError_t run_pad_slices(int n, const float *g, float *slab, size_t pitch_floats, cudaStream_t st) {
-    HF_DISPATCH(n, launch_pad_slices<NN>(g, slab, pitch_floats, st));
+    HF_DISPATCH_ALL(n, launch_pad_slices<NN>(g, slab, pitch_floats, st));
 }
 cudaError_t run_passB(int n, const float2 *X1, const float2 *R1hat, float2 *Y1, float2 *Y2, int nrot, cudaStream_t st) {
-    HF_DISPATCH(n, launch_passB<NN>(X1, R1hat, Y1, Y2, nrot, st));
+    HF_DISPATCH_ALL(n, launch_passB<NN>(X1, R1hat, Y1, Y2, nrot, st));
 }
 cudaError_t run_passB_forward(int n, const float2 *X1, float2 *spec, float scale, cudaStream_t st) {
-    HF_DISPATCH(n, launch_passB_fwd<NN>(X1, spec, scale, st));
+    HF_DISPATCH_ALL(n, launch_passB_fwd<NN>(X1, spec, scale, st));
 }
 cudaError_t run_passC(int n, const float2 *Y1, const float2 *Y2, FieldPtrs out, int nrot, cudaStream_t st) {
     HF_DISPATCH(n, launch_passC<NN>(Y1, Y2, out, nrot, st));
 }
 cudaError_t run_unpermute(int n, const float2 *spec, float2 *out, cudaStream_t st) {
-    HF_DISPATCH(n, launch_unpermute<NN>(spec, out, st));
+    HF_DISPATCH_ALL(n, launch_unpermute<NN>(spec, out, st));
 }
 
 }  // namespace hf

@@ -17,7 +17,25 @@ struct Rot9 {
     float r[9];  // row-major rotation matrix
 };
 
-inline bool supported_n(int n) { return n == 32 || n == 64 || n == 96 || n == 128; }
+inline bool supported_n(int n) { return n == 32 || n == 64 || n == 96 || n == 128 || n == 256; }
+
+// grids too large for one CTA's shared memory per plane use the pencil
+// pipeline; HF_PIPELINE=pencil selects it for every size (cross-checks)
+bool pencil_n(int n);
+
+// Texture layout of a moving grid: N padded (N+1)^2 slices tiled SC across
+// so that the 2D array stays within the gather height limit (32768 texels).
+template <int N>
+struct TexLayout {
+    static constexpr int SC = N <= 128 ? 1 : 4;
+    static constexpr int W = SC * (N + 1);
+    static constexpr int HGT = ((N + SC - 1) / SC) * (N + 1);
+};
+inline void tex_layout(int n, int *w, int *h) {
+    const int sc = n <= 128 ? 1 : 4;
+    *w = sc * (n + 1);
+    *h = ((n + sc - 1) / sc) * (n + 1);
+}
 
 // elements of one half-spectrum intermediate (complex): N * N * (N/2 + 1)
 inline size_t half_spec_elems(int n) { return (size_t)n * n * (n / 2 + 1); }
@@ -40,6 +58,14 @@ cudaError_t run_passB(int n, const float2 *X1, const float2 *R1hat, float2 *Y1, 
 cudaError_t run_passB_forward(int n, const float2 *X1, float2 *spec, float scale, cudaStream_t st);
 cudaError_t run_passC(int n, const float2 *Y1, const float2 *Y2, FieldPtrs out, int nrot, cudaStream_t st);
 cudaError_t run_unpermute(int n, const float2 *spec, float2 *out, cudaStream_t st);
+// pencil pipeline (any N; the only one for N = 256): planes -> Xa -> X1 (forward x, y),
+// then pass B, then Y1/Y2 -> Z_S, Z_Gy, Z_Gz (inverse y) -> fields (inverse x)
+cudaError_t run_xfwd(int n, const float *planes, float2 *Xa, int nrot, cudaStream_t st);
+cudaError_t run_yfwd(int n, const float2 *Xa, float2 *X1, int nrot, cudaStream_t st);
+cudaError_t run_yinv(int n, const float2 *Y1, const float2 *Y2, float2 *ZS, float2 *ZGy, float2 *ZGz, int nrot,
+                     cudaStream_t st);
+cudaError_t run_xinv(int n, const float2 *ZS, const float2 *ZGy, const float2 *ZGz, FieldPtrs out, int nrot,
+                     cudaStream_t st);
 
 // hf_kernels.cu
 cudaError_t run_splat(int n, const float *pts, const float *sigma, const float *amp, int P, float *grid,

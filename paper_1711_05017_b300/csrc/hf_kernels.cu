@@ -287,6 +287,7 @@ __global__ void query_kernel(QueryGeom g, const float *__restrict__ tq, int Q, i
         case 64: { constexpr int NN = 64; call; break; }    \
         case 96: { constexpr int NN = 96; call; break; }    \
         case 128: { constexpr int NN = 128; call; break; }  \
+        case 256: { constexpr int NN = 256; call; break; }  \
         default: return cudaErrorInvalidValue;              \
     }
 

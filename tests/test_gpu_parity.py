@@ -306,3 +306,49 @@ def test_c2_full_size_sampled(hf, ctx):
     for d in range(3):
         assert rel_err(host(fs.get(0, 4 + d)), T[0, d]) <= TOL, d
     del torch
+
+
+# ------------------------------------------------ 256^3 (pencil pipeline)
+
+@pytest.mark.slow
+def test_rfft3d_and_fields_256(hf, ctx):
+    """256^3 runs the pencil pipeline (planes exceed one CTA's shared memory)."""
+    import torch
+    n = 256
+    rng = np.random.default_rng(256)
+    x = rng.standard_normal((n, n, n)).astype(np.float32)
+    got = hf.rfft3d(cuda(x))
+    torch.cuda.synchronize()
+    ref = np.fft.rfftn(x.astype(np.float64))
+    assert np.abs(got.cpu().numpy() - ref).max() <= 1e-5 * np.abs(ref).max()
+    del got, x
+    s1, s2 = synth.c4_pair(0)
+    r1 = oracle.splat(n, s1.pts[:300], s1.sigma[:300]).astype(np.float32)
+    r2 = oracle.splat(n, s2.pts[:300], s2.sigma[:300]).astype(np.float32)
+    q = synth.random_quaternions(4, 1)[0]
+    got = gpu_fields(hf, ctx, r1, r2, q)
+    qn = norm_quats(q.astype(np.float32))[0]
+    R = oracle.quat_to_rot(qn).astype(np.float32).astype(np.float64)
+    ref = oracle.fields(r1.astype(np.float64), oracle.resample(r2.astype(np.float64), R))
+    for g, r in zip(got, ref):
+        assert rel_err(g, r) <= TOL
+
+
+def test_fieldset_256_matches_single_rotation_path(hf, ctx):
+    """The batched 256^3 field set equals the one-rotation entry point."""
+    import torch
+    n, R = 256, 8
+    s1, s2 = synth.c4_pair(1)
+    g1 = ctx.density_build(n, cuda(s1.pts), cuda(s1.sigma))
+    g2 = ctx.density_build(n, cuda(s2.pts), cuda(s2.sigma))
+    q = synth.random_quaternions(8, R).astype(np.float32)
+    p1, p2 = ctx.part(g1, hf.HF_STATIONARY), ctx.part(g2, hf.HF_MOVING)
+    fs = ctx.fieldset(n, R, hf.HF_E | hf.HF_F | hf.HF_T)
+    fs.compute(p1, p2, q)
+    out = [torch.empty((n, n, n), device="cuda") for _ in range(4)]
+    for i in (0, 5):
+        ctx.fields(p1, p2, q[i], *out)
+        for f in range(4):
+            a, b = host(fs.get(i, f)), host(out[f])
+            assert rel_err(a, b) <= 1e-6, (i, f)
+    assert np.isfinite(host(fs.get(3, 4))).all()
