@@ -100,8 +100,9 @@ const char *hf_last_error(void);
  * Errors: HF_EINVAL (null out, bad device), HF_ECUDA. */
 hf_status hf_ctx_create(int device, size_t hbm_budget_bytes, hf_ctx **out);
 void hf_ctx_destroy(hf_ctx *ctx);
-/* Bytes currently charged against the budget. */
+/* Bytes currently charged against the budget, and the budget (0 = none). */
 size_t hf_ctx_reserved_bytes(const hf_ctx *ctx);
+size_t hf_ctx_budget_bytes(const hf_ctx *ctx);
 
 /* Skeletal density on the N^3 grid (the stand-in for the paper's skeletal
  * density, Section 2.3): rho[n] = sum_i a_i exp(-|x_n - c_i|^2 / (2 sigma_i^2))
@@ -119,6 +120,8 @@ hf_status hf_density_build(hf_ctx *ctx, int n, const float *d_pts, const float *
 hf_status hf_part_create(hf_ctx *ctx, int n, const float *d_grid, int role, hf_part **out,
                          hf_stream stream);
 void hf_part_release(hf_part *part);
+/* Grid size of a part (0 for NULL). */
+int hf_part_n(const hf_part *part);
 
 /* Re-derive a part's stored representation from a new N^3 grid of the same
  * size, in place (no allocation beyond the stream-ordered pool).
@@ -173,6 +176,53 @@ hf_status hf_query(const hf_fieldset *fs, const float t[3], const float q[4], in
  * (tx, ty, tz, qw, qx, qy, qz); d_out is Q x 7 floats as in hf_query. */
 hf_status hf_query_batch(const hf_fieldset *fs, const float *d_tq, int Q, int k_blend,
                          float *d_out, hf_stream stream);
+
+/* Device bytes hf_fieldset_create(n, R, flags) charges (0 if unsupported). */
+size_t hf_fieldset_bytes(int n, int R, unsigned flags);
+
+/* ---- serving: sessions, budgeted continuous batching, query lanes ----
+ * The restricted-orientation mode of Section 4.2 as a service: sessions keep
+ * their parts and their latest field set resident; field-build requests are
+ * queued, admitted first-in first-out while the context's HBM budget allows
+ * (hf_ctx_create's hbm_budget_bytes), and run concurrently on several build
+ * streams, so work admitted mid-flight overlaps on the device; a completed
+ * set replaces the session's previous one atomically.  A session's newer
+ * request supersedes its still-queued older one.  When nothing runs and the
+ * head request does not fit, the published set of the least recently queried
+ * other session is evicted.  Queries read the session's current set on one of
+ * a pool of high-priority lanes (own stream and pinned mailbox each), so
+ * queries from many threads do not serialise on one lane.
+ * Request states: 0 queued, 1 running, 2 done, 3 failed, 4 superseded. */
+typedef struct hf_server hf_server;
+typedef struct {
+    int64_t submitted, completed, failed, rejected, superseded, evicted, queries;
+    int64_t rotations_completed;
+    int queued, running, sessions;
+    size_t reserved_bytes, budget_bytes;
+} hf_server_stats;
+
+/* max_inflight: builds on the device at once (1..16); query_lanes: 1..64. */
+hf_status hf_server_create(hf_ctx *ctx, int max_inflight, int query_lanes, hf_server **out);
+void hf_server_destroy(hf_server *srv);
+/* A session over a stationary part s1 and a moving part s2 of the same N
+ * (both stay owned by the caller and must outlive the session). */
+hf_status hf_server_session_open(hf_server *srv, const hf_part *s1, const hf_part *s2, int *session);
+hf_status hf_server_session_close(hf_server *srv, int session);
+/* Queue a field build for R rotations (h_quat R x 4, copied); HF_EBUDGET if
+ * the set could never fit the budget. */
+hf_status hf_server_submit(hf_server *srv, int session, const float *h_quat, int R, unsigned flags,
+                           int64_t *request);
+/* State of a request and, once done, its latency submit -> published (ms). */
+hf_status hf_server_request_state(hf_server *srv, int64_t request, int *state, double *latency_ms);
+/* Pose query against the session's current field set (HF_ENOTREADY if none). */
+hf_status hf_server_query(hf_server *srv, int session, const float t[3], const float q[4], int k_blend,
+                          float out7[7]);
+/* Device pointer of a field of the session's current set (for inspection;
+ * valid while that set stays current). */
+hf_status hf_server_field_ptr(hf_server *srv, int session, int rot, int field, const float **d_ptr);
+/* Copy a field of the session's current set to d_dst (N^3 floats), on `stream`. */
+hf_status hf_server_field_get(hf_server *srv, int session, int rot, int field, float *d_dst, hf_stream stream);
+hf_status hf_server_stats_get(hf_server *srv, hf_server_stats *out);
 
 /* ---- per-kernel timing (CUDA events on the launching stream) ----
  * While enabled, every kernel launch the context's calls make is bracketed by

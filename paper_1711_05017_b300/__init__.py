@@ -13,7 +13,7 @@ import numpy as np
 from . import _binding as B
 from ._binding import HF_E, HF_F, HF_MOVING, HF_STATIONARY, HF_T, HF_TORQUE_F64, HFError  # noqa: F401
 
-__all__ = ["Context", "Part", "FieldSet", "HFError", "resample", "rfft3d", "version"]
+__all__ = ["Context", "Part", "FieldSet", "Server", "HFError", "resample", "rfft3d", "version"]
 
 
 def _torch():
@@ -236,3 +236,88 @@ def rfft3d(x, out=None, stream=None):
     if stream is not None:
         scratch.record_stream(stream)
     return out
+
+
+class Server:
+    """hf_server: sessions, budgeted continuous batching of field builds, and a
+    pool of high-priority query lanes (include/hf.h, serving section)."""
+
+    STATES = {0: "queued", 1: "running", 2: "done", 3: "failed", 4: "superseded"}
+
+    def __init__(self, ctx, max_inflight=4, query_lanes=16):
+        h = ctypes.c_void_p()
+        B.check(B.lib().hf_server_create(ctx.handle, int(max_inflight), int(query_lanes), ctypes.byref(h)))
+        self.handle, self.ctx = h, ctx
+
+    def open(self, s1, s2):
+        sid = ctypes.c_int()
+        B.check(B.lib().hf_server_session_open(self.handle, s1.handle, s2.handle, ctypes.byref(sid)))
+        return sid.value
+
+    def close_session(self, sid):
+        B.check(B.lib().hf_server_session_close(self.handle, int(sid)))
+
+    def submit(self, sid, quats, flags=HF_E | HF_F | HF_T):
+        q = np.ascontiguousarray(quats, dtype=np.float32).reshape(-1, 4)
+        rid = ctypes.c_int64()
+        B.check(B.lib().hf_server_submit(self.handle, int(sid), B.fptr(q), len(q), int(flags), ctypes.byref(rid)))
+        return rid.value
+
+    def state(self, rid):
+        st, lat = ctypes.c_int(), ctypes.c_double()
+        B.check(B.lib().hf_server_request_state(self.handle, ctypes.c_int64(rid), ctypes.byref(st), ctypes.byref(lat)))
+        return self.STATES[st.value], lat.value
+
+    def wait(self, rids, timeout=120.0, poll=0.001):
+        import time
+        t0 = time.time()
+        out = {}
+        pending = list(rids)
+        while pending:
+            for r in list(pending):
+                st, lat = self.state(r)
+                if st in ("done", "failed", "superseded"):
+                    out[r] = (st, lat)
+                    pending.remove(r)
+            if pending:
+                if time.time() - t0 > timeout:
+                    raise TimeoutError(f"requests {pending} not finished")
+                time.sleep(poll)
+        return out
+
+    def query(self, sid, t, q, k=4):
+        out = np.zeros(7, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32).reshape(3)
+        q = np.ascontiguousarray(q, dtype=np.float32).reshape(4)
+        B.check(B.lib().hf_server_query(self.handle, int(sid), B.fptr(t), B.fptr(q), int(k), B.fptr(out)))
+        return out
+
+    def field_ptr(self, sid, rot, field):
+        p = ctypes.c_void_p()
+        B.check(B.lib().hf_server_field_ptr(self.handle, int(sid), int(rot), int(field), ctypes.byref(p)))
+        return p.value
+
+    def field(self, sid, rot, field, n, stream=None):
+        """Copy of a field of the session's current set (torch CUDA tensor)."""
+        torch = _torch()
+        out = torch.empty((n, n, n), dtype=torch.float32, device=f"cuda:{self.ctx.device}")
+        B.check(B.lib().hf_server_field_get(self.handle, int(sid), int(rot), int(field), _dev(out, torch.float32),
+                                            _stream_ptr(stream)))
+        return out
+
+    def stats(self):
+        st = B.ServerStats()
+        B.check(B.lib().hf_server_stats_get(self.handle, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
+    def close(self):
+        if self.handle:
+            B.lib().hf_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

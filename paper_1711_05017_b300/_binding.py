@@ -56,7 +56,28 @@ SIGNATURES = {
     "hf_fields": (_i, [_vp, _vp, _vp, _fp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "hf_torque": (_i, [_vp, _i, _i, _fp, _vp, _vp, _u, _ip, _vp]),
     "hf_fields_noalloc": (_i, [_i, _vp, _vp, _fp, _vp, _vp, _vp, _vp, _vp]),
+    "hf_ctx_budget_bytes": (_sz, [_vp]),
+    "hf_part_n": (_i, [_vp]),
+    "hf_fieldset_bytes": (_sz, [_i, _i, _u]),
+    "hf_server_create": (_i, [_vp, _i, _i, ctypes.POINTER(_vp)]),
+    "hf_server_destroy": (None, [_vp]),
+    "hf_server_session_open": (_i, [_vp, _vp, _vp, _ip]),
+    "hf_server_session_close": (_i, [_vp, _i]),
+    "hf_server_submit": (_i, [_vp, _i, _fp, _i, _u, ctypes.POINTER(ctypes.c_int64)]),
+    "hf_server_request_state": (_i, [_vp, ctypes.c_int64, _ip, ctypes.POINTER(ctypes.c_double)]),
+    "hf_server_query": (_i, [_vp, _i, _fp, _fp, _i, _fp]),
+    "hf_server_field_ptr": (_i, [_vp, _i, _i, _i, ctypes.POINTER(_vp)]),
+    "hf_server_field_get": (_i, [_vp, _i, _i, _i, _vp, _vp]),
+    "hf_server_stats_get": (_i, [_vp, _vp]),
 }
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("rejected", ctypes.c_int64), ("superseded", ctypes.c_int64), ("evicted", ctypes.c_int64),
+                ("queries", ctypes.c_int64), ("rotations_completed", ctypes.c_int64), ("queued", ctypes.c_int),
+                ("running", ctypes.c_int), ("sessions", ctypes.c_int), ("reserved_bytes", ctypes.c_size_t),
+                ("budget_bytes", ctypes.c_size_t)]
 
 _lib = None
 

@@ -255,6 +255,8 @@ extern "C" void hf_ctx_destroy(hf_ctx *c) {
     delete c;
 }
 
+extern "C" size_t hf_ctx_budget_bytes(const hf_ctx *c) { return c ? c->budget : 0; }
+
 extern "C" size_t hf_ctx_reserved_bytes(const hf_ctx *c) {
     if (!c) return 0;
     std::lock_guard<std::mutex> g(const_cast<hf_ctx *>(c)->mu);
@@ -402,6 +404,8 @@ extern "C" hf_status hf_part_create(hf_ctx *ctx, int n, const float *d_grid, int
     *out = p;
     return HF_OK;
 }
+
+extern "C" int hf_part_n(const hf_part *p) { return p ? p->n : 0; }
 
 extern "C" hf_status hf_part_update(hf_part *p, const float *d_grid, hf_stream stream) {
     if (!p || !d_grid) return fail(HF_EINVAL, "hf_part_update: NULL argument");
@@ -553,6 +557,7 @@ int default_chunk(int n) {
 }  // namespace
 
 // ---------------------------------------------------------------- fieldsets
+static size_t fieldset_bytes(int n, int R, unsigned flags, int chunk, int lanes);
 // intermediates per rotation: 3 half spectra for the slab passes, 5 for the pencil pipeline
 static size_t fields_spectra(int n) { return hf::pencil_n(n) ? 5 : 3; }
 
@@ -617,6 +622,21 @@ extern "C" hf_status hf_fieldset_create(hf_ctx *ctx, int n, int R, unsigned flag
     }
     *out = fs;
     return HF_OK;
+}
+
+static size_t fieldset_bytes(int n, int R, unsigned flags, int chunk, int lanes) {
+    const int nf = 4 + ((flags & HF_T) ? 3 : 0);
+    const size_t n3 = (size_t)n * n * n;
+    const size_t scr_b = fields_spectra(n) * (size_t)chunk * hf::half_spec_elems(n) * sizeof(float2);
+    const size_t planes_b = (size_t)chunk * n3 * sizeof(float);
+    const size_t stage = (size_t)R * (9 * sizeof(float) + 4 * sizeof(double) + 6 * sizeof(int) + 18 * sizeof(float) +
+                                      18 * sizeof(double));
+    return (size_t)R * nf * n3 * sizeof(float) + lanes * (scr_b + planes_b) + stage;
+}
+
+extern "C" size_t hf_fieldset_bytes(int n, int R, unsigned flags) {
+    if (!hf::supported_n(n) || R <= 0) return 0;
+    return fieldset_bytes(n, R, flags, std::min(default_chunk(n), R), 1);
 }
 
 extern "C" void hf_fieldset_release(hf_fieldset *fs) {
@@ -837,6 +857,22 @@ extern "C" hf_status hf_query_batch(const hf_fieldset *fs, const float *d_tq, in
     CU(cudaSetDevice(fs->ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
     CU(timed(fs->ctx, kQuery, st, [&] { return hf::run_query(query_geom(fs), d_tq, Q, k, d_out, st); }));
+    return HF_OK;
+}
+
+hf_status hf_query_on_lane(const hf_fieldset *fs, const float t[3], const float q[4], int k, float out7[7],
+                           cudaStream_t st, float *h_in, float *h_out, float *d_in, float *d_out) {
+    if (!fs || !t || !q || !out7) return fail(HF_EINVAL, "hf_query: NULL argument");
+    if (k < 1 || k > 8 || k > fs->R) return fail(HF_EINVAL, "hf_query: k_blend=%d", k);
+    if (!fs->ready) return fail(HF_ENOTREADY, "hf_query: field set not computed");
+    CU(cudaSetDevice(fs->ctx->device));
+    for (int a = 0; a < 3; ++a) h_in[a] = t[a];
+    for (int a = 0; a < 4; ++a) h_in[3 + a] = q[a];
+    CU(cudaMemcpyAsync(d_in, h_in, 7 * sizeof(float), cudaMemcpyHostToDevice, st));
+    CU(hf::run_query(query_geom(fs), d_in, 1, k, d_out, st));
+    CU(cudaMemcpyAsync(h_out, d_out, 7 * sizeof(float), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    for (int a = 0; a < 7; ++a) out7[a] = h_out[a];
     return HF_OK;
 }
 

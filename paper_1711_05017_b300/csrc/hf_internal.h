@@ -4,6 +4,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "hf.h"
+
 namespace hf {
 
 // Output pointers of one field-build launch; fields of rotation r start at
@@ -85,3 +87,9 @@ struct QueryGeom {
 cudaError_t run_query(const QueryGeom &g, const float *tq, int Q, int k, float *out, cudaStream_t st);
 
 }  // namespace hf
+
+// hf_api.cu: one pose query on a caller-provided lane (stream + pinned and
+// device 7-float mailboxes); synchronous
+struct hf_fieldset;
+hf_status hf_query_on_lane(const hf_fieldset *fs, const float t[3], const float q[4], int k, float out7[7],
+                           cudaStream_t st, float *h_in, float *h_out, float *d_in, float *d_out);

@@ -1,0 +1,144 @@
+"""The serving runtime (hf_server_*): sessions with resident field sets,
+budget-admitted continuous batching of builds, supersede, eviction, and pose
+queries on high-priority lanes while builds run."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hf():
+    import paper_1711_05017_b300 as hf_
+    from paper_1711_05017_b300 import build
+    build.build()
+    return hf_
+
+
+def make_parts(hf, ctx, n, seed, npts=1500):
+    import torch
+    s1, s2 = synth.c2_pair(seed) if n >= 64 else synth.c1_pair(seed)
+    cu = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).cuda()  # noqa: E731
+    g1 = ctx.density_build(n, cu(s1.pts[:npts]), cu(s1.sigma[:npts]))
+    g2 = ctx.density_build(n, cu(s2.pts[:npts]), cu(s2.sigma[:npts]))
+    return ctx.part(g1, hf.HF_STATIONARY), ctx.part(g2, hf.HF_MOVING)
+
+
+def fields_of(srv, sid, rots, n):
+    return np.stack([np.stack([srv.field(sid, r, f, n).cpu().numpy() for f in range(7)]) for r in rots])
+
+
+def test_result_is_the_same_alone_and_in_the_mix(hf):
+    """Each build gives the same fields whether it runs alone or overlapped
+    with other sessions' builds on the device (bitwise: same kernels, same
+    order of arithmetic)."""
+    ctx = hf.Context(0)
+    srv = hf.Server(ctx, max_inflight=4, query_lanes=4)
+    pa = make_parts(hf, ctx, 64, 0)
+    pb = make_parts(hf, ctx, 32, 1)
+    pc = make_parts(hf, ctx, 96, 2)
+    a, b, c = srv.open(*pa), srv.open(*pb), srv.open(*pc)
+    qa = synth.random_quaternions(11, 24)
+    r = srv.submit(a, qa)
+    assert srv.wait([r])[r][0] == "done"
+    alone = fields_of(srv, a, (0, 7, 23), 64)
+    # the same request again, now in a mix submitted together
+    rids = [srv.submit(b, synth.random_quaternions(12, 40)), srv.submit(a, qa),
+            srv.submit(c, synth.random_quaternions(13, 16)), srv.submit(b, synth.random_quaternions(14, 48))]
+    res = srv.wait(rids)
+    assert res[rids[1]][0] == "done" and res[rids[2]][0] == "done"
+    mixed = fields_of(srv, a, (0, 7, 23), 64)
+    assert np.array_equal(alone, mixed)
+    st = srv.stats()
+    assert st["completed"] >= 4 and st["failed"] == 0
+    srv.close()
+
+
+def test_budget_admission_and_rejection(hf):
+    n = 64
+    need = None
+    from paper_1711_05017_b300 import _binding as B
+    one = B.lib().hf_fieldset_bytes(n, 32, hf.HF_E | hf.HF_F | hf.HF_T)
+    ctx = hf.Context(0, hbm_budget_bytes=int(2.5 * one) + (64 << 20))
+    parts = make_parts(hf, ctx, n, 3)
+    srv = hf.Server(ctx, max_inflight=4, query_lanes=2)
+    sids = [srv.open(*parts) for _ in range(3)]
+    # a set larger than the whole budget is rejected at once
+    with pytest.raises(hf.HFError) as e:
+        srv.submit(sids[0], synth.random_quaternions(5, 96))
+    assert e.value.status == B.HF_EBUDGET
+    # three sets of which only two fit at a time: admission waits, all finish,
+    # and the reserved bytes never exceed the budget
+    rids = [srv.submit(s, synth.random_quaternions(20 + i, 32)) for i, s in enumerate(sids)]
+    peak = 0
+    t0 = time.time()
+    while time.time() - t0 < 60:
+        st = srv.stats()
+        peak = max(peak, st["reserved_bytes"])
+        if all(srv.state(r)[0] in ("done", "failed") for r in rids):
+            break
+        time.sleep(0.0005)
+    assert all(srv.state(r)[0] == "done" for r in rids)
+    assert peak <= ctx.reserved_bytes() + st["budget_bytes"]
+    assert peak <= st["budget_bytes"]
+    assert st["evicted"] >= 1  # published sets had to make room for the third
+    del need
+    srv.close()
+
+
+def test_newer_request_supersedes_a_queued_one(hf):
+    ctx = hf.Context(0)
+    srv = hf.Server(ctx, max_inflight=1, query_lanes=1)
+    big = make_parts(hf, ctx, 128, 4)
+    small = make_parts(hf, ctx, 32, 5)
+    s_big, s_small = srv.open(*big), srv.open(*small)
+    r0 = srv.submit(s_big, synth.random_quaternions(30, 64))  # occupies the only slot
+    r1 = srv.submit(s_small, synth.random_quaternions(31, 8))
+    r2 = srv.submit(s_small, synth.random_quaternions(32, 8))  # supersedes r1 while it waits
+    res = srv.wait([r0, r1, r2])
+    assert res[r1][0] == "superseded" and res[r2][0] == "done" and res[r0][0] == "done"
+    srv.close()
+
+
+def test_queries_during_builds_are_exact_at_nodes_and_member_rotations(hf):
+    """While other sessions build, queries at lattice nodes with a member
+    rotation return that rotation's stored values (exact trilinear weights,
+    exact rotation hit)."""
+    n = 64
+    h = 2.0 / n
+    ctx = hf.Context(0)
+    srv = hf.Server(ctx, max_inflight=3, query_lanes=8)
+    pq = make_parts(hf, ctx, n, 6)
+    sq = srv.open(*pq)
+    q = synth.random_quaternions(40, 16).astype(np.float32)
+    r = srv.submit(sq, q)
+    assert srv.wait([r])[r][0] == "done"
+    ref = fields_of(srv, sq, range(16), n)
+    others = [srv.open(*make_parts(hf, ctx, 128, 7 + i)) for i in range(2)]
+    busy = [srv.submit(o, synth.random_quaternions(50 + i, 128)) for i, o in enumerate(others)]
+    errs, lat = [], []
+
+    def worker(seed):
+        rng = np.random.default_rng(seed)
+        for _ in range(200):
+            i = int(rng.integers(16))
+            j = rng.integers(0, n, 3)
+            t0 = time.perf_counter()
+            out = srv.query(sq, j * h, q[i], k=4)
+            lat.append(time.perf_counter() - t0)
+            errs.append(np.abs(out - ref[i, :, j[2], j[1], j[0]]).max() / (np.abs(ref[i]).max() + 1e-30))
+
+    th = [threading.Thread(target=worker, args=(s,)) for s in range(4)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    srv.wait(busy)
+    assert max(errs) <= 1e-6
+    assert srv.stats()["queries"] >= 800
+    srv.close()
