@@ -304,6 +304,12 @@ def run_ours(args, rank, world, local_rank):
         cpu = {"value": round(1.0 / t_rot, 4), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": desc, "splat_s": round(t_splat, 2)}
 
+    serving = None
+    if rank == 0 and world == 1 and args.serve_seconds > 0:
+        del fs
+        torch.cuda.empty_cache()
+        serving = run_serving(args, local_rank)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -324,8 +330,95 @@ def run_ours(args, rank, world, local_rank):
             "plain_path": plain,
             "cpu_baseline": cpu,
             "clocks": clk.summary(),
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------- serving workload
+SERVE_RCAP = {64: 512, 128: 96, 256: 12}  # rotations per build, capped so that every session's set plus the builds in flight fit 120 GB
+
+
+def run_serving(args, local_rank):
+    """16 sessions (N from {64, 128, 256}), Poisson field-build requests
+    (2/s per session, 64-512 rotations, capped per N), HBM budget 120 GB,
+    a 1 kHz pose-query random walk per session.  Returns the summary dict."""
+    import torch
+    import paper_1711_05017_b300 as hf
+    dev = torch.device("cuda", local_rank)
+    sess = synth.c5_sessions(0, n_sessions=16, duration_s=args.serve_seconds)
+    ctx = hf.Context(local_rank, hbm_budget_bytes=120 * (1 << 30))
+    srv = hf.Server(ctx, max_inflight=4, query_lanes=16)
+    sids, parts = [], []
+    for s in sess:
+        cu = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=dev)  # noqa: E731
+        g1 = ctx.density_build(s.n, cu(s.s1.pts), cu(s.s1.sigma))
+        g2 = ctx.density_build(s.n, cu(s.s2.pts), cu(s.s2.sigma))
+        p = (ctx.part(g1, hf.HF_STATIONARY), ctx.part(g2, hf.HF_MOVING))
+        parts.append(p)
+        sids.append(srv.open(*p))
+    torch.cuda.synchronize()
+    flags = hf.HF_E | hf.HF_F | hf.HF_T
+    # warm-up: one build per session so that every session can answer queries
+    first = [srv.submit(sid, synth.random_quaternions(900 + i, min(64, SERVE_RCAP[s.n])), flags)
+             for i, (sid, s) in enumerate(zip(sids, sess))]
+    srv.wait(first, timeout=600)
+    st0 = srv.stats()
+    # arrivals merged over sessions
+    events = sorted((t, i, int(min(r, SERVE_RCAP[sess[i].n])), int(qs))
+                    for i, s in enumerate(sess) for t, r, qs in zip(s.arrivals, s.n_rot, s.quat_seeds))
+    steps = int(args.serve_seconds * 1000)
+    poses = np.stack([np.concatenate([synth.translation_walk(3000 + i, steps),
+                                      synth.quaternion_walk(4000 + i, steps)], axis=1)
+                      for i in range(len(sids))])
+    drive = {}
+
+    def driver():  # native threads, one per session, 1 kHz each (the call releases the GIL)
+        drive["res"] = srv.drive_queries(sids, poses, rate_hz=1000.0, k=4)
+
+    th = [threading.Thread(target=driver, daemon=True)]
+    srv.query_latencies()  # drop the warm-up's
+    t_start = time.perf_counter()
+    for t in th:
+        t.start()
+    rids = []
+    for t_ev, i, R, qs in events:
+        wait = t_start + t_ev - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        try:
+            rids.append(srv.submit(sids[i], synth.random_quaternions(qs, R), flags))
+        except hf.HFError:
+            pass
+    for t in th:
+        t.join()
+    elapsed = time.perf_counter() - t_start
+    st1 = srv.stats()
+    lib_lat = srv.query_latencies()
+    res = srv.wait(rids, timeout=900)
+    build_lat = [v[1] for v in res.values() if v[0] == "done"]
+    st2 = srv.stats()
+    answered, not_ready, late = drive["res"]
+    lat = lib_lat if lib_lat.size else np.array([np.nan])
+    out = {
+        "sessions": len(sids), "grid_sizes": sorted(set(s.n for s in sess)), "seconds": round(elapsed, 2),
+        "budget_gb": 120, "query_us": {"p50": round(float(np.percentile(lat, 50)), 1),
+                                       "p99": round(float(np.percentile(lat, 99)), 1),
+                                       "max": round(float(np.max(lat)), 1), "n": int(lat.size),
+                                       "answered": int(answered), "not_ready": int(not_ready),
+                                       "started_late": int(late), "rate_hz_per_session": 1000,
+                                       "budget_us": 1000, "measured": "inside hf_server_query (entry to return)"},
+        "builds": {"submitted": int(st2["submitted"] - st0["submitted"]), "completed": len(build_lat),
+                   "superseded": int(st2["superseded"] - st0["superseded"]),
+                   "rejected": int(st2["rejected"] - st0["rejected"]), "evicted": int(st2["evicted"] - st0["evicted"]),
+                   "latency_ms_p50": round(float(np.percentile(build_lat, 50)), 1) if build_lat else None,
+                   "latency_ms_p99": round(float(np.percentile(build_lat, 99)), 1) if build_lat else None},
+        "fields_per_s": round((st1["rotations_completed"] - st0["rotations_completed"]) / elapsed, 1),
+        "rotation_cap_per_build": SERVE_RCAP,
+    }
+    srv.close()
+    del parts
+    return out
 
 
 # ------------------------------------------------------- reference arm
@@ -367,6 +460,8 @@ def main():
     ap.add_argument("--rotations", type=int, default=N_ROT)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=20.0,
+                    help="length of the 16-session serving run (0 = skip)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

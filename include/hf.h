@@ -32,8 +32,9 @@
  *
  * Memory: pointers named d_* are device pointers owned by the caller (the
  * library never frees them); h_* are host pointers.  Handles (hf_ctx,
- * hf_part, hf_fieldset) are owned by the library, allocated on the context's
- * device and charged against the context's HBM budget.
+ * hf_part, hf_fieldset, hf_server) are owned by the library, allocated on
+ * the context's device and charged against the context's HBM budget; a
+ * context must outlive every handle made from it.
  *
  * Streams: every call taking an hf_stream enqueues asynchronous work on it
  * (NULL = the legacy default stream).  Outputs are valid after the stream is
@@ -223,6 +224,19 @@ hf_status hf_server_field_ptr(hf_server *srv, int session, int rot, int field, c
 /* Copy a field of the session's current set to d_dst (N^3 floats), on `stream`. */
 hf_status hf_server_field_get(hf_server *srv, int session, int rot, int field, float *d_dst, hf_stream stream);
 hf_status hf_server_stats_get(hf_server *srv, hf_server_stats *out);
+/* Latencies (microseconds, call entry to return) of the queries answered since
+ * the last call, oldest first, at most `max` of them (the newest 2^20 are
+ * kept); returns how many were written. */
+int hf_server_query_latencies(hf_server *srv, float *h_out_us, int max);
+/* Replay pose trajectories against sessions from native threads, one per
+ * session, one query every 1/rate_hz seconds (a haptic device's servo loop):
+ * h_poses is nsess x steps x 7 (t, q); blocks until every trajectory has run.
+ * Latencies go to the latency ring; *answered / *not_ready / *late count the
+ * queries answered, refused for want of a field set, and started more than one
+ * period late.  Errors: HF_EINVAL. */
+hf_status hf_server_drive_queries(hf_server *srv, int nsess, const int *sessions, const float *h_poses, int steps,
+                                  double rate_hz, int k_blend, int64_t *answered, int64_t *not_ready,
+                                  int64_t *late);
 
 /* ---- per-kernel timing (CUDA events on the launching stream) ----
  * While enabled, every kernel launch the context's calls make is bracketed by

@@ -248,14 +248,17 @@ class Server:
         h = ctypes.c_void_p()
         B.check(B.lib().hf_server_create(ctx.handle, int(max_inflight), int(query_lanes), ctypes.byref(h)))
         self.handle, self.ctx = h, ctx
+        self._parts = {}  # the parts must outlive their sessions: keep them here
 
     def open(self, s1, s2):
         sid = ctypes.c_int()
         B.check(B.lib().hf_server_session_open(self.handle, s1.handle, s2.handle, ctypes.byref(sid)))
+        self._parts[sid.value] = (s1, s2)
         return sid.value
 
     def close_session(self, sid):
         B.check(B.lib().hf_server_session_close(self.handle, int(sid)))
+        self._parts.pop(int(sid), None)
 
     def submit(self, sid, quats, flags=HF_E | HF_F | HF_T):
         q = np.ascontiguousarray(quats, dtype=np.float32).reshape(-1, 4)
@@ -304,6 +307,23 @@ class Server:
         B.check(B.lib().hf_server_field_get(self.handle, int(sid), int(rot), int(field), _dev(out, torch.float32),
                                             _stream_ptr(stream)))
         return out
+
+    def drive_queries(self, sids, poses, rate_hz=1000.0, k=4):
+        """Replay poses (nsess, steps, 7) at rate_hz from native threads, one per
+        session; blocks.  Returns (answered, not_ready, late)."""
+        poses = np.ascontiguousarray(poses, dtype=np.float32)
+        s = np.ascontiguousarray(sids, dtype=np.int32)
+        a, nr, lt = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        B.check(B.lib().hf_server_drive_queries(self.handle, len(s), s.ctypes.data_as(B._ip), B.fptr(poses),
+                                                poses.shape[1], float(rate_hz), int(k), ctypes.byref(a),
+                                                ctypes.byref(nr), ctypes.byref(lt)))
+        return a.value, nr.value, lt.value
+
+    def query_latencies(self, max_n=1 << 20):
+        """Query latencies (us, measured inside the library) since the last read."""
+        buf = np.empty(max_n, dtype=np.float32)
+        n = B.lib().hf_server_query_latencies(self.handle, B.fptr(buf), int(max_n))
+        return buf[:n].copy()
 
     def stats(self):
         st = B.ServerStats()

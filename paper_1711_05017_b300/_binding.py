@@ -69,6 +69,9 @@ SIGNATURES = {
     "hf_server_field_ptr": (_i, [_vp, _i, _i, _i, ctypes.POINTER(_vp)]),
     "hf_server_field_get": (_i, [_vp, _i, _i, _i, _vp, _vp]),
     "hf_server_stats_get": (_i, [_vp, _vp]),
+    "hf_server_query_latencies": (_i, [_vp, _fp, _i]),
+    "hf_server_drive_queries": (_i, [_vp, _i, _ip, _fp, _i, ctypes.c_double, _i, ctypes.POINTER(ctypes.c_int64),
+                                     ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
 }
 
 

@@ -59,8 +59,8 @@ struct hf_ctx {
     size_t budget = 0, reserved = 0;
     std::mutex mu;
     cudaStream_t qstream = nullptr;             // high-priority stream for hf_query
-    float *h_qin = nullptr, *h_qout = nullptr;  // pinned 7-float mailboxes
-    float *d_qin = nullptr, *d_qout = nullptr;
+    float *h_qout = nullptr;  // mapped pinned 7-float answer mailbox
+    float *d_qout = nullptr;  // its device alias
     std::mutex qmu;
     // per-kernel timing
     bool prof = false;
@@ -76,7 +76,7 @@ struct hf_ctx {
 };
 
 struct hf_part {
-    hf_ctx *ctx;
+    hf_ctx *ctx;  // must outlive the part
     int n, role;
     float *grid;   // HF_MOVING: N^3
     float2 *spec;  // HF_STATIONARY: (h^3/N^3) rho1^ in [ky*][kz*][kx*] slot order
@@ -112,7 +112,9 @@ struct hf_fieldset {
     int lanes = 1;  // pipelines used by compute (HF_LANES=2 alternates chunks over two)
     bool ready = false;
     size_t bytes = 0;
-    void *h_stage = nullptr;     // pinned staging for the per-call uploads
+    cudaStream_t mem_stream = nullptr;  // non-null: stream-ordered device memory, pageable staging
+    std::vector<char> pageable_stage;
+    void *h_stage = nullptr;     // staging for the per-call uploads (pinned unless mem_stream)
     size_t stage_bytes = 0;
     cudaEvent_t stage_done = nullptr;  // the last uploads from h_stage have been consumed
 };
@@ -140,8 +142,11 @@ static cudaEvent_t prof_event(hf_ctx *c) {
 }
 
 // Launch `fn` on `st`, bracketed by timing events when the context profiles.
+// A launch is checked with cudaGetLastError, so a stale non-sticky error left
+// in this thread by an earlier unrelated call is cleared first.
 template <class F>
 static cudaError_t timed(hf_ctx *c, int kind, cudaStream_t st, F &&fn) {
+    (void)cudaGetLastError();
     if (!c || !c->prof) return fn();
     std::lock_guard<std::mutex> g(c->pmu);
     cudaEvent_t a = prof_event(c), b = prof_event(c);
@@ -228,10 +233,8 @@ extern "C" hf_status hf_ctx_create(int device, size_t budget, hf_ctx **out) {
     int lo = 0, hi = 0;
     cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->qstream, cudaStreamNonBlocking, hi);
-    if (e == cudaSuccess) e = cudaMallocHost(&c->h_qin, 8 * sizeof(float));
-    if (e == cudaSuccess) e = cudaMallocHost(&c->h_qout, 8 * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_qin, 8 * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_qout, 8 * sizeof(float));
+    if (e == cudaSuccess) e = cudaHostAlloc(&c->h_qout, 8 * sizeof(float), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&c->d_qout, c->h_qout, 0);
     for (int n : {32, 64, 96, 128, 256})
         if (e == cudaSuccess) e = hf::fft_init_attrs(n);
     if (e != cudaSuccess) {
@@ -246,10 +249,7 @@ extern "C" void hf_ctx_destroy(hf_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->qstream) cudaStreamDestroy(c->qstream);
-    if (c->h_qin) cudaFreeHost(c->h_qin);
     if (c->h_qout) cudaFreeHost(c->h_qout);
-    if (c->d_qin) cudaFree(c->d_qin);
-    if (c->d_qout) cudaFree(c->d_qout);
     hf_profile_read(c);
     for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
     delete c;
@@ -561,7 +561,20 @@ static size_t fieldset_bytes(int n, int R, unsigned flags, int chunk, int lanes)
 // intermediates per rotation: 3 half spectra for the slab passes, 5 for the pencil pipeline
 static size_t fields_spectra(int n) { return hf::pencil_n(n) ? 5 : 3; }
 
+static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags, cudaStream_t mem_stream,
+                                      hf_fieldset **out);
+
 extern "C" hf_status hf_fieldset_create(hf_ctx *ctx, int n, int R, unsigned flags, hf_fieldset **out) {
+    return fieldset_create_impl(ctx, n, R, flags, nullptr, out);
+}
+
+hf_status hf_fieldset_create_stream_ordered(hf_ctx *ctx, int n, int R, unsigned flags, cudaStream_t st,
+                                            hf_fieldset **out) {
+    return fieldset_create_impl(ctx, n, R, flags, st, out);
+}
+
+static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags, cudaStream_t mem_stream,
+                                      hf_fieldset **out) {
     if (!ctx || !out) return fail(HF_EINVAL, "hf_fieldset_create: NULL argument");
     *out = nullptr;
     if (!hf::supported_n(n)) return fail(HF_EUNSUPPORTED, "hf_fieldset_create: N=%d not supported", n);
@@ -600,20 +613,31 @@ extern "C" hf_status hf_fieldset_create(hf_ctx *ctx, int n, int R, unsigned flag
         delete fs;
         return fail(HF_EBUDGET, "hf_fieldset_create: %zu bytes exceed the budget", b);
     }
-    cudaError_t e = cudaMalloc(&fs->data, data_b);
+    fs->mem_stream = mem_stream;
+    auto dalloc = [&](void **p, size_t b) {
+        return mem_stream ? cudaMallocAsync(p, b, mem_stream) : cudaMalloc(p, b);
+    };
+    cudaError_t e = dalloc((void **)&fs->data, data_b);
     for (int l = 0; l < 2; ++l) {
-        if (e == cudaSuccess && l < fs->lanes) e = cudaMalloc(&fs->scratch[l], scr_b);
-        if (e == cudaSuccess && l < fs->lanes) e = cudaMalloc(&fs->planes[l], planes_b);
+        if (e == cudaSuccess && l < fs->lanes) e = dalloc((void **)&fs->scratch[l], scr_b);
+        if (e == cudaSuccess && l < fs->lanes) e = dalloc((void **)&fs->planes[l], planes_b);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&fs->lane[l], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fs->join[l], cudaEventDisableTiming);
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fs->fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMalloc(&fs->d_rot9, (size_t)R * 9 * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&fs->d_quat, (size_t)R * 4 * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&fs->d_nbr, (size_t)R * 6 * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&fs->d_P, (size_t)R * 18 * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&fs->d_P64, (size_t)R * 18 * sizeof(double));
-    if (e == cudaSuccess) e = cudaMallocHost(&fs->h_stage, fs->stage_bytes);
+    if (e == cudaSuccess) e = dalloc((void **)&fs->d_rot9, (size_t)R * 9 * sizeof(float));
+    if (e == cudaSuccess) e = dalloc((void **)&fs->d_quat, (size_t)R * 4 * sizeof(double));
+    if (e == cudaSuccess) e = dalloc((void **)&fs->d_nbr, (size_t)R * 6 * sizeof(int));
+    if (e == cudaSuccess) e = dalloc((void **)&fs->d_P, (size_t)R * 18 * sizeof(float));
+    if (e == cudaSuccess) e = dalloc((void **)&fs->d_P64, (size_t)R * 18 * sizeof(double));
+    if (e == cudaSuccess) {
+        if (mem_stream) {
+            fs->pageable_stage.resize(fs->stage_bytes + 64);
+            fs->h_stage = fs->pageable_stage.data();
+        } else {
+            e = cudaMallocHost(&fs->h_stage, fs->stage_bytes);
+        }
+    }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fs->stage_done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         hf_fieldset_release(fs);
@@ -639,27 +663,37 @@ extern "C" size_t hf_fieldset_bytes(int n, int R, unsigned flags) {
     return fieldset_bytes(n, R, flags, std::min(default_chunk(n), R), 1);
 }
 
+// For stream-ordered sets the caller guarantees no work still uses the set;
+// the frees are then ordered on the set's memory stream without a device-wide
+// synchronisation.
 extern "C" void hf_fieldset_release(hf_fieldset *fs) {
     if (!fs) return;
     cudaSetDevice(fs->ctx->device);
-    cudaFree(fs->data);
+    auto dfree = [&](void *p) {
+        if (!p) return;
+        if (fs->mem_stream) cudaFreeAsync(p, fs->mem_stream);
+        else cudaFree(p);
+    };
+    dfree(fs->data);
     for (int l = 0; l < 2; ++l) {
-        cudaFree(fs->scratch[l]);
-        cudaFree(fs->planes[l]);
+        dfree(fs->scratch[l]);
+        dfree(fs->planes[l]);
         if (fs->lane[l]) cudaStreamDestroy(fs->lane[l]);
         if (fs->join[l]) cudaEventDestroy(fs->join[l]);
     }
     if (fs->fork) cudaEventDestroy(fs->fork);
-    cudaFree(fs->d_rot9);
-    cudaFree(fs->d_quat);
-    cudaFree(fs->d_nbr);
-    cudaFree(fs->d_P);
-    cudaFree(fs->d_P64);
-    if (fs->h_stage) cudaFreeHost(fs->h_stage);
+    dfree(fs->d_rot9);
+    dfree(fs->d_quat);
+    dfree(fs->d_nbr);
+    dfree(fs->d_P);
+    dfree(fs->d_P64);
+    if (fs->h_stage && !fs->mem_stream) cudaFreeHost(fs->h_stage);
     if (fs->stage_done) cudaEventDestroy(fs->stage_done);
     uncharge(fs->ctx, fs->bytes);
     delete fs;
 }
+
+bool hf_fieldset_is_ready(const hf_fieldset *fs) { return fs && fs->ready; }
 
 extern "C" int hf_fieldset_n(const hf_fieldset *fs) { return fs ? fs->n : 0; }
 extern "C" int hf_fieldset_rotations(const hf_fieldset *fs) { return fs ? fs->R : 0; }
@@ -860,43 +894,37 @@ extern "C" hf_status hf_query_batch(const hf_fieldset *fs, const float *d_tq, in
     return HF_OK;
 }
 
+// One pose query: the pose travels as a kernel argument and the kernel
+// writes its 7 results straight into mapped pinned host memory (h_out, whose
+// device alias is d_out), so a query is one launch and one synchronise.
 hf_status hf_query_on_lane(const hf_fieldset *fs, const float t[3], const float q[4], int k, float out7[7],
-                           cudaStream_t st, float *h_in, float *h_out, float *d_in, float *d_out) {
+                           cudaStream_t st, float *h_out, float *d_out) {
     if (!fs || !t || !q || !out7) return fail(HF_EINVAL, "hf_query: NULL argument");
     if (k < 1 || k > 8 || k > fs->R) return fail(HF_EINVAL, "hf_query: k_blend=%d", k);
     if (!fs->ready) return fail(HF_ENOTREADY, "hf_query: field set not computed");
-    CU(cudaSetDevice(fs->ctx->device));
-    for (int a = 0; a < 3; ++a) h_in[a] = t[a];
-    for (int a = 0; a < 4; ++a) h_in[3 + a] = q[a];
-    CU(cudaMemcpyAsync(d_in, h_in, 7 * sizeof(float), cudaMemcpyHostToDevice, st));
-    CU(hf::run_query(query_geom(fs), d_in, 1, k, d_out, st));
-    CU(cudaMemcpyAsync(h_out, d_out, 7 * sizeof(float), cudaMemcpyDeviceToHost, st));
+    (void)cudaGetLastError();  // drop a stale non-sticky error before checking the launch
+    hf::Pose7 pose;
+    for (int a = 0; a < 3; ++a) pose.v[a] = t[a];
+    for (int a = 0; a < 4; ++a) pose.v[3 + a] = q[a];
+    CU(hf::run_query_one(query_geom(fs), pose, k, d_out, st));
     CU(cudaStreamSynchronize(st));
-    for (int a = 0; a < 7; ++a) out7[a] = h_out[a];
+    for (int a = 0; a < 7; ++a) out7[a] = ((volatile float *)h_out)[a];
     return HF_OK;
 }
 
 extern "C" hf_status hf_query(const hf_fieldset *fs, const float t[3], const float q[4], int k, float out7[7]) {
-    if (!fs || !t || !q || !out7) return fail(HF_EINVAL, "hf_query: NULL argument");
-    if (k < 1 || k > 8 || k > fs->R) return fail(HF_EINVAL, "hf_query: k_blend=%d", k);
-    if (!fs->ready) return fail(HF_ENOTREADY, "hf_query: field set not computed");
+    if (!fs) return fail(HF_EINVAL, "hf_query: NULL field set");
     hf_ctx *c = fs->ctx;
     std::lock_guard<std::mutex> g(c->qmu);
     CU(cudaSetDevice(c->device));
-    for (int a = 0; a < 3; ++a) c->h_qin[a] = t[a];
-    for (int a = 0; a < 4; ++a) c->h_qin[3 + a] = q[a];
-    CU(cudaMemcpyAsync(c->d_qin, c->h_qin, 7 * sizeof(float), cudaMemcpyHostToDevice, c->qstream));
-    CU(hf::run_query(query_geom(fs), c->d_qin, 1, k, c->d_qout, c->qstream));
-    CU(cudaMemcpyAsync(c->h_qout, c->d_qout, 7 * sizeof(float), cudaMemcpyDeviceToHost, c->qstream));
-    CU(cudaStreamSynchronize(c->qstream));
-    for (int a = 0; a < 7; ++a) out7[a] = c->h_qout[a];
-    return HF_OK;
+    return hf_query_on_lane(fs, t, q, k, out7, c->qstream, c->h_qout, c->d_qout);
 }
 
 // ----------------------------------------------------- single-step entries
 extern "C" hf_status hf_resample(int n, const float *d_rho, const float h_R[9], float *d_out, hf_stream stream) {
     if (!hf::supported_n(n)) return fail(HF_EUNSUPPORTED, "hf_resample: N=%d not supported", n);
     if (!d_rho || !h_R || !d_out) return fail(HF_EINVAL, "hf_resample: NULL argument");
+    (void)cudaGetLastError();
     hf::Rot9 r;
     for (int k = 0; k < 9; ++k) r.r[k] = h_R[k];
     CU(hf::run_resample(n, d_rho, r, d_out, (cudaStream_t)stream));
@@ -914,6 +942,7 @@ extern "C" hf_status hf_rfft3d(int n, const float *d_in, float *d_out, void *d_s
     if ((uintptr_t)d_scratch % 16) return fail(HF_EINVAL, "hf_rfft3d: scratch must be 16-byte aligned");
     if ((uintptr_t)d_in % 8) return fail(HF_EINVAL, "hf_rfft3d: d_in must be 8-byte aligned");
     CU(ensure_kernel_attrs());
+    (void)cudaGetLastError();
     cudaStream_t st = (cudaStream_t)stream;
     const size_t he = hf::half_spec_elems(n);
     float2 *X1 = (float2 *)d_scratch, *spec = X1 + he;

@@ -85,11 +85,22 @@ struct QueryGeom {
     const double *quats;  // R x 4, normalised, on device
 };
 cudaError_t run_query(const QueryGeom &g, const float *tq, int Q, int k, float *out, cudaStream_t st);
+struct Pose7 {
+    float v[7];  // tx, ty, tz, qw, qx, qy, qz
+};
+// one query, pose by value, 7 results to `out` (device or mapped host memory)
+cudaError_t run_query_one(const QueryGeom &g, Pose7 pose, int k, float *out, cudaStream_t st);
 
 }  // namespace hf
 
-// hf_api.cu: one pose query on a caller-provided lane (stream + pinned and
-// device 7-float mailboxes); synchronous
+// hf_api.cu: one pose query on a caller-provided lane (a stream and a mapped
+// pinned 7-float answer mailbox with its device alias); synchronous
 struct hf_fieldset;
+// whether the set's last compute enqueued all of its work
+bool hf_fieldset_is_ready(const hf_fieldset *fs);
+// a field set whose device memory is allocated and freed in stream order on
+// `st` (no device-wide synchronisation on create or release)
+hf_status hf_fieldset_create_stream_ordered(hf_ctx *ctx, int n, int R, unsigned flags, cudaStream_t st,
+                                            hf_fieldset **out);
 hf_status hf_query_on_lane(const hf_fieldset *fs, const float t[3], const float q[4], int k, float out7[7],
-                           cudaStream_t st, float *h_in, float *h_out, float *d_in, float *d_out);
+                           cudaStream_t st, float *h_out, float *d_out);

@@ -186,13 +186,11 @@ __device__ __forceinline__ bool better(double da, int ia, double db, int ib) {
     return da > db || (da == db && ia < ib);
 }
 
+// One query by one warp: `in` = (t, q), 7 results to `outp`.
 template <int N>
-__global__ void query_kernel(QueryGeom g, const float *__restrict__ tq, int Q, int k, float *__restrict__ out) {
-    __shared__ float part[kQueryWarps][7 * kQueryMaxK];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int qi = blockIdx.x * kQueryWarps + warp;
-    if (qi >= Q) return;  // warp-uniform
-    const float *in = tq + 7 * (size_t)qi;
+__device__ __forceinline__ void query_warp(const QueryGeom &g, const float *in, int k, float *outp,
+                                           float *part) {
+    const int lane = threadIdx.x & 31;
     double q[4] = {in[3], in[4], in[5], in[6]};
     const double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
 #pragma unroll
@@ -270,14 +268,31 @@ __global__ void query_kernel(QueryGeom g, const float *__restrict__ tq, int Q, i
             const float c0 = fmaf(ay, c01 - c00, c00), c1 = fmaf(ay, c11 - c10, c10);
             v = fmaf(az, c1 - c0, c0);
         }
-        part[warp][pidx] = v * (float)w[s];
+        part[pidx] = v * (float)w[s];
     }
     __syncwarp();
     if (lane < 7) {
         float acc = 0.f;
-        for (int s = 0; s < used; ++s) acc += part[warp][7 * s + lane];
-        out[7 * (size_t)qi + lane] = acc;
+        for (int s = 0; s < used; ++s) acc += part[7 * s + lane];
+        outp[lane] = acc;
     }
+}
+
+template <int N>
+__global__ void query_kernel(QueryGeom g, const float *__restrict__ tq, int Q, int k, float *__restrict__ out) {
+    __shared__ float part[kQueryWarps][7 * kQueryMaxK];
+    const int warp = threadIdx.x >> 5;
+    const int qi = blockIdx.x * kQueryWarps + warp;
+    if (qi >= Q) return;  // warp-uniform
+    query_warp<N>(g, tq + 7 * (size_t)qi, k, out + 7 * (size_t)qi, part[warp]);
+}
+
+// a single query whose pose travels as a kernel argument; `out` may be mapped
+// host memory, so the answer needs no copy back
+template <int N>
+__global__ void query_one_kernel(QueryGeom g, Pose7 pose, int k, float *out) {
+    __shared__ float part[7 * kQueryMaxK];
+    query_warp<N>(g, pose.v, k, out, part);
 }
 
 // ------------------------------------------------------------- launchers
@@ -313,6 +328,11 @@ cudaError_t run_torque(int n, int R, const float *E, size_t e_rot_stride, float 
         torque_kernel<true><<<(unsigned)blocks, kTorqueThreads, 0, st>>>(E, e_rot_stride, T, t_rot_stride, nbr, P, P64, R, n3);
     else
         torque_kernel<false><<<(unsigned)blocks, kTorqueThreads, 0, st>>>(E, e_rot_stride, T, t_rot_stride, nbr, P, P64, R, n3);
+    return cudaGetLastError();
+}
+
+cudaError_t run_query_one(const QueryGeom &g, Pose7 pose, int k, float *out, cudaStream_t st) {
+    HF_DISPATCH_K(g.n, (query_one_kernel<NN><<<1, 32, 0, st>>>(g, pose, k, out)));
     return cudaGetLastError();
 }
 

@@ -128,6 +128,7 @@ extern "C" hf_status hf_fields_noalloc(int n, const float *d_rho1, const float *
     hf::FieldPtrs out{d_E, d_Fx, d_Fy, d_Fz, 0};
 
     cudaError_t e;
+    (void)cudaGetLastError();  // drop a stale non-sticky error before checking the launches
     write_rotations<<<1, 32, 0, st>>>(ident, rot, rot9);
     if ((e = cudaGetLastError()) != cudaSuccess ||
         (e = hf::run_passA(n, d_rho1, rot9, X1, 1, st)) != cudaSuccess ||

@@ -25,6 +25,7 @@
 #include <memory>
 #include <mutex>
 #include <thread>
+#include <string>
 #include <unordered_map>
 #include <vector>
 
@@ -50,10 +51,28 @@ hf_status srv_fail(hf_status s, const char *fmt, ...) {
 
 enum { RQ_QUEUED = 0, RQ_RUNNING = 1, RQ_DONE = 2, RQ_FAILED = 3, RQ_SUPERSEDED = 4 };
 
-struct SetHolder {  // a published field set; freed when the last reader lets go
+// Retired field sets wait here until the scheduler frees them, so that no
+// query thread and no holder of the server mutex ever runs a free.
+struct Graveyard {
+    std::mutex mu;
+    std::vector<hf_fieldset *> sets;
+    void put(hf_fieldset *fs) {
+        std::lock_guard<std::mutex> g(mu);
+        sets.push_back(fs);
+    }
+    std::vector<hf_fieldset *> take() {
+        std::lock_guard<std::mutex> g(mu);
+        std::vector<hf_fieldset *> out;
+        out.swap(sets);
+        return out;
+    }
+};
+
+struct SetHolder {  // a published field set; retired when the last reader lets go
     hf_fieldset *fs;
-    explicit SetHolder(hf_fieldset *f) : fs(f) {}
-    ~SetHolder() { hf_fieldset_release(fs); }
+    Graveyard *gy;
+    SetHolder(hf_fieldset *f, Graveyard *g) : fs(f), gy(g) {}
+    ~SetHolder() { gy->put(fs); }
 };
 
 struct Request {
@@ -67,6 +86,7 @@ struct Request {
     hf_fieldset *fs = nullptr;
     cudaEvent_t done = nullptr;
     int stream = -1;
+    std::string error;  // why it failed
 };
 
 struct Session {
@@ -79,7 +99,7 @@ struct Session {
 
 struct Lane {
     cudaStream_t st = nullptr;
-    float *h_in = nullptr, *h_out = nullptr, *d_in = nullptr, *d_out = nullptr;
+    float *h_out = nullptr, *d_out = nullptr;  // mapped pinned answer mailbox and its device alias
 };
 
 }  // namespace
@@ -100,6 +120,10 @@ struct hf_server {
     bool stop = false;
     std::thread sched;
     hf_server_stats stats = {};
+    Graveyard graveyard;
+    std::mutex lat_mu;
+    std::vector<float> lat_us;  // ring of query latencies
+    size_t lat_head = 0, lat_count = 0;
     std::mutex lane_mu;
     std::vector<Lane> lanes;
     std::vector<int> free_lanes;
@@ -108,8 +132,8 @@ struct hf_server {
 
 static void publish(hf_server *s, const std::shared_ptr<Request> &r) {
     Session &ss = s->sessions[r->session];
-    if (ss.open) ss.current = std::make_shared<SetHolder>(r->fs);
-    else hf_fieldset_release(r->fs);
+    if (ss.open) ss.current = std::make_shared<SetHolder>(r->fs, &s->graveyard);
+    else s->graveyard.put(r->fs);
     r->fs = nullptr;
 }
 
@@ -127,84 +151,133 @@ static bool evict_one(hf_server *s, int keep) {
     return true;
 }
 
+static void free_retired(hf_server *s) {
+    for (hf_fieldset *fs : s->graveyard.take()) hf_fieldset_release(fs);
+}
+
+// Scheduler: the server mutex guards only the queues and session table;
+// allocation, the host set-up and the launches of a build, and every free,
+// happen outside it, so queries (which take the mutex briefly) never wait
+// for them.
 static void scheduler(hf_server *s) {
     cudaSetDevice(s->device);
-    std::unique_lock<std::mutex> lk(s->mu);
-    while (!s->stop) {
-        // completions
-        for (size_t i = 0; i < s->running.size();) {
-            auto &r = s->running[i];
-            const cudaError_t q = cudaEventQuery(r->done);
-            if (q == cudaErrorNotReady) { ++i; continue; }
-            r->t_done = now_ms();
-            if (q == cudaSuccess) {
-                publish(s, r);
-                r->state = RQ_DONE;
-                s->stats.completed++;
-                s->stats.rotations_completed += r->R;
-            } else {
-                hf_fieldset_release(r->fs);
-                r->fs = nullptr;
-                r->state = RQ_FAILED;
-                s->stats.failed++;
+    for (;;) {
+        std::shared_ptr<Request> cand;
+        const hf_part *p1 = nullptr, *p2 = nullptr;
+        int n = 0, si = -1;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            if (s->stop) break;
+            // completions
+            for (size_t i = 0; i < s->running.size();) {
+                auto &r = s->running[i];
+                const cudaError_t q = cudaEventQuery(r->done);
+                if (q == cudaErrorNotReady) { ++i; continue; }
+                r->t_done = now_ms();
+                if (q == cudaSuccess) {
+                    publish(s, r);
+                    r->state = RQ_DONE;
+                    s->stats.completed++;
+                    s->stats.rotations_completed += r->R;
+                } else {
+                    s->graveyard.put(r->fs);
+                    r->fs = nullptr;
+                    r->state = RQ_FAILED;
+                    s->stats.failed++;
+                }
+                cudaEventDestroy(r->done);
+                r->done = nullptr;
+                s->stream_busy[r->stream] = 0;
+                s->running.erase(s->running.begin() + i);
             }
-            cudaEventDestroy(r->done);
-            r->done = nullptr;
-            s->stream_busy[r->stream] = 0;
-            s->running.erase(s->running.begin() + i);
-        }
-        // admission, first-in first-out
-        while (!s->queue.empty() && (int)s->running.size() < s->max_inflight) {
-            auto r = s->queue.front();
-            if (r->state == RQ_SUPERSEDED) { s->queue.pop_front(); continue; }
-            Session &ss = s->sessions[r->session];
-            if (!ss.open) {
-                r->state = RQ_FAILED;
-                s->stats.failed++;
+            // next admissible request, first-in first-out
+            while (!s->queue.empty() && (int)s->running.size() < s->max_inflight) {
+                auto r = s->queue.front();
                 s->queue.pop_front();
+                if (r->state == RQ_SUPERSEDED) continue;
+                Session &ss = s->sessions[r->session];
+                if (!ss.open) {
+                    r->state = RQ_FAILED;
+                    s->stats.failed++;
+                    continue;
+                }
+                si = 0;
+                while (si < (int)s->streams.size() && s->stream_busy[si]) ++si;
+                cand = r;
+                p1 = ss.s1;
+                p2 = ss.s2;
+                n = ss.n;
+                s->stream_busy[si] = 1;  // reserved while this thread prepares the build
+                break;
+            }
+            s->stats.queued = (int)s->queue.size();
+            s->stats.running = (int)s->running.size();
+            if (!cand) {
+                const bool idle = s->running.empty();
+                lk.unlock();
+                free_retired(s);
+                lk.lock();
+                if (!s->stop) s->cv.wait_for(lk, std::chrono::microseconds(idle ? 5000 : 200));
                 continue;
             }
-            hf_fieldset *fs = nullptr;
-            hf_status st = hf_fieldset_create(s->ctx, ss.n, r->R, r->flags, &fs);
-            if (st == HF_EBUDGET) {
-                // nothing in flight will free memory: make room from other sessions' sets
-                if (s->running.empty() && evict_one(s, r->session)) continue;
-                break;  // wait for running builds to finish
-            }
-            int si = 0;
-            while (si < (int)s->streams.size() && s->stream_busy[si]) ++si;
-            if (st == HF_OK && si < (int)s->streams.size()) {
-                st = hf_fieldset_compute(s->ctx, ss.s1, ss.s2, r->quats.data(), r->R, fs, s->streams[si]);
-                if (st == HF_EINVAL) st = HF_OK;  // rank-deficient torque neighbourhoods are flagged, not fatal
-            }
-            if (st == HF_OK && cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming) == cudaSuccess &&
-                cudaEventRecord(r->done, s->streams[si]) == cudaSuccess) {
-                r->fs = fs;
-                r->stream = si;
-                r->state = RQ_RUNNING;
-                s->stream_busy[si] = 1;
-                s->running.push_back(r);
-            } else {
-                if (fs) hf_fieldset_release(fs);
-                r->state = RQ_FAILED;
-                s->stats.failed++;
-            }
-            s->queue.pop_front();
         }
-        s->stats.queued = (int)s->queue.size();
-        s->stats.running = (int)s->running.size();
-        // wake on new work, or poll the running builds every 200 us
-        s->cv.wait_for(lk, std::chrono::microseconds(s->running.empty() ? 5000 : 200));
+        free_retired(s);
+        // allocate and launch outside the mutex
+        hf_fieldset *fs = nullptr;
+        hf_status st = hf_fieldset_create_stream_ordered(s->ctx, n, cand->R, cand->flags, s->streams[si], &fs);
+        if (st == HF_EBUDGET) {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->stream_busy[si] = 0;
+            if (s->running.empty()) {
+                // nothing in flight will free memory: make room from other sessions' sets
+                if (evict_one(s, cand->session)) {
+                    s->queue.push_front(cand);  // keep its place; retry once the set is freed
+                } else {
+                    cand->state = RQ_FAILED;  // can never fit next to the resident parts
+                    s->stats.failed++;
+                    s->stats.rejected++;
+                }
+                continue;
+            }
+            s->queue.push_front(cand);  // keep its place and wait for a running build
+            s->cv.wait_for(lk, std::chrono::microseconds(200));
+            continue;
+        }
+        if (st == HF_OK) {
+            st = hf_fieldset_compute(s->ctx, p1, p2, cand->quats.data(), cand->R, fs, s->streams[si]);
+            // a rank-deficient torque neighbourhood is flagged (NaN torque), not fatal
+            if (st == HF_EINVAL && hf_fieldset_is_ready(fs)) st = HF_OK;
+            if (st != HF_OK) cand->error = hf_last_error();
+        }
+        cudaEvent_t ev = nullptr;
+        if (st == HF_OK && (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
+                            cudaEventRecord(ev, s->streams[si]) != cudaSuccess))
+            st = HF_ECUDA;
+        std::lock_guard<std::mutex> g(s->mu);
+        if (st == HF_OK) {
+            cand->fs = fs;
+            cand->done = ev;
+            cand->stream = si;
+            cand->state = RQ_RUNNING;
+            s->running.push_back(cand);
+        } else {
+            if (fs) s->graveyard.put(fs);
+            if (ev) cudaEventDestroy(ev);
+            s->stream_busy[si] = 0;
+            cand->state = RQ_FAILED;
+            s->stats.failed++;
+        }
     }
     // drain: wait for everything in flight, then release
     for (auto &r : s->running) {
         cudaEventSynchronize(r->done);
         cudaEventDestroy(r->done);
-        hf_fieldset_release(r->fs);
+        s->graveyard.put(r->fs);
         r->fs = nullptr;
         r->state = RQ_FAILED;
     }
     s->running.clear();
+    free_retired(s);
 }
 
 extern "C" hf_status hf_server_create(hf_ctx *ctx, int max_inflight, int query_lanes, hf_server **out) {
@@ -228,10 +301,8 @@ extern "C" hf_status hf_server_create(hf_ctx *ctx, int max_inflight, int query_l
     for (int i = 0; i < query_lanes && e == cudaSuccess; ++i) {
         Lane &L = s->lanes[i];
         e = cudaStreamCreateWithPriority(&L.st, cudaStreamNonBlocking, hi);
-        if (e == cudaSuccess) e = cudaMallocHost(&L.h_in, 8 * sizeof(float));
-        if (e == cudaSuccess) e = cudaMallocHost(&L.h_out, 8 * sizeof(float));
-        if (e == cudaSuccess) e = cudaMalloc(&L.d_in, 8 * sizeof(float));
-        if (e == cudaSuccess) e = cudaMalloc(&L.d_out, 8 * sizeof(float));
+        if (e == cudaSuccess) e = cudaHostAlloc(&L.h_out, 8 * sizeof(float), cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer(&L.d_out, L.h_out, 0);
         s->free_lanes.push_back(i);
     }
     if (e != cudaSuccess) {
@@ -252,14 +323,13 @@ extern "C" void hf_server_destroy(hf_server *s) {
     s->cv.notify_all();
     if (s->sched.joinable()) s->sched.join();
     for (auto &ss : s->sessions) ss.current.reset();
+    cudaDeviceSynchronize();
+    free_retired(s);
     for (auto st : s->streams)
         if (st) cudaStreamDestroy(st);
     for (auto &L : s->lanes) {
         if (L.st) cudaStreamDestroy(L.st);
-        if (L.h_in) cudaFreeHost(L.h_in);
         if (L.h_out) cudaFreeHost(L.h_out);
-        if (L.d_in) cudaFree(L.d_in);
-        if (L.d_out) cudaFree(L.d_out);
     }
     delete s;
 }
@@ -332,6 +402,7 @@ extern "C" hf_status hf_server_request_state(hf_server *s, int64_t request, int 
     auto it = s->requests.find(request);
     if (it == s->requests.end()) return srv_fail(HF_EINVAL, "hf_server_request_state: request %lld", (long long)request);
     *state = it->second->state;
+    if (it->second->state == RQ_FAILED) hf::set_last_error(it->second->error.c_str());
     if (latency_ms) *latency_ms = it->second->state == RQ_DONE ? it->second->t_done - it->second->t_submit : -1.0;
     return HF_OK;
 }
@@ -352,9 +423,12 @@ static std::shared_ptr<SetHolder> current_set(hf_server *s, int session, hf_stat
     return ss.current;
 }
 
+constexpr size_t kLatRing = 1u << 20;
+
 extern "C" hf_status hf_server_query(hf_server *s, int session, const float t[3], const float q[4], int k,
                                      float out7[7]) {
     if (!s) return srv_fail(HF_EINVAL, "hf_server_query: NULL server");
+    const double t0 = now_ms();
     hf_status st = HF_OK;
     std::shared_ptr<SetHolder> set = current_set(s, session, &st);
     if (!set) return st;
@@ -366,17 +440,36 @@ extern "C" hf_status hf_server_query(hf_server *s, int session, const float t[3]
         s->free_lanes.pop_back();
     }
     Lane &L = s->lanes[li];
-    st = hf_query_on_lane(set->fs, t, q, k, out7, L.st, L.h_in, L.h_out, L.d_in, L.d_out);
+    st = hf_query_on_lane(set->fs, t, q, k, out7, L.st, L.h_out, L.d_out);
     {
         std::lock_guard<std::mutex> g(s->lane_mu);
         s->free_lanes.push_back(li);
     }
     s->lane_cv.notify_one();
+    if (st == HF_OK) {
+        const float us = (float)((now_ms() - t0) * 1000.0);
+        std::lock_guard<std::mutex> g(s->lat_mu);
+        if (s->lat_us.size() < kLatRing) s->lat_us.resize(kLatRing);
+        s->lat_us[s->lat_head] = us;
+        s->lat_head = (s->lat_head + 1) % kLatRing;
+        s->lat_count = std::min(s->lat_count + 1, kLatRing);
+    }
     {
         std::lock_guard<std::mutex> g(s->mu);
         s->stats.queries++;
     }
     return st;
+}
+
+extern "C" int hf_server_query_latencies(hf_server *s, float *out, int max) {
+    if (!s || !out || max <= 0) return 0;
+    std::lock_guard<std::mutex> g(s->lat_mu);
+    const size_t n = std::min(s->lat_count, (size_t)max);
+    size_t start = (s->lat_head + kLatRing - s->lat_count) % kLatRing;
+    start = (start + (s->lat_count - n)) % kLatRing;  // the newest n
+    for (size_t i = 0; i < n; ++i) out[i] = s->lat_us[(start + i) % kLatRing];
+    s->lat_count = 0;
+    return (int)n;
 }
 
 extern "C" hf_status hf_server_field_ptr(hf_server *s, int session, int rot, int field, const float **d_ptr) {
@@ -406,5 +499,54 @@ extern "C" hf_status hf_server_stats_get(hf_server *s, hf_server_stats *out) {
     *out = s->stats;
     out->reserved_bytes = hf_ctx_reserved_bytes(s->ctx);
     out->budget_bytes = hf_ctx_budget_bytes(s->ctx);
+    return HF_OK;
+}
+
+extern "C" hf_status hf_server_drive_queries(hf_server *s, int nsess, const int *sessions, const float *poses,
+                                             int steps, double rate_hz, int k, int64_t *answered,
+                                             int64_t *not_ready, int64_t *late) {
+    if (!s || nsess <= 0 || !sessions || !poses || steps <= 0 || !(rate_hz > 0))
+        return srv_fail(HF_EINVAL, "hf_server_drive_queries: bad arguments");
+    std::atomic<int64_t> ok{0}, nr{0}, lt{0};
+    std::mutex err_mu;
+    std::string first_err;
+    hf_status first_st = HF_OK;
+    const double period = 1000.0 / rate_hz;  // ms
+    std::vector<std::thread> th;
+    for (int i = 0; i < nsess; ++i) {
+        th.emplace_back([&, i] {
+            cudaSetDevice(s->device);
+            const float *p = poses + (size_t)i * steps * 7;
+            const double t0 = now_ms();
+            for (int j = 0; j < steps; ++j) {
+                const double due = t0 + j * period;
+                double now = now_ms();
+                while (now < due) {  // sleep most of the wait, then spin the last 50 us
+                    const double left = due - now;
+                    if (left > 0.1) std::this_thread::sleep_for(std::chrono::microseconds((int64_t)((left - 0.05) * 1000)));
+                    now = now_ms();
+                }
+                if (now - due > period) lt++;
+                float out[7];
+                const hf_status st = hf_server_query(s, sessions[i], p + 7 * (size_t)j, p + 7 * (size_t)j + 3, k, out);
+                if (st == HF_OK) {
+                    ok++;
+                } else {
+                    nr++;
+                    std::lock_guard<std::mutex> g(err_mu);
+                    if (first_st == HF_OK) {
+                        first_st = st;
+                        first_err = hf_last_error();
+                    }
+                }
+            }
+        });
+    }
+    for (auto &t : th) t.join();
+    if (answered) *answered = ok;
+    if (not_ready) *not_ready = nr;
+    if (late) *late = lt;
+    if (first_st != HF_OK && ok == 0)
+        return srv_fail(first_st, "hf_server_drive_queries: no query answered; first failure: %s", first_err.c_str());
     return HF_OK;
 }

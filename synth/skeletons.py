@@ -222,24 +222,19 @@ def translation_walk(seed, steps, step_sigma=0.002, start=None):
 
 
 def quaternion_walk(seed, steps, step_sigma=0.002, start=None):
-    """Random-walk orientations: each step an axis-angle increment with
-    N(0, step_sigma^2) components composed on the left."""
+    """Random-walk orientations, one step per ms: axis-angle increments with
+    N(0, step_sigma^2) components, accumulated; the orientation at step k is
+    exp(sum of increments) applied on the left of the start orientation."""
     g = _rng(seed)
-    q = np.array([1.0, 0, 0, 0]) if start is None else np.asarray(start, float)
-    out = np.empty((steps, 4))
-    for s in range(steps):
-        v = g.normal(0.0, step_sigma, 3)
-        th = np.linalg.norm(v)
-        if th > 0:
-            dq = np.concatenate([[np.cos(th / 2)], np.sin(th / 2) * v / th])
-        else:
-            dq = np.array([1.0, 0, 0, 0])
-        w1, x1, y1, z1 = dq
-        w2, x2, y2, z2 = q
-        q = np.array([w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2,
-                      w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
-                      w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2,
-                      w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2])
-        q /= np.linalg.norm(q)
-        out[s] = q
-    return out
+    v = np.cumsum(g.normal(0.0, step_sigma, (steps, 3)), axis=0)
+    th = np.linalg.norm(v, axis=1, keepdims=True)
+    safe = np.where(th > 0, th, 1.0)
+    dq = np.concatenate([np.cos(th / 2), np.sin(th / 2) * v / safe], axis=1)
+    q0 = np.array([1.0, 0, 0, 0]) if start is None else np.asarray(start, float)
+    w1, x1, y1, z1 = dq.T
+    w2, x2, y2, z2 = q0
+    q = np.stack([w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2,
+                  w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+                  w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2,
+                  w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2], axis=1)
+    return q / np.linalg.norm(q, axis=1, keepdims=True)

@@ -142,3 +142,34 @@ def test_queries_during_builds_are_exact_at_nodes_and_member_rotations(hf):
     assert max(errs) <= 1e-6
     assert srv.stats()["queries"] >= 800
     srv.close()
+
+
+def test_native_query_driver_meets_the_rate(hf):
+    """Two sessions replayed at 1 kHz from native threads while a third
+    session builds: every query answered, latencies recorded per query."""
+    ctx = hf.Context(0)
+    srv = hf.Server(ctx, max_inflight=2, query_lanes=4)
+    a = srv.open(*make_parts(hf, ctx, 64, 8))
+    b = srv.open(*make_parts(hf, ctx, 32, 9))
+    c = srv.open(*make_parts(hf, ctx, 128, 10))
+    r = [srv.submit(a, synth.random_quaternions(60, 16)), srv.submit(b, synth.random_quaternions(61, 16))]
+    res = srv.wait(r)
+    from paper_1711_05017_b300 import _binding as B
+    for rid in r:
+        st, _ = srv.state(rid)
+        assert st == "done", B.lib().hf_last_error()
+    assert np.isfinite(srv.query(a, [0.1, 0.2, 0.3], synth.random_quaternions(63, 1)[0])).all()
+    busy = srv.submit(c, synth.random_quaternions(62, 96))
+    steps = 300
+    poses = np.stack([np.concatenate([synth.translation_walk(70 + i, steps), synth.quaternion_walk(80 + i, steps)], 1)
+                      for i in range(2)])
+    srv.query_latencies()
+    t0 = time.perf_counter()
+    answered, not_ready, late = srv.drive_queries([a, b], poses, rate_hz=1000.0)
+    took = time.perf_counter() - t0
+    lat = srv.query_latencies()
+    srv.wait([busy])
+    assert answered == 2 * steps and not_ready == 0
+    assert lat.size == 2 * steps and np.isfinite(lat).all()
+    assert took >= 0.29  # paced, not burst
+    srv.close()
