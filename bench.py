@@ -123,6 +123,28 @@ def oracle_rotation_sample(s1, s2, quats, n, count):
     return t_rot, t_splat, f"{count} rotations of the {n}^3 workload (resample + E/F fields), splat timed once"
 
 
+# ------------------------------------------------------- multi-rank logic
+def rank_rotations(rank, R):
+    """Each rank builds its own rotation batch (weak scaling): seed = rank, so
+    rank 0 has the workload's own 1024 rotations."""
+    return synth.random_quaternions(rank, R).astype(np.float32)
+
+
+def max_over_ranks(x, world, device=None):
+    """Slowest rank's value: the job is done when the last rank is."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, seconds):
+    """Whole-job units per second: every rank's units over the slowest time."""
+    return world * units_per_rank / seconds
+
+
 # ------------------------------------------------------------ our arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -134,7 +156,7 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     n, R = args.n, args.rotations
     s1, s2 = synth.c2_pair(0)
-    quats = synth.random_quaternions(rank, R).astype(np.float32)
+    quats = rank_rotations(rank, R)
     rng = np.random.default_rng(1000 + rank)
     tq_h = np.concatenate([rng.uniform(-1, 1, (N_QUERY, 3)), synth.random_quaternions(2000 + rank, N_QUERY)],
                           axis=1).astype(np.float32)
@@ -182,11 +204,8 @@ def run_ours(args, rank, world, local_rank):
     ms = ev0.elapsed_time(ev1) / args.steps
     prof = ctx.profile_read(reset=True)
     ctx.profile(False)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * R / (ms / 1e3)
+    ms = max_over_ranks(ms, world, dev)
+    value = job_throughput(R, world, ms / 1e3)
 
     # ---- roofline of the dominant kernel (algorithmic bytes / event-timed duration)
     he = n * n * (n // 2 + 1) * 8  # one half-spectrum intermediate, bytes
@@ -251,10 +270,7 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(e2e_steps):
         e2e_step()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, world, dev)
     h2d = sum(h.numel() * 4 for h in hp) + tq_pin.numel() * 4 + quats.nbytes
     d2h = res_pin.numel() * 4
 
