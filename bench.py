@@ -145,6 +145,10 @@ def job_throughput(units_per_rank, world, seconds):
     return world * units_per_rank / seconds
 
 
+def tune_is_pencil(ctx, n):
+    return bool(ctx.tune_get(n)[1]) or os.environ.get("HF_PIPELINE") == "pencil"
+
+
 # ------------------------------------------------------------ our arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -169,6 +173,10 @@ def run_ours(args, rank, world, local_rank):
     ctx.density_build(n, pts1, sig1, out=g1)
     ctx.density_build(n, pts2, sig2, out=g2)
     p1, p2 = ctx.part(g1, hf.HF_STATIONARY), ctx.part(g2, hf.HF_MOVING)
+    tune = None
+    if not args.no_tune:  # launch shape for this grid size, timed on this device (not cached)
+        c, pen, rps = ctx.autotune(n)
+        tune = {"chunk": c, "pipeline": "pencil" if pen else "slab", "ef_rot_per_s": round(rps, 1)}
     fs = ctx.fieldset(n, R, hf.HF_E | hf.HF_F | hf.HF_T)
     tq = torch.as_tensor(tq_h, device=dev)
     qout = torch.empty((N_QUERY, 7), device=dev)
@@ -210,7 +218,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- roofline of the dominant kernel (algorithmic bytes / event-timed duration)
     he = n * n * (n // 2 + 1) * 8  # one half-spectrum intermediate, bytes
     n3b = 4 * n**3
-    chunk = min({32: 256, 64: 128, 96: 48}.get(n, 32), R) if not os.environ.get("HF_ROT_CHUNK") else int(os.environ["HF_ROT_CHUNK"])
+    chunk = min(ctx.tune_get(n)[0], R) if not os.environ.get("HF_ROT_CHUNK") else int(os.environ["HF_ROT_CHUNK"])
     alg = {  # bytes per launch: inputs read once + outputs written
         "passA": n3b + chunk * he,
         "passB": chunk * he + he + 2 * chunk * he,
@@ -221,9 +229,11 @@ def run_ours(args, rank, world, local_rank):
         "query": N_QUERY * 7 * 4 * 2,
         "resample": n3b + chunk * n3b,
     }
-    # dram__bytes_read.sum + dram__bytes_write.sum per launch of the current
-    # kernels, 32 rotations per launch (profiles/passC_c2_128.md)
-    traffic = {"passC": 1.5625e9} if (n == 128 and chunk == 32) else {}
+    # dram__bytes_read.sum + dram__bytes_write.sum of one pass C launch over
+    # 32 rotations at 128^3 (profiles/passC_c2_128.md), scaled to this
+    # launch's rotations: the traffic is per rotation (each reads its own two
+    # spectra and writes its own four fields)
+    traffic = {"passC": 1.5625e9 * chunk / 32} if n == 128 and not tune_is_pencil(ctx, n) else {}
     hbm_peak, peak_kind = peaks()
     kernels = {}
     for k, (cnt, tot) in prof.items():
@@ -320,10 +330,14 @@ def run_ours(args, rank, world, local_rank):
         cpu = {"value": round(1.0 / t_rot, 4), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": desc, "splat_s": round(t_splat, 2)}
 
-    serving = None
-    if rank == 0 and world == 1 and args.serve_seconds > 0:
+    serving = batch = None
+    if rank == 0 and world == 1 and (args.serve_seconds > 0 or args.batch_steps > 0):
         del fs
         torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and args.batch_steps > 0:
+        batch = run_batch(args, local_rank)
+        torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and args.serve_seconds > 0:
         serving = run_serving(args, local_rank)
 
     if rank == 0:
@@ -333,7 +347,7 @@ def run_ours(args, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"c2 peg-in-hole skeletons, {n}^3 grid, 5000+5000 points, radii U(0.02,0.08), "
                                    f"{R} random rotations per rank, E+F+T fields, {N_QUERY} pose queries per step",
-                       "grid": n, "rotations_per_rank": R, "parallelism": f"replicas x{world} (rotation batches)",
+                       "grid": n, "rotations_per_rank": R, "launch_shape": tune, "parallelism": f"replicas x{world} (rotation batches)",
                        "l2": "working set > L2 (fields 60 GB per rank)"},
             "e2e": {"value": round(world * R / e2e_s, 1), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
@@ -346,9 +360,98 @@ def run_ours(args, rank, world, local_rank):
             "plain_path": plain,
             "cpu_baseline": cpu,
             "clocks": clk.summary(),
+            "batch": batch,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------- uneven batch workload
+BATCH_SLOTS = 8  # field sets per (size, rotations): 64 pairs' fields (250 GB) plus scratch exceed the device
+# graph branches: 1 (builds in sequence inside the graph).  Measured on B300
+# with 8 slots per size: 1 branch 50.4k rot/s, 3 branches 46.7k, 24 branches
+# 47.5k -- concurrent 96^3/128^3 builds contend for SMs and L2
+BATCH_LANES = 1
+
+
+def run_batch(args, local_rank):
+    """64 part pairs, grid sizes 64/96/128 (24/24/16), 1000-8000 points each,
+    256 rotations per pair, E+F: launch shapes from the autotuner, the whole
+    build recorded as one CUDA graph and replayed; the same builds issued pair
+    by pair without the graph on one stream for comparison."""
+    import tempfile
+
+    import torch
+    import paper_1711_05017_b300 as hf
+    dev = torch.device("cuda", local_rank)
+    specs = synth.c3_pairs(0)
+    ctx = hf.Context(local_rank)
+    flags = hf.HF_E | hf.HF_F
+    tune = {}
+    t0 = time.perf_counter()
+    with tempfile.TemporaryDirectory() as d:
+        for n in sorted(set(p.n for p in specs)):
+            c, pen, rps = ctx.autotune(n, os.path.join(d, "tune.txt"))
+            tune[n] = {"chunk": c, "pipeline": "pencil" if pen else "slab", "rot_per_s": round(rps, 1)}
+    tune_s = time.perf_counter() - t0
+    pairs, quats = [], []
+    for p in specs:
+        cu = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=dev)  # noqa: E731
+        g1 = ctx.density_build(p.n, cu(p.s1.pts), cu(p.s1.sigma))
+        g2 = ctx.density_build(p.n, cu(p.s2.pts), cu(p.s2.sigma))
+        pairs.append((ctx.part(g1, hf.HF_STATIONARY), ctx.part(g2, hf.HF_MOVING)))
+        quats.append(synth.random_quaternions(p.quat_seed, p.n_rot).astype(np.float32))
+    R = [p.n_rot for p in specs]
+    total = sum(R)
+    b = hf.Batch(ctx, pairs, R, flags, slots_per_size=BATCH_SLOTS)
+    for i, q in enumerate(quats):
+        b.set_rotations(i, q)
+    t0 = time.perf_counter()
+    b.capture(BATCH_LANES)
+    cap_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    steps, warm = args.batch_steps, 3
+    for _ in range(warm):
+        b.launch()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        b.launch()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    g_ms = e0.elapsed_time(e1) / steps
+    # the same builds pair by pair, no graph, one stream, into one set per (size, rotations)
+    sets = {}
+    for p in specs:
+        if (p.n, p.n_rot) not in sets:
+            sets[(p.n, p.n_rot)] = ctx.fieldset(p.n, p.n_rot, flags)
+
+    def sequential():
+        for p, pr, q in zip(specs, pairs, quats):
+            sets[(p.n, p.n_rot)].compute(pr[0], pr[1], q)
+
+    sequential()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(max(1, steps // 2)):
+        sequential()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    s_ms = e0.elapsed_time(e1) / max(1, steps // 2)
+    out = {"workload": "64 part pairs, grids 64^3/96^3/128^3 (24/24/16), 1000-8000 skeleton points each, "
+                       "256 random rotations per pair, E+F fields", "pairs": len(specs), "rotations": total,
+           "graph": {"value": round(total / (g_ms / 1e3), 1), "unit": UNIT, "ms_per_launch": round(g_ms, 2),
+                     "slots": b.slots(), "slots_per_size": BATCH_SLOTS, "lanes": BATCH_LANES or b.slots(), "capture_s": round(cap_s, 3),
+                     "launches": steps},
+           "sequential_no_graph": {"value": round(total / (s_ms / 1e3), 1), "unit": UNIT,
+                                   "ms_per_pass": round(s_ms, 2)},
+           "speedup_of_graph": round(s_ms / g_ms, 3), "autotune": tune, "autotune_s": round(tune_s, 1)}
+    b.release()
+    for v in sets.values():
+        v.release()
+    del pairs
+    return out
 
 
 # ------------------------------------------------------- serving workload
@@ -476,6 +579,9 @@ def main():
     ap.add_argument("--rotations", type=int, default=N_ROT)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="built-in launch shapes instead of the autotuner's")
+    ap.add_argument("--batch-steps", type=int, default=5,
+                    help="graph launches of the 64-pair uneven batch (0 = skip)")
     ap.add_argument("--serve-seconds", type=float, default=20.0,
                     help="length of the 16-session serving run (0 = skip)")
     args = ap.parse_args()

@@ -238,6 +238,64 @@ hf_status hf_server_drive_queries(hf_server *srv, int nsess, const int *sessions
                                   double rate_hz, int k_blend, int64_t *answered, int64_t *not_ready,
                                   int64_t *late);
 
+/* ---- a scene's precompute as one CUDA graph ----
+ * The offline precompute of Section 4.2 for many part pairs at once, each
+ * pair with its own grid size (32..256) and its own rotation set: all
+ * builds are recorded once into one CUDA graph and replayed with one call.
+ * Each pair writes its fields into a slot (a field set).  slots_per_size <= 0
+ * gives every pair a slot of its own; slots_per_size = k > 0 lets pairs of
+ * the same grid size and rotation count share k slots round-robin, so a
+ * scene whose fields exceed the device streams through k sets per size (a
+ * slot then holds the last of its pairs after a launch).  Pairs in one slot
+ * run in order; slots run concurrently.  Parts must outlive the batch.
+ *
+ *   hf_batch_create      npairs pairs (s1[i] stationary, s2[i] moving, both of
+ *                        one size), R[i] rotations each; flags as for
+ *                        hf_fieldset_create (HF_T needs R[i] >= 7).
+ *                        Errors: HF_EINVAL, HF_EBUDGET, HF_ENOMEM, HF_ECUDA.
+ *   hf_batch_set_rotations  pair's R[i] x 4 quaternions (host, copied
+ *                        synchronously); may change between launches without
+ *                        a new capture, but not while a launch runs.
+ *                        HF_EINVAL for a bad quaternion or (after uploading)
+ *                        a rank-deficient torque neighbourhood.
+ *   hf_batch_capture     record every pair's launches (all pairs need
+ *                        rotations; HF_ENOTREADY otherwise) on `lanes`
+ *                        concurrent branches (<= 0: one per slot; 1: every
+ *                        build in sequence).  Slot s goes to branch s % lanes.
+ *                        Make it with no other work of the batch's parts in
+ *                        flight; a new capture replaces the previous graph.
+ *   hf_batch_launch      enqueue the whole graph on `stream`.
+ *   hf_batch_fieldset    the set holding `pair`'s fields after the last
+ *                        launch (HF_ENOTREADY if its slot holds another pair);
+ *                        the batch owns it: do not release it.
+ *   hf_batch_slots       number of slots (field sets) the batch holds. */
+typedef struct hf_batch hf_batch;
+hf_status hf_batch_create(hf_ctx *ctx, int npairs, const hf_part *const *s1, const hf_part *const *s2,
+                          const int *R, unsigned flags, int slots_per_size, hf_batch **out);
+hf_status hf_batch_set_rotations(hf_batch *batch, int pair, const float *h_quat);
+hf_status hf_batch_capture(hf_batch *batch, int lanes);
+hf_status hf_batch_launch(hf_batch *batch, hf_stream stream);
+hf_status hf_batch_fieldset(const hf_batch *batch, int pair, const hf_fieldset **out);
+int hf_batch_slots(const hf_batch *batch);
+void hf_batch_release(hf_batch *batch);
+
+/* ---- launch-shape autotuning ----
+ * Per grid size, the context chooses how many rotations each pass launch
+ * covers (the chunk) and whether the slab passes or the pencil pipeline run
+ * (N = 256: pencil only).  hf_autotune times builds of E and F on synthetic
+ * parts for every candidate that fits the budget, keeps the fastest for field
+ * sets created afterwards, and, given a cache_path, first looks for a line
+ * for this device and N there (and writes one after timing).  Cache lines
+ * are text: "<device> <n> <chunk> <pencil> <rotations_per_s>".  Outputs may
+ * be NULL.  hf_tune_set fixes the choice by hand (chunk <= 0 restores the
+ * built-in one); hf_tune_get reads the current choice (rot_per_s 0 when not
+ * timed).  The environment variable HF_ROT_CHUNK overrides all of them.
+ * Errors: HF_EINVAL, HF_EUNSUPPORTED, HF_ENOMEM (nothing fits), HF_ECUDA. */
+hf_status hf_autotune(hf_ctx *ctx, int n, const char *cache_path, int *chunk, int *pencil,
+                      double *rot_per_s);
+hf_status hf_tune_set(hf_ctx *ctx, int n, int chunk, int pencil);
+hf_status hf_tune_get(const hf_ctx *ctx, int n, int *chunk, int *pencil, double *rot_per_s);
+
 /* ---- per-kernel timing (CUDA events on the launching stream) ----
  * While enabled, every kernel launch the context's calls make is bracketed by
  * a pair of CUDA events on its stream.  hf_profile_read synchronises the

@@ -13,7 +13,7 @@ import numpy as np
 from . import _binding as B
 from ._binding import HF_E, HF_F, HF_MOVING, HF_STATIONARY, HF_T, HF_TORQUE_F64, HFError  # noqa: F401
 
-__all__ = ["Context", "Part", "FieldSet", "Server", "HFError", "resample", "rfft3d", "version"]
+__all__ = ["Context", "Part", "FieldSet", "Batch", "Server", "HFError", "resample", "rfft3d", "version"]
 
 
 def _torch():
@@ -98,6 +98,22 @@ class Context:
 
     def part(self, grid, role, stream=None):
         return Part(self, grid, role, stream)
+
+    def autotune(self, n, cache_path=None):
+        """hf_autotune: time the launch shapes for grid size n (or read them
+        from cache_path); returns (chunk, pencil, rotations per second)."""
+        c, p, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        path = None if cache_path is None else str(cache_path).encode()
+        B.check(B.lib().hf_autotune(self.handle, int(n), path, ctypes.byref(c), ctypes.byref(p), ctypes.byref(r)))
+        return int(c.value), int(p.value), float(r.value)
+
+    def tune_set(self, n, chunk, pencil=False):
+        B.check(B.lib().hf_tune_set(self.handle, int(n), int(chunk), 1 if pencil else 0))
+
+    def tune_get(self, n):
+        c, p, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        B.check(B.lib().hf_tune_get(self.handle, int(n), ctypes.byref(c), ctypes.byref(p), ctypes.byref(r)))
+        return int(c.value), int(p.value), float(r.value)
 
     def fieldset(self, n, R, flags=HF_E | HF_F):
         return FieldSet(self, n, R, flags)
@@ -203,6 +219,65 @@ class FieldSet:
     def release(self):
         if self.handle:
             B.lib().hf_fieldset_release(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+class _BorrowedFieldSet(FieldSet):
+    """A field set owned by a Batch: readable, never released from Python."""
+
+    def __init__(self, ctx, handle):
+        L = B.lib()
+        self.handle, self.ctx = handle, ctx
+        self.n, self.R, self.flags = L.hf_fieldset_n(handle), L.hf_fieldset_rotations(handle), L.hf_fieldset_flags(handle)
+
+    def release(self):
+        self.handle = None
+
+
+class Batch:
+    """hf_batch: many part pairs (sizes may differ) built by one CUDA graph.
+    pairs: [(stationary Part, moving Part)]; R: rotations per pair."""
+
+    def __init__(self, ctx, pairs, R, flags=HF_E | HF_F, slots_per_size=0):
+        n = len(pairs)
+        S1 = (ctypes.c_void_p * n)(*[p[0].handle.value for p in pairs])
+        S2 = (ctypes.c_void_p * n)(*[p[1].handle.value for p in pairs])
+        Rs = (ctypes.c_int * n)(*[int(r) for r in R])
+        h = ctypes.c_void_p()
+        B.check(B.lib().hf_batch_create(ctx.handle, n, S1, S2, Rs, int(flags), int(slots_per_size), ctypes.byref(h)))
+        self.handle, self.ctx, self.npairs = h, ctx, n
+        self._pairs = list(pairs)  # the parts must outlive the batch
+
+    def set_rotations(self, pair, quats, allow_rank_deficient=False):
+        q = np.ascontiguousarray(quats, dtype=np.float32).reshape(-1, 4)
+        rc = B.lib().hf_batch_set_rotations(self.handle, int(pair), B.fptr(q))
+        return B.check(rc, allow=(B.HF_EINVAL,) if allow_rank_deficient else ())
+
+    def capture(self, lanes=0):
+        """Record the whole batch as one graph on `lanes` concurrent branches
+        (0: one per slot)."""
+        B.check(B.lib().hf_batch_capture(self.handle, int(lanes)))
+
+    def launch(self, stream=None):
+        B.check(B.lib().hf_batch_launch(self.handle, _stream_ptr(stream)))
+
+    def slots(self):
+        return B.lib().hf_batch_slots(self.handle)
+
+    def fieldset(self, pair):
+        p = ctypes.c_void_p()
+        B.check(B.lib().hf_batch_fieldset(self.handle, int(pair), ctypes.byref(p)))
+        return _BorrowedFieldSet(self.ctx, p)
+
+    def release(self):
+        if self.handle:
+            B.lib().hf_batch_release(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -72,6 +72,16 @@ SIGNATURES = {
     "hf_server_query_latencies": (_i, [_vp, _fp, _i]),
     "hf_server_drive_queries": (_i, [_vp, _i, _ip, _fp, _i, ctypes.c_double, _i, ctypes.POINTER(ctypes.c_int64),
                                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "hf_batch_create": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _ip, _u, _i, ctypes.POINTER(_vp)]),
+    "hf_batch_set_rotations": (_i, [_vp, _i, _fp]),
+    "hf_batch_capture": (_i, [_vp, _i]),
+    "hf_batch_launch": (_i, [_vp, _vp]),
+    "hf_batch_fieldset": (_i, [_vp, _i, ctypes.POINTER(_vp)]),
+    "hf_batch_slots": (_i, [_vp]),
+    "hf_batch_release": (None, [_vp]),
+    "hf_autotune": (_i, [_vp, _i, ctypes.c_char_p, _ip, _ip, ctypes.POINTER(ctypes.c_double)]),
+    "hf_tune_set": (_i, [_vp, _i, _i, _i]),
+    "hf_tune_get": (_i, [_vp, _i, _ip, _ip, ctypes.POINTER(ctypes.c_double)]),
 }
 
 

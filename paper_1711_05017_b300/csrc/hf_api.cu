@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "hf.h"
@@ -54,8 +55,17 @@ enum ProfKind { kSplat, kPassA, kPassB, kPassBFwd, kPassC, kTorque, kQuery, kRes
 static const char *kProfNames[kProfKinds] = {"splat",  "passA", "passB", "passB_fwd",
                                              "passC",  "torque", "query", "resample"};
 
+struct Tune {  // the autotuner's choice for one grid size
+    bool set = false;
+    int chunk = 0;
+    int pencil = 0;
+    double rot_per_s = 0;
+};
+static int tune_slot(int n) { return n == 32 ? 0 : n == 64 ? 1 : n == 96 ? 2 : n == 128 ? 3 : 4; }
+
 struct hf_ctx {
     int device = 0;
+    Tune tune[5];
     size_t budget = 0, reserved = 0;
     std::mutex mu;
     cudaStream_t qstream = nullptr;             // high-priority stream for hf_query
@@ -110,6 +120,7 @@ struct hf_fieldset {
     double *d_P64 = nullptr;     // R x 18
     int chunk = 1;
     int lanes = 1;  // pipelines used by compute (HF_LANES=2 alternates chunks over two)
+    bool pencil = false;  // pencil pipeline (x/y stages as separate kernels) instead of slab passes
     bool ready = false;
     size_t bytes = 0;
     cudaStream_t mem_stream = nullptr;  // non-null: stream-ordered device memory, pageable staging
@@ -148,6 +159,9 @@ template <class F>
 static cudaError_t timed(hf_ctx *c, int kind, cudaStream_t st, F &&fn) {
     (void)cudaGetLastError();
     if (!c || !c->prof) return fn();
+    // launches recorded into a graph are not timed: their events never run
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return fn();
     std::lock_guard<std::mutex> g(c->pmu);
     cudaEvent_t a = prof_event(c), b = prof_event(c);
     if (!a || !b) return fn();
@@ -559,7 +573,7 @@ int default_chunk(int n) {
 // ---------------------------------------------------------------- fieldsets
 static size_t fieldset_bytes(int n, int R, unsigned flags, int chunk, int lanes);
 // intermediates per rotation: 3 half spectra for the slab passes, 5 for the pencil pipeline
-static size_t fields_spectra(int n) { return hf::pencil_n(n) ? 5 : 3; }
+static size_t fields_spectra(bool pencil) { return pencil ? 5 : 3; }
 
 static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags, cudaStream_t mem_stream,
                                       hf_fieldset **out);
@@ -596,14 +610,24 @@ static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags,
     if (flags & HF_T)
         for (int f = 4; f <= 6; ++f) fs->slot[f] = nf++;
     fs->nf = nf;
-    fs->chunk = std::min(default_chunk(n), R);
+    fs->pencil = hf::pencil_n(n);
+    fs->chunk = default_chunk(n);
+    {
+        const Tune &t = ctx->tune[tune_slot(n)];
+        const char *ev = getenv("HF_ROT_CHUNK");
+        if (t.set && !(ev && atoi(ev) > 0)) {
+            fs->chunk = t.chunk;
+            fs->pencil = t.pencil || n >= 256;
+        }
+    }
+    fs->chunk = std::min(fs->chunk, R);
     {
         const char *ev = getenv("HF_LANES");
         fs->lanes = (ev && atoi(ev) == 2) ? 2 : 1;
     }
     const size_t n3 = (size_t)n * n * n;
     const size_t data_b = (size_t)R * nf * n3 * sizeof(float);
-    const size_t scr_b = fields_spectra(n) * (size_t)fs->chunk * hf::half_spec_elems(n) * sizeof(float2);
+    const size_t scr_b = fields_spectra(fs->pencil) * (size_t)fs->chunk * hf::half_spec_elems(n) * sizeof(float2);
     const size_t planes_b = (size_t)fs->chunk * n3 * sizeof(float);
     fs->stage_bytes = (size_t)R * (9 * sizeof(float) + 4 * sizeof(double) + 6 * sizeof(int) + 18 * sizeof(float) +
                                    18 * sizeof(double));
@@ -651,7 +675,7 @@ static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags,
 static size_t fieldset_bytes(int n, int R, unsigned flags, int chunk, int lanes) {
     const int nf = 4 + ((flags & HF_T) ? 3 : 0);
     const size_t n3 = (size_t)n * n * n;
-    const size_t scr_b = fields_spectra(n) * (size_t)chunk * hf::half_spec_elems(n) * sizeof(float2);
+    const size_t scr_b = fields_spectra(hf::pencil_n(n)) * (size_t)chunk * hf::half_spec_elems(n) * sizeof(float2);
     const size_t planes_b = (size_t)chunk * n3 * sizeof(float);
     const size_t stage = (size_t)R * (9 * sizeof(float) + 4 * sizeof(double) + 6 * sizeof(int) + 18 * sizeof(float) +
                                       18 * sizeof(double));
@@ -693,7 +717,10 @@ extern "C" void hf_fieldset_release(hf_fieldset *fs) {
     delete fs;
 }
 
+int hf_ctx_device(const hf_ctx *c) { return c ? c->device : 0; }
 bool hf_fieldset_is_ready(const hf_fieldset *fs) { return fs && fs->ready; }
+void hf_fieldset_mark_ready(hf_fieldset *fs) { fs->ready = true; }
+double *hf_fieldset_device_quats(hf_fieldset *fs) { return fs->d_quat; }
 
 extern "C" int hf_fieldset_n(const hf_fieldset *fs) { return fs ? fs->n : 0; }
 extern "C" int hf_fieldset_rotations(const hf_fieldset *fs) { return fs ? fs->R : 0; }
@@ -701,10 +728,11 @@ extern "C" unsigned hf_fieldset_flags(const hf_fieldset *fs) { return fs ? fs->f
 
 // the energy/force passes for `cnt` rotations whose float matrices are at
 // rot9 (cnt x 9, device); outputs through `out` (first rotation at out.E)
-static hf_status run_fields(hf_ctx *c, int n, const hf_part *s1, const hf_part *s2, const float *rot9, int cnt,
-                            float2 *scratch, size_t scratch_rot, float *planes, FieldPtrs out, cudaStream_t st) {
+static hf_status run_fields(hf_ctx *c, int n, bool pencil, const hf_part *s1, const hf_part *s2, const float *rot9,
+                            int cnt, float2 *scratch, size_t scratch_rot, float *planes, FieldPtrs out,
+                            cudaStream_t st) {
     float2 *X1 = scratch, *Y1 = scratch + scratch_rot, *Y2 = scratch + 2 * scratch_rot;
-    if (hf::pencil_n(n)) {
+    if (pencil) {
         float2 *A = scratch + 3 * scratch_rot, *B = scratch + 4 * scratch_rot;
         if (s2->tex)
             CU(timed(c, kResample, st, [&] { return hf::run_resample_tex(n, s2->tex, rot9, planes, cnt, st); }));
@@ -735,56 +763,45 @@ static hf_status check_pair(const hf_part *s1, const hf_part *s2, int n, const c
     return HF_OK;
 }
 
-extern "C" hf_status hf_fieldset_compute(hf_ctx *ctx, const hf_part *s1, const hf_part *s2, const float *h_quat,
-                                         int R, hf_fieldset *fs, hf_stream stream) {
-    if (!ctx || !fs || !h_quat) return fail(HF_EINVAL, "hf_fieldset_compute: NULL argument");
-    if (R != fs->R) return fail(HF_EINVAL, "hf_fieldset_compute: R=%d but the set holds %d", R, fs->R);
-    hf_status s = check_pair(s1, s2, fs->n, "hf_fieldset_compute");
-    if (s != HF_OK) return s;
-    CU(cudaSetDevice(ctx->device));
-    cudaStream_t st = (cudaStream_t)stream;
-    const int n = fs->n;
+// Host preparation of a rotation set: normalised quaternions, float32
+// matrices and (with torque) the neighbours and float64 least-squares
+// operators.  Returns the number of rank-deficient rotations, or -1 when a
+// quaternion is zero or not finite.
+int hf_prepare_rotations(const float *h_quat, int R, bool torque, std::vector<float> &rot9, std::vector<double> &q64,
+                         std::vector<int> &nbr, std::vector<float> &P32, std::vector<double> &P64) {
     std::vector<Quat> Q(R);
     for (int r = 0; r < R; ++r) {
         Q[r] = qnorm(h_quat + 4 * (size_t)r);
-        if (!qfinite(Q[r])) return fail(HF_EINVAL, "hf_fieldset_compute: quaternion %d is zero or not finite", r);
+        if (!qfinite(Q[r])) return -1;
     }
-    int bad = 0;
-    std::vector<int> nbr;
-    std::vector<float> P32;
-    std::vector<double> P64;
-    if (fs->flags & HF_T) bad = torque_setup(Q, nbr, P32, P64, nullptr);
-    // stage through pinned memory once the previous call's uploads are done
-    CU(cudaEventSynchronize(fs->stage_done));
-    float *s_rot = (float *)fs->h_stage;
-    double *s_q = (double *)(s_rot + (size_t)9 * R);
-    int *s_nbr = (int *)(s_q + (size_t)4 * R);
-    float *s_P = (float *)(s_nbr + (size_t)6 * R);
-    double *s_P64 = (double *)(s_P + (size_t)18 * R);
+    rot9.resize((size_t)R * 9);
+    q64.resize((size_t)R * 4);
     for (int r = 0; r < R; ++r) {
         double M[9];
         rot_from_quat(Q[r], M);
-        for (int k = 0; k < 9; ++k) s_rot[(size_t)9 * r + k] = (float)M[k];
-        s_q[4 * (size_t)r + 0] = Q[r].w;
-        s_q[4 * (size_t)r + 1] = Q[r].x;
-        s_q[4 * (size_t)r + 2] = Q[r].y;
-        s_q[4 * (size_t)r + 3] = Q[r].z;
+        for (int k = 0; k < 9; ++k) rot9[(size_t)9 * r + k] = (float)M[k];
+        q64[4 * (size_t)r + 0] = Q[r].w;
+        q64[4 * (size_t)r + 1] = Q[r].x;
+        q64[4 * (size_t)r + 2] = Q[r].y;
+        q64[4 * (size_t)r + 3] = Q[r].z;
     }
-    fs->ready = false;
-    CU(cudaMemcpyAsync(fs->d_rot9, s_rot, (size_t)R * 9 * sizeof(float), cudaMemcpyHostToDevice, st));
-    CU(cudaMemcpyAsync(fs->d_quat, s_q, (size_t)R * 4 * sizeof(double), cudaMemcpyHostToDevice, st));
-    if (fs->flags & HF_T) {
-        memcpy(s_nbr, nbr.data(), nbr.size() * sizeof(int));
-        memcpy(s_P, P32.data(), P32.size() * sizeof(float));
-        memcpy(s_P64, P64.data(), P64.size() * sizeof(double));
-        CU(cudaMemcpyAsync(fs->d_nbr, s_nbr, nbr.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-        CU(cudaMemcpyAsync(fs->d_P, s_P, P32.size() * sizeof(float), cudaMemcpyHostToDevice, st));
-        CU(cudaMemcpyAsync(fs->d_P64, s_P64, P64.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-    }
-    CU(cudaEventRecord(fs->stage_done, st));
+    return torque ? torque_setup(Q, nbr, P32, P64, nullptr) : 0;
+}
+
+// Device part of a field-set build: every launch, nothing else (so that it
+// can be captured in a CUDA graph).  Rotation data comes from the given
+// device arrays; outputs go to fs.
+hf_status hf_set_launch(hf_ctx *ctx, const hf_part *s1, const hf_part *s2, hf_fieldset *fs, int R,
+                        const float *d_rot9, const int *d_nbr, const float *d_P, const double *d_P64,
+                        cudaStream_t st) {
+    const int n = fs->n;
+    if (R <= 0 || R > fs->R) return fail(HF_EINVAL, "field set holds %d rotations, %d asked", fs->R, R);
+    hf_status cs = check_pair(s1, s2, n, "field-set build");
+    if (cs != HF_OK) return cs;
     const size_t n3 = (size_t)n * n * n;
     const size_t rs = (size_t)fs->nf * n3;
     const size_t scr_rot = (size_t)fs->chunk * hf::half_spec_elems(n);
+    hf_status s;
     // with two pipelines: fork them off the caller's stream, alternate
     // chunks, join; with one: run on the caller's stream
     if (fs->lanes == 2) {
@@ -802,8 +819,8 @@ extern "C" hf_status hf_fieldset_compute(hf_ctx *ctx, const hf_part *s1, const h
         out.Fx = base + n3;
         out.Fy = base + 2 * n3;
         out.Fz = base + 3 * n3;
-        s = run_fields(ctx, n, s1, s2, fs->d_rot9 + (size_t)9 * r0, cnt, fs->scratch[l], scr_rot, fs->planes[l], out,
-                       fs->lanes == 2 ? fs->lane[l] : st);
+        s = run_fields(ctx, n, fs->pencil, s1, s2, d_rot9 + (size_t)9 * r0, cnt, fs->scratch[l], scr_rot,
+                       fs->planes[l], out, fs->lanes == 2 ? fs->lane[l] : st);
         if (s != HF_OK) return s;
     }
     for (int l = 0; l < 2 && fs->lanes == 2; ++l) {
@@ -812,10 +829,49 @@ extern "C" hf_status hf_fieldset_compute(hf_ctx *ctx, const hf_part *s1, const h
     }
     if (fs->flags & HF_T) {
         CU(timed(ctx, kTorque, st, [&] {
-            return hf::run_torque(n, R, fs->data, rs, fs->data + (size_t)fs->slot[4] * n3, rs, fs->d_nbr, fs->d_P,
-                                  fs->d_P64, (fs->flags & HF_TORQUE_F64) != 0, st);
+            return hf::run_torque(n, R, fs->data, rs, fs->data + (size_t)fs->slot[4] * n3, rs, d_nbr, d_P, d_P64,
+                                  (fs->flags & HF_TORQUE_F64) != 0, st);
         }));
     }
+    return HF_OK;
+}
+
+extern "C" hf_status hf_fieldset_compute(hf_ctx *ctx, const hf_part *s1, const hf_part *s2, const float *h_quat,
+                                         int R, hf_fieldset *fs, hf_stream stream) {
+    if (!ctx || !fs || !h_quat) return fail(HF_EINVAL, "hf_fieldset_compute: NULL argument");
+    if (R != fs->R) return fail(HF_EINVAL, "hf_fieldset_compute: R=%d but the set holds %d", R, fs->R);
+    hf_status s = check_pair(s1, s2, fs->n, "hf_fieldset_compute");
+    if (s != HF_OK) return s;
+    CU(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<float> rot9, P32;
+    std::vector<double> q64, P64;
+    std::vector<int> nbr;
+    const int bad = hf_prepare_rotations(h_quat, R, (fs->flags & HF_T) != 0, rot9, q64, nbr, P32, P64);
+    if (bad < 0) return fail(HF_EINVAL, "hf_fieldset_compute: a quaternion is zero or not finite");
+    // stage through the set's staging buffer once the previous call's uploads are done
+    CU(cudaEventSynchronize(fs->stage_done));
+    float *s_rot = (float *)fs->h_stage;
+    double *s_q = (double *)(s_rot + (size_t)9 * R);
+    int *s_nbr = (int *)(s_q + (size_t)4 * R);
+    float *s_P = (float *)(s_nbr + (size_t)6 * R);
+    double *s_P64 = (double *)(s_P + (size_t)18 * R);
+    memcpy(s_rot, rot9.data(), rot9.size() * sizeof(float));
+    memcpy(s_q, q64.data(), q64.size() * sizeof(double));
+    fs->ready = false;
+    CU(cudaMemcpyAsync(fs->d_rot9, s_rot, (size_t)R * 9 * sizeof(float), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(fs->d_quat, s_q, (size_t)R * 4 * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (fs->flags & HF_T) {
+        memcpy(s_nbr, nbr.data(), nbr.size() * sizeof(int));
+        memcpy(s_P, P32.data(), P32.size() * sizeof(float));
+        memcpy(s_P64, P64.data(), P64.size() * sizeof(double));
+        CU(cudaMemcpyAsync(fs->d_nbr, s_nbr, nbr.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        CU(cudaMemcpyAsync(fs->d_P, s_P, P32.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+        CU(cudaMemcpyAsync(fs->d_P64, s_P64, P64.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    }
+    CU(cudaEventRecord(fs->stage_done, st));
+    s = hf_set_launch(ctx, s1, s2, fs, R, fs->d_rot9, fs->d_nbr, fs->d_P, fs->d_P64, st);
+    if (s != HF_OK) return s;
     fs->ready = true;
     if (bad) return fail(HF_EINVAL, "hf_fieldset_compute: %d rotation(s) with a rank-deficient neighbourhood", bad);
     return HF_OK;
@@ -960,7 +1016,7 @@ extern "C" hf_status hf_rfft3d(int n, const float *d_in, float *d_out, void *d_s
 extern "C" size_t hf_fields_scratch_bytes(int n) {
     if (!hf::supported_n(n)) return 0;
     const size_t n3 = (size_t)n * n * n;
-    return fields_spectra(n) * hf::half_spec_elems(n) * sizeof(float2) + 4 * n3 * sizeof(float) + 256;
+    return fields_spectra(hf::pencil_n(n)) * hf::half_spec_elems(n) * sizeof(float2) + 4 * n3 * sizeof(float) + 256;
 }
 
 extern "C" hf_status hf_fields(hf_ctx *ctx, const hf_part *s1, const hf_part *s2, const float h_quat[4], float *d_E,
@@ -974,7 +1030,7 @@ extern "C" hf_status hf_fields(hf_ctx *ctx, const hf_part *s1, const hf_part *s2
     cudaStream_t st = (cudaStream_t)stream;
     const size_t he = hf::half_spec_elems(n), n3 = (size_t)n * n * n;
     float2 *scr = (float2 *)d_scratch;
-    float *dummy = (float *)(scr + fields_spectra(n) * he);
+    float *dummy = (float *)(scr + fields_spectra(hf::pencil_n(n)) * he);
     float *planes = dummy + 3 * n3;
     float *rot = planes + n3;
     const Quat q = qnorm(h_quat);
@@ -985,7 +1041,7 @@ extern "C" hf_status hf_fields(hf_ctx *ctx, const hf_part *s1, const hf_part *s2
     for (int k = 0; k < 9; ++k) m9[k] = (float)M[k];
     CU(cudaMemcpyAsync(rot, m9, sizeof m9, cudaMemcpyHostToDevice, st));
     FieldPtrs out{d_E, d_Fx ? d_Fx : dummy, d_Fy ? d_Fy : dummy + n3, d_Fz ? d_Fz : dummy + 2 * n3, 0};
-    s = run_fields(ctx, n, s1, s2, rot, 1, scr, he, planes, out, st);
+    s = run_fields(ctx, n, hf::pencil_n(n), s1, s2, rot, 1, scr, he, planes, out, st);
     if (s != HF_OK) return s;
     CU(cudaStreamSynchronize(st));  // m9 lives on this stack frame
     return HF_OK;
@@ -1025,5 +1081,192 @@ extern "C" hf_status hf_torque(hf_ctx *ctx, int n, int R, const float *h_quat, c
     CU(cudaFreeAsync(d_P64, st));
     CU(cudaStreamSynchronize(st));  // the host vectors are freed on return
     if (bad) return fail(HF_EINVAL, "hf_torque: %d rotation(s) with a rank-deficient neighbourhood", bad);
+    return HF_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+// Choice of rotation chunk (rotations per launch of each pass) and pipeline
+// (slab passes or the pencil pipeline) for one grid size, by timing a build of
+// E and F on synthetic parts.  Timing does not depend on the densities'
+// values: the passes do the same work for any input.
+extern "C" hf_status hf_tune_set(hf_ctx *ctx, int n, int chunk, int pencil) {
+    if (!ctx) return fail(HF_EINVAL, "hf_tune_set: ctx is NULL");
+    if (!hf::supported_n(n)) return fail(HF_EUNSUPPORTED, "hf_tune_set: N=%d not supported", n);
+    Tune &t = ctx->tune[tune_slot(n)];
+    if (chunk <= 0) {  // back to the built-in choice
+        t = Tune();
+        return HF_OK;
+    }
+    if (n >= 256 && !pencil) return fail(HF_EUNSUPPORTED, "hf_tune_set: N=256 runs the pencil pipeline only");
+    t.set = true;
+    t.chunk = chunk;
+    t.pencil = pencil != 0;
+    return HF_OK;
+}
+
+extern "C" hf_status hf_tune_get(const hf_ctx *ctx, int n, int *chunk, int *pencil, double *rot_per_s) {
+    if (!ctx || !chunk || !pencil) return fail(HF_EINVAL, "hf_tune_get: NULL argument");
+    if (!hf::supported_n(n)) return fail(HF_EUNSUPPORTED, "hf_tune_get: N=%d not supported", n);
+    const Tune &t = ctx->tune[tune_slot(n)];
+    *chunk = t.set ? t.chunk : default_chunk(n);
+    *pencil = t.set ? (int)t.pencil : (int)(hf::pencil_n(n));
+    if (rot_per_s) *rot_per_s = t.set ? t.rot_per_s : 0.0;
+    return HF_OK;
+}
+
+namespace {
+std::string tune_device_key(int device) {
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, device) != cudaSuccess) return "unknown";
+    std::string k = p.name;
+    for (auto &ch : k)
+        if (ch == ' ' || ch == '\t') ch = '_';
+    return k + "_sm" + std::to_string(p.major) + std::to_string(p.minor);
+}
+
+// cache lines: "<device> <n> <chunk> <pencil> <rot_per_s>"
+bool tune_cache_read(const char *path, const std::string &dev, int n, Tune &t) {
+    FILE *f = fopen(path, "r");
+    if (!f) return false;
+    char d[256];
+    int nn, c, pe;
+    double r;
+    bool hit = false;
+    while (fscanf(f, "%255s %d %d %d %lf", d, &nn, &c, &pe, &r) == 5)
+        if (dev == d && nn == n && c > 0) {
+            t.set = true;
+            t.chunk = c;
+            t.pencil = pe != 0;
+            t.rot_per_s = r;
+            hit = true;
+        }
+    fclose(f);
+    return hit;
+}
+
+bool tune_cache_write(const char *path, const std::string &dev, int n, const Tune &t) {
+    std::vector<std::string> keep;
+    if (FILE *f = fopen(path, "r")) {
+        char line[512];
+        while (fgets(line, sizeof line, f)) {
+            char d[256];
+            int nn;
+            if (sscanf(line, "%255s %d", d, &nn) == 2 && dev == d && nn == n) continue;
+            keep.emplace_back(line);
+        }
+        fclose(f);
+    }
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "w");
+    if (!f) return false;
+    for (auto &l : keep) fputs(l.c_str(), f);
+    fprintf(f, "%s %d %d %d %.6g\n", dev.c_str(), n, t.chunk, t.pencil ? 1 : 0, t.rot_per_s);
+    const bool ok = fclose(f) == 0;
+    return ok && rename(tmp.c_str(), path) == 0;
+}
+
+// a smooth synthetic density: a few periodic bumps
+std::vector<float> tune_grid(int n, int seed) {
+    std::vector<float> g((size_t)n * n * n);
+    const double w = 2.0 * M_PI / n;
+    for (int z = 0; z < n; ++z)
+        for (int y = 0; y < n; ++y)
+            for (int x = 0; x < n; ++x) {
+                const double v = cos(w * (x + seed)) * cos(2 * w * y) + 0.5 * sin(3 * w * (z - seed));
+                g[((size_t)z * n + y) * n + x] = (float)(v > 0 ? v : 0);
+            }
+    return g;
+}
+}  // namespace
+
+extern "C" hf_status hf_autotune(hf_ctx *ctx, int n, const char *cache_path, int *chunk_out, int *pencil_out,
+                                 double *rot_per_s_out) {
+    if (!ctx) return fail(HF_EINVAL, "hf_autotune: ctx is NULL");
+    if (!hf::supported_n(n)) return fail(HF_EUNSUPPORTED, "hf_autotune: N=%d not supported", n);
+    CU(cudaSetDevice(ctx->device));
+    const std::string dev = tune_device_key(ctx->device);
+    Tune best;
+    if (cache_path && *cache_path && tune_cache_read(cache_path, dev, n, best)) {
+        ctx->tune[tune_slot(n)] = best;
+    } else {
+        // rotations per timed build: at least two launches of the largest candidate
+        const int R = n <= 32 ? 1024 : n <= 64 ? 512 : n <= 96 ? 192 : n <= 128 ? 256 : 16;
+        const int chunks[] = {4, 8, 12, 16, 24, 32, 48, 64, 96, 128, 256};
+        const size_t n3 = (size_t)n * n * n;
+        float *d_g = nullptr;
+        CU(cudaMalloc(&d_g, 2 * n3 * sizeof(float)));
+        std::vector<float> h1 = tune_grid(n, 1), h2 = tune_grid(n, 5);
+        hf_part *s1 = nullptr, *s2 = nullptr;
+        cudaError_t ce = cudaMemcpy(d_g, h1.data(), n3 * sizeof(float), cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess) ce = cudaMemcpy(d_g + n3, h2.data(), n3 * sizeof(float), cudaMemcpyHostToDevice);
+        hf_status s = ce == cudaSuccess ? HF_OK : HF_ECUDA;
+        if (s == HF_OK) s = hf_part_create(ctx, n, d_g, HF_STATIONARY, &s1, nullptr);
+        if (s == HF_OK) s = hf_part_create(ctx, n, d_g + n3, HF_MOVING, &s2, nullptr);
+        if (s == HF_OK) ce = cudaDeviceSynchronize();
+        cudaFree(d_g);
+        if (s != HF_OK || ce != cudaSuccess) {
+            hf_part_release(s1);
+            hf_part_release(s2);
+            return s != HF_OK ? s : fail(HF_ECUDA, "hf_autotune: %s", cudaGetErrorString(ce));
+        }
+        std::vector<float> quats((size_t)R * 4);
+        for (int r = 0; r < R; ++r) {  // evenly spread unit quaternions (any rotations do)
+            const double a = 0.61803398875 * r, b = 0.7548776662 * r, c = 0.5698402910 * r;
+            quats[4 * r + 0] = (float)(1.0 + cos(2 * M_PI * a));
+            quats[4 * r + 1] = (float)sin(2 * M_PI * b);
+            quats[4 * r + 2] = (float)cos(2 * M_PI * c);
+            quats[4 * r + 3] = (float)(0.3 + sin(2 * M_PI * (a + c)));
+        }
+        const Tune saved = ctx->tune[tune_slot(n)];
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        for (int pencil = 0; pencil <= 1; ++pencil) {
+            if (n >= 256 && !pencil) continue;
+            for (int chunk : chunks) {
+                if (2 * chunk > R) continue;
+                Tune &t = ctx->tune[tune_slot(n)];
+                t.set = true;
+                t.chunk = chunk;
+                t.pencil = pencil != 0;
+                hf_fieldset *fs = nullptr;
+                if (hf_fieldset_create(ctx, n, R, HF_E | HF_F, &fs) != HF_OK) continue;  // does not fit
+                // one untimed build, then the best of three
+                float best_ms = 1e30f;
+                hf_status bs = hf_fieldset_compute(ctx, s1, s2, quats.data(), R, fs, nullptr);
+                for (int rep = 0; rep < 3 && bs == HF_OK; ++rep) {
+                    cudaEventRecord(e0, nullptr);
+                    bs = hf_fieldset_compute(ctx, s1, s2, quats.data(), R, fs, nullptr);
+                    cudaEventRecord(e1, nullptr);
+                    float ms = 0;
+                    if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+                        best_ms = std::min(best_ms, ms);
+                }
+                hf_fieldset_release(fs);
+                if (bs == HF_OK && best_ms < 1e29f) {
+                    const double rps = R / (best_ms * 1e-3);
+                    if (rps > best.rot_per_s) {
+                        best = t;
+                        best.rot_per_s = rps;
+                    }
+                }
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        hf_part_release(s1);
+        hf_part_release(s2);
+        (void)cudaGetLastError();
+        if (!best.set) {
+            ctx->tune[tune_slot(n)] = saved;
+            return fail(HF_ENOMEM, "hf_autotune: no candidate fitted for N=%d", n);
+        }
+        ctx->tune[tune_slot(n)] = best;
+        if (cache_path && *cache_path && !tune_cache_write(cache_path, dev, n, best))
+            return fail(HF_EINVAL, "hf_autotune: cannot write the cache file %s", cache_path);
+    }
+    if (chunk_out) *chunk_out = best.chunk;
+    if (pencil_out) *pencil_out = best.pencil ? 1 : 0;
+    if (rot_per_s_out) *rot_per_s_out = best.rot_per_s;
     return HF_OK;
 }

@@ -4,6 +4,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "hf.h"
 
 namespace hf {
@@ -96,8 +98,20 @@ cudaError_t run_query_one(const QueryGeom &g, Pose7 pose, int k, float *out, cud
 // hf_api.cu: one pose query on a caller-provided lane (a stream and a mapped
 // pinned 7-float answer mailbox with its device alias); synchronous
 struct hf_fieldset;
+int hf_ctx_device(const hf_ctx *c);
 // whether the set's last compute enqueued all of its work
 bool hf_fieldset_is_ready(const hf_fieldset *fs);
+void hf_fieldset_mark_ready(hf_fieldset *fs);
+double *hf_fieldset_device_quats(hf_fieldset *fs);
+// host preparation of a rotation set (float32 matrices, normalised float64
+// quaternions, torque neighbours and operators); -1 for a bad quaternion,
+// else the number of rank-deficient neighbourhoods
+int hf_prepare_rotations(const float *h_quat, int R, bool torque, std::vector<float> &rot9, std::vector<double> &q64,
+                         std::vector<int> &nbr, std::vector<float> &P32, std::vector<double> &P64);
+// launches of a build for the first R rotations of fs from device rotation data
+hf_status hf_set_launch(hf_ctx *ctx, const hf_part *s1, const hf_part *s2, hf_fieldset *fs, int R,
+                        const float *d_rot9, const int *d_nbr, const float *d_P, const double *d_P64,
+                        cudaStream_t st);
 // a field set whose device memory is allocated and freed in stream order on
 // `st` (no device-wide synchronisation on create or release)
 hf_status hf_fieldset_create_stream_ordered(hf_ctx *ctx, int n, int R, unsigned flags, cudaStream_t st,
