@@ -80,6 +80,11 @@ typedef void *hf_stream; /* a cudaStream_t */
 #define HF_F 0x2u           /* force field (3 components) per rotation (always held) */
 #define HF_T 0x4u           /* torque field (3 components) per rotation */
 #define HF_TORQUE_F64 0x10u /* torque differences and products in float64 on the device */
+/* Precision variant (N = 256 only): the y-axis DFT stages run on the tensor
+ * cores as 16 x 16 DFT-matrix GEMMs with operands split into hi + lo parts in
+ * BF16 or FP16 and FP32 accumulation; every other stage stays FP32. */
+#define HF_PREC_SPLIT_BF16 0x20u
+#define HF_PREC_SPLIT_F16 0x40u
 
 /* Field indices for hf_fieldset_get / hf_fieldset_field_ptr and query outputs. */
 #define HF_FIELD_E 0
@@ -130,8 +135,10 @@ int hf_part_n(const hf_part *part);
 hf_status hf_part_update(hf_part *part, const float *d_grid, hf_stream stream);
 
 /* Allocate a field set for R rotations at grid size n holding the fields
- * selected by `flags` (energy and force always; HF_T adds torque).  Bytes: R * N^3 * 4 * (#fields)
- * plus per-set scratch.  Errors: HF_EINVAL, HF_EBUDGET, HF_ENOMEM. */
+ * selected by `flags` (energy and force always; HF_T adds torque; at most one
+ * of HF_PREC_SPLIT_BF16 / HF_PREC_SPLIT_F16, N = 256 only, else
+ * HF_EUNSUPPORTED).  Bytes: R * N^3 * 4 * (#fields) plus per-set scratch.
+ * Errors: HF_EINVAL, HF_EBUDGET, HF_ENOMEM, HF_EUNSUPPORTED. */
 hf_status hf_fieldset_create(hf_ctx *ctx, int n, int R, unsigned flags, hf_fieldset **out);
 
 /* Compute the fields of `fs` for the rotations h_quat (R x 4, w x y z, host,
@@ -296,13 +303,20 @@ hf_status hf_autotune(hf_ctx *ctx, int n, const char *cache_path, int *chunk, in
 hf_status hf_tune_set(hf_ctx *ctx, int n, int chunk, int pencil);
 hf_status hf_tune_get(const hf_ctx *ctx, int n, int *chunk, int *pencil, double *rot_per_s);
 
+/* Number of tensor-core stage thread blocks whose bounded wait for their own
+ * matrix operations gave up since the last reset (each such block wrote no
+ * output: the field set computed with it is invalid); -1 if it cannot be read.
+ * Synchronous (reads device memory). */
+int hf_tc_timeouts(int reset);
+
 /* ---- per-kernel timing (CUDA events on the launching stream) ----
  * While enabled, every kernel launch the context's calls make is bracketed by
  * a pair of CUDA events on its stream.  hf_profile_read synchronises the
  * recorded events and accumulates, per kernel kind, the launch count and the
  * summed device time; hf_profile_entry reads kind i (0 <= i < the count
  * returned); hf_profile_reset clears the totals.  Kinds: "splat", "passA",
- * "passB", "passB_fwd", "passC", "torque", "query", "resample". */
+ * "passB", "passB_fwd", "passC", "torque", "query", "resample", "y_tc"
+ * (the tensor-core y stages of the precision variant). */
 hf_status hf_profile_enable(hf_ctx *ctx, int on);
 int hf_profile_read(hf_ctx *ctx);
 hf_status hf_profile_entry(const hf_ctx *ctx, int i, const char **name, long long *launches,

@@ -11,7 +11,8 @@ import ctypes
 import numpy as np
 
 from . import _binding as B
-from ._binding import HF_E, HF_F, HF_MOVING, HF_STATIONARY, HF_T, HF_TORQUE_F64, HFError  # noqa: F401
+from ._binding import (HF_E, HF_F, HF_MOVING, HF_PREC_SPLIT_BF16, HF_PREC_SPLIT_F16, HF_STATIONARY,  # noqa: F401
+                       HF_T, HF_TORQUE_F64, HFError)
 
 __all__ = ["Context", "Part", "FieldSet", "Batch", "Server", "HFError", "resample", "rfft3d", "version"]
 

@@ -51,9 +51,9 @@ bool pencil_n(int n) {
     } while (0)
 
 // ------------------------------------------------------------------ handles
-enum ProfKind { kSplat, kPassA, kPassB, kPassBFwd, kPassC, kTorque, kQuery, kResample, kProfKinds };
-static const char *kProfNames[kProfKinds] = {"splat",  "passA", "passB", "passB_fwd",
-                                             "passC",  "torque", "query", "resample"};
+enum ProfKind { kSplat, kPassA, kPassB, kPassBFwd, kPassC, kTorque, kQuery, kResample, kYtc, kProfKinds };
+static const char *kProfNames[kProfKinds] = {"splat",  "passA", "passB",    "passB_fwd", "passC",
+                                             "torque", "query", "resample", "y_tc"};
 
 struct Tune {  // the autotuner's choice for one grid size
     bool set = false;
@@ -121,6 +121,7 @@ struct hf_fieldset {
     int chunk = 1;
     int lanes = 1;  // pipelines used by compute (HF_LANES=2 alternates chunks over two)
     bool pencil = false;  // pencil pipeline (x/y stages as separate kernels) instead of slab passes
+    int prec = hf::PREC_FP32;  // y stages on the tensor cores (pencil pipeline at N = 256)
     bool ready = false;
     size_t bytes = 0;
     cudaStream_t mem_stream = nullptr;  // non-null: stream-ordered device memory, pageable staging
@@ -226,6 +227,7 @@ static cudaError_t ensure_kernel_attrs() {
     if (done[dev]) return cudaSuccess;
     for (int n : {32, 64, 96, 128, 256})
         if ((e = hf::fft_init_attrs(n)) != cudaSuccess) return e;
+    if ((e = hf::set_tc_attrs()) != cudaSuccess) return e;
     done[dev] = true;
     return cudaSuccess;
 }
@@ -251,6 +253,7 @@ extern "C" hf_status hf_ctx_create(int device, size_t budget, hf_ctx **out) {
     if (e == cudaSuccess) e = cudaHostGetDevicePointer(&c->d_qout, c->h_qout, 0);
     for (int n : {32, 64, 96, 128, 256})
         if (e == cudaSuccess) e = hf::fft_init_attrs(n);
+    if (e == cudaSuccess) e = hf::set_tc_attrs();
     if (e != cudaSuccess) {
         hf_ctx_destroy(c);
         return fail(HF_ECUDA, "hf_ctx_create: %s", cudaGetErrorString(e));
@@ -270,6 +273,8 @@ extern "C" void hf_ctx_destroy(hf_ctx *c) {
 }
 
 extern "C" size_t hf_ctx_budget_bytes(const hf_ctx *c) { return c ? c->budget : 0; }
+
+extern "C" int hf_tc_timeouts(int reset) { return hf::tc_timeouts(reset != 0); }
 
 extern "C" size_t hf_ctx_reserved_bytes(const hf_ctx *c) {
     if (!c) return 0;
@@ -595,6 +600,10 @@ static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags,
     if (R <= 0) return fail(HF_EINVAL, "hf_fieldset_create: R=%d", R);
     flags |= HF_E | HF_F;  // energy and force are always held
     if ((flags & HF_T) && R < 7) return fail(HF_EINVAL, "hf_fieldset_create: torque needs R >= 7 (R=%d)", R);
+    const unsigned precf = flags & (HF_PREC_SPLIT_BF16 | HF_PREC_SPLIT_F16);
+    if (precf == (HF_PREC_SPLIT_BF16 | HF_PREC_SPLIT_F16))
+        return fail(HF_EINVAL, "hf_fieldset_create: at most one precision flag");
+    if (precf && n != 256) return fail(HF_EUNSUPPORTED, "hf_fieldset_create: split precision needs N=256 (N=%d)", n);
     CU(cudaSetDevice(ctx->device));
     hf_fieldset *fs = new (std::nothrow) hf_fieldset();
     if (!fs) return fail(HF_ENOMEM, "hf_fieldset_create: host allocation");
@@ -611,6 +620,8 @@ static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags,
         for (int f = 4; f <= 6; ++f) fs->slot[f] = nf++;
     fs->nf = nf;
     fs->pencil = hf::pencil_n(n);
+    fs->prec = (flags & HF_PREC_SPLIT_F16) ? hf::PREC_SPLIT_F16 : (flags & HF_PREC_SPLIT_BF16) ? hf::PREC_SPLIT_BF16
+                                                                                             : hf::PREC_FP32;
     fs->chunk = default_chunk(n);
     {
         const Tune &t = ctx->tune[tune_slot(n)];
@@ -728,9 +739,9 @@ extern "C" unsigned hf_fieldset_flags(const hf_fieldset *fs) { return fs ? fs->f
 
 // the energy/force passes for `cnt` rotations whose float matrices are at
 // rot9 (cnt x 9, device); outputs through `out` (first rotation at out.E)
-static hf_status run_fields(hf_ctx *c, int n, bool pencil, const hf_part *s1, const hf_part *s2, const float *rot9,
-                            int cnt, float2 *scratch, size_t scratch_rot, float *planes, FieldPtrs out,
-                            cudaStream_t st) {
+static hf_status run_fields(hf_ctx *c, int n, bool pencil, int prec, const hf_part *s1, const hf_part *s2,
+                            const float *rot9, int cnt, float2 *scratch, size_t scratch_rot, float *planes,
+                            FieldPtrs out, cudaStream_t st) {
     float2 *X1 = scratch, *Y1 = scratch + scratch_rot, *Y2 = scratch + 2 * scratch_rot;
     if (pencil) {
         float2 *A = scratch + 3 * scratch_rot, *B = scratch + 4 * scratch_rot;
@@ -739,9 +750,15 @@ static hf_status run_fields(hf_ctx *c, int n, bool pencil, const hf_part *s1, co
         else
             CU(timed(c, kResample, st, [&] { return hf::run_resample_chunk(n, s2->grid, rot9, planes, cnt, st); }));
         CU(timed(c, kPassA, st, [&] { return hf::run_xfwd(n, planes, A, cnt, st); }));
-        CU(timed(c, kPassA, st, [&] { return hf::run_yfwd(n, A, X1, cnt, st); }));
+        if (prec != hf::PREC_FP32)
+            CU(timed(c, kYtc, st, [&] { return hf::run_yfwd_tc(n, prec, A, X1, cnt, st); }));
+        else
+            CU(timed(c, kPassA, st, [&] { return hf::run_yfwd(n, A, X1, cnt, st); }));
         CU(timed(c, kPassB, st, [&] { return hf::run_passB(n, X1, s1->spec, Y1, Y2, cnt, st); }));
-        CU(timed(c, kPassC, st, [&] { return hf::run_yinv(n, Y1, Y2, A, X1, B, cnt, st); }));
+        if (prec != hf::PREC_FP32)
+            CU(timed(c, kYtc, st, [&] { return hf::run_yinv_tc(n, prec, Y1, Y2, A, X1, B, cnt, st); }));
+        else
+            CU(timed(c, kPassC, st, [&] { return hf::run_yinv(n, Y1, Y2, A, X1, B, cnt, st); }));
         CU(timed(c, kPassC, st, [&] { return hf::run_xinv(n, A, X1, B, out, cnt, st); }));
         return HF_OK;
     }
@@ -819,7 +836,7 @@ hf_status hf_set_launch(hf_ctx *ctx, const hf_part *s1, const hf_part *s2, hf_fi
         out.Fx = base + n3;
         out.Fy = base + 2 * n3;
         out.Fz = base + 3 * n3;
-        s = run_fields(ctx, n, fs->pencil, s1, s2, d_rot9 + (size_t)9 * r0, cnt, fs->scratch[l], scr_rot,
+        s = run_fields(ctx, n, fs->pencil, fs->prec, s1, s2, d_rot9 + (size_t)9 * r0, cnt, fs->scratch[l], scr_rot,
                        fs->planes[l], out, fs->lanes == 2 ? fs->lane[l] : st);
         if (s != HF_OK) return s;
     }
@@ -1041,7 +1058,7 @@ extern "C" hf_status hf_fields(hf_ctx *ctx, const hf_part *s1, const hf_part *s2
     for (int k = 0; k < 9; ++k) m9[k] = (float)M[k];
     CU(cudaMemcpyAsync(rot, m9, sizeof m9, cudaMemcpyHostToDevice, st));
     FieldPtrs out{d_E, d_Fx ? d_Fx : dummy, d_Fy ? d_Fy : dummy + n3, d_Fz ? d_Fz : dummy + 2 * n3, 0};
-    s = run_fields(ctx, n, hf::pencil_n(n), s1, s2, rot, 1, scr, he, planes, out, st);
+    s = run_fields(ctx, n, hf::pencil_n(n), hf::PREC_FP32, s1, s2, rot, 1, scr, he, planes, out, st);
     if (s != HF_OK) return s;
     CU(cudaStreamSynchronize(st));  // m9 lives on this stack frame
     return HF_OK;

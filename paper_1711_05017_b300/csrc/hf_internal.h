@@ -66,6 +66,17 @@ cudaError_t run_unpermute(int n, const float2 *spec, float2 *out, cudaStream_t s
 // then pass B, then Y1/Y2 -> Z_S, Z_Gy, Z_Gz (inverse y) -> fields (inverse x)
 cudaError_t run_xfwd(int n, const float *planes, float2 *Xa, int nrot, cudaStream_t st);
 cudaError_t run_yfwd(int n, const float2 *Xa, float2 *X1, int nrot, cudaStream_t st);
+// hf_tc.cu: the pencil pipeline's y stages as split hi/lo DFT-matrix GEMMs on
+// the tensor cores (N = 256 only); same inputs and outputs as run_yfwd /
+// run_yinv
+enum { PREC_FP32 = 0, PREC_SPLIT_BF16 = 1, PREC_SPLIT_F16 = 2 };
+cudaError_t run_yfwd_tc(int n, int prec, const float2 *Xa, float2 *X1, int nrot, cudaStream_t st);
+cudaError_t run_yinv_tc(int n, int prec, const float2 *Y1, const float2 *Y2, float2 *ZS, float2 *ZGy, float2 *ZGz,
+                        int nrot, cudaStream_t st);
+cudaError_t set_tc_attrs();
+// CTAs of the tensor-core stages whose bounded wait for their MMAs gave up
+// (their outputs are invalid); -1 if the counter cannot be read
+int tc_timeouts(bool reset);
 cudaError_t run_yinv(int n, const float2 *Y1, const float2 *Y2, float2 *ZS, float2 *ZGy, float2 *ZGz, int nrot,
                      cudaStream_t st);
 cudaError_t run_xinv(int n, const float2 *ZS, const float2 *ZGy, const float2 *ZGz, FieldPtrs out, int nrot,
