@@ -331,11 +331,15 @@ def run_ours(args, rank, world, local_rank):
                "sample": desc, "splat_s": round(t_splat, 2)}
 
     serving = batch = None
-    if rank == 0 and world == 1 and (args.serve_seconds > 0 or args.batch_steps > 0):
+    if rank == 0 and world == 1 and (args.serve_seconds > 0 or args.batch_steps > 0 or args.precision_rotations > 0):
         del fs
         torch.cuda.empty_cache()
     if rank == 0 and world == 1 and args.batch_steps > 0:
         batch = run_batch(args, local_rank)
+        torch.cuda.empty_cache()
+    precision = None
+    if rank == 0 and world == 1 and args.precision_rotations > 0:
+        precision = run_precision(args, local_rank)
         torch.cuda.empty_cache()
     if rank == 0 and world == 1 and args.serve_seconds > 0:
         serving = run_serving(args, local_rank)
@@ -361,6 +365,7 @@ def run_ours(args, rank, world, local_rank):
             "cpu_baseline": cpu,
             "clocks": clk.summary(),
             "batch": batch,
+            "precision": precision,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)
@@ -452,6 +457,140 @@ def run_batch(args, local_rank):
         v.release()
     del pairs
     return out
+
+
+# ------------------------------------------------------- precision variant
+def run_precision(args, local_rank):
+    """256^3, 20000 + 20000 skeleton points (radii U(0.01, 0.05)), 512
+    rotations, E+F: the plain FP32 pipeline against the y stages as split
+    BF16 / FP16 DFT-matrix GEMMs on the tensor cores.  Throughput per variant,
+    the tensor-core kernel against the tensor peak, error against the FP32
+    path on 2 rotations, and (--precision-oracle K) per-field error against
+    the FP64 oracle on rotations 0..K-1 of the same rotation set, for parts
+    splatted by the oracle from a 2000-point subset of each part."""
+    import torch
+    import paper_1711_05017_b300 as hf
+    from paper_1711_05017_b300 import _binding as B
+    dev = torch.device("cuda", local_rank)
+    n, R = 256, args.precision_rotations
+    s1, s2 = synth.c4_pair(0)
+    ctx = hf.Context(local_rank)
+    cu = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=dev)  # noqa: E731
+    g1 = ctx.density_build(n, cu(s1.pts), cu(s1.sigma))
+    g2 = ctx.density_build(n, cu(s2.pts), cu(s2.sigma))
+    p1, p2 = ctx.part(g1, hf.HF_STATIONARY), ctx.part(g2, hf.HF_MOVING)
+    q = synth.random_quaternions(0, R).astype(np.float32)
+    stream = torch.cuda.current_stream()
+    B.lib().hf_tc_timeouts(1)
+    variants = (("fp32", 0), ("split_bf16", hf.HF_PREC_SPLIT_BF16), ("split_f16", hf.HF_PREC_SPLIT_F16))
+    out, ref2 = {}, None
+    hbm_peak, _ = peaks()
+    _, tc_peak, tc_kind = tensor_peak()
+    for name, fl in variants:
+        fs = ctx.fieldset(n, R, hf.HF_E | hf.HF_F | fl)
+        fs.compute(p1, p2, q)
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        ctx.profile_read(reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 2
+        e0.record(stream)
+        for _ in range(reps):
+            fs.compute(p1, p2, q)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        prof = ctx.profile_read(reset=True)
+        ctx.profile(False)
+        f2 = np.stack([np.stack([fs.get(r, f).cpu().numpy().astype(np.float64) for f in range(4)]) for r in (0, 1)])
+        if ref2 is None:
+            ref2 = f2
+        v = {"value": round(R / (ms / 1e3), 1), "unit": UNIT, "ms_per_build": round(ms, 2),
+             "max_abs_err_vs_fp32_over_max": [float(np.abs(f2[:, f] - ref2[:, f]).max() / np.abs(ref2[:, f]).max())
+                                              for f in range(4)],
+             "kernels_avg_us": {k: round(t / c * 1e3, 1) for k, (c, t) in prof.items()}}
+        if "y_tc" in prof:
+            cnt, tot = prof["y_tc"]
+            chunk = ctx.tune_get(n)[0]
+            # tensor FLOPs issued per rotation: per 32-column tile 2 stages x
+            # 4 M tiles x 2 K steps x 3 products x (2 x 128 x 32 x 16), over
+            # 1032 tiles, for 1 forward and 3 inverse transforms
+            flops = 4 * 1032 * 48 * (2 * 128 * 32 * 16) * R * reps
+            ach = flops / (tot * 1e-3) / 1e12
+            # HBM bytes: forward reads and writes one half spectrum, the
+            # inverse reads S twice (S and Gy) and Gz once and writes three
+            spec = n * n * (n // 2 + 1) * 8
+            gbs = 8 * spec * R * reps / (tot * 1e-3) / 1e9
+            v["y_tc"] = {"launches": cnt, "tensor": {"achieved": round(ach, 1), "peak": tc_peak, "unit": "TFLOP/s",
+                                                     "frac": round(ach / tc_peak, 4), "peak_source": tc_kind},
+                         "hbm": {"achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                                 "frac": round(gbs / hbm_peak, 4)}, "chunk": chunk}
+        out[name] = v
+        fs.release()
+    out["tc_timeouts"] = B.lib().hf_tc_timeouts(0)
+    if args.precision_oracle > 0:
+        out["oracle_error"] = precision_oracle_error(ctx, hf, q[:args.precision_oracle], variants)
+    del p1, p2
+    return {"workload": f"256^3, 20000+20000 skeleton points (rings, segments, sheets; radii U(0.01,0.05)), "
+                        f"{R} random rotations, E+F fields", "variants": out}
+
+
+def tensor_peak():
+    """(bf16 burst, bf16 sustained, which) from the measured peaks; FP16
+    dense runs at the BF16 rate."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return m["bf16_tflops"], m["bf16_tflops_sustained"], "measured (bf16 sustained)"
+    except (OSError, KeyError, ValueError):
+        return 1800.0, 1400.0, "fallback (bf16 sustained)"
+
+
+def precision_oracle_error(ctx, hf, q, variants):
+    """Per-field max-abs and relative-L2 error of each variant against the
+    FP64 oracle, parts splatted by the oracle (2000-point subsets)."""
+    import torch
+    import oracle
+    n = 256
+    s1, s2 = synth.c4_pair(0)
+    sel = np.random.default_rng(5).choice(len(s1.pts), 2000, replace=False)
+    r1 = oracle.splat(n, s1.pts[sel], s1.sigma[sel])
+    r2 = oracle.splat(n, s2.pts[sel], s2.sigma[sel])
+    cu = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).cuda()  # noqa: E731
+    p1, p2 = ctx.part(cu(r1), hf.HF_STATIONARY), ctx.part(cu(r2), hf.HF_MOVING)
+    r1f, r2f = r1.astype(np.float32).astype(np.float64), r2.astype(np.float32).astype(np.float64)
+    K = len(q)
+    sets = {}
+    for name, fl in variants:
+        fs = ctx.fieldset(n, K, hf.HF_E | hf.HF_F | fl)
+        fs.compute(p1, p2, q)
+        sets[name] = fs
+    torch.cuda.synchronize()
+    acc = {name: {"max_abs": np.zeros(4), "l2_num": np.zeros(4)} for name, _ in variants}
+    ref_max, ref_l2 = np.zeros(4), np.zeros(4)
+    t0 = time.perf_counter()
+    for r in range(K):
+        qq = q[r].astype(np.float64)
+        qq /= np.linalg.norm(qq)
+        Rm = oracle.quat_to_rot(qq).astype(np.float32).astype(np.float64)
+        ref = np.stack(oracle.fields(r1f, oracle.resample(r2f, Rm)))
+        for f in range(4):
+            ref_max[f] = max(ref_max[f], np.abs(ref[f]).max())
+            ref_l2[f] += (ref[f] ** 2).sum()
+        for name, fs in sets.items():
+            for f in range(4):
+                d = fs.get(r, f).cpu().numpy().astype(np.float64) - ref[f]
+                acc[name]["max_abs"][f] = max(acc[name]["max_abs"][f], np.abs(d).max())
+                acc[name]["l2_num"][f] += (d ** 2).sum()
+    for fs in sets.values():
+        fs.release()
+    fields = ("E", "Fx", "Fy", "Fz")
+    res = {"rotations": K, "oracle_s": round(time.perf_counter() - t0, 1),
+           "parts": "2000-point subsets of the 20000-point parts, splatted by the oracle"}
+    for name in acc:
+        res[name] = {fields[f]: {"max_abs_over_max": float(acc[name]["max_abs"][f] / ref_max[f]),
+                                 "rel_l2": float(np.sqrt(acc[name]["l2_num"][f] / ref_l2[f]))} for f in range(4)}
+    return res
 
 
 # ------------------------------------------------------- serving workload
@@ -582,6 +721,10 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="built-in launch shapes instead of the autotuner's")
     ap.add_argument("--batch-steps", type=int, default=5,
                     help="graph launches of the 64-pair uneven batch (0 = skip)")
+    ap.add_argument("--precision-rotations", type=int, default=512,
+                    help="rotations of the 256^3 precision comparison (0 = skip)")
+    ap.add_argument("--precision-oracle", type=int, default=0,
+                    help="rotations checked against the FP64 oracle in the precision comparison (slow)")
     ap.add_argument("--serve-seconds", type=float, default=20.0,
                     help="length of the 16-session serving run (0 = skip)")
     args = ap.parse_args()
