@@ -350,10 +350,11 @@ __device__ __forceinline__ int xslot(int k) {
 template <int N>
 struct PassC {
     static constexpr int H = N / 2 + 1, HALF = N / 2;
-    static constexpr int PW = 2 * H + 1;  // plane pitch: S' at [0,H), Gy at [H,2H)
-    static constexpr int RB = (N >= 128) ? 64 : N / 2;  // rows per x batch
-    static constexpr int TP = N + 1;                    // row-buffer pitch
+    static constexpr int PW = H;  // plane pitch (odd): one half-spectrum plane at a time
+    static constexpr int RB = (N == 96) ? 48 : (N >= 64 ? 32 : 16);  // rows per x batch (divides N / 2)
+    static constexpr int TP = N + 1;                                  // row-buffer pitch
     static constexpr int NT = (N >= 128) ? 512 : (N >= 64 ? 256 : 128);
+    static constexpr int MINB = (N >= 128) ? 2 : 1;
     static constexpr size_t smem = sizeof(float2) * ((size_t)N * PW + (size_t)RB * TP + N) +
                                    sizeof(float4) * (size_t)N;
 };
@@ -374,16 +375,18 @@ __device__ __forceinline__ void build_xtable(float4 *xt) {
     }
 }
 
-// One complex inverse DFT of length N per row, input built from the
-// half-spectrum columns of the plane; real part -> out0, imaginary -> out1.
-// PAIR 0: Z[k] = S(k) (1 + pi kx~)              -> (E, Fx)
-// PAIR 1: Z[k] = -(Gy(k) + i Gz(k))             -> (Fy, Fz)
-// Rows [0, ROWS) of `plane` (pitch PW) go to output rows [0, ROWS), RB rows
-// per batch through the row buffer Tb (pitch TP).
+// One complex inverse DFT of length N per row, input built from half-spectrum
+// rows (pitch PW) by Hermitian symmetry; real part -> out0, imaginary -> out1.
+// PAIR 0: Z[k] = A(k) (1 + pi kx~)         -> (E, Fx) when A = S''
+// PAIR 1: Z[k] = -(B(k) + i A(k))          -> two real fields, -IDFT(B) and
+//         -IDFT(A), from two rows (of one field or of two)
+// Row j of A at planeA + j PW + colA, of B at planeB + j PW + colB; rows
+// [0, ROWS) go to output rows [0, ROWS), RB rows per batch through the row
+// buffer Tb (pitch TP).
 template <int N, int PAIR, int PW, int RB, int TP, int NT, int ROWS>
-__device__ __forceinline__ void x_pass(const float2 *plane, int colA, int colB, float2 *Tb,
-                                       const float2 *twN, const float4 *xt, float *__restrict__ out0,
-                                       float *__restrict__ out1) {
+__device__ __forceinline__ void x_pass(const float2 *planeA, const float2 *planeB, int colA, int colB,
+                                       float2 *Tb, const float2 *twN, const float4 *xt,
+                                       float *__restrict__ out0, float *__restrict__ out1) {
     constexpr int R1 = Fact<N>::R1, R2 = Fact<N>::R2;
 #pragma unroll 1
     for (int y0 = 0; y0 < ROWS; y0 += RB) {
@@ -391,17 +394,18 @@ __device__ __forceinline__ void x_pass(const float2 *plane, int colA, int colB, 
 #pragma unroll 1
         for (int w = threadIdx.x; w < RB * R1; w += NT) {
             const int row = w % RB, k1 = w / RB;
-            const float2 *pr = plane + (size_t)(y0 + row) * PW;
+            const float2 *pa = planeA + (size_t)(y0 + row) * PW + colA;
+            const float2 *pb = planeB + (size_t)(y0 + row) * PW + colB;
             float2 v[R2];
 #pragma unroll
             for (int k2 = 0; k2 < R2; ++k2) {
                 const float4 e = xt[k1 + R1 * k2];
                 const int sl = __float_as_int(e.x);
                 if constexpr (PAIR == 0) {
-                    const float2 a = pr[colA + sl];
+                    const float2 a = pa[sl];
                     v[k2] = make_float2(e.z * a.x, e.w * a.y);
                 } else {
-                    const float2 gy = pr[colB + sl], gz = pr[colA + sl];
+                    const float2 gy = pb[sl], gz = pa[sl];
                     v[k2] = make_float2(fmaf(e.y, gz.y, -gy.x), fmaf(-e.y, gy.y, -gz.x));  // -(gy + i gz)
                 }
             }
@@ -436,12 +440,27 @@ __device__ __forceinline__ void x_pass(const float2 *plane, int colA, int colB, 
     }
 }
 
+// Pass C holds one half-spectrum plane at a time (about 100 KB of shared
+// memory at 128^3, two CTAs per SM):
+//   S'  -> y inverse -> rows of S'' (1 + pi kx~)      -> E + i Fx
+//   S'  (again, from L2) times i pi ky~ = Gy -> y inverse -> rows p and
+//       p + N/2 paired in one complex x inverse    -> Fy
+//   Gz' -> y inverse -> rows paired likewise          -> Fz
 template <int N>
-__global__ void __launch_bounds__(PassC<N>::NT) passC_kernel(const float2 *__restrict__ Y1,
-                                                              const float2 *__restrict__ Y2,
-                                                              FieldPtrs out) {
+__device__ __forceinline__ void passC_load(float2 *plane, const float2 *__restrict__ src) {
+    constexpr int H = PassC<N>::H, PW = PassC<N>::PW, NT = PassC<N>::NT;
+    for (int i = threadIdx.x; i < N * H; i += NT) {
+        const int y = i / H, c = i % H;  // y is the ky slot
+        cp_async8(plane + y * PW + c, src + i);
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(PassC<N>::NT, PassC<N>::MINB) passC_kernel(const float2 *__restrict__ Y1,
+                                                                              const float2 *__restrict__ Y2,
+                                                                              FieldPtrs out) {
     constexpr int H = PassC<N>::H, PW = PassC<N>::PW, RB = PassC<N>::RB, TP = PassC<N>::TP,
-                  NT = PassC<N>::NT;
+                  NT = PassC<N>::NT, HALF = N / 2;
     extern __shared__ float2 sm[];
     float2 *plane = sm;                       // [N][PW]
     float2 *Tb = plane + (size_t)N * PW;      // [RB][TP]
@@ -449,31 +468,34 @@ __global__ void __launch_bounds__(PassC<N>::NT) passC_kernel(const float2 *__res
     float4 *xt = reinterpret_cast<float4 *>(twN + N);
     const int z = blockIdx.x, r = blockIdx.y;
     const float2 *s1 = Y1 + ((size_t)r * N + z) * N * H;
-    for (int i = threadIdx.x; i < N * H; i += NT) {
-        const int y = i / H, c = i % H;  // y is the ky slot
-        cp_async8(plane + y * PW + c, s1 + i);
-    }
+    const size_t fo = (size_t)r * out.rot_stride + (size_t)z * N * N;
+    // E + i Fx
+    passC_load<N>(plane, s1);
     load_tw<N>(twN);
     build_xtable<N>(xt);
     cp_async_wait_all();
     __syncthreads();
+    fft_lines<N, +1, H, PW, 1, NT>(plane, twN);
+    x_pass<N, 0, PW, RB, TP, NT, N>(plane, plane, 0, 0, Tb, twN, xt, out.E + fo, out.Fx + fo);
+    // Fy: Gy = i pi ky~ S' formed in place
+    passC_load<N>(plane, s1);
+    cp_async_wait_all();
+    __syncthreads();
     for (int i = threadIdx.x; i < N * H; i += NT) {
         const int y = i / H, c = i % H;
-        plane[y * PW + H + c] = cmul_is(plane[y * PW + c], signed_k_mult<N>(slot_freq<N>(y)));
+        plane[y * PW + c] = cmul_is(plane[y * PW + c], signed_k_mult<N>(slot_freq<N>(y)));
     }
     __syncthreads();
-    fft_lines<N, +1, 2 * H, PW, 1, NT>(plane, twN);
-    const size_t fo = (size_t)r * out.rot_stride + (size_t)z * N * N;
-    x_pass<N, 0, PW, RB, TP, NT, N>(plane, 0, H, Tb, twN, xt, out.E + fo, out.Fx + fo);
-    const float2 *s2 = Y2 + ((size_t)r * N + z) * N * H;
-    for (int i = threadIdx.x; i < N * H; i += NT) {
-        const int y = i / H, c = i % H;
-        cp_async8(plane + y * PW + c, s2 + i);
-    }
+    fft_lines<N, +1, H, PW, 1, NT>(plane, twN);
+    x_pass<N, 1, PW, RB, TP, NT, HALF>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, xt, out.Fy + fo,
+                                      out.Fy + fo + (size_t)HALF * N);
+    // Fz
+    passC_load<N>(plane, Y2 + ((size_t)r * N + z) * N * H);
     cp_async_wait_all();
     __syncthreads();
     fft_lines<N, +1, H, PW, 1, NT>(plane, twN);
-    x_pass<N, 1, PW, RB, TP, NT, N>(plane, 0, H, Tb, twN, xt, out.Fy + fo, out.Fz + fo);
+    x_pass<N, 1, PW, RB, TP, NT, HALF>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, xt, out.Fz + fo,
+                                      out.Fz + fo + (size_t)HALF * N);
 }
 
 // ------------------------------------------------------- pencil pipeline
@@ -640,8 +662,8 @@ __global__ void __launch_bounds__(Pencil<N>::NT) xinv_kernel(const float2 *__res
     cp_async_wait_all();
     __syncthreads();
     const size_t fo = (size_t)r * out.rot_stride + q0 * N;
-    x_pass<N, 0, PW, RBX, TP, NT, RBX>(plane, 0, H, Tb, twN, xt, out.E + fo, out.Fx + fo);
-    x_pass<N, 1, PW, RBX, TP, NT, RBX>(plane, 2 * H, H, Tb, twN, xt, out.Fy + fo, out.Fz + fo);
+    x_pass<N, 0, PW, RBX, TP, NT, RBX>(plane, plane, 0, H, Tb, twN, xt, out.E + fo, out.Fx + fo);
+    x_pass<N, 1, PW, RBX, TP, NT, RBX>(plane, plane, 2 * H, H, Tb, twN, xt, out.Fy + fo, out.Fz + fo);
 }
 
 // -------------------------------------------- natural-order spectrum copy
