@@ -89,7 +89,7 @@ struct hf_part {
     hf_ctx *ctx;  // must outlive the part
     int n, role;
     float *grid;   // HF_MOVING: N^3
-    float2 *spec;  // HF_STATIONARY: (h^3/N^3) rho1^ in [ky*][kz*][kx*] slot order
+    float2 *spec;  // HF_STATIONARY: (h^3/N^3) rho1^ in [kz*][ky*][kx*] slot order
     size_t bytes;
     // HF_MOVING: the grid as stacked padded z-slices in a gather-capable 2D
     // array, (N+1) wide and N(N+1) high, sampled by 2x2 texture gathers

@@ -269,72 +269,121 @@ __global__ void __launch_bounds__(kRsX * kRsY) resample_chunk_kernel(const float
 }
 
 // ------------------------------------------------------------------ pass B
+// One CTA per CW consecutive columns f = ky* H + kx* (the flattened (ky, kx)
+// index, contiguous in memory for every z) and rotation; all N z-values of
+// a column.  Thread (c, g): column c < CW, digit group g < R2 (N = R1 R2).
+// The z transforms keep their data in registers and use shared memory only
+// for the three digit exchanges, each laid out [digit][digit][column] with
+// the column fastest, so every shared access of a warp is one contiguous row:
+//   forward  stage 1: thread (c, g) loads z = R2 n1 + g (n1 < R1) straight
+//            from HBM, DFT-R1, twiddle W^(g k1), exchange;
+//            stage 2: thread (c, k1) for k1 = g, g + R2, ...: DFT-R2 gives
+//            slot s = R2 k1 + k2 (frequency k1 + R1 k2)
+//   product  S = (h^3/N^3) rho1^ conj(rho2^R^), Gz = i pi kz~ S       Eqs. 5, 6a
+//   inverse  stage 1 on the same registers (DFT-R2, conj twiddle), exchange;
+//            stage 2: thread (c, g): DFT-R1 gives z = R2 n1 + g, stored
+//            straight to HBM
 template <int N>
 struct PassB {
     static constexpr int H = N / 2 + 1;
-    static constexpr int C = N <= 128 ? (H + 1) / 2 : 17;  // kx chunk width
-    static constexpr int NCH = (H + C - 1) / C;
-    static constexpr int NT = (N >= 64) ? 256 : 128;
-    static constexpr int MINB = (N >= 128) ? 3 : 4;
-    static constexpr size_t smem = sizeof(float2) * ((size_t)N * 2 * C + N);
+    static constexpr int R1 = Fact<N>::R1, R2 = Fact<N>::R2;
+    static constexpr int CW = N >= 256 ? 16 : 32;       // columns per CTA (N H is a multiple)
+    static constexpr int NT = CW * R2;
+    static constexpr int KPT = (R1 + R2 - 1) / R2;      // stage-2 k1 values per thread
+    static constexpr int MINB = N >= 128 ? 3 : 4;
+    static constexpr size_t smem = sizeof(float2) * (2 * (size_t)N * CW + N);
+    static_assert((N * H) % CW == 0, "whole column tiles");
 };
 
-// MODE 0: full middle pass (product, gradient, inverse z) -> Y1, Y2
-// MODE 1: forward only, spectrum * scale -> spec[ky*][kz*][kx*]  (stationary part)
+// MODE 0: full middle pass (product, gradient, inverse z) -> Y1 = S', Y2 = Gz'
+// MODE 1: forward only, spectrum * scale -> spec[kz*][ky*][kx*]  (stationary part)
 template <int N, int MODE>
 __global__ void __launch_bounds__(PassB<N>::NT, PassB<N>::MINB) passB_kernel(const float2 *__restrict__ X1,
-                                                              const float2 *__restrict__ R1hat,
-                                                              float2 *__restrict__ Y1,
-                                                              float2 *__restrict__ Y2, float scale) {
-    constexpr int H = PassB<N>::H, C = PassB<N>::C, W2 = 2 * C, NT = PassB<N>::NT;
+                                                                              const float2 *__restrict__ R1hat,
+                                                                              float2 *__restrict__ Y1,
+                                                                              float2 *__restrict__ Y2, float scale) {
+    constexpr int H = PassB<N>::H, R1 = PassB<N>::R1, R2 = PassB<N>::R2, CW = PassB<N>::CW,
+                  KPT = PassB<N>::KPT;
+    constexpr size_t NH = (size_t)N * H;
     extern __shared__ float2 sm[];
-    float2 *T = sm;            // [N][2C]: columns [0,C) = S, [C,2C) = Gz
-    float2 *twN = T + N * W2;
-    const int ky = blockIdx.x, c0 = blockIdx.y * C, r = blockIdx.z;
-    const int cw = min(C, H - c0);
-    // asynchronous loads: the X1 tile into columns [0, C); for the full pass
-    // the matching tile of the stationary spectrum into columns [C, 2C),
-    // which hold Gz only after the product has consumed it
-    const float2 *src = X1 + (size_t)r * N * N * H + (size_t)ky * H + c0;
-    for (int i = threadIdx.x; i < N * C; i += NT) {
-        const int z = i / C, c = i % C;
-        if (c < cw) cp_async8(T + z * W2 + c, src + (size_t)z * N * H + c);
-        else T[z * W2 + c] = make_float2(0.f, 0.f);
-    }
-    if constexpr (MODE == 0) {
-        const float2 *rh = R1hat + (size_t)ky * N * H + c0;
-        for (int i = threadIdx.x; i < N * C; i += NT) {
-            const int s = i / C, c = i % C;
-            if (c < cw) cp_async8(T + s * W2 + C + c, rh + (size_t)s * H + c);
-            else T[s * W2 + C + c] = make_float2(0.f, 0.f);
-        }
-    }
+    float2 *E = sm;                      // [k1][n2][c], later S's [n2][k1][c]
+    float2 *G = sm + (size_t)N * CW;     // Gz's [n2][k1][c]
+    float2 *twN = G + (size_t)N * CW;
+    const int c = threadIdx.x % CW, g = threadIdx.x / CW;
+    const size_t f = (size_t)blockIdx.x * CW + c;
+    const int r = blockIdx.y;
     load_tw<N>(twN);
-    cp_async_wait_all();
+    // forward stage 1
+    {
+        float2 v[R1];
+        const float2 *src = X1 + (size_t)r * N * NH + f;
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1) v[n1] = src[(size_t)(R2 * n1 + g) * NH];
+        __syncthreads();  // twiddles in place
+        RegDFT<R1, -1>::run(v);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) E[(k1 * R2 + g) * CW + c] = k1 ? cmul(v[k1], twN[g * k1]) : v[k1];
+    }
     __syncthreads();
-    fft_lines<N, -1, C, W2, 1, NT>(T, twN);
-    if constexpr (MODE == 1) {
-        float2 *dst = Y1 + (size_t)ky * N * H + c0;
-        for (int i = threadIdx.x; i < N * cw; i += NT) {
-            const int s = i / cw, c = i % cw;
-            dst[(size_t)s * H + c] = cscale(T[s * W2 + c], scale);
+    // forward stage 2: X[j][k2] = slot R2 k1 + k2 for k1 = g + R2 j
+    float2 X[KPT][R2];
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) {
+        const int k1 = g + R2 * j;
+        if (k1 < R1) {
+#pragma unroll
+            for (int n2 = 0; n2 < R2; ++n2) X[j][n2] = E[(k1 * R2 + n2) * CW + c];
+            RegDFT<R2, -1>::run(X[j]);
         }
+    }
+    if constexpr (MODE == 1) {
+#pragma unroll
+        for (int j = 0; j < KPT; ++j) {
+            const int k1 = g + R2 * j;
+            if (k1 < R1) {
+#pragma unroll
+                for (int k2 = 0; k2 < R2; ++k2) Y1[(size_t)(R2 * k1 + k2) * NH + f] = cscale(X[j][k2], scale);
+            }
+        }
+        return;
     } else {
-        for (int i = threadIdx.x; i < N * C; i += NT) {
-            const int s = i / C, c = i % C;
-            const float2 S = cmulc(T[s * W2 + C + c], T[s * W2 + c]);  // (h^3/N^3) rho1^ conj(rho2^R^)
-            T[s * W2 + c] = S;
-            T[s * W2 + C + c] = cmul_is(S, signed_k_mult<N>(slot_freq<N>(s)));
+        __syncthreads();  // E is free: it takes S's exchange
+        // product, gradient, inverse stage 1
+#pragma unroll
+        for (int j = 0; j < KPT; ++j) {
+            const int k1 = g + R2 * j;
+            if (k1 < R1) {
+                float2 Sv[R2], Gv[R2];
+#pragma unroll
+                for (int k2 = 0; k2 < R2; ++k2) {
+                    const int s = R2 * k1 + k2;
+                    Sv[k2] = cmulc(__ldg(R1hat + (size_t)s * NH + f), X[j][k2]);  // (h^3/N^3) rho1^ conj(rho2^R^)
+                    Gv[k2] = cmul_is(Sv[k2], signed_k_mult<N>(slot_freq<N>(s)));
+                }
+                RegDFT<R2, +1>::run(Sv);
+                RegDFT<R2, +1>::run(Gv);
+#pragma unroll
+                for (int n2 = 0; n2 < R2; ++n2) {
+                    const float2 t = twN[n2 * k1];
+                    E[(n2 * R1 + k1) * CW + c] = n2 ? cmulc(Sv[n2], t) : Sv[n2];
+                    G[(n2 * R1 + k1) * CW + c] = n2 ? cmulc(Gv[n2], t) : Gv[n2];
+                }
+            }
         }
         __syncthreads();
-        fft_lines<N, +1, W2, W2, 1, NT>(T, twN);
-        float2 *d1 = Y1 + (size_t)r * N * N * H + (size_t)ky * H + c0;
-        float2 *d2 = Y2 + (size_t)r * N * N * H + (size_t)ky * H + c0;
-        for (int i = threadIdx.x; i < N * cw; i += NT) {
-            const int z = i / cw, c = i % cw;
-            d1[(size_t)z * N * H + c] = T[z * W2 + c];
-            d2[(size_t)z * N * H + c] = T[z * W2 + C + c];
-        }
+        // inverse stage 2: z = R2 n1 + g
+        float2 v[R1];
+        float2 *d1 = Y1 + (size_t)r * N * NH + f, *d2 = Y2 + (size_t)r * N * NH + f;
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) v[k1] = E[(g * R1 + k1) * CW + c];
+        RegDFT<R1, +1>::run(v);
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1) d1[(size_t)(R2 * n1 + g) * NH] = v[n1];
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) v[k1] = G[(g * R1 + k1) * CW + c];
+        RegDFT<R1, +1>::run(v);
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1) d2[(size_t)(R2 * n1 + g) * NH] = v[n1];
     }
 }
 
@@ -667,14 +716,14 @@ __global__ void __launch_bounds__(Pencil<N>::NT) xinv_kernel(const float2 *__res
 }
 
 // -------------------------------------------- natural-order spectrum copy
-// spec[ky*][kz*][kx*] (slot order, as left by pass B mode 1) -> out[kz][ky][kx]
+// spec[kz*][ky*][kx*] (slot order, as left by pass B mode 1) -> out[kz][ky][kx]
 template <int N>
 __global__ void unpermute_spectrum_kernel(const float2 *__restrict__ spec, float2 *__restrict__ out) {
     constexpr int H = N / 2 + 1;
     const size_t total = (size_t)N * N * H;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const int kx = (int)(i % H), ky = (int)((i / H) % N), kz = (int)(i / ((size_t)H * N));
-        out[i] = spec[((size_t)perm_slot<N>(ky) * N + perm_slot<N>(kz)) * H + xslot<N>(kx)];
+        out[i] = spec[((size_t)perm_slot<N>(kz) * N + perm_slot<N>(ky)) * H + xslot<N>(kx)];
     }
 }
 
@@ -726,12 +775,14 @@ static cudaError_t launch_resample_chunk(const float *rho, const float *rot9, fl
 template <int N>
 static cudaError_t launch_passB(const float2 *X1, const float2 *R1hat, float2 *Y1, float2 *Y2, int nrot,
                                 cudaStream_t st) {
-    passB_kernel<N, 0><<<dim3(N, PassB<N>::NCH, nrot), PassB<N>::NT, PassB<N>::smem, st>>>(X1, R1hat, Y1, Y2, 0.f);
+    passB_kernel<N, 0><<<dim3(N * PassB<N>::H / PassB<N>::CW, nrot), PassB<N>::NT, PassB<N>::smem, st>>>(X1, R1hat, Y1,
+                                                                                                       Y2, 0.f);
     return cudaGetLastError();
 }
 template <int N>
 static cudaError_t launch_passB_fwd(const float2 *X1, float2 *spec, float scale, cudaStream_t st) {
-    passB_kernel<N, 1><<<dim3(N, PassB<N>::NCH, 1), PassB<N>::NT, PassB<N>::smem, st>>>(X1, nullptr, spec, nullptr, scale);
+    passB_kernel<N, 1><<<dim3(N * PassB<N>::H / PassB<N>::CW, 1), PassB<N>::NT, PassB<N>::smem, st>>>(X1, nullptr, spec,
+                                                                                                    nullptr, scale);
     return cudaGetLastError();
 }
 template <int N>
