@@ -489,21 +489,70 @@ __device__ __forceinline__ void x_pass(const float2 *planeA, const float2 *plane
     }
 }
 
+// Inverse y transform of one z-plane's H half-spectrum columns: global rows
+// src[s H + c] (ky slot order) -> plane[y PW + c] (natural y).  The N/2 main
+// columns run register-centric (stage 1 straight from HBM, the digit
+// exchange through the plane buffer as [n2][k1][c], stage 2 back into the
+// plane's rows); the Nyquist column is transformed in place last.  MUL
+// multiplies input row s by i pi ky~(s) on the way in (forms Gy from S').
+template <int N, bool MUL>
+__device__ __forceinline__ void y_inverse_plane(const float2 *__restrict__ src, float2 *plane, const float2 *twN) {
+    constexpr int H = N / 2 + 1, HALF = N / 2, R1 = Fact<N>::R1, R2 = Fact<N>::R2, PW = PassC<N>::PW,
+                  NT = PassC<N>::NT;
+    for (int s = threadIdx.x; s < N; s += NT) {
+        float2 v = __ldg(src + (size_t)s * H + HALF);
+        if constexpr (MUL) v = cmul_is(v, signed_k_mult<N>(slot_freq<N>(s)));
+        plane[s * PW + HALF] = v;
+    }
+    // stage 1: items (c, k1), slots R2 k1 + k2
+#pragma unroll 1
+    for (int w = threadIdx.x; w < HALF * R1; w += NT) {
+        const int c = w % HALF, k1 = w / HALF;
+        float2 v[R2];
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) {
+            const int sl = R2 * k1 + k2;
+            v[k2] = __ldg(src + (size_t)sl * H + c);
+            if constexpr (MUL) v[k2] = cmul_is(v[k2], signed_k_mult<N>(slot_freq<N>(sl)));
+        }
+        RegDFT<R2, +1>::run(v);
+#pragma unroll
+        for (int n2 = 0; n2 < R2; ++n2) plane[(n2 * R1 + k1) * PW + c] = n2 ? cmulc(v[n2], twN[n2 * k1]) : v[n2];
+    }
+    __syncthreads();
+    // stage 2: items (c, n2); every item is read before any row is written
+    constexpr int ITEMS = HALF * R2, IPT = (ITEMS + NT - 1) / NT;
+    float2 v[IPT][R1];
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+        const int w = threadIdx.x + j * NT;
+        if (w < ITEMS) {
+            const int c = w % HALF, n2 = w / HALF;
+#pragma unroll
+            for (int k1 = 0; k1 < R1; ++k1) v[j][k1] = plane[(n2 * R1 + k1) * PW + c];
+            RegDFT<R1, +1>::run(v[j]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+        const int w = threadIdx.x + j * NT;
+        if (w < ITEMS) {
+            const int c = w % HALF, n2 = w / HALF;
+#pragma unroll
+            for (int n1 = 0; n1 < R1; ++n1) plane[(R2 * n1 + n2) * PW + c] = v[j][n1];
+        }
+    }
+    __syncthreads();
+    fft_lines<N, +1, 1, PW, 1, NT>(plane + HALF, twN);
+}
+
 // Pass C holds one half-spectrum plane at a time (about 100 KB of shared
 // memory at 128^3, two CTAs per SM):
 //   S'  -> y inverse -> rows of S'' (1 + pi kx~)      -> E + i Fx
 //   S'  (again, from L2) times i pi ky~ = Gy -> y inverse -> rows p and
 //       p + N/2 paired in one complex x inverse    -> Fy
 //   Gz' -> y inverse -> rows paired likewise          -> Fz
-template <int N>
-__device__ __forceinline__ void passC_load(float2 *plane, const float2 *__restrict__ src) {
-    constexpr int H = PassC<N>::H, PW = PassC<N>::PW, NT = PassC<N>::NT;
-    for (int i = threadIdx.x; i < N * H; i += NT) {
-        const int y = i / H, c = i % H;  // y is the ky slot
-        cp_async8(plane + y * PW + c, src + i);
-    }
-}
-
 template <int N>
 __global__ void __launch_bounds__(PassC<N>::NT, PassC<N>::MINB) passC_kernel(const float2 *__restrict__ Y1,
                                                                               const float2 *__restrict__ Y2,
@@ -518,31 +567,18 @@ __global__ void __launch_bounds__(PassC<N>::NT, PassC<N>::MINB) passC_kernel(con
     const int z = blockIdx.x, r = blockIdx.y;
     const float2 *s1 = Y1 + ((size_t)r * N + z) * N * H;
     const size_t fo = (size_t)r * out.rot_stride + (size_t)z * N * N;
-    // E + i Fx
-    passC_load<N>(plane, s1);
     load_tw<N>(twN);
     build_xtable<N>(xt);
-    cp_async_wait_all();
     __syncthreads();
-    fft_lines<N, +1, H, PW, 1, NT>(plane, twN);
+    // E + i Fx
+    y_inverse_plane<N, false>(s1, plane, twN);
     x_pass<N, 0, PW, RB, TP, NT, N>(plane, plane, 0, 0, Tb, twN, xt, out.E + fo, out.Fx + fo);
-    // Fy: Gy = i pi ky~ S' formed in place
-    passC_load<N>(plane, s1);
-    cp_async_wait_all();
-    __syncthreads();
-    for (int i = threadIdx.x; i < N * H; i += NT) {
-        const int y = i / H, c = i % H;
-        plane[y * PW + c] = cmul_is(plane[y * PW + c], signed_k_mult<N>(slot_freq<N>(y)));
-    }
-    __syncthreads();
-    fft_lines<N, +1, H, PW, 1, NT>(plane, twN);
+    // Fy from Gy = i pi ky~ S'
+    y_inverse_plane<N, true>(s1, plane, twN);
     x_pass<N, 1, PW, RB, TP, NT, HALF>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, xt, out.Fy + fo,
                                       out.Fy + fo + (size_t)HALF * N);
     // Fz
-    passC_load<N>(plane, Y2 + ((size_t)r * N + z) * N * H);
-    cp_async_wait_all();
-    __syncthreads();
-    fft_lines<N, +1, H, PW, 1, NT>(plane, twN);
+    y_inverse_plane<N, false>(Y2 + ((size_t)r * N + z) * N * H, plane, twN);
     x_pass<N, 1, PW, RB, TP, NT, HALF>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, xt, out.Fz + fo,
                                       out.Fz + fo + (size_t)HALF * N);
 }
