@@ -174,8 +174,8 @@ def run_ours(args, rank, world, local_rank):
     ctx.density_build(n, pts2, sig2, out=g2)
     p1, p2 = ctx.part(g1, hf.HF_STATIONARY), ctx.part(g2, hf.HF_MOVING)
     tune = None
-    if not args.no_tune:  # launch shape for this grid size, timed on this device (not cached)
-        c, pen, rps = ctx.autotune(n)
+    if not args.no_tune:  # launch shape for this grid size, timed on this device or read from --tune-cache
+        c, pen, rps = ctx.autotune(n, args.tune_cache)
         tune = {"chunk": c, "pipeline": "pencil" if pen else "slab", "ef_rot_per_s": round(rps, 1)}
     fs = ctx.fieldset(n, R, hf.HF_E | hf.HF_F | hf.HF_T)
     tq = torch.as_tensor(tq_h, device=dev)
@@ -233,7 +233,7 @@ def run_ours(args, rank, world, local_rank):
     # 32 rotations at 128^3 (profiles/passC_c2_128.md), scaled to this
     # launch's rotations: the traffic is per rotation (each reads its own two
     # spectra and writes its own four fields)
-    traffic = {"passC": 1.5625e9 * chunk / 32} if n == 128 and not tune_is_pencil(ctx, n) else {}
+    traffic = {"passC": 1.5967e9 * chunk / 32} if n == 128 and not tune_is_pencil(ctx, n) else {}
     hbm_peak, peak_kind = peaks()
     kernels = {}
     for k, (cnt, tot) in prof.items():
@@ -719,6 +719,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="built-in launch shapes instead of the autotuner's")
+    ap.add_argument("--tune-cache", default=None, help="autotuner cache file (read if it has this device and N)")
     ap.add_argument("--batch-steps", type=int, default=5,
                     help="graph launches of the 64-pair uneven batch (0 = skip)")
     ap.add_argument("--precision-rotations", type=int, default=512,
