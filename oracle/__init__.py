@@ -41,6 +41,9 @@ def _L():
         _lib.or_query.argtypes = [i, i, d, d, i, d, d, i, d]
         _lib.or_nearest.argtypes = [i, d, d, i, i, ip, d]
         _lib.or_so3_log.argtypes = [d, d]
+        _lib.or_fields_spec.argtypes = [i, d, d, d, d, d, d]
+        _lib.or_spectral_table.argtypes = [i, i, d, d]
+        _lib.or_spectral_rotate.argtypes = [i, i, d, d, d]
     return _lib
 
 
@@ -118,6 +121,40 @@ def fields(rho1, rho2r):
     outs = [np.empty_like(rho1) for _ in range(4)]
     _L().or_fields(n, _p(rho1), _p(rho2r), *[_p(o) for o in outs])
     return tuple(outs)
+
+
+def fields_spec(rho1, b):
+    """fields() given the moving density's rotated spectrum b = DFT(rho2R)
+    (complex, natural order) instead of the rotated grid (Eqs. 5, 6a)."""
+    rho1 = _f64(rho1)
+    b = np.ascontiguousarray(b, dtype=np.complex128)
+    n = rho1.shape[0]
+    outs = [np.empty_like(rho1) for _ in range(4)]
+    _L().or_fields_spec(n, _p(rho1), b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), *[_p(o) for o in outs])
+    return tuple(outs)
+
+
+def spectral_table(rho2, os=1):
+    """Centred spectrum of rho2 zero-padded to os*N nodes per axis (Section
+    3.2, the precomputed moving spectrum): (-1)^(kx+ky+kz) DFT(pad rho2),
+    complex (os N)^3, natural order."""
+    rho2 = _f64(rho2)
+    n = rho2.shape[0]
+    t = np.empty((os * n,) * 3, dtype=np.complex128)
+    _L().or_spectral_table(n, int(os), _p(rho2), t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return t
+
+
+def spectral_rotate(table, n, R, os=1):
+    """Spectrum of the rotated moving density on the N grid by trilinear
+    interpolation of the table at os R^T k (Section 3.2, step 1); zero on the
+    Nyquist planes."""
+    table = np.ascontiguousarray(table, dtype=np.complex128)
+    assert table.shape == (os * n,) * 3
+    out = np.empty((n, n, n), dtype=np.complex128)
+    _L().or_spectral_rotate(n, int(os), table.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _p(_f64(R)),
+                            out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return out
 
 
 def torque(quats, E, knn=6):

@@ -241,16 +241,32 @@ static int signed_k(int k, int n) { return k < (n + 1) / 2 ? k : k - n; }
 /*           multiplier 0 on each axis' Nyquist index (even N).          */
 /* Outputs are real parts; E and F are real for real densities.         */
 /* ------------------------------------------------------------------ */
+void or_fields_spec(int n, const double *rho1, const double *b_ri,
+                    double *E, double *Fx, double *Fy, double *Fz);
+
 void or_fields(int n, const double *rho1, const double *rho2r,
                double *E, double *Fx, double *Fy, double *Fz)
 {
     const long m = (long)n * n * n;
-    const double h = 2.0 / n, dv = h * h * h;
-    cplx *A = malloc(sizeof(cplx) * m), *B = malloc(sizeof(cplx) * m);
-    cplx *S = malloc(sizeof(cplx) * m), *G = malloc(sizeof(cplx) * m);
-    for (long i = 0; i < m; ++i) { A[i] = rho1[i]; B[i] = rho2r[i]; }
-    or_fft3d(n, (double *)A, -1);
+    cplx *B = malloc(sizeof(cplx) * m);
+    for (long i = 0; i < m; ++i) B[i] = rho2r[i];
     or_fft3d(n, (double *)B, -1);
+    or_fields_spec(n, rho1, (const double *)B, E, Fx, Fy, Fz);
+    free(B);
+}
+
+/* The same fields given the moving density's (rotated) spectrum B = DFT(rho2R)
+ * directly, natural order, complex interleaved. */
+void or_fields_spec(int n, const double *rho1, const double *b_ri,
+                    double *E, double *Fx, double *Fy, double *Fz)
+{
+    const long m = (long)n * n * n;
+    const double h = 2.0 / n, dv = h * h * h;
+    const cplx *B = (const cplx *)b_ri;
+    cplx *A = malloc(sizeof(cplx) * m);
+    cplx *S = malloc(sizeof(cplx) * m), *G = malloc(sizeof(cplx) * m);
+    for (long i = 0; i < m; ++i) A[i] = rho1[i];
+    or_fft3d(n, (double *)A, -1);
     for (long i = 0; i < m; ++i) S[i] = dv * A[i] * conj(B[i]);
 
     memcpy(G, S, sizeof(cplx) * m);
@@ -271,7 +287,81 @@ void or_fields(int n, const double *rho1, const double *rho2r,
         or_fft3d(n, (double *)G, +1);
         for (long i = 0; i < m; ++i) outs[d][i] = -creal(G[i]) / (double)m;
     }
-    free(A); free(B); free(S); free(G);
+    free(A); free(S); free(G);
+}
+
+/* ------------------------------------------------------------------ */
+/* Rotation in the frequency domain, Section 3.2 step 1: the spectrum   */
+/* of the rotated density rho2(R^T p) is rho2^(R^T omega), read off a   */
+/* precomputed spectrum by trilinear interpolation.                     */
+/*                                                                      */
+/* Table: rho2 zero-padded to N' = os N nodes per axis (same spacing h, */
+/* box [-os, os)^3, the original nodes at the centre) and transformed;  */
+/* the phase is taken about the physical origin rather than the box     */
+/* corner: table[k'] = (-1)^(kx'+ky'+kz') DFT_N'(pad rho2)[k'], so a     */
+/* density centred at the origin has a smooth table.  Frequency k' of   */
+/* the table is omega = k'/(2 os); frequency k of the N grid is         */
+/* omega = k/2, index os*k in the table.                                */
+/* ------------------------------------------------------------------ */
+void or_spectral_table(int n, int os, const double *rho, double *table_ri)
+{
+    const int np = os * n, off = (np - n) / 2;
+    const long mp = (long)np * np * np;
+    cplx *T = (cplx *)table_ri;
+    for (long i = 0; i < mp; ++i) T[i] = 0.0;
+    for (int z = 0; z < n; ++z)
+        for (int y = 0; y < n; ++y)
+            for (int x = 0; x < n; ++x)
+                T[idx3(np, z + off, y + off, x + off)] = rho[idx3(n, z, y, x)];
+    or_fft3d(np, table_ri, -1);
+    for (int kz = 0; kz < np; ++kz)
+        for (int ky = 0; ky < np; ++ky)
+            for (int kx = 0; kx < np; ++kx)
+                if ((kx + ky + kz) & 1) T[idx3(np, kz, ky, kx)] = -T[idx3(np, kz, ky, kx)];
+}
+
+/* Periodic trilinear interpolation of a complex n^3 table at index u. */
+static cplx trilinear_c(int n, const cplx *g, const double u[3])
+{
+    long i0[3];
+    double f[3];
+    for (int a = 0; a < 3; ++a) {
+        const double fl = floor(u[a]);
+        i0[a] = (long)fl;
+        f[a] = u[a] - fl;
+    }
+    cplx acc = 0.0;
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+                const double w = (dx ? f[0] : 1 - f[0]) * (dy ? f[1] : 1 - f[1]) * (dz ? f[2] : 1 - f[2]);
+                acc += w * g[idx3(n, wrap(i0[2] + dz, n), wrap(i0[1] + dy, n), wrap(i0[0] + dx, n))];
+            }
+    return acc;
+}
+
+/* Rotated spectrum on the N grid (natural order): for every frequency k   */
+/* with signed index k~, B[k] = (-1)^(kx+ky+kz) trilinear(table, os R^T k~), */
+/* and B = 0 wherever an axis index is the Nyquist index N/2 (a rotated     */
+/* frequency has no Nyquist partner, so those planes are left out).         */
+void or_spectral_rotate(int n, int os, const double *table_ri, const double *R, double *out_ri)
+{
+    const int np = os * n;
+    const cplx *T = (const cplx *)table_ri;
+    cplx *B = (cplx *)out_ri;
+#pragma omp parallel for schedule(static)
+    for (int kz = 0; kz < n; ++kz)
+        for (int ky = 0; ky < n; ++ky)
+            for (int kx = 0; kx < n; ++kx) {
+                const long i = idx3(n, kz, ky, kx);
+                if (2 * kx == n || 2 * ky == n || 2 * kz == n) { B[i] = 0.0; continue; }
+                const double k[3] = {signed_k(kx, n), signed_k(ky, n), signed_k(kz, n)};
+                double u[3];
+                for (int a = 0; a < 3; ++a)  /* (R^T k)_a = sum_b R[b][a] k_b */
+                    u[a] = os * (R[0 * 3 + a] * k[0] + R[1 * 3 + a] * k[1] + R[2 * 3 + a] * k[2]);
+                const cplx v = trilinear_c(np, T, u);
+                B[i] = ((kx + ky + kz) & 1) ? -v : v;
+            }
 }
 
 /* Geodesic angle between two unit quaternions (double cover aware). */
