@@ -85,6 +85,11 @@ typedef void *hf_stream; /* a cudaStream_t */
  * BF16 or FP16 and FP32 accumulation; every other stage stays FP32. */
 #define HF_PREC_SPLIT_BF16 0x20u
 #define HF_PREC_SPLIT_F16 0x40u
+/* Spectral mode (Section 3.2, step 1): each rotation's spectrum of the moving
+ * part is read off its precomputed spectrum (hf_part_spectral) by trilinear
+ * interpolation at R^T omega instead of resampling the grid and transforming
+ * it.  The moving part must have a table (HF_ENOTREADY otherwise). */
+#define HF_SPECTRAL 0x80u
 
 /* Field indices for hf_fieldset_get / hf_fieldset_field_ptr and query outputs. */
 #define HF_FIELD_E 0
@@ -133,6 +138,21 @@ int hf_part_n(const hf_part *part);
  * size, in place (no allocation beyond the stream-ordered pool).
  * Errors: HF_EINVAL, HF_ECUDA. */
 hf_status hf_part_update(hf_part *part, const float *d_grid, hf_stream stream);
+
+/* Spectral table of a moving part (rotation in the frequency domain,
+ * Section 3.2): rho2 zero-padded to os*N nodes per axis (os = 1 or 2, same
+ * spacing, the part at the centre), transformed, its phase taken about the
+ * physical origin ((-1)^(kx+ky+kz)), kept as a full (os N)^3 complex cube
+ * (8 (os N)^3 bytes, charged to the budget; os N must be a supported size).
+ * Field sets with HF_SPECTRAL then read the rotated spectrum at frequency
+ * k as (-1)^(kx+ky+kz) trilinear_periodic(table, os R^T k~), 0 on every
+ * axis's Nyquist plane.  hf_part_update refreshes the table.  Padding (os = 2)
+ * halves the frequency step and with it the interpolation error.
+ * Errors: HF_EINVAL (not a moving part, os), HF_EUNSUPPORTED, HF_EBUDGET,
+ * HF_ENOMEM, HF_ECUDA. */
+hf_status hf_part_spectral(hf_part *part, int os, hf_stream stream);
+/* The part's table padding factor (0 without a table). */
+int hf_part_spectral_os(const hf_part *part);
 
 /* Allocate a field set for R rotations at grid size n holding the fields
  * selected by `flags` (energy and force always; HF_T adds torque; at most one

@@ -11,8 +11,8 @@ import ctypes
 import numpy as np
 
 from . import _binding as B
-from ._binding import (HF_E, HF_F, HF_MOVING, HF_PREC_SPLIT_BF16, HF_PREC_SPLIT_F16, HF_STATIONARY,  # noqa: F401
-                       HF_T, HF_TORQUE_F64, HFError)
+from ._binding import (HF_E, HF_F, HF_MOVING, HF_PREC_SPLIT_BF16, HF_PREC_SPLIT_F16, HF_SPECTRAL,  # noqa: F401
+                       HF_STATIONARY, HF_T, HF_TORQUE_F64, HFError)
 
 __all__ = ["Context", "Part", "FieldSet", "Batch", "Server", "HFError", "resample", "rfft3d", "version"]
 
@@ -155,6 +155,11 @@ class Part:
         B.check(B.lib().hf_part_create(ctx.handle, n, _dev(grid, torch.float32), int(role), ctypes.byref(h),
                                        _stream_ptr(stream)))
         self.handle, self.n, self.role, self.ctx = h, n, role, ctx
+
+    def spectral(self, os=1, stream=None):
+        """hf_part_spectral: build the moving part's centred spectrum table
+        (padding factor os) for HF_SPECTRAL field sets."""
+        B.check(B.lib().hf_part_spectral(self.handle, int(os), _stream_ptr(stream)))
 
     def update(self, grid, stream=None):
         """hf_part_update: re-derive the part from a new grid, in place."""

@@ -14,7 +14,7 @@ STATUS_NAMES = {0: "HF_OK", 1: "HF_EINVAL", 2: "HF_ENOMEM", 3: "HF_EBUDGET", 4: 
                 5: "HF_ETIMEOUT", 6: "HF_ENOTREADY", 7: "HF_EUNSUPPORTED"}
 HF_STATIONARY, HF_MOVING = 0, 1
 HF_E, HF_F, HF_T, HF_TORQUE_F64 = 0x1, 0x2, 0x4, 0x10
-HF_PREC_SPLIT_BF16, HF_PREC_SPLIT_F16 = 0x20, 0x40
+HF_PREC_SPLIT_BF16, HF_PREC_SPLIT_F16, HF_SPECTRAL = 0x20, 0x40, 0x80
 
 _vp = ctypes.c_void_p
 _i = ctypes.c_int
@@ -84,6 +84,8 @@ SIGNATURES = {
     "hf_tune_set": (_i, [_vp, _i, _i, _i]),
     "hf_tune_get": (_i, [_vp, _i, _ip, _ip, ctypes.POINTER(ctypes.c_double)]),
     "hf_tc_timeouts": (_i, [_i]),
+    "hf_part_spectral": (_i, [_vp, _i, _vp]),
+    "hf_part_spectral_os": (_i, [_vp]),
 }
 
 

@@ -97,6 +97,11 @@ struct hf_part {
     size_t slab_pitch = 0;  // bytes
     cudaArray_t arr = nullptr;
     cudaTextureObject_t tex = 0;
+    // HF_MOVING after hf_part_spectral: the centred spectrum of rho2 padded to
+    // table_os * N nodes per axis, full cube, natural order (spectral mode)
+    float2 *table = nullptr;
+    int table_os = 0;
+    size_t table_bytes = 0;
 };
 
 struct hf_fieldset {
@@ -122,6 +127,7 @@ struct hf_fieldset {
     int lanes = 1;  // pipelines used by compute (HF_LANES=2 alternates chunks over two)
     bool pencil = false;  // pencil pipeline (x/y stages as separate kernels) instead of slab passes
     int prec = hf::PREC_FP32;  // y stages on the tensor cores (pencil pipeline at N = 256)
+    bool spectral = false;     // rotated spectrum interpolated from the moving part's table
     bool ready = false;
     size_t bytes = 0;
     cudaStream_t mem_stream = nullptr;  // non-null: stream-ordered device memory, pageable staging
@@ -320,7 +326,13 @@ static float spectrum_scale(int n) {
     return (float)(h * h * h / ((double)n * n * n));
 }
 
+static hf_status spectral_table_fill(hf_part *p, const float *d_grid, cudaStream_t st);
+
 static hf_status part_fill(hf_part *p, const float *d_grid, cudaStream_t st) {
+    if (p->role == HF_MOVING && p->table) {
+        const hf_status s = spectral_table_fill(p, d_grid, st);
+        if (s != HF_OK) return s;
+    }
     if (p->role == HF_MOVING) {
         const int n = p->n;
         CU(cudaMemcpyAsync(p->grid, d_grid, (size_t)n * n * n * sizeof(float), cudaMemcpyDeviceToDevice, st));
@@ -433,9 +445,65 @@ extern "C" hf_status hf_part_update(hf_part *p, const float *d_grid, hf_stream s
     return part_fill(p, d_grid, (cudaStream_t)stream);
 }
 
+// the centred, zero-padded spectrum of a moving part (Section 3.2: the
+// moving spectrum is precomputed, then read at rotated frequencies)
+static hf_status spectral_table_fill(hf_part *p, const float *d_grid, cudaStream_t st) {
+    const int n = p->n, np = p->table_os * n;
+    const size_t np3 = (size_t)np * np * np;
+    float *pad = nullptr;
+    float2 *half = nullptr;
+    CU(cudaMallocAsync(&pad, np3 * sizeof(float), st));
+    cudaError_t e = cudaMallocAsync(&half, hf::half_spec_elems(np) * sizeof(float2), st);
+    hf_status s = HF_OK;
+    if (e == cudaSuccess) e = hf::run_pad_center(n, d_grid, pad, np, st);
+    if (e == cudaSuccess) s = stationary_spectrum(p->ctx, np, pad, half, 1.0f, st);
+    if (e == cudaSuccess && s == HF_OK) e = hf::run_spectral_complete(np, half, p->table, st);
+    if (pad) cudaFreeAsync(pad, st);
+    if (half) cudaFreeAsync(half, st);
+    if (s != HF_OK) return s;
+    if (e != cudaSuccess) return fail(HF_ECUDA, "hf_part_spectral: %s", cudaGetErrorString(e));
+    return HF_OK;
+}
+
+extern "C" hf_status hf_part_spectral(hf_part *p, int os, hf_stream stream) {
+    if (!p) return fail(HF_EINVAL, "hf_part_spectral: NULL part");
+    if (p->role != HF_MOVING) return fail(HF_EINVAL, "hf_part_spectral: the part must be HF_MOVING");
+    if (os != 1 && os != 2) return fail(HF_EINVAL, "hf_part_spectral: os must be 1 or 2 (%d)", os);
+    if (!hf::supported_n(os * p->n))
+        return fail(HF_EUNSUPPORTED, "hf_part_spectral: padded size %d not supported", os * p->n);
+    CU(cudaSetDevice(p->ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t np = (size_t)os * p->n, bytes = np * np * np * sizeof(float2);
+    if (p->table && p->table_os != os) {
+        CU(cudaStreamSynchronize(st));
+        cudaFree(p->table);
+        uncharge(p->ctx, p->table_bytes);
+        p->table = nullptr;
+        p->table_bytes = 0;
+    }
+    if (!p->table) {
+        if (!charge(p->ctx, bytes)) return fail(HF_EBUDGET, "hf_part_spectral: %zu bytes exceed the budget", bytes);
+        const cudaError_t e = cudaMalloc(&p->table, bytes);
+        if (e != cudaSuccess) {
+            p->table = nullptr;
+            uncharge(p->ctx, bytes);
+            return fail(HF_ENOMEM, "hf_part_spectral: cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+        }
+        p->table_bytes = bytes;
+    }
+    p->table_os = os;
+    return spectral_table_fill(p, p->grid, st);
+}
+
+extern "C" int hf_part_spectral_os(const hf_part *p) { return p && p->table ? p->table_os : 0; }
+
 extern "C" void hf_part_release(hf_part *p) {
     if (!p) return;
     cudaSetDevice(p->ctx->device);
+    if (p->table) {
+        cudaFree(p->table);
+        uncharge(p->ctx, p->table_bytes);
+    }
     moving_texture_free(p);
     cudaFree(p->grid ? (void *)p->grid : (void *)p->spec);
     uncharge(p->ctx, p->bytes);
@@ -622,6 +690,7 @@ static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags,
     fs->pencil = hf::pencil_n(n);
     fs->prec = (flags & HF_PREC_SPLIT_F16) ? hf::PREC_SPLIT_F16 : (flags & HF_PREC_SPLIT_BF16) ? hf::PREC_SPLIT_BF16
                                                                                              : hf::PREC_FP32;
+    fs->spectral = (flags & HF_SPECTRAL) != 0;
     fs->chunk = default_chunk(n);
     {
         const Tune &t = ctx->tune[tune_slot(n)];
@@ -741,8 +810,24 @@ extern "C" unsigned hf_fieldset_flags(const hf_fieldset *fs) { return fs ? fs->f
 // rot9 (cnt x 9, device); outputs through `out` (first rotation at out.E)
 static hf_status run_fields(hf_ctx *c, int n, bool pencil, int prec, const hf_part *s1, const hf_part *s2,
                             const float *rot9, int cnt, float2 *scratch, size_t scratch_rot, float *planes,
-                            FieldPtrs out, cudaStream_t st) {
+                            FieldPtrs out, cudaStream_t st, bool spectral = false) {
     float2 *X1 = scratch, *Y1 = scratch + scratch_rot, *Y2 = scratch + 2 * scratch_rot;
+    if (spectral) {
+        CU(timed(c, kPassB, st, [&] {
+            return hf::run_passB_spectral(n, s2->table, s2->table_os, rot9, s1->spec, Y1, Y2, cnt, st);
+        }));
+        if (pencil) {
+            float2 *A = scratch + 3 * scratch_rot, *B = scratch + 4 * scratch_rot;
+            if (prec != hf::PREC_FP32)
+                CU(timed(c, kYtc, st, [&] { return hf::run_yinv_tc(n, prec, Y1, Y2, A, X1, B, cnt, st); }));
+            else
+                CU(timed(c, kPassC, st, [&] { return hf::run_yinv(n, Y1, Y2, A, X1, B, cnt, st); }));
+            CU(timed(c, kPassC, st, [&] { return hf::run_xinv(n, A, X1, B, out, cnt, st); }));
+        } else {
+            CU(timed(c, kPassC, st, [&] { return hf::run_passC(n, Y1, Y2, out, cnt, st); }));
+        }
+        return HF_OK;
+    }
     if (pencil) {
         float2 *A = scratch + 3 * scratch_rot, *B = scratch + 4 * scratch_rot;
         if (s2->tex)
@@ -815,6 +900,8 @@ hf_status hf_set_launch(hf_ctx *ctx, const hf_part *s1, const hf_part *s2, hf_fi
     if (R <= 0 || R > fs->R) return fail(HF_EINVAL, "field set holds %d rotations, %d asked", fs->R, R);
     hf_status cs = check_pair(s1, s2, n, "field-set build");
     if (cs != HF_OK) return cs;
+    if (fs->spectral && !s2->table)
+        return fail(HF_ENOTREADY, "field-set build: HF_SPECTRAL needs hf_part_spectral on the moving part");
     const size_t n3 = (size_t)n * n * n;
     const size_t rs = (size_t)fs->nf * n3;
     const size_t scr_rot = (size_t)fs->chunk * hf::half_spec_elems(n);
@@ -837,7 +924,7 @@ hf_status hf_set_launch(hf_ctx *ctx, const hf_part *s1, const hf_part *s2, hf_fi
         out.Fy = base + 2 * n3;
         out.Fz = base + 3 * n3;
         s = run_fields(ctx, n, fs->pencil, fs->prec, s1, s2, d_rot9 + (size_t)9 * r0, cnt, fs->scratch[l], scr_rot,
-                       fs->planes[l], out, fs->lanes == 2 ? fs->lane[l] : st);
+                       fs->planes[l], out, fs->lanes == 2 ? fs->lane[l] : st, fs->spectral);
         if (s != HF_OK) return s;
     }
     for (int l = 0; l < 2 && fs->lanes == 2; ++l) {

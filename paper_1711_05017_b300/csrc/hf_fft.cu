@@ -295,13 +295,88 @@ struct PassB {
     static_assert((N * H) % CW == 0, "whole column tiles");
 };
 
+// Spectral-mode source (MODE 2): the rotated moving spectrum read off the
+// part's centred table (os N per axis, full cube, natural order) by periodic
+// trilinear interpolation at os R^T k~ (Section 3.2, step 1), times
+// (-1)^(kx+ky+kz) to move the phase back to the box corner; 0 on Nyquist
+// planes.  The coordinate is summed in double-float arithmetic (exact
+// products, compensated sums) so that the fractional weights carry the
+// rotation to ~1e-12 at any table size.
+struct SpecSrc {
+    const float2 *table;
+    int np;  // os * N, power of two
+    int os;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// floor and fraction of r0 k0 + r1 k1 + r2 k2 (integer k), accurate
+__device__ __forceinline__ void rot_coord(float r0, float r1, float r2, float k0, float k1, float k2, int &i0,
+                                          float &fr) {
+    const float p0 = r0 * k0, p1 = r1 * k1, p2 = r2 * k2;
+    const float e0 = fmaf(r0, k0, -p0), e1 = fmaf(r1, k1, -p1), e2 = fmaf(r2, k2, -p2);
+    float s01, t01, s, t;
+    two_sum(p0, p1, s01, t01);
+    two_sum(s01, p2, s, t);
+    const float corr = ((t01 + t) + (e0 + e1)) + e2;
+    const float fl = floorf(s);
+    fr = (s - fl) + corr;  // s - fl is exact
+    i0 = (int)fl;
+    if (fr < 0.f) {
+        fr += 1.f;
+        --i0;
+    } else if (fr >= 1.f) {
+        fr -= 1.f;
+        ++i0;
+    }
+}
+
+template <int N>
+__device__ __forceinline__ float2 spectral_sample(const SpecSrc &src, const float *R, int kx, int ky, int kz) {
+    const int h = N / 2;
+    if (kx == h || ky == h || kz == h) return make_float2(0.f, 0.f);
+    const float ks[3] = {(float)(src.os * (kx < h ? kx : kx - N)), (float)(src.os * (ky < h ? ky : ky - N)),
+                         (float)(src.os * (kz < h ? kz : kz - N))};
+    int i[3];
+    float w[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) rot_coord(R[a], R[3 + a], R[6 + a], ks[0], ks[1], ks[2], i[a], w[a]);
+    // periodic wrap of table indices (np is a power of two except at 96)
+    const int np = src.np;
+    auto wrp = [np](int v) {
+        if ((np & (np - 1)) == 0) return v & (np - 1);
+        const int r = v % np;
+        return r < 0 ? r + np : r;
+    };
+    const int x0 = wrp(i[0]), x1 = wrp(i[0] + 1), y0 = wrp(i[1]), y1 = wrp(i[1] + 1);
+    const float2 *p0 = src.table + (size_t)wrp(i[2]) * np * np;
+    const float2 *p1 = src.table + (size_t)wrp(i[2] + 1) * np * np;
+    const float2 a00 = __ldg(p0 + (size_t)y0 * np + x0), a01 = __ldg(p0 + (size_t)y0 * np + x1);
+    const float2 a10 = __ldg(p0 + (size_t)y1 * np + x0), a11 = __ldg(p0 + (size_t)y1 * np + x1);
+    const float2 b00 = __ldg(p1 + (size_t)y0 * np + x0), b01 = __ldg(p1 + (size_t)y0 * np + x1);
+    const float2 b10 = __ldg(p1 + (size_t)y1 * np + x0), b11 = __ldg(p1 + (size_t)y1 * np + x1);
+    const float wx = w[0], wy = w[1], wz = w[2];
+    auto lerp2 = [](float2 a, float2 b, float t) { return make_float2(fmaf(t, b.x - a.x, a.x), fmaf(t, b.y - a.y, a.y)); };
+    const float2 v = lerp2(lerp2(lerp2(a00, a01, wx), lerp2(a10, a11, wx), wy),
+                           lerp2(lerp2(b00, b01, wx), lerp2(b10, b11, wx), wy), wz);
+    return ((kx + ky + kz) & 1) ? make_float2(-v.x, -v.y) : v;
+}
+
 // MODE 0: full middle pass (product, gradient, inverse z) -> Y1 = S', Y2 = Gz'
 // MODE 1: forward only, spectrum * scale -> spec[kz*][ky*][kx*]  (stationary part)
+// MODE 2: as MODE 0 with the rotated spectrum interpolated from a table
+//         instead of transformed from resampled planes
 template <int N, int MODE>
 __global__ void __launch_bounds__(PassB<N>::NT, PassB<N>::MINB) passB_kernel(const float2 *__restrict__ X1,
                                                                               const float2 *__restrict__ R1hat,
                                                                               float2 *__restrict__ Y1,
-                                                                              float2 *__restrict__ Y2, float scale) {
+                                                                              float2 *__restrict__ Y2, float scale,
+                                                                              SpecSrc spec,
+                                                                              const float *__restrict__ rot9) {
     constexpr int H = PassB<N>::H, R1 = PassB<N>::R1, R2 = PassB<N>::R2, CW = PassB<N>::CW,
                   KPT = PassB<N>::KPT;
     constexpr size_t NH = (size_t)N * H;
@@ -313,27 +388,44 @@ __global__ void __launch_bounds__(PassB<N>::NT, PassB<N>::MINB) passB_kernel(con
     const size_t f = (size_t)blockIdx.x * CW + c;
     const int r = blockIdx.y;
     load_tw<N>(twN);
-    // forward stage 1
-    {
-        float2 v[R1];
-        const float2 *src = X1 + (size_t)r * N * NH + f;
-#pragma unroll
-        for (int n1 = 0; n1 < R1; ++n1) v[n1] = src[(size_t)(R2 * n1 + g) * NH];
-        __syncthreads();  // twiddles in place
-        RegDFT<R1, -1>::run(v);
-#pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1) E[(k1 * R2 + g) * CW + c] = k1 ? cmul(v[k1], twN[g * k1]) : v[k1];
-    }
-    __syncthreads();
-    // forward stage 2: X[j][k2] = slot R2 k1 + k2 for k1 = g + R2 j
     float2 X[KPT][R2];
+    if constexpr (MODE == 2) {
+        float R[9];
 #pragma unroll
-    for (int j = 0; j < KPT; ++j) {
-        const int k1 = g + R2 * j;
-        if (k1 < R1) {
+        for (int k = 0; k < 9; ++k) R[k] = __ldg(rot9 + 9 * r + k);
+        const int kys = (int)(f / H), kxs = (int)(f % H);
+        const int ky = slot_freq<N>(kys), kx = kxs == N / 2 ? N / 2 : slot_freq<N / 2>(kxs);
 #pragma unroll
-            for (int n2 = 0; n2 < R2; ++n2) X[j][n2] = E[(k1 * R2 + n2) * CW + c];
-            RegDFT<R2, -1>::run(X[j]);
+        for (int j = 0; j < KPT; ++j) {
+            const int k1 = g + R2 * j;
+            if (k1 < R1) {
+#pragma unroll
+                for (int k2 = 0; k2 < R2; ++k2) X[j][k2] = spectral_sample<N>(spec, R, kx, ky, slot_freq<N>(R2 * k1 + k2));
+            }
+        }
+        __syncthreads();  // twiddles in place
+    } else {
+        // forward stage 1
+        {
+            float2 v[R1];
+            const float2 *src = X1 + (size_t)r * N * NH + f;
+#pragma unroll
+            for (int n1 = 0; n1 < R1; ++n1) v[n1] = src[(size_t)(R2 * n1 + g) * NH];
+            __syncthreads();  // twiddles in place
+            RegDFT<R1, -1>::run(v);
+#pragma unroll
+            for (int k1 = 0; k1 < R1; ++k1) E[(k1 * R2 + g) * CW + c] = k1 ? cmul(v[k1], twN[g * k1]) : v[k1];
+        }
+        __syncthreads();
+        // forward stage 2: X[j][k2] = slot R2 k1 + k2 for k1 = g + R2 j
+#pragma unroll
+        for (int j = 0; j < KPT; ++j) {
+            const int k1 = g + R2 * j;
+            if (k1 < R1) {
+#pragma unroll
+                for (int n2 = 0; n2 < R2; ++n2) X[j][n2] = E[(k1 * R2 + n2) * CW + c];
+                RegDFT<R2, -1>::run(X[j]);
+            }
         }
     }
     if constexpr (MODE == 1) {
@@ -347,7 +439,7 @@ __global__ void __launch_bounds__(PassB<N>::NT, PassB<N>::MINB) passB_kernel(con
         }
         return;
     } else {
-        __syncthreads();  // E is free: it takes S's exchange
+        if constexpr (MODE == 0) __syncthreads();  // E is free: it takes S's exchange
         // product, gradient, inverse stage 1
 #pragma unroll
         for (int j = 0; j < KPT; ++j) {
@@ -751,6 +843,40 @@ __global__ void __launch_bounds__(Pencil<N>::NT) xinv_kernel(const float2 *__res
     x_pass<N, 1, PW, RBX, TP, NT, RBX>(plane, plane, 2 * H, H, Tb, twN, xt, out.Fy + fo, out.Fz + fo);
 }
 
+// ------------------------------------------- spectral-mode table of a part
+// rho2 (N^3) at the centre of an os N grid of zeros (same spacing): original
+// node n sits at padded node n + (os - 1) N / 2
+template <int N>
+__global__ void pad_center_kernel(const float *__restrict__ g, float *__restrict__ out, int np) {
+    const int off = (np - N) / 2;
+    const size_t total = (size_t)np * np * np;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % np) - off, y = (int)((i / np) % np) - off, z = (int)(i / ((size_t)np * np)) - off;
+        const bool in = x >= 0 && x < N && y >= 0 && y < N && z >= 0 && z < N;
+        out[i] = in ? __ldg(g + ((size_t)z * N + y) * N + x) : 0.f;
+    }
+}
+
+// full centred table [kz][ky][kx] (natural order) from the NP half spectrum
+// in slot order [kz*][ky*][kx*]: negative kx by Hermitian symmetry, and the
+// phase moved to the physical origin by (-1)^(kx+ky+kz)
+template <int NP>
+__global__ void spectral_complete_kernel(const float2 *__restrict__ spec, float2 *__restrict__ table) {
+    constexpr int HP = NP / 2 + 1;
+    const size_t total = (size_t)NP * NP * NP;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int kx = (int)(i % NP), ky = (int)((i / NP) % NP), kz = (int)(i / ((size_t)NP * NP));
+        float2 v;
+        if (2 * kx <= NP) {
+            v = __ldg(spec + ((size_t)perm_slot<NP>(kz) * NP + perm_slot<NP>(ky)) * HP + xslot<NP>(kx));
+        } else {
+            const int mz = (NP - kz) % NP, my = (NP - ky) % NP;
+            v = cconj(__ldg(spec + ((size_t)perm_slot<NP>(mz) * NP + perm_slot<NP>(my)) * HP + xslot<NP>(NP - kx)));
+        }
+        table[i] = ((kx + ky + kz) & 1) ? make_float2(-v.x, -v.y) : v;
+    }
+}
+
 // -------------------------------------------- natural-order spectrum copy
 // spec[kz*][ky*][kx*] (slot order, as left by pass B mode 1) -> out[kz][ky][kx]
 template <int N>
@@ -773,6 +899,7 @@ static cudaError_t set_pencil_attrs() {
     if ((e = cudaFuncSetAttribute(xinv_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Pencil<N>::smem_xinv))) return e;
     if ((e = cudaFuncSetAttribute(passB_kernel<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N>::smem))) return e;
     if ((e = cudaFuncSetAttribute(passB_kernel<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N>::smem))) return e;
+    if ((e = cudaFuncSetAttribute(passB_kernel<N, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N>::smem))) return e;
     return cudaSuccess;
 }
 
@@ -784,6 +911,7 @@ static cudaError_t set_smem_attrs() {
     if ((e = cudaFuncSetAttribute(passA_kernel<N, SRC_PLANES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassA<N>::smem))) return e;
     if ((e = cudaFuncSetAttribute(passB_kernel<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N>::smem))) return e;
     if ((e = cudaFuncSetAttribute(passB_kernel<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N>::smem))) return e;
+    if ((e = cudaFuncSetAttribute(passB_kernel<N, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N>::smem))) return e;
     if ((e = cudaFuncSetAttribute(passC_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassC<N>::smem))) return e;
     return cudaSuccess;
 }
@@ -811,14 +939,21 @@ static cudaError_t launch_resample_chunk(const float *rho, const float *rot9, fl
 template <int N>
 static cudaError_t launch_passB(const float2 *X1, const float2 *R1hat, float2 *Y1, float2 *Y2, int nrot,
                                 cudaStream_t st) {
-    passB_kernel<N, 0><<<dim3(N * PassB<N>::H / PassB<N>::CW, nrot), PassB<N>::NT, PassB<N>::smem, st>>>(X1, R1hat, Y1,
-                                                                                                       Y2, 0.f);
+    passB_kernel<N, 0><<<dim3(N * PassB<N>::H / PassB<N>::CW, nrot), PassB<N>::NT, PassB<N>::smem, st>>>(
+        X1, R1hat, Y1, Y2, 0.f, SpecSrc{nullptr, 0, 0}, nullptr);
     return cudaGetLastError();
 }
 template <int N>
 static cudaError_t launch_passB_fwd(const float2 *X1, float2 *spec, float scale, cudaStream_t st) {
-    passB_kernel<N, 1><<<dim3(N * PassB<N>::H / PassB<N>::CW, 1), PassB<N>::NT, PassB<N>::smem, st>>>(X1, nullptr, spec,
-                                                                                                    nullptr, scale);
+    passB_kernel<N, 1><<<dim3(N * PassB<N>::H / PassB<N>::CW, 1), PassB<N>::NT, PassB<N>::smem, st>>>(
+        X1, nullptr, spec, nullptr, scale, SpecSrc{nullptr, 0, 0}, nullptr);
+    return cudaGetLastError();
+}
+template <int N>
+static cudaError_t launch_passB_spectral(const float2 *table, int os, const float *rot9, const float2 *R1hat,
+                                         float2 *Y1, float2 *Y2, int nrot, cudaStream_t st) {
+    passB_kernel<N, 2><<<dim3(N * PassB<N>::H / PassB<N>::CW, nrot), PassB<N>::NT, PassB<N>::smem, st>>>(
+        nullptr, R1hat, Y1, Y2, 0.f, SpecSrc{table, os * N, os}, rot9);
     return cudaGetLastError();
 }
 template <int N>
@@ -846,6 +981,16 @@ template <int N>
 static cudaError_t launch_xinv(const float2 *ZS, const float2 *ZGy, const float2 *ZGz, FieldPtrs out, int nrot,
                                cudaStream_t st) {
     xinv_kernel<N><<<dim3(N * N / Pencil<N>::RBX, nrot), Pencil<N>::NT, Pencil<N>::smem_xinv, st>>>(ZS, ZGy, ZGz, out);
+    return cudaGetLastError();
+}
+template <int N>
+static cudaError_t launch_pad_center(const float *g, float *out, int np, cudaStream_t st) {
+    pad_center_kernel<N><<<4 * 148, 256, 0, st>>>(g, out, np);
+    return cudaGetLastError();
+}
+template <int NP>
+static cudaError_t launch_spectral_complete(const float2 *spec, float2 *table, cudaStream_t st) {
+    spectral_complete_kernel<NP><<<8 * 148, 256, 0, st>>>(spec, table);
     return cudaGetLastError();
 }
 template <int N>
@@ -914,6 +1059,16 @@ cudaError_t run_passB_forward(int n, const float2 *X1, float2 *spec, float scale
 }
 cudaError_t run_passC(int n, const float2 *Y1, const float2 *Y2, FieldPtrs out, int nrot, cudaStream_t st) {
     HF_DISPATCH(n, launch_passC<NN>(Y1, Y2, out, nrot, st));
+}
+cudaError_t run_pad_center(int n, const float *g, float *out, int np, cudaStream_t st) {
+    HF_DISPATCH_ALL(n, launch_pad_center<NN>(g, out, np, st));
+}
+cudaError_t run_spectral_complete(int np, const float2 *spec, float2 *table, cudaStream_t st) {
+    HF_DISPATCH_ALL(np, launch_spectral_complete<NN>(spec, table, st));
+}
+cudaError_t run_passB_spectral(int n, const float2 *table, int os, const float *rot9, const float2 *R1hat, float2 *Y1,
+                               float2 *Y2, int nrot, cudaStream_t st) {
+    HF_DISPATCH_ALL(n, launch_passB_spectral<NN>(table, os, rot9, R1hat, Y1, Y2, nrot, st));
 }
 cudaError_t run_unpermute(int n, const float2 *spec, float2 *out, cudaStream_t st) {
     HF_DISPATCH_ALL(n, launch_unpermute<NN>(spec, out, st));

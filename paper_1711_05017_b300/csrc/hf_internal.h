@@ -62,6 +62,14 @@ cudaError_t run_passB(int n, const float2 *X1, const float2 *R1hat, float2 *Y1, 
 cudaError_t run_passB_forward(int n, const float2 *X1, float2 *spec, float scale, cudaStream_t st);
 cudaError_t run_passC(int n, const float2 *Y1, const float2 *Y2, FieldPtrs out, int nrot, cudaStream_t st);
 cudaError_t run_unpermute(int n, const float2 *spec, float2 *out, cudaStream_t st);
+// spectral mode (rotation in the frequency domain): a moving part's centred
+// table is built from rho2 padded to np = os n nodes (pad, forward transform
+// at np, complete); pass B then interpolates the table instead of
+// transforming resampled planes
+cudaError_t run_pad_center(int n, const float *g, float *out, int np, cudaStream_t st);
+cudaError_t run_spectral_complete(int np, const float2 *spec, float2 *table, cudaStream_t st);
+cudaError_t run_passB_spectral(int n, const float2 *table, int os, const float *rot9, const float2 *R1hat, float2 *Y1,
+                               float2 *Y2, int nrot, cudaStream_t st);
 // pencil pipeline (any N; the only one for N = 256): planes -> Xa -> X1 (forward x, y),
 // then pass B, then Y1/Y2 -> Z_S, Z_Gy, Z_Gz (inverse y) -> fields (inverse x)
 cudaError_t run_xfwd(int n, const float *planes, float2 *Xa, int nrot, cudaStream_t st);
