@@ -44,6 +44,7 @@ def _L():
         _lib.or_fields_spec.argtypes = [i, d, d, d, d, d, d]
         _lib.or_spectral_table.argtypes = [i, i, d, d]
         _lib.or_spectral_rotate.argtypes = [i, i, d, d, d]
+        _lib.or_lowpass.argtypes = [i, d, d, i, i, d, d, d]
     return _lib
 
 
@@ -154,6 +155,20 @@ def spectral_rotate(table, n, R, os=1):
     out = np.empty((n, n, n), dtype=np.complex128)
     _L().or_spectral_rotate(n, int(os), table.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _p(_f64(R)),
                             out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return out
+
+
+def lowpass(rho1, table, os, K, R, t):
+    """Single-pose (E, Fx, Fy, Fz, Tx, Ty, Tz) from spectra truncated to
+    |k~_a| <= K, the inverse transform summed at the one translation t
+    (Section 4.2, "Truncated Inverse FFT"; Section 3.3 low-pass filtering);
+    T is the exact rotational derivative of the interpolated model."""
+    rho1 = _f64(rho1)
+    table = np.ascontiguousarray(table, dtype=np.complex128)
+    n = rho1.shape[0]
+    out = np.empty(7)
+    _L().or_lowpass(n, _p(rho1), table.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(os), int(K),
+                    _p(_f64(R)), _p(_f64(np.asarray(t, dtype=np.float64).reshape(3))), _p(out))
     return out
 
 

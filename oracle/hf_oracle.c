@@ -364,6 +364,97 @@ void or_spectral_rotate(int n, int os, const double *table_ri, const double *R, 
             }
 }
 
+/* Periodic trilinear interpolation of a complex table and its gradient
+ * (d/du_x, d/du_y, d/du_z in index units) at u. */
+static cplx trilinear_c_grad(int n, const cplx *g, const double u[3], cplx grad[3])
+{
+    long i0[3];
+    double f[3];
+    for (int a = 0; a < 3; ++a) {
+        const double fl = floor(u[a]);
+        i0[a] = (long)fl;
+        f[a] = u[a] - fl;
+    }
+    cplx c[2][2][2];
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx)
+                c[dz][dy][dx] = g[idx3(n, wrap(i0[2] + dz, n), wrap(i0[1] + dy, n), wrap(i0[0] + dx, n))];
+    cplx v = 0.0;
+    grad[0] = grad[1] = grad[2] = 0.0;
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+                const double wx = dx ? f[0] : 1 - f[0], wy = dy ? f[1] : 1 - f[1], wz = dz ? f[2] : 1 - f[2];
+                const double sx = dx ? 1 : -1, sy = dy ? 1 : -1, sz = dz ? 1 : -1;
+                v += wx * wy * wz * c[dz][dy][dx];
+                grad[0] += sx * wy * wz * c[dz][dy][dx];
+                grad[1] += wx * sy * wz * c[dz][dy][dx];
+                grad[2] += wx * wy * sz * c[dz][dy][dx];
+            }
+    return v;
+}
+
+/* ------------------------------------------------------------------ */
+/* Single-pose evaluation with truncated spectra, Section 4.2            */
+/* ("Truncated Inverse FFT") with the low-pass filtering of Section 3.3: */
+/* only the modes with |k~_a| <= K on every axis are kept, and the       */
+/* inverse transform is summed at the one translation t instead of over  */
+/* the grid:                                                             */
+/*   S(k)  = (h^3/N^3) rho1^(k) conj(B(k)),  B(k) = (-1)^(kx+ky+kz)       */
+/*           trilinear(table, os R^T k~)   (Section 3.2, step 1)          */
+/*   E     = sum_k Re S(k) exp(i pi k~.t)    (omega = k~/2, N h = 2)      */
+/*   F_d   = -sum_k Re i pi k~_d S(k) exp(i pi k~.t)        (Eq. 6a)      */
+/*   T_a   = -dE/dtheta_a for R -> exp(theta [e_a]x) R: the exact         */
+/*           derivative of the interpolated model, d(os R^T k~)/dtheta_a  */
+/*           = -os R^T (e_a x k~)                                         */
+/* out7 = (E, Fx, Fy, Fz, Tx, Ty, Tz).                                    */
+/* ------------------------------------------------------------------ */
+void or_lowpass(int n, const double *rho1, const double *table_ri, int os, int K, const double *R,
+                const double *t, double *out7)
+{
+    const long m = (long)n * n * n;
+    const int np = os * n;
+    const double h = 2.0 / n, scale = h * h * h / (double)m;
+    const cplx *T = (const cplx *)table_ri;
+    cplx *A = malloc(sizeof(cplx) * m);
+    for (long i = 0; i < m; ++i) A[i] = rho1[i];
+    or_fft3d(n, (double *)A, -1);
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int kz = -K; kz <= K; ++kz)
+        for (int ky = -K; ky <= K; ++ky)
+            for (int kx = -K; kx <= K; ++kx) {
+                const double k[3] = {kx, ky, kz};
+                double u[3];
+                for (int a = 0; a < 3; ++a)
+                    u[a] = os * (R[0 * 3 + a] * k[0] + R[1 * 3 + a] * k[1] + R[2 * 3 + a] * k[2]);
+                cplx grad[3];
+                cplx b = trilinear_c_grad(np, T, u, grad);
+                const int odd = (kx + ky + kz) & 1;
+                if (odd) { b = -b; grad[0] = -grad[0]; grad[1] = -grad[1]; grad[2] = -grad[2]; }
+                const cplx a1 = scale * A[idx3(n, wrap(kz, n), wrap(ky, n), wrap(kx, n))];
+                const cplx ph = cexp(I * PI * (k[0] * t[0] + k[1] * t[1] + k[2] * t[2]));
+                const cplx term = a1 * conj(b) * ph;
+                acc[0] += creal(term);
+                for (int d = 0; d < 3; ++d) acc[1 + d] -= creal(I * PI * k[d] * term);
+                for (int ax = 0; ax < 3; ++ax) {
+                    /* v = -os R^T (e_a x k) */
+                    double ek[3] = {0, 0, 0};
+                    if (ax == 0) { ek[1] = -k[2]; ek[2] = k[1]; }
+                    else if (ax == 1) { ek[0] = k[2]; ek[2] = -k[0]; }
+                    else { ek[0] = -k[1]; ek[1] = k[0]; }
+                    cplx db = 0.0;
+                    for (int c = 0; c < 3; ++c) {
+                        const double vc = -os * (R[0 * 3 + c] * ek[0] + R[1 * 3 + c] * ek[1] + R[2 * 3 + c] * ek[2]);
+                        db += grad[c] * vc;
+                    }
+                    acc[4 + ax] -= creal(a1 * conj(db) * ph);
+                }
+            }
+    for (int i = 0; i < 7; ++i) out7[i] = acc[i];
+    free(A);
+}
+
 /* Geodesic angle between two unit quaternions (double cover aware). */
 static double quat_angle(const double *a, const double *b)
 {
