@@ -205,6 +205,27 @@ hf_status hf_query(const hf_fieldset *fs, const float t[3], const float q[4], in
 hf_status hf_query_batch(const hf_fieldset *fs, const float *d_tq, int Q, int k_blend,
                          float *d_out, hf_stream stream);
 
+/* ---- single poses from truncated spectra (the paper's real-time mode) ----
+ * Energy, force and torque at an arbitrary pose (R, t), any rotation, from
+ * the stationary part's spectrum and the moving part's spectral table
+ * (hf_part_spectral), keeping only the modes with |k~_a| <= K on every axis
+ * (Section 4.2, "Truncated Inverse FFT"; Section 3.3, low-pass filtering;
+ * (2K+1)^3 modes, K = 8 keeps 17^3) and summing the inverse transform at the
+ * one translation t instead of over the grid:
+ *   S(k) = (h^3/N^3) rho1^(k) conj(B(k)),  B(k) = (-1)^(kx+ky+kz)
+ *          trilinear(table, os R^T k~)      (as HF_SPECTRAL field sets)
+ *   E = sum Re S e^{i pi k~.t},  F = -grad_t E,  T = -grad_theta E for world
+ *   perturbations R -> exp([d]x) R (the exact derivative of the interpolated
+ *   sum).  out7 = (E, Fx, Fy, Fz, Tx, Ty, Tz).
+ * hf_lowpass_query: host in/out, synchronous (the context's query stream).
+ * hf_lowpass_query_batch: d_tq Q x 7 (tx, ty, tz, qw, qx, qy, qz) -> d_out
+ * Q x 7 on `stream`.  Errors: HF_EINVAL (parts, K outside 1..N/2-1, bad
+ * quaternion), HF_ENOTREADY (no table), HF_ECUDA. */
+hf_status hf_lowpass_query(const hf_part *s1, const hf_part *s2, int K, const float t[3], const float q[4],
+                           float out7[7]);
+hf_status hf_lowpass_query_batch(const hf_part *s1, const hf_part *s2, int K, const float *d_tq, int Q,
+                                 float *d_out, hf_stream stream);
+
 /* Device bytes hf_fieldset_create(n, R, flags) charges (0 if unsupported). */
 size_t hf_fieldset_bytes(int n, int R, unsigned flags);
 

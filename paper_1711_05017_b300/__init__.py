@@ -14,7 +14,8 @@ from . import _binding as B
 from ._binding import (HF_E, HF_F, HF_MOVING, HF_PREC_SPLIT_BF16, HF_PREC_SPLIT_F16, HF_SPECTRAL,  # noqa: F401
                        HF_STATIONARY, HF_T, HF_TORQUE_F64, HFError)
 
-__all__ = ["Context", "Part", "FieldSet", "Batch", "Server", "HFError", "resample", "rfft3d", "version"]
+__all__ = ["Context", "Part", "FieldSet", "Batch", "Server", "HFError", "lowpass_query", "lowpass_query_batch",
+           "resample", "rfft3d", "version"]
 
 
 def _torch():
@@ -291,6 +292,27 @@ class Batch:
             self.release()
         except Exception:
             pass
+
+
+def lowpass_query(s1, s2, t, q, K=8):
+    """hf_lowpass_query: (E, Fx, Fy, Fz, Tx, Ty, Tz) at one pose from spectra
+    truncated to |k~| <= K (the moving part needs Part.spectral())."""
+    out = np.zeros(7, dtype=np.float32)
+    t = np.ascontiguousarray(t, dtype=np.float32).reshape(3)
+    q = np.ascontiguousarray(q, dtype=np.float32).reshape(4)
+    B.check(B.lib().hf_lowpass_query(s1.handle, s2.handle, int(K), B.fptr(t), B.fptr(q), B.fptr(out)))
+    return out
+
+
+def lowpass_query_batch(s1, s2, tq, K=8, out=None, stream=None):
+    """hf_lowpass_query_batch: tq (Q, 7) CUDA float32 -> (Q, 7)."""
+    torch = _torch()
+    Q = tq.shape[0]
+    if out is None:
+        out = torch.empty((Q, 7), dtype=torch.float32, device=tq.device)
+    B.check(B.lib().hf_lowpass_query_batch(s1.handle, s2.handle, int(K), _dev(tq, torch.float32), int(Q),
+                                           _dev(out, torch.float32), _stream_ptr(stream)))
+    return out
 
 
 def resample(rho, R, out=None, stream=None):

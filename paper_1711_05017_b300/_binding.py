@@ -86,6 +86,8 @@ SIGNATURES = {
     "hf_tc_timeouts": (_i, [_i]),
     "hf_part_spectral": (_i, [_vp, _i, _vp]),
     "hf_part_spectral_os": (_i, [_vp]),
+    "hf_lowpass_query": (_i, [_vp, _vp, _i, _fp, _fp, _fp]),
+    "hf_lowpass_query_batch": (_i, [_vp, _vp, _i, _vp, _i, _vp, _vp]),
 }
 
 

@@ -72,6 +72,9 @@ struct hf_ctx {
     float *h_qout = nullptr;  // mapped pinned 7-float answer mailbox
     float *d_qout = nullptr;  // its device alias
     std::mutex qmu;
+    // single-pose low-pass scratch (partial sums and the pose counter), under qmu
+    double *lp_part = nullptr;
+    unsigned *lp_count = nullptr;
     // per-kernel timing
     bool prof = false;
     std::mutex pmu;
@@ -273,6 +276,8 @@ extern "C" void hf_ctx_destroy(hf_ctx *c) {
     cudaSetDevice(c->device);
     if (c->qstream) cudaStreamDestroy(c->qstream);
     if (c->h_qout) cudaFreeHost(c->h_qout);
+    if (c->lp_part) cudaFree(c->lp_part);
+    if (c->lp_count) cudaFree(c->lp_count);
     hf_profile_read(c);
     for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
     delete c;
@@ -1081,6 +1086,70 @@ extern "C" hf_status hf_query(const hf_fieldset *fs, const float t[3], const flo
 }
 
 // ----------------------------------------------------- single-step entries
+// ------------------------------------------------- truncated single poses
+static hf_status lowpass_check(const hf_part *s1, const hf_part *s2, int K, const char *who) {
+    if (!s1 || !s2) return fail(HF_EINVAL, "%s: NULL part", who);
+    if (s1->role != HF_STATIONARY || s2->role != HF_MOVING)
+        return fail(HF_EINVAL, "%s: s1 must be HF_STATIONARY and s2 HF_MOVING", who);
+    if (s1->n != s2->n) return fail(HF_EINVAL, "%s: grid sizes differ (%d, %d)", who, s1->n, s2->n);
+    if (K < 1 || 2 * K >= s1->n) return fail(HF_EINVAL, "%s: K=%d outside 1..N/2-1", who, K);
+    if (!s2->table) return fail(HF_ENOTREADY, "%s: the moving part has no spectral table (hf_part_spectral)", who);
+    return HF_OK;
+}
+
+extern "C" hf_status hf_lowpass_query(const hf_part *s1, const hf_part *s2, int K, const float t[3], const float q[4],
+                                      float out7[7]) {
+    if (!t || !q || !out7) return fail(HF_EINVAL, "hf_lowpass_query: NULL argument");
+    hf_status s = lowpass_check(s1, s2, K, "hf_lowpass_query");
+    if (s != HF_OK) return s;
+    const Quat Q = qnorm(q);
+    if (!qfinite(Q)) return fail(HF_EINVAL, "hf_lowpass_query: the quaternion is zero or not finite");
+    double M[9];
+    rot_from_quat(Q, M);
+    hf::LowpassPose pose;
+    for (int k = 0; k < 9; ++k) pose.R[k] = (float)M[k];
+    for (int a = 0; a < 3; ++a) pose.t[a] = t[a];
+    hf_ctx *c = s1->ctx;
+    std::lock_guard<std::mutex> g(c->qmu);
+    CU(cudaSetDevice(c->device));
+    if (!c->lp_part) {
+        CU(cudaMalloc(&c->lp_part, sizeof(double) * 7 * hf::kLowpassMaxSplit));
+        CU(cudaMalloc(&c->lp_count, sizeof(unsigned)));
+        CU(cudaMemset(c->lp_count, 0, sizeof(unsigned)));
+    }
+    (void)cudaGetLastError();
+    CU(hf::run_lowpass(s1->n, s1->spec, s2->table, s2->table_os, K, nullptr, 1, &pose, c->lp_part, c->lp_count,
+                       c->d_qout, c->qstream));
+    CU(cudaStreamSynchronize(c->qstream));
+    for (int a = 0; a < 7; ++a) out7[a] = ((volatile float *)c->h_qout)[a];
+    return HF_OK;
+}
+
+extern "C" hf_status hf_lowpass_query_batch(const hf_part *s1, const hf_part *s2, int K, const float *d_tq, int Q,
+                                            float *d_out, hf_stream stream) {
+    if ((!d_tq || !d_out) && Q > 0) return fail(HF_EINVAL, "hf_lowpass_query_batch: NULL buffer");
+    if (Q < 0) return fail(HF_EINVAL, "hf_lowpass_query_batch: Q=%d", Q);
+    hf_status s = lowpass_check(s1, s2, K, "hf_lowpass_query_batch");
+    if (s != HF_OK) return s;
+    if (Q == 0) return HF_OK;
+    CU(cudaSetDevice(s1->ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t pb = sizeof(double) * 7 * (size_t)hf::lowpass_split(K) * Q;
+    double *part = nullptr;
+    unsigned *count = nullptr;
+    CU(cudaMallocAsync(&part, pb, st));
+    cudaError_t e = cudaMallocAsync(&count, sizeof(unsigned) * (size_t)Q, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(count, 0, sizeof(unsigned) * (size_t)Q, st);
+    if (e == cudaSuccess) {
+        (void)cudaGetLastError();
+        e = hf::run_lowpass(s1->n, s1->spec, s2->table, s2->table_os, K, d_tq, Q, nullptr, part, count, d_out, st);
+    }
+    cudaFreeAsync(part, st);
+    if (count) cudaFreeAsync(count, st);
+    if (e != cudaSuccess) return fail(HF_ECUDA, "hf_lowpass_query_batch: %s", cudaGetErrorString(e));
+    return HF_OK;
+}
+
 extern "C" hf_status hf_resample(int n, const float *d_rho, const float h_R[9], float *d_out, hf_stream stream) {
     if (!hf::supported_n(n)) return fail(HF_EUNSUPPORTED, "hf_resample: N=%d not supported", n);
     if (!d_rho || !h_R || !d_out) return fail(HF_EINVAL, "hf_resample: NULL argument");

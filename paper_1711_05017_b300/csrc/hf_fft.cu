@@ -32,6 +32,7 @@
 #include <stdlib.h>
 
 #include "hf_dft.cuh"
+#include "hf_spec.cuh"
 #include "hf_internal.h"
 #include "hf_sample.cuh"
 
@@ -295,46 +296,9 @@ struct PassB {
     static_assert((N * H) % CW == 0, "whole column tiles");
 };
 
-// Spectral-mode source (MODE 2): the rotated moving spectrum read off the
-// part's centred table (os N per axis, full cube, natural order) by periodic
-// trilinear interpolation at os R^T k~ (Section 3.2, step 1), times
+// Spectral-mode source of pass B: the table interpolated at os R^T k~, times
 // (-1)^(kx+ky+kz) to move the phase back to the box corner; 0 on Nyquist
-// planes.  The coordinate is summed in double-float arithmetic (exact
-// products, compensated sums) so that the fractional weights carry the
-// rotation to ~1e-12 at any table size.
-struct SpecSrc {
-    const float2 *table;
-    int np;  // os * N, power of two
-    int os;
-};
-
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
-
-// floor and fraction of r0 k0 + r1 k1 + r2 k2 (integer k), accurate
-__device__ __forceinline__ void rot_coord(float r0, float r1, float r2, float k0, float k1, float k2, int &i0,
-                                          float &fr) {
-    const float p0 = r0 * k0, p1 = r1 * k1, p2 = r2 * k2;
-    const float e0 = fmaf(r0, k0, -p0), e1 = fmaf(r1, k1, -p1), e2 = fmaf(r2, k2, -p2);
-    float s01, t01, s, t;
-    two_sum(p0, p1, s01, t01);
-    two_sum(s01, p2, s, t);
-    const float corr = ((t01 + t) + (e0 + e1)) + e2;
-    const float fl = floorf(s);
-    fr = (s - fl) + corr;  // s - fl is exact
-    i0 = (int)fl;
-    if (fr < 0.f) {
-        fr += 1.f;
-        --i0;
-    } else if (fr >= 1.f) {
-        fr -= 1.f;
-        ++i0;
-    }
-}
-
+// planes.
 template <int N>
 __device__ __forceinline__ float2 spectral_sample(const SpecSrc &src, const float *R, int kx, int ky, int kz) {
     const int h = N / 2;
@@ -345,16 +309,11 @@ __device__ __forceinline__ float2 spectral_sample(const SpecSrc &src, const floa
     float w[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) rot_coord(R[a], R[3 + a], R[6 + a], ks[0], ks[1], ks[2], i[a], w[a]);
-    // periodic wrap of table indices (np is a power of two except at 96)
     const int np = src.np;
-    auto wrp = [np](int v) {
-        if ((np & (np - 1)) == 0) return v & (np - 1);
-        const int r = v % np;
-        return r < 0 ? r + np : r;
-    };
-    const int x0 = wrp(i[0]), x1 = wrp(i[0] + 1), y0 = wrp(i[1]), y1 = wrp(i[1] + 1);
-    const float2 *p0 = src.table + (size_t)wrp(i[2]) * np * np;
-    const float2 *p1 = src.table + (size_t)wrp(i[2] + 1) * np * np;
+    const int x0 = table_wrap(i[0], np), x1 = table_wrap(i[0] + 1, np);
+    const int y0 = table_wrap(i[1], np), y1 = table_wrap(i[1] + 1, np);
+    const float2 *p0 = src.table + (size_t)table_wrap(i[2], np) * np * np;
+    const float2 *p1 = src.table + (size_t)table_wrap(i[2] + 1, np) * np * np;
     const float2 a00 = __ldg(p0 + (size_t)y0 * np + x0), a01 = __ldg(p0 + (size_t)y0 * np + x1);
     const float2 a10 = __ldg(p0 + (size_t)y1 * np + x0), a11 = __ldg(p0 + (size_t)y1 * np + x1);
     const float2 b00 = __ldg(p1 + (size_t)y0 * np + x0), b01 = __ldg(p1 + (size_t)y0 * np + x1);
@@ -479,11 +438,6 @@ __global__ void __launch_bounds__(PassB<N>::NT, PassB<N>::MINB) passB_kernel(con
     }
 }
 
-// x slot of half-spectrum index k in [0, N/2]
-template <int N>
-__device__ __forceinline__ int xslot(int k) {
-    return k == N / 2 ? N / 2 : perm_slot<N / 2>(k);
-}
 
 // ------------------------------------------------------------------ pass C
 // One CTA per (z-plane, rotation) holding S'' and Gy'' side by side (pitch

@@ -70,6 +70,18 @@ cudaError_t run_pad_center(int n, const float *g, float *out, int np, cudaStream
 cudaError_t run_spectral_complete(int np, const float2 *spec, float2 *table, cudaStream_t st);
 cudaError_t run_passB_spectral(int n, const float2 *table, int os, const float *rot9, const float2 *R1hat, float2 *Y1,
                                float2 *Y2, int nrot, cudaStream_t st);
+// hf_lowpass.cu: single poses from spectra truncated to |k~_a| <= K (one
+// pose by value when `one` is given, else Q poses d_tq Q x 7); out Q x 7
+struct LowpassPose {
+    float R[9];
+    float t[3];
+};
+// thread blocks per pose; scratch per call: part Q x split x 7 doubles and
+// count Q unsigned, zero on entry (each pose's counter is reset on exit)
+constexpr int kLowpassMaxSplit = 512;
+int lowpass_split(int K);
+cudaError_t run_lowpass(int n, const float2 *spec1, const float2 *table, int os, int K, const float *d_tq, int Q,
+                        const LowpassPose *one, double *part, unsigned *count, float *out, cudaStream_t st);
 // pencil pipeline (any N; the only one for N = 256): planes -> Xa -> X1 (forward x, y),
 // then pass B, then Y1/Y2 -> Z_S, Z_Gy, Z_Gz (inverse y) -> fields (inverse x)
 cudaError_t run_xfwd(int n, const float *planes, float2 *Xa, int nrot, cudaStream_t st);
