@@ -331,11 +331,16 @@ def run_ours(args, rank, world, local_rank):
                "sample": desc, "splat_s": round(t_splat, 2)}
 
     serving = batch = None
-    if rank == 0 and world == 1 and (args.serve_seconds > 0 or args.batch_steps > 0 or args.precision_rotations > 0):
+    if rank == 0 and world == 1 and (args.serve_seconds > 0 or args.batch_steps > 0 or args.precision_rotations > 0
+                                     or args.spectral):
         del fs
         torch.cuda.empty_cache()
     if rank == 0 and world == 1 and args.batch_steps > 0:
         batch = run_batch(args, local_rank)
+        torch.cuda.empty_cache()
+    spectral = None
+    if rank == 0 and world == 1 and args.spectral:
+        spectral = run_spectral(args, local_rank)
         torch.cuda.empty_cache()
     precision = None
     if rank == 0 and world == 1 and args.precision_rotations > 0:
@@ -366,6 +371,7 @@ def run_ours(args, rank, world, local_rank):
             "clocks": clk.summary(),
             "batch": batch,
             "precision": precision,
+            "spectral": spectral,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)
@@ -593,6 +599,63 @@ def precision_oracle_error(ctx, hf, q, variants):
     return res
 
 
+# ------------------------------------------------- frequency-domain modes
+def run_spectral(args, local_rank):
+    """The c2 workload (128^3, 1024 rotations, E+F+T) with the rotation done
+    in the frequency domain (HF_SPECTRAL; tables padded os = 1 and 2), its
+    deviation from the spatial route, and single-pose queries from truncated
+    spectra (|k~| <= K) at a 1 kHz-style random walk."""
+    import torch
+    import paper_1711_05017_b300 as hf
+    dev = torch.device("cuda", local_rank)
+    n, R = 128, args.rotations
+    s1, s2 = synth.c2_pair(0)
+    ctx = hf.Context(local_rank)
+    cu = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=dev)  # noqa: E731
+    p1 = ctx.part(ctx.density_build(n, cu(s1.pts), cu(s1.sigma)), hf.HF_STATIONARY)
+    p2 = ctx.part(ctx.density_build(n, cu(s2.pts), cu(s2.sigma)), hf.HF_MOVING)
+    ctx.autotune(n, args.tune_cache)
+    q = rank_rotations(0, R)
+    stream = torch.cuda.current_stream()
+    out, ref = {}, None
+    for name, fl, os_ in (("spatial", 0, 0), ("spectral_os1", hf.HF_SPECTRAL, 1), ("spectral_os2", hf.HF_SPECTRAL, 2)):
+        if os_:
+            p2.spectral(os_)
+        fs = ctx.fieldset(n, R, hf.HF_E | hf.HF_F | hf.HF_T | fl)
+        fs.compute(p1, p2, q)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(2):
+            fs.compute(p1, p2, q)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 2
+        f3 = np.stack([np.stack([fs.get(r, f).cpu().numpy().astype(np.float64) for f in range(4)]) for r in (0, 1)])
+        if ref is None:
+            ref = f3
+        out[name] = {"value": round(R / (ms / 1e3), 1), "unit": UNIT, "ms_per_build": round(ms, 2),
+                     "max_abs_dev_from_spatial_over_max": [
+                         round(float(np.abs(f3[:, f] - ref[:, f]).max() / np.abs(ref[:, f]).max()), 6)
+                         for f in range(4)]}
+        fs.release()
+    lp = {}
+    tw, qw = synth.translation_walk(7, 2000), synth.quaternion_walk(8, 2000)
+    for os_ in (1, 2):
+        p2.spectral(os_)
+        for K in (8, 16):
+            lat = []
+            for i in range(2000):
+                a = time.perf_counter()
+                hf.lowpass_query(p1, p2, tw[i], qw[i], K=K)
+                lat.append((time.perf_counter() - a) * 1e6)
+            lat = np.array(lat[100:])
+            lp[f"os{os_}_K{K}"] = {"modes": (2 * K + 1) ** 3, "p50_us": round(float(np.percentile(lat, 50)), 1),
+                                  "p99_us": round(float(np.percentile(lat, 99)), 1)}
+    return {"workload": f"c2 peg-in-hole skeletons, 128^3, {R} rotations, E+F+T; rotation in the frequency domain",
+            "field_build": out, "lowpass_single_pose": lp}
+
+
 # ------------------------------------------------------- serving workload
 SERVE_RCAP = {64: 512, 128: 96, 256: 12}  # rotations per build, capped so that every session's set plus the builds in flight fit 120 GB
 
@@ -726,6 +789,7 @@ def main():
                     help="rotations of the 256^3 precision comparison (0 = skip)")
     ap.add_argument("--precision-oracle", type=int, default=0,
                     help="rotations checked against the FP64 oracle in the precision comparison (slow)")
+    ap.add_argument("--spectral", type=int, default=1, help="measure the frequency-domain modes (0 = skip)")
     ap.add_argument("--serve-seconds", type=float, default=20.0,
                     help="length of the 16-session serving run (0 = skip)")
     args = ap.parse_args()
