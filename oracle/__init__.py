@@ -45,6 +45,7 @@ def _L():
         _lib.or_spectral_table.argtypes = [i, i, d, d]
         _lib.or_spectral_rotate.argtypes = [i, i, d, d, d]
         _lib.or_lowpass.argtypes = [i, d, d, i, i, d, d, d]
+        _lib.or_torque_analytic.argtypes = [i, d, d, d, d, d]
     return _lib
 
 
@@ -156,6 +157,18 @@ def spectral_rotate(table, n, R, os=1):
     _L().or_spectral_rotate(n, int(os), table.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _p(_f64(R)),
                             out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     return out
+
+
+def torque_analytic(rho1, rho2r):
+    """Torque fields (Tx, Ty, Tz) over all lags by the rotational gradient of
+    Eq. 6b, with the moment moved onto the stationary part by integrating by
+    parts: T = C(-u x grad rho1, rho2R) - t x F (T = -grad_theta E for world
+    perturbations about the moving part's reference point)."""
+    rho1, rho2r = _f64(rho1), _f64(rho2r)
+    n = rho1.shape[0]
+    outs = [np.empty_like(rho1) for _ in range(3)]
+    _L().or_torque_analytic(n, _p(rho1), _p(rho2r), *[_p(o) for o in outs])
+    return tuple(outs)
 
 
 def lowpass(rho1, table, os, K, R, t):

@@ -291,6 +291,75 @@ void or_fields_spec(int n, const double *rho1, const double *b_ri,
 }
 
 /* ------------------------------------------------------------------ */
+/* Analytic torque field, the rotational gradient of Eq. 6b.  For world-  */
+/* frame perturbations R -> exp(theta [e_a]x) R of the moving part about  */
+/* its reference point (at t),                                           */
+/*   T_a(t) = -dE/dtheta_a = integral rho1(t + r) (r x grad rho2R(r))_a dr */
+/* (Eq. 6b's moment field r rho2).  Integrating by parts moves the moment */
+/* onto the stationary part:                                             */
+/*   T(t) = C(G, rho2R)(t) - t x F(t),  G(u) = -u x grad rho1(u),         */
+/* with C the correlation that gives E (Eqs. 3, 5) and F the force.      */
+/* Discretisation: grad rho1 is the spectral derivative (multiplier      */
+/* 2 pi i omega, Nyquist 0, as for the force), u_n = -1 + n h per axis,   */
+/* t the signed lag j~ h; outputs the three torque fields.                */
+/* ------------------------------------------------------------------ */
+void or_torque_analytic(int n, const double *rho1, const double *rho2r, double *Tx, double *Ty, double *Tz)
+{
+    const long m = (long)n * n * n;
+    const double h = 2.0 / n, dv = h * h * h;
+    cplx *A = malloc(sizeof(cplx) * m), *B = malloc(sizeof(cplx) * m), *W = malloc(sizeof(cplx) * m);
+    double *g[3], *F[3];
+    for (int d = 0; d < 3; ++d) { g[d] = malloc(sizeof(double) * m); F[d] = malloc(sizeof(double) * m); }
+    for (long i = 0; i < m; ++i) { A[i] = rho1[i]; B[i] = rho2r[i]; }
+    or_fft3d(n, (double *)A, -1);
+    or_fft3d(n, (double *)B, -1);
+    /* grad rho1, spectrally */
+    for (int d = 0; d < 3; ++d) {
+        for (int kz = 0; kz < n; ++kz)
+            for (int ky = 0; ky < n; ++ky)
+                for (int kx = 0; kx < n; ++kx) {
+                    const int kd = d == 0 ? kx : d == 1 ? ky : kz;
+                    const double kt = (n % 2 == 0 && kd == n / 2) ? 0.0 : (double)signed_k(kd, n);
+                    const long i = idx3(n, kz, ky, kx);
+                    W[i] = 2.0 * PI * I * (kt / (n * h)) * A[i];
+                }
+        or_fft3d(n, (double *)W, +1);
+        for (long i = 0; i < m; ++i) g[d][i] = creal(W[i]) / (double)m;
+    }
+    /* force field of the pair (for the t x F term) */
+    double *E = malloc(sizeof(double) * m);
+    or_fields(n, rho1, rho2r, E, F[0], F[1], F[2]);
+    free(E);
+    double *outs[3] = {Tx, Ty, Tz};
+    for (int a = 0; a < 3; ++a) {
+        /* G_a = -(u x grad rho1)_a */
+        for (int z = 0; z < n; ++z)
+            for (int y = 0; y < n; ++y)
+                for (int x = 0; x < n; ++x) {
+                    const double u[3] = {-1.0 + x * h, -1.0 + y * h, -1.0 + z * h};
+                    const long i = idx3(n, z, y, x);
+                    const double gx = g[0][i], gy = g[1][i], gz = g[2][i];
+                    const double c = a == 0 ? u[1] * gz - u[2] * gy : a == 1 ? u[2] * gx - u[0] * gz : u[0] * gy - u[1] * gx;
+                    W[i] = -c;
+                }
+        or_fft3d(n, (double *)W, -1);
+        for (long i = 0; i < m; ++i) W[i] = dv * W[i] * conj(B[i]);
+        or_fft3d(n, (double *)W, +1);
+        for (int jz = 0; jz < n; ++jz)
+            for (int jy = 0; jy < n; ++jy)
+                for (int jx = 0; jx < n; ++jx) {
+                    const long i = idx3(n, jz, jy, jx);
+                    const double t[3] = {signed_k(jx, n) * h, signed_k(jy, n) * h, signed_k(jz, n) * h};
+                    const double f[3] = {F[0][i], F[1][i], F[2][i]};
+                    const double txf = a == 0 ? t[1] * f[2] - t[2] * f[1] : a == 1 ? t[2] * f[0] - t[0] * f[2] : t[0] * f[1] - t[1] * f[0];
+                    outs[a][i] = creal(W[i]) / (double)m - txf;
+                }
+    }
+    for (int d = 0; d < 3; ++d) { free(g[d]); free(F[d]); }
+    free(A); free(B); free(W);
+}
+
+/* ------------------------------------------------------------------ */
 /* Rotation in the frequency domain, Section 3.2 step 1: the spectrum   */
 /* of the rotated density rho2(R^T p) is rho2^(R^T omega), read off a   */
 /* precomputed spectrum by trilinear interpolation.                     */
