@@ -90,6 +90,15 @@ typedef void *hf_stream; /* a cudaStream_t */
  * interpolation at R^T omega instead of resampling the grid and transforming
  * it.  The moving part must have a table (HF_ENOTREADY otherwise). */
 #define HF_SPECTRAL 0x80u
+/* Analytic torque (the rotational gradient of Eq. 6b) in the torque slots
+ * instead of the least-squares differences of HF_T: with the moment moved
+ * onto the stationary part by integration by parts,
+ *   T(t) = C(G, rho2R)(t) - t x F(t),  G(u) = -u x grad rho1(u),
+ * C the correlation that gives E, t the signed lag; T = -grad_theta E for
+ * world perturbations about the moving part's reference point, exact for the
+ * band-limited fields.  Needs hf_part_moments on the stationary part; N <=
+ * 128, spatial route (HF_EUNSUPPORTED otherwise); excludes HF_T. */
+#define HF_TA 0x100u
 
 /* Field indices for hf_fieldset_get / hf_fieldset_field_ptr and query outputs. */
 #define HF_FIELD_E 0
@@ -153,6 +162,13 @@ hf_status hf_part_update(hf_part *part, const float *d_grid, hf_stream stream);
 hf_status hf_part_spectral(hf_part *part, int os, hf_stream stream);
 /* The part's table padding factor (0 without a table). */
 int hf_part_spectral_os(const hf_part *part);
+
+/* Moment spectra of a stationary part for HF_TA field sets: the spectra of
+ * G_a = -(u x grad rho1)_a (u the node position, grad the spectral
+ * derivative of the force), 3 half spectra (charged to the budget);
+ * hf_part_update refreshes them.  Errors: HF_EINVAL (not stationary),
+ * HF_EUNSUPPORTED (N > 128), HF_EBUDGET, HF_ENOMEM, HF_ECUDA. */
+hf_status hf_part_moments(hf_part *part, hf_stream stream);
 
 /* Allocate a field set for R rotations at grid size n holding the fields
  * selected by `flags` (energy and force always; HF_T adds torque; at most one

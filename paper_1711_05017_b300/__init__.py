@@ -12,7 +12,7 @@ import numpy as np
 
 from . import _binding as B
 from ._binding import (HF_E, HF_F, HF_MOVING, HF_PREC_SPLIT_BF16, HF_PREC_SPLIT_F16, HF_SPECTRAL,  # noqa: F401
-                       HF_STATIONARY, HF_T, HF_TORQUE_F64, HFError)
+                       HF_STATIONARY, HF_T, HF_TA, HF_TORQUE_F64, HFError)
 
 __all__ = ["Context", "Part", "FieldSet", "Batch", "Server", "HFError", "lowpass_query", "lowpass_query_batch",
            "resample", "rfft3d", "version"]
@@ -156,6 +156,11 @@ class Part:
         B.check(B.lib().hf_part_create(ctx.handle, n, _dev(grid, torch.float32), int(role), ctypes.byref(h),
                                        _stream_ptr(stream)))
         self.handle, self.n, self.role, self.ctx = h, n, role, ctx
+
+    def moments(self, stream=None):
+        """hf_part_moments: the stationary part's moment spectra for HF_TA
+        (analytic torque) field sets."""
+        B.check(B.lib().hf_part_moments(self.handle, _stream_ptr(stream)))
 
     def spectral(self, os=1, stream=None):
         """hf_part_spectral: build the moving part's centred spectrum table

@@ -14,7 +14,7 @@ STATUS_NAMES = {0: "HF_OK", 1: "HF_EINVAL", 2: "HF_ENOMEM", 3: "HF_EBUDGET", 4: 
                 5: "HF_ETIMEOUT", 6: "HF_ENOTREADY", 7: "HF_EUNSUPPORTED"}
 HF_STATIONARY, HF_MOVING = 0, 1
 HF_E, HF_F, HF_T, HF_TORQUE_F64 = 0x1, 0x2, 0x4, 0x10
-HF_PREC_SPLIT_BF16, HF_PREC_SPLIT_F16, HF_SPECTRAL = 0x20, 0x40, 0x80
+HF_PREC_SPLIT_BF16, HF_PREC_SPLIT_F16, HF_SPECTRAL, HF_TA = 0x20, 0x40, 0x80, 0x100
 
 _vp = ctypes.c_void_p
 _i = ctypes.c_int
@@ -88,6 +88,7 @@ SIGNATURES = {
     "hf_part_spectral_os": (_i, [_vp]),
     "hf_lowpass_query": (_i, [_vp, _vp, _i, _fp, _fp, _fp]),
     "hf_lowpass_query_batch": (_i, [_vp, _vp, _i, _vp, _i, _vp, _vp]),
+    "hf_part_moments": (_i, [_vp, _vp]),
 }
 
 

@@ -105,6 +105,9 @@ struct hf_part {
     float2 *table = nullptr;
     int table_os = 0;
     size_t table_bytes = 0;
+    // HF_STATIONARY after hf_part_moments: the spectra of the moment fields
+    // G_a = -(u x grad rho1)_a, 3 half spectra (slot order, scaled like spec)
+    float2 *mspec = nullptr;
 };
 
 struct hf_fieldset {
@@ -131,6 +134,7 @@ struct hf_fieldset {
     bool pencil = false;  // pencil pipeline (x/y stages as separate kernels) instead of slab passes
     int prec = hf::PREC_FP32;  // y stages on the tensor cores (pencil pipeline at N = 256)
     bool spectral = false;     // rotated spectrum interpolated from the moving part's table
+    bool torque_analytic = false;  // HF_TA: torque from the stationary moment spectra
     bool ready = false;
     size_t bytes = 0;
     cudaStream_t mem_stream = nullptr;  // non-null: stream-ordered device memory, pageable staging
@@ -332,6 +336,7 @@ static float spectrum_scale(int n) {
 }
 
 static hf_status spectral_table_fill(hf_part *p, const float *d_grid, cudaStream_t st);
+static hf_status moment_spectra_fill(hf_part *p, cudaStream_t st);
 
 static hf_status part_fill(hf_part *p, const float *d_grid, cudaStream_t st) {
     if (p->role == HF_MOVING && p->table) {
@@ -350,7 +355,9 @@ static hf_status part_fill(hf_part *p, const float *d_grid, cudaStream_t st) {
         }
         return HF_OK;
     }
-    return stationary_spectrum(p->ctx, p->n, d_grid, p->spec, spectrum_scale(p->n), st);
+    hf_status s = stationary_spectrum(p->ctx, p->n, d_grid, p->spec, spectrum_scale(p->n), st);
+    if (s == HF_OK && p->mspec) s = moment_spectra_fill(p, st);
+    return s;
 }
 
 static void moving_texture_free(hf_part *p) {
@@ -502,12 +509,68 @@ extern "C" hf_status hf_part_spectral(hf_part *p, int os, hf_stream stream) {
 
 extern "C" int hf_part_spectral_os(const hf_part *p) { return p && p->table ? p->table_os : 0; }
 
+// The moment spectra of a stationary part (analytic torque): grad rho1 from
+// the part's spectrum by the force passes against a unit delta at node 0
+// (E = h^3 rho1, F = -h^3 grad rho1), the moment fields G = -(u x grad rho1),
+// and their forward transforms scaled like the spectrum.  Pass B takes the
+// moving density transformed along x and y only: for the delta that is 1 on
+// the z = 0 plane and 0 elsewhere.
+static hf_status moment_spectra_fill(hf_part *p, cudaStream_t st) {
+    const int n = p->n;
+    const size_t he = hf::half_spec_elems(n), n3 = (size_t)n * n * n;
+    std::vector<float2> ones((size_t)n * (n / 2 + 1), make_float2(1.f, 0.f));  // the z = 0 plane
+    float2 *sc = nullptr;  // delta spectrum, Y1, Y2
+    float *fl = nullptr;   // E, Fx, Fy, Fz, then G (3 fields)
+    CU(cudaMallocAsync(&sc, 3 * he * sizeof(float2), st));
+    cudaError_t e = cudaMallocAsync(&fl, 7 * n3 * sizeof(float), st);
+    hf_status s = HF_OK;
+    if (e == cudaSuccess) e = cudaMemsetAsync(sc, 0, he * sizeof(float2), st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sc, ones.data(), ones.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = hf::run_passB(n, sc, p->spec, sc + he, sc + 2 * he, 1, st);
+    if (e == cudaSuccess) {
+        FieldPtrs out{fl, fl + n3, fl + 2 * n3, fl + 3 * n3, 4 * n3};
+        e = hf::run_passC(n, sc + he, sc + 2 * he, out, 1, st);
+    }
+    if (e == cudaSuccess) e = hf::run_moment_fields(n, fl + n3, fl + 2 * n3, fl + 3 * n3, fl + 4 * n3, st);
+    for (int a = 0; a < 3 && e == cudaSuccess && s == HF_OK; ++a)
+        s = stationary_spectrum(p->ctx, n, fl + (4 + a) * n3, p->mspec + a * he, spectrum_scale(n), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // `ones` is pageable and lives here
+    if (sc) cudaFreeAsync(sc, st);
+    if (fl) cudaFreeAsync(fl, st);
+    if (s != HF_OK) return s;
+    if (e != cudaSuccess) return fail(HF_ECUDA, "hf_part_moments: %s", cudaGetErrorString(e));
+    return HF_OK;
+}
+
+extern "C" hf_status hf_part_moments(hf_part *p, hf_stream stream) {
+    if (!p) return fail(HF_EINVAL, "hf_part_moments: NULL part");
+    if (p->role != HF_STATIONARY) return fail(HF_EINVAL, "hf_part_moments: the part must be HF_STATIONARY");
+    if (p->n > 128) return fail(HF_EUNSUPPORTED, "hf_part_moments: N=%d (the analytic torque runs at N <= 128)", p->n);
+    CU(cudaSetDevice(p->ctx->device));
+    if (!p->mspec) {
+        const size_t bytes = 3 * hf::half_spec_elems(p->n) * sizeof(float2);
+        if (!charge(p->ctx, bytes)) return fail(HF_EBUDGET, "hf_part_moments: %zu bytes exceed the budget", bytes);
+        const cudaError_t e = cudaMalloc(&p->mspec, bytes);
+        if (e != cudaSuccess) {
+            p->mspec = nullptr;
+            uncharge(p->ctx, bytes);
+            return fail(HF_ENOMEM, "hf_part_moments: cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+        }
+    }
+    return moment_spectra_fill(p, (cudaStream_t)stream);
+}
+
 extern "C" void hf_part_release(hf_part *p) {
     if (!p) return;
     cudaSetDevice(p->ctx->device);
     if (p->table) {
         cudaFree(p->table);
         uncharge(p->ctx, p->table_bytes);
+    }
+    if (p->mspec) {
+        cudaFree(p->mspec);
+        uncharge(p->ctx, 3 * hf::half_spec_elems(p->n) * sizeof(float2));
     }
     moving_texture_free(p);
     cudaFree(p->grid ? (void *)p->grid : (void *)p->spec);
@@ -673,6 +736,10 @@ static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags,
     if (R <= 0) return fail(HF_EINVAL, "hf_fieldset_create: R=%d", R);
     flags |= HF_E | HF_F;  // energy and force are always held
     if ((flags & HF_T) && R < 7) return fail(HF_EINVAL, "hf_fieldset_create: torque needs R >= 7 (R=%d)", R);
+    if ((flags & HF_T) && (flags & HF_TA))
+        return fail(HF_EINVAL, "hf_fieldset_create: HF_T and HF_TA are alternatives");
+    if ((flags & HF_TA) && (n > 128 || (flags & HF_SPECTRAL)))
+        return fail(HF_EUNSUPPORTED, "hf_fieldset_create: HF_TA needs N <= 128 and the spatial route");
     const unsigned precf = flags & (HF_PREC_SPLIT_BF16 | HF_PREC_SPLIT_F16);
     if (precf == (HF_PREC_SPLIT_BF16 | HF_PREC_SPLIT_F16))
         return fail(HF_EINVAL, "hf_fieldset_create: at most one precision flag");
@@ -689,9 +756,10 @@ static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags,
     fs->slot[0] = nf++;
     if (flags & HF_F)
         for (int f = 1; f <= 3; ++f) fs->slot[f] = nf++;
-    if (flags & HF_T)
+    if (flags & (HF_T | HF_TA))
         for (int f = 4; f <= 6; ++f) fs->slot[f] = nf++;
     fs->nf = nf;
+    fs->torque_analytic = (flags & HF_TA) != 0;
     fs->pencil = hf::pencil_n(n);
     fs->prec = (flags & HF_PREC_SPLIT_F16) ? hf::PREC_SPLIT_F16 : (flags & HF_PREC_SPLIT_BF16) ? hf::PREC_SPLIT_BF16
                                                                                              : hf::PREC_FP32;
@@ -712,7 +780,8 @@ static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags,
     }
     const size_t n3 = (size_t)n * n * n;
     const size_t data_b = (size_t)R * nf * n3 * sizeof(float);
-    const size_t scr_b = fields_spectra(fs->pencil) * (size_t)fs->chunk * hf::half_spec_elems(n) * sizeof(float2);
+    const size_t scr_b = (fields_spectra(fs->pencil) + ((flags & HF_TA) ? 3 : 0)) * (size_t)fs->chunk *
+                         hf::half_spec_elems(n) * sizeof(float2);
     const size_t planes_b = (size_t)fs->chunk * n3 * sizeof(float);
     fs->stage_bytes = (size_t)R * (9 * sizeof(float) + 4 * sizeof(double) + 6 * sizeof(int) + 18 * sizeof(float) +
                                    18 * sizeof(double));
@@ -758,9 +827,10 @@ static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags,
 }
 
 static size_t fieldset_bytes(int n, int R, unsigned flags, int chunk, int lanes) {
-    const int nf = 4 + ((flags & HF_T) ? 3 : 0);
+    const int nf = 4 + ((flags & (HF_T | HF_TA)) ? 3 : 0);
     const size_t n3 = (size_t)n * n * n;
-    const size_t scr_b = fields_spectra(hf::pencil_n(n)) * (size_t)chunk * hf::half_spec_elems(n) * sizeof(float2);
+    const size_t scr_b = (fields_spectra(hf::pencil_n(n)) + ((flags & HF_TA) ? 3 : 0)) * (size_t)chunk *
+                         hf::half_spec_elems(n) * sizeof(float2);
     const size_t planes_b = (size_t)chunk * n3 * sizeof(float);
     const size_t stage = (size_t)R * (9 * sizeof(float) + 4 * sizeof(double) + 6 * sizeof(int) + 18 * sizeof(float) +
                                       18 * sizeof(double));
@@ -858,6 +928,12 @@ static hf_status run_fields(hf_ctx *c, int n, bool pencil, int prec, const hf_pa
         CU(timed(c, kResample, st, [&] { return hf::run_resample_chunk(n, s2->grid, rot9, planes, cnt, st); }));
     CU(timed(c, kPassA, st, [&] { return hf::run_passA_planes(n, planes, X1, cnt, st); }));
     CU(timed(c, kPassB, st, [&] { return hf::run_passB(n, X1, s1->spec, Y1, Y2, cnt, st); }));
+    if (out.Tx) {  // analytic torque: three more spectra after Y2 in the scratch
+        float2 *YT = scratch + 3 * scratch_rot;
+        CU(timed(c, kPassB, st, [&] { return hf::run_passB_torque(n, X1, s1->mspec, YT, scratch_rot, cnt, st); }));
+        CU(timed(c, kPassC, st, [&] { return hf::run_passC_torque(n, Y1, Y2, YT, scratch_rot, out, cnt, st); }));
+        return HF_OK;
+    }
     CU(timed(c, kPassC, st, [&] { return hf::run_passC(n, Y1, Y2, out, cnt, st); }));
     return HF_OK;
 }
@@ -907,6 +983,8 @@ hf_status hf_set_launch(hf_ctx *ctx, const hf_part *s1, const hf_part *s2, hf_fi
     if (cs != HF_OK) return cs;
     if (fs->spectral && !s2->table)
         return fail(HF_ENOTREADY, "field-set build: HF_SPECTRAL needs hf_part_spectral on the moving part");
+    if (fs->torque_analytic && !s1->mspec)
+        return fail(HF_ENOTREADY, "field-set build: HF_TA needs hf_part_moments on the stationary part");
     const size_t n3 = (size_t)n * n * n;
     const size_t rs = (size_t)fs->nf * n3;
     const size_t scr_rot = (size_t)fs->chunk * hf::half_spec_elems(n);
@@ -928,6 +1006,11 @@ hf_status hf_set_launch(hf_ctx *ctx, const hf_part *s1, const hf_part *s2, hf_fi
         out.Fx = base + n3;
         out.Fy = base + 2 * n3;
         out.Fz = base + 3 * n3;
+        if (fs->torque_analytic) {
+            out.Tx = base + (size_t)fs->slot[4] * n3;
+            out.Ty = base + (size_t)fs->slot[5] * n3;
+            out.Tz = base + (size_t)fs->slot[6] * n3;
+        }
         s = run_fields(ctx, n, fs->pencil, fs->prec, s1, s2, d_rot9 + (size_t)9 * r0, cnt, fs->scratch[l], scr_rot,
                        fs->planes[l], out, fs->lanes == 2 ? fs->lane[l] : st, fs->spectral);
         if (s != HF_OK) return s;

@@ -439,6 +439,75 @@ __global__ void __launch_bounds__(PassB<N>::NT, PassB<N>::MINB) passB_kernel(con
 }
 
 
+// Torque spectra: the same forward z transform of X1 as pass B, then the
+// three products Gm_a conj(rho2^R^) (a = x, y, z) with the stationary moment
+// spectra and their inverse z transforms, straight to YT[a].
+template <int N>
+__global__ void __launch_bounds__(PassB<N>::NT, 2) passB_torque_kernel(const float2 *__restrict__ X1,
+                                                                        const float2 *__restrict__ Gm,
+                                                                        float2 *__restrict__ YT, size_t yt_stride) {
+    constexpr int H = PassB<N>::H, R1 = PassB<N>::R1, R2 = PassB<N>::R2, CW = PassB<N>::CW,
+                  KPT = PassB<N>::KPT;
+    constexpr size_t NH = (size_t)N * H;
+    extern __shared__ float2 sm[];
+    float2 *E[3] = {sm, sm + (size_t)N * CW, sm + 2 * (size_t)N * CW};  // E[0] is also the forward exchange
+    float2 *twN = sm + 3 * (size_t)N * CW;
+    const int c = threadIdx.x % CW, g = threadIdx.x / CW;
+    const size_t f = (size_t)blockIdx.x * CW + c;
+    const int r = blockIdx.y;
+    load_tw<N>(twN);
+    {
+        float2 v[R1];
+        const float2 *src = X1 + (size_t)r * N * NH + f;
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1) v[n1] = src[(size_t)(R2 * n1 + g) * NH];
+        __syncthreads();
+        RegDFT<R1, -1>::run(v);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) E[0][(k1 * R2 + g) * CW + c] = k1 ? cmul(v[k1], twN[g * k1]) : v[k1];
+    }
+    __syncthreads();
+    float2 X[KPT][R2];
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) {
+        const int k1 = g + R2 * j;
+        if (k1 < R1) {
+#pragma unroll
+            for (int n2 = 0; n2 < R2; ++n2) X[j][n2] = E[0][(k1 * R2 + n2) * CW + c];
+            RegDFT<R2, -1>::run(X[j]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) {
+        const int k1 = g + R2 * j;
+        if (k1 < R1) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                float2 T[R2];
+#pragma unroll
+                for (int k2 = 0; k2 < R2; ++k2)
+                    T[k2] = cmulc(__ldg(Gm + (size_t)a * N * NH + (size_t)(R2 * k1 + k2) * NH + f), X[j][k2]);
+                RegDFT<R2, +1>::run(T);
+#pragma unroll
+                for (int n2 = 0; n2 < R2; ++n2)
+                    E[a][(n2 * R1 + k1) * CW + c] = n2 ? cmulc(T[n2], twN[n2 * k1]) : T[n2];
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float2 v[R1];
+        float2 *d = YT + a * yt_stride + (size_t)r * N * NH + f;
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) v[k1] = E[a][(g * R1 + k1) * CW + c];
+        RegDFT<R1, +1>::run(v);
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1) d[(size_t)(R2 * n1 + g) * NH] = v[n1];
+    }
+}
+
 // ------------------------------------------------------------------ pass C
 // One CTA per (z-plane, rotation) holding S'' and Gy'' side by side (pitch
 // 2H+1), then Gz'' in place of S''.
@@ -478,10 +547,21 @@ __device__ __forceinline__ void build_xtable(float4 *xt) {
 // Row j of A at planeA + j PW + colA, of B at planeB + j PW + colB; rows
 // [0, ROWS) go to output rows [0, ROWS), RB rows per batch through the row
 // buffer Tb (pitch TP).
+// Torque epilogue of an x pass (analytic torque): the stored value is
+// -(IDFT) of the pass minus (t x F)_axis at the lag, i.e. T = C(G, rho2R) -
+// t x F; F is this plane's force, already written by the same CTA.
+struct TorqueCorr {
+    const float *F[3];  // row y of F_d at F[d] + y N
+    int axis;
+    int zlag;           // signed z lag of the plane
+    int row1;           // out1's rows are out0's rows + row1
+};
+
 template <int N, int PAIR, int PW, int RB, int TP, int NT, int ROWS>
 __device__ __forceinline__ void x_pass(const float2 *planeA, const float2 *planeB, int colA, int colB,
                                        float2 *Tb, const float2 *twN, const float4 *xt,
-                                       float *__restrict__ out0, float *__restrict__ out1) {
+                                       float *__restrict__ out0, float *__restrict__ out1,
+                                       const TorqueCorr *tc = nullptr) {
     constexpr int R1 = Fact<N>::R1, R2 = Fact<N>::R2;
 #pragma unroll 1
     for (int y0 = 0; y0 < ROWS; y0 += RB) {
@@ -524,12 +604,38 @@ __device__ __forceinline__ void x_pass(const float2 *planeA, const float2 *plane
         }
         __syncthreads();
         // coalesced store of the RB rows
-        for (int i = threadIdx.x; i < RB * N; i += NT) {
-            const int row = i / N, x = i % N;
-            const float2 v = Tb[row * TP + x];
-            const size_t o = (size_t)(y0 + row) * N + x;
-            out0[o] = v.x;
-            out1[o] = v.y;
+        if (tc) {
+            const float h = 2.0f / N, tz = tc->zlag * h;
+            auto sgn = [](int j) { return j < N / 2 ? j : j - N; };
+            for (int i = threadIdx.x; i < RB * N; i += NT) {
+                const int row = i / N, x = i % N, y = y0 + row;
+                const float2 v = Tb[row * TP + x];
+                const size_t o = (size_t)y * N + x, o1 = o + (size_t)tc->row1 * N;
+                const float tx = sgn(x) * h, ty0 = sgn(y) * h, ty1 = sgn(y + tc->row1) * h;
+                const float f0[3] = {tc->F[0][o], tc->F[1][o], tc->F[2][o]};
+                const float f1[3] = {tc->F[0][o1], tc->F[1][o1], tc->F[2][o1]};
+                float c0, c1;
+                if (tc->axis == 0) {
+                    c0 = ty0 * f0[2] - tz * f0[1];
+                    c1 = ty1 * f1[2] - tz * f1[1];
+                } else if (tc->axis == 1) {
+                    c0 = tz * f0[0] - tx * f0[2];
+                    c1 = tz * f1[0] - tx * f1[2];
+                } else {
+                    c0 = tx * f0[1] - ty0 * f0[0];
+                    c1 = tx * f1[1] - ty1 * f1[0];
+                }
+                out0[o] = -v.x - c0;
+                out1[o] = -v.y - c1;
+            }
+        } else {
+            for (int i = threadIdx.x; i < RB * N; i += NT) {
+                const int row = i / N, x = i % N;
+                const float2 v = Tb[row * TP + x];
+                const size_t o = (size_t)(y0 + row) * N + x;
+                out0[o] = v.x;
+                out1[o] = v.y;
+            }
         }
         __syncthreads();
     }
@@ -599,10 +705,12 @@ __device__ __forceinline__ void y_inverse_plane(const float2 *__restrict__ src, 
 //   S'  (again, from L2) times i pi ky~ = Gy -> y inverse -> rows p and
 //       p + N/2 paired in one complex x inverse    -> Fy
 //   Gz' -> y inverse -> rows paired likewise          -> Fz
-template <int N>
+template <int N, bool TQ>
 __global__ void __launch_bounds__(PassC<N>::NT, PassC<N>::MINB) passC_kernel(const float2 *__restrict__ Y1,
                                                                               const float2 *__restrict__ Y2,
-                                                                              FieldPtrs out) {
+                                                                              FieldPtrs out,
+                                                                              const float2 *__restrict__ YT,
+                                                                              size_t yt_stride) {
     constexpr int H = PassC<N>::H, PW = PassC<N>::PW, RB = PassC<N>::RB, TP = PassC<N>::TP,
                   NT = PassC<N>::NT, HALF = N / 2;
     extern __shared__ float2 sm[];
@@ -627,6 +735,33 @@ __global__ void __launch_bounds__(PassC<N>::NT, PassC<N>::MINB) passC_kernel(con
     y_inverse_plane<N, false>(Y2 + ((size_t)r * N + z) * N * H, plane, twN);
     x_pass<N, 1, PW, RB, TP, NT, HALF>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, xt, out.Fz + fo,
                                       out.Fz + fo + (size_t)HALF * N);
+    if constexpr (TQ) {
+        // analytic torque: T_a = C(G_a, rho2R) - (t x F)_a, rows paired like Fy
+        float *T[3] = {out.Tx, out.Ty, out.Tz};
+#pragma unroll 1
+        for (int a = 0; a < 3; ++a) {
+            y_inverse_plane<N, false>(YT + a * yt_stride + ((size_t)r * N + z) * N * H, plane, twN);
+            const TorqueCorr tc{{out.Fx + fo, out.Fy + fo, out.Fz + fo}, a, z < HALF ? z : z - N, HALF};
+            x_pass<N, 1, PW, RB, TP, NT, HALF>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, xt, T[a] + fo,
+                                              T[a] + fo + (size_t)HALF * N, &tc);
+        }
+    }
+}
+
+// the stationary moment fields G_a = (u x F)_a / h^3 (F = -h^3 grad rho1)
+template <int N>
+__global__ void moment_fields_kernel(const float *__restrict__ Fx, const float *__restrict__ Fy,
+                                     const float *__restrict__ Fz, float *__restrict__ G) {
+    const size_t n3 = (size_t)N * N * N;
+    const float h = 2.0f / N, inv_h3 = 1.0f / (h * h * h);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n3; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % N), y = (int)((i / N) % N), z = (int)(i / ((size_t)N * N));
+        const float ux = -1.0f + x * h, uy = -1.0f + y * h, uz = -1.0f + z * h;
+        const float fx = Fx[i], fy = Fy[i], fz = Fz[i];
+        G[i] = (uy * fz - uz * fy) * inv_h3;
+        G[n3 + i] = (uz * fx - ux * fz) * inv_h3;
+        G[2 * n3 + i] = (ux * fy - uy * fx) * inv_h3;
+    }
 }
 
 // ------------------------------------------------------- pencil pipeline
@@ -866,7 +1001,11 @@ static cudaError_t set_smem_attrs() {
     if ((e = cudaFuncSetAttribute(passB_kernel<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N>::smem))) return e;
     if ((e = cudaFuncSetAttribute(passB_kernel<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N>::smem))) return e;
     if ((e = cudaFuncSetAttribute(passB_kernel<N, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N>::smem))) return e;
-    if ((e = cudaFuncSetAttribute(passC_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassC<N>::smem))) return e;
+    if ((e = cudaFuncSetAttribute(passC_kernel<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassC<N>::smem))) return e;
+    if ((e = cudaFuncSetAttribute(passC_kernel<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassC<N>::smem))) return e;
+    if ((e = cudaFuncSetAttribute(passB_torque_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(sizeof(float2) * (3 * (size_t)N * PassB<N>::CW + N)))))
+        return e;
     return cudaSuccess;
 }
 
@@ -912,7 +1051,25 @@ static cudaError_t launch_passB_spectral(const float2 *table, int os, const floa
 }
 template <int N>
 static cudaError_t launch_passC(const float2 *Y1, const float2 *Y2, FieldPtrs out, int nrot, cudaStream_t st) {
-    passC_kernel<N><<<dim3(N, nrot), PassC<N>::NT, PassC<N>::smem, st>>>(Y1, Y2, out);
+    passC_kernel<N, false><<<dim3(N, nrot), PassC<N>::NT, PassC<N>::smem, st>>>(Y1, Y2, out, nullptr, 0);
+    return cudaGetLastError();
+}
+template <int N>
+static cudaError_t launch_passC_torque(const float2 *Y1, const float2 *Y2, const float2 *YT, size_t yt_stride,
+                                       FieldPtrs out, int nrot, cudaStream_t st) {
+    passC_kernel<N, true><<<dim3(N, nrot), PassC<N>::NT, PassC<N>::smem, st>>>(Y1, Y2, out, YT, yt_stride);
+    return cudaGetLastError();
+}
+template <int N>
+static cudaError_t launch_passB_torque(const float2 *X1, const float2 *Gm, float2 *YT, size_t yt_stride, int nrot,
+                                       cudaStream_t st) {
+    const size_t sm = sizeof(float2) * (3 * (size_t)N * PassB<N>::CW + N);
+    passB_torque_kernel<N><<<dim3(N * PassB<N>::H / PassB<N>::CW, nrot), PassB<N>::NT, sm, st>>>(X1, Gm, YT, yt_stride);
+    return cudaGetLastError();
+}
+template <int N>
+static cudaError_t launch_moment_fields(const float *Fx, const float *Fy, const float *Fz, float *G, cudaStream_t st) {
+    moment_fields_kernel<N><<<4 * 148, 256, 0, st>>>(Fx, Fy, Fz, G);
     return cudaGetLastError();
 }
 template <int N>
@@ -1023,6 +1180,17 @@ cudaError_t run_spectral_complete(int np, const float2 *spec, float2 *table, cud
 cudaError_t run_passB_spectral(int n, const float2 *table, int os, const float *rot9, const float2 *R1hat, float2 *Y1,
                                float2 *Y2, int nrot, cudaStream_t st) {
     HF_DISPATCH_ALL(n, launch_passB_spectral<NN>(table, os, rot9, R1hat, Y1, Y2, nrot, st));
+}
+cudaError_t run_passB_torque(int n, const float2 *X1, const float2 *Gm, float2 *YT, size_t yt_stride, int nrot,
+                             cudaStream_t st) {
+    HF_DISPATCH(n, launch_passB_torque<NN>(X1, Gm, YT, yt_stride, nrot, st));
+}
+cudaError_t run_passC_torque(int n, const float2 *Y1, const float2 *Y2, const float2 *YT, size_t yt_stride,
+                             FieldPtrs out, int nrot, cudaStream_t st) {
+    HF_DISPATCH(n, launch_passC_torque<NN>(Y1, Y2, YT, yt_stride, out, nrot, st));
+}
+cudaError_t run_moment_fields(int n, const float *Fx, const float *Fy, const float *Fz, float *G, cudaStream_t st) {
+    HF_DISPATCH_ALL(n, launch_moment_fields<NN>(Fx, Fy, Fz, G, st));
 }
 cudaError_t run_unpermute(int n, const float2 *spec, float2 *out, cudaStream_t st) {
     HF_DISPATCH_ALL(n, launch_unpermute<NN>(spec, out, st));

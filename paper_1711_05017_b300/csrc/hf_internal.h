@@ -15,6 +15,7 @@ namespace hf {
 struct FieldPtrs {
     float *E, *Fx, *Fy, *Fz;
     size_t rot_stride;
+    float *Tx = nullptr, *Ty = nullptr, *Tz = nullptr;  // analytic torque fields (HF_TA), else unused
 };
 
 struct Rot9 {
@@ -70,6 +71,18 @@ cudaError_t run_pad_center(int n, const float *g, float *out, int np, cudaStream
 cudaError_t run_spectral_complete(int np, const float2 *spec, float2 *table, cudaStream_t st);
 cudaError_t run_passB_spectral(int n, const float2 *table, int os, const float *rot9, const float2 *R1hat, float2 *Y1,
                                float2 *Y2, int nrot, cudaStream_t st);
+// analytic torque (rotational gradient of Eq. 6b, moment on the stationary
+// side): the three products Gm_a conj(rho2^R^) of the stationary moment
+// spectra Gm (3 half spectra, slot order, scaled) with the rotated moving
+// spectrum, inverse z -> YT (3 half spectra per rotation); pass C then turns
+// them into T = C(G, rho2R) - t x F
+cudaError_t run_passB_torque(int n, const float2 *X1, const float2 *Gm, float2 *YT, size_t yt_stride, int nrot,
+                             cudaStream_t st);
+cudaError_t run_passC_torque(int n, const float2 *Y1, const float2 *Y2, const float2 *YT, size_t yt_stride,
+                             FieldPtrs out, int nrot, cudaStream_t st);
+// G_a = (u x F)_a / h^3 for the field set of rho1 against a unit delta (F =
+// -h^3 grad rho1), u the node position: the stationary moment fields
+cudaError_t run_moment_fields(int n, const float *Fx, const float *Fy, const float *Fz, float *G, cudaStream_t st);
 // hf_lowpass.cu: single poses from spectra truncated to |k~_a| <= K (one
 // pose by value when `one` is given, else Q poses d_tq Q x 7); out Q x 7
 struct LowpassPose {
