@@ -639,6 +639,30 @@ def run_spectral(args, local_rank):
                          round(float(np.abs(f3[:, f] - ref[:, f]).max() / np.abs(ref[:, f]).max()), 6)
                          for f in range(4)]}
         fs.release()
+    # analytic torque (HF_TA) against the least-squares differences (HF_T)
+    p1.moments()
+    ta = {}
+    tref = None
+    for name, fl in (("fd_least_squares", hf.HF_T), ("analytic", hf.HF_TA)):
+        fs = ctx.fieldset(n, R, hf.HF_E | hf.HF_F | fl)
+        fs.compute(p1, p2, q)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(2):
+            fs.compute(p1, p2, q)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 2
+        T = np.stack([fs.get(0, 4 + a).cpu().numpy().astype(np.float64) for a in range(3)])
+        ta[name] = {"value": round(R / (ms / 1e3), 1), "unit": UNIT, "ms_per_build": round(ms, 2)}
+        if tref is None:
+            tref = T
+        else:
+            ta[name]["max_abs_dev_from_fd_over_max"] = [round(float(np.abs(T[a] - tref[a]).max() / np.abs(T[a]).max()), 4)
+                                                        for a in range(3)]
+        fs.release()
+    out["torque"] = ta
     lp = {}
     tw, qw = synth.translation_walk(7, 2000), synth.quaternion_walk(8, 2000)
     for os_ in (1, 2):
