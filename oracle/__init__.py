@@ -46,6 +46,7 @@ def _L():
         _lib.or_spectral_rotate.argtypes = [i, i, d, d, d]
         _lib.or_lowpass.argtypes = [i, d, d, i, i, d, d, d]
         _lib.or_torque_analytic.argtypes = [i, d, d, d, d, d]
+        _lib.or_mesh_sdf.argtypes = [i, i, d, i, ip, ctypes.c_double, ctypes.c_double, i, d, d, d]
     return _lib
 
 
@@ -168,6 +169,20 @@ def torque_analytic(rho1, rho2r):
     n = rho1.shape[0]
     outs = [np.empty_like(rho1) for _ in range(3)]
     _L().or_torque_analytic(n, _p(rho1), _p(rho2r), *[_p(o) for o in outs])
+    return tuple(outs)
+
+
+def mesh_sdf(n, V, T, sigma=0.5, gamma_max=0.05, dmax=8):
+    """Mesh descriptor of Eq. 2 on the N^3 nodes for a closed, outward
+    oriented triangle mesh: (W, xi, rho) = winding number (PMC), signed
+    distance (negative inside), and the skeletal density (1/4pi) integral of
+    exp(-(eta/|xi| - 1)^2 / 2 sigma^2) d gamma (solid-angle element), by
+    adaptive subdivision down to gamma_max per piece (depth <= dmax)."""
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.int32)
+    outs = [np.empty((n, n, n)) for _ in range(3)]
+    _L().or_mesh_sdf(int(n), len(V), _p(V), len(T), T.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), float(sigma),
+                     float(gamma_max), int(dmax), *[_p(o) for o in outs])
     return tuple(outs)
 
 

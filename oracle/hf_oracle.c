@@ -291,6 +291,134 @@ void or_fields_spec(int n, const double *rho1, const double *b_ri,
 }
 
 /* ------------------------------------------------------------------ */
+/* Mesh descriptor, Eq. 2 (Section 2.3, "Skeletal Density"; Section 3.1), */
+/* for a closed triangle mesh with outward orientation:                   */
+/*   PMC   winding number W(p) = (1/4 pi) sum of the triangles' signed     */
+/*         solid angles (Eq. 2 with the inverse-square kernel), W = 1      */
+/*         inside, 0 outside;                                              */
+/*   xi    signed distance, -min_q |p - q| inside, + outside;              */
+/*   rho   (1/4 pi) integral over the surface of g(eta/|xi| - 1) d gamma,  */
+/*         g(x) = exp(-x^2 / 2 sigma^2), eta = |p - q|, d gamma the signed */
+/*         solid-angle element (= eta^-2 dA_perp): the inverse-square      */
+/*         kernel times the Gaussian that weights approximate nearest      */
+/*         boundary points, so rho -> W as sigma -> infinity.              */
+/* The integral is a Riemann sum over triangles subdivided (4 ways, at the */
+/* edge midpoints) until each piece subtends at most gamma_max or depth    */
+/* dmax is reached; a piece contributes g at its centroid times its exact  */
+/* solid angle (solid angles add up, so subdividing never changes the      */
+/* g = 1 limit).                                                           */
+/* ------------------------------------------------------------------ */
+static void sub3(const double *a, const double *b, double *o) { o[0] = a[0] - b[0]; o[1] = a[1] - b[1]; o[2] = a[2] - b[2]; }
+static double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void cross3(const double *a, const double *b, double *o)
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* signed solid angle of triangle (A, B, C) seen from p (van Oosterom and
+ * Strackee's formula): positive when p is on the side opposite the normal
+ * (B - A) x (C - A) */
+static double solid_angle(const double *p, const double *A, const double *B, const double *C)
+{
+    double a[3], b[3], c[3], bc[3];
+    sub3(A, p, a); sub3(B, p, b); sub3(C, p, c);
+    cross3(b, c, bc);
+    const double la = sqrt(dot3(a, a)), lb = sqrt(dot3(b, b)), lc = sqrt(dot3(c, c));
+    const double num = dot3(a, bc);
+    const double den = la * lb * lc + dot3(a, b) * lc + dot3(a, c) * lb + dot3(b, c) * la;
+    return 2.0 * atan2(num, den);
+}
+
+/* distance from p to triangle (A, B, C): the closest point lies in the face,
+ * on an edge or at a vertex; the face case by barycentric coordinates of
+ * the projection, the others by clamped projections onto the edges */
+static double tri_distance(const double *p, const double *A, const double *B, const double *C)
+{
+    double e0[3], e1[3], v[3], nrm[3];
+    sub3(B, A, e0); sub3(C, A, e1); sub3(p, A, v);
+    cross3(e0, e1, nrm);
+    const double a00 = dot3(e0, e0), a01 = dot3(e0, e1), a11 = dot3(e1, e1);
+    const double b0 = dot3(v, e0), b1 = dot3(v, e1);
+    const double det = a00 * a11 - a01 * a01;
+    if (det > 0) {
+        const double s = (a11 * b0 - a01 * b1) / det, t = (a00 * b1 - a01 * b0) / det;
+        if (s >= 0 && t >= 0 && s + t <= 1) {
+            const double nn = sqrt(dot3(nrm, nrm));
+            return fabs(dot3(v, nrm)) / nn;
+        }
+    }
+    const double *P[3] = {A, B, C};
+    double best = INFINITY;
+    for (int k = 0; k < 3; ++k) {
+        const double *X = P[k], *Y = P[(k + 1) % 3];
+        double e[3], w[3];
+        sub3(Y, X, e); sub3(p, X, w);
+        double t = dot3(w, e) / dot3(e, e);
+        t = t < 0 ? 0 : t > 1 ? 1 : t;
+        const double d[3] = {w[0] - t * e[0], w[1] - t * e[1], w[2] - t * e[2]};
+        const double dd = sqrt(dot3(d, d));
+        if (dd < best) best = dd;
+    }
+    return best;
+}
+
+static double mesh_sdf_piece(const double *p, const double *A, const double *B, const double *C, double axi,
+                             double sigma, double gamma_max, int depth, int dmax)
+{
+    const double om = solid_angle(p, A, B, C);
+    if (fabs(om) > gamma_max && depth < dmax) {
+        double ab[3], bc[3], ca[3];
+        for (int i = 0; i < 3; ++i) {
+            ab[i] = 0.5 * (A[i] + B[i]);
+            bc[i] = 0.5 * (B[i] + C[i]);
+            ca[i] = 0.5 * (C[i] + A[i]);
+        }
+        return mesh_sdf_piece(p, A, ab, ca, axi, sigma, gamma_max, depth + 1, dmax) +
+               mesh_sdf_piece(p, ab, B, bc, axi, sigma, gamma_max, depth + 1, dmax) +
+               mesh_sdf_piece(p, ca, bc, C, axi, sigma, gamma_max, depth + 1, dmax) +
+               mesh_sdf_piece(p, ab, bc, ca, axi, sigma, gamma_max, depth + 1, dmax);
+    }
+    const double q[3] = {(A[0] + B[0] + C[0]) / 3, (A[1] + B[1] + C[1]) / 3, (A[2] + B[2] + C[2]) / 3};
+    double d[3];
+    sub3(q, p, d);
+    const double eta = sqrt(dot3(d, d));
+    const double x = eta / axi - 1.0;
+    return exp(-0.5 * x * x / (sigma * sigma)) * om;
+}
+
+/* On the N^3 nodes: W (winding number), XI (signed distance), RHO (descriptor). */
+void or_mesh_sdf(int n, int nv, const double *V, int nt, const int *T, double sigma, double gamma_max, int dmax,
+                 double *W, double *XI, double *RHO)
+{
+    const double h = 2.0 / n;
+    (void)nv;
+#pragma omp parallel for schedule(dynamic)
+    for (long i = 0; i < (long)n * n * n; ++i) {
+        const int x = (int)(i % n), y = (int)((i / n) % n), z = (int)(i / ((long)n * n));
+        const double p[3] = {-1.0 + x * h, -1.0 + y * h, -1.0 + z * h};
+        double w = 0, dist = INFINITY;
+        for (int t = 0; t < nt; ++t) {
+            const double *A = V + 3 * T[3 * t], *B = V + 3 * T[3 * t + 1], *C = V + 3 * T[3 * t + 2];
+            w += solid_angle(p, A, B, C);
+            const double d = tri_distance(p, A, B, C);
+            if (d < dist) dist = d;
+        }
+        w /= 4.0 * PI;
+        const double xi = w >= 0.5 ? -dist : dist;
+        double rho = 0;
+        if (dist > 1e-12)
+            for (int t = 0; t < nt; ++t)
+                rho += mesh_sdf_piece(p, V + 3 * T[3 * t], V + 3 * T[3 * t + 1], V + 3 * T[3 * t + 2], dist, sigma,
+                                      gamma_max, 0, dmax);
+        W[i] = w;
+        XI[i] = xi;
+        RHO[i] = rho / (4.0 * PI);
+    }
+}
+
+/* ------------------------------------------------------------------ */
 /* Analytic torque field, the rotational gradient of Eq. 6b.  For world-  */
 /* frame perturbations R -> exp(theta [e_a]x) R of the moving part about  */
 /* its reference point (at t),                                           */

@@ -8,7 +8,9 @@ the FP64 oracle consume.  Every generator is a pure function of its seed.
 The paper's own test pair (a three-peg / three-hole assembly with zero
 clearance, its Fig. 4) is third-party CAD data; these skeletons stand in for
 it: rings, axis segments and planar sheets of skeleton points, each point
-carrying a ball radius that becomes the Gaussian width sigma.
+carrying a ball radius that becomes the Gaussian width sigma.  Closed
+triangle meshes of a peg and a holed block (synth.meshes) stand in for the
+CAD B-reps of the paper's mesh descriptor (Eq. 2).
 """
 from .skeletons import (  # noqa: F401
     Part,
@@ -25,3 +27,4 @@ from .skeletons import (  # noqa: F401
     quaternion_walk,
     translation_walk,
 )
+from .meshes import box, cylinder, peg_hole_pair, tube  # noqa: F401
