@@ -340,7 +340,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.empty_cache()
     spectral = None
     if rank == 0 and world == 1 and args.spectral:
-        spectral = run_spectral(args, local_rank)
+        spectral = run_next_rows(args, local_rank)
         torch.cuda.empty_cache()
     precision = None
     if rank == 0 and world == 1 and args.precision_rotations > 0:
@@ -371,7 +371,7 @@ def run_ours(args, rank, world, local_rank):
             "clocks": clk.summary(),
             "batch": batch,
             "precision": precision,
-            "spectral": spectral,
+            "next_rows": spectral,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)
@@ -600,11 +600,13 @@ def precision_oracle_error(ctx, hf, q, variants):
 
 
 # ------------------------------------------------- frequency-domain modes
-def run_spectral(args, local_rank):
-    """The c2 workload (128^3, 1024 rotations, E+F+T) with the rotation done
-    in the frequency domain (HF_SPECTRAL; tables padded os = 1 and 2), its
-    deviation from the spatial route, and single-pose queries from truncated
-    spectra (|k~| <= K) at a 1 kHz-style random walk."""
+def run_next_rows(args, local_rank):
+    """The later rows on the c2 workload (128^3, 1024 rotations, E+F+T):
+    rotation in the frequency domain (HF_SPECTRAL; tables padded os = 1 and 2)
+    with its deviation from the spatial route; the analytic torque (HF_TA)
+    against the least-squares one; single-pose queries from truncated
+    spectra (|k~| <= K) at a 1 kHz-style random walk; and the mesh
+    descriptor of a procedural peg and holed block."""
     import torch
     import paper_1711_05017_b300 as hf
     dev = torch.device("cuda", local_rank)
@@ -676,8 +678,20 @@ def run_spectral(args, local_rank):
             lat = np.array(lat[100:])
             lp[f"os{os_}_K{K}"] = {"modes": (2 * K + 1) ** 3, "p50_us": round(float(np.percentile(lat, 50)), 1),
                                   "p99_us": round(float(np.percentile(lat, 99)), 1)}
-    return {"workload": f"c2 peg-in-hole skeletons, 128^3, {R} rotations, E+F+T; rotation in the frequency domain",
-            "field_build": out, "lowpass_single_pose": lp}
+    mesh = {}
+    for seg in (32, 64):
+        hole, peg = synth.peg_hole_pair(seg)
+        ctx.density_mesh(n, *hole)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.density_mesh(n, *hole)
+        ctx.density_mesh(n, *peg)
+        torch.cuda.synchronize()
+        mesh[f"segments_{seg}"] = {"triangles": int(len(hole[1]) + len(peg[1])), "grid": n,
+                                   "seconds_both_parts": round(time.perf_counter() - t0, 3),
+                                   "sigma": 0.5, "gamma_max": 0.05, "max_depth": 8}
+    return {"workload": f"c2 peg-in-hole skeletons, 128^3, {R} rotations, E+F+T; procedural peg/hole meshes",
+            "field_build": out, "lowpass_single_pose": lp, "mesh_descriptor": mesh}
 
 
 # ------------------------------------------------------- serving workload
@@ -813,7 +827,8 @@ def main():
                     help="rotations of the 256^3 precision comparison (0 = skip)")
     ap.add_argument("--precision-oracle", type=int, default=0,
                     help="rotations checked against the FP64 oracle in the precision comparison (slow)")
-    ap.add_argument("--spectral", type=int, default=1, help="measure the frequency-domain modes (0 = skip)")
+    ap.add_argument("--spectral", type=int, default=1,
+                    help="measure the later rows: frequency-domain modes, analytic torque, mesh descriptor (0 = skip)")
     ap.add_argument("--serve-seconds", type=float, default=20.0,
                     help="length of the 16-session serving run (0 = skip)")
     args = ap.parse_args()

@@ -133,6 +133,25 @@ size_t hf_ctx_budget_bytes(const hf_ctx *ctx);
 hf_status hf_density_build(hf_ctx *ctx, int n, const float *d_pts, const float *d_sigma,
                            const float *d_amp, int P, float *d_grid_out, hf_stream stream);
 
+/* Mesh descriptor (Eq. 2, Section 2.3 "Skeletal Density"; the CAD route of
+ * Section 3.1) of a closed triangle mesh with outward orientation on the N^3
+ * grid: d_V nv x 3 float64 vertices, d_T nt x 3 int vertex indices (device;
+ * checked on the host, HF_EINVAL if out of range).  With eta = |p - q| and
+ * xi(p) the signed distance to the surface (negative inside, by the winding
+ * number of Eq. 2's inverse-square kernel):
+ *   rho(p) = (1/4 pi) integral exp(-(eta/|xi| - 1)^2 / 2 sigma^2) d gamma,
+ * d gamma the signed solid-angle element, summed over triangles subdivided
+ * 4 ways until each piece subtends at most gamma_max steradians or
+ * max_depth (<= 12) is reached.  rho -> the indicator as sigma grows; it is
+ * high on the skeleton inside and negative outside.  d_grid_out: N^3 float;
+ * d_aux_out (may be NULL): winding number then signed distance, N^3 each.
+ * float64 arithmetic; an offline step (every node visits every triangle).
+ * Any 2 <= N <= 512 (parts need a supported N).
+ * Errors: HF_EINVAL, HF_EUNSUPPORTED, HF_ECUDA. */
+hf_status hf_density_mesh(hf_ctx *ctx, int n, const double *d_V, int nv, const int *d_T, int nt, double sigma,
+                          double gamma_max, int max_depth, float *d_grid_out, float *d_aux_out,
+                          hf_stream stream);
+
 /* Make a part from an N^3 density grid (caller-owned, 8-byte aligned, read by
  * the call's stream work).  HF_STATIONARY parts keep (h^3/N^3) F{rho1} (Eq. 7a with the
  * volume element and the inverse's normalisation folded in); HF_MOVING parts

@@ -98,6 +98,22 @@ class Context:
                                          _dev(out, torch.float32), _stream_ptr(stream)))
         return out
 
+    def density_mesh(self, n, V, T, sigma=0.5, gamma_max=0.05, max_depth=8, out=None, aux=None, stream=None):
+        """hf_density_mesh: Eq. 2's descriptor of a closed triangle mesh;
+        V (nv, 3) float64 and T (nt, 3) int32 CUDA tensors (or numpy arrays,
+        copied to the device)."""
+        torch = _torch()
+        dev = torch.device("cuda", self.device)
+        Vt = torch.as_tensor(np.ascontiguousarray(V, dtype=np.float64), device=dev) if not torch.is_tensor(V) else V
+        Tt = torch.as_tensor(np.ascontiguousarray(T, dtype=np.int32), device=dev) if not torch.is_tensor(T) else T
+        if out is None:
+            out = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+        B.check(B.lib().hf_density_mesh(self.handle, int(n), _dev(Vt, torch.float64), int(Vt.shape[0]),
+                                        _dev(Tt, torch.int32), int(Tt.shape[0]), float(sigma), float(gamma_max),
+                                        int(max_depth), _dev(out, torch.float32),
+                                        None if aux is None else _dev(aux, torch.float32), _stream_ptr(stream)))
+        return out
+
     def part(self, grid, role, stream=None):
         return Part(self, grid, role, stream)
 

@@ -89,6 +89,7 @@ SIGNATURES = {
     "hf_lowpass_query": (_i, [_vp, _vp, _i, _fp, _fp, _fp]),
     "hf_lowpass_query_batch": (_i, [_vp, _vp, _i, _vp, _i, _vp, _vp]),
     "hf_part_moments": (_i, [_vp, _vp]),
+    "hf_density_mesh": (_i, [_vp, _i, _vp, _i, _vp, _i, ctypes.c_double, ctypes.c_double, _i, _vp, _vp, _vp]),
 }
 
 

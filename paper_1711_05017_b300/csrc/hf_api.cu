@@ -310,6 +310,25 @@ extern "C" hf_status hf_density_build(hf_ctx *ctx, int n, const float *d_pts, co
     return HF_OK;
 }
 
+extern "C" hf_status hf_density_mesh(hf_ctx *ctx, int n, const double *d_V, int nv, const int *d_T, int nt,
+                                     double sigma, double gamma_max, int max_depth, float *d_grid_out,
+                                     float *d_aux_out, hf_stream stream) {
+    if (!ctx || !d_V || !d_T || !d_grid_out) return fail(HF_EINVAL, "hf_density_mesh: NULL argument");
+    if (n < 2 || n > 512) return fail(HF_EUNSUPPORTED, "hf_density_mesh: N=%d outside 2..512", n);
+    if (nv < 3 || nt < 1) return fail(HF_EINVAL, "hf_density_mesh: %d vertices, %d triangles", nv, nt);
+    if (!(sigma > 0) || !(gamma_max > 0) || max_depth < 0 || max_depth > 12)
+        return fail(HF_EINVAL, "hf_density_mesh: sigma, gamma_max > 0 and 0 <= max_depth <= 12 required");
+    CU(cudaSetDevice(ctx->device));
+    // every index must name a vertex: checked on the host before any kernel reads them
+    std::vector<int> tri((size_t)3 * nt);
+    CU(cudaMemcpy(tri.data(), d_T, tri.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int v : tri)
+        if (v < 0 || v >= nv) return fail(HF_EINVAL, "hf_density_mesh: triangle index %d outside 0..%d", v, nv - 1);
+    (void)cudaGetLastError();
+    CU(hf::run_mesh_sdf(n, d_V, d_T, nt, sigma, gamma_max, max_depth, d_grid_out, d_aux_out, (cudaStream_t)stream));
+    return HF_OK;
+}
+
 // --------------------------------------------------------------------- parts
 static hf_status stationary_spectrum(hf_ctx *c, int n, const float *d_grid, float2 *spec, float scale,
                                      cudaStream_t st) {

@@ -80,6 +80,10 @@ cudaError_t run_passB_torque(int n, const float2 *X1, const float2 *Gm, float2 *
                              cudaStream_t st);
 cudaError_t run_passC_torque(int n, const float2 *Y1, const float2 *Y2, const float2 *YT, size_t yt_stride,
                              FieldPtrs out, int nrot, cudaStream_t st);
+// hf_mesh.cu: the mesh descriptor of Eq. 2 on the N^3 nodes (rho; aux, if
+// not null, gets W then the signed distance, N^3 each)
+cudaError_t run_mesh_sdf(int n, const double *V, const int *T, int nt, double sigma, double gamma_max, int dmax,
+                         float *rho, float *aux, cudaStream_t st);
 // G_a = (u x F)_a / h^3 for the field set of rho1 against a unit delta (F =
 // -h^3 grad rho1), u the node position: the stationary moment fields
 cudaError_t run_moment_fields(int n, const float *Fx, const float *Fy, const float *Fz, float *G, cudaStream_t st);
