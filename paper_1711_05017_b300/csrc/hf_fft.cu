@@ -562,10 +562,14 @@ __device__ __forceinline__ void x_pass(const float2 *planeA, const float2 *plane
                                        float2 *Tb, const float2 *twN, const float4 *xt,
                                        float *__restrict__ out0, float *__restrict__ out1,
                                        const TorqueCorr *tc = nullptr) {
-    constexpr int R1 = Fact<N>::R1, R2 = Fact<N>::R2;
+    // N = R1 R2 with the longer digit second, so that stage 2 runs with lanes
+    // along it: its reads of the row buffer are contiguous and its outputs
+    // (x = R2 n1 + n2) go straight to HBM as full 32-byte sectors
+    constexpr int R1 = Fact<N>::R1 < Fact<N>::R2 ? Fact<N>::R1 : Fact<N>::R2;
+    constexpr int R2 = N / R1;
 #pragma unroll 1
     for (int y0 = 0; y0 < ROWS; y0 += RB) {
-        // stage 1 (inverse), items (row, k1): slots R2*k1 + k2 <- Z[k1 + R1*k2]
+        // stage 1 (inverse), items (row, k1): Tb[row][R2 k1 + n2] from Z[k1 + R1 k2]
 #pragma unroll 1
         for (int w = threadIdx.x; w < RB * R1; w += NT) {
             const int row = w % RB, k1 = w / RB;
@@ -590,51 +594,48 @@ __device__ __forceinline__ void x_pass(const float2 *planeA, const float2 *plane
             for (int n2 = 0; n2 < R2; ++n2) tr[n2] = n2 ? cmulc(v[n2], twN[n2 * k1]) : v[n2];
         }
         __syncthreads();
-        // stage 2 (inverse), items (row, n2): natural order back into the row buffer
+        // stage 2 (inverse), items (row, n2), lanes along n2: x = R2 n1 + n2
 #pragma unroll 1
         for (int w = threadIdx.x; w < RB * R2; w += NT) {
-            const int row = w % RB, n2 = w / RB;
-            float2 *tr = Tb + row * TP + n2;
+            const int n2 = w % R2, row = w / R2;
+            const float2 *tr = Tb + row * TP + n2;
             float2 v[R1];
 #pragma unroll
             for (int k1 = 0; k1 < R1; ++k1) v[k1] = tr[R2 * k1];
             RegDFT<R1, +1>::run(v);
+            const int y = y0 + row;
+            const size_t o = (size_t)y * N + n2;
+            if (tc) {
+                const float h = 2.0f / N, tz = tc->zlag * h;
+                auto sgn = [](int j) { return j < N / 2 ? j : j - N; };
+                const float ty0 = sgn(y) * h, ty1 = sgn(y + tc->row1) * h;
 #pragma unroll
-            for (int n1 = 0; n1 < R1; ++n1) tr[R2 * n1] = v[n1];
-        }
-        __syncthreads();
-        // coalesced store of the RB rows
-        if (tc) {
-            const float h = 2.0f / N, tz = tc->zlag * h;
-            auto sgn = [](int j) { return j < N / 2 ? j : j - N; };
-            for (int i = threadIdx.x; i < RB * N; i += NT) {
-                const int row = i / N, x = i % N, y = y0 + row;
-                const float2 v = Tb[row * TP + x];
-                const size_t o = (size_t)y * N + x, o1 = o + (size_t)tc->row1 * N;
-                const float tx = sgn(x) * h, ty0 = sgn(y) * h, ty1 = sgn(y + tc->row1) * h;
-                const float f0[3] = {tc->F[0][o], tc->F[1][o], tc->F[2][o]};
-                const float f1[3] = {tc->F[0][o1], tc->F[1][o1], tc->F[2][o1]};
-                float c0, c1;
-                if (tc->axis == 0) {
-                    c0 = ty0 * f0[2] - tz * f0[1];
-                    c1 = ty1 * f1[2] - tz * f1[1];
-                } else if (tc->axis == 1) {
-                    c0 = tz * f0[0] - tx * f0[2];
-                    c1 = tz * f1[0] - tx * f1[2];
-                } else {
-                    c0 = tx * f0[1] - ty0 * f0[0];
-                    c1 = tx * f1[1] - ty1 * f1[0];
+                for (int n1 = 0; n1 < R1; ++n1) {
+                    const int x = R2 * n1 + n2;
+                    const size_t oo = o + (size_t)R2 * n1, o1 = oo + (size_t)tc->row1 * N;
+                    const float tx = sgn(x) * h;
+                    const float f0[3] = {tc->F[0][oo], tc->F[1][oo], tc->F[2][oo]};
+                    const float f1[3] = {tc->F[0][o1], tc->F[1][o1], tc->F[2][o1]};
+                    float c0, c1;
+                    if (tc->axis == 0) {
+                        c0 = ty0 * f0[2] - tz * f0[1];
+                        c1 = ty1 * f1[2] - tz * f1[1];
+                    } else if (tc->axis == 1) {
+                        c0 = tz * f0[0] - tx * f0[2];
+                        c1 = tz * f1[0] - tx * f1[2];
+                    } else {
+                        c0 = tx * f0[1] - ty0 * f0[0];
+                        c1 = tx * f1[1] - ty1 * f1[0];
+                    }
+                    out0[oo] = -v[n1].x - c0;
+                    out1[oo] = -v[n1].y - c1;
                 }
-                out0[o] = -v.x - c0;
-                out1[o] = -v.y - c1;
-            }
-        } else {
-            for (int i = threadIdx.x; i < RB * N; i += NT) {
-                const int row = i / N, x = i % N;
-                const float2 v = Tb[row * TP + x];
-                const size_t o = (size_t)(y0 + row) * N + x;
-                out0[o] = v.x;
-                out1[o] = v.y;
+            } else {
+#pragma unroll
+                for (int n1 = 0; n1 < R1; ++n1) {
+                    out0[o + (size_t)R2 * n1] = v[n1].x;
+                    out1[o + (size_t)R2 * n1] = v[n1].y;
+                }
             }
         }
         __syncthreads();
