@@ -344,22 +344,40 @@ __global__ void __launch_bounds__(PassB<N>::NT, PassB<N>::MINB) passB_kernel(con
     float2 *G = sm + (size_t)N * CW;     // Gz's [n2][k1][c]
     float2 *twN = G + (size_t)N * CW;
     const int c = threadIdx.x % CW, g = threadIdx.x / CW;
-    const size_t f = (size_t)blockIdx.x * CW + c;
+    size_t f = (size_t)blockIdx.x * CW + c;
+    bool active = true;  // every column is live in modes 0 and 1
     const int r = blockIdx.y;
     load_tw<N>(twN);
     float2 X[KPT][R2];
     if constexpr (MODE == 2) {
+        // a CTA takes CW consecutive frequencies kx (natural order, so that
+        // neighbouring lanes read neighbouring table cells) of one ky slot;
+        // the Nyquist column kx = N/2 is zero in this mode and is written by
+        // the first tile of the row
+        constexpr int HALF = N / 2, TILES = (HALF + CW - 1) / CW;
+        const int kys = blockIdx.x / TILES, tile = blockIdx.x % TILES;
+        const int kx = tile * CW + c;
+        active = kx < HALF;
+        f = (size_t)kys * H + (active ? xslot<N>(kx) : 0);
+        if (tile == 0) {
+            const size_t fq = (size_t)kys * H + HALF;
+            for (int z = threadIdx.x; z < N; z += PassB<N>::NT) {
+                Y1[(size_t)r * N * NH + (size_t)z * NH + fq] = make_float2(0.f, 0.f);
+                Y2[(size_t)r * N * NH + (size_t)z * NH + fq] = make_float2(0.f, 0.f);
+            }
+        }
         float R[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) R[k] = __ldg(rot9 + 9 * r + k);
-        const int kys = (int)(f / H), kxs = (int)(f % H);
-        const int ky = slot_freq<N>(kys), kx = kxs == N / 2 ? N / 2 : slot_freq<N / 2>(kxs);
+        const int ky = slot_freq<N>(kys);
 #pragma unroll
         for (int j = 0; j < KPT; ++j) {
             const int k1 = g + R2 * j;
             if (k1 < R1) {
 #pragma unroll
-                for (int k2 = 0; k2 < R2; ++k2) X[j][k2] = spectral_sample<N>(spec, R, kx, ky, slot_freq<N>(R2 * k1 + k2));
+                for (int k2 = 0; k2 < R2; ++k2)
+                    X[j][k2] = active ? spectral_sample<N>(spec, R, kx, ky, slot_freq<N>(R2 * k1 + k2))
+                                      : make_float2(0.f, 0.f);
             }
         }
         __syncthreads();  // twiddles in place
@@ -408,7 +426,8 @@ __global__ void __launch_bounds__(PassB<N>::NT, PassB<N>::MINB) passB_kernel(con
 #pragma unroll
                 for (int k2 = 0; k2 < R2; ++k2) {
                     const int s = R2 * k1 + k2;
-                    Sv[k2] = cmulc(__ldg(R1hat + (size_t)s * NH + f), X[j][k2]);  // (h^3/N^3) rho1^ conj(rho2^R^)
+                    const float2 a1 = active ? __ldg(R1hat + (size_t)s * NH + f) : make_float2(0.f, 0.f);
+                    Sv[k2] = cmulc(a1, X[j][k2]);  // (h^3/N^3) rho1^ conj(rho2^R^)
                     Gv[k2] = cmul_is(Sv[k2], signed_k_mult<N>(slot_freq<N>(s)));
                 }
                 RegDFT<R2, +1>::run(Sv);
@@ -428,13 +447,15 @@ __global__ void __launch_bounds__(PassB<N>::NT, PassB<N>::MINB) passB_kernel(con
 #pragma unroll
         for (int k1 = 0; k1 < R1; ++k1) v[k1] = E[(g * R1 + k1) * CW + c];
         RegDFT<R1, +1>::run(v);
+        if (active)
 #pragma unroll
-        for (int n1 = 0; n1 < R1; ++n1) d1[(size_t)(R2 * n1 + g) * NH] = v[n1];
+            for (int n1 = 0; n1 < R1; ++n1) d1[(size_t)(R2 * n1 + g) * NH] = v[n1];
 #pragma unroll
         for (int k1 = 0; k1 < R1; ++k1) v[k1] = G[(g * R1 + k1) * CW + c];
         RegDFT<R1, +1>::run(v);
+        if (active)
 #pragma unroll
-        for (int n1 = 0; n1 < R1; ++n1) d2[(size_t)(R2 * n1 + g) * NH] = v[n1];
+            for (int n1 = 0; n1 < R1; ++n1) d2[(size_t)(R2 * n1 + g) * NH] = v[n1];
     }
 }
 
@@ -1046,7 +1067,8 @@ static cudaError_t launch_passB_fwd(const float2 *X1, float2 *spec, float scale,
 template <int N>
 static cudaError_t launch_passB_spectral(const float2 *table, int os, const float *rot9, const float2 *R1hat,
                                          float2 *Y1, float2 *Y2, int nrot, cudaStream_t st) {
-    passB_kernel<N, 2><<<dim3(N * PassB<N>::H / PassB<N>::CW, nrot), PassB<N>::NT, PassB<N>::smem, st>>>(
+    constexpr int tiles = (N / 2 + PassB<N>::CW - 1) / PassB<N>::CW;
+    passB_kernel<N, 2><<<dim3(N * tiles, nrot), PassB<N>::NT, PassB<N>::smem, st>>>(
         nullptr, R1hat, Y1, Y2, 0.f, SpecSrc{table, os * N, os}, rot9);
     return cudaGetLastError();
 }
