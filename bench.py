@@ -220,6 +220,8 @@ def run_ours(args, rank, world, local_rank):
     n3b = 4 * n**3
     chunk = min(ctx.tune_get(n)[0], R) if not os.environ.get("HF_ROT_CHUNK") else int(os.environ["HF_ROT_CHUNK"])
     alg = {  # bytes per launch: inputs read once + outputs written
+        # pass A samples the moving grid through the texture units (read once,
+        # then L2/texture-cache resident) and writes the chunk's spectra
         "passA": n3b + chunk * he,
         "passB": chunk * he + he + 2 * chunk * he,
         "passC": 2 * chunk * he + chunk * 4 * n3b,

@@ -941,11 +941,14 @@ static hf_status run_fields(hf_ctx *c, int n, bool pencil, int prec, const hf_pa
         CU(timed(c, kPassC, st, [&] { return hf::run_xinv(n, A, X1, B, out, cnt, st); }));
         return HF_OK;
     }
-    if (s2->tex)
-        CU(timed(c, kResample, st, [&] { return hf::run_resample_tex(n, s2->tex, rot9, planes, cnt, st); }));
-    else
+    // the rotated resample runs inside pass A through the texture units;
+    // without a texture (its size outside the gather limits) it runs on its own
+    if (s2->tex) {
+        CU(timed(c, kPassA, st, [&] { return hf::run_passA_tex(n, s2->tex, rot9, X1, cnt, st); }));
+    } else {
         CU(timed(c, kResample, st, [&] { return hf::run_resample_chunk(n, s2->grid, rot9, planes, cnt, st); }));
-    CU(timed(c, kPassA, st, [&] { return hf::run_passA_planes(n, planes, X1, cnt, st); }));
+        CU(timed(c, kPassA, st, [&] { return hf::run_passA_planes(n, planes, X1, cnt, st); }));
+    }
     CU(timed(c, kPassB, st, [&] { return hf::run_passB(n, X1, s1->spec, Y1, Y2, cnt, st); }));
     if (out.Tx) {  // analytic torque: three more spectra after Y2 in the scratch
         float2 *YT = scratch + 3 * scratch_rot;

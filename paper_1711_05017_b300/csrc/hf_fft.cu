@@ -76,7 +76,10 @@ __device__ __forceinline__ float signed_k_mult(int k) {
 // node positions (8 loads per trilinear sample); SRC_PLANES reads plane z of
 // rotation r of an already resampled chunk rho2^R[r][z][y][x] (the identity
 // rotation is this mode with r = 0) by asynchronous 8-byte copies.
-enum { SRC_RAW = 0, SRC_PLANES = 1 };
+// SRC_TEX samples through the texture units' 2x2 gathers (trilinear_tex),
+// with the operation order of resample_tex_kernel so both routes give the
+// same samples bit for bit.
+enum { SRC_RAW = 0, SRC_PLANES = 1, SRC_TEX = 2 };
 
 template <int N>
 struct PassA {
@@ -94,10 +97,36 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+// The same resample through the texture units.  The moving grid is held as a
+// 2D float array of stacked z-slices, each (N+1) x (N+1) with the wrapped
+// row y = N and column x = N appended, so slice z spans rows
+// [z(N+1), z(N+1)+N].  One 2x2 gather at the corner (x0 + 1, row0 + 1)
+// returns texels (x0, x0+1) x (row0, row0+1) exactly (the footprint of an
+// integer corner does not depend on the unit's coordinate rounding), so a
+// trilinear sample is two gathers; the weights stay in float32 software.
+template <int N>
+__device__ __forceinline__ float trilinear_tex(cudaTextureObject_t t, float vx, float vy, float vz) {
+    constexpr int SC = TexLayout<N>::SC;
+    const float fx = floorf(vx), fy = floorf(vy), fz = floorf(vz);
+    const float ax = vx - fx, ay = vy - fy, az = vz - fz;
+    const int x0 = wrapN<N>((int)fx + N / 2), y0 = wrapN<N>((int)fy + N / 2), z0 = wrapN<N>((int)fz + N / 2);
+    const int z1 = wrapN<N>(z0 + 1);
+    // slice z sits at texel origin ((z % SC)(N+1), (z / SC)(N+1))
+    // gather components: w = (x0, y0), z = (x0+1, y0), x = (x0, y0+1), y = (x0+1, y0+1)
+    const float4 a = tex2Dgather<float4>(t, (float)((z0 % SC) * (N + 1) + x0) + 1.0f,
+                                         (float)((z0 / SC) * (N + 1) + y0) + 1.0f, 0);
+    const float4 b = tex2Dgather<float4>(t, (float)((z1 % SC) * (N + 1) + x0) + 1.0f,
+                                         (float)((z1 / SC) * (N + 1) + y0) + 1.0f, 0);
+    const float a0 = fmaf(ax, a.z - a.w, a.w), a1 = fmaf(ax, a.y - a.x, a.x);
+    const float b0 = fmaf(ax, b.z - b.w, b.w), b1 = fmaf(ax, b.y - b.x, b.x);
+    const float c0 = fmaf(ay, a1 - a0, a0), c1 = fmaf(ay, b1 - b0, b0);
+    return fmaf(az, c1 - c0, c0);
+}
+
 template <int N, int SRC>
-__global__ void __launch_bounds__(PassA<N>::NT, PassA<N>::MINB) passA_kernel(const float *__restrict__ rho,
-                                                                              const float *__restrict__ rot9,
-                                                                              float2 *__restrict__ X1) {
+__global__ void __launch_bounds__(PassA<N>::NT, SRC == SRC_TEX ? 2 : PassA<N>::MINB)
+    passA_kernel(const float *__restrict__ rho, const float *__restrict__ rot9, float2 *__restrict__ X1,
+                 cudaTextureObject_t tex) {
     constexpr int H = PassA<N>::H, HALF = PassA<N>::HALF, NT = PassA<N>::NT;
     extern __shared__ float2 sm[];
     float2 *P = sm;            // [N rows y][H]  (row = N reals = N/2 complex + Nyquist slot)
@@ -131,7 +160,14 @@ __global__ void __launch_bounds__(PassA<N>::NT, PassA<N>::MINB) passA_kernel(con
             const float vx = fmaf(R[0], cx, fmaf(R[3], cy, bx));
             const float vy = fmaf(R[1], cx, fmaf(R[4], cy, by));
             const float vz = fmaf(R[2], cx, fmaf(R[5], cy, bz));
-            Pf[(size_t)y * 2 * H + x] = trilinear_c<N>(rho, vx, vy, vz);
+            if constexpr (SRC == SRC_TEX) {
+                const float ax = fmaf(R[0], cx, R[3] * cy), ay = fmaf(R[1], cx, R[4] * cy),
+                            az = fmaf(R[2], cx, R[5] * cy);
+                Pf[(size_t)y * 2 * H + x] =
+                    trilinear_tex<N>(tex, fmaf(R[6], cz, ax), fmaf(R[7], cz, ay), fmaf(R[8], cz, az));
+            } else {
+                Pf[(size_t)y * 2 * H + x] = trilinear_c<N>(rho, vx, vy, vz);
+            }
         }
     }
     __syncthreads();
@@ -173,32 +209,6 @@ __global__ void __launch_bounds__(PassA<N>::NT, PassA<N>::MINB) passA_kernel(con
 // rotations.  No shared memory, so the whole L1 serves the gathers; each
 // thread samples kZ nodes along z so that their loads are in flight together.
 constexpr int kRsX = 32, kRsY = 8, kRsZ = 4;
-
-// The same resample through the texture units.  The moving grid is held as a
-// 2D float array of stacked z-slices, each (N+1) x (N+1) with the wrapped
-// row y = N and column x = N appended, so slice z spans rows
-// [z(N+1), z(N+1)+N].  One 2x2 gather at the corner (x0 + 1, row0 + 1)
-// returns texels (x0, x0+1) x (row0, row0+1) exactly (the footprint of an
-// integer corner does not depend on the unit's coordinate rounding), so a
-// trilinear sample is two gathers; the weights stay in float32 software.
-template <int N>
-__device__ __forceinline__ float trilinear_tex(cudaTextureObject_t t, float vx, float vy, float vz) {
-    constexpr int SC = TexLayout<N>::SC;
-    const float fx = floorf(vx), fy = floorf(vy), fz = floorf(vz);
-    const float ax = vx - fx, ay = vy - fy, az = vz - fz;
-    const int x0 = wrapN<N>((int)fx + N / 2), y0 = wrapN<N>((int)fy + N / 2), z0 = wrapN<N>((int)fz + N / 2);
-    const int z1 = wrapN<N>(z0 + 1);
-    // slice z sits at texel origin ((z % SC)(N+1), (z / SC)(N+1))
-    // gather components: w = (x0, y0), z = (x0+1, y0), x = (x0, y0+1), y = (x0+1, y0+1)
-    const float4 a = tex2Dgather<float4>(t, (float)((z0 % SC) * (N + 1) + x0) + 1.0f,
-                                         (float)((z0 / SC) * (N + 1) + y0) + 1.0f, 0);
-    const float4 b = tex2Dgather<float4>(t, (float)((z1 % SC) * (N + 1) + x0) + 1.0f,
-                                         (float)((z1 / SC) * (N + 1) + y0) + 1.0f, 0);
-    const float a0 = fmaf(ax, a.z - a.w, a.w), a1 = fmaf(ax, a.y - a.x, a.x);
-    const float b0 = fmaf(ax, b.z - b.w, b.w), b1 = fmaf(ax, b.y - b.x, b.x);
-    const float c0 = fmaf(ay, a1 - a0, a0), c1 = fmaf(ay, b1 - b0, b0);
-    return fmaf(az, c1 - c0, c0);
-}
 
 template <int N>
 __global__ void __launch_bounds__(kRsX * kRsY) resample_tex_kernel(cudaTextureObject_t tex,
@@ -1020,6 +1030,10 @@ static cudaError_t set_smem_attrs() {
     if ((e = set_pencil_attrs<N>())) return e;
     if ((e = cudaFuncSetAttribute(passA_kernel<N, SRC_RAW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassA<N>::smem))) return e;
     if ((e = cudaFuncSetAttribute(passA_kernel<N, SRC_PLANES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassA<N>::smem))) return e;
+    if ((e = cudaFuncSetAttribute(passA_kernel<N, SRC_TEX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassA<N>::smem))) return e;
+    // two CTAs per SM (136 KB of shared memory) leave the rest of the unified
+    // L1 to the texture cache that the fused resample reads through
+    if ((e = cudaFuncSetAttribute(passA_kernel<N, SRC_TEX>, cudaFuncAttributePreferredSharedMemoryCarveout, 62))) return e;
     if ((e = cudaFuncSetAttribute(passB_kernel<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N>::smem))) return e;
     if ((e = cudaFuncSetAttribute(passB_kernel<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N>::smem))) return e;
     if ((e = cudaFuncSetAttribute(passB_kernel<N, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N>::smem))) return e;
@@ -1032,8 +1046,9 @@ static cudaError_t set_smem_attrs() {
 }
 
 template <int N, int SRC>
-static cudaError_t launch_passA(const float *rho, const float *rot9, float2 *X1, int nrot, cudaStream_t st) {
-    passA_kernel<N, SRC><<<dim3(N, nrot), PassA<N>::NT, PassA<N>::smem, st>>>(rho, rot9, X1);
+static cudaError_t launch_passA(const float *rho, const float *rot9, float2 *X1, int nrot, cudaStream_t st,
+                               cudaTextureObject_t tex = 0) {
+    passA_kernel<N, SRC><<<dim3(N, nrot), PassA<N>::NT, PassA<N>::smem, st>>>(rho, rot9, X1, tex);
     return cudaGetLastError();
 }
 template <int N>
@@ -1172,6 +1187,9 @@ cudaError_t run_xinv(int n, const float2 *ZS, const float2 *ZGy, const float2 *Z
 }
 cudaError_t run_passA(int n, const float *rho, const float *rot9, float2 *X1, int nrot, cudaStream_t st) {
     HF_DISPATCH(n, (launch_passA<NN, SRC_RAW>(rho, rot9, X1, nrot, st)));
+}
+cudaError_t run_passA_tex(int n, cudaTextureObject_t tex, const float *rot9, float2 *X1, int nrot, cudaStream_t st) {
+    HF_DISPATCH(n, (launch_passA<NN, SRC_TEX>(nullptr, rot9, X1, nrot, st, tex)));
 }
 cudaError_t run_passA_planes(int n, const float *planes, float2 *X1, int nrot, cudaStream_t st) {
     HF_DISPATCH(n, (launch_passA<NN, SRC_PLANES>(planes, nullptr, X1, nrot, st)));

@@ -53,6 +53,7 @@ cudaError_t fft_init_attrs(int n);
 cudaError_t run_passA(int n, const float *rho, const float *rot9, float2 *X1, int nrot, cudaStream_t st);
 // pass A from planes already in memory: plane z of rotation r at planes + (r N + z) N^2
 cudaError_t run_passA_planes(int n, const float *planes, float2 *X1, int nrot, cudaStream_t st);
+cudaError_t run_passA_tex(int n, cudaTextureObject_t tex, const float *rot9, float2 *X1, int nrot, cudaStream_t st);
 // rotated resample of a chunk: out[r] = rho(R_r^T x_n), r < nrot
 cudaError_t run_resample_chunk(int n, const float *rho, const float *rot9, float *out, int nrot, cudaStream_t st);
 // the same through 2x2 texture gathers of the stacked padded slices (see hf_fft.cu)
