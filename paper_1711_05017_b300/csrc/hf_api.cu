@@ -924,11 +924,12 @@ static hf_status run_fields(hf_ctx *c, int n, bool pencil, int prec, const hf_pa
     }
     if (pencil) {
         float2 *A = scratch + 3 * scratch_rot, *B = scratch + 4 * scratch_rot;
-        if (s2->tex)
-            CU(timed(c, kResample, st, [&] { return hf::run_resample_tex(n, s2->tex, rot9, planes, cnt, st); }));
-        else
+        if (s2->tex) {  // resample fused into the x forward through the texture units
+            CU(timed(c, kPassA, st, [&] { return hf::run_xfwd_tex(n, s2->tex, rot9, A, cnt, st); }));
+        } else {
             CU(timed(c, kResample, st, [&] { return hf::run_resample_chunk(n, s2->grid, rot9, planes, cnt, st); }));
-        CU(timed(c, kPassA, st, [&] { return hf::run_xfwd(n, planes, A, cnt, st); }));
+            CU(timed(c, kPassA, st, [&] { return hf::run_xfwd(n, planes, A, cnt, st); }));
+        }
         if (prec != hf::PREC_FP32)
             CU(timed(c, kYtc, st, [&] { return hf::run_yfwd_tc(n, prec, A, X1, cnt, st); }));
         else

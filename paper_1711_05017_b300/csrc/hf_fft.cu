@@ -817,10 +817,14 @@ struct Pencil {
         sizeof(float2) * ((size_t)RBX * PW + (size_t)RBX * TP + N) + sizeof(float4) * (size_t)N;
 };
 
-// x forward: RBX rows (q = z N + y) of rotation r -> half-spectrum rows Xa[r][q][kx*]
-template <int N>
+// x forward: RBX rows (q = z N + y) of rotation r -> half-spectrum rows Xa[r][q][kx*].
+// TEX: the rows are sampled from the moving part's texture at the rotated
+// node positions (the resample fused in, same samples bit for bit as
+// resample_tex_kernel) instead of read from resampled planes.
+template <int N, bool TEX>
 __global__ void __launch_bounds__(Pencil<N>::NT) xfwd_kernel(const float *__restrict__ planes,
-                                                             float2 *__restrict__ Xa) {
+                                                             float2 *__restrict__ Xa, cudaTextureObject_t tex,
+                                                             const float *__restrict__ rot9) {
     constexpr int H = Pencil<N>::H, HALF = Pencil<N>::HALF, RBX = Pencil<N>::RBX, NT = Pencil<N>::NT;
     extern __shared__ float2 sm[];
     float2 *P = sm;               // [RBX][H]
@@ -828,14 +832,32 @@ __global__ void __launch_bounds__(Pencil<N>::NT) xfwd_kernel(const float *__rest
     float2 *twH = twN + N;
     const size_t q0 = (size_t)blockIdx.x * RBX;
     const int r = blockIdx.y;
-    const float2 *src = reinterpret_cast<const float2 *>(planes + ((size_t)r * N * N + q0) * N);
-    for (int i = threadIdx.x; i < RBX * HALF; i += NT) {
-        const int row = i / HALF, x2 = i % HALF;
-        cp_async8(P + row * H + x2, src + i);
+    if constexpr (TEX) {
+        float R[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) R[k] = __ldg(rot9 + 9 * r + k);
+        float *Pf = reinterpret_cast<float *>(P);
+        for (int i = threadIdx.x; i < RBX * N; i += NT) {
+            const int row = i / N, x = i % N;
+            const size_t q = q0 + row;
+            const int y = (int)(q % N), z = (int)(q / N);
+            const float cx = (float)(x - N / 2), cy = (float)(y - N / 2), cz = (float)(z - N / 2);
+            const float ax = fmaf(R[0], cx, R[3] * cy), ay = fmaf(R[1], cx, R[4] * cy), az = fmaf(R[2], cx, R[5] * cy);
+            Pf[(size_t)row * 2 * H + x] =
+                trilinear_tex<N>(tex, fmaf(R[6], cz, ax), fmaf(R[7], cz, ay), fmaf(R[8], cz, az));
+        }
+        load_tw<N>(twN);
+        load_tw<HALF>(twH);
+    } else {
+        const float2 *src = reinterpret_cast<const float2 *>(planes + ((size_t)r * N * N + q0) * N);
+        for (int i = threadIdx.x; i < RBX * HALF; i += NT) {
+            const int row = i / HALF, x2 = i % HALF;
+            cp_async8(P + row * H + x2, src + i);
+        }
+        load_tw<N>(twN);
+        load_tw<HALF>(twH);
+        cp_async_wait_all();
     }
-    load_tw<N>(twN);
-    load_tw<HALF>(twH);
-    cp_async_wait_all();
     __syncthreads();
     fft_lines<HALF, -1, RBX, 1, H, NT>(P, twH);
     for (int i = threadIdx.x; i < RBX * (N / 4 + 1); i += NT) {
@@ -1014,7 +1036,8 @@ __global__ void unpermute_spectrum_kernel(const float2 *__restrict__ spec, float
 template <int N>
 static cudaError_t set_pencil_attrs() {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(xfwd_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Pencil<N>::smem_xfwd))) return e;
+    if ((e = cudaFuncSetAttribute(xfwd_kernel<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Pencil<N>::smem_xfwd))) return e;
+    if ((e = cudaFuncSetAttribute(xfwd_kernel<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Pencil<N>::smem_xfwd))) return e;
     if ((e = cudaFuncSetAttribute(yfwd_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Pencil<N>::smem_yfwd))) return e;
     if ((e = cudaFuncSetAttribute(yinv_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Pencil<N>::smem_yinv))) return e;
     if ((e = cudaFuncSetAttribute(xinv_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Pencil<N>::smem_xinv))) return e;
@@ -1112,7 +1135,14 @@ static cudaError_t launch_moment_fields(const float *Fx, const float *Fy, const 
 }
 template <int N>
 static cudaError_t launch_xfwd(const float *planes, float2 *Xa, int nrot, cudaStream_t st) {
-    xfwd_kernel<N><<<dim3(N * N / Pencil<N>::RBX, nrot), Pencil<N>::NT, Pencil<N>::smem_xfwd, st>>>(planes, Xa);
+    xfwd_kernel<N, false><<<dim3(N * N / Pencil<N>::RBX, nrot), Pencil<N>::NT, Pencil<N>::smem_xfwd, st>>>(
+        planes, Xa, 0, nullptr);
+    return cudaGetLastError();
+}
+template <int N>
+static cudaError_t launch_xfwd_tex(cudaTextureObject_t tex, const float *rot9, float2 *Xa, int nrot, cudaStream_t st) {
+    xfwd_kernel<N, true><<<dim3(N * N / Pencil<N>::RBX, nrot), Pencil<N>::NT, Pencil<N>::smem_xfwd, st>>>(
+        nullptr, Xa, tex, rot9);
     return cudaGetLastError();
 }
 template <int N>
@@ -1173,6 +1203,9 @@ cudaError_t fft_init_attrs(int n) {
 }
 cudaError_t run_xfwd(int n, const float *planes, float2 *Xa, int nrot, cudaStream_t st) {
     HF_DISPATCH_ALL(n, launch_xfwd<NN>(planes, Xa, nrot, st));
+}
+cudaError_t run_xfwd_tex(int n, cudaTextureObject_t tex, const float *rot9, float2 *Xa, int nrot, cudaStream_t st) {
+    HF_DISPATCH_ALL(n, launch_xfwd_tex<NN>(tex, rot9, Xa, nrot, st));
 }
 cudaError_t run_yfwd(int n, const float2 *Xa, float2 *X1, int nrot, cudaStream_t st) {
     HF_DISPATCH_ALL(n, launch_yfwd<NN>(Xa, X1, nrot, st));

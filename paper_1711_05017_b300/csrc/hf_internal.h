@@ -103,6 +103,8 @@ cudaError_t run_lowpass(int n, const float2 *spec1, const float2 *table, int os,
 // pencil pipeline (any N; the only one for N = 256): planes -> Xa -> X1 (forward x, y),
 // then pass B, then Y1/Y2 -> Z_S, Z_Gy, Z_Gz (inverse y) -> fields (inverse x)
 cudaError_t run_xfwd(int n, const float *planes, float2 *Xa, int nrot, cudaStream_t st);
+// the x forward of the pencil pipeline sampling the moving texture directly
+cudaError_t run_xfwd_tex(int n, cudaTextureObject_t tex, const float *rot9, float2 *Xa, int nrot, cudaStream_t st);
 cudaError_t run_yfwd(int n, const float2 *Xa, float2 *X1, int nrot, cudaStream_t st);
 // hf_tc.cu: the pencil pipeline's y stages as split hi/lo DFT-matrix GEMMs on
 // the tensor cores (N = 256 only); same inputs and outputs as run_yfwd /
