@@ -121,7 +121,7 @@ struct hf_fieldset {
     // two internal streams so that one chunk's texture-bound resample can
     // overlap the other's shared-memory-bound passes
     float2 *scratch[2] = {};     // 3 x chunk x N*N*(N/2+1): X1, Y1, Y2
-    float *planes[2] = {};       // chunk x N^3: the chunk's resampled moving densities
+    float *planes[2] = {};       // unused: the resample runs inside the first FFT pass
     cudaStream_t lane[2] = {};
     cudaEvent_t fork = nullptr, join[2] = {};
     float *d_rot9 = nullptr;     // R x 9
@@ -801,7 +801,7 @@ static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags,
     const size_t data_b = (size_t)R * nf * n3 * sizeof(float);
     const size_t scr_b = (fields_spectra(fs->pencil) + ((flags & HF_TA) ? 3 : 0)) * (size_t)fs->chunk *
                          hf::half_spec_elems(n) * sizeof(float2);
-    const size_t planes_b = (size_t)fs->chunk * n3 * sizeof(float);
+    const size_t planes_b = 0;  // the resample is fused into pass A / the x forward
     fs->stage_bytes = (size_t)R * (9 * sizeof(float) + 4 * sizeof(double) + 6 * sizeof(int) + 18 * sizeof(float) +
                                    18 * sizeof(double));
     fs->bytes = data_b + fs->lanes * (scr_b + planes_b) + fs->stage_bytes;
@@ -817,7 +817,7 @@ static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags,
     cudaError_t e = dalloc((void **)&fs->data, data_b);
     for (int l = 0; l < 2; ++l) {
         if (e == cudaSuccess && l < fs->lanes) e = dalloc((void **)&fs->scratch[l], scr_b);
-        if (e == cudaSuccess && l < fs->lanes) e = dalloc((void **)&fs->planes[l], planes_b);
+
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&fs->lane[l], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fs->join[l], cudaEventDisableTiming);
     }
@@ -850,7 +850,7 @@ static size_t fieldset_bytes(int n, int R, unsigned flags, int chunk, int lanes)
     const size_t n3 = (size_t)n * n * n;
     const size_t scr_b = (fields_spectra(hf::pencil_n(n)) + ((flags & HF_TA) ? 3 : 0)) * (size_t)chunk *
                          hf::half_spec_elems(n) * sizeof(float2);
-    const size_t planes_b = (size_t)chunk * n3 * sizeof(float);
+    const size_t planes_b = 0;
     const size_t stage = (size_t)R * (9 * sizeof(float) + 4 * sizeof(double) + 6 * sizeof(int) + 18 * sizeof(float) +
                                       18 * sizeof(double));
     return (size_t)R * nf * n3 * sizeof(float) + lanes * (scr_b + planes_b) + stage;
@@ -927,6 +927,7 @@ static hf_status run_fields(hf_ctx *c, int n, bool pencil, int prec, const hf_pa
         if (s2->tex) {  // resample fused into the x forward through the texture units
             CU(timed(c, kPassA, st, [&] { return hf::run_xfwd_tex(n, s2->tex, rot9, A, cnt, st); }));
         } else {
+            if (!planes) return fail(HF_EUNSUPPORTED, "field-set build: the moving part has no texture");
             CU(timed(c, kResample, st, [&] { return hf::run_resample_chunk(n, s2->grid, rot9, planes, cnt, st); }));
             CU(timed(c, kPassA, st, [&] { return hf::run_xfwd(n, planes, A, cnt, st); }));
         }
@@ -947,6 +948,7 @@ static hf_status run_fields(hf_ctx *c, int n, bool pencil, int prec, const hf_pa
     if (s2->tex) {
         CU(timed(c, kPassA, st, [&] { return hf::run_passA_tex(n, s2->tex, rot9, X1, cnt, st); }));
     } else {
+        if (!planes) return fail(HF_EUNSUPPORTED, "field-set build: the moving part has no texture");
         CU(timed(c, kResample, st, [&] { return hf::run_resample_chunk(n, s2->grid, rot9, planes, cnt, st); }));
         CU(timed(c, kPassA, st, [&] { return hf::run_passA_planes(n, planes, X1, cnt, st); }));
     }
