@@ -44,6 +44,13 @@
  * Errors: every call returns an hf_status; no exception or abort crosses the
  * ABI.  On failure the call has written no output handle, and hf_last_error()
  * returns a message for the calling thread.
+ *
+ * Threads: a context may be shared.  Creating and releasing parts and field
+ * sets, computing different field sets, queries and the server's calls are
+ * safe from several threads (budget accounting, the profiler and the query
+ * mailbox are locked).  One field set must not be computed by two threads at
+ * once, nor released while its work runs; hf_autotune / hf_tune_set must not
+ * run while field sets of the same context are being created.
  */
 #ifndef HF_H
 #define HF_H
