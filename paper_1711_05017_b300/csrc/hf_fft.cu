@@ -105,22 +105,73 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // integer corner does not depend on the unit's coordinate rounding), so a
 // trilinear sample is two gathers; the weights stay in float32 software.
 template <int N>
-__device__ __forceinline__ float trilinear_tex(cudaTextureObject_t t, float vx, float vy, float vz) {
+struct TexSample {
+    float4 a, b;       // gathers at slices z0 and z0 + 1
+    float ax, ay, az;  // fractional offsets
+};
+
+// Issue the two gathers of one sample; tex_combine waits for them.  Splitting
+// the two lets a thread keep the gathers of several samples in flight.
+template <int N>
+__device__ __forceinline__ TexSample<N> tex_issue(cudaTextureObject_t t, float vx, float vy, float vz) {
     constexpr int SC = TexLayout<N>::SC;
+    TexSample<N> s;
     const float fx = floorf(vx), fy = floorf(vy), fz = floorf(vz);
-    const float ax = vx - fx, ay = vy - fy, az = vz - fz;
+    s.ax = vx - fx;
+    s.ay = vy - fy;
+    s.az = vz - fz;
     const int x0 = wrapN<N>((int)fx + N / 2), y0 = wrapN<N>((int)fy + N / 2), z0 = wrapN<N>((int)fz + N / 2);
     const int z1 = wrapN<N>(z0 + 1);
     // slice z sits at texel origin ((z % SC)(N+1), (z / SC)(N+1))
     // gather components: w = (x0, y0), z = (x0+1, y0), x = (x0, y0+1), y = (x0+1, y0+1)
-    const float4 a = tex2Dgather<float4>(t, (float)((z0 % SC) * (N + 1) + x0) + 1.0f,
-                                         (float)((z0 / SC) * (N + 1) + y0) + 1.0f, 0);
-    const float4 b = tex2Dgather<float4>(t, (float)((z1 % SC) * (N + 1) + x0) + 1.0f,
-                                         (float)((z1 / SC) * (N + 1) + y0) + 1.0f, 0);
-    const float a0 = fmaf(ax, a.z - a.w, a.w), a1 = fmaf(ax, a.y - a.x, a.x);
-    const float b0 = fmaf(ax, b.z - b.w, b.w), b1 = fmaf(ax, b.y - b.x, b.x);
-    const float c0 = fmaf(ay, a1 - a0, a0), c1 = fmaf(ay, b1 - b0, b0);
-    return fmaf(az, c1 - c0, c0);
+    s.a = tex2Dgather<float4>(t, (float)((z0 % SC) * (N + 1) + x0) + 1.0f, (float)((z0 / SC) * (N + 1) + y0) + 1.0f, 0);
+    s.b = tex2Dgather<float4>(t, (float)((z1 % SC) * (N + 1) + x0) + 1.0f, (float)((z1 / SC) * (N + 1) + y0) + 1.0f, 0);
+    return s;
+}
+
+template <int N>
+__device__ __forceinline__ float tex_combine(const TexSample<N> &s) {
+    const float4 a = s.a, b = s.b;
+    const float a0 = fmaf(s.ax, a.z - a.w, a.w), a1 = fmaf(s.ax, a.y - a.x, a.x);
+    const float b0 = fmaf(s.ax, b.z - b.w, b.w), b1 = fmaf(s.ax, b.y - b.x, b.x);
+    const float c0 = fmaf(s.ay, a1 - a0, a0), c1 = fmaf(s.ay, b1 - b0, b0);
+    return fmaf(s.az, c1 - c0, c0);
+}
+
+template <int N>
+__device__ __forceinline__ float trilinear_tex(cudaTextureObject_t t, float vx, float vy, float vz) {
+    return tex_combine<N>(tex_issue<N>(t, vx, vy, vz));
+}
+
+// Resample COUNT consecutive nodes of the rotated grid into reals at
+// Pf[row * 2H + x] through the texture, U samples per thread in flight.
+// node(i) gives the node's (x, y, z, row) for i in [0, COUNT).
+constexpr int kTexInFlight = 8;
+template <int N, int NT, int COUNT, class Node>
+__device__ __forceinline__ void tex_resample(cudaTextureObject_t t, const float *R, float *Pf, Node node) {
+    constexpr int H = N / 2 + 1, U = kTexInFlight;
+#pragma unroll 1
+    for (int i0 = threadIdx.x; i0 < COUNT; i0 += NT * U) {
+        TexSample<N> s[U];
+        int dst[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * NT;
+            if (COUNT % (NT * U) == 0 || i < COUNT) {
+                int x, y, z, row;
+                node(i, x, y, z, row);
+                const float cx = (float)(x - N / 2), cy = (float)(y - N / 2), cz = (float)(z - N / 2);
+                // (R^T c)_a = R[0][a] cx + R[1][a] cy + R[2][a] cz
+                const float ax = fmaf(R[0], cx, R[3] * cy), ay = fmaf(R[1], cx, R[4] * cy),
+                            az = fmaf(R[2], cx, R[5] * cy);
+                s[u] = tex_issue<N>(t, fmaf(R[6], cz, ax), fmaf(R[7], cz, ay), fmaf(R[8], cz, az));
+                dst[u] = row * 2 * H + x;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (COUNT % (NT * U) == 0 || i0 + u * NT < COUNT) Pf[dst[u]] = tex_combine<N>(s[u]);
+    }
 }
 
 template <int N, int SRC>
@@ -151,21 +202,22 @@ __global__ void __launch_bounds__(PassA<N>::NT, SRC == SRC_TEX ? 2 : PassA<N>::M
         float R[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) R[k] = __ldg(rot9 + 9 * r + k);
-        const float cz = (float)(z - N / 2);
-        const float bx = R[6] * cz, by = R[7] * cz, bz = R[8] * cz;
-        for (int i = threadIdx.x; i < N * N; i += NT) {
-            const int x = i % N, y = i / N;
-            const float cx = (float)(x - N / 2), cy = (float)(y - N / 2);
-            // (R^T c)_a = R[0][a] cx + R[1][a] cy + R[2][a] cz
-            const float vx = fmaf(R[0], cx, fmaf(R[3], cy, bx));
-            const float vy = fmaf(R[1], cx, fmaf(R[4], cy, by));
-            const float vz = fmaf(R[2], cx, fmaf(R[5], cy, bz));
-            if constexpr (SRC == SRC_TEX) {
-                const float ax = fmaf(R[0], cx, R[3] * cy), ay = fmaf(R[1], cx, R[4] * cy),
-                            az = fmaf(R[2], cx, R[5] * cy);
-                Pf[(size_t)y * 2 * H + x] =
-                    trilinear_tex<N>(tex, fmaf(R[6], cz, ax), fmaf(R[7], cz, ay), fmaf(R[8], cz, az));
-            } else {
+        if constexpr (SRC == SRC_TEX) {
+            tex_resample<N, NT, N * N>(tex, R, Pf, [z](int i, int &x, int &y, int &zz, int &row) {
+                x = i % N;
+                y = row = i / N;
+                zz = z;
+            });
+        } else {
+            const float cz = (float)(z - N / 2);
+            const float bx = R[6] * cz, by = R[7] * cz, bz = R[8] * cz;
+            for (int i = threadIdx.x; i < N * N; i += NT) {
+                const int x = i % N, y = i / N;
+                const float cx = (float)(x - N / 2), cy = (float)(y - N / 2);
+                // (R^T c)_a = R[0][a] cx + R[1][a] cy + R[2][a] cz
+                const float vx = fmaf(R[0], cx, fmaf(R[3], cy, bx));
+                const float vy = fmaf(R[1], cx, fmaf(R[4], cy, by));
+                const float vz = fmaf(R[2], cx, fmaf(R[5], cy, bz));
                 Pf[(size_t)y * 2 * H + x] = trilinear_c<N>(rho, vx, vy, vz);
             }
         }
@@ -837,15 +889,13 @@ __global__ void __launch_bounds__(Pencil<N>::NT) xfwd_kernel(const float *__rest
 #pragma unroll
         for (int k = 0; k < 9; ++k) R[k] = __ldg(rot9 + 9 * r + k);
         float *Pf = reinterpret_cast<float *>(P);
-        for (int i = threadIdx.x; i < RBX * N; i += NT) {
-            const int row = i / N, x = i % N;
-            const size_t q = q0 + row;
-            const int y = (int)(q % N), z = (int)(q / N);
-            const float cx = (float)(x - N / 2), cy = (float)(y - N / 2), cz = (float)(z - N / 2);
-            const float ax = fmaf(R[0], cx, R[3] * cy), ay = fmaf(R[1], cx, R[4] * cy), az = fmaf(R[2], cx, R[5] * cy);
-            Pf[(size_t)row * 2 * H + x] =
-                trilinear_tex<N>(tex, fmaf(R[6], cz, ax), fmaf(R[7], cz, ay), fmaf(R[8], cz, az));
-        }
+        tex_resample<N, NT, RBX * N>(tex, R, Pf, [q0](int i, int &x, int &y, int &z, int &row) {
+            row = i / N;
+            x = i % N;
+            const int q = (int)q0 + row;
+            y = q % N;
+            z = q / N;
+        });
         load_tw<N>(twN);
         load_tw<HALF>(twH);
     } else {
