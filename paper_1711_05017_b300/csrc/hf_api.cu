@@ -12,6 +12,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "hf.h"
@@ -692,26 +693,43 @@ int torque_setup(const std::vector<Quat> &Q, std::vector<int> &nbr, std::vector<
     nbr.assign((size_t)R * 6, 0);
     P32.assign((size_t)R * 18, 0.f);
     P64.assign((size_t)R * 18, 0.0);
+    std::vector<char> deficient((size_t)R, 0);
+    // rotation i's neighbours and operator depend on Q alone, so the O(R^2)
+    // search splits over host threads by rotation with unchanged results
+    auto rows = [&](int i0, int i1) {
+        for (int i = i0; i < i1; ++i) {
+            int nb[6];
+            nearest6(Q, i, nb);
+            double A[6][3], P[3][6];
+            bool ok = true;
+            for (int s = 0; s < 6; ++s) {
+                if (nb[s] < 0) { ok = false; break; }
+                rel_log(Q[i], Q[nb[s]], A[s]);
+            }
+            ok = ok && ls_pinv(A, P);
+            for (int s = 0; s < 6; ++s) nbr[(size_t)6 * i + s] = nb[s] < 0 ? i : nb[s];
+            for (int r = 0; r < 3; ++r)
+                for (int s = 0; s < 6; ++s) {
+                    const double v = ok ? P[r][s] : NAN;
+                    P64[(size_t)18 * i + 6 * r + s] = v;
+                    P32[(size_t)18 * i + 6 * r + s] = (float)v;
+                }
+            deficient[i] = ok ? 0 : 1;
+        }
+    };
+    const int hw = (int)std::thread::hardware_concurrency();
+    const int nth = std::max(1, std::min({hw > 0 ? hw : 1, 16, R / 128}));
+    if (nth == 1) {
+        rows(0, R);
+    } else {
+        std::vector<std::thread> pool;
+        for (int t = 0; t < nth; ++t) pool.emplace_back(rows, (int)((long)R * t / nth), (int)((long)R * (t + 1) / nth));
+        for (auto &th : pool) th.join();
+    }
     int bad = 0;
     for (int i = 0; i < R; ++i) {
-        int nb[6];
-        nearest6(Q, i, nb);
-        double A[6][3], P[3][6];
-        bool ok = true;
-        for (int s = 0; s < 6; ++s) {
-            if (nb[s] < 0) { ok = false; break; }
-            rel_log(Q[i], Q[nb[s]], A[s]);
-        }
-        ok = ok && ls_pinv(A, P);
-        for (int s = 0; s < 6; ++s) nbr[(size_t)6 * i + s] = nb[s] < 0 ? i : nb[s];
-        for (int r = 0; r < 3; ++r)
-            for (int s = 0; s < 6; ++s) {
-                const double v = ok ? P[r][s] : NAN;
-                P64[(size_t)18 * i + 6 * r + s] = v;
-                P32[(size_t)18 * i + 6 * r + s] = (float)v;
-            }
-        if (h_status) h_status[i] = ok ? 0 : 1;
-        bad += ok ? 0 : 1;
+        if (h_status) h_status[i] = deficient[i];
+        bad += deficient[i];
     }
     return bad;
 }

@@ -729,17 +729,17 @@ __device__ __forceinline__ void x_pass(const float2 *planeA, const float2 *plane
 // src[s H + c] (ky slot order) -> plane[y PW + c] (natural y).  The N/2 main
 // columns run register-centric (stage 1 straight from HBM, the digit
 // exchange through the plane buffer as [n2][k1][c], stage 2 back into the
-// plane's rows); the Nyquist column is transformed in place last.  MUL
-// multiplies input row s by i pi ky~(s) on the way in (forms Gy from S').
+// plane's rows).  The Nyquist column is loaded while stage 1 runs and
+// transformed in place in two small steps that ride along with stage 2's
+// read and write phases (one warp each), so it costs no barrier of its own.
+// MUL multiplies input row s by i pi ky~(s) on the way in (forms Gy from S').
 template <int N, bool MUL>
 __device__ __forceinline__ void y_inverse_plane(const float2 *__restrict__ src, float2 *plane, const float2 *twN) {
     constexpr int H = N / 2 + 1, HALF = N / 2, R1 = Fact<N>::R1, R2 = Fact<N>::R2, PW = PassC<N>::PW,
                   NT = PassC<N>::NT;
-    for (int s = threadIdx.x; s < N; s += NT) {
-        float2 v = __ldg(src + (size_t)s * H + HALF);
-        if constexpr (MUL) v = cmul_is(v, signed_k_mult<N>(slot_freq<N>(s)));
-        plane[s * PW + HALF] = v;
-    }
+    static_assert(NT >= N && NT >= 32 + R2, "one Nyquist value per thread; Nyquist steps on warps 0 and 1");
+    float2 nyq = make_float2(0.f, 0.f);
+    if (threadIdx.x < N) nyq = __ldg(src + (size_t)threadIdx.x * H + HALF);
     // stage 1: items (c, k1), slots R2 k1 + k2
 #pragma unroll 1
     for (int w = threadIdx.x; w < HALF * R1; w += NT) {
@@ -755,7 +755,22 @@ __device__ __forceinline__ void y_inverse_plane(const float2 *__restrict__ src, 
 #pragma unroll
         for (int n2 = 0; n2 < R2; ++n2) plane[(n2 * R1 + k1) * PW + c] = n2 ? cmulc(v[n2], twN[n2 * k1]) : v[n2];
     }
+    if (threadIdx.x < N) {
+        if constexpr (MUL) nyq = cmul_is(nyq, signed_k_mult<N>(slot_freq<N>(threadIdx.x)));
+        plane[threadIdx.x * PW + HALF] = nyq;
+    }
     __syncthreads();
+    // Nyquist column, step 1 (warp 0, items k1, in place): slots R2 k1 + k2
+    if (threadIdx.x < R1) {
+        const int k1 = threadIdx.x;
+        float2 *p = plane + (size_t)(R2 * k1) * PW + HALF;
+        float2 v[R2];
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) v[k2] = p[k2 * PW];
+        RegDFT<R2, +1>::run(v);
+#pragma unroll
+        for (int n2 = 0; n2 < R2; ++n2) p[n2 * PW] = n2 ? cmulc(v[n2], twN[n2 * k1]) : v[n2];
+    }
     // stage 2: items (c, n2); every item is read before any row is written
     constexpr int ITEMS = HALF * R2, IPT = (ITEMS + NT - 1) / NT;
     float2 v[IPT][R1];
@@ -779,8 +794,18 @@ __device__ __forceinline__ void y_inverse_plane(const float2 *__restrict__ src, 
             for (int n1 = 0; n1 < R1; ++n1) plane[(R2 * n1 + n2) * PW + c] = v[j][n1];
         }
     }
+    // Nyquist column, step 2 (warp 1, items n2, in place): natural y = R2 n1 + n2
+    if (threadIdx.x >= 32 && threadIdx.x < 32 + R2) {
+        const int n2 = threadIdx.x - 32;
+        float2 *p = plane + (size_t)n2 * PW + HALF;
+        float2 u[R1];
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) u[k1] = p[k1 * R2 * PW];
+        RegDFT<R1, +1>::run(u);
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1) p[n1 * R2 * PW] = u[n1];
+    }
     __syncthreads();
-    fft_lines<N, +1, 1, PW, 1, NT>(plane + HALF, twN);
 }
 
 // Pass C holds one half-spectrum plane at a time (about 100 KB of shared

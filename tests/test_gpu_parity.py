@@ -308,6 +308,36 @@ def test_c2_full_size_sampled(hf, ctx):
     del torch
 
 
+@pytest.mark.parametrize("pencil", [False, True])
+def test_ragged_last_chunk(hf, pencil):
+    """11 rotations launched 4 at a time (chunks 4, 4, 3) on either
+    pipeline: every rotation, those of the short last chunk included, matches
+    the oracle, and so does the torque of a rotation in that chunk (its
+    neighbours lie in other chunks)."""
+    n, R = 64, 11
+    ctx = hf.Context(0)
+    ctx.tune_set(n, 4, pencil=pencil)
+    s1, s2 = synth.c2_pair(12)
+    k = 800
+    r1 = oracle.splat(n, s1.pts[:k], s1.sigma[:k]).astype(np.float32)
+    r2 = oracle.splat(n, s2.pts[:k], s2.sigma[:k]).astype(np.float32)
+    p1, p2 = ctx.part(cuda(r1), hf.HF_STATIONARY), ctx.part(cuda(r2), hf.HF_MOVING)
+    q = synth.random_quaternions(13, R).astype(np.float32)
+    fs = ctx.fieldset(n, R, hf.HF_E | hf.HF_F | hf.HF_T)
+    fs.compute(p1, p2, q)
+    qn = norm_quats(q)
+    ref = np.stack([np.stack(oracle.fields(r1.astype(np.float64), oracle.resample(
+        r2.astype(np.float64), oracle.quat_to_rot(qq).astype(np.float32).astype(np.float64)))) for qq in qn])
+    for r in range(R):
+        for f in range(4):
+            assert rel_err(host(fs.get(r, f)), ref[r, f]) <= TOL, (r, f)
+    T, st = oracle.torque(qn, ref[:, 0], 6)
+    for r in (8, 10):  # both in the last chunk
+        assert st[r] == 0
+        for d in range(3):
+            assert rel_err(host(fs.get(r, 4 + d)), T[r, d]) <= TOL, (r, d)
+
+
 # ------------------------------------------------ 256^3 (pencil pipeline)
 
 @pytest.mark.slow
