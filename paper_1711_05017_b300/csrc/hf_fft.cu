@@ -76,9 +76,7 @@ __device__ __forceinline__ float signed_k_mult(int k) {
 // node positions (8 loads per trilinear sample); SRC_PLANES reads plane z of
 // rotation r of an already resampled chunk rho2^R[r][z][y][x] (the identity
 // rotation is this mode with r = 0) by asynchronous 8-byte copies.
-// SRC_TEX samples through the texture units' 2x2 gathers (trilinear_tex),
-// with the operation order of resample_tex_kernel so both routes give the
-// same samples bit for bit.
+// SRC_TEX samples through the texture units' 2x2 gathers (tex_resample).
 enum { SRC_RAW = 0, SRC_PLANES = 1, SRC_TEX = 2 };
 
 template <int N>
@@ -97,7 +95,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-// The same resample through the texture units.  The moving grid is held as a
+// The rotated resample through the texture units.  The moving grid is held as a
 // 2D float array of stacked z-slices, each (N+1) x (N+1) with the wrapped
 // row y = N and column x = N appended, so slice z spans rows
 // [z(N+1), z(N+1)+N].  One 2x2 gather at the corner (x0 + 1, row0 + 1)
@@ -136,11 +134,6 @@ __device__ __forceinline__ float tex_combine(const TexSample<N> &s) {
     const float b0 = fmaf(s.ax, b.z - b.w, b.w), b1 = fmaf(s.ax, b.y - b.x, b.x);
     const float c0 = fmaf(s.ay, a1 - a0, a0), c1 = fmaf(s.ay, b1 - b0, b0);
     return fmaf(s.az, c1 - c0, c0);
-}
-
-template <int N>
-__device__ __forceinline__ float trilinear_tex(cudaTextureObject_t t, float vx, float vy, float vz) {
-    return tex_combine<N>(tex_issue<N>(t, vx, vy, vz));
 }
 
 // Resample COUNT consecutive nodes of the rotated grid into reals at
@@ -261,33 +254,6 @@ __global__ void __launch_bounds__(PassA<N>::NT, SRC == SRC_TEX ? 2 : PassA<N>::M
 // rotations.  No shared memory, so the whole L1 serves the gathers; each
 // thread samples kZ nodes along z so that their loads are in flight together.
 constexpr int kRsX = 32, kRsY = 8, kRsZ = 4;
-
-template <int N>
-__global__ void __launch_bounds__(kRsX * kRsY) resample_tex_kernel(cudaTextureObject_t tex,
-                                                                 const float *__restrict__ rot9,
-                                                                 float *__restrict__ out) {
-    const int tiles_x = N / kRsX, tiles_y = N / kRsY;
-    int t = blockIdx.x;
-    const int tx = t % tiles_x; t /= tiles_x;
-    const int ty = t % tiles_y; t /= tiles_y;
-    const int tz = t;
-    const int r = blockIdx.y;
-    float R[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) R[k] = __ldg(rot9 + 9 * r + k);
-    const int x = tx * kRsX + (threadIdx.x % kRsX), y = ty * kRsY + (threadIdx.x / kRsX);
-    const float cx = (float)(x - N / 2), cy = (float)(y - N / 2);
-    const float ax = fmaf(R[0], cx, R[3] * cy), ay = fmaf(R[1], cx, R[4] * cy), az = fmaf(R[2], cx, R[5] * cy);
-    float v[kRsZ];
-#pragma unroll
-    for (int j = 0; j < kRsZ; ++j) {
-        const float cz = (float)(tz * kRsZ + j - N / 2);
-        v[j] = trilinear_tex<N>(tex, fmaf(R[6], cz, ax), fmaf(R[7], cz, ay), fmaf(R[8], cz, az));
-    }
-    float *o = out + (size_t)r * N * N * N + (size_t)y * N + x;
-#pragma unroll
-    for (int j = 0; j < kRsZ; ++j) o[(size_t)(tz * kRsZ + j) * N * N] = v[j];
-}
 
 // padded slices for the texture: slice z, local (x, y) in [0, N]^2, at
 // slab[((z / SC)(N+1) + y) * pitch + (z % SC)(N+1) + x]
@@ -896,8 +862,8 @@ struct Pencil {
 
 // x forward: RBX rows (q = z N + y) of rotation r -> half-spectrum rows Xa[r][q][kx*].
 // TEX: the rows are sampled from the moving part's texture at the rotated
-// node positions (the resample fused in, same samples bit for bit as
-// resample_tex_kernel) instead of read from resampled planes.
+// node positions (the resample fused in, the same samples bit for bit as
+// pass A's) instead of read from resampled planes.
 template <int N, bool TEX>
 __global__ void __launch_bounds__(Pencil<N>::NT) xfwd_kernel(const float *__restrict__ planes,
                                                              float2 *__restrict__ Xa, cudaTextureObject_t tex,
@@ -1150,11 +1116,6 @@ static cudaError_t launch_passA(const float *rho, const float *rot9, float2 *X1,
     return cudaGetLastError();
 }
 template <int N>
-static cudaError_t launch_resample_tex(cudaTextureObject_t tex, const float *rot9, float *out, int nrot, cudaStream_t st) {
-    resample_tex_kernel<N><<<dim3((N / kRsX) * (N / kRsY) * (N / kRsZ), nrot), kRsX * kRsY, 0, st>>>(tex, rot9, out);
-    return cudaGetLastError();
-}
-template <int N>
 static cudaError_t launch_pad_slices(const float *g, float *slab, size_t pitch_floats, cudaStream_t st) {
     pad_slices_kernel<N><<<4 * 148, 256, 0, st>>>(g, slab, pitch_floats);
     return cudaGetLastError();
@@ -1304,9 +1265,6 @@ cudaError_t run_passA_planes(int n, const float *planes, float2 *X1, int nrot, c
 }
 cudaError_t run_resample_chunk(int n, const float *rho, const float *rot9, float *out, int nrot, cudaStream_t st) {
     HF_DISPATCH_ALL(n, launch_resample_chunk<NN>(rho, rot9, out, nrot, st));
-}
-cudaError_t run_resample_tex(int n, cudaTextureObject_t tex, const float *rot9, float *out, int nrot, cudaStream_t st) {
-    HF_DISPATCH_ALL(n, launch_resample_tex<NN>(tex, rot9, out, nrot, st));
 }
 cudaError_t run_pad_slices(int n, const float *g, float *slab, size_t pitch_floats, cudaStream_t st) {
     HF_DISPATCH_ALL(n, launch_pad_slices<NN>(g, slab, pitch_floats, st));

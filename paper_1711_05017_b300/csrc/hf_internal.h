@@ -57,7 +57,6 @@ cudaError_t run_passA_tex(int n, cudaTextureObject_t tex, const float *rot9, flo
 // rotated resample of a chunk: out[r] = rho(R_r^T x_n), r < nrot
 cudaError_t run_resample_chunk(int n, const float *rho, const float *rot9, float *out, int nrot, cudaStream_t st);
 // the same through 2x2 texture gathers of the stacked padded slices (see hf_fft.cu)
-cudaError_t run_resample_tex(int n, cudaTextureObject_t tex, const float *rot9, float *out, int nrot, cudaStream_t st);
 cudaError_t run_pad_slices(int n, const float *g, float *slab, size_t pitch_floats, cudaStream_t st);
 cudaError_t run_passB(int n, const float2 *X1, const float2 *R1hat, float2 *Y1, float2 *Y2, int nrot,
                       cudaStream_t st);
