@@ -568,24 +568,28 @@ struct PassC {
     static constexpr int TP = N + 1;                                  // row-buffer pitch
     static constexpr int NT = (N >= 128) ? 512 : (N >= 64 ? 256 : 128);
     static constexpr int MINB = (N >= 128) ? 2 : 1;
-    static constexpr size_t smem = sizeof(float2) * ((size_t)N * PW + (size_t)RB * TP + N) +
-                                   sizeof(float4) * (size_t)N;
+    static constexpr size_t smem = sizeof(float2) * ((size_t)N * PW + (size_t)RB * TP + N);
 };
 
-// Per frequency k of the full x row: where its half-spectrum value sits and
-// how it enters the row:  k <= N/2 reads slot(k) as is, k > N/2 reads
-// slot(N-k) conjugated (Hermitian symmetry); for the (E, Fx) row the value is
-// also scaled by 1 + pi kx~ (kx~ signed, Nyquist 0).
-//   entry = (slot as float bits, conj sign, scale, scale * conj sign)
+// Frequency k of the full x row, built from the half spectrum: k <= N/2
+// reads slot(k) as is, k > N/2 reads slot(N-k) conjugated (Hermitian
+// symmetry); for the (E, Fx) row the value is also scaled by 1 + pi kx~ (kx~
+// signed, Nyquist 0).  With k = k1 + R1 k2 and k2 unrolled, most of this folds
+// to constants.
+struct XEntry {
+    int slot;
+    float cs;    // +1, or -1 where the value is conjugated
+    float mult;  // 1 + pi kx~
+};
 template <int N>
-__device__ __forceinline__ void build_xtable(float4 *xt) {
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        const bool neg = 2 * k > N;
-        const int m = neg ? N - k : k;
-        const float cs = neg ? -1.0f : 1.0f;
-        const float mult = (2 * k == N) ? 1.0f : 1.0f + (neg ? -kPi * (float)m : kPi * (float)m);
-        xt[k] = make_float4(__int_as_float(xslot<N>(m)), cs, mult, mult * cs);
-    }
+__device__ __forceinline__ XEntry x_entry(int k) {
+    const bool neg = 2 * k > N;
+    const int m = neg ? N - k : k;
+    XEntry e;
+    e.slot = xslot<N>(m);
+    e.cs = neg ? -1.0f : 1.0f;
+    e.mult = (2 * k == N) ? 1.0f : 1.0f + kPi * (float)(neg ? k - N : k);
+    return e;
 }
 
 // One complex inverse DFT of length N per row, input built from half-spectrum
@@ -608,7 +612,7 @@ struct TorqueCorr {
 
 template <int N, int PAIR, int PW, int RB, int TP, int NT, int ROWS>
 __device__ __forceinline__ void x_pass(const float2 *planeA, const float2 *planeB, int colA, int colB,
-                                       float2 *Tb, const float2 *twN, const float4 *xt,
+                                       float2 *Tb, const float2 *twN,
                                        float *__restrict__ out0, float *__restrict__ out1,
                                        const TorqueCorr *tc = nullptr) {
     // N = R1 R2 with the longer digit second, so that stage 2 runs with lanes
@@ -627,14 +631,13 @@ __device__ __forceinline__ void x_pass(const float2 *planeA, const float2 *plane
             float2 v[R2];
 #pragma unroll
             for (int k2 = 0; k2 < R2; ++k2) {
-                const float4 e = xt[k1 + R1 * k2];
-                const int sl = __float_as_int(e.x);
+                const XEntry e = x_entry<N>(k1 + R1 * k2);
                 if constexpr (PAIR == 0) {
-                    const float2 a = pa[sl];
-                    v[k2] = make_float2(e.z * a.x, e.w * a.y);
+                    const float2 a = pa[e.slot];
+                    v[k2] = make_float2(e.mult * a.x, (e.mult * e.cs) * a.y);
                 } else {
-                    const float2 gy = pb[sl], gz = pa[sl];
-                    v[k2] = make_float2(fmaf(e.y, gz.y, -gy.x), fmaf(-e.y, gy.y, -gz.x));  // -(gy + i gz)
+                    const float2 gy = pb[e.slot], gz = pa[e.slot];
+                    v[k2] = make_float2(fmaf(e.cs, gz.y, -gy.x), fmaf(-e.cs, gy.y, -gz.x));  // -(gy + i gz)
                 }
             }
             RegDFT<R2, +1>::run(v);
@@ -792,23 +795,21 @@ __global__ void __launch_bounds__(PassC<N>::NT, PassC<N>::MINB) passC_kernel(con
     float2 *plane = sm;                       // [N][PW]
     float2 *Tb = plane + (size_t)N * PW;      // [RB][TP]
     float2 *twN = Tb + (size_t)RB * TP;
-    float4 *xt = reinterpret_cast<float4 *>(twN + N);
     const int z = blockIdx.x, r = blockIdx.y;
     const float2 *s1 = Y1 + ((size_t)r * N + z) * N * H;
     const size_t fo = (size_t)r * out.rot_stride + (size_t)z * N * N;
     load_tw<N>(twN);
-    build_xtable<N>(xt);
     __syncthreads();
     // E + i Fx
     y_inverse_plane<N, false>(s1, plane, twN);
-    x_pass<N, 0, PW, RB, TP, NT, N>(plane, plane, 0, 0, Tb, twN, xt, out.E + fo, out.Fx + fo);
+    x_pass<N, 0, PW, RB, TP, NT, N>(plane, plane, 0, 0, Tb, twN, out.E + fo, out.Fx + fo);
     // Fy from Gy = i pi ky~ S'
     y_inverse_plane<N, true>(s1, plane, twN);
-    x_pass<N, 1, PW, RB, TP, NT, HALF>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, xt, out.Fy + fo,
+    x_pass<N, 1, PW, RB, TP, NT, HALF>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, out.Fy + fo,
                                       out.Fy + fo + (size_t)HALF * N);
     // Fz
     y_inverse_plane<N, false>(Y2 + ((size_t)r * N + z) * N * H, plane, twN);
-    x_pass<N, 1, PW, RB, TP, NT, HALF>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, xt, out.Fz + fo,
+    x_pass<N, 1, PW, RB, TP, NT, HALF>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, out.Fz + fo,
                                       out.Fz + fo + (size_t)HALF * N);
     if constexpr (TQ) {
         // analytic torque: T_a = C(G_a, rho2R) - (t x F)_a, rows paired like Fy
@@ -817,7 +818,7 @@ __global__ void __launch_bounds__(PassC<N>::NT, PassC<N>::MINB) passC_kernel(con
         for (int a = 0; a < 3; ++a) {
             y_inverse_plane<N, false>(YT + a * yt_stride + ((size_t)r * N + z) * N * H, plane, twN);
             const TorqueCorr tc{{out.Fx + fo, out.Fy + fo, out.Fz + fo}, a, z < HALF ? z : z - N, HALF};
-            x_pass<N, 1, PW, RB, TP, NT, HALF>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, xt, T[a] + fo,
+            x_pass<N, 1, PW, RB, TP, NT, HALF>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, T[a] + fo,
                                               T[a] + fo + (size_t)HALF * N, &tc);
         }
     }
@@ -857,7 +858,7 @@ struct Pencil {
     static constexpr size_t smem_yfwd = sizeof(float2) * ((size_t)N * CY + N);
     static constexpr size_t smem_yinv = sizeof(float2) * ((size_t)N * 3 * CY + N);
     static constexpr size_t smem_xinv =
-        sizeof(float2) * ((size_t)RBX * PW + (size_t)RBX * TP + N) + sizeof(float4) * (size_t)N;
+        sizeof(float2) * ((size_t)RBX * PW + (size_t)RBX * TP + N);
 };
 
 // x forward: RBX rows (q = z N + y) of rotation r -> half-spectrum rows Xa[r][q][kx*].
@@ -1008,7 +1009,6 @@ __global__ void __launch_bounds__(Pencil<N>::NT) xinv_kernel(const float2 *__res
     float2 *plane = sm;                    // [RBX][PW]
     float2 *Tb = plane + RBX * PW;         // [RBX][TP]
     float2 *twN = Tb + RBX * TP;
-    float4 *xt = reinterpret_cast<float4 *>(twN + N);
     const size_t q0 = (size_t)blockIdx.x * RBX;
     const int r = blockIdx.y;
     const size_t in = ((size_t)r * N * N + q0) * H;
@@ -1019,12 +1019,11 @@ __global__ void __launch_bounds__(Pencil<N>::NT) xinv_kernel(const float2 *__res
         cp_async8(plane + row * PW + 2 * H + c, ZGz + in + i);
     }
     load_tw<N>(twN);
-    build_xtable<N>(xt);
     cp_async_wait_all();
     __syncthreads();
     const size_t fo = (size_t)r * out.rot_stride + q0 * N;
-    x_pass<N, 0, PW, RBX, TP, NT, RBX>(plane, plane, 0, H, Tb, twN, xt, out.E + fo, out.Fx + fo);
-    x_pass<N, 1, PW, RBX, TP, NT, RBX>(plane, plane, 2 * H, H, Tb, twN, xt, out.Fy + fo, out.Fz + fo);
+    x_pass<N, 0, PW, RBX, TP, NT, RBX>(plane, plane, 0, H, Tb, twN, out.E + fo, out.Fx + fo);
+    x_pass<N, 1, PW, RBX, TP, NT, RBX>(plane, plane, 2 * H, H, Tb, twN, out.Fy + fo, out.Fz + fo);
 }
 
 // ------------------------------------------- spectral-mode table of a part
