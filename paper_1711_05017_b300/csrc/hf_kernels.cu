@@ -113,8 +113,8 @@ __global__ void resample_kernel(const float *__restrict__ rho, Rot9 rot, float *
 // fastest over cell tiles so that one tile of every rotation's energy stays
 // in L2 while all rotations that use it run.
 constexpr int kTorqueThreads = 256;
-constexpr int kTorqueVec = 4;  // cells per thread (one float4)
-constexpr int kTorqueTile = kTorqueThreads * kTorqueVec;
+constexpr int kTorqueVec = 2;  // float4 groups of cells per thread, all loads in flight together
+constexpr int kTorqueTile = kTorqueThreads * 4 * kTorqueVec;
 
 template <bool F64>
 __global__ void __launch_bounds__(kTorqueThreads) torque_kernel(const float *__restrict__ E, size_t es,
@@ -125,54 +125,67 @@ __global__ void __launch_bounds__(kTorqueThreads) torque_kernel(const float *__r
                                                                 size_t n3) {
     const int r = blockIdx.x % R;
     const size_t tile = blockIdx.x / R;
-    const size_t c0 = tile * kTorqueTile + (size_t)threadIdx.x * kTorqueVec;
-    if (c0 >= n3) return;
+    // group j of the thread covers cells c0 + 4 (j kTorqueThreads) .. + 3: a
+    // warp's accesses stay contiguous for every j
+    const size_t c0 = tile * kTorqueTile + (size_t)threadIdx.x * 4;
     int nb[6];
 #pragma unroll
     for (int s = 0; s < 6; ++s) nb[s] = __ldg(nbr + 6 * r + s);
-    const float4 ei = __ldg(reinterpret_cast<const float4 *>(E + (size_t)r * es + c0));
-    float4 g[3];
-    if constexpr (!F64) {
-        float p[18];
+    float4 ei[kTorqueVec], ej[kTorqueVec][6];
+    bool live[kTorqueVec];
 #pragma unroll
-        for (int k = 0; k < 18; ++k) p[k] = __ldg(P + 18 * r + k);
+    for (int j = 0; j < kTorqueVec; ++j) {
+        const size_t c = c0 + (size_t)j * kTorqueThreads * 4;
+        live[j] = c < n3;  // n3 is a multiple of 4
+        if (live[j]) {
+            ei[j] = __ldg(reinterpret_cast<const float4 *>(E + (size_t)r * es + c));
 #pragma unroll
-        for (int d = 0; d < 3; ++d) g[d] = make_float4(0, 0, 0, 0);
-#pragma unroll
-        for (int s = 0; s < 6; ++s) {
-            const float4 ej = __ldg(reinterpret_cast<const float4 *>(E + (size_t)nb[s] * es + c0));
-            const float4 b = make_float4(ej.x - ei.x, ej.y - ei.y, ej.z - ei.z, ej.w - ei.w);
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const float w = p[6 * d + s];
-                g[d].x = fmaf(w, b.x, g[d].x);
-                g[d].y = fmaf(w, b.y, g[d].y);
-                g[d].z = fmaf(w, b.z, g[d].z);
-                g[d].w = fmaf(w, b.w, g[d].w);
-            }
+            for (int s = 0; s < 6; ++s) ej[j][s] = __ldg(reinterpret_cast<const float4 *>(E + (size_t)nb[s] * es + c));
         }
-    } else {
-        double gd[3][4] = {};
+    }
 #pragma unroll
-        for (int s = 0; s < 6; ++s) {
-            const float4 ej = __ldg(reinterpret_cast<const float4 *>(E + (size_t)nb[s] * es + c0));
-            const double b[4] = {(double)ej.x - ei.x, (double)ej.y - ei.y, (double)ej.z - ei.z,
-                                 (double)ej.w - ei.w};
+    for (int j = 0; j < kTorqueVec; ++j) {
+        if (!live[j]) continue;
+        const size_t c = c0 + (size_t)j * kTorqueThreads * 4;
+        float4 g[3];
+        if constexpr (!F64) {
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const double w = __ldg(P64 + 18 * r + 6 * d + s);
+            for (int d = 0; d < 3; ++d) g[d] = make_float4(0, 0, 0, 0);
 #pragma unroll
-                for (int c = 0; c < 4; ++c) gd[d][c] = fma(w, b[c], gd[d][c]);
+            for (int s = 0; s < 6; ++s) {
+                const float4 b = make_float4(ej[j][s].x - ei[j].x, ej[j][s].y - ei[j].y, ej[j][s].z - ei[j].z,
+                                             ej[j][s].w - ei[j].w);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const float w = __ldg(P + 18 * r + 6 * d + s);
+                    g[d].x = fmaf(w, b.x, g[d].x);
+                    g[d].y = fmaf(w, b.y, g[d].y);
+                    g[d].z = fmaf(w, b.z, g[d].z);
+                    g[d].w = fmaf(w, b.w, g[d].w);
+                }
             }
+        } else {
+            double gd[3][4] = {};
+#pragma unroll
+            for (int s = 0; s < 6; ++s) {
+                const double b[4] = {(double)ej[j][s].x - ei[j].x, (double)ej[j][s].y - ei[j].y,
+                                     (double)ej[j][s].z - ei[j].z, (double)ej[j][s].w - ei[j].w};
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const double w = __ldg(P64 + 18 * r + 6 * d + s);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) gd[d][q] = fma(w, b[q], gd[d][q]);
+                }
+            }
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                g[d] = make_float4((float)gd[d][0], (float)gd[d][1], (float)gd[d][2], (float)gd[d][3]);
         }
 #pragma unroll
         for (int d = 0; d < 3; ++d)
-            g[d] = make_float4((float)gd[d][0], (float)gd[d][1], (float)gd[d][2], (float)gd[d][3]);
+            *reinterpret_cast<float4 *>(T + (size_t)r * ts + (size_t)d * n3 + c) =
+                make_float4(-g[d].x, -g[d].y, -g[d].z, -g[d].w);
     }
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-        *reinterpret_cast<float4 *>(T + (size_t)r * ts + (size_t)d * n3 + c0) =
-            make_float4(-g[d].x, -g[d].y, -g[d].z, -g[d].w);
 }
 
 // ------------------------------------------------------------------ query
