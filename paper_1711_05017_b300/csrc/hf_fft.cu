@@ -57,6 +57,15 @@ constexpr TwTab<L> make_tw() {
 }
 template <int L>
 __device__ const TwTab<L> g_tw = make_tw<L>();
+// the same table in constant memory, for twiddles read at a warp-uniform
+// index (served by the constant cache, off the shared-memory pipe)
+template <int L>
+__constant__ TwTab<L> c_tw = make_tw<L>();
+template <int L>
+__device__ __forceinline__ float2 tw_uniform(int j) {
+    const cf2 t = c_tw<L>.v[j];
+    return make_float2(t.x, t.y);
+}
 
 template <int L>
 __device__ __forceinline__ void load_tw(float2 *dst) {
@@ -610,7 +619,7 @@ struct TorqueCorr {
     int row1;           // out1's rows are out0's rows + row1
 };
 
-template <int N, int PAIR, int PW, int RB, int TP, int NT, int ROWS>
+template <int N, int PAIR, int PW, int RB, int TP, int NT, int ROWS, bool CTW = true>
 __device__ __forceinline__ void x_pass(const float2 *planeA, const float2 *planeB, int colA, int colB,
                                        float2 *Tb, const float2 *twN,
                                        float *__restrict__ out0, float *__restrict__ out1,
@@ -643,7 +652,12 @@ __device__ __forceinline__ void x_pass(const float2 *planeA, const float2 *plane
             RegDFT<R2, +1>::run(v);
             float2 *tr = Tb + row * TP + R2 * k1;
 #pragma unroll
-            for (int n2 = 0; n2 < R2; ++n2) tr[n2] = n2 ? cmulc(v[n2], twN[n2 * k1]) : v[n2];
+            for (int n2 = 0; n2 < R2; ++n2) {
+                // twiddles from constant memory where k1 is warp-uniform (RB a
+                // multiple of 32), else from the shared table
+                const float2 t = (CTW && RB % 32 == 0) ? tw_uniform<N>(n2 * k1) : twN[n2 * k1];
+                tr[n2] = n2 ? cmulc(v[n2], t) : v[n2];
+            }
         }
         __syncthreads();
         // stage 2 (inverse), items (row, n2), lanes along n2: x = R2 n1 + n2
@@ -702,7 +716,7 @@ __device__ __forceinline__ void x_pass(const float2 *planeA, const float2 *plane
 // transformed in place in two small steps that ride along with stage 2's
 // read and write phases (one warp each), so it costs no barrier of its own.
 // MUL multiplies input row s by i pi ky~(s) on the way in (forms Gy from S').
-template <int N, bool MUL>
+template <int N, bool MUL, bool CTW = true>
 __device__ __forceinline__ void y_inverse_plane(const float2 *__restrict__ src, float2 *plane, const float2 *twN) {
     constexpr int H = N / 2 + 1, HALF = N / 2, R1 = Fact<N>::R1, R2 = Fact<N>::R2, PW = PassC<N>::PW,
                   NT = PassC<N>::NT;
@@ -722,7 +736,11 @@ __device__ __forceinline__ void y_inverse_plane(const float2 *__restrict__ src, 
         }
         RegDFT<R2, +1>::run(v);
 #pragma unroll
-        for (int n2 = 0; n2 < R2; ++n2) plane[(n2 * R1 + k1) * PW + c] = n2 ? cmulc(v[n2], twN[n2 * k1]) : v[n2];
+        for (int n2 = 0; n2 < R2; ++n2) {
+            // k1 is warp-uniform when N/2 is a multiple of 32
+            const float2 t = (CTW && HALF % 32 == 0) ? tw_uniform<N>(n2 * k1) : twN[n2 * k1];
+            plane[(n2 * R1 + k1) * PW + c] = n2 ? cmulc(v[n2], t) : v[n2];
+        }
     }
     if (threadIdx.x < N) {
         if constexpr (MUL) nyq = cmul_is(nyq, signed_k_mult<N>(slot_freq<N>(threadIdx.x)));
@@ -801,24 +819,24 @@ __global__ void __launch_bounds__(PassC<N>::NT, PassC<N>::MINB) passC_kernel(con
     load_tw<N>(twN);
     __syncthreads();
     // E + i Fx
-    y_inverse_plane<N, false>(s1, plane, twN);
-    x_pass<N, 0, PW, RB, TP, NT, N>(plane, plane, 0, 0, Tb, twN, out.E + fo, out.Fx + fo);
+    y_inverse_plane<N, false, !TQ>(s1, plane, twN);
+    x_pass<N, 0, PW, RB, TP, NT, N, !TQ>(plane, plane, 0, 0, Tb, twN, out.E + fo, out.Fx + fo);
     // Fy from Gy = i pi ky~ S'
-    y_inverse_plane<N, true>(s1, plane, twN);
-    x_pass<N, 1, PW, RB, TP, NT, HALF>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, out.Fy + fo,
+    y_inverse_plane<N, true, !TQ>(s1, plane, twN);
+    x_pass<N, 1, PW, RB, TP, NT, HALF, !TQ>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, out.Fy + fo,
                                       out.Fy + fo + (size_t)HALF * N);
     // Fz
-    y_inverse_plane<N, false>(Y2 + ((size_t)r * N + z) * N * H, plane, twN);
-    x_pass<N, 1, PW, RB, TP, NT, HALF>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, out.Fz + fo,
+    y_inverse_plane<N, false, !TQ>(Y2 + ((size_t)r * N + z) * N * H, plane, twN);
+    x_pass<N, 1, PW, RB, TP, NT, HALF, !TQ>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, out.Fz + fo,
                                       out.Fz + fo + (size_t)HALF * N);
     if constexpr (TQ) {
         // analytic torque: T_a = C(G_a, rho2R) - (t x F)_a, rows paired like Fy
         float *T[3] = {out.Tx, out.Ty, out.Tz};
 #pragma unroll 1
         for (int a = 0; a < 3; ++a) {
-            y_inverse_plane<N, false>(YT + a * yt_stride + ((size_t)r * N + z) * N * H, plane, twN);
+            y_inverse_plane<N, false, !TQ>(YT + a * yt_stride + ((size_t)r * N + z) * N * H, plane, twN);
             const TorqueCorr tc{{out.Fx + fo, out.Fy + fo, out.Fz + fo}, a, z < HALF ? z : z - N, HALF};
-            x_pass<N, 1, PW, RB, TP, NT, HALF>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, T[a] + fo,
+            x_pass<N, 1, PW, RB, TP, NT, HALF, !TQ>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, T[a] + fo,
                                               T[a] + fo + (size_t)HALF * N, &tc);
         }
     }
