@@ -74,6 +74,43 @@ __host__ __device__ constexpr double trig(long j, long R, int which) {
 }
 }  // namespace ct
 
+// ---------------------------------------------------------------- twiddles
+struct cf2 {
+    float x, y;
+};
+template <int L>
+struct TwTab {
+    cf2 v[L];
+};
+template <int L>
+constexpr TwTab<L> make_tw() {
+    TwTab<L> t{};
+    for (int j = 0; j < L; ++j) {
+        t.v[j].x = (float)ct::trig(j, L, 0);
+        t.v[j].y = (float)(-ct::trig(j, L, 1));  // exp(-2 pi i j / L)
+    }
+    return t;
+}
+template <int L>
+__device__ const TwTab<L> g_tw = make_tw<L>();
+// the same table in constant memory, for twiddles read at a warp-uniform
+// index (served by the constant cache, off the shared-memory pipe)
+template <int L>
+__constant__ TwTab<L> c_tw = make_tw<L>();
+template <int L>
+__device__ __forceinline__ float2 tw_uniform(int j) {
+    const cf2 t = c_tw<L>.v[j];
+    return make_float2(t.x, t.y);
+}
+// twiddle j of length L: from constant memory when the caller's index is
+// warp-uniform (UNIFORM), else from the shared copy tw
+template <int L, bool UNIFORM>
+__device__ __forceinline__ float2 tw_pick(const float2 *tw, int j) {
+    if constexpr (UNIFORM) return tw_uniform<L>(j);
+    else return tw[j];
+}
+
+
 template <int I, int E, class F>
 __device__ __forceinline__ void static_for(F &&f) {
     if constexpr (I < E) {
@@ -210,7 +247,9 @@ __device__ __forceinline__ int slot_freq(int s) {
 }
 
 // ------------------------------------------------ two-stage batched FFT
-// tw[j] = exp(-2 pi i j / L), j < L (forward sign), in shared memory.
+// tw[j] = exp(-2 pi i j / L), j < L (forward sign), in shared memory; where
+// M is a multiple of 32 a warp's twiddle index is uniform and the constant-
+// memory copy of the same table is read instead.
 // M lines; element j of line f at base[f * LS + j * ES]; NT threads.  All
 // sizes are compile-time so every index is a multiply-shift.  All threads of
 // the block must call; ends with __syncthreads.
@@ -228,7 +267,7 @@ __device__ __forceinline__ void fft_lines(float2 *base, const float2 *tw) {
             for (int n1 = 0; n1 < R1; ++n1) v[n1] = p[n1 * R2 * ES];
             RegDFT<R1, -1>::run(v);
 #pragma unroll
-            for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmul(v[k1], tw[n2 * k1]);
+            for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmul(v[k1], tw_pick<L, M % 32 == 0>(tw, n2 * k1));
 #pragma unroll
             for (int k1 = 0; k1 < R1; ++k1) p[k1 * R2 * ES] = v[k1];
         }
@@ -257,7 +296,7 @@ __device__ __forceinline__ void fft_lines(float2 *base, const float2 *tw) {
             for (int k2 = 0; k2 < R2; ++k2) v[k2] = p[k2 * ES];
             RegDFT<R2, +1>::run(v);
 #pragma unroll
-            for (int n2 = 1; n2 < R2; ++n2) v[n2] = cmulc(v[n2], tw[n2 * k1]);
+            for (int n2 = 1; n2 < R2; ++n2) v[n2] = cmulc(v[n2], tw_pick<L, M % 32 == 0>(tw, n2 * k1));
 #pragma unroll
             for (int n2 = 0; n2 < R2; ++n2) p[n2 * ES] = v[n2];
         }

@@ -38,35 +38,6 @@
 
 namespace hf {
 
-// ---------------------------------------------------------------- twiddles
-struct cf2 {
-    float x, y;
-};
-template <int L>
-struct TwTab {
-    cf2 v[L];
-};
-template <int L>
-constexpr TwTab<L> make_tw() {
-    TwTab<L> t{};
-    for (int j = 0; j < L; ++j) {
-        t.v[j].x = (float)ct::trig(j, L, 0);
-        t.v[j].y = (float)(-ct::trig(j, L, 1));  // exp(-2 pi i j / L)
-    }
-    return t;
-}
-template <int L>
-__device__ const TwTab<L> g_tw = make_tw<L>();
-// the same table in constant memory, for twiddles read at a warp-uniform
-// index (served by the constant cache, off the shared-memory pipe)
-template <int L>
-__constant__ TwTab<L> c_tw = make_tw<L>();
-template <int L>
-__device__ __forceinline__ float2 tw_uniform(int j) {
-    const cf2 t = c_tw<L>.v[j];
-    return make_float2(t.x, t.y);
-}
-
 template <int L>
 __device__ __forceinline__ void load_tw(float2 *dst) {
     for (int i = threadIdx.x; i < L; i += blockDim.x) dst[i] = make_float2(g_tw<L>.v[i].x, g_tw<L>.v[i].y);
@@ -246,7 +217,7 @@ __global__ void __launch_bounds__(PassA<N>::NT, SRC == SRC_TEX ? 2 : PassA<N>::M
             const float2 a = row[s1], b = row[s2];
             const float2 Ek = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
             const float2 Ok = make_float2(0.5f * (a.y + b.y), -0.5f * (a.x - b.x));
-            const float2 WO = cmul(twN[k], Ok);
+            const float2 WO = cmul(tw_pick<N, N % 32 == 0>(twN, k), Ok);  // k = i / N: warp-uniform
             row[s1] = cadd(Ek, WO);
             row[s2] = cconj(csub(Ek, WO));
         }
@@ -428,7 +399,8 @@ __global__ void __launch_bounds__(PassB<N>::NT, PassB<N>::MINB) passB_kernel(con
             __syncthreads();  // twiddles in place
             RegDFT<R1, -1>::run(v);
 #pragma unroll
-            for (int k1 = 0; k1 < R1; ++k1) E[(k1 * R2 + g) * CW + c] = k1 ? cmul(v[k1], twN[g * k1]) : v[k1];
+            for (int k1 = 0; k1 < R1; ++k1)
+                E[(k1 * R2 + g) * CW + c] = k1 ? cmul(v[k1], tw_pick<N, CW % 32 == 0>(twN, g * k1)) : v[k1];
         }
         __syncthreads();
         // forward stage 2: X[j][k2] = slot R2 k1 + k2 for k1 = g + R2 j
@@ -471,7 +443,7 @@ __global__ void __launch_bounds__(PassB<N>::NT, PassB<N>::MINB) passB_kernel(con
                 RegDFT<R2, +1>::run(Gv);
 #pragma unroll
                 for (int n2 = 0; n2 < R2; ++n2) {
-                    const float2 t = twN[n2 * k1];
+                    const float2 t = tw_pick<N, CW % 32 == 0>(twN, n2 * k1);
                     E[(n2 * R1 + k1) * CW + c] = n2 ? cmulc(Sv[n2], t) : Sv[n2];
                     G[(n2 * R1 + k1) * CW + c] = n2 ? cmulc(Gv[n2], t) : Gv[n2];
                 }
@@ -522,7 +494,8 @@ __global__ void __launch_bounds__(PassB<N>::NT, 2) passB_torque_kernel(const flo
         __syncthreads();
         RegDFT<R1, -1>::run(v);
 #pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1) E[0][(k1 * R2 + g) * CW + c] = k1 ? cmul(v[k1], twN[g * k1]) : v[k1];
+        for (int k1 = 0; k1 < R1; ++k1)
+            E[0][(k1 * R2 + g) * CW + c] = k1 ? cmul(v[k1], tw_pick<N, CW % 32 == 0>(twN, g * k1)) : v[k1];
     }
     __syncthreads();
     float2 X[KPT][R2];
@@ -549,7 +522,7 @@ __global__ void __launch_bounds__(PassB<N>::NT, 2) passB_torque_kernel(const flo
                 RegDFT<R2, +1>::run(T);
 #pragma unroll
                 for (int n2 = 0; n2 < R2; ++n2)
-                    E[a][(n2 * R1 + k1) * CW + c] = n2 ? cmulc(T[n2], twN[n2 * k1]) : T[n2];
+                    E[a][(n2 * R1 + k1) * CW + c] = n2 ? cmulc(T[n2], tw_pick<N, CW % 32 == 0>(twN, n2 * k1)) : T[n2];
             }
         }
     }
