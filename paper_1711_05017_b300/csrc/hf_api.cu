@@ -105,7 +105,11 @@ struct hf_part {
     // table_os * N nodes per axis, full cube, natural order (spectral mode)
     float2 *table = nullptr;
     int table_os = 0;
-    size_t table_bytes = 0;
+    size_t table_bytes = 0;  // the table and its gather array
+    // the table as a float2 gather texture of stacked, wrap-padded slices
+    // (read by the spectral field build; the queries read the table itself)
+    cudaArray_t tarr = nullptr;
+    cudaTextureObject_t ttex = 0;
     // HF_STATIONARY after hf_part_moments: the spectra of the moment fields
     // G_a = -(u x grad rho1)_a, 3 half spectra (slot order, scaled like spec)
     float2 *mspec = nullptr;
@@ -479,6 +483,17 @@ extern "C" hf_status hf_part_update(hf_part *p, const float *d_grid, hf_stream s
 
 // the centred, zero-padded spectrum of a moving part (Section 3.2: the
 // moving spectrum is precomputed, then read at rotated frequencies)
+static void table_free(hf_part *p) {
+    if (p->ttex) cudaDestroyTextureObject(p->ttex);
+    if (p->tarr) cudaFreeArray(p->tarr);
+    if (p->table) cudaFree(p->table);
+    if (p->table_bytes) uncharge(p->ctx, p->table_bytes);
+    p->ttex = 0;
+    p->tarr = nullptr;
+    p->table = nullptr;
+    p->table_bytes = 0;
+}
+
 static hf_status spectral_table_fill(hf_part *p, const float *d_grid, cudaStream_t st) {
     const int n = p->n, np = p->table_os * n;
     const size_t np3 = (size_t)np * np * np;
@@ -492,6 +507,17 @@ static hf_status spectral_table_fill(hf_part *p, const float *d_grid, cudaStream
     if (e == cudaSuccess && s == HF_OK) e = hf::run_spectral_complete(np, half, p->table, st);
     if (pad) cudaFreeAsync(pad, st);
     if (half) cudaFreeAsync(half, st);
+    if (e == cudaSuccess && s == HF_OK) {  // the gather texture, through a padded staging slab
+        int w = 0, h = 0;
+        hf::table_tex_layout(np, &w, &h);
+        float2 *slab = nullptr;
+        e = cudaMallocAsync(&slab, (size_t)w * h * sizeof(float2), st);
+        if (e == cudaSuccess) e = hf::run_pad_table(p->table, np, slab, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DToArrayAsync(p->tarr, 0, 0, slab, (size_t)w * sizeof(float2), (size_t)w * sizeof(float2),
+                                         (size_t)h, cudaMemcpyDeviceToDevice, st);
+        if (slab) cudaFreeAsync(slab, st);
+    }
     if (s != HF_OK) return s;
     if (e != cudaSuccess) return fail(HF_ECUDA, "hf_part_spectral: %s", cudaGetErrorString(e));
     return HF_OK;
@@ -505,23 +531,46 @@ extern "C" hf_status hf_part_spectral(hf_part *p, int os, hf_stream stream) {
         return fail(HF_EUNSUPPORTED, "hf_part_spectral: padded size %d not supported", os * p->n);
     CU(cudaSetDevice(p->ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t np = (size_t)os * p->n, bytes = np * np * np * sizeof(float2);
+    const size_t np = (size_t)os * p->n, tbytes = np * np * np * sizeof(float2);
+    int tw = 0, th = 0, maxw = 0, maxh = 0;
+    hf::table_tex_layout((int)np, &tw, &th);
+    if (cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxTexture2DGatherWidth, p->ctx->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&maxh, cudaDevAttrMaxTexture2DGatherHeight, p->ctx->device) != cudaSuccess ||
+        tw > maxw || th > maxh)
+        return fail(HF_EUNSUPPORTED, "hf_part_spectral: a %d x %d gather texture exceeds the device's limits", tw, th);
+    const size_t bytes = tbytes + (size_t)tw * th * sizeof(float2);
     if (p->table && p->table_os != os) {
         CU(cudaStreamSynchronize(st));
-        cudaFree(p->table);
-        uncharge(p->ctx, p->table_bytes);
-        p->table = nullptr;
-        p->table_bytes = 0;
+        table_free(p);
     }
     if (!p->table) {
         if (!charge(p->ctx, bytes)) return fail(HF_EBUDGET, "hf_part_spectral: %zu bytes exceed the budget", bytes);
-        const cudaError_t e = cudaMalloc(&p->table, bytes);
-        if (e != cudaSuccess) {
-            p->table = nullptr;
-            uncharge(p->ctx, bytes);
-            return fail(HF_ENOMEM, "hf_part_spectral: cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
-        }
         p->table_bytes = bytes;
+        cudaError_t e = cudaMalloc(&p->table, tbytes);
+        if (e != cudaSuccess) p->table = nullptr;
+        if (e == cudaSuccess) {
+            cudaChannelFormatDesc fd = cudaCreateChannelDesc<float2>();
+            e = cudaMallocArray(&p->tarr, &fd, (size_t)tw, (size_t)th, cudaArrayTextureGather);
+            if (e != cudaSuccess) p->tarr = nullptr;
+        }
+        if (e == cudaSuccess) {
+            cudaResourceDesc rd = {};
+            rd.resType = cudaResourceTypeArray;
+            rd.res.array.array = p->tarr;
+            cudaTextureDesc td = {};
+            td.addressMode[0] = cudaAddressModeClamp;
+            td.addressMode[1] = cudaAddressModeClamp;
+            td.filterMode = cudaFilterModePoint;
+            td.readMode = cudaReadModeElementType;
+            td.normalizedCoords = 0;
+            e = cudaCreateTextureObject(&p->ttex, &rd, &td, nullptr);
+            if (e != cudaSuccess) p->ttex = 0;
+        }
+        if (e != cudaSuccess) {
+            table_free(p);
+            return fail(e == cudaErrorMemoryAllocation ? HF_ENOMEM : HF_ECUDA, "hf_part_spectral: %zu bytes: %s", bytes,
+                        cudaGetErrorString(e));
+        }
     }
     p->table_os = os;
     return spectral_table_fill(p, p->grid, st);
@@ -584,10 +633,7 @@ extern "C" hf_status hf_part_moments(hf_part *p, hf_stream stream) {
 extern "C" void hf_part_release(hf_part *p) {
     if (!p) return;
     cudaSetDevice(p->ctx->device);
-    if (p->table) {
-        cudaFree(p->table);
-        uncharge(p->ctx, p->table_bytes);
-    }
+    table_free(p);
     if (p->mspec) {
         cudaFree(p->mspec);
         uncharge(p->ctx, 3 * hf::half_spec_elems(p->n) * sizeof(float2));
@@ -926,7 +972,7 @@ static hf_status run_fields(hf_ctx *c, int n, bool pencil, int prec, const hf_pa
     float2 *X1 = scratch, *Y1 = scratch + scratch_rot, *Y2 = scratch + 2 * scratch_rot;
     if (spectral) {
         CU(timed(c, kPassB, st, [&] {
-            return hf::run_passB_spectral(n, s2->table, s2->table_os, rot9, s1->spec, Y1, Y2, cnt, st);
+            return hf::run_passB_spectral(n, s2->table, s2->ttex, s2->table_os, rot9, s1->spec, Y1, Y2, cnt, st);
         }));
         if (pencil) {
             float2 *A = scratch + 3 * scratch_rot, *B = scratch + 4 * scratch_rot;

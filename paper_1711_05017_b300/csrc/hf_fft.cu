@@ -317,15 +317,20 @@ __device__ __forceinline__ float2 spectral_sample(const SpecSrc &src, const floa
     float w[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) rot_coord(R[a], R[3 + a], R[6 + a], ks[0], ks[1], ks[2], i[a], w[a]);
-    const int np = src.np;
-    const int x0 = table_wrap(i[0], np), x1 = table_wrap(i[0] + 1, np);
-    const int y0 = table_wrap(i[1], np), y1 = table_wrap(i[1] + 1, np);
-    const float2 *p0 = src.table + (size_t)table_wrap(i[2], np) * np * np;
-    const float2 *p1 = src.table + (size_t)table_wrap(i[2] + 1, np) * np * np;
-    const float2 a00 = __ldg(p0 + (size_t)y0 * np + x0), a01 = __ldg(p0 + (size_t)y0 * np + x1);
-    const float2 a10 = __ldg(p0 + (size_t)y1 * np + x0), a11 = __ldg(p0 + (size_t)y1 * np + x1);
-    const float2 b00 = __ldg(p1 + (size_t)y0 * np + x0), b01 = __ldg(p1 + (size_t)y0 * np + x1);
-    const float2 b10 = __ldg(p1 + (size_t)y1 * np + x0), b11 = __ldg(p1 + (size_t)y1 * np + x1);
+    const int np = src.np, sc = src.sc;
+    const int x0 = table_wrap(i[0], np), y0 = table_wrap(i[1], np);
+    const int z0 = table_wrap(i[2], np), z1 = table_wrap(i[2] + 1, np);
+    // one 2x2 gather per slice and component at the integer corner (x0+1,
+    // y0+1) of the padded slice: w = (x0, y0), z = (x0+1, y0), x = (x0, y0+1),
+    // y = (x0+1, y0+1); the wrapped neighbours come from the padding
+    const float u0 = (float)((z0 % sc) * (np + 1) + x0) + 1.0f, v0 = (float)((z0 / sc) * (np + 1) + y0) + 1.0f;
+    const float u1 = (float)((z1 % sc) * (np + 1) + x0) + 1.0f, v1 = (float)((z1 / sc) * (np + 1) + y0) + 1.0f;
+    const float4 ra = tex2Dgather<float4>(src.tex, u0, v0, 0), ia = tex2Dgather<float4>(src.tex, u0, v0, 1);
+    const float4 rb = tex2Dgather<float4>(src.tex, u1, v1, 0), ib = tex2Dgather<float4>(src.tex, u1, v1, 1);
+    const float2 a00 = make_float2(ra.w, ia.w), a01 = make_float2(ra.z, ia.z);
+    const float2 a10 = make_float2(ra.x, ia.x), a11 = make_float2(ra.y, ia.y);
+    const float2 b00 = make_float2(rb.w, ib.w), b01 = make_float2(rb.z, ib.z);
+    const float2 b10 = make_float2(rb.x, ib.x), b11 = make_float2(rb.y, ib.y);
     const float wx = w[0], wy = w[1], wz = w[2];
     auto lerp2 = [](float2 a, float2 b, float t) { return make_float2(fmaf(t, b.x - a.x, a.x), fmaf(t, b.y - a.y, a.y)); };
     const float2 v = lerp2(lerp2(lerp2(a00, a01, wx), lerp2(a10, a11, wx), wy),
@@ -1129,11 +1134,11 @@ static cudaError_t launch_passB_fwd(const float2 *X1, float2 *spec, float scale,
     return cudaGetLastError();
 }
 template <int N>
-static cudaError_t launch_passB_spectral(const float2 *table, int os, const float *rot9, const float2 *R1hat,
-                                         float2 *Y1, float2 *Y2, int nrot, cudaStream_t st) {
+static cudaError_t launch_passB_spectral(const float2 *table, cudaTextureObject_t tex, int os, const float *rot9,
+                                         const float2 *R1hat, float2 *Y1, float2 *Y2, int nrot, cudaStream_t st) {
     constexpr int tiles = (N / 2 + PassB<N>::CW - 1) / PassB<N>::CW;
     passB_kernel<N, 2><<<dim3(N * tiles, nrot), PassB<N>::NT, PassB<N>::smem, st>>>(
-        nullptr, R1hat, Y1, Y2, 0.f, SpecSrc{table, os * N, os}, rot9);
+        nullptr, R1hat, Y1, Y2, 0.f, SpecSrc{table, os * N, os, tex, table_tex_sc(os * N)}, rot9);
     return cudaGetLastError();
 }
 template <int N>
@@ -1274,9 +1279,34 @@ cudaError_t run_pad_center(int n, const float *g, float *out, int np, cudaStream
 cudaError_t run_spectral_complete(int np, const float2 *spec, float2 *table, cudaStream_t st) {
     HF_DISPATCH_ALL(np, launch_spectral_complete<NN>(spec, table, st));
 }
-cudaError_t run_passB_spectral(int n, const float2 *table, int os, const float *rot9, const float2 *R1hat, float2 *Y1,
-                               float2 *Y2, int nrot, cudaStream_t st) {
-    HF_DISPATCH_ALL(n, launch_passB_spectral<NN>(table, os, rot9, R1hat, Y1, Y2, nrot, st));
+cudaError_t run_passB_spectral(int n, const float2 *table, cudaTextureObject_t tex, int os, const float *rot9,
+                               const float2 *R1hat, float2 *Y1, float2 *Y2, int nrot, cudaStream_t st) {
+    HF_DISPATCH_ALL(n, launch_passB_spectral<NN>(table, tex, os, rot9, R1hat, Y1, Y2, nrot, st));
+}
+// the table as stacked, wrap-padded (np+1)^2 slices, sc to a texture row:
+// texel (X, Y) of the width x height slab is cell (X mod (np+1), Y mod (np+1))
+// of slice (Y / (np+1)) sc + X / (np+1), indices np wrapping to 0
+__global__ void pad_table_kernel(const float2 *__restrict__ table, int np, int sc, float2 *__restrict__ slab,
+                                 int width, int height) {
+    const size_t total = (size_t)width * height;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int X = (int)(i % width), Y = (int)(i / width);
+        const int z = (Y / (np + 1)) * sc + X / (np + 1);
+        const int lx = X % (np + 1), ly = Y % (np + 1);
+        slab[i] = z < np ? table[((size_t)z * np + (ly == np ? 0 : ly)) * np + (lx == np ? 0 : lx)]
+                         : make_float2(0.f, 0.f);
+    }
+}
+void table_tex_layout(int np, int *width, int *height) {
+    const int sc = table_tex_sc(np);
+    *width = sc * (np + 1);
+    *height = ((np + sc - 1) / sc) * (np + 1);
+}
+cudaError_t run_pad_table(const float2 *table, int np, float2 *slab, cudaStream_t st) {
+    int w = 0, h = 0;
+    table_tex_layout(np, &w, &h);
+    pad_table_kernel<<<8 * 148, 256, 0, st>>>(table, np, table_tex_sc(np), slab, w, h);
+    return cudaGetLastError();
 }
 cudaError_t run_passB_torque(int n, const float2 *X1, const float2 *Gm, float2 *YT, size_t yt_stride, int nrot,
                              cudaStream_t st) {

@@ -69,8 +69,12 @@ cudaError_t run_unpermute(int n, const float2 *spec, float2 *out, cudaStream_t s
 // transforming resampled planes
 cudaError_t run_pad_center(int n, const float *g, float *out, int np, cudaStream_t st);
 cudaError_t run_spectral_complete(int np, const float2 *spec, float2 *table, cudaStream_t st);
-cudaError_t run_passB_spectral(int n, const float2 *table, int os, const float *rot9, const float2 *R1hat, float2 *Y1,
-                               float2 *Y2, int nrot, cudaStream_t st);
+cudaError_t run_passB_spectral(int n, const float2 *table, cudaTextureObject_t tex, int os, const float *rot9,
+                               const float2 *R1hat, float2 *Y1, float2 *Y2, int nrot, cudaStream_t st);
+// the spectral table's gather texture: np^3 cells as stacked, wrap-padded
+// (np+1)^2 slices (table_tex_sc(np) per row) in a width x height float2 array
+void table_tex_layout(int np, int *width, int *height);
+cudaError_t run_pad_table(const float2 *table, int np, float2 *slab, cudaStream_t st);
 // analytic torque (rotational gradient of Eq. 6b, moment on the stationary
 // side): the three products Gm_a conj(rho2^R^) of the stationary moment
 // spectra Gm (3 half spectra, slot order, scaled) with the rotated moving

@@ -25,7 +25,14 @@ struct SpecSrc {
     const float2 *table;
     int np;  // os * N
     int os;
+    // the same table as stacked, wrap-padded (np+1)^2 slices of a float2
+    // gather texture, sc slices per texture row (read by the field build)
+    cudaTextureObject_t tex = 0;
+    int sc = 0;
 };
+
+// slices per row of a table texture of np^3 cells
+__host__ __device__ __forceinline__ int table_tex_sc(int np) { return np >= 128 ? 16 : 8; }
 
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     s = a + b;
