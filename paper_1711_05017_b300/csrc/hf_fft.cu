@@ -597,7 +597,18 @@ struct TorqueCorr {
     int row1;           // out1's rows are out0's rows + row1
 };
 
-template <int N, int PAIR, int PW, int RB, int TP, int NT, int ROWS, bool CTW = true>
+// store with an L2 evict-last policy: rows that the same CTA reads back soon
+__device__ __forceinline__ uint64_t l2_keep_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void st_keep(float *p, float v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
+}
+
+template <int N, int PAIR, int PW, int RB, int TP, int NT, int ROWS, bool CTW = true, bool KEEP0 = false,
+          bool KEEP1 = false>
 __device__ __forceinline__ void x_pass(const float2 *planeA, const float2 *planeB, int colA, int colB,
                                        float2 *Tb, const float2 *twN,
                                        float *__restrict__ out0, float *__restrict__ out1,
@@ -675,10 +686,18 @@ __device__ __forceinline__ void x_pass(const float2 *planeA, const float2 *plane
                     out1[oo] = -v[n1].y - c1;
                 }
             } else {
+                uint64_t pol = 0;
+                if constexpr (KEEP0 || KEEP1) pol = l2_keep_policy();
 #pragma unroll
                 for (int n1 = 0; n1 < R1; ++n1) {
-                    out0[o + (size_t)R2 * n1] = v[n1].x;
-                    out1[o + (size_t)R2 * n1] = v[n1].y;
+                    if constexpr (KEEP0)
+                        st_keep(out0 + o + (size_t)R2 * n1, v[n1].x, pol);
+                    else
+                        out0[o + (size_t)R2 * n1] = v[n1].x;
+                    if constexpr (KEEP1)
+                        st_keep(out1 + o + (size_t)R2 * n1, v[n1].y, pol);
+                    else
+                        out1[o + (size_t)R2 * n1] = v[n1].y;
                 }
             }
         }
@@ -798,14 +817,15 @@ __global__ void __launch_bounds__(PassC<N>::NT, PassC<N>::MINB) passC_kernel(con
     __syncthreads();
     // E + i Fx
     y_inverse_plane<N, false, !TQ>(s1, plane, twN);
-    x_pass<N, 0, PW, RB, TP, NT, N, !TQ>(plane, plane, 0, 0, Tb, twN, out.E + fo, out.Fx + fo);
+    // with the torque phases (TQ) this CTA reads its force rows back: keep them in L2
+    x_pass<N, 0, PW, RB, TP, NT, N, !TQ, false, TQ>(plane, plane, 0, 0, Tb, twN, out.E + fo, out.Fx + fo);
     // Fy from Gy = i pi ky~ S'
     y_inverse_plane<N, true, !TQ>(s1, plane, twN);
-    x_pass<N, 1, PW, RB, TP, NT, HALF, !TQ>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, out.Fy + fo,
+    x_pass<N, 1, PW, RB, TP, NT, HALF, !TQ, TQ, TQ>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, out.Fy + fo,
                                       out.Fy + fo + (size_t)HALF * N);
     // Fz
     y_inverse_plane<N, false, !TQ>(Y2 + ((size_t)r * N + z) * N * H, plane, twN);
-    x_pass<N, 1, PW, RB, TP, NT, HALF, !TQ>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, out.Fz + fo,
+    x_pass<N, 1, PW, RB, TP, NT, HALF, !TQ, TQ, TQ>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, out.Fz + fo,
                                       out.Fz + fo + (size_t)HALF * N);
     if constexpr (TQ) {
         // analytic torque: T_a = C(G_a, rho2R) - (t x F)_a, rows paired like Fy

@@ -16,10 +16,13 @@ fields.
     so that a tie resolved differently by rounding cannot drop a neighbour),
     in global index order, so that a neighbour search inside the build set
     breaks ties exactly as one over the whole set;
-  - queries: a pose is routed to the rank that owns its nearest sampled
-    rotation, or to the first rank whose build set holds all k rotations the
-    query blends.  When no build set holds them all, the route says so
-    (exact False): the blend on that rank then uses its own nearest k.
+  - queries: a pose blends the fields of its k nearest sampled rotations,
+    torque included, so it is exact on a rank whose set of complete
+    rotations holds all k: rotations whose 6 nearest are all in the rank's
+    build set (the owned ones and part of the halo).  A pose goes to the
+    owner of its nearest rotation when that rank qualifies, else to the
+    first rank that does; when none does, the route says so (exact False)
+    and the owner answers with its own nearest k.
 
 This is host logic only (which rotations each rank builds); every field is
 computed by the library's kernels on the rank's own GPU.
@@ -92,15 +95,18 @@ def cluster(quats, world, iters=8):
 class Shard:
     """One rank's share of a rotation set.
 
-    owned  -- global indices this rank reports (torque included), ascending
-    build  -- global indices this rank builds fields for, ascending: owned
-              plus the halo; its field set holds them in this order
-    local  -- position in `build` of each owned rotation
+    owned    -- global indices this rank reports (torque included), ascending
+    build    -- global indices this rank builds fields for, ascending: owned
+                plus the halo; its field set holds them in this order
+    local    -- position in `build` of each owned rotation
+    complete -- global indices in `build` whose 6 nearest are all in `build`
+                (their torque is the whole set's), ascending
     """
 
-    def __init__(self, owned, build):
+    def __init__(self, owned, build, complete):
         self.owned = np.asarray(owned, dtype=np.int64)
         self.build = np.asarray(build, dtype=np.int64)
+        self.complete = np.asarray(complete, dtype=np.int64)
         pos = {int(g): i for i, g in enumerate(self.build)}
         self.local = np.array([pos[int(g)] for g in self.owned], dtype=np.int64)
 
@@ -116,18 +122,19 @@ def shard(quats, world, halo=8):
     for r in range(world):
         owned = np.flatnonzero(owner == r)
         build = np.union1d(owned, nb[owned].ravel())
-        out.append(Shard(owned, build))
+        complete = build[np.isin(nb[build, :6], build).all(axis=1)]
+        out.append(Shard(owned, build, complete))
     return out
 
 
 def route(quats, shards, q, k=4):
     """Rank for a pose query with rotation q blending k sampled rotations:
-    (rank, exact).  exact is True when that rank's build set holds the k
-    rotations the query blends over the whole set."""
+    (rank, exact).  exact is True when the k rotations the query blends over
+    the whole set are complete rotations of that rank."""
     want = nearest(quats, k, q=np.asarray(q).reshape(1, 4), skip_self=False)[0]
-    owner_of_nearest = next(r for r, s in enumerate(shards) if want[0] in set(s.owned.tolist()))
+    owner_of_nearest = next(r for r, s in enumerate(shards) if np.isin(want[0], s.owned))
     order = [owner_of_nearest] + [r for r in range(len(shards)) if r != owner_of_nearest]
     for r in order:
-        if np.isin(want, shards[r].build).all():
+        if np.isin(want, shards[r].complete).all():
             return r, True
     return owner_of_nearest, False

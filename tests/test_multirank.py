@@ -118,14 +118,24 @@ def test_shard_neighbourhoods_and_query_routing():
             full, _ = oracle.nearest(qn, qn[g], 6, skip=int(g))
             loc, _ = oracle.nearest(sub, sub[l], 6, skip=int(l))
             assert np.array_equal(full, s.build[loc]), g
+    # a complete rotation's 6 nearest all lie in the build set
+    for s in shards:
+        for g in s.complete[::5]:
+            full, _ = oracle.nearest(qn, qn[g], 6, skip=int(g))
+            assert np.isin(full, s.build).all(), g
     poses = synth.random_quaternions(8, 200)
-    exact = 0
-    for p in poses:
-        r, ok = S.route(q, shards, p, k=4)
-        want, _ = oracle.nearest(qn, p / np.linalg.norm(p), 4)
-        if ok:
-            assert np.isin(want, shards[r].build).all()
-        exact += ok
-    assert exact >= 180
+    counts = {}
+    for halo in (8, 16):
+        sh = S.shard(q, 3, halo=halo)
+        exact = 0
+        for p in poses:
+            r, ok = S.route(q, sh, p, k=4)
+            want, _ = oracle.nearest(qn, p / np.linalg.norm(p), 4)
+            if ok:
+                assert np.isin(want, sh[r].complete).all()
+            exact += ok
+        counts[halo] = exact
+    # a deeper halo makes more rotations complete and more routes exact
+    assert counts[8] >= 120 and counts[16] >= 170 and counts[16] > counts[8]
     with pytest.raises(ValueError):
         S.shard(q, 2, halo=5)
