@@ -307,10 +307,21 @@ struct PassB {
 // Spectral-mode source of pass B: the table interpolated at os R^T k~, times
 // (-1)^(kx+ky+kz) to move the phase back to the box corner; 0 on Nyquist
 // planes.
+// One rotated frequency read off the table: issue its four gathers (re and
+// im at two slices) and keep the weights; spec_combine interpolates.  Split
+// so that a thread keeps several samples' gathers in flight.
+struct SpecTap {
+    float4 ra, ia, rb, ib;
+    float wx, wy, wz;
+    bool zero, neg;
+};
 template <int N>
-__device__ __forceinline__ float2 spectral_sample(const SpecSrc &src, const float *R, int kx, int ky, int kz) {
+__device__ __forceinline__ SpecTap spec_issue(const SpecSrc &src, const float *R, int kx, int ky, int kz) {
     const int h = N / 2;
-    if (kx == h || ky == h || kz == h) return make_float2(0.f, 0.f);
+    SpecTap t;
+    t.zero = kx == h || ky == h || kz == h;
+    t.neg = ((kx + ky + kz) & 1) != 0;
+    if (t.zero) return t;
     const float ks[3] = {(float)(src.os * (kx < h ? kx : kx - N)), (float)(src.os * (ky < h ? ky : ky - N)),
                          (float)(src.os * (kz < h ? kz : kz - N))};
     int i[3];
@@ -325,25 +336,34 @@ __device__ __forceinline__ float2 spectral_sample(const SpecSrc &src, const floa
     // y = (x0+1, y0+1); the wrapped neighbours come from the padding
     const float u0 = (float)((z0 % sc) * (np + 1) + x0) + 1.0f, v0 = (float)((z0 / sc) * (np + 1) + y0) + 1.0f;
     const float u1 = (float)((z1 % sc) * (np + 1) + x0) + 1.0f, v1 = (float)((z1 / sc) * (np + 1) + y0) + 1.0f;
-    const float4 ra = tex2Dgather<float4>(src.tex, u0, v0, 0), ia = tex2Dgather<float4>(src.tex, u0, v0, 1);
-    const float4 rb = tex2Dgather<float4>(src.tex, u1, v1, 0), ib = tex2Dgather<float4>(src.tex, u1, v1, 1);
-    const float2 a00 = make_float2(ra.w, ia.w), a01 = make_float2(ra.z, ia.z);
-    const float2 a10 = make_float2(ra.x, ia.x), a11 = make_float2(ra.y, ia.y);
-    const float2 b00 = make_float2(rb.w, ib.w), b01 = make_float2(rb.z, ib.z);
-    const float2 b10 = make_float2(rb.x, ib.x), b11 = make_float2(rb.y, ib.y);
-    const float wx = w[0], wy = w[1], wz = w[2];
-    auto lerp2 = [](float2 a, float2 b, float t) { return make_float2(fmaf(t, b.x - a.x, a.x), fmaf(t, b.y - a.y, a.y)); };
-    const float2 v = lerp2(lerp2(lerp2(a00, a01, wx), lerp2(a10, a11, wx), wy),
-                           lerp2(lerp2(b00, b01, wx), lerp2(b10, b11, wx), wy), wz);
-    return ((kx + ky + kz) & 1) ? make_float2(-v.x, -v.y) : v;
+    t.ra = tex2Dgather<float4>(src.tex, u0, v0, 0);
+    t.ia = tex2Dgather<float4>(src.tex, u0, v0, 1);
+    t.rb = tex2Dgather<float4>(src.tex, u1, v1, 0);
+    t.ib = tex2Dgather<float4>(src.tex, u1, v1, 1);
+    t.wx = w[0];
+    t.wy = w[1];
+    t.wz = w[2];
+    return t;
 }
+__device__ __forceinline__ float2 spec_combine(const SpecTap &t) {
+    if (t.zero) return make_float2(0.f, 0.f);
+    const float2 a00 = make_float2(t.ra.w, t.ia.w), a01 = make_float2(t.ra.z, t.ia.z);
+    const float2 a10 = make_float2(t.ra.x, t.ia.x), a11 = make_float2(t.ra.y, t.ia.y);
+    const float2 b00 = make_float2(t.rb.w, t.ib.w), b01 = make_float2(t.rb.z, t.ib.z);
+    const float2 b10 = make_float2(t.rb.x, t.ib.x), b11 = make_float2(t.rb.y, t.ib.y);
+    auto lerp2 = [](float2 a, float2 b, float u) { return make_float2(fmaf(u, b.x - a.x, a.x), fmaf(u, b.y - a.y, a.y)); };
+    const float2 v = lerp2(lerp2(lerp2(a00, a01, t.wx), lerp2(a10, a11, t.wx), t.wy),
+                           lerp2(lerp2(b00, b01, t.wx), lerp2(b10, b11, t.wx), t.wy), t.wz);
+    return t.neg ? make_float2(-v.x, -v.y) : v;
+}
+constexpr int kSpecInFlight = 4;  // samples whose gathers a thread issues together
 
 // MODE 0: full middle pass (product, gradient, inverse z) -> Y1 = S', Y2 = Gz'
 // MODE 1: forward only, spectrum * scale -> spec[kz*][ky*][kx*]  (stationary part)
 // MODE 2: as MODE 0 with the rotated spectrum interpolated from a table
 //         instead of transformed from resampled planes
 template <int N, int MODE>
-__global__ void __launch_bounds__(PassB<N>::NT, PassB<N>::MINB) passB_kernel(const float2 *__restrict__ X1,
+__global__ void __launch_bounds__(PassB<N>::NT, MODE == 2 ? 2 : PassB<N>::MINB) passB_kernel(const float2 *__restrict__ X1,
                                                                               const float2 *__restrict__ R1hat,
                                                                               float2 *__restrict__ Y1,
                                                                               float2 *__restrict__ Y2, float scale,
@@ -383,14 +403,21 @@ __global__ void __launch_bounds__(PassB<N>::NT, PassB<N>::MINB) passB_kernel(con
 #pragma unroll
         for (int k = 0; k < 9; ++k) R[k] = __ldg(rot9 + 9 * r + k);
         const int ky = slot_freq<N>(kys);
+        static_assert(R2 % kSpecInFlight == 0, "whole groups of samples");
 #pragma unroll
         for (int j = 0; j < KPT; ++j) {
             const int k1 = g + R2 * j;
             if (k1 < R1) {
 #pragma unroll
-                for (int k2 = 0; k2 < R2; ++k2)
-                    X[j][k2] = active ? spectral_sample<N>(spec, R, kx, ky, slot_freq<N>(R2 * k1 + k2))
-                                      : make_float2(0.f, 0.f);
+                for (int k0 = 0; k0 < R2; k0 += kSpecInFlight) {
+                    SpecTap tap[kSpecInFlight];
+#pragma unroll
+                    for (int u = 0; u < kSpecInFlight; ++u)
+                        if (active) tap[u] = spec_issue<N>(spec, R, kx, ky, slot_freq<N>(R2 * k1 + k0 + u));
+#pragma unroll
+                    for (int u = 0; u < kSpecInFlight; ++u)
+                        X[j][k0 + u] = active ? spec_combine(tap[u]) : make_float2(0.f, 0.f);
+                }
             }
         }
         __syncthreads();  // twiddles in place
