@@ -126,7 +126,6 @@ struct hf_fieldset {
     // two internal streams so that one chunk's texture-bound resample can
     // overlap the other's shared-memory-bound passes
     float2 *scratch[2] = {};     // 3 x chunk x N*N*(N/2+1): X1, Y1, Y2
-    float *planes[2] = {};       // unused: the resample runs inside the first FFT pass
     cudaStream_t lane[2] = {};
     cudaEvent_t fork = nullptr, join[2] = {};
     float *d_rot9 = nullptr;     // R x 9
@@ -865,10 +864,9 @@ static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags,
     const size_t data_b = (size_t)R * nf * n3 * sizeof(float);
     const size_t scr_b = (fields_spectra(fs->pencil) + ((flags & HF_TA) ? 3 : 0)) * (size_t)fs->chunk *
                          hf::half_spec_elems(n) * sizeof(float2);
-    const size_t planes_b = 0;  // the resample is fused into pass A / the x forward
     fs->stage_bytes = (size_t)R * (9 * sizeof(float) + 4 * sizeof(double) + 6 * sizeof(int) + 18 * sizeof(float) +
                                    18 * sizeof(double));
-    fs->bytes = data_b + fs->lanes * (scr_b + planes_b) + fs->stage_bytes;
+    fs->bytes = data_b + fs->lanes * scr_b + fs->stage_bytes;
     if (!charge(ctx, fs->bytes)) {
         const size_t b = fs->bytes;
         delete fs;
@@ -914,10 +912,9 @@ static size_t fieldset_bytes(int n, int R, unsigned flags, int chunk, int lanes)
     const size_t n3 = (size_t)n * n * n;
     const size_t scr_b = (fields_spectra(hf::pencil_n(n)) + ((flags & HF_TA) ? 3 : 0)) * (size_t)chunk *
                          hf::half_spec_elems(n) * sizeof(float2);
-    const size_t planes_b = 0;
     const size_t stage = (size_t)R * (9 * sizeof(float) + 4 * sizeof(double) + 6 * sizeof(int) + 18 * sizeof(float) +
                                       18 * sizeof(double));
-    return (size_t)R * nf * n3 * sizeof(float) + lanes * (scr_b + planes_b) + stage;
+    return (size_t)R * nf * n3 * sizeof(float) + lanes * scr_b + stage;
 }
 
 extern "C" size_t hf_fieldset_bytes(int n, int R, unsigned flags) {
@@ -939,7 +936,6 @@ extern "C" void hf_fieldset_release(hf_fieldset *fs) {
     dfree(fs->data);
     for (int l = 0; l < 2; ++l) {
         dfree(fs->scratch[l]);
-        dfree(fs->planes[l]);
         if (fs->lane[l]) cudaStreamDestroy(fs->lane[l]);
         if (fs->join[l]) cudaEventDestroy(fs->join[l]);
     }
@@ -1101,7 +1097,7 @@ hf_status hf_set_launch(hf_ctx *ctx, const hf_part *s1, const hf_part *s2, hf_fi
             out.Tz = base + (size_t)fs->slot[6] * n3;
         }
         s = run_fields(ctx, n, fs->pencil, fs->prec, s1, s2, d_rot9 + (size_t)9 * r0, cnt, fs->scratch[l], scr_rot,
-                       fs->planes[l], out, fs->lanes == 2 ? fs->lane[l] : st, fs->spectral);
+                       nullptr, out, fs->lanes == 2 ? fs->lane[l] : st, fs->spectral);
         if (s != HF_OK) return s;
     }
     for (int l = 0; l < 2 && fs->lanes == 2; ++l) {
