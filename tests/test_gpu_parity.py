@@ -254,6 +254,22 @@ def test_errors_are_status_codes(hf, ctx, small_set):
     with pytest.raises(hf.HFError) as e:
         small.fieldset(64, 4)
     assert e.value.status == B.HF_EBUDGET
+    # degenerate inputs: a zero or non-finite quaternion is refused before any
+    # launch; an empty query batch is a no-op
+    fs = small_set["fs"]
+    p1, p2 = small_set["p"]
+    bad = small_set["q"].copy()
+    bad[3] = 0.0
+    with pytest.raises(hf.HFError) as e:
+        fs.compute(p1, p2, bad)
+    assert e.value.status == B.HF_EINVAL
+    bad[3] = [np.nan, 0, 0, 1]
+    with pytest.raises(hf.HFError) as e:
+        fs.compute(p1, p2, bad)
+    assert e.value.status == B.HF_EINVAL
+    empty = torch.zeros((0, 7), device="cuda")
+    assert fs.query_batch(empty).shape == (0, 7)
+    torch.cuda.synchronize()
 
 
 def test_rank_deficient_rotation_set_flags_nan(hf, ctx, small_set):
