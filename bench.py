@@ -814,6 +814,41 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_spectral_only(args, local_rank):
+    """Spectral (os 1) field builds of the c2 workload alone: a small, self-
+    contained run of the frequency-domain route for kernel profiles."""
+    import torch
+    import paper_1711_05017_b300 as hf
+    from paper_1711_05017_b300 import build
+
+    build.build()
+    torch.cuda.set_device(local_rank)
+    n, R = args.n, args.spectral_only
+    dev = torch.device("cuda", local_rank)
+    s1, s2 = synth.c2_pair(0)
+    ctx = hf.Context(local_rank)
+    f32 = dict(dtype=torch.float32, device=dev)
+    g1 = ctx.density_build(n, torch.as_tensor(s1.pts, **f32), torch.as_tensor(s1.sigma, **f32))
+    g2 = ctx.density_build(n, torch.as_tensor(s2.pts, **f32), torch.as_tensor(s2.sigma, **f32))
+    p1, p2 = ctx.part(g1, hf.HF_STATIONARY), ctx.part(g2, hf.HF_MOVING)
+    p2.spectral(1)
+    q = synth.random_quaternions(0, R).astype(np.float32)
+    fs = ctx.fieldset(n, R, hf.HF_E | hf.HF_F | hf.HF_SPECTRAL)
+    for _ in range(args.warmup):
+        fs.compute(p1, p2, q)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        fs.compute(p1, p2, q)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    print(json.dumps({"metric": "spectral (os 1) E+F field build", "value": round(R / (ms / 1e3), 1),
+                      "unit": "rotations/s", "rotations": R, "grid": n, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_build": round(ms, 3)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -836,12 +871,18 @@ def main():
                     help="measure the later rows: frequency-domain modes, analytic torque, mesh descriptor (0 = skip)")
     ap.add_argument("--serve-seconds", type=float, default=20.0,
                     help="length of the 16-session serving run (0 = skip)")
+    ap.add_argument("--spectral-only", type=int, default=0, metavar="R",
+                    help="profiling aid: only R-rotation spectral (os 1) field builds of the c2 workload, "
+                         "warm-up plus --steps timed, one JSON line")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.spectral_only > 0:
+        run_spectral_only(args, local_rank)
         return
     if world > 1:
         import torch
