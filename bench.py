@@ -619,8 +619,8 @@ def run_next_rows(args, local_rank):
     s1, s2 = synth.c2_pair(0)
     ctx = hf.Context(local_rank)
     cu = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=dev)  # noqa: E731
-    p1 = ctx.part(ctx.density_build(n, cu(s1.pts), cu(s1.sigma)), hf.HF_STATIONARY)
-    p2 = ctx.part(ctx.density_build(n, cu(s2.pts), cu(s2.sigma)), hf.HF_MOVING)
+    g1, g2 = ctx.density_build(n, cu(s1.pts), cu(s1.sigma)), ctx.density_build(n, cu(s2.pts), cu(s2.sigma))
+    p1, p2 = ctx.part(g1, hf.HF_STATIONARY), ctx.part(g2, hf.HF_MOVING)
     ctx.autotune(n, args.tune_cache)
     q = rank_rotations(0, R)
     stream = torch.cuda.current_stream()
@@ -696,7 +696,70 @@ def run_next_rows(args, local_rank):
                                    "seconds_both_parts": round(time.perf_counter() - t0, 3),
                                    "sigma": 0.5, "gamma_max": 0.05, "max_depth": 8}
     return {"workload": f"c2 peg-in-hole skeletons, 128^3, {R} rotations, E+F+T; procedural peg/hole meshes",
-            "field_build": out, "lowpass_single_pose": lp, "mesh_descriptor": mesh}
+            "field_build": out, "lowpass_single_pose": lp, "mesh_descriptor": mesh,
+            "cufft_comparison": run_cufft_comparison(ctx, p1, p2, g1, g2, n, dev)}
+
+
+def _quat_to_rot(q):
+    w, x, y, z = np.asarray(q, dtype=np.float64) / np.linalg.norm(q)
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def run_cufft_comparison(ctx, p1, p2, g1, g2, n, dev, R=32, reps=5):
+    """The E+F build of R rotations as cuFFT (torch.fft) would do it, timed
+    beside this library's: resampled moving grids (made by the library's
+    resample kernel, outside the timed region) -> batched R2C -> conjugate
+    product with the stationary spectrum and the i pi k~ multipliers -> four
+    C2R inverses.  A timing reference only: no cuFFT is on the library's path.
+    The fields of both routes are compared first."""
+    import torch
+    import paper_1711_05017_b300 as hf
+    q = rank_rotations(0, R)
+    fs = ctx.fieldset(n, R, hf.HF_E | hf.HF_F)
+    fs.compute(p1, p2, q)
+    grids = torch.stack([hf.resample(g2, _quat_to_rot(qq).astype(np.float32)) for qq in q])
+    h3 = (2.0 / n) ** 3
+    k = torch.fft.fftfreq(n, d=1.0 / n, device=dev)
+    k[n // 2] = 0.0  # Nyquist multiplier 0
+    kx = torch.fft.rfftfreq(n, d=1.0 / n, device=dev)
+    kx[-1] = 0.0
+    mult = [np.pi * kx.view(1, 1, 1, -1), np.pi * k.view(1, 1, -1, 1), np.pi * k.view(1, -1, 1, 1)]
+    r1h = torch.fft.rfftn(g1)
+
+    def cufft_build():
+        S = r1h * torch.fft.rfftn(grids, dim=(1, 2, 3)).conj()
+        E = torch.fft.irfftn(S, s=(n, n, n), dim=(1, 2, 3)) * h3
+        F = [torch.fft.irfftn(S * (1j * m), s=(n, n, n), dim=(1, 2, 3)) * (-h3) for m in mult]
+        return E, F
+
+    E, F = cufft_build()
+    dev_max = []
+    for r in (0, R - 1):
+        for f, a in enumerate([E[r], *[Fd[r] for Fd in F]]):
+            b = fs.get(r, f)
+            dev_max.append(round(float((a - b).abs().max() / b.abs().max()), 8))
+    del E, F
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_cufft = timed(cufft_build)
+    ms_ours = timed(lambda: fs.compute(p1, p2, q))
+    return {"rotations": R, "grid": n, "cufft_ms_per_build": round(ms_cufft, 3),
+            "cufft_rot_per_s": round(R / (ms_cufft / 1e3), 1), "ours_ms_per_build": round(ms_ours, 3),
+            "ours_rot_per_s": round(R / (ms_ours / 1e3), 1), "speedup": round(ms_cufft / ms_ours, 2),
+            "cufft_scope": "R2C + product + 4 C2R (resample excluded); ours: the whole E+F build",
+            "max_abs_dev_over_max": dev_max}
 
 
 # ------------------------------------------------------- serving workload
