@@ -38,6 +38,9 @@ N_ROT = 1024
 N_QUERY = 1024
 
 
+NOMINAL_HBM_GBS = 7700.0  # B300 HBM3e, NVIDIA's figure (context beside the measured copy peak)
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -253,6 +256,7 @@ def run_ours(args, rank, world, local_rank):
         achieved = alg.get(dom, 0) / (prof[dom][1] / prof[dom][0] * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
                 "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
+                "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
                 "traffic": traffic.get(dom), "alg_bytes_per_launch": alg.get(dom, 0)}
     launches = sum(v[0] for v in prof.values())
 
