@@ -585,26 +585,60 @@ struct PassC {
     static constexpr size_t smem = sizeof(float2) * ((size_t)N * PW + (size_t)RB * TP + N);
 };
 
-// Frequency k of the full x row, built from the half spectrum: k <= N/2
-// reads slot(k) as is, k > N/2 reads slot(N-k) conjugated (Hermitian
-// symmetry); for the (E, Fx) row the value is also scaled by 1 + pi kx~ (kx~
-// signed, Nyquist 0).  With k = k1 + R1 k2 and k2 unrolled, most of this folds
-// to constants.
+// Frequency k of the full x row, built from the half spectrum: k < N/2 reads
+// xslot(k) as is, k > N/2 reads xslot(N-k) conjugated (Hermitian symmetry),
+// k = N/2 reads the Nyquist slot; for the (E, Fx) row the value is also
+// scaled by 1 + pi kx~ (kx~ = k, or k - N above N/2; 1 at the Nyquist
+// frequency).
 struct XEntry {
     int slot;
     float cs;    // +1, or -1 where the value is conjugated
     float mult;  // 1 + pi kx~
 };
-template <int N>
-__device__ __forceinline__ XEntry x_entry(int k) {
-    const bool neg = 2 * k > N;
-    const int m = neg ? N - k : k;
-    XEntry e;
-    e.slot = xslot<N>(m);
-    e.cs = neg ? -1.0f : 1.0f;
-    e.mult = (2 * k == N) ? 1.0f : 1.0f + kPi * (float)(neg ? k - N : k);
-    return e;
-}
+
+// The entries for all k = k1 + R1 K2 of one stage-1 item (k1 fixed,
+// 0 <= k1 < R1; K2 compile-time).  With HALF = N/2 = a b (slot of m in a half
+// row: b (m % a) + m / a) and a dividing R1, the slot is a per-item base plus a
+// constant: t1 + (R1/a) K2 below N/2, t2 + (R1/a)(R2-K2-1) above it, where t1
+// and t2 are the slots of k1 and of R1 - k1; only the Nyquist frequency
+// (K2 = R2/2, k1 = 0) is special.  kx~ is formed as k1 + R1 K2 (- N) in exact
+// small-integer float arithmetic.
+template <int N, int R1>
+struct XItem {
+    static constexpr int R2 = N / R1, HALF = N / 2, A = Fact<N / 2>::R1, B = Fact<N / 2>::R2;
+    static_assert(R1 % A == 0, "the half row's first digit divides the x pass's");
+    int t1, t2;
+    float k1f;
+    bool nyq;  // k1 = 0: K2 = R2/2 is the Nyquist frequency
+    __device__ __forceinline__ explicit XItem(int k1) {
+        const int j = R1 - k1;
+        t1 = B * (k1 % A) + k1 / A;
+        t2 = B * (j % A) + j / A;
+        k1f = (float)k1;
+        nyq = k1 == 0;
+    }
+    template <int K2>
+    __device__ __forceinline__ XEntry entry() const {
+        XEntry e;
+        if constexpr (2 * K2 < R2) {
+            e.slot = t1 + (R1 / A) * K2;
+            e.cs = 1.0f;
+            e.mult = 1.0f + kPi * (k1f + (float)(R1 * K2));
+        } else {
+            e.slot = t2 + (R1 / A) * (R2 - K2 - 1);
+            e.cs = -1.0f;
+            e.mult = 1.0f + kPi * (k1f + (float)(R1 * K2 - N));
+            if constexpr (2 * K2 == R2) {
+                if (nyq) {
+                    e.slot = HALF;
+                    e.cs = 1.0f;
+                    e.mult = 1.0f;
+                }
+            }
+        }
+        return e;
+    }
+};
 
 // One complex inverse DFT of length N per row, input built from half-spectrum
 // rows (pitch PW) by Hermitian symmetry; real part -> out0, imaginary -> out1.
@@ -654,9 +688,10 @@ __device__ __forceinline__ void x_pass(const float2 *planeA, const float2 *plane
             const float2 *pa = planeA + (size_t)(y0 + row) * PW + colA;
             const float2 *pb = planeB + (size_t)(y0 + row) * PW + colB;
             float2 v[R2];
-#pragma unroll
-            for (int k2 = 0; k2 < R2; ++k2) {
-                const XEntry e = x_entry<N>(k1 + R1 * k2);
+            const XItem<N, R1> xi(k1);
+            static_for<0, R2>([&](auto kk) {
+                constexpr int k2 = decltype(kk)::value;
+                const XEntry e = xi.template entry<k2>();
                 if constexpr (PAIR == 0) {
                     const float2 a = pa[e.slot];
                     v[k2] = make_float2(e.mult * a.x, (e.mult * e.cs) * a.y);
@@ -664,7 +699,7 @@ __device__ __forceinline__ void x_pass(const float2 *planeA, const float2 *plane
                     const float2 gy = pb[e.slot], gz = pa[e.slot];
                     v[k2] = make_float2(fmaf(e.cs, gz.y, -gy.x), fmaf(-e.cs, gy.y, -gz.x));  // -(gy + i gz)
                 }
-            }
+            });
             RegDFT<R2, +1>::run(v);
             float2 *tr = Tb + row * TP + R2 * k1;
 #pragma unroll
