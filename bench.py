@@ -240,7 +240,7 @@ def run_ours(args, rank, world, local_rank):
     # 32 rotations at 128^3 (profiles/fieldbuild_kernels_c2_128.md), scaled to
     # this launch's rotations: the traffic is per rotation (each reads its own
     # two spectra and writes its own four fields)
-    traffic = {"passC": 1.5800e9 * chunk / 32} if n == 128 and not tune_is_pencil(ctx, n) else {}
+    traffic = {"passC": 1.5809e9 * chunk / 32} if n == 128 and not tune_is_pencil(ctx, n) else {}
     hbm_peak, peak_kind = peaks()
     kernels = {}
     for k, (cnt, tot) in prof.items():
