@@ -20,54 +20,75 @@ namespace hf {
 // point list in chunks, keeps (in point order) the points whose cutoff
 // sphere reaches the tile's box, and every thread adds their Gaussians to
 // its node.  Gather form: deterministic, no atomics.
+//
+// A kept point is stored as its offset from the tile centre, taken at its
+// periodic image nearest that centre; a node's own offset from the centre,
+// (l - 3.5) h per axis, is exact.  When the cutoff radius c and the tile's
+// half-width w satisfy c + w < 1 (half the period), every node within c of
+// the point sees it at that same image, and any other node lies beyond c at
+// any image, so the node-point distance is one subtraction per axis.  A
+// chunk holding a point with a cutoff too wide for that takes the minimum
+// image per node instead.
 constexpr int kSplatTile = 8;
 constexpr int kSplatThreads = kSplatTile * kSplatTile * kSplatTile;
 
 __device__ __forceinline__ float min_image(float d) { return d - 2.0f * rintf(0.5f * d); }
 
+// 2^t for t <= 0 down to -30 (the arguments here): the PTX base-2
+// exponential, relative error within 2^-22 (its documented bound)
+__device__ __forceinline__ float exp2_neg(float t) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(t));
+    return r;
+}
+
 template <int N>
-__global__ void __launch_bounds__(kSplatThreads) splat_kernel(const float *__restrict__ pts,
+__global__ void __launch_bounds__(kSplatThreads, 3) splat_kernel(const float *__restrict__ pts,
                                                               const float *__restrict__ sigma,
                                                               const float *__restrict__ amp, int P,
                                                               float *__restrict__ grid) {
-    __shared__ float4 cand[kSplatThreads];  // x, y, z, a
-    __shared__ float2 cpar[kSplatThreads];  // cutoff^2, 1/(2 sigma^2)
+    __shared__ float4 cand[kSplatThreads];  // offset from the tile centre (x, y, z), amplitude
+    __shared__ float2 cpar[kSplatThreads];  // cutoff^2, -log2(e) / (2 sigma^2)
     __shared__ int warp_cnt[kSplatThreads / 32];
     constexpr int TPA = N / kSplatTile;  // tiles per axis
+    constexpr float kLog2e = 1.4426950408889634f;
     const int t = blockIdx.x;
     const int tx = t % TPA, ty = (t / TPA) % TPA, tz = t / (TPA * TPA);
     const float h = 2.0f / N;
     const int lx = threadIdx.x % kSplatTile, ly = (threadIdx.x / kSplatTile) % kSplatTile,
               lz = threadIdx.x / (kSplatTile * kSplatTile);
     const int nx = tx * kSplatTile + lx, ny = ty * kSplatTile + ly, nz = tz * kSplatTile + lz;
-    const float px = (float)(nx - N / 2) * h, py = (float)(ny - N / 2) * h, pz = (float)(nz - N / 2) * h;
-    // tile box: centre and half-width per axis
+    // tile box: centre and half-width per axis; node offsets from the centre
     const float half = 0.5f * (kSplatTile - 1) * h;
     const float bx = (float)(tx * kSplatTile - N / 2) * h + half;
     const float by = (float)(ty * kSplatTile - N / 2) * h + half;
     const float bz = (float)(tz * kSplatTile - N / 2) * h + half;
+    const float qx = (float)(2 * lx - (kSplatTile - 1)) * (0.5f * h);
+    const float qy = (float)(2 * ly - (kSplatTile - 1)) * (0.5f * h);
+    const float qz = (float)(2 * lz - (kSplatTile - 1)) * (0.5f * h);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float acc = 0.0f;
     for (int base = 0; base < P; base += kSplatThreads) {
         const int i = base + threadIdx.x;
-        bool keep = false;
+        bool keep = false, wide = false;
         float4 c = make_float4(0, 0, 0, 0);
         float2 cp = make_float2(0, 0);
         if (i < P) {
-            c = make_float4(__ldg(pts + 3 * i), __ldg(pts + 3 * i + 1), __ldg(pts + 3 * i + 2),
-                            amp ? __ldg(amp + i) : 1.0f);
             const float s = __ldg(sigma + i);
             const float cut = 6.0f * s;
+            c = make_float4(min_image(__ldg(pts + 3 * i) - bx), min_image(__ldg(pts + 3 * i + 1) - by),
+                            min_image(__ldg(pts + 3 * i + 2) - bz), amp ? __ldg(amp + i) : 1.0f);
             // distance from the point to the tile box on the torus, per axis
-            const float dx = fmaxf(fabsf(min_image(c.x - bx)) - half, 0.f);
-            const float dy = fmaxf(fabsf(min_image(c.y - by)) - half, 0.f);
-            const float dz = fmaxf(fabsf(min_image(c.z - bz)) - half, 0.f);
+            const float dx = fmaxf(fabsf(c.x) - half, 0.f);
+            const float dy = fmaxf(fabsf(c.y) - half, 0.f);
+            const float dz = fmaxf(fabsf(c.z) - half, 0.f);
             keep = dx * dx + dy * dy + dz * dz <= cut * cut * 1.0001f + 1e-12f;
-            cp = make_float2(36.0f * s * s, 1.0f / (2.0f * s * s));
+            wide = keep && !(cut + half < 0.99f);
+            cp = make_float2(36.0f * s * s, -kLog2e / (2.0f * s * s));
         }
         const unsigned m = __ballot_sync(0xffffffffu, keep);
         if (lane == 0) warp_cnt[warp] = __popc(m);
-        __syncthreads();
+        const bool any_wide = __syncthreads_or(wide);
         int off = 0, total = 0;
         for (int wv = 0; wv < kSplatThreads / 32; ++wv) {
             const int cnt = warp_cnt[wv];
@@ -80,12 +101,24 @@ __global__ void __launch_bounds__(kSplatThreads) splat_kernel(const float *__res
             cpar[pos] = cp;
         }
         __syncthreads();
-        for (int j = 0; j < total; ++j) {
-            const float4 cj = cand[j];
-            const float2 pj = cpar[j];
-            const float dx = min_image(px - cj.x), dy = min_image(py - cj.y), dz = min_image(pz - cj.z);
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            if (r2 <= pj.x) acc = fmaf(cj.w, expf(-r2 * pj.y), acc);
+        if (!any_wide) {
+#pragma unroll 4
+            for (int j = 0; j < total; ++j) {
+                const float4 cj = cand[j];
+                const float2 pj = cpar[j];
+                const float dx = qx - cj.x, dy = qy - cj.y, dz = qz - cj.z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const float g = exp2_neg(r2 * pj.y);
+                acc = fmaf(r2 <= pj.x ? cj.w : 0.0f, g, acc);
+            }
+        } else {
+            for (int j = 0; j < total; ++j) {
+                const float4 cj = cand[j];
+                const float2 pj = cpar[j];
+                const float dx = min_image(qx - cj.x), dy = min_image(qy - cj.y), dz = min_image(qz - cj.z);
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                if (r2 <= pj.x) acc = fmaf(cj.w, exp2_neg(r2 * pj.y), acc);
+            }
         }
         __syncthreads();
     }

@@ -60,6 +60,23 @@ def test_splat_parity(ctx, n, which):
         assert rel_err(got, ref) <= TOL
 
 
+@pytest.mark.parametrize("n", [64, 128])
+def test_splat_wide_and_narrow_cutoffs(ctx, n):
+    """Radii up to 0.17 put some cutoff spheres (6 sigma) within a tile's
+    half-width of half the period, where the nearest image to a tile's
+    centre is not the minimum image of every node: those chunks take the
+    per-node minimum image, the rest the direct offsets."""
+    rng = np.random.default_rng(11)
+    pts = rng.uniform(-1, 1, (1500, 3)).astype(np.float32)
+    # the first 20 points wide: the first chunk of 512 takes the minimum
+    # image, later chunks of the same tile the direct offsets
+    sig = np.where(np.arange(1500) < 20, rng.uniform(0.15, 0.17, 1500),
+                   rng.uniform(0.01, 0.05, 1500)).astype(np.float32)
+    got = host(ctx.density_build(n, cuda(pts), cuda(sig)))
+    ref = oracle.splat(n, pts.astype(np.float64), sig.astype(np.float64))
+    assert rel_err(got, ref) <= TOL
+
+
 def test_splat_signed_amplitudes_and_empty(ctx):
     import torch
     rng = np.random.default_rng(4)
