@@ -162,7 +162,14 @@ hf_status hf_density_mesh(hf_ctx *ctx, int n, const double *d_V, int nv, const i
 /* Make a part from an N^3 density grid (caller-owned, 8-byte aligned, read by
  * the call's stream work).  HF_STATIONARY parts keep (h^3/N^3) F{rho1} (Eq. 7a with the
  * volume element and the inverse's normalisation folded in); HF_MOVING parts
- * keep a copy of the grid.  Errors: HF_EINVAL, HF_EBUDGET, HF_ENOMEM, HF_ECUDA. */
+ * keep a copy of the grid and its support: per axis, the circular range of
+ * nodes outside which every slab is zero (a truncated splat leaves most of
+ * a padded grid at exactly zero).  The rotated resample reads no texels for
+ * samples whose cell lies outside that support on some axis: the cell's
+ * corners are zero, so the sample is +0 either way, bit for bit.  With the
+ * environment variable HF_SUPPORT=0 at creation the part keeps no support
+ * and every sample reads the texture.
+ * Errors: HF_EINVAL, HF_EBUDGET, HF_ENOMEM, HF_ECUDA. */
 hf_status hf_part_create(hf_ctx *ctx, int n, const float *d_grid, int role, hf_part **out,
                          hf_stream stream);
 void hf_part_release(hf_part *part);

@@ -101,6 +101,11 @@ struct hf_part {
     size_t slab_pitch = 0;  // bytes
     cudaArray_t arr = nullptr;
     cudaTextureObject_t tex = 0;
+    // with the texture: the grid's support as cell intervals per axis (6 ints
+    // after kSupportMaskWords words of mask scratch); the texture resample
+    // issues no gathers for samples in cells outside it
+    unsigned *supmask = nullptr;
+    int *box = nullptr;
     // HF_MOVING after hf_part_spectral: the centred spectrum of rho2 padded to
     // table_os * N nodes per axis, full cube, natural order (spectral mode)
     float2 *table = nullptr;
@@ -375,6 +380,7 @@ static hf_status part_fill(hf_part *p, const float *d_grid, cudaStream_t st) {
             CU(hf::run_pad_slices(n, d_grid, p->slab, p->slab_pitch / sizeof(float), st));
             CU(cudaMemcpy2DToArrayAsync(p->arr, 0, 0, p->slab, p->slab_pitch, (size_t)tw * sizeof(float), (size_t)th,
                                         cudaMemcpyDeviceToDevice, st));
+            if (p->box) CU(hf::run_support(n, d_grid, p->supmask, p->box, st));
         }
         return HF_OK;
     }
@@ -387,9 +393,12 @@ static void moving_texture_free(hf_part *p) {
     if (p->tex) cudaDestroyTextureObject(p->tex);
     if (p->arr) cudaFreeArray(p->arr);
     if (p->slab) cudaFree(p->slab);
+    if (p->supmask) cudaFree(p->supmask);
     p->tex = 0;
     p->arr = nullptr;
     p->slab = nullptr;
+    p->supmask = nullptr;
+    p->box = nullptr;
 }
 
 // the gather-capable array + texture object of a moving part; when the device
@@ -419,6 +428,11 @@ static hf_status moving_texture_alloc(hf_part *p) {
         td.normalizedCoords = 0;
         e = cudaCreateTextureObject(&p->tex, &rd, &td, nullptr);
     }
+    const char *sup = getenv("HF_SUPPORT");
+    if (e == cudaSuccess && !(sup && sup[0] == '0')) {
+        e = cudaMalloc(&p->supmask, (hf::kSupportMaskWords + 6) * sizeof(unsigned));
+        if (e == cudaSuccess) p->box = reinterpret_cast<int *>(p->supmask + hf::kSupportMaskWords);
+    }
     if (e != cudaSuccess) {
         moving_texture_free(p);
         return fail(e == cudaErrorMemoryAllocation ? HF_ENOMEM : HF_ECUDA, "hf_part_create: texture: %s",
@@ -437,10 +451,12 @@ extern "C" hf_status hf_part_create(hf_ctx *ctx, int n, const float *d_grid, int
     CU(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n3 = (size_t)n * n * n;
-    // moving: the grid plus the padded slices (pitched buffer and array)
+    // moving: the grid plus the padded slices (pitched buffer and array) and
+    // the support words
     int tw = 0, th = 0;
     hf::tex_layout(n, &tw, &th);
-    const size_t bytes = role == HF_MOVING ? n3 * sizeof(float) + 2 * ((size_t)tw + 32) * th * sizeof(float)
+    const size_t bytes = role == HF_MOVING ? n3 * sizeof(float) + 2 * ((size_t)tw + 32) * th * sizeof(float) +
+                                                 (hf::kSupportMaskWords + 6) * sizeof(unsigned)
                                            : hf::half_spec_elems(n) * sizeof(float2);
     if (!charge(ctx, bytes)) return fail(HF_EBUDGET, "hf_part_create: %zu bytes exceed the budget", bytes);
     hf_part *p = new (std::nothrow) hf_part{ctx, n, role, nullptr, nullptr, bytes};
@@ -985,7 +1001,7 @@ static hf_status run_fields(hf_ctx *c, int n, bool pencil, int prec, const hf_pa
     if (pencil) {
         float2 *A = scratch + 3 * scratch_rot, *B = scratch + 4 * scratch_rot;
         if (s2->tex) {  // resample fused into the x forward through the texture units
-            CU(timed(c, kPassA, st, [&] { return hf::run_xfwd_tex(n, s2->tex, rot9, A, cnt, st); }));
+            CU(timed(c, kPassA, st, [&] { return hf::run_xfwd_tex(n, s2->tex, s2->box, rot9, A, cnt, st); }));
         } else {
             if (!planes) return fail(HF_EUNSUPPORTED, "field-set build: the moving part has no texture");
             CU(timed(c, kResample, st, [&] { return hf::run_resample_chunk(n, s2->grid, rot9, planes, cnt, st); }));
@@ -1006,7 +1022,7 @@ static hf_status run_fields(hf_ctx *c, int n, bool pencil, int prec, const hf_pa
     // the rotated resample runs inside pass A through the texture units;
     // without a texture (its size outside the gather limits) it runs on its own
     if (s2->tex) {
-        CU(timed(c, kPassA, st, [&] { return hf::run_passA_tex(n, s2->tex, rot9, X1, cnt, st); }));
+        CU(timed(c, kPassA, st, [&] { return hf::run_passA_tex(n, s2->tex, s2->box, rot9, X1, cnt, st); }));
     } else {
         if (!planes) return fail(HF_EUNSUPPORTED, "field-set build: the moving part has no texture");
         CU(timed(c, kResample, st, [&] { return hf::run_resample_chunk(n, s2->grid, rot9, planes, cnt, st); }));

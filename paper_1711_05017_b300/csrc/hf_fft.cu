@@ -88,10 +88,37 @@ struct TexSample {
     float ax, ay, az;  // fractional offsets
 };
 
-// Issue the two gathers of one sample; tex_combine waits for them.  Splitting
-// the two lets a thread keep the gathers of several samples in flight.
+// The support of the moving density as cell intervals, per axis a: a cell
+// with lower corner c (corners c and c + 1, mod N) holds a nonzero node only
+// if ((c - lo[a]) mod N) < len[a] (support_box_kernel).  Any other cell's
+// eight corners are zero, and so is every sample in it.
+struct CellBox {
+    int lo[3], len[3];
+};
 template <int N>
-__device__ __forceinline__ TexSample<N> tex_issue(cudaTextureObject_t t, float vx, float vy, float vz) {
+__device__ __forceinline__ CellBox load_cell_box(const int *__restrict__ box) {
+    CellBox b;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        b.lo[a] = box ? __ldg(box + 2 * a) : 0;
+        b.len[a] = box ? __ldg(box + 2 * a + 1) : N;
+    }
+    return b;
+}
+template <int N>
+__device__ __forceinline__ bool cell_in(int c, int lo, int len) {
+    int d = c - lo;
+    d += d < 0 ? N : 0;
+    return d < len;
+}
+
+// Issue the two gathers of one sample; tex_combine waits for them.  Splitting
+// the two lets a thread keep the gathers of several samples in flight.  A
+// sample in a cell outside the support box issues none: its corners are all
+// zero, and the zeros it combines give the +0 the gathers would.
+template <int N>
+__device__ __forceinline__ TexSample<N> tex_issue(cudaTextureObject_t t, float vx, float vy, float vz,
+                                                  const CellBox &box) {
     constexpr int SC = TexLayout<N>::SC;
     TexSample<N> s;
     const float fx = floorf(vx), fy = floorf(vy), fz = floorf(vz);
@@ -100,10 +127,18 @@ __device__ __forceinline__ TexSample<N> tex_issue(cudaTextureObject_t t, float v
     s.az = vz - fz;
     const int x0 = wrapN<N>((int)fx + N / 2), y0 = wrapN<N>((int)fy + N / 2), z0 = wrapN<N>((int)fz + N / 2);
     const int z1 = wrapN<N>(z0 + 1);
-    // slice z sits at texel origin ((z % SC)(N+1), (z / SC)(N+1))
-    // gather components: w = (x0, y0), z = (x0+1, y0), x = (x0, y0+1), y = (x0+1, y0+1)
-    s.a = tex2Dgather<float4>(t, (float)((z0 % SC) * (N + 1) + x0) + 1.0f, (float)((z0 / SC) * (N + 1) + y0) + 1.0f, 0);
-    s.b = tex2Dgather<float4>(t, (float)((z1 % SC) * (N + 1) + x0) + 1.0f, (float)((z1 / SC) * (N + 1) + y0) + 1.0f, 0);
+    const bool need = cell_in<N>(x0, box.lo[0], box.len[0]) & cell_in<N>(y0, box.lo[1], box.len[1]) &
+                      cell_in<N>(z0, box.lo[2], box.len[2]);
+    if (need) {
+        // slice z sits at texel origin ((z % SC)(N+1), (z / SC)(N+1))
+        // gather components: w = (x0, y0), z = (x0+1, y0), x = (x0, y0+1), y = (x0+1, y0+1)
+        s.a = tex2Dgather<float4>(t, (float)((z0 % SC) * (N + 1) + x0) + 1.0f,
+                                  (float)((z0 / SC) * (N + 1) + y0) + 1.0f, 0);
+        s.b = tex2Dgather<float4>(t, (float)((z1 % SC) * (N + 1) + x0) + 1.0f,
+                                  (float)((z1 / SC) * (N + 1) + y0) + 1.0f, 0);
+    } else {
+        s.a = s.b = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     return s;
 }
 
@@ -121,8 +156,10 @@ __device__ __forceinline__ float tex_combine(const TexSample<N> &s) {
 // node(i) gives the node's (x, y, z, row) for i in [0, COUNT).
 constexpr int kTexInFlight = 8;
 template <int N, int NT, int COUNT, class Node>
-__device__ __forceinline__ void tex_resample(cudaTextureObject_t t, const float *R, float *Pf, Node node) {
+__device__ __forceinline__ void tex_resample(cudaTextureObject_t t, const float *R, float *Pf, const int *box,
+                                             Node node) {
     constexpr int H = N / 2 + 1, U = kTexInFlight;
+    const CellBox cb = load_cell_box<N>(box);
 #pragma unroll 1
     for (int i0 = threadIdx.x; i0 < COUNT; i0 += NT * U) {
         TexSample<N> s[U];
@@ -137,7 +174,7 @@ __device__ __forceinline__ void tex_resample(cudaTextureObject_t t, const float 
                 // (R^T c)_a = R[0][a] cx + R[1][a] cy + R[2][a] cz
                 const float ax = fmaf(R[0], cx, R[3] * cy), ay = fmaf(R[1], cx, R[4] * cy),
                             az = fmaf(R[2], cx, R[5] * cy);
-                s[u] = tex_issue<N>(t, fmaf(R[6], cz, ax), fmaf(R[7], cz, ay), fmaf(R[8], cz, az));
+                s[u] = tex_issue<N>(t, fmaf(R[6], cz, ax), fmaf(R[7], cz, ay), fmaf(R[8], cz, az), cb);
                 dst[u] = row * 2 * H + x;
             }
         }
@@ -150,7 +187,7 @@ __device__ __forceinline__ void tex_resample(cudaTextureObject_t t, const float 
 template <int N, int SRC>
 __global__ void __launch_bounds__(PassA<N>::NT, SRC == SRC_TEX ? 2 : PassA<N>::MINB)
     passA_kernel(const float *__restrict__ rho, const float *__restrict__ rot9, float2 *__restrict__ X1,
-                 cudaTextureObject_t tex) {
+                 cudaTextureObject_t tex, const int *__restrict__ box) {
     constexpr int H = PassA<N>::H, HALF = PassA<N>::HALF, NT = PassA<N>::NT;
     extern __shared__ float2 sm[];
     float2 *P = sm;            // [N rows y][H]  (row = N reals = N/2 complex + Nyquist slot)
@@ -176,7 +213,7 @@ __global__ void __launch_bounds__(PassA<N>::NT, SRC == SRC_TEX ? 2 : PassA<N>::M
 #pragma unroll
         for (int k = 0; k < 9; ++k) R[k] = __ldg(rot9 + 9 * r + k);
         if constexpr (SRC == SRC_TEX) {
-            tex_resample<N, NT, N * N>(tex, R, Pf, [z](int i, int &x, int &y, int &zz, int &row) {
+            tex_resample<N, NT, N * N>(tex, R, Pf, box, [z](int i, int &x, int &y, int &zz, int &row) {
                 x = i % N;
                 y = row = i / N;
                 zz = z;
@@ -248,6 +285,68 @@ __global__ void pad_slices_kernel(const float *__restrict__ g, float *__restrict
         const size_t row = (size_t)(z / SC) * (N + 1) + y, col = (size_t)(z % SC) * (N + 1) + x;
         slab[row * pitch_floats + col] = __ldg(g + ((size_t)z * N + wrapN<N>(y)) * N + wrapN<N>(x));
     }
+}
+
+// Support of the moving density, pass 1: one CTA per z-slab, thread x walks
+// column x.  Bit i of masks[8 a + i / 32] is set when the slab normal to axis
+// a (0 = x, 1 = y, 2 = z) at index i holds a nonzero node (masks zeroed
+// before the launch).
+template <int N>
+__global__ void __launch_bounds__(N) support_masks_kernel(const float *__restrict__ g, unsigned *__restrict__ masks) {
+    constexpr int W = (N + 31) / 32;
+    __shared__ unsigned ym[W];
+    const int z = blockIdx.x, x = threadIdx.x, lane = x & 31;
+    if (x < W) ym[x] = 0u;
+    __syncthreads();
+    const float *col = g + (size_t)z * N * N + x;
+    bool nzc = false;
+    for (int y = 0; y < N; ++y) {
+        const bool nz = __ldg(col + (size_t)y * N) != 0.0f;
+        nzc |= nz;
+        if (__any_sync(0xffffffffu, nz) && lane == 0) atomicOr(&ym[y >> 5], 1u << (y & 31));
+    }
+    const unsigned xb = __ballot_sync(0xffffffffu, nzc);
+    if (lane == 0 && xb) atomicOr(&masks[x >> 5], xb);
+    const bool any = __syncthreads_or(nzc);
+    if (x < W && ym[x]) atomicOr(&masks[8 + x], ym[x]);
+    if (x == 0 && any) atomicOr(&masks[16 + (z >> 5)], 1u << (z & 31));
+}
+
+// Pass 2, one thread per axis: the nonzero slabs lie in the circular interval
+// [lo, lo + len) that leaves out the longest circular run of zero slabs.  A
+// cell with lower corner c touches it iff c is in [lo - 1, lo + len), stored
+// as box[2a] = lo - 1 (mod N), box[2a + 1] = min(len + 1, N); an all-zero
+// grid gives len 0 (no cell touches it).
+template <int N>
+__global__ void support_box_kernel(const unsigned *__restrict__ masks, int *__restrict__ box) {
+    const int a = threadIdx.x;
+    if (a >= 3) return;
+    const unsigned *m = masks + 8 * a;
+    auto bit = [m](int i) { return (m[i >> 5] >> (i & 31)) & 1u; };
+    int first = -1;
+    for (int i = 0; i < N && first < 0; ++i)
+        if (bit(i)) first = i;
+    int lo1 = 0, len1 = 0;
+    if (first >= 0) {
+        int best = 0, start = first, run = 0;  // longest zero run, and the set index after it
+        for (int k = 1; k <= N; ++k) {
+            const int i = (first + k) % N;
+            if (bit(i)) {
+                if (run > best) {
+                    best = run;
+                    start = i;
+                }
+                run = 0;
+            } else {
+                ++run;
+            }
+        }
+        const int len = N - best;
+        lo1 = (start - 1 + N) % N;
+        len1 = len + 1 < N ? len + 1 : N;
+    }
+    box[2 * a] = lo1;
+    box[2 * a + 1] = len1;
 }
 
 template <int N>
@@ -946,7 +1045,8 @@ struct Pencil {
 template <int N, bool TEX>
 __global__ void __launch_bounds__(Pencil<N>::NT) xfwd_kernel(const float *__restrict__ planes,
                                                              float2 *__restrict__ Xa, cudaTextureObject_t tex,
-                                                             const float *__restrict__ rot9) {
+                                                             const float *__restrict__ rot9,
+                                                             const int *__restrict__ box) {
     constexpr int H = Pencil<N>::H, HALF = Pencil<N>::HALF, RBX = Pencil<N>::RBX, NT = Pencil<N>::NT;
     extern __shared__ float2 sm[];
     float2 *P = sm;               // [RBX][H]
@@ -959,7 +1059,7 @@ __global__ void __launch_bounds__(Pencil<N>::NT) xfwd_kernel(const float *__rest
 #pragma unroll
         for (int k = 0; k < 9; ++k) R[k] = __ldg(rot9 + 9 * r + k);
         float *Pf = reinterpret_cast<float *>(P);
-        tex_resample<N, NT, RBX * N>(tex, R, Pf, [q0](int i, int &x, int &y, int &z, int &row) {
+        tex_resample<N, NT, RBX * N>(tex, R, Pf, box, [q0](int i, int &x, int &y, int &z, int &row) {
             row = i / N;
             x = i % N;
             const int q = (int)q0 + row;
@@ -1188,13 +1288,21 @@ static cudaError_t set_smem_attrs() {
 
 template <int N, int SRC>
 static cudaError_t launch_passA(const float *rho, const float *rot9, float2 *X1, int nrot, cudaStream_t st,
-                               cudaTextureObject_t tex = 0) {
-    passA_kernel<N, SRC><<<dim3(N, nrot), PassA<N>::NT, PassA<N>::smem, st>>>(rho, rot9, X1, tex);
+                               cudaTextureObject_t tex = 0, const int *box = nullptr) {
+    passA_kernel<N, SRC><<<dim3(N, nrot), PassA<N>::NT, PassA<N>::smem, st>>>(rho, rot9, X1, tex, box);
     return cudaGetLastError();
 }
 template <int N>
 static cudaError_t launch_pad_slices(const float *g, float *slab, size_t pitch_floats, cudaStream_t st) {
     pad_slices_kernel<N><<<4 * 148, 256, 0, st>>>(g, slab, pitch_floats);
+    return cudaGetLastError();
+}
+template <int N>
+static cudaError_t launch_support(const float *g, unsigned *masks, int *box, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(masks, 0, kSupportMaskWords * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    support_masks_kernel<N><<<N, N, 0, st>>>(g, masks);
+    support_box_kernel<N><<<1, 32, 0, st>>>(masks, box);
     return cudaGetLastError();
 }
 template <int N>
@@ -1249,13 +1357,14 @@ static cudaError_t launch_moment_fields(const float *Fx, const float *Fy, const 
 template <int N>
 static cudaError_t launch_xfwd(const float *planes, float2 *Xa, int nrot, cudaStream_t st) {
     xfwd_kernel<N, false><<<dim3(N * N / Pencil<N>::RBX, nrot), Pencil<N>::NT, Pencil<N>::smem_xfwd, st>>>(
-        planes, Xa, 0, nullptr);
+        planes, Xa, 0, nullptr, nullptr);
     return cudaGetLastError();
 }
 template <int N>
-static cudaError_t launch_xfwd_tex(cudaTextureObject_t tex, const float *rot9, float2 *Xa, int nrot, cudaStream_t st) {
+static cudaError_t launch_xfwd_tex(cudaTextureObject_t tex, const int *box, const float *rot9, float2 *Xa, int nrot,
+                                   cudaStream_t st) {
     xfwd_kernel<N, true><<<dim3(N * N / Pencil<N>::RBX, nrot), Pencil<N>::NT, Pencil<N>::smem_xfwd, st>>>(
-        nullptr, Xa, tex, rot9);
+        nullptr, Xa, tex, rot9, box);
     return cudaGetLastError();
 }
 template <int N>
@@ -1317,8 +1426,9 @@ cudaError_t fft_init_attrs(int n) {
 cudaError_t run_xfwd(int n, const float *planes, float2 *Xa, int nrot, cudaStream_t st) {
     HF_DISPATCH_ALL(n, launch_xfwd<NN>(planes, Xa, nrot, st));
 }
-cudaError_t run_xfwd_tex(int n, cudaTextureObject_t tex, const float *rot9, float2 *Xa, int nrot, cudaStream_t st) {
-    HF_DISPATCH_ALL(n, launch_xfwd_tex<NN>(tex, rot9, Xa, nrot, st));
+cudaError_t run_xfwd_tex(int n, cudaTextureObject_t tex, const int *box, const float *rot9, float2 *Xa, int nrot,
+                         cudaStream_t st) {
+    HF_DISPATCH_ALL(n, launch_xfwd_tex<NN>(tex, box, rot9, Xa, nrot, st));
 }
 cudaError_t run_yfwd(int n, const float2 *Xa, float2 *X1, int nrot, cudaStream_t st) {
     HF_DISPATCH_ALL(n, launch_yfwd<NN>(Xa, X1, nrot, st));
@@ -1334,14 +1444,18 @@ cudaError_t run_xinv(int n, const float2 *ZS, const float2 *ZGy, const float2 *Z
 cudaError_t run_passA(int n, const float *rho, const float *rot9, float2 *X1, int nrot, cudaStream_t st) {
     HF_DISPATCH(n, (launch_passA<NN, SRC_RAW>(rho, rot9, X1, nrot, st)));
 }
-cudaError_t run_passA_tex(int n, cudaTextureObject_t tex, const float *rot9, float2 *X1, int nrot, cudaStream_t st) {
-    HF_DISPATCH(n, (launch_passA<NN, SRC_TEX>(nullptr, rot9, X1, nrot, st, tex)));
+cudaError_t run_passA_tex(int n, cudaTextureObject_t tex, const int *box, const float *rot9, float2 *X1, int nrot,
+                          cudaStream_t st) {
+    HF_DISPATCH(n, (launch_passA<NN, SRC_TEX>(nullptr, rot9, X1, nrot, st, tex, box)));
 }
 cudaError_t run_passA_planes(int n, const float *planes, float2 *X1, int nrot, cudaStream_t st) {
     HF_DISPATCH(n, (launch_passA<NN, SRC_PLANES>(planes, nullptr, X1, nrot, st)));
 }
 cudaError_t run_resample_chunk(int n, const float *rho, const float *rot9, float *out, int nrot, cudaStream_t st) {
     HF_DISPATCH_ALL(n, launch_resample_chunk<NN>(rho, rot9, out, nrot, st));
+}
+cudaError_t run_support(int n, const float *g, unsigned *masks, int *box, cudaStream_t st) {
+    HF_DISPATCH_ALL(n, launch_support<NN>(g, masks, box, st));
 }
 cudaError_t run_pad_slices(int n, const float *g, float *slab, size_t pitch_floats, cudaStream_t st) {
     HF_DISPATCH_ALL(n, launch_pad_slices<NN>(g, slab, pitch_floats, st));

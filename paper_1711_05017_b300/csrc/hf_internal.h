@@ -53,11 +53,19 @@ cudaError_t fft_init_attrs(int n);
 cudaError_t run_passA(int n, const float *rho, const float *rot9, float2 *X1, int nrot, cudaStream_t st);
 // pass A from planes already in memory: plane z of rotation r at planes + (r N + z) N^2
 cudaError_t run_passA_planes(int n, const float *planes, float2 *X1, int nrot, cudaStream_t st);
-cudaError_t run_passA_tex(int n, cudaTextureObject_t tex, const float *rot9, float2 *X1, int nrot, cudaStream_t st);
+// box: the moving density's support as cell intervals (run_support), or null
+// for the whole torus
+cudaError_t run_passA_tex(int n, cudaTextureObject_t tex, const int *box, const float *rot9, float2 *X1, int nrot,
+                          cudaStream_t st);
 // rotated resample of a chunk: out[r] = rho(R_r^T x_n), r < nrot
 cudaError_t run_resample_chunk(int n, const float *rho, const float *rot9, float *out, int nrot, cudaStream_t st);
 // the same through 2x2 texture gathers of the stacked padded slices (see hf_fft.cu)
 cudaError_t run_pad_slices(int n, const float *g, float *slab, size_t pitch_floats, cudaStream_t st);
+// the support of an N^3 grid g: per axis the circular interval of cells that
+// hold a nonzero node, as box[2a] = first cell, box[2a + 1] = cell count
+// (a = 0, 1, 2 for x, y, z); masks is kSupportMaskWords words of scratch
+constexpr int kSupportMaskWords = 24;
+cudaError_t run_support(int n, const float *g, unsigned *masks, int *box, cudaStream_t st);
 cudaError_t run_passB(int n, const float2 *X1, const float2 *R1hat, float2 *Y1, float2 *Y2, int nrot,
                       cudaStream_t st);
 cudaError_t run_passB_forward(int n, const float2 *X1, float2 *spec, float scale, cudaStream_t st);
@@ -107,7 +115,8 @@ cudaError_t run_lowpass(int n, const float2 *spec1, const float2 *table, int os,
 // then pass B, then Y1/Y2 -> Z_S, Z_Gy, Z_Gz (inverse y) -> fields (inverse x)
 cudaError_t run_xfwd(int n, const float *planes, float2 *Xa, int nrot, cudaStream_t st);
 // the x forward of the pencil pipeline sampling the moving texture directly
-cudaError_t run_xfwd_tex(int n, cudaTextureObject_t tex, const float *rot9, float2 *Xa, int nrot, cudaStream_t st);
+cudaError_t run_xfwd_tex(int n, cudaTextureObject_t tex, const int *box, const float *rot9, float2 *Xa, int nrot,
+                         cudaStream_t st);
 cudaError_t run_yfwd(int n, const float2 *Xa, float2 *X1, int nrot, cudaStream_t st);
 // hf_tc.cu: the pencil pipeline's y stages as split hi/lo DFT-matrix GEMMs on
 // the tensor cores (N = 256 only); same inputs and outputs as run_yfwd /
