@@ -107,9 +107,13 @@ __device__ __forceinline__ CellBox load_cell_box(const int *__restrict__ box) {
 }
 template <int N>
 __device__ __forceinline__ bool cell_in(int c, int lo, int len) {
-    int d = c - lo;
-    d += d < 0 ? N : 0;
-    return d < len;
+    if constexpr ((N & (N - 1)) == 0) {
+        return ((c - lo) & (N - 1)) < len;
+    } else {
+        int d = c - lo;
+        d += d < 0 ? N : 0;
+        return d < len;
+    }
 }
 
 // Issue the two gathers of one sample; tex_combine waits for them.  Splitting
@@ -151,36 +155,68 @@ __device__ __forceinline__ float tex_combine(const TexSample<N> &s) {
     return fmaf(s.az, c1 - c0, c0);
 }
 
-// Resample COUNT consecutive nodes of the rotated grid into reals at
-// Pf[row * 2H + x] through the texture, U samples per thread in flight.
-// node(i) gives the node's (x, y, z, row) for i in [0, COUNT).
+// Resample ROWS rows of the rotated grid, nodes (x, y0 + row, z) for x in
+// [0, N), into reals at Pf[row * 2H + x] through the texture, U samples per
+// thread in flight.  Sample i is node (i % N, i / N).  With COUNTERS (NT a
+// multiple of N) a thread keeps one x and steps its row by NT / N, so its
+// node coordinates are float counters (exact small integers) instead of
+// per-sample index arithmetic; the sample positions are the same either way.
+// The counters take more registers: pass A has them to spare, the pencil x
+// forward (four CTAs per SM at 64 registers) does not.
 constexpr int kTexInFlight = 8;
-template <int N, int NT, int COUNT, class Node>
-__device__ __forceinline__ void tex_resample(cudaTextureObject_t t, const float *R, float *Pf, const int *box,
-                                             Node node) {
-    constexpr int H = N / 2 + 1, U = kTexInFlight;
+template <int N>
+__device__ __forceinline__ float3 rotated_node(const float *R, float cx, float cy, float cz) {
+    // (R^T c)_a = R[0][a] cx + R[1][a] cy + R[2][a] cz
+    const float ax = fmaf(R[0], cx, R[3] * cy), ay = fmaf(R[1], cx, R[4] * cy), az = fmaf(R[2], cx, R[5] * cy);
+    return make_float3(fmaf(R[6], cz, ax), fmaf(R[7], cz, ay), fmaf(R[8], cz, az));
+}
+template <int N, int NT, int ROWS, bool COUNTERS, int U = kTexInFlight>
+__device__ __forceinline__ void tex_resample(cudaTextureObject_t t, const float *R, float *Pf, const int *box, int y0,
+                                             int z) {
+    constexpr int H = N / 2 + 1, COUNT = ROWS * N;
     const CellBox cb = load_cell_box<N>(box);
+    const float cz = (float)(z - N / 2);
+    if constexpr (COUNTERS && NT % N == 0) {
+        constexpr int RS = NT / N;  // rows per step of a thread
+        const int x = threadIdx.x % N, row0 = threadIdx.x / N;
+        const float cx = (float)(x - N / 2);
+        float cy = (float)(y0 + row0 - N / 2);
+        float *dst = Pf + row0 * 2 * H + x;
 #pragma unroll 1
-    for (int i0 = threadIdx.x; i0 < COUNT; i0 += NT * U) {
-        TexSample<N> s[U];
-        int dst[U];
+        for (int i0 = threadIdx.x; i0 < COUNT; i0 += NT * U) {
+            TexSample<N> s[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int i = i0 + u * NT;
-            if (COUNT % (NT * U) == 0 || i < COUNT) {
-                int x, y, z, row;
-                node(i, x, y, z, row);
-                const float cx = (float)(x - N / 2), cy = (float)(y - N / 2), cz = (float)(z - N / 2);
-                // (R^T c)_a = R[0][a] cx + R[1][a] cy + R[2][a] cz
-                const float ax = fmaf(R[0], cx, R[3] * cy), ay = fmaf(R[1], cx, R[4] * cy),
-                            az = fmaf(R[2], cx, R[5] * cy);
-                s[u] = tex_issue<N>(t, fmaf(R[6], cz, ax), fmaf(R[7], cz, ay), fmaf(R[8], cz, az), cb);
-                dst[u] = row * 2 * H + x;
+            for (int u = 0; u < U; ++u) {
+                if (COUNT % (NT * U) == 0 || i0 + u * NT < COUNT) {
+                    const float3 v = rotated_node<N>(R, cx, cy + (float)(u * RS), cz);
+                    s[u] = tex_issue<N>(t, v.x, v.y, v.z, cb);
+                }
             }
-        }
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (COUNT % (NT * U) == 0 || i0 + u * NT < COUNT) Pf[dst[u]] = tex_combine<N>(s[u]);
+            for (int u = 0; u < U; ++u)
+                if (COUNT % (NT * U) == 0 || i0 + u * NT < COUNT) dst[u * RS * 2 * H] = tex_combine<N>(s[u]);
+            cy += (float)(U * RS);
+            dst += U * RS * 2 * H;
+        }
+    } else {
+#pragma unroll 1
+        for (int i0 = threadIdx.x; i0 < COUNT; i0 += NT * U) {
+            TexSample<N> s[U];
+            int dst[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = i0 + u * NT;
+                if (COUNT % (NT * U) == 0 || i < COUNT) {
+                    const int x = i % N, row = i / N;
+                    const float3 v = rotated_node<N>(R, (float)(x - N / 2), (float)(y0 + row - N / 2), cz);
+                    s[u] = tex_issue<N>(t, v.x, v.y, v.z, cb);
+                    dst[u] = row * 2 * H + x;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (COUNT % (NT * U) == 0 || i0 + u * NT < COUNT) Pf[dst[u]] = tex_combine<N>(s[u]);
+        }
     }
 }
 
@@ -213,11 +249,7 @@ __global__ void __launch_bounds__(PassA<N>::NT, SRC == SRC_TEX ? 2 : PassA<N>::M
 #pragma unroll
         for (int k = 0; k < 9; ++k) R[k] = __ldg(rot9 + 9 * r + k);
         if constexpr (SRC == SRC_TEX) {
-            tex_resample<N, NT, N * N>(tex, R, Pf, box, [z](int i, int &x, int &y, int &zz, int &row) {
-                x = i % N;
-                y = row = i / N;
-                zz = z;
-            });
+            tex_resample<N, NT, N, true>(tex, R, Pf, box, 0, z);
         } else {
             const float cz = (float)(z - N / 2);
             const float bx = R[6] * cz, by = R[7] * cz, bz = R[8] * cz;
@@ -1029,6 +1061,9 @@ struct Pencil {
     static constexpr int CY = 16;                       // kx columns per CTA, y stages
     static constexpr int NCY = (H + CY - 1) / CY;
     static constexpr int NT = 256;
+    // texture x forward: 4 samples in flight per thread and 4 CTAs per SM (64
+    // registers) beat 8 in flight at 2 CTAs per SM; 96 would spill at 64
+    static constexpr int XU = 4, XMINB = (N & (N - 1)) == 0 ? 4 : 1;
     static constexpr int PW = 3 * H;                    // x-inverse row pitch: S | Gy | Gz (odd)
     static constexpr int TP = N + 1;
     static constexpr size_t smem_xfwd = sizeof(float2) * ((size_t)RBX * H + N + HALF);
@@ -1043,7 +1078,7 @@ struct Pencil {
 // node positions (the resample fused in, the same samples bit for bit as
 // pass A's) instead of read from resampled planes.
 template <int N, bool TEX>
-__global__ void __launch_bounds__(Pencil<N>::NT) xfwd_kernel(const float *__restrict__ planes,
+__global__ void __launch_bounds__(Pencil<N>::NT, Pencil<N>::XMINB) xfwd_kernel(const float *__restrict__ planes,
                                                              float2 *__restrict__ Xa, cudaTextureObject_t tex,
                                                              const float *__restrict__ rot9,
                                                              const int *__restrict__ box) {
@@ -1059,13 +1094,8 @@ __global__ void __launch_bounds__(Pencil<N>::NT) xfwd_kernel(const float *__rest
 #pragma unroll
         for (int k = 0; k < 9; ++k) R[k] = __ldg(rot9 + 9 * r + k);
         float *Pf = reinterpret_cast<float *>(P);
-        tex_resample<N, NT, RBX * N>(tex, R, Pf, box, [q0](int i, int &x, int &y, int &z, int &row) {
-            row = i / N;
-            x = i % N;
-            const int q = (int)q0 + row;
-            y = q % N;
-            z = q / N;
-        });
+        static_assert(N % RBX == 0, "a CTA's rows lie in one z-slice");
+        tex_resample<N, NT, RBX, false, Pencil<N>::XU>(tex, R, Pf, box, (int)(q0 % N), (int)(q0 / N));
         load_tw<N>(twN);
         load_tw<HALF>(twH);
     } else {
