@@ -275,9 +275,9 @@ __global__ void __launch_bounds__(PassA<N>::NT, SRC == SRC_TEX ? 2 : PassA<N>::M
         const int y = i % N, k = i / N;
         float2 *row = P + y * H;
         if (k == 0) {
+            // X[0] and X[N/2] are real: packed as X[0] + i X[N/2] for the y transform
             const float2 z0 = row[0];
-            row[0] = make_float2(z0.x + z0.y, 0.f);
-            row[HALF] = make_float2(z0.x - z0.y, 0.f);
+            row[0] = make_float2(z0.x + z0.y, z0.x - z0.y);
         } else if (4 * k == N) {
             const int s = perm_slot<HALF>(k);
             row[s] = cconj(row[s]);
@@ -292,8 +292,26 @@ __global__ void __launch_bounds__(PassA<N>::NT, SRC == SRC_TEX ? 2 : PassA<N>::M
         }
     }
     __syncthreads();
-    // y: H columns of length N
-    fft_lines<N, -1, H, H, 1, NT>(P, twN);
+    // y: the N/2 columns 0..N/2-1 of length N, column 0 carrying the real
+    // columns kx = 0 and kx = N/2 as one complex sequence
+    fft_lines<N, -1, HALF, H, 1, NT>(P, twN);
+    // separate them: with Z = Y0 + i YN (Y0, YN transforms of real columns),
+    // Y0[k] = (Z[k] + conj Z[-k]) / 2 and YN[k] = -i (Z[k] - conj Z[-k]) / 2;
+    // thread k < N/2 + 1 owns the slots of k and N - k
+    if (threadIdx.x <= HALF) {
+        const int k = threadIdx.x;
+        const int sa = perm_slot<N>(k), sb = perm_slot<N>((N - k) % N);
+        const float2 a = P[sa * H], b = P[sb * H];
+        const float2 y0 = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+        const float2 yn = make_float2(0.5f * (a.y + b.y), -0.5f * (a.x - b.x));
+        P[sa * H] = y0;
+        P[sa * H + HALF] = yn;
+        if (sb != sa) {
+            P[sb * H] = cconj(y0);
+            P[sb * H + HALF] = cconj(yn);
+        }
+    }
+    __syncthreads();
     float2 *dst = X1 + ((size_t)r * N + z) * N * H;
     for (int i = threadIdx.x; i < N * H; i += NT) dst[i] = P[i];
 }
