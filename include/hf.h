@@ -215,7 +215,10 @@ hf_status hf_fieldset_create(hf_ctx *ctx, int n, int R, unsigned flags, hf_field
  * part s1 (Eqs. 3, 5, 6a per rotation; the torque by least squares over the
  * 6 nearest rotations of the set).  R must equal the set's size; with HF_T,
  * R >= 7.  Rotations whose neighbourhood is rank deficient get NaN torque and
- * the call returns HF_EINVAL after enqueueing everything else.
+ * the call returns HF_EINVAL after enqueueing everything else.  The host
+ * preparation of the rotation set (matrices, neighbours, least-squares
+ * operators) is kept in `fs` and reused by the next call whose h_quat holds
+ * the same bytes; the uploads happen on every call.
  * Errors: HF_EINVAL, HF_ECUDA. */
 hf_status hf_fieldset_compute(hf_ctx *ctx, const hf_part *s1, const hf_part *s2,
                               const float *h_quat, int R, hf_fieldset *fs, hf_stream stream);

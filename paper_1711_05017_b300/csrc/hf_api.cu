@@ -151,6 +151,14 @@ struct hf_fieldset {
     void *h_stage = nullptr;     // staging for the per-call uploads (pinned unless mem_stream)
     size_t stage_bytes = 0;
     cudaEvent_t stage_done = nullptr;  // the last uploads from h_stage have been consumed
+    // the host preparation of the last rotation set (matrices, neighbours,
+    // least-squares operators), reused while the quaternions are the same
+    // bytes: a field set is typically recomputed over one rotation set as
+    // the parts change
+    std::vector<float> prep_quat, prep_rot9, prep_P32;
+    std::vector<double> prep_q64, prep_P64;
+    std::vector<int> prep_nbr;
+    int prep_bad = -1;
 };
 
 static bool charge(hf_ctx *c, size_t b) {
@@ -1137,11 +1145,19 @@ extern "C" hf_status hf_fieldset_compute(hf_ctx *ctx, const hf_part *s1, const h
     if (s != HF_OK) return s;
     CU(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
-    std::vector<float> rot9, P32;
-    std::vector<double> q64, P64;
-    std::vector<int> nbr;
-    const int bad = hf_prepare_rotations(h_quat, R, (fs->flags & HF_T) != 0, rot9, q64, nbr, P32, P64);
-    if (bad < 0) return fail(HF_EINVAL, "hf_fieldset_compute: a quaternion is zero or not finite");
+    const size_t qbytes = (size_t)R * 4 * sizeof(float);
+    if (fs->prep_bad < 0 || fs->prep_quat.size() != (size_t)R * 4 || memcmp(fs->prep_quat.data(), h_quat, qbytes)) {
+        fs->prep_bad = -1;
+        const int b = hf_prepare_rotations(h_quat, R, (fs->flags & HF_T) != 0, fs->prep_rot9, fs->prep_q64,
+                                           fs->prep_nbr, fs->prep_P32, fs->prep_P64);
+        if (b < 0) return fail(HF_EINVAL, "hf_fieldset_compute: a quaternion is zero or not finite");
+        fs->prep_quat.assign(h_quat, h_quat + (size_t)R * 4);
+        fs->prep_bad = b;
+    }
+    const int bad = fs->prep_bad;
+    const std::vector<float> &rot9 = fs->prep_rot9, &P32 = fs->prep_P32;
+    const std::vector<double> &q64 = fs->prep_q64, &P64 = fs->prep_P64;
+    const std::vector<int> &nbr = fs->prep_nbr;
     // stage through the set's staging buffer once the previous call's uploads are done
     CU(cudaEventSynchronize(fs->stage_done));
     float *s_rot = (float *)fs->h_stage;
