@@ -158,9 +158,11 @@ __device__ __forceinline__ float tex_combine(const TexSample<N> &s) {
 // Resample ROWS rows of the rotated grid, nodes (x, y0 + row, z) for x in
 // [0, N), into reals at Pf[row * 2H + x] through the texture, U samples per
 // thread in flight.  Sample i is node (i % N, i / N).  With COUNTERS (NT a
-// multiple of N) a thread keeps one x and steps its row by NT / N, so its
-// node coordinates are float counters (exact small integers) instead of
-// per-sample index arithmetic; the sample positions are the same either way.
+// multiple of N) a thread keeps one x and steps its row by NT / N: its node
+// coordinates are float counters (exact small integers) instead of per-sample
+// index arithmetic, and the x and z terms of R^T c are formed once, so a
+// sample's position is one fma per axis (the same point, rounded in another
+// order).
 // The counters take more registers: pass A has them to spare, the pencil x
 // forward (four CTAs per SM at 64 registers) does not.
 constexpr int kTexInFlight = 8;
@@ -182,14 +184,16 @@ __device__ __forceinline__ void tex_resample(cudaTextureObject_t t, const float 
         const float cx = (float)(x - N / 2);
         float cy = (float)(y0 + row0 - N / 2);
         float *dst = Pf + row0 * 2 * H + x;
+        // the thread's fixed x and z terms of R^T c, so that a sample adds R[1][a] cy in one fma
+        const float bx = fmaf(R[6], cz, R[0] * cx), by = fmaf(R[7], cz, R[1] * cx), bz = fmaf(R[8], cz, R[2] * cx);
 #pragma unroll 1
         for (int i0 = threadIdx.x; i0 < COUNT; i0 += NT * U) {
             TexSample<N> s[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 if (COUNT % (NT * U) == 0 || i0 + u * NT < COUNT) {
-                    const float3 v = rotated_node<N>(R, cx, cy + (float)(u * RS), cz);
-                    s[u] = tex_issue<N>(t, v.x, v.y, v.z, cb);
+                    const float cyu = cy + (float)(u * RS);
+                    s[u] = tex_issue<N>(t, fmaf(R[3], cyu, bx), fmaf(R[4], cyu, by), fmaf(R[5], cyu, bz), cb);
                 }
             }
 #pragma unroll
