@@ -452,7 +452,7 @@ hf_status hf_torque(hf_ctx *ctx, int n, int R, const float *h_quat, const float 
  * plug-in whose host application owns all device memory; a runtime that
  * forbids allocation after start-up.  It computes what hf_fields computes
  * (energy and force of the rotated moving density against the stationary
- * one, Eqs. 3, 5, 6a) directly from the two caller-owned N^3 grids d_rho1
+ * one, for one rotation) directly from the two caller-owned N^3 grids d_rho1
  * (stationary) and d_rho2 (moving) into the caller-owned N^3 outputs (all
  * four required), and allocates nothing: its intermediates live in one
  * static device array of HF_NOALLOC_MAX_N-sized buffers (about 4.3 MB) that
@@ -460,9 +460,13 @@ hf_status hf_torque(hf_ctx *ctx, int n, int R, const float *h_quat, const float 
  *   - N must be 32 or 64 (N > HF_NOALLOC_MAX_N: HF_EINVAL with a message).
  *   - All calls share that array: calls whose GPU work overlaps (other
  *     streams or threads) race and give wrong results; order them.
- *   - The first call on a device resolves the array's address and sets
- *     kernel attributes with that device current; make it before any
- *     stream capture.
+ *   - The first call on a device is its set-up and is NOT allocation-free:
+ *     CUDA loads device code lazily, so that call loads the library's
+ *     kernels and the array onto the device (reserving the array), resolves
+ *     the array's address and sets kernel attributes, with that device
+ *     current.  Make one warm-up call per device at start-up, before the
+ *     time-critical loop and before any stream capture; later calls
+ *     allocate nothing.
  * Errors: HF_EINVAL, HF_ECUDA (message in hf_last_error()). */
 #define HF_NOALLOC_MAX_N 64
 hf_status hf_fields_noalloc(int n, const float *d_rho1, const float *d_rho2, const float h_quat[4],

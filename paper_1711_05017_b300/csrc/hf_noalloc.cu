@@ -8,8 +8,7 @@
 // all device memory may only use the buffers it is handed.  A runtime that
 // forbids dynamic allocation after start-up is in the same position.  Such a
 // caller owns the two density grids and the four output fields; everything
-// the pipeline needs between them lives in one file-scope device array that
-// the library reserves when it is loaded.
+// the pipeline needs between them lives in one file-scope device array.
 //
 // Properties of that array:
 //   * size: 4 half-spectrum buffers of the largest supported grid
@@ -22,9 +21,15 @@
 //   * each call overwrites every element it later reads, so nothing has to
 //     be cleared between calls even though the array keeps the previous
 //     call's contents.
-// The first call on a device looks up the array's device address
-// (cudaGetSymbolAddress) with that device current and sets the kernels'
-// shared-memory limits; make that first call before any stream capture.
+// The first call on a device is the set-up, and it is not allocation-free:
+// with CUDA's default lazy module loading, the device code of this file (the
+// array included) and of the pass kernels is loaded onto the device only
+// when first used, so the first call loads those modules -- reserving the
+// array -- when it looks up the array's device address
+// (cudaGetSymbolAddress) with that device current, and it sets the kernels'
+// shared-memory limits.  Make one warm-up call per device at start-up,
+// before the time-critical loop and before any stream capture; the calls
+// after it allocate nothing.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
