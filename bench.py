@@ -145,9 +145,9 @@ def numpy_fft_sample(r1, r2, quats, count):
     A = np.fft.rfftn(r1)
     for g in grids:
         S = A * np.conj(np.fft.rfftn(g)) * h3
-        np.fft.irfftn(S, s=(n, n, n))
+        np.fft.irfftn(S, s=(n, n, n), axes=(0, 1, 2))
         for m in mult:
-            np.fft.irfftn(S * (1j * m), s=(n, n, n))
+            np.fft.irfftn(S * (1j * m), s=(n, n, n), axes=(0, 1, 2))
     return (time.perf_counter() - t0) / count
 
 
@@ -835,13 +835,12 @@ def run_cufft_comparison(ctx, p1, p2, g1, g2, n, dev, R=32, reps=5):
 
 
 # ------------------------------------------------------- serving workload
-SERVE_RCAP = {64: 512, 128: 96, 256: 12}  # rotations per build, capped so that every session's set plus the builds in flight fit 120 GB
-
-
 def run_serving(args, local_rank):
     """16 sessions (N from {64, 128, 256}), Poisson field-build requests
-    (2/s per session, 64-512 rotations, capped per N), HBM budget 120 GB,
-    a 1 kHz pose-query random walk per session.  Returns the summary dict."""
+    (2/s per session, 64-512 rotations each, E+F+T), HBM budget 120 GB, a
+    1 kHz pose-query random walk per session from native threads.  Requests
+    whose set exceeds a third of the budget are built in rotation chunks
+    admitted as memory frees.  Returns the summary dict."""
     import torch
     import paper_1711_05017_b300 as hf
     dev = torch.device("cuda", local_rank)
@@ -858,13 +857,17 @@ def run_serving(args, local_rank):
         sids.append(srv.open(*p))
     torch.cuda.synchronize()
     flags = hf.HF_E | hf.HF_F | hf.HF_T
-    # warm-up: one build per session so that every session can answer queries
-    first = [srv.submit(sid, synth.random_quaternions(900 + i, min(64, SERVE_RCAP[s.n])), flags)
-             for i, (sid, s) in enumerate(zip(sids, sess))]
+    # warm-up: one 64-rotation build per session so that every session can answer queries
+    first = [srv.submit(sid, synth.random_quaternions(900 + i, 64), flags) for i, sid in enumerate(sids)]
     srv.wait(first, timeout=600)
+    for sid in sids:  # load the query kernels before the timed run (lazy module loading)
+        try:
+            srv.query(sid, [0.0, 0.0, 0.0], [1.0, 0.0, 0.0, 0.0])
+        except hf.HFError:
+            pass
     st0 = srv.stats()
     # arrivals merged over sessions
-    events = sorted((t, i, int(min(r, SERVE_RCAP[sess[i].n])), int(qs))
+    events = sorted((t, i, int(r), int(qs))
                     for i, s in enumerate(sess) for t, r, qs in zip(s.arrivals, s.n_rot, s.quat_seeds))
     steps = int(args.serve_seconds * 1000)
     poses = np.stack([np.concatenate([synth.translation_walk(3000 + i, steps),
@@ -877,43 +880,76 @@ def run_serving(args, local_rank):
 
     th = [threading.Thread(target=driver, daemon=True)]
     srv.query_latencies()  # drop the warm-up's
+    srv.trace(0)
+    srv.trace(1)
     t_start = time.perf_counter()
     for t in th:
         t.start()
-    rids = []
+    rids, rej = [], 0
     for t_ev, i, R, qs in events:
         wait = t_start + t_ev - time.perf_counter()
         if wait > 0:
             time.sleep(wait)
         try:
-            rids.append(srv.submit(sids[i], synth.random_quaternions(qs, R), flags))
+            rids.append((srv.submit(sids[i], synth.random_quaternions(qs, R), flags), sess[i].n, R))
         except hf.HFError:
-            pass
+            rej += 1
     for t in th:
         t.join()
     elapsed = time.perf_counter() - t_start
     st1 = srv.stats()
     lib_lat = srv.query_latencies()
-    res = srv.wait(rids, timeout=900)
+    slow_q, slow_c = srv.trace(0), srv.trace(1)
+    res = srv.wait([r[0] for r in rids], timeout=900)
     build_lat = [v[1] for v in res.values() if v[0] == "done"]
+    chunked = [srv.request_chunks(r, R)[0] for r, _, R in rids if res[r][0] == "done"]
     st2 = srv.stats()
     answered, not_ready, late = drive["res"]
     lat = lib_lat if lib_lat.size else np.array([np.nan])
+
+    def pct(a, p):
+        return round(float(np.percentile(a, p)), 1)
+
+    # the slowest queries, with what the scheduler was doing when they ran
+    worst = []
+    for row in slow_q[np.argsort(-slow_q[:, 1])[:5]] if len(slow_q) else []:
+        t0q, us = row[0], row[1]
+        over = [{"kind": ("create", "compute", "release")[int(c[2])], "start_ms": round(c[0], 2),
+                 "us": round(c[1], 1)} for c in slow_c if c[0] <= t0q + us / 1e3 and c[0] + c[1] / 1e3 >= t0q]
+        worst.append({"start_ms": round(t0q, 2), "us": round(us, 1), "mutex_us": round(row[2], 1),
+                      "lane_wait_us": round(row[3], 1), "launch_sync_us": round(row[4], 1),
+                      "session_n": sess[int(row[5])].n, "overlapping_scheduler_calls": over[:4]})
+    per_n = {}
+    for sid, s in zip(sids, sess):
+        a, nr = srv.session_counts(sid)
+        d = per_n.setdefault(str(s.n), {"sessions": 0, "answered": 0, "not_ready": 0})
+        d["sessions"] += 1
+        d["answered"] += a
+        d["not_ready"] += nr
     out = {
         "sessions": len(sids), "grid_sizes": sorted(set(s.n for s in sess)), "seconds": round(elapsed, 2),
-        "budget_gb": 120, "query_us": {"p50": round(float(np.percentile(lat, 50)), 1),
-                                       "p99": round(float(np.percentile(lat, 99)), 1),
-                                       "max": round(float(np.max(lat)), 1), "n": int(lat.size),
-                                       "answered": int(answered), "not_ready": int(not_ready),
-                                       "started_late": int(late), "rate_hz_per_session": 1000,
-                                       "budget_us": 1000, "measured": "inside hf_server_query (entry to return)"},
+        "queries_by_grid": per_n,
+        "budget_gb": 120, "chunk_limit_gb": round(st2["chunk_bytes"] / (1 << 30), 1),
+        "query_us": {"p50": pct(lat, 50), "p99": pct(lat, 99), "p99.9": pct(lat, 99.9),
+                     "max": round(float(np.max(lat)), 1), "n": int(lat.size),
+                     "over_1ms": int((lat > 1000).sum()),
+                     "answered": int(answered), "not_ready": int(not_ready),
+                     "started_late": int(late), "rate_hz_per_session": 1000,
+                     "budget_us": 1000, "measured": "inside hf_server_query (entry to return)"},
         "builds": {"submitted": int(st2["submitted"] - st0["submitted"]), "completed": len(build_lat),
+                   "rejected_at_submit": rej,
                    "superseded": int(st2["superseded"] - st0["superseded"]),
-                   "rejected": int(st2["rejected"] - st0["rejected"]), "evicted": int(st2["evicted"] - st0["evicted"]),
-                   "latency_ms_p50": round(float(np.percentile(build_lat, 50)), 1) if build_lat else None,
-                   "latency_ms_p99": round(float(np.percentile(build_lat, 99)), 1) if build_lat else None},
+                   "failed": int(st2["failed"] - st0["failed"]),
+                   "chunked": int(sum(c > 1 for c in chunked)),
+                   "chunks_built": int(st2["chunks_completed"] - st0["chunks_completed"]),
+                   "evicted_chunks": int(st2["evicted"] - st0["evicted"]),
+                   "rotations_per_request": "U-integer[64, 512] at every N",
+                   "latency_ms_p50": pct(build_lat, 50) if build_lat else None,
+                   "latency_ms_p99": pct(build_lat, 99) if build_lat else None},
         "fields_per_s": round((st1["rotations_completed"] - st0["rotations_completed"]) / elapsed, 1),
-        "rotation_cap_per_build": SERVE_RCAP,
+        "slowest_queries": worst,
+        "slow_scheduler_calls": {"n": int(len(slow_c)),
+                                 "max_us": round(float(slow_c[:, 1].max()), 1) if len(slow_c) else 0.0},
     }
     srv.close()
     del parts
@@ -1005,7 +1041,7 @@ def main():
                     help="rotations (0..K-1) of the precision comparison checked against the FP64 oracle (0 = skip)")
     ap.add_argument("--spectral", type=int, default=1,
                     help="measure the later rows: frequency-domain modes, analytic torque, mesh descriptor (0 = skip)")
-    ap.add_argument("--serve-seconds", type=float, default=20.0,
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="length of the 16-session serving run (0 = skip)")
     ap.add_argument("--spectral-only", type=int, default=0, metavar="R",
                     help="profiling aid: only R-rotation spectral (os 1) field builds of the c2 workload, "

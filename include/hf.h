@@ -281,18 +281,49 @@ hf_status hf_lowpass_query_batch(const hf_part *s1, const hf_part *s2, int K, co
 /* Device bytes hf_fieldset_create(n, R, flags) charges (0 if unsupported). */
 size_t hf_fieldset_bytes(int n, int R, unsigned flags);
 
+/* ---- rotation-set chunking (host only) ----
+ * Split R rotations (h_quat R x 4) into chunks whose build sets hold at most
+ * max_build rotations, for rotation sets too large for one field set.  A
+ * chunk owns a compact group on SO(3): the lowest-index unassigned rotation
+ * and its nearest unassigned ones by geodesic angle 2 acos|q_i . q_j|,
+ * added while the build set fits.  With halo != 0 the build set is the owned
+ * rotations plus the 6 nearest of each in the whole set (the least-squares
+ * torque's neighbours, Section 2.4's rotational gradient taken by finite
+ * differences), in ascending global index, so an owned rotation's torque
+ * from its chunk's set equals the whole set's; max_build must be >= 7.
+ * Outputs: h_owner[r] = chunk owning r; chunk c's build set is
+ * h_build[h_offsets[c] .. h_offsets[c+1]) (global indices, ascending);
+ * h_offsets holds R + 1 ints, h_build build_cap ints (7 R always suffice).
+ * Returns the number of chunks, or -1 (bad argument, non-finite quaternion,
+ * R < 7 with halo, capacity).  No GPU is used. */
+int hf_rotation_chunks(const float *h_quat, int R, int max_build, int halo, int *h_owner, int *h_offsets,
+                       int *h_build, int build_cap);
+
 /* ---- serving: sessions, budgeted continuous batching, query lanes ----
  * The restricted-orientation mode of Section 4.2 as a service: sessions keep
- * their parts and their latest field set resident; field-build requests are
+ * their parts and their latest field data resident; field-build requests are
  * queued, admitted first-in first-out while the context's HBM budget allows
  * (hf_ctx_create's hbm_budget_bytes), and run concurrently on several build
- * streams, so work admitted mid-flight overlaps on the device; a completed
- * set replaces the session's previous one atomically.  A session's newer
- * request supersedes its still-queued older one.  When nothing runs and the
- * head request does not fit, the published set of the least recently queried
- * other session is evicted.  Queries read the session's current set on one of
- * a pool of high-priority lanes (own stream and pinned mailbox each), so
- * queries from many threads do not serialise on one lane.
+ * streams, so work admitted mid-flight overlaps on the device.
+ *   - A request whose field set exceeds the server's chunk limit (default:
+ *     a third of the budget; hf_server_set_chunk_bytes) is split by
+ *     hf_rotation_chunks (with torque halos when it asks for HF_T) into
+ *     chunks, each its own field set, admitted one by one as memory frees.
+ *   - A finished chunk is published at once: a request's first chunk
+ *     replaces the session's previous data atomically, later ones fill in.
+ *     A session's newer request supersedes its still-queued chunks.
+ *   - When nothing runs and the head chunk does not fit, a published chunk
+ *     is evicted: the least recently queried of those idle for 20 ms, else
+ *     the largest.
+ *   - Queries run on a pool of high-priority lanes (own stream and pinned
+ *     mailbox each) against the chunk that owns the query's nearest rotation
+ *     (HF_ENOTREADY if that chunk is not resident); they equal the whole
+ *     set's answer when the query's k nearest rotations are owned by it.
+ *   - Queries take no lock that the scheduler or a submitting thread holds
+ *     (the published data is read through atomic shared pointers).
+ *   - The builds allocate from the device's default stream-ordered memory
+ *     pool, whose release threshold the server sets to keep its reserve
+ *     (trimmed when the server is destroyed).
  * Request states: 0 queued, 1 running, 2 done, 3 failed, 4 superseded. */
 typedef struct hf_server hf_server;
 typedef struct {
@@ -300,34 +331,55 @@ typedef struct {
     int64_t rotations_completed;
     int queued, running, sessions;
     size_t reserved_bytes, budget_bytes;
+    int64_t chunks_submitted, chunks_completed;
+    int chunks_resident;
+    size_t chunk_bytes;
 } hf_server_stats;
 
 /* max_inflight: builds on the device at once (1..16); query_lanes: 1..64. */
 hf_status hf_server_create(hf_ctx *ctx, int max_inflight, int query_lanes, hf_server **out);
 void hf_server_destroy(hf_server *srv);
+/* Requests whose field set exceeds `bytes` are split into chunks (0: never). */
+hf_status hf_server_set_chunk_bytes(hf_server *srv, size_t bytes);
 /* A session over a stationary part s1 and a moving part s2 of the same N
  * (both stay owned by the caller and must outlive the session). */
 hf_status hf_server_session_open(hf_server *srv, const hf_part *s1, const hf_part *s2, int *session);
 hf_status hf_server_session_close(hf_server *srv, int session);
 /* Queue a field build for R rotations (h_quat R x 4, copied); HF_EBUDGET if
- * the set could never fit the budget. */
+ * it could never fit (unchunked and above the budget, or a chunk of one
+ * rotation and its halo above the chunk limit). */
 hf_status hf_server_submit(hf_server *srv, int session, const float *h_quat, int R, unsigned flags,
                            int64_t *request);
-/* State of a request and, once done, its latency submit -> published (ms). */
+/* State of a request and, once done (every chunk published), its latency
+ * submit -> published (ms). */
 hf_status hf_server_request_state(hf_server *srv, int64_t request, int *state, double *latency_ms);
-/* Pose query against the session's current field set (HF_ENOTREADY if none). */
+/* Number of chunks of a request and (h_owner, R ints, may be NULL) the chunk
+ * owning each rotation. */
+hf_status hf_server_request_chunks(hf_server *srv, int64_t request, int *chunks, int *h_owner);
+/* Pose query against the session's current field data (HF_ENOTREADY if
+ * none, or if the chunk owning the nearest rotation is not resident). */
 hf_status hf_server_query(hf_server *srv, int session, const float t[3], const float q[4], int k_blend,
                           float out7[7]);
-/* Device pointer of a field of the session's current set (for inspection;
- * valid while that set stays current). */
+/* Device pointer of field `field` of rotation `rot` (index in the request)
+ * of the session's current data (valid while that data stays current). */
 hf_status hf_server_field_ptr(hf_server *srv, int session, int rot, int field, const float **d_ptr);
-/* Copy a field of the session's current set to d_dst (N^3 floats), on `stream`. */
+/* Copy that field to d_dst (N^3 floats), on `stream`. */
 hf_status hf_server_field_get(hf_server *srv, int session, int rot, int field, float *d_dst, hf_stream stream);
 hf_status hf_server_stats_get(hf_server *srv, hf_server_stats *out);
+/* Queries of a session answered and refused as not ready, so far. */
+hf_status hf_server_session_counts(hf_server *srv, int session, int64_t *answered, int64_t *not_ready);
 /* Latencies (microseconds, call entry to return) of the queries answered since
  * the last call, oldest first, at most `max` of them (the newest 2^20 are
  * kept); returns how many were written. */
 int hf_server_query_latencies(hf_server *srv, float *h_out_us, int max);
+/* Diagnostics since the last call, oldest first, 6 doubles per row, at most
+ * `max` rows (the newest 4096 are kept); returns the row count.
+ *   which 0, queries of 500 us or more: start (ms since hf_server_create),
+ *     total us, us spent resolving the session's set (server mutex), waiting
+ *     for a lane, and in the lane's launch + synchronise; the session.
+ *   which 1, scheduler calls of 1 ms or more: start (ms), duration (us),
+ *     kind (0 field-set create, 1 compute launch, 2 release), 0, 0, 0. */
+int hf_server_trace(hf_server *srv, int which, double *h_out, int max);
 /* Replay pose trajectories against sessions from native threads, one per
  * session, one query every 1/rate_hz seconds (a haptic device's servo loop):
  * h_poses is nsess x steps x 7 (t, q); blocks until every trajectory has run.

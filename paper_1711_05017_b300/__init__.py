@@ -15,6 +15,7 @@ from ._binding import (HF_E, HF_F, HF_MOVING, HF_PREC_SPLIT_BF16, HF_PREC_SPLIT_
                        HF_STATIONARY, HF_T, HF_TA, HF_TORQUE_F64, HFError)
 
 __all__ = ["Context", "Part", "FieldSet", "Batch", "Server", "HFError", "lowpass_query", "lowpass_query_batch",
+           "rotation_chunks",
            "resample", "rfft3d", "version"]
 
 
@@ -362,6 +363,22 @@ def rfft3d(x, out=None, stream=None):
     return out
 
 
+def rotation_chunks(quats, max_build, halo=True):
+    """hf_rotation_chunks: split a rotation set into chunks of at most
+    max_build rotations per build set (with the 6-nearest torque halo).
+    Returns (owner (R,), list of build-set index arrays)."""
+    q = np.ascontiguousarray(quats, dtype=np.float32).reshape(-1, 4)
+    R = len(q)
+    owner = np.zeros(R, dtype=np.int32)
+    offs = np.zeros(R + 1, dtype=np.int32)
+    build = np.zeros(7 * R, dtype=np.int32)
+    C = B.lib().hf_rotation_chunks(B.fptr(q), R, int(max_build), 1 if halo else 0, owner.ctypes.data_as(B._ip),
+                                   offs.ctypes.data_as(B._ip), build.ctypes.data_as(B._ip), len(build))
+    if C < 1:
+        raise HFError(B.HF_EINVAL, "hf_rotation_chunks: invalid arguments")
+    return owner, [build[offs[c]:offs[c + 1]].copy() for c in range(C)]
+
+
 class Server:
     """hf_server: sessions, budgeted continuous batching of field builds, and a
     pool of high-priority query lanes (include/hf.h, serving section)."""
@@ -373,6 +390,32 @@ class Server:
         B.check(B.lib().hf_server_create(ctx.handle, int(max_inflight), int(query_lanes), ctypes.byref(h)))
         self.handle, self.ctx = h, ctx
         self._parts = {}  # the parts must outlive their sessions: keep them here
+
+    def set_chunk_bytes(self, nbytes):
+        """Requests whose field set exceeds nbytes are split into rotation
+        chunks (0: never split)."""
+        B.check(B.lib().hf_server_set_chunk_bytes(self.handle, int(nbytes)))
+
+    def request_chunks(self, rid, R):
+        """(number of chunks, owner chunk of each of the request's R rotations)."""
+        c = ctypes.c_int()
+        own = np.zeros(R, dtype=np.int32)
+        B.check(B.lib().hf_server_request_chunks(self.handle, ctypes.c_int64(rid), ctypes.byref(c),
+                                                 own.ctypes.data_as(B._ip)))
+        return c.value, own
+
+    def session_counts(self, sid):
+        """(queries answered, queries refused as not ready) of a session."""
+        a, nr = ctypes.c_int64(), ctypes.c_int64()
+        B.check(B.lib().hf_server_session_counts(self.handle, int(sid), ctypes.byref(a), ctypes.byref(nr)))
+        return a.value, nr.value
+
+    def trace(self, which):
+        """Diagnostic rows since the last read (hf_server_trace): which 0 slow
+        queries, 1 slow scheduler calls; an (n, 6) float64 array."""
+        buf = np.zeros((4096, 6), dtype=np.float64)
+        n = B.lib().hf_server_trace(self.handle, int(which), buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 4096)
+        return buf[:n].copy()
 
     def open(self, s1, s2):
         sid = ctypes.c_int()

@@ -71,6 +71,11 @@ SIGNATURES = {
     "hf_server_field_get": (_i, [_vp, _i, _i, _i, _vp, _vp]),
     "hf_server_stats_get": (_i, [_vp, _vp]),
     "hf_server_query_latencies": (_i, [_vp, _fp, _i]),
+    "hf_server_set_chunk_bytes": (_i, [_vp, _sz]),
+    "hf_server_request_chunks": (_i, [_vp, ctypes.c_int64, _ip, _ip]),
+    "hf_server_session_counts": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "hf_server_trace": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_double), _i]),
+    "hf_rotation_chunks": (_i, [_fp, _i, _i, _i, _ip, _ip, _ip, _i]),
     "hf_server_drive_queries": (_i, [_vp, _i, _ip, _fp, _i, ctypes.c_double, _i, ctypes.POINTER(ctypes.c_int64),
                                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "hf_batch_create": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _ip, _u, _i, ctypes.POINTER(_vp)]),
@@ -98,7 +103,8 @@ class ServerStats(ctypes.Structure):
                 ("rejected", ctypes.c_int64), ("superseded", ctypes.c_int64), ("evicted", ctypes.c_int64),
                 ("queries", ctypes.c_int64), ("rotations_completed", ctypes.c_int64), ("queued", ctypes.c_int),
                 ("running", ctypes.c_int), ("sessions", ctypes.c_int), ("reserved_bytes", ctypes.c_size_t),
-                ("budget_bytes", ctypes.c_size_t)]
+                ("budget_bytes", ctypes.c_size_t), ("chunks_submitted", ctypes.c_int64),
+                ("chunks_completed", ctypes.c_int64), ("chunks_resident", ctypes.c_int), ("chunk_bytes", ctypes.c_size_t)]
 
 _lib = None
 

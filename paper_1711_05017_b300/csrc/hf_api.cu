@@ -817,6 +817,75 @@ int default_chunk(int n) {
 
 }  // namespace
 
+// -------------------------------------------------- rotation-set chunking
+// A rotation set too large for one build is split into chunks that are built
+// (and kept) separately.  Each chunk owns a compact group of rotations: the
+// lowest-index unassigned rotation and its nearest unassigned ones by
+// geodesic angle, added while the chunk's build set still fits max_build.
+// With halo, the build set is the owned rotations plus their 6 nearest in
+// the whole set, in global index order: the least-squares torque of an owned
+// rotation then sees exactly the neighbours (and tie order) it has in the
+// whole set, so its fields equal those of a build of the whole set.
+extern "C" int hf_rotation_chunks(const float *h_quat, int R, int max_build, int halo, int *h_owner, int *h_offsets,
+                                  int *h_build, int build_cap) {
+    if (!h_quat || !h_owner || !h_offsets || !h_build || R < 1 || max_build < (halo ? 7 : 1) || build_cap < R)
+        return -1;
+    std::vector<Quat> Q((size_t)R);
+    for (int r = 0; r < R; ++r) {
+        Q[r] = qnorm(h_quat + 4 * (size_t)r);
+        if (!qfinite(Q[r])) return -1;
+    }
+    std::vector<int> nb;
+    if (halo) {
+        if (R < 7) return -1;  // the torque needs 6 neighbours
+        nb.assign((size_t)R * 6, 0);
+        for (int i = 0; i < R; ++i) nearest6(Q, i, &nb[(size_t)6 * i]);
+    }
+    std::vector<char> assigned((size_t)R, 0), inb((size_t)R, 0);
+    std::vector<std::pair<double, int>> order;
+    int nchunks = 0, used = 0, left = R;
+    h_offsets[0] = 0;
+    while (left > 0) {
+        int seed = 0;
+        while (assigned[seed]) ++seed;
+        order.clear();
+        const Quat &a = Q[seed];
+        for (int j = 0; j < R; ++j)
+            if (!assigned[j]) order.push_back({-fabs(a.w * Q[j].w + a.x * Q[j].x + a.y * Q[j].y + a.z * Q[j].z), j});
+        std::stable_sort(order.begin(), order.end(),
+                         [](const std::pair<double, int> &u, const std::pair<double, int> &v) { return u.first < v.first; });
+        std::vector<int> members;
+        int owned = 0;
+        for (const auto &o : order) {
+            const int j = o.second;
+            int add[7], na = 0;
+            if (!inb[j]) add[na++] = j;
+            if (halo)
+                for (int s = 0; s < 6; ++s) {
+                    const int k = nb[(size_t)6 * j + s];
+                    if (!inb[k]) add[na++] = k;
+                }
+            if (owned > 0 && (int)members.size() + na > max_build) break;
+            for (int t = 0; t < na; ++t) {
+                inb[add[t]] = 1;
+                members.push_back(add[t]);
+            }
+            assigned[j] = 1;
+            h_owner[j] = nchunks;
+            ++owned;
+            --left;
+        }
+        std::sort(members.begin(), members.end());
+        if (used + (int)members.size() > build_cap) return -1;
+        for (int m : members) {
+            h_build[used++] = m;
+            inb[m] = 0;
+        }
+        h_offsets[++nchunks] = used;
+    }
+    return nchunks;
+}
+
 // ---------------------------------------------------------------- fieldsets
 static size_t fieldset_bytes(int n, int R, unsigned flags, int chunk, int lanes);
 // intermediates per rotation: 3 half spectra for the slab passes, 5 for the pencil pipeline

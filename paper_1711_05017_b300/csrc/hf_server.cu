@@ -2,18 +2,34 @@
 // orientation mode of Section 4.2 (fields precomputed per permitted
 // orientation, queried during motion) for many assembly sessions at once.
 //
-//   * sessions own a stationary and a moving part and the field set most
+//   * sessions own a stationary and a moving part and the field data most
 //     recently published for them;
-//   * build requests queue first-in first-out; a scheduler thread admits the
-//     head while its field set fits the context's HBM budget and fewer than
-//     max_inflight builds run, launching it on one of max_inflight build
-//     streams (continuous batching: builds admitted mid-flight overlap on the
-//     device with those already running);
-//   * a completed build replaces the session's set atomically; readers hold
-//     a reference, so a set retired while a query uses it is freed afterwards;
-//   * queries run on a pool of high-priority lanes.
+//   * a build request whose field set exceeds the server's chunk limit is
+//     split into rotation chunks (hf_rotation_chunks: compact groups on
+//     SO(3), each built with its torque neighbours so that the least-squares
+//     torque is the whole set's); each chunk is a job;
+//   * jobs queue first-in first-out; a scheduler thread admits the head while
+//     its field set fits the context's HBM budget and fewer than max_inflight
+//     jobs run, launching it on one of max_inflight build streams
+//     (continuous batching: jobs admitted mid-flight overlap on the device
+//     with those already running, and a large request's chunks are admitted
+//     one by one as memory frees);
+//   * a completed chunk is published at once: the request's first chunk
+//     replaces the session's previous data atomically, later chunks fill in;
+//     readers hold a reference, so data retired while a query uses it is
+//     freed afterwards;
+//   * when the head job does not fit and nothing runs, a published chunk is
+//     evicted: the least recently queried idle one, else the largest;
+//   * queries run on a pool of high-priority lanes, against the chunk that
+//     owns the query's nearest rotation.  The query path takes no lock that
+//     the scheduler or a submitting thread holds: the session table has a
+//     fixed capacity, and the published data and its chunk slots are read
+//     and replaced as atomic shared pointers, so a query never waits for a
+//     thread that the OS has descheduled inside a critical section.
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdarg.h>
+#include <stdint.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -71,30 +87,63 @@ struct Graveyard {
 struct SetHolder {  // a published field set; retired when the last reader lets go
     hf_fieldset *fs;
     Graveyard *gy;
-    SetHolder(hf_fieldset *f, Graveyard *g) : fs(f), gy(g) {}
+    size_t bytes;
+    SetHolder(hf_fieldset *f, Graveyard *g, size_t b) : fs(f), gy(g), bytes(b) {}
     ~SetHolder() { gy->put(fs); }
 };
 
+// A build request.  Fixed after submission except for the state fields,
+// which the server mutex guards.
 struct Request {
     int64_t id = 0;
     int session = -1;
-    std::vector<float> quats;
+    int n = 0;
     int R = 0;
     unsigned flags = 0;
+    std::vector<double> q;           // R x 4, normalised (routing)
+    std::vector<int> owner, local;   // rotation -> chunk, index in that chunk's set
+    int nchunks = 1;
+    // guarded by the server mutex
     int state = RQ_QUEUED;
+    int chunks_done = 0;
     double t_submit = 0, t_done = 0;
-    hf_fieldset *fs = nullptr;
-    cudaEvent_t done = nullptr;
-    int stream = -1;
     std::string error;  // why it failed
 };
 
+struct Job {  // one chunk of a request
+    std::shared_ptr<Request> req;
+    int chunk = 0;
+    std::vector<float> quats;  // the chunk's build set, global index order
+    int R = 0;
+    bool superseded = false;   // server mutex
+    hf_fieldset *fs = nullptr;
+    cudaEvent_t done = nullptr;
+    int stream = -1;
+};
+
+// A session's published field data: one set per chunk of one request.  The
+// request (routing tables) is fixed; the slots are atomic shared pointers
+// and the use times atomics, so readers take no lock.
+struct Published {
+    std::shared_ptr<Request> req;
+    std::unique_ptr<std::shared_ptr<SetHolder>[]> chunk;
+    std::unique_ptr<std::atomic<double>[]> last_use;
+    explicit Published(const std::shared_ptr<Request> &r)
+        : req(r), chunk(new std::shared_ptr<SetHolder>[r->nchunks]), last_use(new std::atomic<double>[r->nchunks]) {
+        for (int c = 0; c < r->nchunks; ++c) last_use[c].store(0.0);
+    }
+    std::shared_ptr<SetHolder> get(int c) const { return std::atomic_load(&chunk[c]); }
+    void set(int c, std::shared_ptr<SetHolder> h) { std::atomic_store(&chunk[c], std::move(h)); }
+};
+
 struct Session {
-    bool open = false;
-    const hf_part *s1 = nullptr, *s2 = nullptr;
+    std::atomic<bool> open{false};
+    const hf_part *s1 = nullptr, *s2 = nullptr;  // fixed once the session is visible
     int n = 0;
-    std::shared_ptr<SetHolder> current;
-    double last_use = 0;
+    std::shared_ptr<Published> current_;         // atomic access only
+    std::atomic<int64_t> answered{0}, not_ready{0};
+    std::shared_ptr<Published> current() const { return std::atomic_load(&current_); }
+    void set_current(std::shared_ptr<Published> p) { std::atomic_store(&current_, std::move(p)); }
 };
 
 struct Lane {
@@ -102,24 +151,47 @@ struct Lane {
     float *h_out = nullptr, *d_out = nullptr;  // mapped pinned answer mailbox and its device alias
 };
 
+// fixed-size ring of diagnostic rows (slow queries, slow scheduler calls)
+struct TraceRing {
+    static constexpr int kRows = 4096, kCols = 6;
+    std::mutex mu;
+    std::vector<double> rows = std::vector<double>((size_t)kRows * kCols);
+    int head = 0, count = 0;
+    void put(const double *v) {
+        std::lock_guard<std::mutex> g(mu);
+        memcpy(&rows[(size_t)head * kCols], v, sizeof(double) * kCols);
+        head = (head + 1) % kRows;
+        count = std::min(count + 1, kRows);
+    }
+};
+
+constexpr size_t kLatRing = 1u << 20;
+constexpr int kMaxSessions = 4096;
+constexpr double kSlowQueryUs = 500.0, kSlowCallUs = 1000.0;
+constexpr double kIdleMs = 20.0;  // a chunk unqueried this long is idle (first to evict)
+
 }  // namespace
 
 struct hf_server {
     hf_ctx *ctx = nullptr;
     int device = 0;
     int max_inflight = 1;
-    std::mutex mu;
+    size_t chunk_bytes = 0;  // 0: never split a request (server mutex)
+    double t0 = 0;           // creation time (trace timestamps)
+    std::mutex mu;           // queue, requests, request states, stats; never taken by queries
     std::condition_variable cv;
-    std::deque<std::shared_ptr<Request>> queue;
-    std::vector<std::shared_ptr<Request>> running;
+    std::deque<std::shared_ptr<Job>> queue;
+    std::vector<std::shared_ptr<Job>> running;  // the scheduler thread's own
     std::unordered_map<int64_t, std::shared_ptr<Request>> requests;
-    std::vector<Session> sessions;
+    std::unique_ptr<Session[]> sessions{new Session[kMaxSessions]};
+    std::atomic<int> nsessions{0};
     std::vector<cudaStream_t> streams;
     std::vector<int> stream_busy;
     int64_t next_id = 1;
     bool stop = false;
     std::thread sched;
     hf_server_stats stats = {};
+    std::atomic<int64_t> queries{0};
     Graveyard graveyard;
     std::mutex lat_mu;
     std::vector<float> lat_us;  // ring of query latencies
@@ -128,82 +200,160 @@ struct hf_server {
     std::vector<Lane> lanes;
     std::vector<int> free_lanes;
     std::condition_variable lane_cv;
+    TraceRing slow_queries, slow_calls;
 };
 
-static void publish(hf_server *s, const std::shared_ptr<Request> &r) {
-    Session &ss = s->sessions[r->session];
-    if (ss.open) ss.current = std::make_shared<SetHolder>(r->fs, &s->graveyard);
-    else s->graveyard.put(r->fs);
-    r->fs = nullptr;
+static Session *session_at(hf_server *s, int session) {
+    if (session < 0 || session >= s->nsessions.load(std::memory_order_acquire)) return nullptr;
+    Session *ss = &s->sessions[session];
+    return ss->open.load() ? ss : nullptr;
 }
 
-// evict the published set of the least recently used other session
-static bool evict_one(hf_server *s, int keep) {
-    int best = -1;
-    for (int i = 0; i < (int)s->sessions.size(); ++i) {
-        const Session &ss = s->sessions[i];
-        if (i == keep || !ss.current) continue;
-        if (best < 0 || ss.last_use < s->sessions[best].last_use) best = i;
+static void trace_call(hf_server *s, int kind, double t_start, double t_end) {
+    const double us = (t_end - t_start) * 1000.0;
+    if (us < kSlowCallUs) return;
+    const double row[TraceRing::kCols] = {t_start - s->t0, us, (double)kind, 0, 0, 0};
+    s->slow_calls.put(row);
+}
+
+// publish a finished chunk (server mutex held); false if it is stale (its
+// request is older than the data the session already shows)
+static bool publish(hf_server *s, const std::shared_ptr<Job> &j) {
+    Session &ss = s->sessions[j->req->session];
+    std::shared_ptr<Published> cur = ss.current();
+    if (!ss.open.load() || (cur && cur->req->id > j->req->id)) {
+        s->graveyard.put(j->fs);
+        j->fs = nullptr;
+        return false;
     }
-    if (best < 0) return false;
-    s->sessions[best].current.reset();
+    if (!cur || cur->req->id != j->req->id) {
+        cur = std::make_shared<Published>(j->req);
+        cur->last_use[j->chunk].store(now_ms());
+        cur->set(j->chunk, std::make_shared<SetHolder>(j->fs, &s->graveyard,
+                                                       hf_fieldset_bytes(j->req->n, j->R, j->req->flags)));
+        ss.set_current(cur);  // the previous data is retired once its readers let go
+    } else {
+        cur->last_use[j->chunk].store(now_ms());
+        cur->set(j->chunk, std::make_shared<SetHolder>(j->fs, &s->graveyard,
+                                                       hf_fieldset_bytes(j->req->n, j->R, j->req->flags)));
+    }
+    j->fs = nullptr;
+    return true;
+}
+
+// evict one published chunk (server mutex held): the least recently queried
+// idle one; if every resident chunk was queried within kIdleMs, the largest
+// (the fewest sessions lose their data per byte freed)
+static bool evict_one(hf_server *s) {
+    const double now = now_ms();
+    Published *bp = nullptr;
+    int bc = -1;
+    bool b_idle = false;
+    double bt = 0;
+    size_t bb = 0;
+    const int ns = s->nsessions.load();
+    for (int i = 0; i < ns; ++i) {
+        std::shared_ptr<Published> cur = s->sessions[i].current();
+        if (!cur) continue;
+        for (int c = 0; c < cur->req->nchunks; ++c) {
+            std::shared_ptr<SetHolder> h = cur->get(c);
+            if (!h) continue;
+            const double t = cur->last_use[c].load();
+            const bool idle = now - t > kIdleMs;
+            bool better;
+            if (!bp) better = true;
+            else if (idle != b_idle) better = idle;
+            else if (idle) better = t < bt;
+            else better = h->bytes > bb || (h->bytes == bb && t < bt);
+            if (better) {
+                bp = cur.get();
+                bc = c;
+                b_idle = idle;
+                bt = t;
+                bb = h->bytes;
+            }
+        }
+    }
+    if (!bp) return false;
+    bp->set(bc, nullptr);
     s->stats.evicted++;
     return true;
 }
 
 static void free_retired(hf_server *s) {
-    for (hf_fieldset *fs : s->graveyard.take()) hf_fieldset_release(fs);
+    for (hf_fieldset *fs : s->graveyard.take()) {
+        const double a = now_ms();
+        hf_fieldset_release(fs);
+        trace_call(s, 2, a, now_ms());
+    }
 }
 
-// Scheduler: the server mutex guards only the queues and session table;
-// allocation, the host set-up and the launches of a build, and every free,
-// happen outside it, so queries (which take the mutex briefly) never wait
-// for them.
+// server mutex held
+static void finish_job(hf_server *s, const std::shared_ptr<Job> &j, bool ok) {
+    Request &r = *j->req;
+    if (!ok) {
+        if (r.state != RQ_SUPERSEDED) r.state = RQ_FAILED;
+        s->stats.failed++;
+        return;
+    }
+    s->stats.chunks_completed++;
+    int owned = 0;
+    for (int i = 0; i < r.R; ++i) owned += r.owner[i] == j->chunk;
+    s->stats.rotations_completed += owned;
+    if (++r.chunks_done == r.nchunks && r.state != RQ_FAILED && r.state != RQ_SUPERSEDED) {
+        r.state = RQ_DONE;
+        r.t_done = now_ms();
+        s->stats.completed++;
+    }
+}
+
+// Scheduler: the server mutex guards only the queue, the requests and the
+// statistics; allocation, the host set-up and the launches of a build, the
+// event polls and every free happen outside it.
 static void scheduler(hf_server *s) {
     cudaSetDevice(s->device);
+    std::vector<std::pair<std::shared_ptr<Job>, bool>> finished;
     for (;;) {
-        std::shared_ptr<Request> cand;
+        // completions, polled outside the mutex (the running list is this thread's)
+        finished.clear();
+        for (size_t i = 0; i < s->running.size();) {
+            auto &j = s->running[i];
+            const cudaError_t q = cudaEventQuery(j->done);
+            if (q == cudaErrorNotReady) { ++i; continue; }
+            finished.push_back({j, q == cudaSuccess});
+            cudaEventDestroy(j->done);
+            j->done = nullptr;
+            s->stream_busy[j->stream] = 0;
+            s->running.erase(s->running.begin() + i);
+        }
+        std::shared_ptr<Job> cand;
         const hf_part *p1 = nullptr, *p2 = nullptr;
         int n = 0, si = -1;
         {
             std::unique_lock<std::mutex> lk(s->mu);
             if (s->stop) break;
-            // completions
-            for (size_t i = 0; i < s->running.size();) {
-                auto &r = s->running[i];
-                const cudaError_t q = cudaEventQuery(r->done);
-                if (q == cudaErrorNotReady) { ++i; continue; }
-                r->t_done = now_ms();
-                if (q == cudaSuccess) {
-                    publish(s, r);
-                    r->state = RQ_DONE;
-                    s->stats.completed++;
-                    s->stats.rotations_completed += r->R;
+            for (auto &f : finished) {
+                if (f.second) {
+                    publish(s, f.first);
                 } else {
-                    s->graveyard.put(r->fs);
-                    r->fs = nullptr;
-                    r->state = RQ_FAILED;
-                    s->stats.failed++;
+                    s->graveyard.put(f.first->fs);
+                    f.first->fs = nullptr;
                 }
-                cudaEventDestroy(r->done);
-                r->done = nullptr;
-                s->stream_busy[r->stream] = 0;
-                s->running.erase(s->running.begin() + i);
+                finish_job(s, f.first, f.second);
             }
-            // next admissible request, first-in first-out
+            // next admissible job, first-in first-out
             while (!s->queue.empty() && (int)s->running.size() < s->max_inflight) {
-                auto r = s->queue.front();
+                auto j = s->queue.front();
                 s->queue.pop_front();
-                if (r->state == RQ_SUPERSEDED) continue;
-                Session &ss = s->sessions[r->session];
-                if (!ss.open) {
-                    r->state = RQ_FAILED;
-                    s->stats.failed++;
+                if (j->superseded) continue;
+                Session &ss = s->sessions[j->req->session];
+                if (!ss.open.load()) {
+                    finish_job(s, j, false);
                     continue;
                 }
                 si = 0;
                 while (si < (int)s->streams.size() && s->stream_busy[si]) ++si;
-                cand = r;
+                cand = j;
                 p1 = ss.s1;
                 p2 = ss.s2;
                 n = ss.n;
@@ -224,17 +374,19 @@ static void scheduler(hf_server *s) {
         free_retired(s);
         // allocate and launch outside the mutex
         hf_fieldset *fs = nullptr;
-        hf_status st = hf_fieldset_create_stream_ordered(s->ctx, n, cand->R, cand->flags, s->streams[si], &fs);
+        double a = now_ms();
+        hf_status st = hf_fieldset_create_stream_ordered(s->ctx, n, cand->R, cand->req->flags, s->streams[si], &fs);
+        trace_call(s, 0, a, now_ms());
         if (st == HF_EBUDGET) {
             std::unique_lock<std::mutex> lk(s->mu);
             s->stream_busy[si] = 0;
             if (s->running.empty()) {
-                // nothing in flight will free memory: make room from other sessions' sets
-                if (evict_one(s, cand->session)) {
+                // nothing in flight will free memory: make room from published chunks
+                if (evict_one(s)) {
                     s->queue.push_front(cand);  // keep its place; retry once the set is freed
                 } else {
-                    cand->state = RQ_FAILED;  // can never fit next to the resident parts
-                    s->stats.failed++;
+                    cand->req->error = "the chunk cannot fit next to the resident parts";
+                    finish_job(s, cand, false);
                     s->stats.rejected++;
                 }
                 continue;
@@ -243,38 +395,45 @@ static void scheduler(hf_server *s) {
             s->cv.wait_for(lk, std::chrono::microseconds(200));
             continue;
         }
+        std::string err;
         if (st == HF_OK) {
+            a = now_ms();
             st = hf_fieldset_compute(s->ctx, p1, p2, cand->quats.data(), cand->R, fs, s->streams[si]);
+            trace_call(s, 1, a, now_ms());
             // a rank-deficient torque neighbourhood is flagged (NaN torque), not fatal
             if (st == HF_EINVAL && hf_fieldset_is_ready(fs)) st = HF_OK;
-            if (st != HF_OK) cand->error = hf_last_error();
+            if (st != HF_OK) err = hf_last_error();
+        } else {
+            err = hf_last_error();
         }
         cudaEvent_t ev = nullptr;
         if (st == HF_OK && (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
                             cudaEventRecord(ev, s->streams[si]) != cudaSuccess))
             st = HF_ECUDA;
-        std::lock_guard<std::mutex> g(s->mu);
         if (st == HF_OK) {
             cand->fs = fs;
             cand->done = ev;
             cand->stream = si;
-            cand->state = RQ_RUNNING;
             s->running.push_back(cand);
+            std::lock_guard<std::mutex> g(s->mu);
+            if (cand->req->state == RQ_QUEUED) cand->req->state = RQ_RUNNING;
         } else {
             if (fs) s->graveyard.put(fs);
             if (ev) cudaEventDestroy(ev);
+            std::lock_guard<std::mutex> g(s->mu);
             s->stream_busy[si] = 0;
-            cand->state = RQ_FAILED;
-            s->stats.failed++;
+            cand->req->error = err;
+            finish_job(s, cand, false);
         }
     }
     // drain: wait for everything in flight, then release
-    for (auto &r : s->running) {
-        cudaEventSynchronize(r->done);
-        cudaEventDestroy(r->done);
-        s->graveyard.put(r->fs);
-        r->fs = nullptr;
-        r->state = RQ_FAILED;
+    for (auto &j : s->running) {
+        cudaEventSynchronize(j->done);
+        cudaEventDestroy(j->done);
+        s->graveyard.put(j->fs);
+        j->fs = nullptr;
+        std::lock_guard<std::mutex> g(s->mu);
+        if (j->req->state != RQ_DONE) j->req->state = RQ_FAILED;
     }
     s->running.clear();
     free_retired(s);
@@ -288,9 +447,22 @@ extern "C" hf_status hf_server_create(hf_ctx *ctx, int max_inflight, int query_l
     hf_server *s = new hf_server();
     s->ctx = ctx;
     s->max_inflight = max_inflight;
+    s->chunk_bytes = hf_ctx_budget_bytes(ctx) / 3;
+    s->t0 = now_ms();
+    s->lat_us.resize(kLatRing);  // no allocation on the query path
     cudaGetDevice(&s->device);
+    // the builds allocate stream-ordered from the device's default pool: keep
+    // what it has reserved instead of handing it back at every
+    // synchronisation, so that later builds do not map memory again while
+    // queries launch (the memory is returned when the server is destroyed)
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = cudaDeviceGetDefaultMemPool(&pool, s->device);
+    if (e == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
     int lo = 0, hi = 0;
-    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
     for (int i = 0; i < max_inflight && e == cudaSuccess; ++i) {
         cudaStream_t st = nullptr;
         e = cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, lo);
@@ -322,7 +494,7 @@ extern "C" void hf_server_destroy(hf_server *s) {
     }
     s->cv.notify_all();
     if (s->sched.joinable()) s->sched.join();
-    for (auto &ss : s->sessions) ss.current.reset();
+    for (int i = 0; i < s->nsessions.load(); ++i) s->sessions[i].set_current(nullptr);
     cudaDeviceSynchronize();
     free_retired(s);
     for (auto st : s->streams)
@@ -331,22 +503,36 @@ extern "C" void hf_server_destroy(hf_server *s) {
         if (L.st) cudaStreamDestroy(L.st);
         if (L.h_out) cudaFreeHost(L.h_out);
     }
+    cudaMemPool_t pool = nullptr;
+    if (cudaDeviceGetDefaultMemPool(&pool, s->device) == cudaSuccess) {
+        cudaDeviceSynchronize();
+        cudaMemPoolTrimTo(pool, 0);
+    }
     delete s;
+}
+
+extern "C" hf_status hf_server_set_chunk_bytes(hf_server *s, size_t bytes) {
+    if (!s) return srv_fail(HF_EINVAL, "hf_server_set_chunk_bytes: NULL server");
+    std::lock_guard<std::mutex> g(s->mu);
+    s->chunk_bytes = bytes;
+    return HF_OK;
 }
 
 extern "C" hf_status hf_server_session_open(hf_server *s, const hf_part *s1, const hf_part *s2, int *session) {
     if (!s || !s1 || !s2 || !session) return srv_fail(HF_EINVAL, "hf_server_session_open: NULL argument");
     // the pair is validated by the first build (roles, sizes)
+    const int n = hf_part_n(s1);
+    if (n <= 0 || n != hf_part_n(s2)) return srv_fail(HF_EINVAL, "hf_server_session_open: part sizes differ");
     std::lock_guard<std::mutex> g(s->mu);
-    Session ss;
-    ss.open = true;
+    const int i = s->nsessions.load();
+    if (i >= kMaxSessions) return srv_fail(HF_EINVAL, "hf_server_session_open: more than %d sessions", kMaxSessions);
+    Session &ss = s->sessions[i];
     ss.s1 = s1;
     ss.s2 = s2;
-    ss.n = hf_part_n(s1);
-    ss.last_use = now_ms();
-    if (ss.n <= 0 || ss.n != hf_part_n(s2)) return srv_fail(HF_EINVAL, "hf_server_session_open: part sizes differ");
-    s->sessions.push_back(ss);
-    *session = (int)s->sessions.size() - 1;
+    ss.n = n;
+    ss.open.store(true);
+    s->nsessions.store(i + 1, std::memory_order_release);  // visible to readers from here on
+    *session = i;
     s->stats.sessions++;
     return HF_OK;
 }
@@ -354,43 +540,115 @@ extern "C" hf_status hf_server_session_open(hf_server *s, const hf_part *s1, con
 extern "C" hf_status hf_server_session_close(hf_server *s, int session) {
     if (!s) return srv_fail(HF_EINVAL, "hf_server_session_close: NULL server");
     std::lock_guard<std::mutex> g(s->mu);
-    if (session < 0 || session >= (int)s->sessions.size() || !s->sessions[session].open)
-        return srv_fail(HF_EINVAL, "hf_server_session_close: session %d", session);
-    s->sessions[session].open = false;
-    s->sessions[session].current.reset();
+    Session *ss = session_at(s, session);
+    if (!ss) return srv_fail(HF_EINVAL, "hf_server_session_close: session %d", session);
+    ss->open.store(false);
+    ss->set_current(nullptr);
     s->stats.sessions--;
     return HF_OK;
+}
+
+// largest build set (rotations) whose field set fits `limit` bytes
+static int max_build_rotations(int n, unsigned flags, size_t limit) {
+    int lo = 0, hi = 1;
+    while (hi < (1 << 20) && hf_fieldset_bytes(n, hi, flags) <= limit) hi *= 2;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        (hf_fieldset_bytes(n, mid, flags) <= limit ? lo : hi) = mid;
+    }
+    return lo;
 }
 
 extern "C" hf_status hf_server_submit(hf_server *s, int session, const float *h_quat, int R, unsigned flags,
                                       int64_t *request) {
     if (!s || !h_quat || !request) return srv_fail(HF_EINVAL, "hf_server_submit: NULL argument");
-    std::lock_guard<std::mutex> g(s->mu);
-    if (session < 0 || session >= (int)s->sessions.size() || !s->sessions[session].open)
-        return srv_fail(HF_EINVAL, "hf_server_submit: session %d", session);
     if (R <= 0) return srv_fail(HF_EINVAL, "hf_server_submit: R=%d", R);
-    const size_t need = hf_fieldset_bytes(s->sessions[session].n, R, flags);
-    const size_t budget = hf_ctx_budget_bytes(s->ctx);
-    if (budget && need > budget) {
-        s->stats.rejected++;
-        return srv_fail(HF_EBUDGET, "hf_server_submit: %zu bytes exceed the budget of %zu", need, budget);
+    Session *ss = session_at(s, session);
+    if (!ss) return srv_fail(HF_EINVAL, "hf_server_submit: session %d", session);
+    const int n = ss->n;
+    size_t chunk_bytes;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        chunk_bytes = s->chunk_bytes;
     }
-    // a newer request supersedes this session's still-queued one
-    for (auto &q : s->queue)
-        if (q->session == session && q->state == RQ_QUEUED) {
-            q->state = RQ_SUPERSEDED;
-            s->stats.superseded++;
-        }
     auto r = std::make_shared<Request>();
-    r->id = s->next_id++;
     r->session = session;
-    r->quats.assign(h_quat, h_quat + 4 * (size_t)R);
+    r->n = n;
     r->R = R;
     r->flags = flags;
+    r->q.resize(4 * (size_t)R);
+    for (int i = 0; i < R; ++i) {
+        const float *v = h_quat + 4 * (size_t)i;
+        const double w = v[0], x = v[1], y = v[2], z = v[3], nq = sqrt(w * w + x * x + y * y + z * z);
+        if (!(nq > 0) || !isfinite(nq)) return srv_fail(HF_EINVAL, "hf_server_submit: quaternion %d", i);
+        double *o = &r->q[4 * (size_t)i];
+        o[0] = w / nq; o[1] = x / nq; o[2] = y / nq; o[3] = z / nq;
+    }
+    // split the request when its set exceeds the chunk limit (host work,
+    // outside the server mutex)
+    std::vector<std::shared_ptr<Job>> jobs;
+    const size_t need = hf_fieldset_bytes(n, R, flags);
+    const size_t budget = hf_ctx_budget_bytes(s->ctx);
+    if (chunk_bytes && need > chunk_bytes) {
+        const bool halo = (flags & HF_T) != 0;  // the least-squares torque needs its 6 neighbours
+        const int mb = max_build_rotations(n, flags, chunk_bytes);
+        if (mb < (halo ? 7 : 1)) {
+            std::lock_guard<std::mutex> g(s->mu);
+            s->stats.rejected++;
+            return srv_fail(HF_EBUDGET, "hf_server_submit: a chunk of N=%d does not fit %zu bytes", n, chunk_bytes);
+        }
+        std::vector<int> offs((size_t)R + 1), build((size_t)R * 7);
+        r->owner.resize(R);
+        const int C = hf_rotation_chunks(h_quat, R, mb, halo ? 1 : 0, r->owner.data(), offs.data(), build.data(),
+                                         (int)build.size());
+        if (C < 1) return srv_fail(HF_EINVAL, "hf_server_submit: rotation chunking failed");
+        r->nchunks = C;
+        r->local.assign(R, -1);
+        for (int c = 0; c < C; ++c) {
+            auto j = std::make_shared<Job>();
+            j->req = r;
+            j->chunk = c;
+            j->R = offs[c + 1] - offs[c];
+            j->quats.resize(4 * (size_t)j->R);
+            for (int m = 0; m < j->R; ++m) {
+                const int g = build[offs[c] + m];
+                memcpy(&j->quats[4 * (size_t)m], h_quat + 4 * (size_t)g, 4 * sizeof(float));
+                if (r->owner[g] == c) r->local[g] = m;
+            }
+            jobs.push_back(j);
+        }
+    } else {
+        if (budget && need > budget) {
+            std::lock_guard<std::mutex> g(s->mu);
+            s->stats.rejected++;
+            return srv_fail(HF_EBUDGET, "hf_server_submit: %zu bytes exceed the budget of %zu", need, budget);
+        }
+        r->owner.assign(R, 0);
+        r->local.resize(R);
+        for (int i = 0; i < R; ++i) r->local[i] = i;
+        auto j = std::make_shared<Job>();
+        j->req = r;
+        j->R = R;
+        j->quats.assign(h_quat, h_quat + 4 * (size_t)R);
+        jobs.push_back(j);
+    }
+    std::lock_guard<std::mutex> g(s->mu);
+    if (!ss->open.load()) return srv_fail(HF_EINVAL, "hf_server_submit: session %d", session);
+    // a newer request supersedes this session's still-queued jobs
+    for (auto &j : s->queue)
+        if (j->req->session == session && !j->superseded) {
+            j->superseded = true;
+            if (j->req->state != RQ_SUPERSEDED) {
+                j->req->state = RQ_SUPERSEDED;
+                s->stats.superseded++;
+            }
+        }
+    r->id = s->next_id++;
     r->t_submit = now_ms();
-    s->queue.push_back(r);
+    for (auto &j : jobs) s->queue.push_back(j);
     s->requests[r->id] = r;
     s->stats.submitted++;
+    s->stats.chunks_submitted += (int64_t)jobs.size();
     *request = r->id;
     s->cv.notify_all();
     return HF_OK;
@@ -407,31 +665,79 @@ extern "C" hf_status hf_server_request_state(hf_server *s, int64_t request, int 
     return HF_OK;
 }
 
-static std::shared_ptr<SetHolder> current_set(hf_server *s, int session, hf_status *st) {
+extern "C" hf_status hf_server_request_chunks(hf_server *s, int64_t request, int *chunks, int *owner) {
+    if (!s || !chunks) return srv_fail(HF_EINVAL, "hf_server_request_chunks: NULL argument");
     std::lock_guard<std::mutex> g(s->mu);
-    if (session < 0 || session >= (int)s->sessions.size() || !s->sessions[session].open) {
+    auto it = s->requests.find(request);
+    if (it == s->requests.end()) return srv_fail(HF_EINVAL, "hf_server_request_chunks: request %lld", (long long)request);
+    *chunks = it->second->nchunks;
+    if (owner) std::copy(it->second->owner.begin(), it->second->owner.end(), owner);
+    return HF_OK;
+}
+
+// nearest rotation of the published request to q (|q . q_r| largest, ties to
+// the lower index)
+static int route(const Request &r, const float *q) {
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    int best = 0;
+    double bd = -1.0;
+    for (int i = 0; i < r.R; ++i) {
+        const double *v = &r.q[4 * (size_t)i];
+        const double d = fabs(w * v[0] + x * v[1] + y * v[2] + z * v[3]);
+        if (d > bd) { bd = d; best = i; }
+    }
+    return best;
+}
+
+// The set that answers for the session (no server lock): the chunk owning
+// rotation `rot` (rot >= 0) or the one owning the nearest rotation to q;
+// *local receives rot's index in that set.
+static std::shared_ptr<SetHolder> session_set(hf_server *s, int session, int rot, const float *q, int *local,
+                                              hf_status *st) {
+    Session *ss = session_at(s, session);
+    if (!ss) {
         *st = srv_fail(HF_EINVAL, "hf_server: session %d", session);
         return nullptr;
     }
-    Session &ss = s->sessions[session];
-    ss.last_use = now_ms();
-    if (!ss.current) {
+    std::shared_ptr<Published> cur = ss->current();
+    if (!cur) {
         *st = srv_fail(HF_ENOTREADY, "hf_server: session %d has no field set yet", session);
         return nullptr;
     }
+    const Request &r = *cur->req;
+    int c = 0;
+    if (rot >= 0) {
+        if (rot >= r.R) {
+            *st = srv_fail(HF_EINVAL, "hf_server: rotation %d of %d", rot, r.R);
+            return nullptr;
+        }
+        c = r.owner[rot];
+        if (local) *local = r.local[rot];
+    } else if (r.nchunks > 1) {
+        c = r.owner[route(r, q)];
+    }
+    std::shared_ptr<SetHolder> h = cur->get(c);
+    if (!h) {
+        *st = srv_fail(HF_ENOTREADY, "hf_server: session %d: chunk %d of its field set is not resident", session, c);
+        return nullptr;
+    }
+    cur->last_use[c].store(now_ms());
     *st = HF_OK;
-    return ss.current;
+    return h;
 }
-
-constexpr size_t kLatRing = 1u << 20;
 
 extern "C" hf_status hf_server_query(hf_server *s, int session, const float t[3], const float q[4], int k,
                                      float out7[7]) {
-    if (!s) return srv_fail(HF_EINVAL, "hf_server_query: NULL server");
+    if (!s || !t || !q || !out7) return srv_fail(HF_EINVAL, "hf_server_query: NULL argument");
     const double t0 = now_ms();
     hf_status st = HF_OK;
-    std::shared_ptr<SetHolder> set = current_set(s, session, &st);
-    if (!set) return st;
+    std::shared_ptr<SetHolder> set = session_set(s, session, -1, q, nullptr, &st);
+    Session *ss = session_at(s, session);
+    if (!set) {
+        if (ss && st == HF_ENOTREADY) ss->not_ready++;
+        return st;
+    }
+    const double t1 = now_ms();
     int li;
     {
         std::unique_lock<std::mutex> g(s->lane_mu);
@@ -439,25 +745,31 @@ extern "C" hf_status hf_server_query(hf_server *s, int session, const float t[3]
         li = s->free_lanes.back();
         s->free_lanes.pop_back();
     }
+    const double t2 = now_ms();
     Lane &L = s->lanes[li];
     st = hf_query_on_lane(set->fs, t, q, k, out7, L.st, L.h_out, L.d_out);
+    const double t3 = now_ms();
     {
         std::lock_guard<std::mutex> g(s->lane_mu);
         s->free_lanes.push_back(li);
     }
     s->lane_cv.notify_one();
     if (st == HF_OK) {
-        const float us = (float)((now_ms() - t0) * 1000.0);
-        std::lock_guard<std::mutex> g(s->lat_mu);
-        if (s->lat_us.size() < kLatRing) s->lat_us.resize(kLatRing);
-        s->lat_us[s->lat_head] = us;
-        s->lat_head = (s->lat_head + 1) % kLatRing;
-        s->lat_count = std::min(s->lat_count + 1, kLatRing);
+        if (ss) ss->answered++;
+        const double us = (t3 - t0) * 1000.0;
+        {
+            std::lock_guard<std::mutex> g(s->lat_mu);
+            s->lat_us[s->lat_head] = (float)us;
+            s->lat_head = (s->lat_head + 1) % kLatRing;
+            s->lat_count = std::min(s->lat_count + 1, kLatRing);
+        }
+        if (us >= kSlowQueryUs) {
+            const double row[TraceRing::kCols] = {t0 - s->t0, us, (t1 - t0) * 1e3, (t2 - t1) * 1e3, (t3 - t2) * 1e3,
+                                                  (double)session};
+            s->slow_queries.put(row);
+        }
     }
-    {
-        std::lock_guard<std::mutex> g(s->mu);
-        s->stats.queries++;
-    }
+    s->queries++;
     return st;
 }
 
@@ -472,21 +784,48 @@ extern "C" int hf_server_query_latencies(hf_server *s, float *out, int max) {
     return (int)n;
 }
 
+extern "C" int hf_server_trace(hf_server *s, int which, double *out, int max) {
+    if (!s || !out || max <= 0 || (which != 0 && which != 1)) return 0;
+    TraceRing &t = which == 0 ? s->slow_queries : s->slow_calls;
+    std::lock_guard<std::mutex> g(t.mu);
+    const int n = std::min(t.count, max);
+    const int start = (t.head + TraceRing::kRows - t.count + (t.count - n)) % TraceRing::kRows;
+    for (int i = 0; i < n; ++i)
+        memcpy(out + (size_t)i * TraceRing::kCols, &t.rows[(size_t)((start + i) % TraceRing::kRows) * TraceRing::kCols],
+               sizeof(double) * TraceRing::kCols);
+    t.count = 0;
+    return n;
+}
+
+extern "C" hf_status hf_server_session_counts(hf_server *s, int session, int64_t *answered, int64_t *not_ready) {
+    if (!s) return srv_fail(HF_EINVAL, "hf_server_session_counts: NULL server");
+    if (session < 0 || session >= s->nsessions.load())
+        return srv_fail(HF_EINVAL, "hf_server_session_counts: session %d", session);
+    const Session &ss = s->sessions[session];
+    if (answered) *answered = ss.answered.load();
+    if (not_ready) *not_ready = ss.not_ready.load();
+    return HF_OK;
+}
+
 extern "C" hf_status hf_server_field_ptr(hf_server *s, int session, int rot, int field, const float **d_ptr) {
     if (!s) return srv_fail(HF_EINVAL, "hf_server_field_ptr: NULL server");
+    if (rot < 0) return srv_fail(HF_EINVAL, "hf_server_field_ptr: rotation %d", rot);
     hf_status st = HF_OK;
-    std::shared_ptr<SetHolder> set = current_set(s, session, &st);
+    int local = 0;
+    std::shared_ptr<SetHolder> set = session_set(s, session, rot, nullptr, &local, &st);
     if (!set) return st;
-    return hf_fieldset_field_ptr(set->fs, rot, field, d_ptr);
+    return hf_fieldset_field_ptr(set->fs, local, field, d_ptr);
 }
 
 extern "C" hf_status hf_server_field_get(hf_server *s, int session, int rot, int field, float *d_dst,
                                          hf_stream stream) {
     if (!s) return srv_fail(HF_EINVAL, "hf_server_field_get: NULL server");
+    if (rot < 0) return srv_fail(HF_EINVAL, "hf_server_field_get: rotation %d", rot);
     hf_status st = HF_OK;
-    std::shared_ptr<SetHolder> set = current_set(s, session, &st);
+    int local = 0;
+    std::shared_ptr<SetHolder> set = session_set(s, session, rot, nullptr, &local, &st);
     if (!set) return st;
-    st = hf_fieldset_get(set->fs, rot, field, d_dst, stream);
+    st = hf_fieldset_get(set->fs, local, field, d_dst, stream);
     // keep the set alive until the copy has run
     if (st == HF_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
         return srv_fail(HF_ECUDA, "hf_server_field_get: synchronise failed");
@@ -497,8 +836,17 @@ extern "C" hf_status hf_server_stats_get(hf_server *s, hf_server_stats *out) {
     if (!s || !out) return srv_fail(HF_EINVAL, "hf_server_stats_get: NULL argument");
     std::lock_guard<std::mutex> g(s->mu);
     *out = s->stats;
+    out->queries = s->queries.load();
     out->reserved_bytes = hf_ctx_reserved_bytes(s->ctx);
     out->budget_bytes = hf_ctx_budget_bytes(s->ctx);
+    out->chunk_bytes = s->chunk_bytes;
+    int resident = 0;
+    for (int i = 0; i < s->nsessions.load(); ++i) {
+        std::shared_ptr<Published> cur = s->sessions[i].current();
+        if (cur)
+            for (int c = 0; c < cur->req->nchunks; ++c) resident += cur->get(c) ? 1 : 0;
+    }
+    out->chunks_resident = resident;
     return HF_OK;
 }
 

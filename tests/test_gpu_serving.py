@@ -67,6 +67,7 @@ def test_budget_admission_and_rejection(hf):
     ctx = hf.Context(0, hbm_budget_bytes=int(2.5 * one) + (64 << 20))
     parts = make_parts(hf, ctx, n, 3)
     srv = hf.Server(ctx, max_inflight=4, query_lanes=2)
+    srv.set_chunk_bytes(0)  # whole sets only: an oversized request is rejected, not split
     sids = [srv.open(*parts) for _ in range(3)]
     # a set larger than the whole budget is rejected at once
     with pytest.raises(hf.HFError) as e:
@@ -172,4 +173,81 @@ def test_native_query_driver_meets_the_rate(hf):
     assert answered == 2 * steps and not_ready == 0
     assert lat.size == 2 * steps and np.isfinite(lat).all()
     assert took >= 0.29  # paced, not burst
+    srv.close()
+
+
+def test_chunked_request_equals_single_shot_bitwise(hf):
+    """A request split into rotation chunks (each built with its torque
+    neighbours) gives, for every rotation of the request, the same E, F and
+    least-squares T as one build of the whole set, bit for bit; a query at a
+    member rotation is routed to the chunk that owns it."""
+    from paper_1711_05017_b300 import _binding as B
+    n, R = 64, 60
+    flags = hf.HF_E | hf.HF_F | hf.HF_T
+    ctx = hf.Context(0)
+    p1, p2 = make_parts(hf, ctx, n, 21)
+    srv = hf.Server(ctx, max_inflight=3, query_lanes=2)
+    srv.set_chunk_bytes(B.lib().hf_fieldset_bytes(n, 24, flags))
+    sid = srv.open(p1, p2)
+    q = synth.random_quaternions(90, R).astype(np.float32)
+    rid = srv.submit(sid, q, flags)
+    assert srv.wait([rid])[rid][0] == "done"
+    nchunks, owner = srv.request_chunks(rid, R)
+    assert nchunks > 1 and set(owner) == set(range(nchunks))
+    fs = ctx.fieldset(n, R, flags)
+    fs.compute(p1, p2, q)
+    for r in range(R):
+        for f in range(7):
+            a = srv.field(sid, r, f, n).cpu().numpy()
+            b = fs.get(r, f).cpu().numpy()
+            assert np.array_equal(a, b), (r, f, owner[r])
+    h = 2.0 / n
+    for r in (0, R // 2, R - 1):
+        t = np.array([3, 5, 7]) * h
+        got = srv.query(sid, t, q[r], k=1)
+        ref = fs.query(t, q[r], k=1)
+        assert np.array_equal(got, ref), r
+    st = srv.stats()
+    assert st["chunks_completed"] == nchunks and st["chunks_resident"] == nchunks
+    fs.release()
+    srv.close()
+
+
+def test_chunks_admitted_as_memory_frees_and_evicted_least_recent_first(hf):
+    """A request four times larger than the budget is built chunk by chunk:
+    the reserved bytes stay within the budget, earlier chunks are evicted to
+    admit later ones, the request completes, and a query that routes to an
+    evicted chunk is refused as not ready while one that routes to a
+    resident chunk is answered."""
+    from paper_1711_05017_b300 import _binding as B
+    n, R = 64, 96
+    flags = hf.HF_E | hf.HF_F | hf.HF_T
+    one = B.lib().hf_fieldset_bytes(n, 24, flags)
+    ctx = hf.Context(0, hbm_budget_bytes=int(2.2 * one) + (64 << 20))
+    p1, p2 = make_parts(hf, ctx, n, 22)
+    srv = hf.Server(ctx, max_inflight=2, query_lanes=2)
+    srv.set_chunk_bytes(one)
+    sid = srv.open(p1, p2)
+    q = synth.random_quaternions(91, R).astype(np.float32)
+    rid = srv.submit(sid, q, flags)
+    peak = 0
+    t0 = time.time()
+    while time.time() - t0 < 120 and srv.state(rid)[0] not in ("done", "failed"):
+        peak = max(peak, srv.stats()["reserved_bytes"])
+        time.sleep(0.0005)
+    assert srv.state(rid)[0] == "done", B.lib().hf_last_error()
+    nchunks, owner = srv.request_chunks(rid, R)
+    st = srv.stats()
+    assert nchunks >= 4
+    assert peak <= st["budget_bytes"]
+    assert st["evicted"] >= 1 and st["chunks_resident"] < nchunks
+    resident, refused = 0, 0
+    for r in range(R):
+        try:
+            srv.query(sid, [0.0, 0.0, 0.0], q[r], k=1)
+            resident += 1
+        except hf.HFError as e:
+            assert e.status == B.HF_ENOTREADY
+            refused += 1
+    assert resident > 0 and refused > 0
     srv.close()
