@@ -281,6 +281,44 @@ hf_status hf_lowpass_query_batch(const hf_part *s1, const hf_part *s2, int K, co
 /* Device bytes hf_fieldset_create(n, R, flags) charges (0 if unsupported). */
 size_t hf_fieldset_bytes(int n, int R, unsigned flags);
 
+/* ---- checkpoints ----
+ * Section 3.2 precomputes the parts' densities and spectra before the
+ * assembly session and Section 4.2 the fields of the permitted
+ * orientations; these save that state to a file and load it back, so that a
+ * restarted service does not recompute it.  A file is a concatenation of NPY
+ * (version 1.0) arrays, readable one after the other with numpy's
+ * np.lib.format.read_array: first an int64 header [tag, version, kind, N,
+ * ...], then
+ *   kind HF_CKPT_PART: header [.., N, role]; a moving part's grid
+ *     (float32 N x N x N, [z][y][x]) or a stationary part's stored spectrum
+ *     (complex64 N x N x (N/2+1): (h^3/N^3) DFT(rho1) in the library's
+ *     digit-permuted slot order);
+ *   kind HF_CKPT_FIELDSET: header [.., N, R, flags, nf, slot[7]]; the
+ *     rotations (float32 R x 4, as given to the compute); the fields
+ *     (float32 R x nf x N^3, field f of rotation r at slot[f]);
+ *   kind HF_CKPT_SESSION (hf_server_session_save): header [.., N, R, flags,
+ *     chunks]; the request's rotations (float32 R x 4); the chunk owning each
+ *     rotation and its index there (int64 R each); which chunks follow
+ *     (int64, one per chunk); then a field-set record (header, rotations,
+ *     fields) per resident chunk.
+ * Loading reproduces the saved state bit for bit (a moving part's texture
+ * and support are rebuilt from its grid).  Saves copy device data through a
+ * host buffer on `stream` and return when the file is written; loads
+ * allocate as hf_part_create / hf_fieldset_create (charged to the budget)
+ * and return with the data on the device.  Errors: HF_EINVAL (open, write,
+ * not a checkpoint of this kind, wrong types or shapes), HF_ENOTREADY (a set
+ * never computed), HF_EBUDGET, HF_ENOMEM, HF_ECUDA. */
+#define HF_CKPT_PART 1
+#define HF_CKPT_FIELDSET 2
+#define HF_CKPT_SESSION 3
+hf_status hf_part_save(const hf_part *p, const char *path, hf_stream stream);
+hf_status hf_part_load(hf_ctx *ctx, const char *path, hf_part **out, hf_stream stream);
+hf_status hf_fieldset_save(const hf_fieldset *fs, const char *path, hf_stream stream);
+hf_status hf_fieldset_load(hf_ctx *ctx, const char *path, hf_fieldset **out, hf_stream stream);
+/* Kind, N, R (0 for a part) and flags (a part's role) of a checkpoint file;
+ * host only, no GPU. */
+hf_status hf_checkpoint_info(const char *path, int *kind, int *n, int *R, unsigned *flags);
+
 /* ---- rotation-set chunking (host only) ----
  * Split R rotations (h_quat R x 4) into chunks whose build sets hold at most
  * max_build rotations, for rotation sets too large for one field set.  A
@@ -366,6 +404,13 @@ hf_status hf_server_field_ptr(hf_server *srv, int session, int rot, int field, c
 /* Copy that field to d_dst (N^3 floats), on `stream`. */
 hf_status hf_server_field_get(hf_server *srv, int session, int rot, int field, float *d_dst, hf_stream stream);
 hf_status hf_server_stats_get(hf_server *srv, hf_server_stats *out);
+/* Save a session's published data (its request's rotations and routing and
+ * every resident chunk's field set) to a checkpoint file, and restore such a
+ * file as the current data of an open session over parts of the same N
+ * (typically hf_part_load'ed after a restart); chunks that were not resident
+ * stay missing.  Queries and field reads then answer as before the save. */
+hf_status hf_server_session_save(hf_server *srv, int session, const char *path);
+hf_status hf_server_session_restore(hf_server *srv, int session, const char *path);
 /* Queries of a session answered and refused as not ready, so far. */
 hf_status hf_server_session_counts(hf_server *srv, int session, int64_t *answered, int64_t *not_ready);
 /* Latencies (microseconds, call entry to return) of the queries answered since

@@ -7,15 +7,17 @@ in the library's sm_103a kernels.  There is no CPU fallback: without the
 built library or a CUDA device the calls raise.
 """
 import ctypes
+import os
 
 import numpy as np
 
 from . import _binding as B
-from ._binding import (HF_E, HF_F, HF_MOVING, HF_PREC_SPLIT_BF16, HF_PREC_SPLIT_F16, HF_SPECTRAL,  # noqa: F401
+from ._binding import (HF_CKPT_FIELDSET, HF_CKPT_PART, HF_CKPT_SESSION,  # noqa: F401
+                       HF_E, HF_F, HF_MOVING, HF_PREC_SPLIT_BF16, HF_PREC_SPLIT_F16, HF_SPECTRAL,
                        HF_STATIONARY, HF_T, HF_TA, HF_TORQUE_F64, HFError)
 
 __all__ = ["Context", "Part", "FieldSet", "Batch", "Server", "HFError", "lowpass_query", "lowpass_query_batch",
-           "rotation_chunks",
+           "rotation_chunks", "checkpoint_info",
            "resample", "rfft3d", "version"]
 
 
@@ -184,6 +186,21 @@ class Part:
         (padding factor os) for HF_SPECTRAL field sets."""
         B.check(B.lib().hf_part_spectral(self.handle, int(os), _stream_ptr(stream)))
 
+    def save(self, path, stream=None):
+        """hf_part_save: the part's state (a moving grid or the stored
+        stationary spectrum) to a checkpoint file."""
+        B.check(B.lib().hf_part_save(self.handle, os.fsencode(path), _stream_ptr(stream)))
+
+    @classmethod
+    def load(cls, ctx, path, stream=None):
+        """hf_part_load: a part from a checkpoint file (bitwise the saved state)."""
+        h = ctypes.c_void_p()
+        B.check(B.lib().hf_part_load(ctx.handle, os.fsencode(path), ctypes.byref(h), _stream_ptr(stream)))
+        p = cls.__new__(cls)
+        _, n, _, role = checkpoint_info(path)
+        p.handle, p.n, p.role, p.ctx = h, n, role, ctx
+        return p
+
     def update(self, grid, stream=None):
         """hf_part_update: re-derive the part from a new grid, in place."""
         torch = _torch()
@@ -244,6 +261,23 @@ class FieldSet:
         B.check(B.lib().hf_query_batch(self.handle, _dev(tq, torch.float32), int(Q), int(k),
                                        _dev(out, torch.float32), _stream_ptr(stream)))
         return out
+
+    def save(self, path, stream=None):
+        """hf_fieldset_save: the computed set (rotations and fields) to a
+        checkpoint file."""
+        B.check(B.lib().hf_fieldset_save(self.handle, os.fsencode(path), _stream_ptr(stream)))
+
+    @classmethod
+    def load(cls, ctx, path, stream=None):
+        """hf_fieldset_load: a computed set from a checkpoint file, ready for
+        queries (bitwise the saved fields)."""
+        h = ctypes.c_void_p()
+        B.check(B.lib().hf_fieldset_load(ctx.handle, os.fsencode(path), ctypes.byref(h), _stream_ptr(stream)))
+        L = B.lib()
+        fs = cls.__new__(cls)
+        fs.handle, fs.ctx = h, ctx
+        fs.n, fs.R, fs.flags = L.hf_fieldset_n(h), L.hf_fieldset_rotations(h), L.hf_fieldset_flags(h)
+        return fs
 
     def release(self):
         if self.handle:
@@ -363,6 +397,15 @@ def rfft3d(x, out=None, stream=None):
     return out
 
 
+def checkpoint_info(path):
+    """hf_checkpoint_info: (kind, N, R, flags) of a checkpoint file (kind
+    HF_CKPT_PART / FIELDSET / SESSION; a part's R is 0 and its flags its role)."""
+    kind, n, R, fl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_uint()
+    B.check(B.lib().hf_checkpoint_info(os.fsencode(path), ctypes.byref(kind), ctypes.byref(n), ctypes.byref(R),
+                                       ctypes.byref(fl)))
+    return kind.value, n.value, R.value, fl.value
+
+
 def rotation_chunks(quats, max_build, halo=True):
     """hf_rotation_chunks: split a rotation set into chunks of at most
     max_build rotations per build set (with the 6-nearest torque halo).
@@ -403,6 +446,15 @@ class Server:
         B.check(B.lib().hf_server_request_chunks(self.handle, ctypes.c_int64(rid), ctypes.byref(c),
                                                  own.ctypes.data_as(B._ip)))
         return c.value, own
+
+    def session_save(self, sid, path):
+        """hf_server_session_save: the session's published data to a file."""
+        B.check(B.lib().hf_server_session_save(self.handle, int(sid), os.fsencode(path)))
+
+    def session_restore(self, sid, path):
+        """hf_server_session_restore: a saved session's data as this open
+        session's current data."""
+        B.check(B.lib().hf_server_session_restore(self.handle, int(sid), os.fsencode(path)))
 
     def session_counts(self, sid):
         """(queries answered, queries refused as not ready) of a session."""

@@ -15,6 +15,7 @@ STATUS_NAMES = {0: "HF_OK", 1: "HF_EINVAL", 2: "HF_ENOMEM", 3: "HF_EBUDGET", 4: 
 HF_STATIONARY, HF_MOVING = 0, 1
 HF_E, HF_F, HF_T, HF_TORQUE_F64 = 0x1, 0x2, 0x4, 0x10
 HF_PREC_SPLIT_BF16, HF_PREC_SPLIT_F16, HF_SPECTRAL, HF_TA = 0x20, 0x40, 0x80, 0x100
+HF_CKPT_PART, HF_CKPT_FIELDSET, HF_CKPT_SESSION = 1, 2, 3
 
 _vp = ctypes.c_void_p
 _i = ctypes.c_int
@@ -74,6 +75,13 @@ SIGNATURES = {
     "hf_server_set_chunk_bytes": (_i, [_vp, _sz]),
     "hf_server_request_chunks": (_i, [_vp, ctypes.c_int64, _ip, _ip]),
     "hf_server_session_counts": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "hf_server_session_save": (_i, [_vp, _i, ctypes.c_char_p]),
+    "hf_server_session_restore": (_i, [_vp, _i, ctypes.c_char_p]),
+    "hf_part_save": (_i, [_vp, ctypes.c_char_p, _vp]),
+    "hf_part_load": (_i, [_vp, ctypes.c_char_p, ctypes.POINTER(_vp), _vp]),
+    "hf_fieldset_save": (_i, [_vp, ctypes.c_char_p, _vp]),
+    "hf_fieldset_load": (_i, [_vp, ctypes.c_char_p, ctypes.POINTER(_vp), _vp]),
+    "hf_checkpoint_info": (_i, [ctypes.c_char_p, _ip, _ip, _ip, ctypes.POINTER(_u)]),
     "hf_server_trace": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_double), _i]),
     "hf_rotation_chunks": (_i, [_fp, _i, _i, _i, _ip, _ip, _ip, _i]),
     "hf_server_drive_queries": (_i, [_vp, _i, _ip, _fp, _i, ctypes.c_double, _i, ctypes.POINTER(ctypes.c_int64),

@@ -1712,3 +1712,325 @@ extern "C" hf_status hf_autotune(hf_ctx *ctx, int n, const char *cache_path, int
     if (rot_per_s_out) *rot_per_s_out = best.rot_per_s;
     return HF_OK;
 }
+
+// ------------------------------------------------------------- checkpoints
+// Section 3.2 precomputes the parts' densities and spectra "prior to the
+// virtual assembly session", and Section 4.2 precomputes the fields of the
+// permitted orientations; these save that state and load it back, so that a
+// service restarts without recomputing it.  A file is a concatenation of NPY
+// (format version 1.0) arrays, a small int64 header array first, so numpy
+// reads each array in turn with np.lib.format.read_array.
+namespace {
+
+constexpr int64_t kCkptMagic = 0x31504B4348465348LL;  // tag of this library's checkpoint files
+constexpr int64_t kCkptVersion = 1;
+
+bool npy_write_header(FILE *f, const char *descr, const std::vector<int64_t> &shape) {
+    std::string d = std::string("{'descr': '") + descr + "', 'fortran_order': False, 'shape': (";
+    for (int64_t s : shape) d += std::to_string(s) + ", ";
+    d += "), }";
+    const size_t total = 10 + d.size() + 1;  // magic, version, length, dict, newline
+    d.append((64 - total % 64) % 64, ' ');
+    d += '\n';
+    if (d.size() > 65535) return false;
+    const unsigned char pre[10] = {0x93, 'N', 'U', 'M', 'P', 'Y', 1, 0, (unsigned char)(d.size() & 0xff),
+                                   (unsigned char)(d.size() >> 8)};
+    return fwrite(pre, 1, 10, f) == 10 && fwrite(d.data(), 1, d.size(), f) == d.size();
+}
+
+// reads a version 1.0 / 2.0 / 3.0 header of a C-ordered array
+bool npy_read_header(FILE *f, std::string &descr, std::vector<int64_t> &shape) {
+    unsigned char pre[8];
+    if (fread(pre, 1, 8, f) != 8 || pre[0] != 0x93 || memcmp(pre + 1, "NUMPY", 5) != 0) return false;
+    size_t len = 0;
+    if (pre[6] == 1) {
+        unsigned char l[2];
+        if (fread(l, 1, 2, f) != 2) return false;
+        len = l[0] | (size_t)l[1] << 8;
+    } else if (pre[6] == 2 || pre[6] == 3) {
+        unsigned char l[4];
+        if (fread(l, 1, 4, f) != 4) return false;
+        len = l[0] | (size_t)l[1] << 8 | (size_t)l[2] << 16 | (size_t)l[3] << 24;
+    } else {
+        return false;
+    }
+    if (len > (1u << 20)) return false;
+    std::string h(len, '\0');
+    if (fread(&h[0], 1, len, f) != len) return false;
+    const size_t dp = h.find("'descr'"), fp = h.find("'fortran_order'"), sp = h.find("'shape'");
+    if (dp == std::string::npos || fp == std::string::npos || sp == std::string::npos) return false;
+    const size_t q0 = h.find('\'', h.find(':', dp) + 1), q1 = h.find('\'', q0 + 1);
+    if (q0 == std::string::npos || q1 == std::string::npos) return false;
+    descr = h.substr(q0 + 1, q1 - q0 - 1);
+    if (h.compare(h.find_first_not_of(' ', h.find(':', fp) + 1), 5, "False") != 0) return false;
+    const size_t p0 = h.find('(', sp), p1 = h.find(')', sp);
+    if (p0 == std::string::npos || p1 == std::string::npos) return false;
+    shape.clear();
+    const char *c = h.c_str() + p0 + 1, *e = h.c_str() + p1;
+    while (c < e) {
+        while (c < e && (*c == ' ' || *c == ',')) ++c;
+        if (c >= e) break;
+        char *end = nullptr;
+        const long long v = strtoll(c, &end, 10);
+        if (end == c || v < 0) return false;
+        shape.push_back(v);
+        c = end;
+    }
+    return true;
+}
+
+size_t npy_count(const std::vector<int64_t> &shape) {
+    size_t n = 1;
+    for (int64_t s : shape) n *= (size_t)s;
+    return n;
+}
+
+bool write_host_array(FILE *f, const char *descr, const std::vector<int64_t> &shape, const void *p, size_t elem) {
+    const size_t b = npy_count(shape) * elem;
+    return npy_write_header(f, descr, shape) && fwrite(p, 1, b, f) == b;
+}
+
+// an array whose descr and element count the caller checks
+bool read_host_array(FILE *f, const char *descr, std::vector<int64_t> &shape, std::vector<char> &out, size_t elem) {
+    std::string d;
+    if (!npy_read_header(f, d, shape) || d != descr) return false;
+    out.resize(npy_count(shape) * elem);
+    return fread(out.data(), 1, out.size(), f) == out.size();
+}
+
+constexpr size_t kIoChunk = 64u << 20;
+
+// device bytes to the file through a host buffer, chunk by chunk
+hf_status write_device(FILE *f, const void *d, size_t bytes, cudaStream_t st) {
+    std::vector<char> buf(std::min(bytes, kIoChunk));
+    for (size_t o = 0; o < bytes; o += kIoChunk) {
+        const size_t b = std::min(kIoChunk, bytes - o);
+        CU(cudaMemcpyAsync(buf.data(), (const char *)d + o, b, cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        if (fwrite(buf.data(), 1, b, f) != b) return fail(HF_EINVAL, "checkpoint: write failed");
+    }
+    return HF_OK;
+}
+
+hf_status read_device(FILE *f, void *d, size_t bytes, cudaStream_t st) {
+    std::vector<char> buf(std::min(bytes, kIoChunk));
+    for (size_t o = 0; o < bytes; o += kIoChunk) {
+        const size_t b = std::min(kIoChunk, bytes - o);
+        if (fread(buf.data(), 1, b, f) != b) return fail(HF_EINVAL, "checkpoint: file is truncated");
+        CU(cudaMemcpyAsync((char *)d + o, buf.data(), b, cudaMemcpyHostToDevice, st));
+        CU(cudaStreamSynchronize(st));
+    }
+    return HF_OK;
+}
+
+bool read_meta(FILE *f, int64_t kind, std::vector<int64_t> &meta) {
+    std::vector<int64_t> shape;
+    std::vector<char> raw;
+    if (!read_host_array(f, "<i8", shape, raw, 8) || shape.size() != 1 || shape[0] < 8) return false;
+    meta.resize(shape[0]);
+    memcpy(meta.data(), raw.data(), raw.size());
+    return meta[0] == kCkptMagic && meta[1] == kCkptVersion && meta[2] == kind;
+}
+
+struct FileCloser {
+    FILE *f;
+    ~FileCloser() {
+        if (f) fclose(f);
+    }
+};
+
+}  // namespace
+
+extern "C" hf_status hf_checkpoint_info(const char *path, int *kind, int *n, int *R, unsigned *flags) {
+    if (!path) return fail(HF_EINVAL, "hf_checkpoint_info: NULL path");
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(HF_EINVAL, "hf_checkpoint_info: cannot open %s", path);
+    FileCloser fc{f};
+    std::vector<int64_t> shape;
+    std::vector<char> raw;
+    if (!read_host_array(f, "<i8", shape, raw, 8) || shape.size() != 1 || shape[0] < 8)
+        return fail(HF_EINVAL, "hf_checkpoint_info: %s is not a checkpoint of this library", path);
+    const int64_t *m = (const int64_t *)raw.data();
+    if (m[0] != kCkptMagic || m[1] != kCkptVersion || m[2] < HF_CKPT_PART || m[2] > HF_CKPT_SESSION)
+        return fail(HF_EINVAL, "hf_checkpoint_info: %s is not a checkpoint of this library", path);
+    if (kind) *kind = (int)m[2];
+    if (n) *n = (int)m[3];
+    if (R) *R = m[2] == HF_CKPT_PART ? 0 : (int)m[4];
+    if (flags) *flags = m[2] == HF_CKPT_PART ? (unsigned)m[4] : (unsigned)m[5];
+    return HF_OK;
+}
+
+extern "C" hf_status hf_part_save(const hf_part *p, const char *path, hf_stream stream) {
+    if (!p || !path) return fail(HF_EINVAL, "hf_part_save: NULL argument");
+    CU(cudaSetDevice(p->ctx->device));
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(HF_EINVAL, "hf_part_save: cannot create %s", path);
+    FileCloser fc{f};
+    const int n = p->n;
+    const std::vector<int64_t> meta = {kCkptMagic, kCkptVersion, HF_CKPT_PART, n, p->role, 0, 0, 0};
+    if (!write_host_array(f, "<i8", {8}, meta.data(), 8)) return fail(HF_EINVAL, "hf_part_save: write failed");
+    if (p->role == HF_MOVING) {
+        if (!npy_write_header(f, "<f4", {n, n, n})) return fail(HF_EINVAL, "hf_part_save: write failed");
+        return write_device(f, p->grid, (size_t)n * n * n * sizeof(float), (cudaStream_t)stream);
+    }
+    if (!npy_write_header(f, "<c8", {n, n, n / 2 + 1})) return fail(HF_EINVAL, "hf_part_save: write failed");
+    return write_device(f, p->spec, hf::half_spec_elems(n) * sizeof(float2), (cudaStream_t)stream);
+}
+
+extern "C" hf_status hf_part_load(hf_ctx *ctx, const char *path, hf_part **out, hf_stream stream) {
+    if (!ctx || !path || !out) return fail(HF_EINVAL, "hf_part_load: NULL argument");
+    *out = nullptr;
+    CU(cudaSetDevice(ctx->device));
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(HF_EINVAL, "hf_part_load: cannot open %s", path);
+    FileCloser fc{f};
+    std::vector<int64_t> meta, shape;
+    if (!read_meta(f, HF_CKPT_PART, meta)) return fail(HF_EINVAL, "hf_part_load: %s is not a part checkpoint", path);
+    const int n = (int)meta[3], role = (int)meta[4];
+    if (!hf::supported_n(n) || (role != HF_STATIONARY && role != HF_MOVING))
+        return fail(HF_EINVAL, "hf_part_load: N=%d, role %d", n, role);
+    std::string descr;
+    if (!npy_read_header(f, descr, shape)) return fail(HF_EINVAL, "hf_part_load: %s: bad array header", path);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (role == HF_MOVING) {
+        if (descr != "<f4" || shape != std::vector<int64_t>{n, n, n})
+            return fail(HF_EINVAL, "hf_part_load: %s: grid array of the wrong type or shape", path);
+        const size_t b = (size_t)n * n * n * sizeof(float);
+        float *tmp = nullptr;
+        CU(cudaMallocAsync(&tmp, b, st));
+        hf_status s = read_device(f, tmp, b, st);
+        if (s == HF_OK) s = hf_part_create(ctx, n, tmp, HF_MOVING, out, stream);
+        cudaFreeAsync(tmp, st);
+        return s;
+    }
+    if (descr != "<c8" || shape != std::vector<int64_t>{n, n, n / 2 + 1})
+        return fail(HF_EINVAL, "hf_part_load: %s: spectrum array of the wrong type or shape", path);
+    const size_t bytes = hf::half_spec_elems(n) * sizeof(float2);
+    if (!charge(ctx, bytes)) return fail(HF_EBUDGET, "hf_part_load: %zu bytes exceed the budget", bytes);
+    hf_part *p = new (std::nothrow) hf_part{ctx, n, HF_STATIONARY, nullptr, nullptr, bytes};
+    cudaError_t e = p ? cudaMalloc(&p->spec, bytes) : cudaErrorMemoryAllocation;
+    hf_status s = e == cudaSuccess ? read_device(f, p->spec, bytes, st)
+                                   : fail(HF_ENOMEM, "hf_part_load: %s", cudaGetErrorString(e));
+    if (s != HF_OK) {
+        if (p && p->spec) cudaFree(p->spec);
+        delete p;
+        uncharge(ctx, bytes);
+        return s;
+    }
+    *out = p;
+    return HF_OK;
+}
+
+hf_status hf_fieldset_write(const hf_fieldset *fs, FILE *f, cudaStream_t st) {
+    if (!fs->ready || fs->prep_quat.size() != (size_t)fs->R * 4)
+        return fail(HF_ENOTREADY, "field-set save: the set holds no computed rotation set");
+    const int n = fs->n;
+    std::vector<int64_t> meta = {kCkptMagic, kCkptVersion, HF_CKPT_FIELDSET, n, fs->R, fs->flags, fs->nf};
+    for (int k = 0; k < 7; ++k) meta.push_back(fs->slot[k]);
+    meta.resize(16, 0);
+    if (!write_host_array(f, "<i8", {16}, meta.data(), 8) ||
+        !write_host_array(f, "<f4", {fs->R, 4}, fs->prep_quat.data(), 4) ||
+        !npy_write_header(f, "<f4", {fs->R, fs->nf, n, n, n}))
+        return fail(HF_EINVAL, "field-set save: write failed");
+    return write_device(f, fs->data, (size_t)fs->R * fs->nf * n * n * n * sizeof(float), st);
+}
+
+hf_status hf_fieldset_read(hf_ctx *ctx, FILE *f, hf_fieldset **out, cudaStream_t mem_stream, cudaStream_t st) {
+    *out = nullptr;
+    std::vector<int64_t> meta, shape;
+    std::vector<char> raw;
+    if (!read_meta(f, HF_CKPT_FIELDSET, meta) || meta.size() < 14)
+        return fail(HF_EINVAL, "field-set load: not a field-set checkpoint");
+    const int n = (int)meta[3], R = (int)meta[4], nf = (int)meta[6];
+    const unsigned flags = (unsigned)meta[5];
+    if (!read_host_array(f, "<f4", shape, raw, 4) || shape != std::vector<int64_t>{R, 4})
+        return fail(HF_EINVAL, "field-set load: rotation array of the wrong type or shape");
+    const float *q = (const float *)raw.data();
+    hf_fieldset *fs = nullptr;
+    hf_status s = fieldset_create_impl(ctx, n, R, flags, mem_stream, &fs);
+    if (s != HF_OK) return s;
+    std::string descr;
+    if (fs->nf != nf || !npy_read_header(f, descr, shape) || descr != "<f4" ||
+        shape != std::vector<int64_t>{R, nf, n, n, n}) {
+        hf_fieldset_release(fs);
+        return fail(HF_EINVAL, "field-set load: field array of the wrong type or shape");
+    }
+    for (int k = 0; k < 7; ++k)
+        if (fs->slot[k] != (int)meta[7 + k]) {
+            hf_fieldset_release(fs);
+            return fail(HF_EINVAL, "field-set load: field layout differs from this library's");
+        }
+    // the rotation set's host preparation and uploads, as a compute would make them
+    const int bad = hf_prepare_rotations(q, R, (flags & HF_T) != 0, fs->prep_rot9, fs->prep_q64, fs->prep_nbr,
+                                         fs->prep_P32, fs->prep_P64);
+    if (bad < 0) {
+        hf_fieldset_release(fs);
+        return fail(HF_EINVAL, "field-set load: a quaternion is zero or not finite");
+    }
+    fs->prep_quat.assign(q, q + (size_t)R * 4);
+    fs->prep_bad = bad;
+    cudaError_t e = cudaMemcpyAsync(fs->d_rot9, fs->prep_rot9.data(), fs->prep_rot9.size() * sizeof(float),
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(fs->d_quat, fs->prep_q64.data(), fs->prep_q64.size() * sizeof(double),
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && (flags & HF_T)) {
+        e = cudaMemcpyAsync(fs->d_nbr, fs->prep_nbr.data(), fs->prep_nbr.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(fs->d_P, fs->prep_P32.data(), fs->prep_P32.size() * sizeof(float),
+                                cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(fs->d_P64, fs->prep_P64.data(), fs->prep_P64.size() * sizeof(double),
+                                cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host vectors are pageable
+    s = e == cudaSuccess ? read_device(f, fs->data, (size_t)R * nf * n * n * n * sizeof(float), st)
+                         : fail(HF_ECUDA, "field-set load: %s", cudaGetErrorString(e));
+    if (s != HF_OK) {
+        hf_fieldset_release(fs);
+        return s;
+    }
+    fs->ready = true;
+    *out = fs;
+    return HF_OK;
+}
+
+extern "C" hf_status hf_fieldset_save(const hf_fieldset *fs, const char *path, hf_stream stream) {
+    if (!fs || !path) return fail(HF_EINVAL, "hf_fieldset_save: NULL argument");
+    CU(cudaSetDevice(fs->ctx->device));
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(HF_EINVAL, "hf_fieldset_save: cannot create %s", path);
+    FileCloser fc{f};
+    CU(cudaStreamSynchronize((cudaStream_t)stream));
+    return hf_fieldset_write(fs, f, (cudaStream_t)stream);
+}
+
+extern "C" hf_status hf_fieldset_load(hf_ctx *ctx, const char *path, hf_fieldset **out, hf_stream stream) {
+    if (!ctx || !path || !out) return fail(HF_EINVAL, "hf_fieldset_load: NULL argument");
+    CU(cudaSetDevice(ctx->device));
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(HF_EINVAL, "hf_fieldset_load: cannot open %s", path);
+    FileCloser fc{f};
+    return hf_fieldset_read(ctx, f, out, nullptr, (cudaStream_t)stream);
+}
+
+// the checkpoint's array helpers for the server's session files
+bool hf_ckpt_write_i64(FILE *f, const std::vector<int64_t> &v) { return write_host_array(f, "<i8", {(int64_t)v.size()}, v.data(), 8); }
+bool hf_ckpt_write_f32(FILE *f, const std::vector<int64_t> &shape, const float *p) { return write_host_array(f, "<f4", shape, p, 4); }
+bool hf_ckpt_read_i64(FILE *f, std::vector<int64_t> &v) {
+    std::vector<int64_t> shape;
+    std::vector<char> raw;
+    if (!read_host_array(f, "<i8", shape, raw, 8) || shape.size() != 1) return false;
+    v.resize(shape[0]);
+    memcpy(v.data(), raw.data(), raw.size());
+    return true;
+}
+bool hf_ckpt_read_f32(FILE *f, std::vector<int64_t> &shape, std::vector<float> &v) {
+    std::vector<char> raw;
+    if (!read_host_array(f, "<f4", shape, raw, 4)) return false;
+    v.resize(raw.size() / 4);
+    memcpy(v.data(), raw.data(), raw.size());
+    return true;
+}
+int64_t hf_ckpt_magic() { return kCkptMagic; }
+int64_t hf_ckpt_version() { return kCkptVersion; }

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stddef.h>
+#include <stdio.h>
 #include <stdint.h>
 
 #include <vector>
@@ -179,5 +180,16 @@ hf_status hf_set_launch(hf_ctx *ctx, const hf_part *s1, const hf_part *s2, hf_fi
 // `st` (no device-wide synchronisation on create or release)
 hf_status hf_fieldset_create_stream_ordered(hf_ctx *ctx, int n, int R, unsigned flags, cudaStream_t st,
                                             hf_fieldset **out);
+// checkpoints (hf_api.cu): a computed field set as NPY arrays on an open
+// file, and back (device memory stream-ordered on mem_stream if non-null);
+// the NPY array helpers and the file tag for the server's session files
+hf_status hf_fieldset_write(const hf_fieldset *fs, FILE *f, cudaStream_t st);
+hf_status hf_fieldset_read(hf_ctx *ctx, FILE *f, hf_fieldset **out, cudaStream_t mem_stream, cudaStream_t st);
+bool hf_ckpt_write_i64(FILE *f, const std::vector<int64_t> &v);
+bool hf_ckpt_write_f32(FILE *f, const std::vector<int64_t> &shape, const float *p);
+bool hf_ckpt_read_i64(FILE *f, std::vector<int64_t> &v);
+bool hf_ckpt_read_f32(FILE *f, std::vector<int64_t> &shape, std::vector<float> &v);
+int64_t hf_ckpt_magic();
+int64_t hf_ckpt_version();
 hf_status hf_query_on_lane(const hf_fieldset *fs, const float t[3], const float q[4], int k, float out7[7],
                            cudaStream_t st, float *h_out, float *d_out);

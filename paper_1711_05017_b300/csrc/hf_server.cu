@@ -100,6 +100,7 @@ struct Request {
     int n = 0;
     int R = 0;
     unsigned flags = 0;
+    std::vector<float> quats;        // R x 4 as submitted
     std::vector<double> q;           // R x 4, normalised (routing)
     std::vector<int> owner, local;   // rotation -> chunk, index in that chunk's set
     int nchunks = 1;
@@ -576,6 +577,7 @@ extern "C" hf_status hf_server_submit(hf_server *s, int session, const float *h_
     r->n = n;
     r->R = R;
     r->flags = flags;
+    r->quats.assign(h_quat, h_quat + 4 * (size_t)R);
     r->q.resize(4 * (size_t)R);
     for (int i = 0; i < R; ++i) {
         const float *v = h_quat + 4 * (size_t)i;
@@ -847,6 +849,112 @@ extern "C" hf_status hf_server_stats_get(hf_server *s, hf_server_stats *out) {
             for (int c = 0; c < cur->req->nchunks; ++c) resident += cur->get(c) ? 1 : 0;
     }
     out->chunks_resident = resident;
+    return HF_OK;
+}
+
+// ------------------------------------------------- session checkpoints
+// A session's published data (the request's rotations, its chunk routing and
+// every resident chunk's field set) as NPY arrays, so that a restarted
+// server serves it again without rebuilding.
+extern "C" hf_status hf_server_session_save(hf_server *s, int session, const char *path) {
+    if (!s || !path) return srv_fail(HF_EINVAL, "hf_server_session_save: NULL argument");
+    Session *ss = session_at(s, session);
+    if (!ss) return srv_fail(HF_EINVAL, "hf_server_session_save: session %d", session);
+    std::shared_ptr<Published> cur = ss->current();
+    if (!cur) return srv_fail(HF_ENOTREADY, "hf_server_session_save: session %d has no field data", session);
+    const Request &r = *cur->req;
+    std::vector<std::shared_ptr<SetHolder>> held(r.nchunks);  // kept alive while they are written
+    std::vector<int64_t> present(r.nchunks), owner(r.owner.begin(), r.owner.end()), local(r.local.begin(), r.local.end());
+    for (int c = 0; c < r.nchunks; ++c) {
+        held[c] = cur->get(c);
+        present[c] = held[c] ? 1 : 0;
+    }
+    cudaSetDevice(s->device);
+    FILE *f = fopen(path, "wb");
+    if (!f) return srv_fail(HF_EINVAL, "hf_server_session_save: cannot create %s", path);
+    const std::vector<int64_t> meta = {hf_ckpt_magic(), hf_ckpt_version(), HF_CKPT_SESSION, r.n, r.R, r.flags,
+                                       r.nchunks, 0};
+    bool ok = hf_ckpt_write_i64(f, meta) && hf_ckpt_write_f32(f, {r.R, 4}, r.quats.data()) &&
+              hf_ckpt_write_i64(f, owner) && hf_ckpt_write_i64(f, local) && hf_ckpt_write_i64(f, present);
+    hf_status st = ok ? HF_OK : srv_fail(HF_EINVAL, "hf_server_session_save: write failed");
+    cudaStream_t io = nullptr;
+    if (st == HF_OK && cudaStreamCreateWithFlags(&io, cudaStreamNonBlocking) != cudaSuccess)
+        st = srv_fail(HF_ECUDA, "hf_server_session_save: stream");
+    for (int c = 0; c < r.nchunks && st == HF_OK; ++c)
+        if (held[c]) st = hf_fieldset_write(held[c]->fs, f, io);
+    if (io) cudaStreamDestroy(io);
+    fclose(f);
+    return st;
+}
+
+extern "C" hf_status hf_server_session_restore(hf_server *s, int session, const char *path) {
+    if (!s || !path) return srv_fail(HF_EINVAL, "hf_server_session_restore: NULL argument");
+    Session *ss = session_at(s, session);
+    if (!ss) return srv_fail(HF_EINVAL, "hf_server_session_restore: session %d", session);
+    cudaSetDevice(s->device);
+    FILE *f = fopen(path, "rb");
+    if (!f) return srv_fail(HF_EINVAL, "hf_server_session_restore: cannot open %s", path);
+    std::vector<int64_t> meta, owner, local, present, shape;
+    std::vector<float> quats;
+    const bool ok = hf_ckpt_read_i64(f, meta) && meta.size() >= 8 && meta[0] == hf_ckpt_magic() &&
+                    meta[1] == hf_ckpt_version() && meta[2] == HF_CKPT_SESSION;
+    const int n = ok ? (int)meta[3] : 0, R = ok ? (int)meta[4] : 0, C = ok ? (int)meta[6] : 0;
+    if (!ok || n != ss->n || R < 1 || C < 1 || !hf_ckpt_read_f32(f, shape, quats) ||
+        shape != std::vector<int64_t>{R, 4} || !hf_ckpt_read_i64(f, owner) || (int)owner.size() != R ||
+        !hf_ckpt_read_i64(f, local) || (int)local.size() != R || !hf_ckpt_read_i64(f, present) ||
+        (int)present.size() != C) {
+        fclose(f);
+        return srv_fail(HF_EINVAL, "hf_server_session_restore: %s is not a session checkpoint for N=%d", path, ss->n);
+    }
+    auto r = std::make_shared<Request>();
+    r->session = session;
+    r->n = n;
+    r->R = R;
+    r->flags = (unsigned)meta[5];
+    r->nchunks = C;
+    r->quats = quats;
+    r->owner.assign(owner.begin(), owner.end());
+    r->local.assign(local.begin(), local.end());
+    r->q.resize(4 * (size_t)R);
+    for (int i = 0; i < R; ++i) {
+        const float *v = &quats[4 * (size_t)i];
+        const double w = v[0], x = v[1], y = v[2], z = v[3], nq = sqrt(w * w + x * x + y * y + z * z);
+        double *o = &r->q[4 * (size_t)i];
+        o[0] = w / nq; o[1] = x / nq; o[2] = y / nq; o[3] = z / nq;
+    }
+    for (int i = 0; i < R; ++i)
+        if (r->owner[i] < 0 || r->owner[i] >= C) {
+            fclose(f);
+            return srv_fail(HF_EINVAL, "hf_server_session_restore: %s: bad chunk routing", path);
+        }
+    auto pub = std::make_shared<Published>(r);
+    hf_status st = HF_OK;
+    cudaStream_t io = nullptr;
+    if (cudaStreamCreateWithFlags(&io, cudaStreamNonBlocking) != cudaSuccess)
+        st = srv_fail(HF_ECUDA, "hf_server_session_restore: stream");
+    for (int c = 0; c < C && st == HF_OK; ++c) {
+        if (!present[c]) continue;
+        hf_fieldset *fs = nullptr;
+        st = hf_fieldset_read(s->ctx, f, &fs, nullptr, io);
+        if (st != HF_OK) break;
+        if (hf_fieldset_n(fs) != n || hf_fieldset_flags(fs) != (r->flags | HF_E | HF_F)) {
+            hf_fieldset_release(fs);
+            st = srv_fail(HF_EINVAL, "hf_server_session_restore: chunk %d does not match the session", c);
+            break;
+        }
+        pub->last_use[c].store(now_ms());
+        pub->set(c, std::make_shared<SetHolder>(fs, &s->graveyard, hf_fieldset_bytes(n, hf_fieldset_rotations(fs), r->flags)));
+    }
+    if (io) cudaStreamDestroy(io);
+    fclose(f);
+    if (st != HF_OK) return st;  // the sets loaded so far go to the graveyard with pub
+    std::lock_guard<std::mutex> g(s->mu);
+    r->id = s->next_id++;
+    r->t_submit = r->t_done = now_ms();
+    r->state = RQ_DONE;
+    r->chunks_done = C;
+    s->requests[r->id] = r;
+    ss->set_current(pub);
     return HF_OK;
 }
 
