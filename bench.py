@@ -520,8 +520,31 @@ def run_batch(args, local_rank):
     e1.record(stream)
     torch.cuda.synchronize()
     s_ms = e0.elapsed_time(e1) / max(1, steps // 2)
+    # the same batch as ONE launch of the work-queue kernel
+    queue = None
+    try:
+        t0 = time.perf_counter()
+        b.capture_queue(chunk=args.queue_chunk)
+        qcap_s = time.perf_counter() - t0
+        for _ in range(warm):
+            b.launch()
+        b.status()
+        e0.record(stream)
+        for _ in range(steps):
+            b.launch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        items, runs = b.status()
+        q_ms = e0.elapsed_time(e1) / steps
+        queue = {"value": round(total / (q_ms / 1e3), 1), "unit": UNIT, "ms_per_launch": round(q_ms, 2),
+                 "kernel_launches_per_batch": 1, "work_items": items, "item_runs": runs,
+                 "rotations_per_chunk": args.queue_chunk, "capture_s": round(qcap_s, 3), "launches": steps,
+                 "vs_graph": round(g_ms / q_ms, 3)}
+    except hf.HFError as ex:
+        queue = {"error": str(ex)}
     out = {"workload": "64 part pairs, grids 64^3/96^3/128^3 (24/24/16), 1000-8000 skeleton points each, "
                        "256 random rotations per pair, E+F fields", "pairs": len(specs), "rotations": total,
+           "one_launch_queue": queue,
            "graph": {"value": round(total / (g_ms / 1e3), 1), "unit": UNIT, "ms_per_launch": round(g_ms, 2),
                      "slots": b.slots(), "slots_per_size": BATCH_SLOTS, "lanes": BATCH_LANES or b.slots(), "capture_s": round(cap_s, 3),
                      "launches": steps},
@@ -1033,6 +1056,7 @@ def main():
     ap.add_argument("--cpu-rotations", type=int, default=16, help="rotations of the oracle CPU baseline")
     ap.add_argument("--no-tune", action="store_true", help="built-in launch shapes instead of the autotuner's")
     ap.add_argument("--tune-cache", default=None, help="autotuner cache file (read if it has this device and N)")
+    ap.add_argument("--queue-chunk", type=int, default=32, help="rotations per work unit of the one-launch batch")
     ap.add_argument("--batch-steps", type=int, default=5,
                     help="graph launches of the 64-pair uneven batch (0 = skip)")
     ap.add_argument("--precision-rotations", type=int, default=512,

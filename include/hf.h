@@ -471,6 +471,28 @@ hf_status hf_batch_create(hf_ctx *ctx, int npairs, const hf_part *const *s1, con
                           const int *R, unsigned flags, int slots_per_size, hf_batch **out);
 hf_status hf_batch_set_rotations(hf_batch *batch, int pair, const float *h_quat);
 hf_status hf_batch_capture(hf_batch *batch, int lanes);
+/* The batch as ONE launch of a work-queue kernel instead of a graph of
+ * per-size kernels (the uneven-batch precompute of Section 4.2 in one
+ * launch, recorded as a CUDA graph with the reset of its counters):
+ *   - every pair's rotations are cut into chunks of `chunk` rotations (0:
+ *     32); each chunk's pass A, B and C blocks are work items, and every
+ *     block of the launch takes the next item by ticket from a device
+ *     counter, running it with the per-pass kernels' code (256 threads);
+ *   - an item waits (bounded, spin_limit polls, 0: about two seconds) only
+ *     for items ticketed before it: its pass's producer, and the previous
+ *     chunk using its intermediates or its output rotations;
+ *   - E and F only, grids 64, 96 and 128; the results equal the per-pass
+ *     kernels' bit for bit.
+ * self_test bit 0 plants a wait that nothing satisfies, to exercise the
+ * bounded wait: hf_batch_status then reports HF_ETIMEOUT, and the context
+ * stays usable.  hf_batch_launch runs it.  Errors: HF_EUNSUPPORTED (flags,
+ * sizes), HF_ENOTREADY (a pair without rotations), HF_EINVAL, HF_ENOMEM,
+ * HF_ECUDA. */
+hf_status hf_batch_capture_queue(hf_batch *b, int chunk, long long spin_limit, int self_test);
+/* Synchronise `stream` and report the last one-launch run: HF_OK, or
+ * HF_ETIMEOUT if a wait ran out; *items and *runs (may be NULL) receive the
+ * size of its work queue. */
+hf_status hf_batch_status(hf_batch *b, hf_stream stream, int *items, int *runs);
 hf_status hf_batch_launch(hf_batch *batch, hf_stream stream);
 hf_status hf_batch_fieldset(const hf_batch *batch, int pair, const hf_fieldset **out);
 int hf_batch_slots(const hf_batch *batch);

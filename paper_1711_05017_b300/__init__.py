@@ -327,8 +327,20 @@ class Batch:
         (0: one per slot)."""
         B.check(B.lib().hf_batch_capture(self.handle, int(lanes)))
 
+    def capture_queue(self, chunk=0, spin_limit=0, self_test=0):
+        """Record the whole batch as ONE launch of the work-queue kernel
+        (hf_batch_capture_queue: E + F, grids 64/96/128)."""
+        B.check(B.lib().hf_batch_capture_queue(self.handle, int(chunk), int(spin_limit), int(self_test)))
+
     def launch(self, stream=None):
         B.check(B.lib().hf_batch_launch(self.handle, _stream_ptr(stream)))
+
+    def status(self, stream=None):
+        """hf_batch_status after a one-launch run: (items, runs) of its
+        queue; raises HFError(HF_ETIMEOUT) if a bounded wait ran out."""
+        it, ru = ctypes.c_int(), ctypes.c_int()
+        B.check(B.lib().hf_batch_status(self.handle, _stream_ptr(stream), ctypes.byref(it), ctypes.byref(ru)))
+        return it.value, ru.value
 
     def slots(self):
         return B.lib().hf_batch_slots(self.handle)

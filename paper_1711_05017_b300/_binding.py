@@ -90,6 +90,8 @@ SIGNATURES = {
     "hf_batch_set_rotations": (_i, [_vp, _i, _fp]),
     "hf_batch_capture": (_i, [_vp, _i]),
     "hf_batch_launch": (_i, [_vp, _vp]),
+    "hf_batch_capture_queue": (_i, [_vp, _i, ctypes.c_longlong, _i]),
+    "hf_batch_status": (_i, [_vp, _vp, _ip, _ip]),
     "hf_batch_fieldset": (_i, [_vp, _i, ctypes.POINTER(_vp)]),
     "hf_batch_slots": (_i, [_vp]),
     "hf_batch_release": (None, [_vp]),

@@ -1048,6 +1048,15 @@ int hf_ctx_device(const hf_ctx *c) { return c ? c->device : 0; }
 bool hf_fieldset_is_ready(const hf_fieldset *fs) { return fs && fs->ready; }
 void hf_fieldset_mark_ready(hf_fieldset *fs) { fs->ready = true; }
 double *hf_fieldset_device_quats(hf_fieldset *fs) { return fs->d_quat; }
+hf::FieldPtrs hf_fieldset_fields(hf_fieldset *fs, int rot) {
+    const size_t n3 = (size_t)fs->n * fs->n * fs->n, rs = (size_t)fs->nf * n3;
+    float *base = fs->data + (size_t)rot * rs;
+    return hf::FieldPtrs{base, base + n3, base + 2 * n3, base + 3 * n3, rs};
+}
+cudaTextureObject_t hf_part_texture(const hf_part *p) { return p->tex; }
+const int *hf_part_support(const hf_part *p) { return p->box; }
+const float2 *hf_part_spectrum(const hf_part *p) { return p->spec; }
+int hf_part_role(const hf_part *p) { return p->role; }
 
 extern "C" int hf_fieldset_n(const hf_fieldset *fs) { return fs ? fs->n : 0; }
 extern "C" int hf_fieldset_rotations(const hf_fieldset *fs) { return fs ? fs->R : 0; }

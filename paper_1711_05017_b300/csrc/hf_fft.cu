@@ -224,16 +224,19 @@ __device__ __forceinline__ void tex_resample(cudaTextureObject_t t, const float 
     }
 }
 
+// The body of one pass A block, plane z of rotation r (a kernel's blockIdx
+// or a persistent kernel's work item); sm is the block's dynamic shared memory.
 template <int N, int SRC>
-__global__ void __launch_bounds__(PassA<N>::NT, SRC == SRC_TEX ? 2 : PassA<N>::MINB)
-    passA_kernel(const float *__restrict__ rho, const float *__restrict__ rot9, float2 *__restrict__ X1,
-                 cudaTextureObject_t tex, const int *__restrict__ box) {
+__device__ __forceinline__ void passA_body(const float *__restrict__ rho, const float *__restrict__ rot9,
+                                           float2 *__restrict__ X1, cudaTextureObject_t tex,
+                                           const int *__restrict__ box, unsigned zu, unsigned ru) {
+    __builtin_assume(zu < (1u << 16) && ru < (1u << 16));  // the ranges of the blockIdx they stand for
+    const int z = (int)zu, r = (int)ru;
     constexpr int H = PassA<N>::H, HALF = PassA<N>::HALF, NT = PassA<N>::NT;
     extern __shared__ float2 sm[];
     float2 *P = sm;            // [N rows y][H]  (row = N reals = N/2 complex + Nyquist slot)
     float2 *twN = P + N * H;   // exp(-2 pi i j / N)
     float2 *twH = twN + N;     // exp(-2 pi i j / (N/2))
-    const int z = blockIdx.x, r = blockIdx.y;
     float *Pf = reinterpret_cast<float *>(P);
 
     if constexpr (SRC == SRC_PLANES) {
@@ -318,6 +321,13 @@ __global__ void __launch_bounds__(PassA<N>::NT, SRC == SRC_TEX ? 2 : PassA<N>::M
     __syncthreads();
     float2 *dst = X1 + ((size_t)r * N + z) * N * H;
     for (int i = threadIdx.x; i < N * H; i += NT) dst[i] = P[i];
+}
+
+template <int N, int SRC>
+__global__ void __launch_bounds__(PassA<N>::NT, SRC == SRC_TEX ? 2 : PassA<N>::MINB)
+    passA_kernel(const float *__restrict__ rho, const float *__restrict__ rot9, float2 *__restrict__ X1,
+                 cudaTextureObject_t tex, const int *__restrict__ box) {
+    passA_body<N, SRC>(rho, rot9, X1, tex, box, blockIdx.x, blockIdx.y);
 }
 
 // ------------------------------------------------------- rotated resample
@@ -515,13 +525,28 @@ constexpr int kSpecInFlight = 4;  // samples whose gathers a thread issues toget
 // MODE 1: forward only, spectrum * scale -> spec[kz*][ky*][kx*]  (stationary part)
 // MODE 2: as MODE 0 with the rotated spectrum interpolated from a table
 //         instead of transformed from resampled planes
-template <int N, int MODE>
-__global__ void __launch_bounds__(PassB<N>::NT, MODE == 2 ? 2 : PassB<N>::MINB) passB_kernel(const float2 *__restrict__ X1,
-                                                                              const float2 *__restrict__ R1hat,
-                                                                              float2 *__restrict__ Y1,
-                                                                              float2 *__restrict__ Y2, float scale,
-                                                                              SpecSrc spec,
-                                                                              const float *__restrict__ rot9) {
+// Loads of a pass's input intermediates: through the read-only path in a
+// pass of its own (the producer was an earlier launch), at L2 (.cg) in the
+// persistent kernel, where the producer is another block of the same launch
+// and the non-coherent caches could hold an earlier chunk's lines.
+template <bool COH>
+__device__ __forceinline__ float2 ld_inter(const float2 *p) {
+    if constexpr (COH) return __ldcg(p);
+    else return __ldg(p);
+}
+template <bool COH>
+__device__ __forceinline__ float2 ldg_inter(const float2 *p) {
+    if constexpr (COH) return __ldcg(p);
+    else return __ldg(p);
+}
+
+// The body of one pass B block: column tile bx of rotation r.
+template <int N, int MODE, bool COH = false>
+__device__ __forceinline__ void passB_body(const float2 *__restrict__ X1, const float2 *__restrict__ R1hat,
+                                           float2 *__restrict__ Y1, float2 *__restrict__ Y2, float scale,
+                                           const SpecSrc &spec, const float *__restrict__ rot9, unsigned bx,
+                                           unsigned r) {
+    __builtin_assume(bx < (1u << 24) && r < (1u << 16));  // the ranges of the blockIdx they stand for
     constexpr int H = PassB<N>::H, R1 = PassB<N>::R1, R2 = PassB<N>::R2, CW = PassB<N>::CW,
                   KPT = PassB<N>::KPT;
     constexpr size_t NH = (size_t)N * H;
@@ -530,9 +555,8 @@ __global__ void __launch_bounds__(PassB<N>::NT, MODE == 2 ? 2 : PassB<N>::MINB) 
     float2 *G = sm + (size_t)N * CW;     // Gz's [n2][k1][c]
     float2 *twN = G + (size_t)N * CW;
     const int c = threadIdx.x % CW, g = threadIdx.x / CW;
-    size_t f = (size_t)blockIdx.x * CW + c;
+    size_t f = (size_t)bx * CW + c;
     bool active = true;  // every column is live in modes 0 and 1
-    const int r = blockIdx.y;
     load_tw<N>(twN);
     float2 X[KPT][R2];
     if constexpr (MODE == 2) {
@@ -541,7 +565,7 @@ __global__ void __launch_bounds__(PassB<N>::NT, MODE == 2 ? 2 : PassB<N>::MINB) 
         // the Nyquist column kx = N/2 is zero in this mode and is written by
         // the first tile of the row
         constexpr int HALF = N / 2, TILES = (HALF + CW - 1) / CW;
-        const int kys = blockIdx.x / TILES, tile = blockIdx.x % TILES;
+        const int kys = bx / TILES, tile = bx % TILES;
         const int kx = tile * CW + c;
         active = kx < HALF;
         f = (size_t)kys * H + (active ? xslot<N>(kx) : 0);
@@ -580,7 +604,7 @@ __global__ void __launch_bounds__(PassB<N>::NT, MODE == 2 ? 2 : PassB<N>::MINB) 
             float2 v[R1];
             const float2 *src = X1 + (size_t)r * N * NH + f;
 #pragma unroll
-            for (int n1 = 0; n1 < R1; ++n1) v[n1] = src[(size_t)(R2 * n1 + g) * NH];
+            for (int n1 = 0; n1 < R1; ++n1) v[n1] = ld_inter<COH>(src + (size_t)(R2 * n1 + g) * NH);
             __syncthreads();  // twiddles in place
             RegDFT<R1, -1>::run(v);
 #pragma unroll
@@ -651,6 +675,16 @@ __global__ void __launch_bounds__(PassB<N>::NT, MODE == 2 ? 2 : PassB<N>::MINB) 
 #pragma unroll
             for (int n1 = 0; n1 < R1; ++n1) d2[(size_t)(R2 * n1 + g) * NH] = v[n1];
     }
+}
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(PassB<N>::NT, MODE == 2 ? 2 : PassB<N>::MINB) passB_kernel(const float2 *__restrict__ X1,
+                                                                              const float2 *__restrict__ R1hat,
+                                                                              float2 *__restrict__ Y1,
+                                                                              float2 *__restrict__ Y2, float scale,
+                                                                              SpecSrc spec,
+                                                                              const float *__restrict__ rot9) {
+    passB_body<N, MODE>(X1, R1hat, Y1, Y2, scale, spec, rot9, blockIdx.x, blockIdx.y);
 }
 
 
@@ -928,13 +962,12 @@ __device__ __forceinline__ void x_pass(const float2 *planeA, const float2 *plane
 // transformed in place in two small steps that ride along with stage 2's
 // read and write phases (one warp each), so it costs no barrier of its own.
 // MUL multiplies input row s by i pi ky~(s) on the way in (forms Gy from S').
-template <int N, bool MUL, bool CTW = true>
+template <int N, bool MUL, bool CTW = true, int NT = PassC<N>::NT, bool COH = false>
 __device__ __forceinline__ void y_inverse_plane(const float2 *__restrict__ src, float2 *plane, const float2 *twN) {
-    constexpr int H = N / 2 + 1, HALF = N / 2, R1 = Fact<N>::R1, R2 = Fact<N>::R2, PW = PassC<N>::PW,
-                  NT = PassC<N>::NT;
+    constexpr int H = N / 2 + 1, HALF = N / 2, R1 = Fact<N>::R1, R2 = Fact<N>::R2, PW = PassC<N>::PW;
     static_assert(NT >= N && NT >= 32 + R2, "one Nyquist value per thread; Nyquist steps on warps 0 and 1");
     float2 nyq = make_float2(0.f, 0.f);
-    if (threadIdx.x < N) nyq = __ldg(src + (size_t)threadIdx.x * H + HALF);
+    if (threadIdx.x < N) nyq = ldg_inter<COH>(src + (size_t)threadIdx.x * H + HALF);
     // stage 1: items (c, k1), slots R2 k1 + k2
 #pragma unroll 1
     for (int w = threadIdx.x; w < HALF * R1; w += NT) {
@@ -943,7 +976,7 @@ __device__ __forceinline__ void y_inverse_plane(const float2 *__restrict__ src, 
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2) {
             const int sl = R2 * k1 + k2;
-            v[k2] = __ldg(src + (size_t)sl * H + c);
+            v[k2] = ldg_inter<COH>(src + (size_t)sl * H + c);
             if constexpr (MUL) v[k2] = cmul_is(v[k2], signed_k_mult<N>(slot_freq<N>(sl)));
         }
         RegDFT<R2, +1>::run(v);
@@ -1013,33 +1046,33 @@ __device__ __forceinline__ void y_inverse_plane(const float2 *__restrict__ src, 
 //   S'  (again, from L2) times i pi ky~ = Gy -> y inverse -> rows p and
 //       p + N/2 paired in one complex x inverse    -> Fy
 //   Gz' -> y inverse -> rows paired likewise          -> Fz
-template <int N, bool TQ>
-__global__ void __launch_bounds__(PassC<N>::NT, PassC<N>::MINB) passC_kernel(const float2 *__restrict__ Y1,
-                                                                              const float2 *__restrict__ Y2,
-                                                                              FieldPtrs out,
-                                                                              const float2 *__restrict__ YT,
-                                                                              size_t yt_stride) {
-    constexpr int H = PassC<N>::H, PW = PassC<N>::PW, RB = PassC<N>::RB, TP = PassC<N>::TP,
-                  NT = PassC<N>::NT, HALF = N / 2;
+// The body of one pass C block: plane z of rotation r.  NT threads (the
+// kernel's 512 at N = 128, a persistent block's 256); COH as for ld_inter.
+template <int N, bool TQ, int NT = PassC<N>::NT, bool COH = false>
+__device__ __forceinline__ void passC_body(const float2 *__restrict__ Y1, const float2 *__restrict__ Y2,
+                                           const FieldPtrs &out, const float2 *__restrict__ YT, size_t yt_stride,
+                                           unsigned zu, unsigned ru) {
+    __builtin_assume(zu < (1u << 16) && ru < (1u << 16));  // the ranges of the blockIdx they stand for
+    const int z = (int)zu, r = (int)ru;
+    constexpr int H = PassC<N>::H, PW = PassC<N>::PW, RB = PassC<N>::RB, TP = PassC<N>::TP, HALF = N / 2;
     extern __shared__ float2 sm[];
     float2 *plane = sm;                       // [N][PW]
     float2 *Tb = plane + (size_t)N * PW;      // [RB][TP]
     float2 *twN = Tb + (size_t)RB * TP;
-    const int z = blockIdx.x, r = blockIdx.y;
     const float2 *s1 = Y1 + ((size_t)r * N + z) * N * H;
     const size_t fo = (size_t)r * out.rot_stride + (size_t)z * N * N;
     load_tw<N>(twN);
     __syncthreads();
     // E + i Fx
-    y_inverse_plane<N, false, !TQ>(s1, plane, twN);
+    y_inverse_plane<N, false, !TQ, NT, COH>(s1, plane, twN);
     // with the torque phases (TQ) this CTA reads its force rows back: keep them in L2
     x_pass<N, 0, PW, RB, TP, NT, N, !TQ, false, TQ>(plane, plane, 0, 0, Tb, twN, out.E + fo, out.Fx + fo);
     // Fy from Gy = i pi ky~ S'
-    y_inverse_plane<N, true, !TQ>(s1, plane, twN);
+    y_inverse_plane<N, true, !TQ, NT, COH>(s1, plane, twN);
     x_pass<N, 1, PW, RB, TP, NT, HALF, !TQ, TQ, TQ>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, out.Fy + fo,
                                       out.Fy + fo + (size_t)HALF * N);
     // Fz
-    y_inverse_plane<N, false, !TQ>(Y2 + ((size_t)r * N + z) * N * H, plane, twN);
+    y_inverse_plane<N, false, !TQ, NT, COH>(Y2 + ((size_t)r * N + z) * N * H, plane, twN);
     x_pass<N, 1, PW, RB, TP, NT, HALF, !TQ, TQ, TQ>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, out.Fz + fo,
                                       out.Fz + fo + (size_t)HALF * N);
     if constexpr (TQ) {
@@ -1047,12 +1080,21 @@ __global__ void __launch_bounds__(PassC<N>::NT, PassC<N>::MINB) passC_kernel(con
         float *T[3] = {out.Tx, out.Ty, out.Tz};
 #pragma unroll 1
         for (int a = 0; a < 3; ++a) {
-            y_inverse_plane<N, false, !TQ>(YT + a * yt_stride + ((size_t)r * N + z) * N * H, plane, twN);
+            y_inverse_plane<N, false, !TQ, NT, COH>(YT + a * yt_stride + ((size_t)r * N + z) * N * H, plane, twN);
             const TorqueCorr tc{{out.Fx + fo, out.Fy + fo, out.Fz + fo}, a, z < HALF ? z : z - N, HALF};
             x_pass<N, 1, PW, RB, TP, NT, HALF, !TQ>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, T[a] + fo,
                                               T[a] + fo + (size_t)HALF * N, &tc);
         }
     }
+}
+
+template <int N, bool TQ>
+__global__ void __launch_bounds__(PassC<N>::NT, PassC<N>::MINB) passC_kernel(const float2 *__restrict__ Y1,
+                                                                              const float2 *__restrict__ Y2,
+                                                                              FieldPtrs out,
+                                                                              const float2 *__restrict__ YT,
+                                                                              size_t yt_stride) {
+    passC_body<N, TQ>(Y1, Y2, out, YT, yt_stride, blockIdx.x, blockIdx.y);
 }
 
 // the stationary moment fields G_a = (u x F)_a / h^3 (F = -h^3 grad rho1)
@@ -1449,6 +1491,115 @@ static cudaError_t launch_spectral_complete(const float2 *spec, float2 *table, c
 template <int N>
 static cudaError_t launch_unpermute(const float2 *spec, float2 *out, cudaStream_t st) {
     unpermute_spectrum_kernel<N><<<148, 256, 0, st>>>(spec, out);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------- one-launch field build
+// A whole batch of pairs in one launch over a device work queue: each block
+// takes the next item by ticket (a global counter) and runs it with the same
+// bodies as the per-pass kernels (256 threads: pass C at 128^3 with 256
+// instead of 512); an item is one block's worth of pass A, B or C of one
+// (pair, rotation chunk).  The launch has one block per item and no block
+// loops: a looping block lets the compiler hoist the bodies' per-thread
+// terms out of the loop, and with every body in one function that spilled
+// 2.1 KB per thread at the 128-register cap; the hardware block scheduler
+// keeps the SMs fed instead.  Tickets go out in the order blocks start, and
+// an item waits only for items with smaller tickets (its pass's producers,
+// or the previous user of its intermediates or outputs), so every wait is
+// for a block that has already started.  Waits are bounded: after
+// spin_limit polls the block sets the status word to PERSIST_TIMEOUT, and
+// every block that starts later returns at once.
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_relaxed_s32(const int *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+constexpr size_t kPersistSmem =
+    cmax(cmax(cmax(PassA<64>::smem, PassA<96>::smem), cmax(PassA<128>::smem, PassB<64>::smem)),
+         cmax(cmax(PassB<96>::smem, PassB<128>::smem), cmax(PassC<64>::smem, cmax(PassC<96>::smem, PassC<128>::smem))));
+
+template <int N>
+__device__ __forceinline__ void persist_item(const PersistSeg &g, int local) {
+    static_assert(PassA<N>::NT == kPersistNT && PassB<N>::NT == kPersistNT, "256-thread passes A and B");
+    constexpr int BT = N * PassB<N>::H / PassB<N>::CW;  // pass B column tiles per rotation
+    if (g.pass == 0) {
+        passA_body<N, SRC_TEX>(nullptr, g.rot9, g.X1, g.tex, g.box, local % N, local / N);
+    } else if (g.pass == 1) {
+        passB_body<N, 0, true>(g.X1, g.R1hat, g.Y1, g.Y2, 0.f, SpecSrc{nullptr, 0, 0}, nullptr, local % BT,
+                               local / BT);
+    } else {
+        passC_body<N, false, kPersistNT, true>(g.Y1, g.Y2, g.out, nullptr, 0, local % N, local / N);
+    }
+}
+
+__global__ void __launch_bounds__(kPersistNT, 2)
+    queue_kernel(const PersistSeg *__restrict__ segs, const int *__restrict__ lut, int nseg, int total,
+                 unsigned *queue, unsigned *counters, int *status, long long spin_limit) {
+    __shared__ int s_item, s_seg, s_stop;
+    if (threadIdx.x == 0) {
+        const int it = (int)atomicAdd(queue, 1u);
+        int stop = it >= total || ld_relaxed_s32(status) != PERSIST_OK;
+        int sg = 0;
+        if (!stop) {
+            // the run holding item it: from the run holding item it & ~255, forward
+            sg = __ldg(lut + (it >> 8));
+            while (sg + 1 < nseg && __ldg(&segs[sg + 1].base) <= it) ++sg;
+            for (int d = 0; d < 2 && !stop; ++d) {
+                const int c = segs[sg].dep[d];
+                if (c < 0) continue;
+                const unsigned target = (unsigned)segs[sg].dep_target[d];
+                long long k = 0;
+                while (ld_acquire_u32(counters + c) < target) {
+                    if (++k > spin_limit || ld_relaxed_s32(status) != PERSIST_OK) {
+                        atomicCAS(status, PERSIST_OK, PERSIST_TIMEOUT);
+                        stop = 1;
+                        break;
+                    }
+                    __nanosleep(256);
+                }
+            }
+        }
+        s_item = it;
+        s_seg = sg;
+        s_stop = stop;
+    }
+    __syncthreads();
+    if (s_stop) return;
+    const PersistSeg &g = segs[s_seg];
+    const int local = s_item - g.base + g.first;
+    if (g.n == 64) persist_item<64>(g, local);
+    else if (g.n == 96) persist_item<96>(g, local);
+    else persist_item<128>(g, local);
+    __syncthreads();  // every thread's writes of the item are done
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(counters + g.done, 1u);
+    }
+}
+
+cudaError_t persist_init() {
+    cudaError_t e = cudaFuncSetAttribute(queue_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPersistSmem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(queue_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+}
+size_t persist_smem() { return kPersistSmem; }
+int persist_blocks_per_sm() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, queue_kernel, kPersistNT, kPersistSmem) != cudaSuccess)
+        return 0;
+    return nb;
+}
+cudaError_t run_persistent(const PersistSeg *d_segs, const int *d_lut, int nseg, int total, unsigned *d_queue,
+                           unsigned *d_counters, int *d_status, long long spin_limit, cudaStream_t st) {
+    queue_kernel<<<total, kPersistNT, kPersistSmem, st>>>(d_segs, d_lut, nseg, total, d_queue, d_counters, d_status,
+                                                           spin_limit);
     return cudaGetLastError();
 }
 

@@ -19,6 +19,27 @@ struct FieldPtrs {
     float *Tx = nullptr, *Ty = nullptr, *Tz = nullptr;  // analytic torque fields (HF_TA), else unused
 };
 
+// One run of work items of the persistent field-build kernel: `count`
+// items of one pass (0 A, 1 B, 2 C) at one grid size over one pair's
+// rotation chunk, items first .. first + count - 1 of that pass.  A pass-A
+// or pass-C item is one (plane, rotation), a pass-B item one (column tile,
+// rotation).  Before an item runs, counters dep[d] must reach dep_target[d];
+// each finished item adds 1 to counter `done`.
+struct PersistSeg {
+    int pass, n;
+    int base, count, first;
+    int dep[2], dep_target[2];
+    int done;
+    const float *rot9;           // the chunk's rotations (row-major 3 x 3 each)
+    cudaTextureObject_t tex;     // the moving part's gather texture
+    const int *box;              // and its support
+    const float2 *R1hat;         // the stationary spectrum
+    float2 *X1, *Y1, *Y2;        // the chunk's intermediates
+    FieldPtrs out;               // fields of the chunk's first rotation
+};
+constexpr int kPersistNT = 256;
+enum { PERSIST_OK = 0, PERSIST_TIMEOUT = 1 };
+
 struct Rot9 {
     float r[9];  // row-major rotation matrix
 };
@@ -51,6 +72,15 @@ void set_last_error(const char *msg);
 
 // hf_fft.cu
 cudaError_t fft_init_attrs(int n);
+// the one-launch field build over a table of item runs (sorted by base;
+// total items in all; lut[i] = the run holding item 256 i), with its queue
+// head, counters and status word (all zero before a launch); the blocks per
+// SM it runs at
+cudaError_t persist_init();
+int persist_blocks_per_sm();
+size_t persist_smem();
+cudaError_t run_persistent(const PersistSeg *d_segs, const int *d_lut, int nseg, int total, unsigned *d_queue,
+                           unsigned *d_counters, int *d_status, long long spin_limit, cudaStream_t st);
 cudaError_t run_passA(int n, const float *rho, const float *rot9, float2 *X1, int nrot, cudaStream_t st);
 // pass A from planes already in memory: plane z of rotation r at planes + (r N + z) N^2
 cudaError_t run_passA_planes(int n, const float *planes, float2 *X1, int nrot, cudaStream_t st);
@@ -167,6 +197,14 @@ int hf_ctx_device(const hf_ctx *c);
 bool hf_fieldset_is_ready(const hf_fieldset *fs);
 void hf_fieldset_mark_ready(hf_fieldset *fs);
 double *hf_fieldset_device_quats(hf_fieldset *fs);
+// the E, Fx, Fy, Fz pointers of rotation rot of a set (rot_stride per rotation)
+hf::FieldPtrs hf_fieldset_fields(hf_fieldset *fs, int rot);
+// a part's gather texture and support box (moving), stored spectrum
+// (stationary) and role
+cudaTextureObject_t hf_part_texture(const hf_part *p);
+const int *hf_part_support(const hf_part *p);
+const float2 *hf_part_spectrum(const hf_part *p);
+int hf_part_role(const hf_part *p);
 // host preparation of a rotation set (float32 matrices, normalised float64
 // quaternions, torque neighbours and operators); -1 for a bad quaternion,
 // else the number of rank-deficient neighbourhoods

@@ -210,3 +210,110 @@ def test_autotune_choice_cache_and_results(hf, tmp_path):
     with pytest.raises(hf.HFError) as e:
         ctx2.tune_set(256, 4, pencil=False)
     assert e.value.status == B.HF_EUNSUPPORTED
+
+
+# ------------------------------------------------ one launch over a work queue
+
+def _queue_pairs(hf, ctx, spec):
+    pairs, quats = [], []
+    for i, (n, R) in enumerate(spec):
+        p1, p2, _ = make_pair(hf, ctx, n, 70 + i)
+        pairs.append((p1, p2))
+        quats.append(synth.random_quaternions(80 + i, R).astype(np.float32))
+    return pairs, quats
+
+
+def test_one_launch_queue_equals_per_pair_builds(hf):
+    """Pairs of 64^3, 96^3 and 128^3 with ragged rotation counts, built by
+    ONE launch of the work-queue kernel: every field of every rotation equals
+    the pair's own per-pass build bit for bit, on two launches in a row."""
+    ctx = hf.Context(0)
+    flags = hf.HF_E | hf.HF_F
+    spec = [(64, 40), (128, 24), (96, 33), (64, 17), (128, 20)]
+    pairs, quats = _queue_pairs(hf, ctx, spec)
+    b = hf.Batch(ctx, pairs, [R for _, R in spec], flags)
+    for i, q in enumerate(quats):
+        b.set_rotations(i, q)
+    b.capture_queue(chunk=16)
+    for launch in range(2):
+        b.launch()
+        items, runs = b.status()
+        assert items > 0 and runs > 0
+        for i, (pr, q) in enumerate(zip(pairs, quats)):
+            ref = plain(hf, ctx, pr, q, flags)
+            got = b.fieldset(i)
+            assert np.array_equal(all_fields(got, len(q), 4), all_fields(ref, len(q), 4)), (launch, i)
+            ref.release()
+    b.release()
+
+
+def test_one_launch_queue_matches_the_oracle(hf):
+    """One 64^3 pair of the one-launch build against the FP64 oracle."""
+    ctx = hf.Context(0)
+    n, R = 64, 12
+    s1, s2 = synth.c2_pair(91)
+    r1 = oracle.splat(n, s1.pts[:600], s1.sigma[:600]).astype(np.float32)
+    r2 = oracle.splat(n, s2.pts[:600], s2.sigma[:600]).astype(np.float32)
+    p = (ctx.part(cuda(r1), hf.HF_STATIONARY), ctx.part(cuda(r2), hf.HF_MOVING))
+    q = synth.random_quaternions(92, R).astype(np.float32)
+    b = hf.Batch(ctx, [p], [R], hf.HF_E | hf.HF_F)
+    b.set_rotations(0, q)
+    b.capture_queue(chunk=5)
+    b.launch()
+    b.status()
+    fs = b.fieldset(0)
+    for r in (0, 6, 11):
+        qq = q[r].astype(np.float64)
+        Rm = oracle.quat_to_rot(qq / np.linalg.norm(qq)).astype(np.float32).astype(np.float64)
+        ref = oracle.fields(r1.astype(np.float64), oracle.resample(r2.astype(np.float64), Rm))
+        for f in range(4):
+            got = host(fs.get(r, f)).astype(np.float64)
+            assert np.abs(got - ref[f]).max() <= TOL * np.abs(ref[f]).max(), (r, f)
+    b.release()
+
+
+def test_one_launch_shared_output_sets_hold_the_last_pair(hf):
+    """Three 64^3 pairs sharing one output set: items of a later pair wait
+    for the earlier pair's same rotations, so after the launch the set holds
+    the last pair's fields exactly."""
+    ctx = hf.Context(0)
+    flags = hf.HF_E | hf.HF_F
+    spec = [(64, 20), (64, 20), (64, 20)]
+    pairs, quats = _queue_pairs(hf, ctx, spec)
+    b = hf.Batch(ctx, pairs, [20, 20, 20], flags, slots_per_size=1)
+    assert b.slots() == 1
+    for i, q in enumerate(quats):
+        b.set_rotations(i, q)
+    b.capture_queue(chunk=8)
+    b.launch()
+    b.status()
+    ref = plain(hf, ctx, pairs[2], quats[2], flags)
+    assert np.array_equal(all_fields(b.fieldset(2), 20, 4), all_fields(ref, 20, 4))
+    ref.release()
+    b.release()
+
+
+def test_one_launch_bounded_wait_reports_timeout(hf):
+    """A planted wait that nothing satisfies runs out its bounded poll count:
+    the launch stops early, the status says HF_ETIMEOUT, and the same context
+    then builds correctly."""
+    from paper_1711_05017_b300 import _binding as B
+    ctx = hf.Context(0)
+    flags = hf.HF_E | hf.HF_F
+    spec = [(64, 16), (96, 16)]
+    pairs, quats = _queue_pairs(hf, ctx, spec)
+    b = hf.Batch(ctx, pairs, [16, 16], flags)
+    for i, q in enumerate(quats):
+        b.set_rotations(i, q)
+    b.capture_queue(chunk=8, spin_limit=20000, self_test=1)
+    b.launch()
+    with pytest.raises(hf.HFError) as e:
+        b.status()
+    assert e.value.status == B.HF_ETIMEOUT
+    b.capture_queue(chunk=8)
+    b.launch()
+    b.status()
+    ref = plain(hf, ctx, pairs[1], quats[1], flags)
+    assert np.array_equal(all_fields(b.fieldset(1), 16, 4), all_fields(ref, 16, 4))
+    ref.release()
+    b.release()
