@@ -227,7 +227,9 @@ def run_ours(args, rank, world, local_rank):
     tune = None
     if not args.no_tune:  # launch shape for this grid size, timed on this device or read from --tune-cache
         c, pen, rps = ctx.autotune(n, args.tune_cache)
-        tune = {"chunk": c, "pipeline": "pencil" if pen else "slab", "ef_rot_per_s": round(rps, 1)}
+        tb, tc = ctx.tune_tiles(n)
+        tune = {"chunk": c, "pipeline": "pencil" if pen else "slab", "tile_b": tb, "tile_c": tc,
+                "ef_rot_per_s": round(rps, 1)}
     fs = ctx.fieldset(n, R, hf.HF_E | hf.HF_F | hf.HF_T)
     tq = torch.as_tensor(tq_h, device=dev)
     qout = torch.empty((N_QUERY, 7), device=dev)
@@ -472,8 +474,12 @@ def run_batch(args, local_rank):
     t0 = time.perf_counter()
     with tempfile.TemporaryDirectory() as d:
         for n in sorted(set(p.n for p in specs)):
-            c, pen, rps = ctx.autotune(n, os.path.join(d, "tune.txt"))
-            tune[n] = {"chunk": c, "pipeline": "pencil" if pen else "slab", "rot_per_s": round(rps, 1)}
+            c, pen, rps = ctx.autotune(n, os.path.join(d, "tune.json"))
+            tb, tc = ctx.tune_tiles(n)
+            tune[n] = {"chunk": c, "pipeline": "pencil" if pen else "slab", "tile_b": tb, "tile_c": tc,
+                       "rot_per_s": round(rps, 1)}
+        with open(os.path.join(d, "tune.json")) as f:
+            tune["cache"] = json.load(f)["tune"]
     tune_s = time.perf_counter() - t0
     pairs, quats = [], []
     for p in specs:

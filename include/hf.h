@@ -514,6 +514,14 @@ hf_status hf_autotune(hf_ctx *ctx, int n, const char *cache_path, int *chunk, in
                       double *rot_per_s);
 hf_status hf_tune_set(hf_ctx *ctx, int n, int chunk, int pencil);
 hf_status hf_tune_get(const hf_ctx *ctx, int n, int *chunk, int *pencil, double *rot_per_s);
+/* Launch shapes of passes B and C for grid n (the autotuner's compiled
+ * candidates, kept in the context like the chunk): tile_b 0 = 32 columns
+ * per CTA, 1 = 16; tile_c 0 = the built-in rows per x batch and threads,
+ * 1 = 16 rows per x batch, 2 = 256 threads per CTA (N = 128 only); other
+ * than 0 only for N = 64, 96, 128.  set != 0 stores *tile_b / *tile_c (the
+ * fields do not change, only their speed), else reads them.  Errors:
+ * HF_EINVAL, HF_EUNSUPPORTED. */
+hf_status hf_tune_tiles(hf_ctx *ctx, int n, int set, int *tile_b, int *tile_c);
 
 /* Number of tensor-core stage thread blocks whose bounded wait for their own
  * matrix operations gave up since the last reset (each such block wrote no

@@ -131,6 +131,16 @@ class Context:
     def tune_set(self, n, chunk, pencil=False):
         B.check(B.lib().hf_tune_set(self.handle, int(n), int(chunk), 1 if pencil else 0))
 
+    def tune_tiles(self, n, tiles=None):
+        """hf_tune_tiles: read, or set to (tile_b, tile_c), the launch shapes
+        of passes B and C at grid n."""
+        tb, tc = ctypes.c_int(), ctypes.c_int()
+        if tiles is not None:
+            tb.value, tc.value = int(tiles[0]), int(tiles[1])
+        B.check(B.lib().hf_tune_tiles(self.handle, int(n), 1 if tiles is not None else 0, ctypes.byref(tb),
+                                      ctypes.byref(tc)))
+        return tb.value, tc.value
+
     def tune_get(self, n):
         c, p, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
         B.check(B.lib().hf_tune_get(self.handle, int(n), ctypes.byref(c), ctypes.byref(p), ctypes.byref(r)))

@@ -60,6 +60,7 @@ struct Tune {  // the autotuner's choice for one grid size
     bool set = false;
     int chunk = 0;
     int pencil = 0;
+    int tile_b = 0, tile_c = 0;  // launch-shape candidates of passes B and C (hf::run_passB/C)
     double rot_per_s = 0;
 };
 static int tune_slot(int n) { return n == 32 ? 0 : n == 64 ? 1 : n == 96 ? 2 : n == 128 ? 3 : 4; }
@@ -139,6 +140,7 @@ struct hf_fieldset {
     float *d_P = nullptr;        // R x 18
     double *d_P64 = nullptr;     // R x 18
     int chunk = 1;
+    int tile_b = 0, tile_c = 0;  // launch shapes of passes B and C (autotuner)
     int lanes = 1;  // pipelines used by compute (HF_LANES=2 alternates chunks over two)
     bool pencil = false;  // pencil pipeline (x/y stages as separate kernels) instead of slab passes
     int prec = hf::PREC_FP32;  // y stages on the tensor cores (pencil pipeline at N = 256)
@@ -946,6 +948,8 @@ static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags,
         if (t.set && !(ev && atoi(ev) > 0)) {
             fs->chunk = t.chunk;
             fs->pencil = t.pencil || n >= 256;
+            fs->tile_b = t.tile_b;
+            fs->tile_c = t.tile_c;
         }
     }
     fs->chunk = std::min(fs->chunk, R);
@@ -1066,7 +1070,7 @@ extern "C" unsigned hf_fieldset_flags(const hf_fieldset *fs) { return fs ? fs->f
 // rot9 (cnt x 9, device); outputs through `out` (first rotation at out.E)
 static hf_status run_fields(hf_ctx *c, int n, bool pencil, int prec, const hf_part *s1, const hf_part *s2,
                             const float *rot9, int cnt, float2 *scratch, size_t scratch_rot, float *planes,
-                            FieldPtrs out, cudaStream_t st, bool spectral = false) {
+                            FieldPtrs out, cudaStream_t st, bool spectral = false, int tile_b = 0, int tile_c = 0) {
     float2 *X1 = scratch, *Y1 = scratch + scratch_rot, *Y2 = scratch + 2 * scratch_rot;
     if (spectral) {
         CU(timed(c, kPassB, st, [&] {
@@ -1114,14 +1118,14 @@ static hf_status run_fields(hf_ctx *c, int n, bool pencil, int prec, const hf_pa
         CU(timed(c, kResample, st, [&] { return hf::run_resample_chunk(n, s2->grid, rot9, planes, cnt, st); }));
         CU(timed(c, kPassA, st, [&] { return hf::run_passA_planes(n, planes, X1, cnt, st); }));
     }
-    CU(timed(c, kPassB, st, [&] { return hf::run_passB(n, X1, s1->spec, Y1, Y2, cnt, st); }));
+    CU(timed(c, kPassB, st, [&] { return hf::run_passB(n, X1, s1->spec, Y1, Y2, cnt, st, tile_b); }));
     if (out.Tx) {  // analytic torque: three more spectra after Y2 in the scratch
         float2 *YT = scratch + 3 * scratch_rot;
         CU(timed(c, kPassB, st, [&] { return hf::run_passB_torque(n, X1, s1->mspec, YT, scratch_rot, cnt, st); }));
         CU(timed(c, kPassC, st, [&] { return hf::run_passC_torque(n, Y1, Y2, YT, scratch_rot, out, cnt, st); }));
         return HF_OK;
     }
-    CU(timed(c, kPassC, st, [&] { return hf::run_passC(n, Y1, Y2, out, cnt, st); }));
+    CU(timed(c, kPassC, st, [&] { return hf::run_passC(n, Y1, Y2, out, cnt, st, tile_c); }));
     return HF_OK;
 }
 
@@ -1199,7 +1203,7 @@ hf_status hf_set_launch(hf_ctx *ctx, const hf_part *s1, const hf_part *s2, hf_fi
             out.Tz = base + (size_t)fs->slot[6] * n3;
         }
         s = run_fields(ctx, n, fs->pencil, fs->prec, s1, s2, d_rot9 + (size_t)9 * r0, cnt, fs->scratch[l], scr_rot,
-                       nullptr, out, fs->lanes == 2 ? fs->lane[l] : st, fs->spectral);
+                       nullptr, out, fs->lanes == 2 ? fs->lane[l] : st, fs->spectral, fs->tile_b, fs->tile_c);
         if (s != HF_OK) return s;
     }
     for (int l = 0; l < 2 && fs->lanes == 2; ++l) {
@@ -1565,6 +1569,28 @@ extern "C" hf_status hf_tune_get(const hf_ctx *ctx, int n, int *chunk, int *penc
     return HF_OK;
 }
 
+extern "C" hf_status hf_tune_tiles(hf_ctx *ctx, int n, int set, int *tile_b, int *tile_c) {
+    if (!ctx || !tile_b || !tile_c) return fail(HF_EINVAL, "hf_tune_tiles: NULL argument");
+    if (!hf::supported_n(n)) return fail(HF_EUNSUPPORTED, "hf_tune_tiles: N=%d not supported", n);
+    Tune &t = ctx->tune[tune_slot(n)];
+    if (set) {
+        if (*tile_b < 0 || *tile_b > 1 || *tile_c < 0 || *tile_c > 2 || (*tile_c == 2 && n != 128) ||
+            ((*tile_b || *tile_c) && (n < 64 || n > 128)))
+            return fail(HF_EINVAL, "hf_tune_tiles: tile_b %d, tile_c %d at N=%d", *tile_b, *tile_c, n);
+        if (!t.set) {  // keep the built-in chunk and pipeline
+            t.set = true;
+            t.chunk = default_chunk(n);
+            t.pencil = hf::pencil_n(n);
+        }
+        t.tile_b = *tile_b;
+        t.tile_c = *tile_c;
+    } else {
+        *tile_b = t.set ? t.tile_b : 0;
+        *tile_c = t.set ? t.tile_c : 0;
+    }
+    return HF_OK;
+}
+
 namespace {
 std::string tune_device_key(int device) {
     cudaDeviceProp p;
@@ -1575,43 +1601,97 @@ std::string tune_device_key(int device) {
     return k + "_sm" + std::to_string(p.major) + std::to_string(p.minor);
 }
 
-// cache lines: "<device> <n> <chunk> <pencil> <rot_per_s>"
-bool tune_cache_read(const char *path, const std::string &dev, int n, Tune &t) {
+// The cache is a JSON document, one entry per line (device, N):
+//   {"tune": [
+//    {"device": "<name>_sm<cc>", "n": 128, "chunk": 128, "pipeline": "slab", "tile_b": 0, "tile_c": 0,
+//     "radix": "16x8", "passB_columns_per_cta": 32, "passC_rows_per_x_batch": 32, "passC_threads": 512,
+//     "rot_per_s": 33400},
+//    ...]}
+// It is read back by the key scan below, which accepts the lines it writes.
+const char *tune_radix(int n) {
+    return n == 32 ? "8x4" : n == 64 ? "8x8" : n == 96 ? "12x8" : n == 128 ? "16x8" : "16x16";
+}
+int tune_pass_b_columns(int n, int tile_b) { return tile_b == 1 && n <= 128 ? 16 : (n >= 256 ? 16 : 32); }
+int tune_pass_c_rows(int n, int tile_c) {
+    if (tile_c == 1 && n >= 64 && n <= 128) return 16;
+    return n == 96 ? 48 : (n >= 64 ? 32 : 16);
+}
+int tune_pass_c_threads(int n, int tile_c) {
+    if (tile_c == 2 && n == 128) return 256;
+    return n >= 128 ? 512 : (n >= 64 ? 256 : 128);
+}
+
+std::string tune_json_line(const std::string &dev, int n, const Tune &t) {
+    char buf[512];
+    snprintf(buf, sizeof buf,
+             "{\"device\": \"%s\", \"n\": %d, \"chunk\": %d, \"pipeline\": \"%s\", \"tile_b\": %d, \"tile_c\": %d, "
+             "\"radix\": \"%s\", \"passB_columns_per_cta\": %d, \"passC_rows_per_x_batch\": %d, "
+             "\"passC_threads\": %d, \"rot_per_s\": %.6g}",
+             dev.c_str(), n, t.chunk, t.pencil ? "pencil" : "slab", t.tile_b, t.tile_c, tune_radix(n),
+             tune_pass_b_columns(n, t.tile_b), tune_pass_c_rows(n, t.tile_c), tune_pass_c_threads(n, t.tile_c),
+             t.rot_per_s);
+    return buf;
+}
+
+// value of "key": in a line (string values unquoted); empty if absent
+std::string json_field(const std::string &line, const char *key) {
+    const std::string k = std::string("\"") + key + "\": ";
+    size_t p = line.find(k);
+    if (p == std::string::npos) return "";
+    p += k.size();
+    if (p < line.size() && line[p] == '"') {
+        const size_t q = line.find('"', p + 1);
+        return q == std::string::npos ? "" : line.substr(p + 1, q - p - 1);
+    }
+    const size_t q = line.find_first_of(",}", p);
+    return line.substr(p, q == std::string::npos ? std::string::npos : q - p);
+}
+
+std::vector<std::string> tune_cache_lines(const char *path) {
+    std::vector<std::string> out;
     FILE *f = fopen(path, "r");
-    if (!f) return false;
-    char d[256];
-    int nn, c, pe;
-    double r;
-    bool hit = false;
-    while (fscanf(f, "%255s %d %d %d %lf", d, &nn, &c, &pe, &r) == 5)
-        if (dev == d && nn == n && c > 0) {
-            t.set = true;
-            t.chunk = c;
-            t.pencil = pe != 0;
-            t.rot_per_s = r;
-            hit = true;
-        }
+    if (!f) return out;
+    char line[1024];
+    while (fgets(line, sizeof line, f)) {
+        std::string l(line);
+        if (l.find("\"device\"") != std::string::npos) out.push_back(l);
+    }
     fclose(f);
+    return out;
+}
+
+bool tune_cache_read(const char *path, const std::string &dev, int n, Tune &t) {
+    bool hit = false;
+    for (const std::string &l : tune_cache_lines(path)) {
+        if (json_field(l, "device") != dev || atoi(json_field(l, "n").c_str()) != n) continue;
+        const int c = atoi(json_field(l, "chunk").c_str());
+        if (c <= 0) continue;
+        t.set = true;
+        t.chunk = c;
+        t.pencil = json_field(l, "pipeline") == "pencil";
+        t.tile_b = atoi(json_field(l, "tile_b").c_str());
+        t.tile_c = atoi(json_field(l, "tile_c").c_str());
+        t.rot_per_s = atof(json_field(l, "rot_per_s").c_str());
+        hit = true;
+    }
     return hit;
 }
 
 bool tune_cache_write(const char *path, const std::string &dev, int n, const Tune &t) {
     std::vector<std::string> keep;
-    if (FILE *f = fopen(path, "r")) {
-        char line[512];
-        while (fgets(line, sizeof line, f)) {
-            char d[256];
-            int nn;
-            if (sscanf(line, "%255s %d", d, &nn) == 2 && dev == d && nn == n) continue;
-            keep.emplace_back(line);
+    for (const std::string &l : tune_cache_lines(path))
+        if (!(json_field(l, "device") == dev && atoi(json_field(l, "n").c_str()) == n)) {
+            std::string x = l;
+            while (!x.empty() && (x.back() == '\n' || x.back() == ',' || x.back() == ' ')) x.pop_back();
+            keep.push_back(x);
         }
-        fclose(f);
-    }
+    keep.push_back(tune_json_line(dev, n, t));
     const std::string tmp = std::string(path) + ".tmp";
     FILE *f = fopen(tmp.c_str(), "w");
     if (!f) return false;
-    for (auto &l : keep) fputs(l.c_str(), f);
-    fprintf(f, "%s %d %d %d %.6g\n", dev.c_str(), n, t.chunk, t.pencil ? 1 : 0, t.rot_per_s);
+    fputs("{\"tune\": [\n", f);
+    for (size_t i = 0; i < keep.size(); ++i) fprintf(f, " %s%s\n", keep[i].c_str(), i + 1 < keep.size() ? "," : "");
+    fputs("]}\n", f);
     const bool ok = fclose(f) == 0;
     return ok && rename(tmp.c_str(), path) == 0;
 }
@@ -1702,6 +1782,37 @@ extern "C" hf_status hf_autotune(hf_ctx *ctx, int n, const char *cache_path, int
                     }
                 }
             }
+        }
+        // the launch shapes of passes B and C at the best slab shape: every
+        // compiled candidate (tile 0 is the one timed above)
+        if (best.set && !best.pencil && n >= 64 && n <= 128) {
+            const int tc_max = n == 128 ? 2 : 1;
+            for (int tb = 0; tb <= 1; ++tb)
+                for (int tc = 0; tc <= tc_max; ++tc) {
+                    if (tb == 0 && tc == 0) continue;
+                    Tune &t = ctx->tune[tune_slot(n)];
+                    t = best;
+                    t.tile_b = tb;
+                    t.tile_c = tc;
+                    hf_fieldset *fs = nullptr;
+                    if (hf_fieldset_create(ctx, n, R, HF_E | HF_F, &fs) != HF_OK) continue;
+                    float best_ms = 1e30f;
+                    hf_status bs = hf_fieldset_compute(ctx, s1, s2, quats.data(), R, fs, nullptr);
+                    for (int rep = 0; rep < 3 && bs == HF_OK; ++rep) {
+                        cudaEventRecord(e0, nullptr);
+                        bs = hf_fieldset_compute(ctx, s1, s2, quats.data(), R, fs, nullptr);
+                        cudaEventRecord(e1, nullptr);
+                        float ms = 0;
+                        if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+                            best_ms = std::min(best_ms, ms);
+                    }
+                    hf_fieldset_release(fs);
+                    if (bs == HF_OK && best_ms < 1e29f && R / (best_ms * 1e-3) > best.rot_per_s) {
+                        const double rps = R / (best_ms * 1e-3);
+                        best = t;
+                        best.rot_per_s = rps;
+                    }
+                }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);

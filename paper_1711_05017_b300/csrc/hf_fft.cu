@@ -455,14 +455,15 @@ __global__ void __launch_bounds__(kRsX * kRsY) resample_chunk_kernel(const float
 //   inverse  stage 1 on the same registers (DFT-R2, conj twiddle), exchange;
 //            stage 2: thread (c, g): DFT-R1 gives z = R2 n1 + g, stored
 //            straight to HBM
-template <int N>
+// CWO != 0 selects another column-tile width (an autotuner candidate)
+template <int N, int CWO = 0>
 struct PassB {
     static constexpr int H = N / 2 + 1;
     static constexpr int R1 = Fact<N>::R1, R2 = Fact<N>::R2;
-    static constexpr int CW = N >= 256 ? 16 : 32;       // columns per CTA (N H is a multiple)
+    static constexpr int CW = CWO ? CWO : (N >= 256 ? 16 : 32);  // columns per CTA (N H is a multiple)
     static constexpr int NT = CW * R2;
     static constexpr int KPT = (R1 + R2 - 1) / R2;      // stage-2 k1 values per thread
-    static constexpr int MINB = N >= 128 ? 3 : 4;
+    static constexpr int MINB = CW < 32 && N < 256 ? 6 : (N >= 128 ? 3 : 4);
     static constexpr size_t smem = sizeof(float2) * (2 * (size_t)N * CW + N);
     static_assert((N * H) % CW == 0, "whole column tiles");
 };
@@ -541,14 +542,14 @@ __device__ __forceinline__ float2 ldg_inter(const float2 *p) {
 }
 
 // The body of one pass B block: column tile bx of rotation r.
-template <int N, int MODE, bool COH = false>
+template <int N, int MODE, bool COH = false, int CWO = 0>
 __device__ __forceinline__ void passB_body(const float2 *__restrict__ X1, const float2 *__restrict__ R1hat,
                                            float2 *__restrict__ Y1, float2 *__restrict__ Y2, float scale,
                                            const SpecSrc &spec, const float *__restrict__ rot9, unsigned bx,
                                            unsigned r) {
     __builtin_assume(bx < (1u << 24) && r < (1u << 16));  // the ranges of the blockIdx they stand for
-    constexpr int H = PassB<N>::H, R1 = PassB<N>::R1, R2 = PassB<N>::R2, CW = PassB<N>::CW,
-                  KPT = PassB<N>::KPT;
+    using PB = PassB<N, CWO>;
+    constexpr int H = PB::H, R1 = PB::R1, R2 = PB::R2, CW = PB::CW, KPT = PB::KPT;
     constexpr size_t NH = (size_t)N * H;
     extern __shared__ float2 sm[];
     float2 *E = sm;                      // [k1][n2][c], later S's [n2][k1][c]
@@ -571,7 +572,7 @@ __device__ __forceinline__ void passB_body(const float2 *__restrict__ X1, const 
         f = (size_t)kys * H + (active ? xslot<N>(kx) : 0);
         if (tile == 0) {
             const size_t fq = (size_t)kys * H + HALF;
-            for (int z = threadIdx.x; z < N; z += PassB<N>::NT) {
+            for (int z = threadIdx.x; z < N; z += PB::NT) {
                 Y1[(size_t)r * N * NH + (size_t)z * NH + fq] = make_float2(0.f, 0.f);
                 Y2[(size_t)r * N * NH + (size_t)z * NH + fq] = make_float2(0.f, 0.f);
             }
@@ -677,14 +678,14 @@ __device__ __forceinline__ void passB_body(const float2 *__restrict__ X1, const 
     }
 }
 
-template <int N, int MODE>
-__global__ void __launch_bounds__(PassB<N>::NT, MODE == 2 ? 2 : PassB<N>::MINB) passB_kernel(const float2 *__restrict__ X1,
+template <int N, int MODE, int CWO = 0>
+__global__ void __launch_bounds__(PassB<N, CWO>::NT, MODE == 2 ? 2 : PassB<N, CWO>::MINB) passB_kernel(const float2 *__restrict__ X1,
                                                                               const float2 *__restrict__ R1hat,
                                                                               float2 *__restrict__ Y1,
                                                                               float2 *__restrict__ Y2, float scale,
                                                                               SpecSrc spec,
                                                                               const float *__restrict__ rot9) {
-    passB_body<N, MODE>(X1, R1hat, Y1, Y2, scale, spec, rot9, blockIdx.x, blockIdx.y);
+    passB_body<N, MODE, false, CWO>(X1, R1hat, Y1, Y2, scale, spec, rot9, blockIdx.x, blockIdx.y);
 }
 
 
@@ -761,13 +762,16 @@ __global__ void __launch_bounds__(PassB<N>::NT, 2) passB_torque_kernel(const flo
 // ------------------------------------------------------------------ pass C
 // One CTA per (z-plane, rotation) holding S'' and Gy'' side by side (pitch
 // 2H+1), then Gz'' in place of S''.
-template <int N>
+// RBO / NTO != 0 select other rows per x batch / threads per CTA (autotuner
+// candidates)
+template <int N, int RBO = 0, int NTO = 0>
 struct PassC {
     static constexpr int H = N / 2 + 1, HALF = N / 2;
     static constexpr int PW = H;  // plane pitch (odd): one half-spectrum plane at a time
-    static constexpr int RB = (N == 96) ? 48 : (N >= 64 ? 32 : 16);  // rows per x batch (divides N / 2)
+    static constexpr int RB = RBO ? RBO : (N == 96) ? 48 : (N >= 64 ? 32 : 16);  // rows per x batch (divides N / 2)
+    static_assert((N / 2) % RB == 0, "whole row batches");
     static constexpr int TP = N + 1;                                  // row-buffer pitch
-    static constexpr int NT = (N >= 128) ? 512 : (N >= 64 ? 256 : 128);
+    static constexpr int NT = NTO ? NTO : (N >= 128) ? 512 : (N >= 64 ? 256 : 128);
     static constexpr int MINB = (N >= 128) ? 2 : 1;
     static constexpr size_t smem = sizeof(float2) * ((size_t)N * PW + (size_t)RB * TP + N);
 };
@@ -1048,13 +1052,14 @@ __device__ __forceinline__ void y_inverse_plane(const float2 *__restrict__ src, 
 //   Gz' -> y inverse -> rows paired likewise          -> Fz
 // The body of one pass C block: plane z of rotation r.  NT threads (the
 // kernel's 512 at N = 128, a persistent block's 256); COH as for ld_inter.
-template <int N, bool TQ, int NT = PassC<N>::NT, bool COH = false>
+template <int N, bool TQ, int NT = PassC<N>::NT, bool COH = false, int RBO = 0>
 __device__ __forceinline__ void passC_body(const float2 *__restrict__ Y1, const float2 *__restrict__ Y2,
                                            const FieldPtrs &out, const float2 *__restrict__ YT, size_t yt_stride,
                                            unsigned zu, unsigned ru) {
     __builtin_assume(zu < (1u << 16) && ru < (1u << 16));  // the ranges of the blockIdx they stand for
     const int z = (int)zu, r = (int)ru;
-    constexpr int H = PassC<N>::H, PW = PassC<N>::PW, RB = PassC<N>::RB, TP = PassC<N>::TP, HALF = N / 2;
+    using PC = PassC<N, RBO>;
+    constexpr int H = PC::H, PW = PC::PW, RB = PC::RB, TP = PC::TP, HALF = N / 2;
     extern __shared__ float2 sm[];
     float2 *plane = sm;                       // [N][PW]
     float2 *Tb = plane + (size_t)N * PW;      // [RB][TP]
@@ -1088,13 +1093,13 @@ __device__ __forceinline__ void passC_body(const float2 *__restrict__ Y1, const 
     }
 }
 
-template <int N, bool TQ>
-__global__ void __launch_bounds__(PassC<N>::NT, PassC<N>::MINB) passC_kernel(const float2 *__restrict__ Y1,
+template <int N, bool TQ, int RBO = 0, int NTO = 0>
+__global__ void __launch_bounds__(PassC<N, RBO, NTO>::NT, PassC<N, RBO, NTO>::MINB) passC_kernel(const float2 *__restrict__ Y1,
                                                                               const float2 *__restrict__ Y2,
                                                                               FieldPtrs out,
                                                                               const float2 *__restrict__ YT,
                                                                               size_t yt_stride) {
-    passC_body<N, TQ>(Y1, Y2, out, YT, yt_stride, blockIdx.x, blockIdx.y);
+    passC_body<N, TQ, PassC<N, RBO, NTO>::NT, false, RBO>(Y1, Y2, out, YT, yt_stride, blockIdx.x, blockIdx.y);
 }
 
 // the stationary moment fields G_a = (u x F)_a / h^3 (F = -h^3 grad rho1)
@@ -1373,6 +1378,12 @@ static cudaError_t set_smem_attrs() {
     if ((e = cudaFuncSetAttribute(passB_kernel<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N>::smem))) return e;
     if ((e = cudaFuncSetAttribute(passB_kernel<N, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N>::smem))) return e;
     if ((e = cudaFuncSetAttribute(passC_kernel<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassC<N>::smem))) return e;
+    if constexpr (N >= 64 && N <= 128) {  // the autotuner's tile candidates
+        if ((e = cudaFuncSetAttribute(passB_kernel<N, 0, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N, 16>::smem))) return e;
+        if ((e = cudaFuncSetAttribute(passC_kernel<N, false, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassC<N, 16>::smem))) return e;
+        if constexpr (N == 128)
+            if ((e = cudaFuncSetAttribute(passC_kernel<N, false, 0, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassC<N, 0, 256>::smem))) return e;
+    }
     if ((e = cudaFuncSetAttribute(passC_kernel<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassC<N>::smem))) return e;
     if ((e = cudaFuncSetAttribute(passB_torque_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)(sizeof(float2) * (3 * (size_t)N * PassB<N>::CW + N)))))
@@ -1404,10 +1415,11 @@ static cudaError_t launch_resample_chunk(const float *rho, const float *rot9, fl
     resample_chunk_kernel<N><<<dim3((N / kRsX) * (N / kRsY) * (N / kRsZ), nrot), kRsX * kRsY, 0, st>>>(rho, rot9, out);
     return cudaGetLastError();
 }
-template <int N>
+template <int N, int CWO = 0>
 static cudaError_t launch_passB(const float2 *X1, const float2 *R1hat, float2 *Y1, float2 *Y2, int nrot,
                                 cudaStream_t st) {
-    passB_kernel<N, 0><<<dim3(N * PassB<N>::H / PassB<N>::CW, nrot), PassB<N>::NT, PassB<N>::smem, st>>>(
+    using PB = PassB<N, CWO>;
+    passB_kernel<N, 0, CWO><<<dim3(N * PB::H / PB::CW, nrot), PB::NT, PB::smem, st>>>(
         X1, R1hat, Y1, Y2, 0.f, SpecSrc{nullptr, 0, 0}, nullptr);
     return cudaGetLastError();
 }
@@ -1425,9 +1437,10 @@ static cudaError_t launch_passB_spectral(const float2 *table, cudaTextureObject_
         nullptr, R1hat, Y1, Y2, 0.f, SpecSrc{table, os * N, os, tex, table_tex_sc(os * N)}, rot9);
     return cudaGetLastError();
 }
-template <int N>
+template <int N, int RBO = 0, int NTO = 0>
 static cudaError_t launch_passC(const float2 *Y1, const float2 *Y2, FieldPtrs out, int nrot, cudaStream_t st) {
-    passC_kernel<N, false><<<dim3(N, nrot), PassC<N>::NT, PassC<N>::smem, st>>>(Y1, Y2, out, nullptr, 0);
+    using PC = PassC<N, RBO, NTO>;
+    passC_kernel<N, false, RBO, NTO><<<dim3(N, nrot), PC::NT, PC::smem, st>>>(Y1, Y2, out, nullptr, 0);
     return cudaGetLastError();
 }
 template <int N>
@@ -1663,13 +1676,32 @@ cudaError_t run_support(int n, const float *g, unsigned *masks, int *box, cudaSt
 cudaError_t run_pad_slices(int n, const float *g, float *slab, size_t pitch_floats, cudaStream_t st) {
     HF_DISPATCH_ALL(n, launch_pad_slices<NN>(g, slab, pitch_floats, st));
 }
-cudaError_t run_passB(int n, const float2 *X1, const float2 *R1hat, float2 *Y1, float2 *Y2, int nrot, cudaStream_t st) {
+cudaError_t run_passB(int n, const float2 *X1, const float2 *R1hat, float2 *Y1, float2 *Y2, int nrot, cudaStream_t st,
+                      int tile) {
+    if (tile == 1) {  // 16 columns per CTA
+        switch (n) {
+            case 64: return launch_passB<64, 16>(X1, R1hat, Y1, Y2, nrot, st);
+            case 96: return launch_passB<96, 16>(X1, R1hat, Y1, Y2, nrot, st);
+            case 128: return launch_passB<128, 16>(X1, R1hat, Y1, Y2, nrot, st);
+            default: break;
+        }
+    }
     HF_DISPATCH_ALL(n, launch_passB<NN>(X1, R1hat, Y1, Y2, nrot, st));
 }
 cudaError_t run_passB_forward(int n, const float2 *X1, float2 *spec, float scale, cudaStream_t st) {
     HF_DISPATCH_ALL(n, launch_passB_fwd<NN>(X1, spec, scale, st));
 }
-cudaError_t run_passC(int n, const float2 *Y1, const float2 *Y2, FieldPtrs out, int nrot, cudaStream_t st) {
+cudaError_t run_passC(int n, const float2 *Y1, const float2 *Y2, FieldPtrs out, int nrot, cudaStream_t st, int tile) {
+    if (tile == 1) {  // 16 rows per x batch
+        switch (n) {
+            case 64: return launch_passC<64, 16>(Y1, Y2, out, nrot, st);
+            case 96: return launch_passC<96, 16>(Y1, Y2, out, nrot, st);
+            case 128: return launch_passC<128, 16>(Y1, Y2, out, nrot, st);
+            default: break;
+        }
+    } else if (tile == 2 && n == 128) {  // 256 threads per CTA
+        return launch_passC<128, 0, 256>(Y1, Y2, out, nrot, st);
+    }
     HF_DISPATCH(n, launch_passC<NN>(Y1, Y2, out, nrot, st));
 }
 cudaError_t run_pad_center(int n, const float *g, float *out, int np, cudaStream_t st) {

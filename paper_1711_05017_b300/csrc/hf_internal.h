@@ -97,10 +97,14 @@ cudaError_t run_pad_slices(int n, const float *g, float *slab, size_t pitch_floa
 // (a = 0, 1, 2 for x, y, z); masks is kSupportMaskWords words of scratch
 constexpr int kSupportMaskWords = 24;
 cudaError_t run_support(int n, const float *g, unsigned *masks, int *box, cudaStream_t st);
+// tile: the autotuner's launch-shape candidate (pass B: 0 the built-in 32
+// columns per CTA, 1 16 columns; pass C: 0 built-in, 1 16 rows per x batch,
+// 2 256 threads per CTA at N = 128)
 cudaError_t run_passB(int n, const float2 *X1, const float2 *R1hat, float2 *Y1, float2 *Y2, int nrot,
-                      cudaStream_t st);
+                      cudaStream_t st, int tile = 0);
 cudaError_t run_passB_forward(int n, const float2 *X1, float2 *spec, float scale, cudaStream_t st);
-cudaError_t run_passC(int n, const float2 *Y1, const float2 *Y2, FieldPtrs out, int nrot, cudaStream_t st);
+cudaError_t run_passC(int n, const float2 *Y1, const float2 *Y2, FieldPtrs out, int nrot, cudaStream_t st,
+                      int tile = 0);
 cudaError_t run_unpermute(int n, const float2 *spec, float2 *out, cudaStream_t st);
 // spectral mode (rotation in the frequency domain): a moving part's centred
 // table is built from rho2 padded to np = os n nodes (pad, forward transform

@@ -183,12 +183,16 @@ def test_batch_errors(hf):
 def test_autotune_choice_cache_and_results(hf, tmp_path):
     from paper_1711_05017_b300 import _binding as B
     ctx = hf.Context(0)
-    path = tmp_path / "tune.txt"
+    import json
+    path = tmp_path / "tune.json"
     chunk, pencil, rps = ctx.autotune(64, path)
     assert chunk > 0 and pencil in (0, 1) and rps > 0
     assert ctx.tune_get(64)[:2] == (chunk, pencil)
-    line = path.read_text().split()
-    assert len(line) == 5 and int(line[1]) == 64 and int(line[2]) == chunk
+    doc = json.loads(path.read_text())  # the cache is JSON: one entry per (device, N)
+    (ent,) = [e for e in doc["tune"] if e["n"] == 64]
+    assert ent["chunk"] == chunk and ent["pipeline"] == ("pencil" if pencil else "slab")
+    assert ent["radix"] == "8x8" and ent["passB_columns_per_cta"] in (16, 32)
+    assert (ent["tile_b"], ent["tile_c"]) == ctx.tune_tiles(64)
     # a second context reads the cache instead of timing
     ctx2 = hf.Context(0)
     assert ctx2.autotune(64, path) == (chunk, pencil, pytest.approx(rps, rel=1e-5))
@@ -210,6 +214,25 @@ def test_autotune_choice_cache_and_results(hf, tmp_path):
     with pytest.raises(hf.HFError) as e:
         ctx2.tune_set(256, 4, pencil=False)
     assert e.value.status == B.HF_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("n", [64, 96, 128])
+def test_tile_candidates_give_the_same_fields(hf, n):
+    """Every compiled launch-shape candidate of passes B and C (the
+    autotuner's choices) gives the built-in shape's fields bit for bit: the
+    per-item arithmetic is the same, only the blocks' tiling differs."""
+    ctx = hf.Context(0)
+    pair = make_pair(hf, ctx, n, 60)[:2]
+    q = synth.random_quaternions(61, 10).astype(np.float32)
+    base = all_fields(plain(hf, ctx, pair, q, hf.HF_E | hf.HF_F), 10, 4)
+    for tb in (0, 1):
+        for tc in ((0, 1, 2) if n == 128 else (0, 1)):
+            ctx.tune_tiles(n, (tb, tc))
+            assert ctx.tune_tiles(n) == (tb, tc)
+            got = all_fields(plain(hf, ctx, pair, q, hf.HF_E | hf.HF_F), 10, 4)
+            assert np.array_equal(got, base), (tb, tc)
+    with pytest.raises(hf.HFError):
+        ctx.tune_tiles(n, (0, 2) if n != 128 else (2, 0))
 
 
 # ------------------------------------------------ one launch over a work queue
