@@ -86,7 +86,7 @@ typedef void *hf_stream; /* a cudaStream_t */
 #define HF_E 0x1u           /* energy field per rotation (always held) */
 #define HF_F 0x2u           /* force field (3 components) per rotation (always held) */
 #define HF_T 0x4u           /* torque field (3 components) per rotation */
-#define HF_TORQUE_F64 0x10u /* torque differences and products in float64 on the device */
+#define HF_TORQUE_F64 0x10u /* torque least-squares product in float64 on the device (over float32 differences) */
 /* Precision variant (N = 256 only): the y-axis DFT stages run on the tensor
  * cores as 16 x 16 DFT-matrix GEMMs with operands split into hi + lo parts in
  * BF16 or FP16 and FP32 accumulation; every other stage stays FP32. */
@@ -126,6 +126,10 @@ const char *hf_last_error(void);
  * device memory the context's handles may hold (0 = no bound).
  * Errors: HF_EINVAL (null out, bad device), HF_ECUDA. */
 hf_status hf_ctx_create(int device, size_t hbm_budget_bytes, hf_ctx **out);
+/* Drop the caller's handle.  Every part, field set, batch and server made
+ * from the context holds a reference to it, so they may be released before
+ * or after this call, in any order; the context's own resources go with the
+ * last of them. */
 void hf_ctx_destroy(hf_ctx *ctx);
 /* Bytes currently charged against the budget, and the budget (0 = none). */
 size_t hf_ctx_reserved_bytes(const hf_ctx *ctx);
@@ -360,8 +364,11 @@ int hf_rotation_chunks(const float *h_quat, int R, int max_build, int halo, int 
  *   - Queries take no lock that the scheduler or a submitting thread holds
  *     (the published data is read through atomic shared pointers).
  *   - The builds allocate from the device's default stream-ordered memory
- *     pool, whose release threshold the server sets to keep its reserve
- *     (trimmed when the server is destroyed).
+ *     pool, whose release threshold the server sets to keep its reserve; at
+ *     creation the server reserves the context's remaining budget in the
+ *     pool (up to the free memory less 4 GB), so that builds do not map
+ *     memory while queries run (the pool is trimmed when the server is
+ *     destroyed).
  * Request states: 0 queued, 1 running, 2 done, 3 failed, 4 superseded. */
 typedef struct hf_server hf_server;
 typedef struct {
@@ -517,8 +524,10 @@ hf_status hf_tune_get(const hf_ctx *ctx, int n, int *chunk, int *pencil, double 
 /* Launch shapes of passes B and C for grid n (the autotuner's compiled
  * candidates, kept in the context like the chunk): tile_b 0 = 32 columns
  * per CTA, 1 = 16; tile_c 0 = the built-in rows per x batch and threads,
- * 1 = 16 rows per x batch, 2 = 256 threads per CTA (N = 128 only); other
- * than 0 only for N = 64, 96, 128.  set != 0 stores *tile_b / *tile_c (the
+ * 1 = 16 rows per x batch, and at N = 128 only 2 = 256 threads per CTA,
+ * 3 = that and an L2 prefetch of the block's third input plane, 4 = that
+ * and two y-stage items' loads in flight per thread; other than 0 only for
+ * N = 64, 96, 128.  set != 0 stores *tile_b / *tile_c (the
  * fields do not change, only their speed), else reads them.  Errors:
  * HF_EINVAL, HF_EUNSUPPORTED. */
 hf_status hf_tune_tiles(hf_ctx *ctx, int n, int set, int *tile_b, int *tile_c);

@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <string>
@@ -67,6 +68,11 @@ static int tune_slot(int n) { return n == 32 ? 0 : n == 64 ? 1 : n == 96 ? 2 : n
 
 struct hf_ctx {
     int device = 0;
+    // The context lives while the caller's handle or any part, field set,
+    // batch or server made from it does: each holds a reference, so the
+    // objects can be released in any order (a garbage collector finalises
+    // the members of a reference cycle in no particular order).
+    std::atomic<int> refs{1};
     Tune tune[5];
     size_t budget = 0, reserved = 0;
     std::mutex mu;
@@ -294,8 +300,18 @@ extern "C" hf_status hf_ctx_create(int device, size_t budget, hf_ctx **out) {
     return HF_OK;
 }
 
-extern "C" void hf_ctx_destroy(hf_ctx *c) {
-    if (!c) return;
+static void ctx_free(hf_ctx *c);
+void hf_ctx_retain(hf_ctx *c) {
+    if (c) c->refs.fetch_add(1);
+}
+void hf_ctx_release(hf_ctx *c) {
+    if (c && c->refs.fetch_sub(1) == 1) ctx_free(c);
+}
+
+// the caller's handle goes; the context itself once its last object has
+extern "C" void hf_ctx_destroy(hf_ctx *c) { hf_ctx_release(c); }
+
+static void ctx_free(hf_ctx *c) {
     cudaSetDevice(c->device);
     if (c->qstream) cudaStreamDestroy(c->qstream);
     if (c->h_qout) cudaFreeHost(c->h_qout);
@@ -493,6 +509,7 @@ extern "C" hf_status hf_part_create(hf_ctx *ctx, int n, const float *d_grid, int
         uncharge(ctx, bytes);
         return s;
     }
+    hf_ctx_retain(ctx);
     *out = p;
     return HF_OK;
 }
@@ -666,7 +683,9 @@ extern "C" void hf_part_release(hf_part *p) {
     moving_texture_free(p);
     cudaFree(p->grid ? (void *)p->grid : (void *)p->spec);
     uncharge(p->ctx, p->bytes);
+    hf_ctx *c = p->ctx;
     delete p;
+    hf_ctx_release(c);
 }
 
 // ---------------------------------------------- rotation set-up (float64)
@@ -925,6 +944,7 @@ static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags,
     hf_fieldset *fs = new (std::nothrow) hf_fieldset();
     if (!fs) return fail(HF_ENOMEM, "hf_fieldset_create: host allocation");
     fs->ctx = ctx;
+    hf_ctx_retain(ctx);
     fs->n = n;
     fs->R = R;
     fs->flags = flags;
@@ -967,6 +987,7 @@ static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags,
     if (!charge(ctx, fs->bytes)) {
         const size_t b = fs->bytes;
         delete fs;
+        hf_ctx_release(ctx);
         return fail(HF_EBUDGET, "hf_fieldset_create: %zu bytes exceed the budget", b);
     }
     fs->mem_stream = mem_stream;
@@ -1045,7 +1066,9 @@ extern "C" void hf_fieldset_release(hf_fieldset *fs) {
     if (fs->h_stage && !fs->mem_stream) cudaFreeHost(fs->h_stage);
     if (fs->stage_done) cudaEventDestroy(fs->stage_done);
     uncharge(fs->ctx, fs->bytes);
+    hf_ctx *c = fs->ctx;
     delete fs;
+    hf_ctx_release(c);
 }
 
 int hf_ctx_device(const hf_ctx *c) { return c ? c->device : 0; }
@@ -1574,7 +1597,7 @@ extern "C" hf_status hf_tune_tiles(hf_ctx *ctx, int n, int set, int *tile_b, int
     if (!hf::supported_n(n)) return fail(HF_EUNSUPPORTED, "hf_tune_tiles: N=%d not supported", n);
     Tune &t = ctx->tune[tune_slot(n)];
     if (set) {
-        if (*tile_b < 0 || *tile_b > 1 || *tile_c < 0 || *tile_c > 2 || (*tile_c == 2 && n != 128) ||
+        if (*tile_b < 0 || *tile_b > 1 || *tile_c < 0 || *tile_c > 4 || (*tile_c >= 2 && n != 128) ||
             ((*tile_b || *tile_c) && (n < 64 || n > 128)))
             return fail(HF_EINVAL, "hf_tune_tiles: tile_b %d, tile_c %d at N=%d", *tile_b, *tile_c, n);
         if (!t.set) {  // keep the built-in chunk and pipeline
@@ -1617,11 +1640,11 @@ int tune_pass_c_rows(int n, int tile_c) {
     return n == 96 ? 48 : (n >= 64 ? 32 : 16);
 }
 int tune_pass_c_threads(int n, int tile_c) {
-    if (tile_c == 2 && n == 128) return 256;
+    if (tile_c >= 2 && n == 128) return 256;
     return n >= 128 ? 512 : (n >= 64 ? 256 : 128);
 }
 
-std::string tune_json_line(const std::string &dev, int n, const Tune &t) {
+std::string tune_json_line(const std::string &dev, int n, const Tune &t, const std::string &cands = "") {
     char buf[512];
     snprintf(buf, sizeof buf,
              "{\"device\": \"%s\", \"n\": %d, \"chunk\": %d, \"pipeline\": \"%s\", \"tile_b\": %d, \"tile_c\": %d, "
@@ -1630,7 +1653,12 @@ std::string tune_json_line(const std::string &dev, int n, const Tune &t) {
              dev.c_str(), n, t.chunk, t.pencil ? "pencil" : "slab", t.tile_b, t.tile_c, tune_radix(n),
              tune_pass_b_columns(n, t.tile_b), tune_pass_c_rows(n, t.tile_c), tune_pass_c_threads(n, t.tile_c),
              t.rot_per_s);
-    return buf;
+    std::string l = buf;
+    if (!cands.empty()) {  // every timed candidate: [chunk, pencil, tile_b, tile_c, rot_per_s]
+        l.pop_back();
+        l += ", \"candidates\": [" + cands + "]}";
+    }
+    return l;
 }
 
 // value of "key": in a line (string values unquoted); empty if absent
@@ -1651,10 +1679,15 @@ std::vector<std::string> tune_cache_lines(const char *path) {
     std::vector<std::string> out;
     FILE *f = fopen(path, "r");
     if (!f) return out;
-    char line[1024];
-    while (fgets(line, sizeof line, f)) {
-        std::string l(line);
-        if (l.find("\"device\"") != std::string::npos) out.push_back(l);
+    std::string l;
+    for (int ch = fgetc(f);; ch = fgetc(f)) {  // whole lines, however long
+        if (ch == EOF || ch == '\n') {
+            if (l.find("\"device\"") != std::string::npos) out.push_back(l);
+            l.clear();
+            if (ch == EOF) break;
+        } else {
+            l += (char)ch;
+        }
     }
     fclose(f);
     return out;
@@ -1677,7 +1710,7 @@ bool tune_cache_read(const char *path, const std::string &dev, int n, Tune &t) {
     return hit;
 }
 
-bool tune_cache_write(const char *path, const std::string &dev, int n, const Tune &t) {
+bool tune_cache_write(const char *path, const std::string &dev, int n, const Tune &t, const std::string &cands) {
     std::vector<std::string> keep;
     for (const std::string &l : tune_cache_lines(path))
         if (!(json_field(l, "device") == dev && atoi(json_field(l, "n").c_str()) == n)) {
@@ -1685,7 +1718,7 @@ bool tune_cache_write(const char *path, const std::string &dev, int n, const Tun
             while (!x.empty() && (x.back() == '\n' || x.back() == ',' || x.back() == ' ')) x.pop_back();
             keep.push_back(x);
         }
-    keep.push_back(tune_json_line(dev, n, t));
+    keep.push_back(tune_json_line(dev, n, t, cands));
     const std::string tmp = std::string(path) + ".tmp";
     FILE *f = fopen(tmp.c_str(), "w");
     if (!f) return false;
@@ -1749,6 +1782,13 @@ extern "C" hf_status hf_autotune(hf_ctx *ctx, int n, const char *cache_path, int
             quats[4 * r + 3] = (float)(0.3 + sin(2 * M_PI * (a + c)));
         }
         const Tune saved = ctx->tune[tune_slot(n)];
+        std::string cands;  // every timed candidate, for the cache file
+        auto note = [&](const Tune &t, double rps) {
+            char b[96];
+            snprintf(b, sizeof b, "%s[%d, %d, %d, %d, %.6g]", cands.empty() ? "" : ", ", t.chunk, t.pencil ? 1 : 0,
+                     t.tile_b, t.tile_c, rps);
+            cands += b;
+        };
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
@@ -1776,6 +1816,7 @@ extern "C" hf_status hf_autotune(hf_ctx *ctx, int n, const char *cache_path, int
                 hf_fieldset_release(fs);
                 if (bs == HF_OK && best_ms < 1e29f) {
                     const double rps = R / (best_ms * 1e-3);
+                    note(t, rps);
                     if (rps > best.rot_per_s) {
                         best = t;
                         best.rot_per_s = rps;
@@ -1786,7 +1827,7 @@ extern "C" hf_status hf_autotune(hf_ctx *ctx, int n, const char *cache_path, int
         // the launch shapes of passes B and C at the best slab shape: every
         // compiled candidate (tile 0 is the one timed above)
         if (best.set && !best.pencil && n >= 64 && n <= 128) {
-            const int tc_max = n == 128 ? 2 : 1;
+            const int tc_max = n == 128 ? 4 : 1;
             for (int tb = 0; tb <= 1; ++tb)
                 for (int tc = 0; tc <= tc_max; ++tc) {
                     if (tb == 0 && tc == 0) continue;
@@ -1807,6 +1848,7 @@ extern "C" hf_status hf_autotune(hf_ctx *ctx, int n, const char *cache_path, int
                             best_ms = std::min(best_ms, ms);
                     }
                     hf_fieldset_release(fs);
+                    if (bs == HF_OK && best_ms < 1e29f) note(t, R / (best_ms * 1e-3));
                     if (bs == HF_OK && best_ms < 1e29f && R / (best_ms * 1e-3) > best.rot_per_s) {
                         const double rps = R / (best_ms * 1e-3);
                         best = t;
@@ -1824,7 +1866,7 @@ extern "C" hf_status hf_autotune(hf_ctx *ctx, int n, const char *cache_path, int
             return fail(HF_ENOMEM, "hf_autotune: no candidate fitted for N=%d", n);
         }
         ctx->tune[tune_slot(n)] = best;
-        if (cache_path && *cache_path && !tune_cache_write(cache_path, dev, n, best))
+        if (cache_path && *cache_path && !tune_cache_write(cache_path, dev, n, best, cands))
             return fail(HF_EINVAL, "hf_autotune: cannot write the cache file %s", cache_path);
     }
     if (chunk_out) *chunk_out = best.chunk;
@@ -2037,6 +2079,7 @@ extern "C" hf_status hf_part_load(hf_ctx *ctx, const char *path, hf_part **out, 
         uncharge(ctx, bytes);
         return s;
     }
+    hf_ctx_retain(ctx);
     *out = p;
     return HF_OK;
 }

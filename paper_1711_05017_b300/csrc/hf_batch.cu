@@ -76,7 +76,9 @@ extern "C" void hf_batch_release(hf_batch *b) {
     for (auto e : b->join) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->cap) cudaStreamDestroy(b->cap);
+    hf_ctx *c = b->ctx;
     delete b;
+    hf_ctx_release(c);
 }
 
 extern "C" hf_status hf_batch_create(hf_ctx *ctx, int npairs, const hf_part *const *s1, const hf_part *const *s2,
@@ -85,6 +87,7 @@ extern "C" hf_status hf_batch_create(hf_ctx *ctx, int npairs, const hf_part *con
     *out = nullptr;
     hf_batch *b = new hf_batch();
     b->ctx = ctx;
+    hf_ctx_retain(ctx);
     b->npairs = npairs;
     b->flags = flags | HF_E | HF_F;
     b->s1.assign(s1, s1 + npairs);

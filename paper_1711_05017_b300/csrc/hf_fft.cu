@@ -966,29 +966,43 @@ __device__ __forceinline__ void x_pass(const float2 *planeA, const float2 *plane
 // transformed in place in two small steps that ride along with stage 2's
 // read and write phases (one warp each), so it costs no barrier of its own.
 // MUL multiplies input row s by i pi ky~(s) on the way in (forms Gy from S').
-template <int N, bool MUL, bool CTW = true, int NT = PassC<N>::NT, bool COH = false>
+template <int N, bool MUL, bool CTW = true, int NT = PassC<N>::NT, bool COH = false, int YU = 1>
 __device__ __forceinline__ void y_inverse_plane(const float2 *__restrict__ src, float2 *plane, const float2 *twN) {
     constexpr int H = N / 2 + 1, HALF = N / 2, R1 = Fact<N>::R1, R2 = Fact<N>::R2, PW = PassC<N>::PW;
     static_assert(NT >= N && NT >= 32 + R2, "one Nyquist value per thread; Nyquist steps on warps 0 and 1");
     float2 nyq = make_float2(0.f, 0.f);
     if (threadIdx.x < N) nyq = ldg_inter<COH>(src + (size_t)threadIdx.x * H + HALF);
-    // stage 1: items (c, k1), slots R2 k1 + k2
+    // stage 1: items (c, k1), slots R2 k1 + k2; YU items' loads in flight per thread
 #pragma unroll 1
-    for (int w = threadIdx.x; w < HALF * R1; w += NT) {
-        const int c = w % HALF, k1 = w / HALF;
-        float2 v[R2];
+    for (int w0 = threadIdx.x; w0 < HALF * R1; w0 += NT * YU) {
+        float2 v[YU][R2];
 #pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) {
-            const int sl = R2 * k1 + k2;
-            v[k2] = ldg_inter<COH>(src + (size_t)sl * H + c);
-            if constexpr (MUL) v[k2] = cmul_is(v[k2], signed_k_mult<N>(slot_freq<N>(sl)));
+        for (int u = 0; u < YU; ++u) {
+            const int w = w0 + u * NT;
+            if ((HALF * R1) % (NT * YU) == 0 || w < HALF * R1) {
+                const int c = w % HALF, k1 = w / HALF;
+#pragma unroll
+                for (int k2 = 0; k2 < R2; ++k2) v[u][k2] = ldg_inter<COH>(src + (size_t)(R2 * k1 + k2) * H + c);
+            }
         }
-        RegDFT<R2, +1>::run(v);
 #pragma unroll
-        for (int n2 = 0; n2 < R2; ++n2) {
-            // k1 is warp-uniform when N/2 is a multiple of 32
-            const float2 t = (CTW && HALF % 32 == 0) ? tw_uniform<N>(n2 * k1) : twN[n2 * k1];
-            plane[(n2 * R1 + k1) * PW + c] = n2 ? cmulc(v[n2], t) : v[n2];
+        for (int u = 0; u < YU; ++u) {
+            const int w = w0 + u * NT;
+            if ((HALF * R1) % (NT * YU) == 0 || w < HALF * R1) {
+                const int c = w % HALF, k1 = w / HALF;
+                if constexpr (MUL) {
+#pragma unroll
+                    for (int k2 = 0; k2 < R2; ++k2)
+                        v[u][k2] = cmul_is(v[u][k2], signed_k_mult<N>(slot_freq<N>(R2 * k1 + k2)));
+                }
+                RegDFT<R2, +1>::run(v[u]);
+#pragma unroll
+                for (int n2 = 0; n2 < R2; ++n2) {
+                    // k1 is warp-uniform when N/2 is a multiple of 32
+                    const float2 t = (CTW && HALF % 32 == 0) ? tw_uniform<N>(n2 * k1) : twN[n2 * k1];
+                    plane[(n2 * R1 + k1) * PW + c] = n2 ? cmulc(v[u][n2], t) : v[u][n2];
+                }
+            }
         }
     }
     if (threadIdx.x < N) {
@@ -1052,7 +1066,14 @@ __device__ __forceinline__ void y_inverse_plane(const float2 *__restrict__ src, 
 //   Gz' -> y inverse -> rows paired likewise          -> Fz
 // The body of one pass C block: plane z of rotation r.  NT threads (the
 // kernel's 512 at N = 128, a persistent block's 256); COH as for ld_inter.
-template <int N, bool TQ, int NT = PassC<N>::NT, bool COH = false, int RBO = 0>
+// L2 prefetch of `bytes` (a multiple of 16, 16-byte aligned) at p
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// YU: y-stage items whose loads a thread keeps in flight; PF: prefetch the
+// block's Gz' plane into L2 when the block starts (it is read third)
+template <int N, bool TQ, int NT = PassC<N>::NT, bool COH = false, int RBO = 0, int YU = 1, bool PF = false>
 __device__ __forceinline__ void passC_body(const float2 *__restrict__ Y1, const float2 *__restrict__ Y2,
                                            const FieldPtrs &out, const float2 *__restrict__ YT, size_t yt_stride,
                                            unsigned zu, unsigned ru) {
@@ -1066,18 +1087,22 @@ __device__ __forceinline__ void passC_body(const float2 *__restrict__ Y1, const 
     float2 *twN = Tb + (size_t)RB * TP;
     const float2 *s1 = Y1 + ((size_t)r * N + z) * N * H;
     const size_t fo = (size_t)r * out.rot_stride + (size_t)z * N * N;
+    if constexpr (PF) {
+        static_assert((sizeof(float2) * N * H) % 16 == 0, "whole 16-byte units");
+        if (threadIdx.x == 0) prefetch_l2(Y2 + ((size_t)r * N + z) * N * H, (unsigned)(sizeof(float2) * N * H));
+    }
     load_tw<N>(twN);
     __syncthreads();
     // E + i Fx
-    y_inverse_plane<N, false, !TQ, NT, COH>(s1, plane, twN);
+    y_inverse_plane<N, false, !TQ, NT, COH, YU>(s1, plane, twN);
     // with the torque phases (TQ) this CTA reads its force rows back: keep them in L2
     x_pass<N, 0, PW, RB, TP, NT, N, !TQ, false, TQ>(plane, plane, 0, 0, Tb, twN, out.E + fo, out.Fx + fo);
     // Fy from Gy = i pi ky~ S'
-    y_inverse_plane<N, true, !TQ, NT, COH>(s1, plane, twN);
+    y_inverse_plane<N, true, !TQ, NT, COH, YU>(s1, plane, twN);
     x_pass<N, 1, PW, RB, TP, NT, HALF, !TQ, TQ, TQ>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, out.Fy + fo,
                                       out.Fy + fo + (size_t)HALF * N);
     // Fz
-    y_inverse_plane<N, false, !TQ, NT, COH>(Y2 + ((size_t)r * N + z) * N * H, plane, twN);
+    y_inverse_plane<N, false, !TQ, NT, COH, YU>(Y2 + ((size_t)r * N + z) * N * H, plane, twN);
     x_pass<N, 1, PW, RB, TP, NT, HALF, !TQ, TQ, TQ>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, out.Fz + fo,
                                       out.Fz + fo + (size_t)HALF * N);
     if constexpr (TQ) {
@@ -1093,13 +1118,13 @@ __device__ __forceinline__ void passC_body(const float2 *__restrict__ Y1, const 
     }
 }
 
-template <int N, bool TQ, int RBO = 0, int NTO = 0>
+template <int N, bool TQ, int RBO = 0, int NTO = 0, int YU = 1, bool PF = false>
 __global__ void __launch_bounds__(PassC<N, RBO, NTO>::NT, PassC<N, RBO, NTO>::MINB) passC_kernel(const float2 *__restrict__ Y1,
                                                                               const float2 *__restrict__ Y2,
                                                                               FieldPtrs out,
                                                                               const float2 *__restrict__ YT,
                                                                               size_t yt_stride) {
-    passC_body<N, TQ, PassC<N, RBO, NTO>::NT, false, RBO>(Y1, Y2, out, YT, yt_stride, blockIdx.x, blockIdx.y);
+    passC_body<N, TQ, PassC<N, RBO, NTO>::NT, false, RBO, YU, PF>(Y1, Y2, out, YT, yt_stride, blockIdx.x, blockIdx.y);
 }
 
 // the stationary moment fields G_a = (u x F)_a / h^3 (F = -h^3 grad rho1)
@@ -1381,8 +1406,11 @@ static cudaError_t set_smem_attrs() {
     if constexpr (N >= 64 && N <= 128) {  // the autotuner's tile candidates
         if ((e = cudaFuncSetAttribute(passB_kernel<N, 0, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N, 16>::smem))) return e;
         if ((e = cudaFuncSetAttribute(passC_kernel<N, false, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassC<N, 16>::smem))) return e;
-        if constexpr (N == 128)
+        if constexpr (N == 128) {
             if ((e = cudaFuncSetAttribute(passC_kernel<N, false, 0, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassC<N, 0, 256>::smem))) return e;
+            if ((e = cudaFuncSetAttribute(passC_kernel<N, false, 0, 256, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassC<N, 0, 256>::smem))) return e;
+            if ((e = cudaFuncSetAttribute(passC_kernel<N, false, 0, 256, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassC<N, 0, 256>::smem))) return e;
+        }
     }
     if ((e = cudaFuncSetAttribute(passC_kernel<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassC<N>::smem))) return e;
     if ((e = cudaFuncSetAttribute(passB_torque_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1437,10 +1465,10 @@ static cudaError_t launch_passB_spectral(const float2 *table, cudaTextureObject_
         nullptr, R1hat, Y1, Y2, 0.f, SpecSrc{table, os * N, os, tex, table_tex_sc(os * N)}, rot9);
     return cudaGetLastError();
 }
-template <int N, int RBO = 0, int NTO = 0>
+template <int N, int RBO = 0, int NTO = 0, int YU = 1, bool PF = false>
 static cudaError_t launch_passC(const float2 *Y1, const float2 *Y2, FieldPtrs out, int nrot, cudaStream_t st) {
     using PC = PassC<N, RBO, NTO>;
-    passC_kernel<N, false, RBO, NTO><<<dim3(N, nrot), PC::NT, PC::smem, st>>>(Y1, Y2, out, nullptr, 0);
+    passC_kernel<N, false, RBO, NTO, YU, PF><<<dim3(N, nrot), PC::NT, PC::smem, st>>>(Y1, Y2, out, nullptr, 0);
     return cudaGetLastError();
 }
 template <int N>
@@ -1701,6 +1729,10 @@ cudaError_t run_passC(int n, const float2 *Y1, const float2 *Y2, FieldPtrs out, 
         }
     } else if (tile == 2 && n == 128) {  // 256 threads per CTA
         return launch_passC<128, 0, 256>(Y1, Y2, out, nrot, st);
+    } else if (tile == 3 && n == 128) {  // and an L2 prefetch of the Gz' plane
+        return launch_passC<128, 0, 256, 1, true>(Y1, Y2, out, nrot, st);
+    } else if (tile == 4 && n == 128) {  // and two y-stage items' loads in flight
+        return launch_passC<128, 0, 256, 2, true>(Y1, Y2, out, nrot, st);
     }
     HF_DISPATCH(n, launch_passC<NN>(Y1, Y2, out, nrot, st));
 }

@@ -197,6 +197,9 @@ cudaError_t run_query_one(const QueryGeom &g, Pose7 pose, int k, float *out, cud
 // pinned 7-float answer mailbox with its device alias); synchronous
 struct hf_fieldset;
 int hf_ctx_device(const hf_ctx *c);
+// a reference to the context, held by every object made from it
+void hf_ctx_retain(hf_ctx *c);
+void hf_ctx_release(hf_ctx *c);
 // whether the set's last compute enqueued all of its work
 bool hf_fieldset_is_ready(const hf_fieldset *fs);
 void hf_fieldset_mark_ready(hf_fieldset *fs);

@@ -198,11 +198,17 @@ __global__ void __launch_bounds__(kTorqueThreads) torque_kernel(const float *__r
                 }
             }
         } else {
+            // the 3 x 6 product in float64 over float32 differences: a
+            // difference of two float32 energies within a factor of two of
+            // each other (neighbouring rotations, the common case) is exact in
+            // float32 (Sterbenz), and otherwise carries one rounding of at
+            // most 2^-24 of itself; the float64 pipe then does 18 fma per cell
+            // instead of 6 subtractions more
             double gd[3][4] = {};
 #pragma unroll
             for (int s = 0; s < 6; ++s) {
-                const double b[4] = {(double)ej[j][s].x - ei[j].x, (double)ej[j][s].y - ei[j].y,
-                                     (double)ej[j][s].z - ei[j].z, (double)ej[j][s].w - ei[j].w};
+                const double b[4] = {(double)(ej[j][s].x - ei[j].x), (double)(ej[j][s].y - ei[j].y),
+                                     (double)(ej[j][s].z - ei[j].z), (double)(ej[j][s].w - ei[j].w)};
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
                     const double w = __ldg(P64 + 18 * r + 6 * d + s);

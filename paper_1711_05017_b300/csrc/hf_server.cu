@@ -447,6 +447,7 @@ extern "C" hf_status hf_server_create(hf_ctx *ctx, int max_inflight, int query_l
         return srv_fail(HF_EINVAL, "hf_server_create: max_inflight %d, query_lanes %d", max_inflight, query_lanes);
     hf_server *s = new hf_server();
     s->ctx = ctx;
+    hf_ctx_retain(ctx);
     s->max_inflight = max_inflight;
     s->chunk_bytes = hf_ctx_budget_bytes(ctx) / 3;
     s->t0 = now_ms();
@@ -461,6 +462,22 @@ extern "C" hf_status hf_server_create(hf_ctx *ctx, int max_inflight, int query_l
     if (e == cudaSuccess) {
         uint64_t keep = UINT64_MAX;
         e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    // and reserve the budget in the pool now: mapping tens of GB on the first
+    // builds took the driver 10+ ms, during which query launches waited
+    const size_t budget = hf_ctx_budget_bytes(ctx), held = hf_ctx_reserved_bytes(ctx);
+    size_t free_b = 0, total_b = 0;
+    if (e == cudaSuccess && budget > held && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+        const size_t margin = (size_t)4 << 30;
+        const size_t want = std::min(budget - held, free_b > margin ? free_b - margin : 0);
+        cudaStream_t tmp = nullptr;
+        void *blk = nullptr;
+        if (want > 0 && cudaStreamCreateWithFlags(&tmp, cudaStreamNonBlocking) == cudaSuccess) {
+            if (cudaMallocAsync(&blk, want, tmp) == cudaSuccess) cudaFreeAsync(blk, tmp);
+            cudaStreamSynchronize(tmp);
+            cudaStreamDestroy(tmp);
+        }
+        (void)cudaGetLastError();  // a reservation that does not fit is not an error
     }
     int lo = 0, hi = 0;
     if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
@@ -509,7 +526,9 @@ extern "C" void hf_server_destroy(hf_server *s) {
         cudaDeviceSynchronize();
         cudaMemPoolTrimTo(pool, 0);
     }
+    hf_ctx *c = s->ctx;
     delete s;
+    hf_ctx_release(c);
 }
 
 extern "C" hf_status hf_server_set_chunk_bytes(hf_server *s, size_t bytes) {
