@@ -286,11 +286,12 @@ def run_ours(args, rank, world, local_rank):
         "query": N_QUERY * 7 * 4 * 2,
         "resample": n3b + chunk * n3b,
     }
-    # dram__bytes_read.sum + dram__bytes_write.sum of one pass C launch over
-    # 32 rotations at 128^3 (profiles/fieldbuild_kernels_c2_128.md), scaled to
-    # this launch's rotations: the traffic is per rotation (each reads its own
-    # two spectra and writes its own four fields)
-    traffic = {"passC": 1.5809e9 * chunk / 32} if n == 128 and not tune_is_pencil(ctx, n) else {}
+    # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the
+    # tuned pass C kernel (256 threads per CTA) over 32 rotations at 128^3,
+    # scaled to this launch's rotations: the traffic is per rotation (each
+    # reads its own two spectra and writes its own four fields); none for
+    # another launch shape
+    traffic = {"passC": 1.5742e9 * chunk / 32} if n == 128 and not tune_is_pencil(ctx, n) and ctx.tune_tiles(n)[1] == 2 else {}
     hbm_peak, peak_kind = peaks()
     kernels = {}
     for k, (cnt, tot) in prof.items():
