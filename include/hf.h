@@ -531,6 +531,12 @@ hf_status hf_tune_get(const hf_ctx *ctx, int n, int *chunk, int *pencil, double 
  * fields do not change, only their speed), else reads them.  Errors:
  * HF_EINVAL, HF_EUNSUPPORTED. */
 hf_status hf_tune_tiles(hf_ctx *ctx, int n, int set, int *tile_b, int *tile_c);
+/* Pipelines a field-set compute at grid n runs (1, or 2 alternating its
+ * rotation chunks over two streams so that passes of neighbouring chunks
+ * overlap on the device; twice the intermediates).  set != 0 stores *lanes,
+ * else reads it.  The HF_LANES environment variable, when set, overrides it.
+ * Errors: HF_EINVAL, HF_EUNSUPPORTED. */
+hf_status hf_tune_lanes(hf_ctx *ctx, int n, int set, int *lanes);
 
 /* Number of tensor-core stage thread blocks whose bounded wait for their own
  * matrix operations gave up since the last reset (each such block wrote no

@@ -141,6 +141,12 @@ class Context:
                                       ctypes.byref(tc)))
         return tb.value, tc.value
 
+    def tune_lanes(self, n, lanes=None):
+        """hf_tune_lanes: read, or set (1 or 2), the pipelines of a compute at grid n."""
+        v = ctypes.c_int(int(lanes) if lanes is not None else 0)
+        B.check(B.lib().hf_tune_lanes(self.handle, int(n), 1 if lanes is not None else 0, ctypes.byref(v)))
+        return v.value
+
     def tune_get(self, n):
         c, p, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
         B.check(B.lib().hf_tune_get(self.handle, int(n), ctypes.byref(c), ctypes.byref(p), ctypes.byref(r)))

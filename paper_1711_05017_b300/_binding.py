@@ -99,6 +99,7 @@ SIGNATURES = {
     "hf_tune_set": (_i, [_vp, _i, _i, _i]),
     "hf_tune_get": (_i, [_vp, _i, _ip, _ip, ctypes.POINTER(ctypes.c_double)]),
     "hf_tune_tiles": (_i, [_vp, _i, _i, _ip, _ip]),
+    "hf_tune_lanes": (_i, [_vp, _i, _i, _ip]),
     "hf_tc_timeouts": (_i, [_i]),
     "hf_part_spectral": (_i, [_vp, _i, _vp]),
     "hf_part_spectral_os": (_i, [_vp]),

@@ -62,6 +62,7 @@ struct Tune {  // the autotuner's choice for one grid size
     int chunk = 0;
     int pencil = 0;
     int tile_b = 0, tile_c = 0;  // launch-shape candidates of passes B and C (hf::run_passB/C)
+    int lanes = 1;               // 2: alternate chunks over two streams, so passes of neighbouring chunks overlap
     double rot_per_s = 0;
 };
 static int tune_slot(int n) { return n == 32 ? 0 : n == 64 ? 1 : n == 96 ? 2 : n == 128 ? 3 : 4; }
@@ -975,7 +976,8 @@ static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags,
     fs->chunk = std::min(fs->chunk, R);
     {
         const char *ev = getenv("HF_LANES");
-        fs->lanes = (ev && atoi(ev) == 2) ? 2 : 1;
+        const Tune &t = ctx->tune[tune_slot(n)];
+        fs->lanes = ev ? ((atoi(ev) == 2) ? 2 : 1) : (t.set && t.lanes == 2 ? 2 : 1);
     }
     const size_t n3 = (size_t)n * n * n;
     const size_t data_b = (size_t)R * nf * n3 * sizeof(float);
@@ -1614,6 +1616,24 @@ extern "C" hf_status hf_tune_tiles(hf_ctx *ctx, int n, int set, int *tile_b, int
     return HF_OK;
 }
 
+extern "C" hf_status hf_tune_lanes(hf_ctx *ctx, int n, int set, int *lanes) {
+    if (!ctx || !lanes) return fail(HF_EINVAL, "hf_tune_lanes: NULL argument");
+    if (!hf::supported_n(n)) return fail(HF_EUNSUPPORTED, "hf_tune_lanes: N=%d not supported", n);
+    Tune &t = ctx->tune[tune_slot(n)];
+    if (set) {
+        if (*lanes != 1 && *lanes != 2) return fail(HF_EINVAL, "hf_tune_lanes: lanes %d", *lanes);
+        if (!t.set) {
+            t.set = true;
+            t.chunk = default_chunk(n);
+            t.pencil = hf::pencil_n(n);
+        }
+        t.lanes = *lanes;
+    } else {
+        *lanes = t.set ? t.lanes : 1;
+    }
+    return HF_OK;
+}
+
 namespace {
 std::string tune_device_key(int device) {
     cudaDeviceProp p;
@@ -1648,13 +1668,13 @@ std::string tune_json_line(const std::string &dev, int n, const Tune &t, const s
     char buf[512];
     snprintf(buf, sizeof buf,
              "{\"device\": \"%s\", \"n\": %d, \"chunk\": %d, \"pipeline\": \"%s\", \"tile_b\": %d, \"tile_c\": %d, "
-             "\"radix\": \"%s\", \"passB_columns_per_cta\": %d, \"passC_rows_per_x_batch\": %d, "
+             "\"lanes\": %d, \"radix\": \"%s\", \"passB_columns_per_cta\": %d, \"passC_rows_per_x_batch\": %d, "
              "\"passC_threads\": %d, \"rot_per_s\": %.6g}",
-             dev.c_str(), n, t.chunk, t.pencil ? "pencil" : "slab", t.tile_b, t.tile_c, tune_radix(n),
+             dev.c_str(), n, t.chunk, t.pencil ? "pencil" : "slab", t.tile_b, t.tile_c, t.lanes, tune_radix(n),
              tune_pass_b_columns(n, t.tile_b), tune_pass_c_rows(n, t.tile_c), tune_pass_c_threads(n, t.tile_c),
              t.rot_per_s);
     std::string l = buf;
-    if (!cands.empty()) {  // every timed candidate: [chunk, pencil, tile_b, tile_c, rot_per_s]
+    if (!cands.empty()) {  // every timed candidate: [chunk, pencil, tile_b, tile_c, lanes, rot_per_s]
         l.pop_back();
         l += ", \"candidates\": [" + cands + "]}";
     }
@@ -1704,6 +1724,7 @@ bool tune_cache_read(const char *path, const std::string &dev, int n, Tune &t) {
         t.pencil = json_field(l, "pipeline") == "pencil";
         t.tile_b = atoi(json_field(l, "tile_b").c_str());
         t.tile_c = atoi(json_field(l, "tile_c").c_str());
+        t.lanes = json_field(l, "lanes") == "2" ? 2 : 1;
         t.rot_per_s = atof(json_field(l, "rot_per_s").c_str());
         hit = true;
     }
@@ -1785,8 +1806,8 @@ extern "C" hf_status hf_autotune(hf_ctx *ctx, int n, const char *cache_path, int
         std::string cands;  // every timed candidate, for the cache file
         auto note = [&](const Tune &t, double rps) {
             char b[96];
-            snprintf(b, sizeof b, "%s[%d, %d, %d, %d, %.6g]", cands.empty() ? "" : ", ", t.chunk, t.pencil ? 1 : 0,
-                     t.tile_b, t.tile_c, rps);
+            snprintf(b, sizeof b, "%s[%d, %d, %d, %d, %d, %.6g]", cands.empty() ? "" : ", ", t.chunk,
+                     t.pencil ? 1 : 0, t.tile_b, t.tile_c, t.lanes, rps);
             cands += b;
         };
         cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1855,6 +1876,34 @@ extern "C" hf_status hf_autotune(hf_ctx *ctx, int n, const char *cache_path, int
                         best.rot_per_s = rps;
                     }
                 }
+        }
+        // two pipelines alternating chunks on two streams, at the best shape
+        if (best.set && getenv("HF_LANES") == nullptr) {
+            Tune &t = ctx->tune[tune_slot(n)];
+            t = best;
+            t.lanes = 2;
+            hf_fieldset *fs = nullptr;
+            if (hf_fieldset_create(ctx, n, R, HF_E | HF_F, &fs) == HF_OK) {
+                float best_ms = 1e30f;
+                hf_status bs = hf_fieldset_compute(ctx, s1, s2, quats.data(), R, fs, nullptr);
+                for (int rep = 0; rep < 3 && bs == HF_OK; ++rep) {
+                    cudaEventRecord(e0, nullptr);
+                    bs = hf_fieldset_compute(ctx, s1, s2, quats.data(), R, fs, nullptr);
+                    cudaEventRecord(e1, nullptr);
+                    float ms = 0;
+                    if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+                        best_ms = std::min(best_ms, ms);
+                }
+                hf_fieldset_release(fs);
+                if (bs == HF_OK && best_ms < 1e29f) {
+                    const double rps = R / (best_ms * 1e-3);
+                    note(t, rps);
+                    if (rps > best.rot_per_s) {
+                        best = t;
+                        best.rot_per_s = rps;
+                    }
+                }
+            }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);

@@ -233,6 +233,12 @@ def test_tile_candidates_give_the_same_fields(hf, n):
             assert np.array_equal(got, base), (tb, tc)
     with pytest.raises(hf.HFError):
         ctx.tune_tiles(n, (0, 2) if n != 128 else (2, 0))
+    # two pipelines alternating chunks on two streams: the same fields
+    ctx.tune_tiles(n, (0, 0))
+    ctx.tune_set(n, 4)
+    assert ctx.tune_lanes(n, 2) == 2 and ctx.tune_lanes(n) == 2
+    got = all_fields(plain(hf, ctx, pair, q, hf.HF_E | hf.HF_F), 10, 4)
+    assert np.array_equal(got, base)
 
 
 # ------------------------------------------------ one launch over a work queue
