@@ -201,8 +201,14 @@ __device__ __forceinline__ float pi_k_signed(int k) {  // pi k~, 0 at the Nyquis
 // One length-256 y transform per column of a 32-column tile.  Forward
 // (INV = false): src rows in natural y order, dst rows in the digit-permuted
 // slot order of the FP32 pipeline (slot 16 k1 + k2 for ky = k1 + 16 k2).
-// Inverse: src rows in slot order, dst in natural y.  blockIdx.z selects
-// (src0 -> dst0), (src0 times i pi ky~ -> dst1) or (src1 -> dst2).
+// Inverse: src rows in slot order, dst in natural y; blockIdx.z = 0 runs two
+// transforms from one load of src0, src0 -> dst0 and src0 times i pi ky~ ->
+// dst1, and blockIdx.z = 1 runs src1 -> dst2.
+//
+// Operand staging: every thread writes its rows' K-values as 16-byte vectors
+// (4 complex values of consecutive K digit b), so a warp's stores fill whole
+// 128-byte rows of the K-major core matrices without bank conflicts; the
+// element locations (kmaj_off) are those the descriptors read.
 template <bool INV, bool F16>
 __global__ void __launch_bounds__(NT, 2) y_tc_kernel(const float2 *__restrict__ src0, const float2 *__restrict__ src1,
                                                      float2 *__restrict__ dst0, float2 *__restrict__ dst1,
@@ -218,8 +224,8 @@ __global__ void __launch_bounds__(NT, 2) y_tc_kernel(const float2 *__restrict__ 
     // outputs are invalid either way) so that a failure ends quickly
     if (*reinterpret_cast<volatile int *>(&g_tc_timeouts) != 0) return;
     const int set = blockIdx.z;
-    const float2 *src = set == 2 ? src1 : src0;
-    float2 *dst = set == 0 ? dst0 : (set == 1 ? dst1 : dst2);
+    const float2 *src = set == 1 ? src1 : src0;
+    const int ntr = (INV && set == 0) ? 2 : 1;  // transforms of this block
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int f = blockIdx.x * CT + lane;  // flattened (z, kx slot) column of this lane
     const int zc = f / H, cc = f - zc * H;
@@ -249,52 +255,23 @@ __global__ void __launch_bounds__(NT, 2) y_tc_kernel(const float2 *__restrict__ 
         *reinterpret_cast<uint16_t *>(Bhi + kmaj_off(jj, kk)) = h;
         *reinterpret_cast<uint16_t *>(Blo + kmaj_off(jj, kk)) = l;
     }
-    // stage-1 operand: warp w loads rows y = w + 8 i of the tile's 32 columns
+    // stage-1 operand rows: thread (warp w) holds, for 8 (group digit a,
+    // K block m) pairs p = w + 8 q, the 4 input rows of K digits b = 4 m ..
+    // 4 m + 3 of group a.  Forward: input row y = a + 16 b; inverse: the row
+    // of slot order holding frequency a + 16 b, i.e. slot 16 a + b.
     float2 x[32];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) x[i] = src[col + (size_t)(warp + 8 * i) * H];
-    if (set == 1) {
+    for (int q = 0; q < 8; ++q) {
+        const int p = warp + 8 * q, a = p >> 2, m = p & 3;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) x[i] = cmul_is(x[i], pi_k_signed(slot_freq<N>(warp + 8 * i)));
-    }
-    float scale = 1.f, unscale = 1.f;
-    if constexpr (F16) {  // a power of two bringing the tile's largest magnitude into [0.5, 1)
-        float m = 0.f;
-#pragma unroll
-        for (int i = 0; i < 32; ++i) m = fmaxf(m, fmaxf(fabsf(x[i].x), fabsf(x[i].y)));
-#pragma unroll
-        for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0) red[warp] = m;
-        __syncthreads();
-        m = red[0];
-#pragma unroll
-        for (int w = 1; w < NT / 32; ++w) m = fmaxf(m, red[w]);
-        if (m > 0.f && isfinite(m)) {
-            int e;
-            frexpf(m, &e);
-            scale = ldexpf(1.f, -e);
-            unscale = ldexpf(1.f, e);
+        for (int u = 0; u < 4; ++u) {
+            const int b = 4 * m + u;
+            const int y = INV ? 16 * a + b : a + 16 * b;
+            x[4 * q + u] = src[col + (size_t)y * H];
         }
     }
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
-        const int y = warp + 8 * i;
-        int a, b;  // GEMM row group and K digit of input row y
-        if (INV) {
-            const int k = slot_freq<N>(y);
-            a = k & 15;
-            b = k >> 4;
-        } else {
-            a = y & 15;
-            b = y >> 4;
-        }
-        uint32_t hi, lo;
-        split2<F16>(x[i].x * scale, x[i].y * scale, hi, lo);
-        const uint32_t off = kmaj_off(a * CT + lane, 2 * b);
-        *reinterpret_cast<uint32_t *>(Ahi + off) = hi;
-        *reinterpret_cast<uint32_t *>(Alo + off) = lo;
-    }
-    fence_async_smem();
+    // the tensor-memory address that warp 0's allocation wrote, and the
+    // initialised mbarrier, are visible to every thread after this barrier
     fence_before();
     __syncthreads();
     fence_after();
@@ -316,66 +293,122 @@ __global__ void __launch_bounds__(NT, 2) y_tc_kernel(const float2 *__restrict__ 
         }
         mma_commit(sbar);
     };
-    if (threadIdx.x == 0) issue();
-    bool ok = mbar_wait(sbar, 0);
-    fence_after();
     const int sp = warp & 3;
-    if (ok) {
-        // stage-1 epilogue: twiddle, split, and re-stage as the stage-2 operand
-        // (rows (j, column), K digit a)
+    bool ok = true;
+    uint32_t phase = 0;
+    for (int tr = 0; tr < ntr && ok; ++tr) {
+        float2 *dst = set == 1 ? dst2 : (tr == 0 ? dst0 : dst1);
+        if (INV && set == 0 && tr == 1) {  // Gy = i pi ky~ S, ky~ of the row's slot (S is no longer needed)
 #pragma unroll
-        for (int tt = 0; tt < 2; ++tt) {
-            const int t = (warp >> 2) * 2 + tt;
-            const int a = 4 * t + sp;
+            for (int i = 0; i < 32; ++i) {
+                const int q = i >> 2, u = i & 3, p = warp + 8 * q;
+                x[i] = cmul_is(x[i], pi_k_signed(slot_freq<N>(16 * (p >> 2) + 4 * (p & 3) + u)));
+            }
+        }
+        float scale = 1.f, unscale = 1.f;
+        if constexpr (F16) {  // a power of two bringing the tile's largest magnitude into [0.5, 1)
+            float mx = 0.f;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                float v[16];
-                load_acc<F16>(tbase, sp, t, h, v);
+            for (int i = 0; i < 32; ++i) mx = fmaxf(mx, fmaxf(fabsf(x[i].x), fabsf(x[i].y)));
 #pragma unroll
-                for (int jl = 0; jl < RD / 2; ++jl) {
-                    const int j = 8 * h + jl;
-                    const int tw = (a * j) & (N - 1);
-                    const float c = g_trig.c[tw], s = INV ? g_trig.s[tw] : -g_trig.s[tw];
-                    const float re = v[2 * jl] * c - v[2 * jl + 1] * s, im = v[2 * jl] * s + v[2 * jl + 1] * c;
-                    uint32_t hi, lo;
-                    split2<F16>(re, im, hi, lo);
-                    const uint32_t off = kmaj_off(j * CT + lane, 2 * a);
-                    *reinterpret_cast<uint32_t *>(Ahi + off) = hi;
-                    *reinterpret_cast<uint32_t *>(Alo + off) = lo;
+            for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            __syncthreads();  // the previous transform's readers of red are done
+            if (lane == 0) red[warp] = mx;
+            __syncthreads();
+            mx = red[0];
+#pragma unroll
+            for (int w = 1; w < NT / 32; ++w) mx = fmaxf(mx, red[w]);
+            if (mx > 0.f && isfinite(mx)) {
+                int e;
+                frexpf(mx, &e);
+                scale = ldexpf(1.f, -e);
+                unscale = ldexpf(1.f, e);
+            }
+        }
+        // the stage-1 operand: per (a, m) one 16-byte vector of hi and one of lo
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int p = warp + 8 * q, a = p >> 2, m = p & 3;
+            uint4 vh, vl;
+            split2<F16>(x[4 * q + 0].x * scale, x[4 * q + 0].y * scale, vh.x, vl.x);
+            split2<F16>(x[4 * q + 1].x * scale, x[4 * q + 1].y * scale, vh.y, vl.y);
+            split2<F16>(x[4 * q + 2].x * scale, x[4 * q + 2].y * scale, vh.z, vl.z);
+            split2<F16>(x[4 * q + 3].x * scale, x[4 * q + 3].y * scale, vh.w, vl.w);
+            const uint32_t off = kmaj_off(a * CT + lane, 8 * m);
+            *reinterpret_cast<uint4 *>(Ahi + off) = vh;
+            *reinterpret_cast<uint4 *>(Alo + off) = vl;
+        }
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        fence_after();
+        if (threadIdx.x == 0) issue();
+        ok = mbar_wait(sbar, phase);
+        phase ^= 1;
+        fence_after();
+        if (ok) {
+            // stage-1 epilogue: twiddle, split, and re-stage as the stage-2 operand
+            // (rows (j, column), K digit a)
+#pragma unroll
+            for (int tt = 0; tt < 2; ++tt) {
+                const int t = (warp >> 2) * 2 + tt;
+                const int a = 4 * t + sp;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    float v[16];
+                    load_acc<F16>(tbase, sp, t, h, v);
+#pragma unroll
+                    for (int jl = 0; jl < RD / 2; ++jl) {
+                        const int j = 8 * h + jl;
+                        const int tw = (a * j) & (N - 1);
+                        const float c = g_trig.c[tw], s = INV ? g_trig.s[tw] : -g_trig.s[tw];
+                        const float re = v[2 * jl] * c - v[2 * jl + 1] * s, im = v[2 * jl] * s + v[2 * jl + 1] * c;
+                        uint32_t hi, lo;
+                        split2<F16>(re, im, hi, lo);
+                        const uint32_t off = kmaj_off(j * CT + lane, 2 * a);
+                        *reinterpret_cast<uint32_t *>(Ahi + off) = hi;
+                        *reinterpret_cast<uint32_t *>(Alo + off) = lo;
+                    }
                 }
             }
         }
-    }
-    fence_async_smem();
-    fence_before();
-    __syncthreads();
-    fence_after();
-    ok = __syncthreads_and(ok);
-    if (ok) {
-        if (threadIdx.x == 0) issue();
-        ok = mbar_wait(sbar, 1);
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
         fence_after();
         ok = __syncthreads_and(ok);
-    }
-    if (ok) {
-        // stage-2 epilogue: row (j, column) holds the 16 outputs of digit o
+        if (ok) {
+            if (threadIdx.x == 0) issue();
+            ok = mbar_wait(sbar, phase);
+            phase ^= 1;
+            fence_after();
+            ok = __syncthreads_and(ok);
+        }
+        if (ok) {
+            // stage-2 epilogue: row (j, column) holds the 16 outputs of digit o
 #pragma unroll
-        for (int tt = 0; tt < 2; ++tt) {
-            const int t = (warp >> 2) * 2 + tt;
-            const int j = 4 * t + sp;
+            for (int tt = 0; tt < 2; ++tt) {
+                const int t = (warp >> 2) * 2 + tt;
+                const int j = 4 * t + sp;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                float v[16];
-                load_acc<F16>(tbase, sp, t, h, v);
+                for (int h = 0; h < 2; ++h) {
+                    float v[16];
+                    load_acc<F16>(tbase, sp, t, h, v);
 #pragma unroll
-                for (int ol = 0; ol < RD / 2; ++ol) {
-                    const int o = 8 * h + ol;
-                    const int row = INV ? j + RD * o : perm_slot<N>(j + RD * o);
-                    dst[col + (size_t)row * H] = make_float2(v[2 * ol] * unscale, v[2 * ol + 1] * unscale);
+                    for (int ol = 0; ol < RD / 2; ++ol) {
+                        const int o = 8 * h + ol;
+                        const int row = INV ? j + RD * o : perm_slot<N>(j + RD * o);
+                        dst[col + (size_t)row * H] = make_float2(v[2 * ol] * unscale, v[2 * ol + 1] * unscale);
+                    }
                 }
             }
+            // the next transform's operand overwrites A and the accumulators
+            fence_before();
+            __syncthreads();
+            fence_after();
         }
-    } else if (threadIdx.x == 0) {
+    }
+    if (!ok && threadIdx.x == 0) {
         atomicAdd(&g_tc_timeouts, 1);
         // give a stalled MMA group a last bounded chance to drain before the
         // tensor memory is released
@@ -401,7 +434,7 @@ static cudaError_t launch(const float2 *s0, const float2 *s1, float2 *d0, float2
         if (e) return e;
         attr = true;
     }
-    const dim3 grid(N * H / CT, nrot, INV ? 3 : 1);
+    const dim3 grid(N * H / CT, nrot, INV ? 2 : 1);
     y_tc_kernel<INV, F16><<<grid, NT, SMEM, st>>>(s0, s1, d0, d1, d2);
     return cudaGetLastError();
 }
