@@ -122,6 +122,14 @@ const char *hf_version(void);
 /* Thread-local message describing the calling thread's last failure. */
 const char *hf_last_error(void);
 
+/* Test hook for the error paths: the nth device, array or pinned-host
+ * allocation the library makes from now on (any thread, any handle) fails as
+ * if the device were out of memory; nth <= 0 turns it off.  *count (may be
+ * NULL) receives the number of allocations made so far, so a test counts an
+ * operation's allocations and then fails each in turn.  The allocation-free
+ * entry point's own set-up is not counted. */
+void hf_inject_alloc_failure(long long nth, long long *count);
+
 /* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the
  * device memory the context's handles may hold (0 = no bound).
  * Errors: HF_EINVAL (null out, bad device), HF_ECUDA. */
@@ -176,6 +184,9 @@ hf_status hf_density_mesh(hf_ctx *ctx, int n, const double *d_V, int nv, const i
  * Errors: HF_EINVAL, HF_EBUDGET, HF_ENOMEM, HF_ECUDA. */
 hf_status hf_part_create(hf_ctx *ctx, int n, const float *d_grid, int role, hf_part **out,
                          hf_stream stream);
+/* Drops the caller's handle.  Server sessions, their builds in flight and
+ * batches hold references of their own: the part's memory is freed when the
+ * last of them goes, so the caller may release a part they still use. */
 void hf_part_release(hf_part *part);
 /* Grid size of a part (0 for NULL). */
 int hf_part_n(const hf_part *part);
@@ -387,16 +398,20 @@ void hf_server_destroy(hf_server *srv);
 /* Requests whose field set exceeds `bytes` are split into chunks (0: never). */
 hf_status hf_server_set_chunk_bytes(hf_server *srv, size_t bytes);
 /* A session over a stationary part s1 and a moving part s2 of the same N
- * (both stay owned by the caller and must outlive the session). */
+ * (the session holds a reference to each until it is closed, and a build of
+ * the session in flight holds its own until it completes). */
 hf_status hf_server_session_open(hf_server *srv, const hf_part *s1, const hf_part *s2, int *session);
+/* Closes a session: its published fields are retired once their readers let
+ * go, and its unfinished requests end failed (state 3). */
 hf_status hf_server_session_close(hf_server *srv, int session);
 /* Queue a field build for R rotations (h_quat R x 4, copied); HF_EBUDGET if
  * it could never fit (unchunked and above the budget, or a chunk of one
  * rotation and its halo above the chunk limit). */
 hf_status hf_server_submit(hf_server *srv, int session, const float *h_quat, int R, unsigned flags,
                            int64_t *request);
-/* State of a request and, once done (every chunk published), its latency
- * submit -> published (ms). */
+/* State of a request (0 queued, 1 running, 2 done, 3 failed, 4 superseded)
+ * and, once done (every chunk published), its latency submit -> published
+ * (ms). */
 hf_status hf_server_request_state(hf_server *srv, int64_t request, int *state, double *latency_ms);
 /* Number of chunks of a request and (h_owner, R ints, may be NULL) the chunk
  * owning each rotation. */
@@ -411,6 +426,18 @@ hf_status hf_server_field_ptr(hf_server *srv, int session, int rot, int field, c
 /* Copy that field to d_dst (N^3 floats), on `stream`. */
 hf_status hf_server_field_get(hf_server *srv, int session, int rot, int field, float *d_dst, hf_stream stream);
 hf_status hf_server_stats_get(hf_server *srv, hf_server_stats *out);
+/* A metrics log in JSON lines: appends to `path` one line every period_ms
+ * (>= 10) from a thread of its own, and a last line at hf_server_log_close
+ * or hf_server_destroy; opening again closes the previous log first.  Each
+ * line: t_s (since the server's creation), period_s, the hf_server_stats
+ * counters, "query" {n, p50_us, p99_us, p999_us, max_us} of the queries
+ * answered in the period, "build" {n, p50_ms, p99_ms, max_ms} of the requests
+ * finished in it (submit -> published), and "session_queries" [[session,
+ * answered, not_ready], ...] totals of the open sessions.  Percentiles are
+ * upper edges of log-spaced bins (8 per octave: within 9%); null when n = 0.
+ * Errors: HF_EINVAL (bad period, unopenable path). */
+hf_status hf_server_log_open(hf_server *srv, const char *path, int period_ms);
+hf_status hf_server_log_close(hf_server *srv);
 /* Save a session's published data (its request's rotations and routing and
  * every resident chunk's field set) to a checkpoint file, and restore such a
  * file as the current data of an open session over parts of the same N
@@ -451,7 +478,8 @@ hf_status hf_server_drive_queries(hf_server *srv, int nsess, const int *sessions
  * the same grid size and rotation count share k slots round-robin, so a
  * scene whose fields exceed the device streams through k sets per size (a
  * slot then holds the last of its pairs after a launch).  Pairs in one slot
- * run in order; slots run concurrently.  Parts must outlive the batch.
+ * run in order; slots run concurrently.  The batch holds a reference to each
+ * part until it is released.
  *
  *   hf_batch_create      npairs pairs (s1[i] stationary, s2[i] moving, both of
  *                        one size), R[i] rotations each; flags as for

@@ -331,7 +331,7 @@ class Batch:
         h = ctypes.c_void_p()
         B.check(B.lib().hf_batch_create(ctx.handle, n, S1, S2, Rs, int(flags), int(slots_per_size), ctypes.byref(h)))
         self.handle, self.ctx, self.npairs = h, ctx, n
-        self._pairs = list(pairs)  # the parts must outlive the batch
+        self._pairs = list(pairs)
 
     def set_rotations(self, pair, quats, allow_rank_deficient=False):
         q = np.ascontiguousarray(quats, dtype=np.float32).reshape(-1, 4)
@@ -423,6 +423,14 @@ def rfft3d(x, out=None, stream=None):
     if stream is not None:
         scratch.record_stream(stream)
     return out
+
+
+def inject_alloc_failure(nth=0):
+    """hf_inject_alloc_failure: the library's nth allocation from now on fails
+    as out of memory (nth <= 0: off); returns the allocations made so far."""
+    c = ctypes.c_longlong()
+    B.lib().hf_inject_alloc_failure(int(nth), ctypes.byref(c))
+    return c.value
 
 
 def checkpoint_info(path):
@@ -571,6 +579,14 @@ class Server:
         buf = np.empty(max_n, dtype=np.float32)
         n = B.lib().hf_server_query_latencies(self.handle, B.fptr(buf), int(max_n))
         return buf[:n].copy()
+
+    def log_open(self, path, period_ms=1000):
+        """hf_server_log_open: a JSON-lines metrics log appended to `path`
+        every period_ms (counters, per-period query and build percentiles)."""
+        B.check(B.lib().hf_server_log_open(self.handle, os.fsencode(path), int(period_ms)))
+
+    def log_close(self):
+        B.check(B.lib().hf_server_log_close(self.handle))
 
     def stats(self):
         st = B.ServerStats()

@@ -28,6 +28,7 @@ _ip = ctypes.POINTER(ctypes.c_int)
 SIGNATURES = {
     "hf_version": (ctypes.c_char_p, []),
     "hf_last_error": (ctypes.c_char_p, []),
+    "hf_inject_alloc_failure": (None, [ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]),
     "hf_ctx_create": (_i, [_i, _sz, ctypes.POINTER(_vp)]),
     "hf_ctx_destroy": (None, [_vp]),
     "hf_ctx_reserved_bytes": (_sz, [_vp]),
@@ -71,6 +72,8 @@ SIGNATURES = {
     "hf_server_field_ptr": (_i, [_vp, _i, _i, _i, ctypes.POINTER(_vp)]),
     "hf_server_field_get": (_i, [_vp, _i, _i, _i, _vp, _vp]),
     "hf_server_stats_get": (_i, [_vp, _vp]),
+    "hf_server_log_open": (_i, [_vp, ctypes.c_char_p, _i]),
+    "hf_server_log_close": (_i, [_vp]),
     "hf_server_query_latencies": (_i, [_vp, _fp, _i]),
     "hf_server_set_chunk_bytes": (_i, [_vp, _sz]),
     "hf_server_request_chunks": (_i, [_vp, ctypes.c_int64, _ip, _ip]),

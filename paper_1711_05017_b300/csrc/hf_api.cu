@@ -126,6 +126,9 @@ struct hf_part {
     // HF_STATIONARY after hf_part_moments: the spectra of the moment fields
     // G_a = -(u x grad rho1)_a, 3 half spectra (slot order, scaled like spec)
     float2 *mspec = nullptr;
+    // the caller's handle, each server session over the part, each build in
+    // flight and each batch holding it; freed with the last
+    std::atomic<int> refs{1};
 };
 
 struct hf_fieldset {
@@ -274,6 +277,14 @@ static cudaError_t ensure_kernel_attrs() {
 extern "C" const char *hf_version(void) { return "hf 1.0 sm_103a"; }
 extern "C" const char *hf_last_error(void) { return g_err; }
 
+std::atomic<long long> hf::g_alloc_count{0}, hf::g_alloc_fail_at{0};
+
+extern "C" void hf_inject_alloc_failure(long long nth, long long *count) {
+    const long long c = hf::g_alloc_count.load();
+    hf::g_alloc_fail_at.store(nth > 0 ? c + nth : 0);
+    if (count) *count = c;
+}
+
 extern "C" hf_status hf_ctx_create(int device, size_t budget, hf_ctx **out) {
     if (!out) return fail(HF_EINVAL, "hf_ctx_create: out is NULL");
     *out = nullptr;
@@ -336,6 +347,7 @@ extern "C" size_t hf_ctx_reserved_bytes(const hf_ctx *c) {
 // ------------------------------------------------------------------ density
 extern "C" hf_status hf_density_build(hf_ctx *ctx, int n, const float *d_pts, const float *d_sigma,
                                       const float *d_amp, int P, float *d_grid_out, hf_stream stream) {
+    hf::Range range_("hf_density_build");
     if (!ctx) return fail(HF_EINVAL, "hf_density_build: ctx is NULL");
     if (!hf::supported_n(n)) return fail(HF_EUNSUPPORTED, "hf_density_build: N=%d not supported", n);
     if (P < 0 || !d_grid_out || (P > 0 && (!d_pts || !d_sigma)))
@@ -349,6 +361,7 @@ extern "C" hf_status hf_density_build(hf_ctx *ctx, int n, const float *d_pts, co
 extern "C" hf_status hf_density_mesh(hf_ctx *ctx, int n, const double *d_V, int nv, const int *d_T, int nt,
                                      double sigma, double gamma_max, int max_depth, float *d_grid_out,
                                      float *d_aux_out, hf_stream stream) {
+    hf::Range range_("hf_density_mesh");
     if (!ctx || !d_V || !d_T || !d_grid_out) return fail(HF_EINVAL, "hf_density_mesh: NULL argument");
     if (n < 2 || n > 512) return fail(HF_EUNSUPPORTED, "hf_density_mesh: N=%d outside 2..512", n);
     if (nv < 3 || nt < 1) return fail(HF_EINVAL, "hf_density_mesh: %d vertices, %d triangles", nv, nt);
@@ -371,15 +384,18 @@ static hf_status stationary_spectrum(hf_ctx *c, int n, const float *d_grid, floa
     // pass A with the identity: a plain copy of each plane into the transform
     const size_t he = hf::half_spec_elems(n);
     float2 *X1 = nullptr;
-    CU(cudaMallocAsync(&X1, 2 * he * sizeof(float2), st));
+    CU(hf::dmalloc_async(&X1, 2 * he * sizeof(float2), st));
+    cudaError_t e;
     if (hf::pencil_n(n)) {
-        CU(timed(c, kPassA, st, [&] { return hf::run_xfwd(n, d_grid, X1 + he, 1, st); }));
-        CU(timed(c, kPassA, st, [&] { return hf::run_yfwd(n, X1 + he, X1, 1, st); }));
+        e = timed(c, kPassA, st, [&] { return hf::run_xfwd(n, d_grid, X1 + he, 1, st); });
+        if (e == cudaSuccess) e = timed(c, kPassA, st, [&] { return hf::run_yfwd(n, X1 + he, X1, 1, st); });
     } else {
-        CU(timed(c, kPassA, st, [&] { return hf::run_passA_planes(n, d_grid, X1, 1, st); }));
+        e = timed(c, kPassA, st, [&] { return hf::run_passA_planes(n, d_grid, X1, 1, st); });
     }
-    CU(timed(c, kPassBFwd, st, [&] { return hf::run_passB_forward(n, X1, spec, scale, st); }));
-    CU(cudaFreeAsync(X1, st));
+    if (e == cudaSuccess) e = timed(c, kPassBFwd, st, [&] { return hf::run_passB_forward(n, X1, spec, scale, st); });
+    const cudaError_t f = cudaFreeAsync(X1, st);
+    if (e == cudaSuccess) e = f;
+    if (e != cudaSuccess) return fail(HF_ECUDA, "stationary spectrum: %s", cudaGetErrorString(e));
     return HF_OK;
 }
 
@@ -441,8 +457,8 @@ static hf_status moving_texture_alloc(hf_part *p) {
         return HF_OK;
     const size_t w = (size_t)tw, h = (size_t)th;
     cudaChannelFormatDesc fd = cudaCreateChannelDesc<float>();
-    CU(cudaMallocPitch(&p->slab, &p->slab_pitch, w * sizeof(float), h));
-    cudaError_t e = cudaMallocArray(&p->arr, &fd, w, h, cudaArrayTextureGather);
+    CU(hf::dmalloc_pitch(&p->slab, &p->slab_pitch, w * sizeof(float), h));
+    cudaError_t e = hf::dmalloc_array(&p->arr, &fd, w, h, cudaArrayTextureGather);
     if (e == cudaSuccess) {
         cudaResourceDesc rd = {};
         rd.resType = cudaResourceTypeArray;
@@ -457,7 +473,7 @@ static hf_status moving_texture_alloc(hf_part *p) {
     }
     const char *sup = getenv("HF_SUPPORT");
     if (e == cudaSuccess && !(sup && sup[0] == '0')) {
-        e = cudaMalloc(&p->supmask, (hf::kSupportMaskWords + 6) * sizeof(unsigned));
+        e = hf::dmalloc(&p->supmask, (hf::kSupportMaskWords + 6) * sizeof(unsigned));
         if (e == cudaSuccess) p->box = reinterpret_cast<int *>(p->supmask + hf::kSupportMaskWords);
     }
     if (e != cudaSuccess) {
@@ -470,6 +486,7 @@ static hf_status moving_texture_alloc(hf_part *p) {
 
 extern "C" hf_status hf_part_create(hf_ctx *ctx, int n, const float *d_grid, int role, hf_part **out,
                                     hf_stream stream) {
+    hf::Range range_("hf_part_create");
     if (!ctx || !out || !d_grid) return fail(HF_EINVAL, "hf_part_create: NULL argument");
     *out = nullptr;
     if (!hf::supported_n(n)) return fail(HF_EUNSUPPORTED, "hf_part_create: N=%d not supported", n);
@@ -492,7 +509,7 @@ extern "C" hf_status hf_part_create(hf_ctx *ctx, int n, const float *d_grid, int
         return fail(HF_ENOMEM, "hf_part_create: host allocation");
     }
     void *mem = nullptr;
-    cudaError_t e = cudaMalloc(&mem, role == HF_MOVING ? n3 * sizeof(float) : bytes);
+    cudaError_t e = hf::dmalloc(&mem, role == HF_MOVING ? n3 * sizeof(float) : bytes);
     if (e != cudaSuccess) {
         delete p;
         uncharge(ctx, bytes);
@@ -542,8 +559,8 @@ static hf_status spectral_table_fill(hf_part *p, const float *d_grid, cudaStream
     const size_t np3 = (size_t)np * np * np;
     float *pad = nullptr;
     float2 *half = nullptr;
-    CU(cudaMallocAsync(&pad, np3 * sizeof(float), st));
-    cudaError_t e = cudaMallocAsync(&half, hf::half_spec_elems(np) * sizeof(float2), st);
+    CU(hf::dmalloc_async(&pad, np3 * sizeof(float), st));
+    cudaError_t e = hf::dmalloc_async(&half, hf::half_spec_elems(np) * sizeof(float2), st);
     hf_status s = HF_OK;
     if (e == cudaSuccess) e = hf::run_pad_center(n, d_grid, pad, np, st);
     if (e == cudaSuccess) s = stationary_spectrum(p->ctx, np, pad, half, 1.0f, st);
@@ -554,7 +571,7 @@ static hf_status spectral_table_fill(hf_part *p, const float *d_grid, cudaStream
         int w = 0, h = 0;
         hf::table_tex_layout(np, &w, &h);
         float2 *slab = nullptr;
-        e = cudaMallocAsync(&slab, (size_t)w * h * sizeof(float2), st);
+        e = hf::dmalloc_async(&slab, (size_t)w * h * sizeof(float2), st);
         if (e == cudaSuccess) e = hf::run_pad_table(p->table, np, slab, st);
         if (e == cudaSuccess)
             e = cudaMemcpy2DToArrayAsync(p->tarr, 0, 0, slab, (size_t)w * sizeof(float2), (size_t)w * sizeof(float2),
@@ -567,6 +584,7 @@ static hf_status spectral_table_fill(hf_part *p, const float *d_grid, cudaStream
 }
 
 extern "C" hf_status hf_part_spectral(hf_part *p, int os, hf_stream stream) {
+    hf::Range range_("hf_part_spectral");
     if (!p) return fail(HF_EINVAL, "hf_part_spectral: NULL part");
     if (p->role != HF_MOVING) return fail(HF_EINVAL, "hf_part_spectral: the part must be HF_MOVING");
     if (os != 1 && os != 2) return fail(HF_EINVAL, "hf_part_spectral: os must be 1 or 2 (%d)", os);
@@ -589,11 +607,11 @@ extern "C" hf_status hf_part_spectral(hf_part *p, int os, hf_stream stream) {
     if (!p->table) {
         if (!charge(p->ctx, bytes)) return fail(HF_EBUDGET, "hf_part_spectral: %zu bytes exceed the budget", bytes);
         p->table_bytes = bytes;
-        cudaError_t e = cudaMalloc(&p->table, tbytes);
+        cudaError_t e = hf::dmalloc(&p->table, tbytes);
         if (e != cudaSuccess) p->table = nullptr;
         if (e == cudaSuccess) {
             cudaChannelFormatDesc fd = cudaCreateChannelDesc<float2>();
-            e = cudaMallocArray(&p->tarr, &fd, (size_t)tw, (size_t)th, cudaArrayTextureGather);
+            e = hf::dmalloc_array(&p->tarr, &fd, (size_t)tw, (size_t)th, cudaArrayTextureGather);
             if (e != cudaSuccess) p->tarr = nullptr;
         }
         if (e == cudaSuccess) {
@@ -616,7 +634,12 @@ extern "C" hf_status hf_part_spectral(hf_part *p, int os, hf_stream stream) {
         }
     }
     p->table_os = os;
-    return spectral_table_fill(p, p->grid, st);
+    const hf_status s = spectral_table_fill(p, p->grid, st);
+    if (s != HF_OK) {  // no half-filled table stays behind
+        cudaStreamSynchronize(st);
+        table_free(p);
+    }
+    return s;
 }
 
 extern "C" int hf_part_spectral_os(const hf_part *p) { return p && p->table ? p->table_os : 0; }
@@ -633,8 +656,8 @@ static hf_status moment_spectra_fill(hf_part *p, cudaStream_t st) {
     std::vector<float2> ones((size_t)n * (n / 2 + 1), make_float2(1.f, 0.f));  // the z = 0 plane
     float2 *sc = nullptr;  // delta spectrum, Y1, Y2
     float *fl = nullptr;   // E, Fx, Fy, Fz, then G (3 fields)
-    CU(cudaMallocAsync(&sc, 3 * he * sizeof(float2), st));
-    cudaError_t e = cudaMallocAsync(&fl, 7 * n3 * sizeof(float), st);
+    CU(hf::dmalloc_async(&sc, 3 * he * sizeof(float2), st));
+    cudaError_t e = hf::dmalloc_async(&fl, 7 * n3 * sizeof(float), st);
     hf_status s = HF_OK;
     if (e == cudaSuccess) e = cudaMemsetAsync(sc, 0, he * sizeof(float2), st);
     if (e == cudaSuccess)
@@ -656,6 +679,7 @@ static hf_status moment_spectra_fill(hf_part *p, cudaStream_t st) {
 }
 
 extern "C" hf_status hf_part_moments(hf_part *p, hf_stream stream) {
+    hf::Range range_("hf_part_moments");
     if (!p) return fail(HF_EINVAL, "hf_part_moments: NULL part");
     if (p->role != HF_STATIONARY) return fail(HF_EINVAL, "hf_part_moments: the part must be HF_STATIONARY");
     if (p->n > 128) return fail(HF_EUNSUPPORTED, "hf_part_moments: N=%d (the analytic torque runs at N <= 128)", p->n);
@@ -663,18 +687,31 @@ extern "C" hf_status hf_part_moments(hf_part *p, hf_stream stream) {
     if (!p->mspec) {
         const size_t bytes = 3 * hf::half_spec_elems(p->n) * sizeof(float2);
         if (!charge(p->ctx, bytes)) return fail(HF_EBUDGET, "hf_part_moments: %zu bytes exceed the budget", bytes);
-        const cudaError_t e = cudaMalloc(&p->mspec, bytes);
+        const cudaError_t e = hf::dmalloc(&p->mspec, bytes);
         if (e != cudaSuccess) {
             p->mspec = nullptr;
             uncharge(p->ctx, bytes);
             return fail(HF_ENOMEM, "hf_part_moments: cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
         }
     }
-    return moment_spectra_fill(p, (cudaStream_t)stream);
+    const hf_status s = moment_spectra_fill(p, (cudaStream_t)stream);
+    if (s != HF_OK) {  // no half-filled moment spectra stay behind
+        cudaStreamSynchronize((cudaStream_t)stream);
+        cudaFree(p->mspec);
+        p->mspec = nullptr;
+        uncharge(p->ctx, 3 * hf::half_spec_elems(p->n) * sizeof(float2));
+    }
+    return s;
 }
 
+void hf_part_retain(const hf_part *p) {
+    if (p) const_cast<hf_part *>(p)->refs.fetch_add(1);
+}
+
+void hf_part_drop(const hf_part *p) { hf_part_release(const_cast<hf_part *>(p)); }
+
 extern "C" void hf_part_release(hf_part *p) {
-    if (!p) return;
+    if (!p || p->refs.fetch_sub(1) != 1) return;
     cudaSetDevice(p->ctx->device);
     table_free(p);
     if (p->mspec) {
@@ -994,7 +1031,7 @@ static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags,
     }
     fs->mem_stream = mem_stream;
     auto dalloc = [&](void **p, size_t b) {
-        return mem_stream ? cudaMallocAsync(p, b, mem_stream) : cudaMalloc(p, b);
+        return mem_stream ? hf::dmalloc_async(p, b, mem_stream) : hf::dmalloc(p, b);
     };
     cudaError_t e = dalloc((void **)&fs->data, data_b);
     for (int l = 0; l < 2; ++l) {
@@ -1014,7 +1051,7 @@ static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags,
             fs->pageable_stage.resize(fs->stage_bytes + 64);
             fs->h_stage = fs->pageable_stage.data();
         } else {
-            e = cudaMallocHost(&fs->h_stage, fs->stage_bytes);
+            e = hf::hmalloc(&fs->h_stage, fs->stage_bytes);
         }
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fs->stage_done, cudaEventDisableTiming);
@@ -1246,6 +1283,7 @@ hf_status hf_set_launch(hf_ctx *ctx, const hf_part *s1, const hf_part *s2, hf_fi
 
 extern "C" hf_status hf_fieldset_compute(hf_ctx *ctx, const hf_part *s1, const hf_part *s2, const float *h_quat,
                                          int R, hf_fieldset *fs, hf_stream stream) {
+    hf::Range range_("hf_fieldset_compute");
     if (!ctx || !fs || !h_quat) return fail(HF_EINVAL, "hf_fieldset_compute: NULL argument");
     if (R != fs->R) return fail(HF_EINVAL, "hf_fieldset_compute: R=%d but the set holds %d", R, fs->R);
     hf_status s = check_pair(s1, s2, fs->n, "hf_fieldset_compute");
@@ -1356,6 +1394,7 @@ static hf::QueryGeom query_geom(const hf_fieldset *fs) {
 
 extern "C" hf_status hf_query_batch(const hf_fieldset *fs, const float *d_tq, int Q, int k, float *d_out,
                                     hf_stream stream) {
+    hf::Range range_("hf_query_batch");
     if (!fs) return fail(HF_EINVAL, "hf_query_batch: NULL field set");
     if (Q < 0 || (Q > 0 && (!d_tq || !d_out))) return fail(HF_EINVAL, "hf_query_batch: bad buffers");
     if (k < 1 || k > 8 || k > fs->R) return fail(HF_EINVAL, "hf_query_batch: k_blend=%d", k);
@@ -1419,10 +1458,22 @@ extern "C" hf_status hf_lowpass_query(const hf_part *s1, const hf_part *s2, int 
     hf_ctx *c = s1->ctx;
     std::lock_guard<std::mutex> g(c->qmu);
     CU(cudaSetDevice(c->device));
-    if (!c->lp_part) {
-        CU(cudaMalloc(&c->lp_part, sizeof(double) * 7 * hf::kLowpassMaxSplit));
-        CU(cudaMalloc(&c->lp_count, sizeof(unsigned)));
-        CU(cudaMemset(c->lp_count, 0, sizeof(unsigned)));
+    if (!c->lp_part || !c->lp_count) {  // both or neither
+        double *part = nullptr;
+        unsigned *count = nullptr;
+        cudaError_t e = hf::dmalloc(&part, sizeof(double) * 7 * hf::kLowpassMaxSplit);
+        if (e == cudaSuccess) e = hf::dmalloc(&count, sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMemset(count, 0, sizeof(unsigned));
+        if (e != cudaSuccess) {
+            if (part) cudaFree(part);
+            if (count) cudaFree(count);
+            return fail(e == cudaErrorMemoryAllocation ? HF_ENOMEM : HF_ECUDA, "hf_lowpass_query: scratch: %s",
+                        cudaGetErrorString(e));
+        }
+        if (c->lp_part) cudaFree(c->lp_part);
+        if (c->lp_count) cudaFree(c->lp_count);
+        c->lp_part = part;
+        c->lp_count = count;
     }
     (void)cudaGetLastError();
     CU(hf::run_lowpass(s1->n, s1->spec, s2->table, s2->table_os, K, nullptr, 1, &pose, c->lp_part, c->lp_count,
@@ -1444,8 +1495,8 @@ extern "C" hf_status hf_lowpass_query_batch(const hf_part *s1, const hf_part *s2
     const size_t pb = sizeof(double) * 7 * (size_t)hf::lowpass_split(K) * Q;
     double *part = nullptr;
     unsigned *count = nullptr;
-    CU(cudaMallocAsync(&part, pb, st));
-    cudaError_t e = cudaMallocAsync(&count, sizeof(unsigned) * (size_t)Q, st);
+    CU(hf::dmalloc_async(&part, pb, st));
+    cudaError_t e = hf::dmalloc_async(&count, sizeof(unsigned) * (size_t)Q, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(count, 0, sizeof(unsigned) * (size_t)Q, st);
     if (e == cudaSuccess) {
         (void)cudaGetLastError();
@@ -1501,6 +1552,7 @@ extern "C" size_t hf_fields_scratch_bytes(int n) {
 
 extern "C" hf_status hf_fields(hf_ctx *ctx, const hf_part *s1, const hf_part *s2, const float h_quat[4], float *d_E,
                                float *d_Fx, float *d_Fy, float *d_Fz, void *d_scratch, hf_stream stream) {
+    hf::Range range_("hf_fields");
     if (!ctx || !h_quat || !d_E || !d_scratch) return fail(HF_EINVAL, "hf_fields: NULL argument");
     if ((uintptr_t)d_scratch % 16) return fail(HF_EINVAL, "hf_fields: scratch must be 16-byte aligned");
     hf_status s = check_pair(s1, s2, s1 ? s1->n : 0, "hf_fields");
@@ -1529,6 +1581,7 @@ extern "C" hf_status hf_fields(hf_ctx *ctx, const hf_part *s1, const hf_part *s2
 
 extern "C" hf_status hf_torque(hf_ctx *ctx, int n, int R, const float *h_quat, const float *d_E, float *d_T,
                                unsigned flags, int *h_status, hf_stream stream) {
+    hf::Range range_("hf_torque");
     if (!ctx || !h_quat || !d_E || !d_T) return fail(HF_EINVAL, "hf_torque: NULL argument");
     if (!hf::supported_n(n)) return fail(HF_EUNSUPPORTED, "hf_torque: N=%d not supported", n);
     if (R < 7) return fail(HF_EINVAL, "hf_torque: R=%d < 7", R);
@@ -1546,20 +1599,26 @@ extern "C" hf_status hf_torque(hf_ctx *ctx, int n, int R, const float *h_quat, c
     int *d_nbr = nullptr;
     float *d_P = nullptr;
     double *d_P64 = nullptr;
-    CU(cudaMallocAsync(&d_nbr, nbr.size() * sizeof(int), st));
-    CU(cudaMallocAsync(&d_P, P32.size() * sizeof(float), st));
-    CU(cudaMallocAsync(&d_P64, P64.size() * sizeof(double), st));
-    CU(cudaMemcpyAsync(d_nbr, nbr.data(), nbr.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-    CU(cudaMemcpyAsync(d_P, P32.data(), P32.size() * sizeof(float), cudaMemcpyHostToDevice, st));
-    CU(cudaMemcpyAsync(d_P64, P64.data(), P64.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    cudaError_t e = hf::dmalloc_async(&d_nbr, nbr.size() * sizeof(int), st);
+    if (e == cudaSuccess) e = hf::dmalloc_async(&d_P, P32.size() * sizeof(float), st);
+    if (e == cudaSuccess) e = hf::dmalloc_async(&d_P64, P64.size() * sizeof(double), st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_nbr, nbr.data(), nbr.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_P, P32.data(), P32.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_P64, P64.data(), P64.size() * sizeof(double), cudaMemcpyHostToDevice, st);
     const size_t n3 = (size_t)n * n * n;
-    CU(timed(ctx, kTorque, st, [&] {
-        return hf::run_torque(n, R, d_E, n3, d_T, 3 * n3, d_nbr, d_P, d_P64, (flags & HF_TORQUE_F64) != 0, st);
-    }));
-    CU(cudaFreeAsync(d_nbr, st));
-    CU(cudaFreeAsync(d_P, st));
-    CU(cudaFreeAsync(d_P64, st));
-    CU(cudaStreamSynchronize(st));  // the host vectors are freed on return
+    if (e == cudaSuccess)
+        e = timed(ctx, kTorque, st, [&] {
+            return hf::run_torque(n, R, d_E, n3, d_T, 3 * n3, d_nbr, d_P, d_P64, (flags & HF_TORQUE_F64) != 0, st);
+        });
+    if (d_nbr) cudaFreeAsync(d_nbr, st);
+    if (d_P) cudaFreeAsync(d_P, st);
+    if (d_P64) cudaFreeAsync(d_P64, st);
+    const cudaError_t y = cudaStreamSynchronize(st);  // the host vectors are freed on return
+    if (e == cudaSuccess) e = y;
+    if (e != cudaSuccess)
+        return fail(e == cudaErrorMemoryAllocation ? HF_ENOMEM : HF_ECUDA, "hf_torque: %s", cudaGetErrorString(e));
     if (bad) return fail(HF_EINVAL, "hf_torque: %d rotation(s) with a rank-deficient neighbourhood", bad);
     return HF_OK;
 }
@@ -1766,6 +1825,7 @@ std::vector<float> tune_grid(int n, int seed) {
 
 extern "C" hf_status hf_autotune(hf_ctx *ctx, int n, const char *cache_path, int *chunk_out, int *pencil_out,
                                  double *rot_per_s_out) {
+    hf::Range range_("hf_autotune");
     if (!ctx) return fail(HF_EINVAL, "hf_autotune: ctx is NULL");
     if (!hf::supported_n(n)) return fail(HF_EUNSUPPORTED, "hf_autotune: N=%d not supported", n);
     CU(cudaSetDevice(ctx->device));
@@ -1779,7 +1839,7 @@ extern "C" hf_status hf_autotune(hf_ctx *ctx, int n, const char *cache_path, int
         const int chunks[] = {4, 8, 12, 16, 24, 32, 48, 64, 96, 128, 256};
         const size_t n3 = (size_t)n * n * n;
         float *d_g = nullptr;
-        CU(cudaMalloc(&d_g, 2 * n3 * sizeof(float)));
+        CU(hf::dmalloc(&d_g, 2 * n3 * sizeof(float)));
         std::vector<float> h1 = tune_grid(n, 1), h2 = tune_grid(n, 5);
         hf_part *s1 = nullptr, *s2 = nullptr;
         cudaError_t ce = cudaMemcpy(d_g, h1.data(), n3 * sizeof(float), cudaMemcpyHostToDevice);
@@ -2108,7 +2168,7 @@ extern "C" hf_status hf_part_load(hf_ctx *ctx, const char *path, hf_part **out, 
             return fail(HF_EINVAL, "hf_part_load: %s: grid array of the wrong type or shape", path);
         const size_t b = (size_t)n * n * n * sizeof(float);
         float *tmp = nullptr;
-        CU(cudaMallocAsync(&tmp, b, st));
+        CU(hf::dmalloc_async(&tmp, b, st));
         hf_status s = read_device(f, tmp, b, st);
         if (s == HF_OK) s = hf_part_create(ctx, n, tmp, HF_MOVING, out, stream);
         cudaFreeAsync(tmp, st);
@@ -2119,7 +2179,7 @@ extern "C" hf_status hf_part_load(hf_ctx *ctx, const char *path, hf_part **out, 
     const size_t bytes = hf::half_spec_elems(n) * sizeof(float2);
     if (!charge(ctx, bytes)) return fail(HF_EBUDGET, "hf_part_load: %zu bytes exceed the budget", bytes);
     hf_part *p = new (std::nothrow) hf_part{ctx, n, HF_STATIONARY, nullptr, nullptr, bytes};
-    cudaError_t e = p ? cudaMalloc(&p->spec, bytes) : cudaErrorMemoryAllocation;
+    cudaError_t e = p ? hf::dmalloc(&p->spec, bytes) : cudaErrorMemoryAllocation;
     hf_status s = e == cudaSuccess ? read_device(f, p->spec, bytes, st)
                                    : fail(HF_ENOMEM, "hf_part_load: %s", cudaGetErrorString(e));
     if (s != HF_OK) {

@@ -76,6 +76,8 @@ extern "C" void hf_batch_release(hf_batch *b) {
     for (auto e : b->join) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->cap) cudaStreamDestroy(b->cap);
+    for (auto p : b->s1) hf_part_drop(p);
+    for (auto p : b->s2) hf_part_drop(p);
     hf_ctx *c = b->ctx;
     delete b;
     hf_ctx_release(c);
@@ -92,6 +94,10 @@ extern "C" hf_status hf_batch_create(hf_ctx *ctx, int npairs, const hf_part *con
     b->flags = flags | HF_E | HF_F;
     b->s1.assign(s1, s1 + npairs);
     b->s2.assign(s2, s2 + npairs);
+    for (int i = 0; i < npairs; ++i) {
+        hf_part_retain(s1[i]);
+        hf_part_retain(s2[i]);
+    }
     b->R.assign(R, R + npairs);
     b->n.resize(npairs);
     b->slot_of.resize(npairs);
@@ -134,11 +140,11 @@ extern "C" hf_status hf_batch_create(hf_ctx *ctx, int npairs, const hf_part *con
     b->d_nbr.assign(npairs, nullptr);
     b->have_rot.assign(npairs, 0);
     for (int i = 0; i < npairs && st == HF_OK && e == cudaSuccess; ++i) {
-        e = cudaMalloc(&b->d_rot9[i], (size_t)R[i] * 9 * sizeof(float));
+        e = hf::dmalloc(&b->d_rot9[i], (size_t)R[i] * 9 * sizeof(float));
         if (e == cudaSuccess && (flags & HF_T)) {
-            e = cudaMalloc(&b->d_nbr[i], (size_t)R[i] * 6 * sizeof(int));
-            if (e == cudaSuccess) e = cudaMalloc(&b->d_P[i], (size_t)R[i] * 18 * sizeof(float));
-            if (e == cudaSuccess) e = cudaMalloc(&b->d_P64[i], (size_t)R[i] * 18 * sizeof(double));
+            e = hf::dmalloc(&b->d_nbr[i], (size_t)R[i] * 6 * sizeof(int));
+            if (e == cudaSuccess) e = hf::dmalloc(&b->d_P[i], (size_t)R[i] * 18 * sizeof(float));
+            if (e == cudaSuccess) e = hf::dmalloc(&b->d_P64[i], (size_t)R[i] * 18 * sizeof(double));
         }
     }
     if (st == HF_OK && e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
@@ -187,6 +193,7 @@ extern "C" hf_status hf_batch_set_rotations(hf_batch *b, int pair, const float *
 }
 
 extern "C" hf_status hf_batch_capture(hf_batch *b, int lanes) {
+    hf::Range range_("hf_batch_capture");
     if (!b) return bfail(HF_EINVAL, "hf_batch_capture: NULL batch");
     for (int i = 0; i < b->npairs; ++i)
         if (!b->have_rot[i]) return bfail(HF_ENOTREADY, "hf_batch_capture: a pair has no rotations");
@@ -240,6 +247,7 @@ constexpr long long kDefaultSpin = 1LL << 21;  // polls of at least 256 ns each:
 }  // namespace
 
 extern "C" hf_status hf_batch_capture_queue(hf_batch *b, int chunk, long long spin_limit, int self_test) {
+    hf::Range range_("hf_batch_capture_queue");
     if (!b) return bfail(HF_EINVAL, "hf_batch_capture_queue: NULL batch");
     if (b->flags & ~(unsigned)(HF_E | HF_F))
         return bfail(HF_EUNSUPPORTED, "hf_batch_capture_queue: the one-launch build holds E and F only");
@@ -256,6 +264,10 @@ extern "C" hf_status hf_batch_capture_queue(hf_batch *b, int chunk, long long sp
     if (cudaSetDevice(hf_ctx_device(b->ctx)) != cudaSuccess) return bfail(HF_ECUDA, "hf_batch_capture_queue: device");
     cudaError_t e = hf::persist_init();
     if (e != cudaSuccess) return bfail(HF_ECUDA, "hf_batch_capture_queue: kernel set-up failed");
+    // the previous graph reads the tables and intermediates freed below: it
+    // goes first, so that a failure from here on leaves nothing to launch
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
     // the pair-chunks, in pair order
     struct PC {
         int pair, n, r0, cnt, slot, cA, cB, cC;
@@ -283,7 +295,7 @@ extern "C" hf_status hf_batch_capture_queue(hf_batch *b, int chunk, long long sp
         const int n = kv.first;
         const size_t he = (size_t)n * n * (n / 2 + 1);
         float2 *p = nullptr;
-        e = cudaMalloc(&p, (size_t)kSlots * 3 * chunk * he * sizeof(float2));
+        e = hf::dmalloc(&p, (size_t)kSlots * 3 * chunk * he * sizeof(float2));
         if (e != cudaSuccess) return bfail(HF_ENOMEM, "hf_batch_capture_queue: intermediates");
         b->scratch.push_back(p);
         base[n] = p;
@@ -400,15 +412,15 @@ extern "C" hf_status hf_batch_capture_queue(hf_batch *b, int chunk, long long sp
     if (b->d_segs) cudaFree(b->d_segs);
     if (b->d_lut) cudaFree(b->d_lut);
     if (b->d_queue) cudaFree(b->d_queue);
-    b->d_lut = nullptr;
-    if (!b->d_status && cudaMalloc(&b->d_status, sizeof(int)) != cudaSuccess)
-        return bfail(HF_ENOMEM, "hf_batch_capture_queue: status word");
     b->d_segs = nullptr;
+    b->d_lut = nullptr;
     b->d_queue = nullptr;
+    if (!b->d_status && hf::dmalloc(&b->d_status, sizeof(int)) != cudaSuccess)
+        return bfail(HF_ENOMEM, "hf_batch_capture_queue: status word");
     const size_t ncount = 1 + 3 * pcs.size();
-    if (cudaMalloc(&b->d_segs, segs.size() * sizeof(hf::PersistSeg)) != cudaSuccess ||
-        cudaMalloc(&b->d_lut, lut.size() * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&b->d_queue, ncount * sizeof(unsigned)) != cudaSuccess)
+    if (hf::dmalloc(&b->d_segs, segs.size() * sizeof(hf::PersistSeg)) != cudaSuccess ||
+        hf::dmalloc(&b->d_lut, lut.size() * sizeof(int)) != cudaSuccess ||
+        hf::dmalloc(&b->d_queue, ncount * sizeof(unsigned)) != cudaSuccess)
         return bfail(HF_ENOMEM, "hf_batch_capture_queue: work tables");
     if (cudaMemcpy(b->d_segs, segs.data(), segs.size() * sizeof(hf::PersistSeg), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->d_lut, lut.data(), lut.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -453,6 +465,7 @@ extern "C" hf_status hf_batch_status(hf_batch *b, hf_stream stream, int *items, 
 }
 
 extern "C" hf_status hf_batch_launch(hf_batch *b, hf_stream stream) {
+    hf::Range range_("hf_batch_launch");
     if (!b || !b->exec) return bfail(HF_ENOTREADY, "hf_batch_launch: capture first");
     if (cudaGraphLaunch(b->exec, (cudaStream_t)stream) != cudaSuccess) return bfail(HF_ECUDA, "hf_batch_launch: launch failed");
     for (size_t s = 0; s < b->slots.size(); ++s) {

@@ -5,6 +5,10 @@
 #include <stdio.h>
 #include <stdint.h>
 
+#include <atomic>
+
+#include <nvtx3/nvToolsExt.h>
+
 #include <vector>
 
 #include "hf.h"
@@ -191,6 +195,50 @@ struct Pose7 {
 // one query, pose by value, 7 results to `out` (device or mapped host memory)
 cudaError_t run_query_one(const QueryGeom &g, Pose7 pose, int k, float *out, cudaStream_t st);
 
+// An NVTX range over a library call (a profiler with NVTX support shows the
+// call's kernels under its name; without one the push and pop do nothing).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
+
+// Allocation-failure injection for the error paths' tests (hf_inject_alloc_failure):
+// every device, array and pinned-host allocation the library makes goes
+// through these, which count it and, for the one the test picked, return the
+// allocator's out-of-memory error without allocating.
+extern std::atomic<long long> g_alloc_count, g_alloc_fail_at;
+inline bool alloc_fails() {
+    const long long k = g_alloc_count.fetch_add(1, std::memory_order_relaxed) + 1;
+    return k == g_alloc_fail_at.load(std::memory_order_relaxed);
+}
+template <class T>
+inline cudaError_t dmalloc(T **p, size_t b) {
+    if (alloc_fails()) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, b);
+}
+template <class T>
+inline cudaError_t dmalloc_async(T **p, size_t b, cudaStream_t st) {
+    if (alloc_fails()) return cudaErrorMemoryAllocation;
+    return cudaMallocAsync((void **)p, b, st);
+}
+template <class T>
+inline cudaError_t dmalloc_pitch(T **p, size_t *pitch, size_t w, size_t h) {
+    if (alloc_fails()) return cudaErrorMemoryAllocation;
+    return cudaMallocPitch(p, pitch, w, h);
+}
+inline cudaError_t dmalloc_array(cudaArray_t *a, const cudaChannelFormatDesc *fd, size_t w, size_t h,
+                                 unsigned flags) {
+    if (alloc_fails()) return cudaErrorMemoryAllocation;
+    return cudaMallocArray(a, fd, w, h, flags);
+}
+template <class T>
+inline cudaError_t hmalloc(T **p, size_t b) {
+    if (alloc_fails()) return cudaErrorMemoryAllocation;
+    return cudaMallocHost((void **)p, b);
+}
+
 }  // namespace hf
 
 // hf_api.cu: one pose query on a caller-provided lane (a stream and a mapped
@@ -200,6 +248,11 @@ int hf_ctx_device(const hf_ctx *c);
 // a reference to the context, held by every object made from it
 void hf_ctx_retain(hf_ctx *c);
 void hf_ctx_release(hf_ctx *c);
+// a reference to a part, held by server sessions, their builds in flight and
+// batches; the part is freed when the last reference (hf_part_release or
+// hf_part_drop) goes
+void hf_part_retain(const hf_part *p);
+void hf_part_drop(const hf_part *p);
 // whether the set's last compute enqueued all of its work
 bool hf_fieldset_is_ready(const hf_fieldset *fs);
 void hf_fieldset_mark_ready(hf_fieldset *fs);

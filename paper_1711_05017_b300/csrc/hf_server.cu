@@ -120,6 +120,7 @@ struct Job {  // one chunk of a request
     hf_fieldset *fs = nullptr;
     cudaEvent_t done = nullptr;
     int stream = -1;
+    const hf_part *p1 = nullptr, *p2 = nullptr;  // held from launch to completion
 };
 
 // A session's published field data: one set per chunk of one request.  The
@@ -139,7 +140,7 @@ struct Published {
 
 struct Session {
     std::atomic<bool> open{false};
-    const hf_part *s1 = nullptr, *s2 = nullptr;  // fixed once the session is visible
+    const hf_part *s1 = nullptr, *s2 = nullptr;  // held while open; fixed once the session is visible
     int n = 0;
     std::shared_ptr<Published> current_;         // atomic access only
     std::atomic<int64_t> answered{0}, not_ready{0};
@@ -164,6 +165,49 @@ struct TraceRing {
         head = (head + 1) % kRows;
         count = std::min(count + 1, kRows);
     }
+};
+
+// Lock-free latency histogram on a log scale (8 bins per octave from 1 us,
+// to about 71 minutes), for the metrics log's per-period percentiles; a
+// percentile is reported as its bin's upper edge (within 9%).
+struct LogHist {
+    static constexpr int kPerOctave = 8, kBins = 8 * 32;
+    std::atomic<uint32_t> bin[kBins];
+    std::atomic<uint64_t> max_bits{0};  // largest sample since the last take_max (bits of a positive double)
+    LogHist() {
+        for (auto &b : bin) b.store(0, std::memory_order_relaxed);
+    }
+    static int index(double us) {
+        if (!(us > 1.0)) return 0;
+        return std::min((int)ceil(log2(us) * kPerOctave), kBins - 1);
+    }
+    static double upper(int i) { return exp2((double)i / kPerOctave); }
+    void add(double us) {
+        bin[index(us)].fetch_add(1, std::memory_order_relaxed);
+        uint64_t bits;
+        memcpy(&bits, &us, 8);
+        uint64_t cur = max_bits.load(std::memory_order_relaxed);
+        while (bits > cur && !max_bits.compare_exchange_weak(cur, bits, std::memory_order_relaxed)) {
+        }
+    }
+    double take_max() {
+        const uint64_t bits = max_bits.exchange(0, std::memory_order_relaxed);
+        double v;
+        memcpy(&v, &bits, 8);
+        return v;
+    }
+};
+
+// the JSON-lines metrics log: one line per period from its own thread
+struct MetricsLog {
+    FILE *f = nullptr;
+    int period_ms = 1000;
+    std::thread th;
+    std::mutex mu;
+    std::condition_variable cv;
+    bool stop = false;
+    uint32_t prev_q[LogHist::kBins] = {}, prev_b[LogHist::kBins] = {};
+    double t_last = 0;
 };
 
 constexpr size_t kLatRing = 1u << 20;
@@ -197,6 +241,9 @@ struct hf_server {
     std::mutex lat_mu;
     std::vector<float> lat_us;  // ring of query latencies
     size_t lat_head = 0, lat_count = 0;
+    LogHist query_hist, build_hist;  // answered queries (us), finished requests submit -> published (us)
+    std::mutex log_mu;               // the metrics log's open and close
+    std::unique_ptr<MetricsLog> log;
     std::mutex lane_mu;
     std::vector<Lane> lanes;
     std::vector<int> free_lanes;
@@ -305,6 +352,7 @@ static void finish_job(hf_server *s, const std::shared_ptr<Job> &j, bool ok) {
         r.state = RQ_DONE;
         r.t_done = now_ms();
         s->stats.completed++;
+        s->build_hist.add((r.t_done - r.t_submit) * 1000.0);
     }
 }
 
@@ -324,6 +372,9 @@ static void scheduler(hf_server *s) {
             finished.push_back({j, q == cudaSuccess});
             cudaEventDestroy(j->done);
             j->done = nullptr;
+            hf_part_drop(j->p1);
+            hf_part_drop(j->p2);
+            j->p1 = j->p2 = nullptr;
             s->stream_busy[j->stream] = 0;
             s->running.erase(s->running.begin() + i);
         }
@@ -357,6 +408,8 @@ static void scheduler(hf_server *s) {
                 cand = j;
                 p1 = ss.s1;
                 p2 = ss.s2;
+                hf_part_retain(p1);  // a session closed from here on leaves the build its parts
+                hf_part_retain(p2);
                 n = ss.n;
                 s->stream_busy[si] = 1;  // reserved while this thread prepares the build
                 break;
@@ -379,6 +432,8 @@ static void scheduler(hf_server *s) {
         hf_status st = hf_fieldset_create_stream_ordered(s->ctx, n, cand->R, cand->req->flags, s->streams[si], &fs);
         trace_call(s, 0, a, now_ms());
         if (st == HF_EBUDGET) {
+            hf_part_drop(p1);
+            hf_part_drop(p2);
             std::unique_lock<std::mutex> lk(s->mu);
             s->stream_busy[si] = 0;
             if (s->running.empty()) {
@@ -415,12 +470,17 @@ static void scheduler(hf_server *s) {
             cand->fs = fs;
             cand->done = ev;
             cand->stream = si;
+            cand->p1 = p1;
+            cand->p2 = p2;
             s->running.push_back(cand);
             std::lock_guard<std::mutex> g(s->mu);
             if (cand->req->state == RQ_QUEUED) cand->req->state = RQ_RUNNING;
         } else {
             if (fs) s->graveyard.put(fs);
             if (ev) cudaEventDestroy(ev);
+            cudaStreamSynchronize(s->streams[si]);  // a partial enqueue may still read the parts
+            hf_part_drop(p1);
+            hf_part_drop(p2);
             std::lock_guard<std::mutex> g(s->mu);
             s->stream_busy[si] = 0;
             cand->req->error = err;
@@ -433,6 +493,9 @@ static void scheduler(hf_server *s) {
         cudaEventDestroy(j->done);
         s->graveyard.put(j->fs);
         j->fs = nullptr;
+        hf_part_drop(j->p1);
+        hf_part_drop(j->p2);
+        j->p1 = j->p2 = nullptr;
         std::lock_guard<std::mutex> g(s->mu);
         if (j->req->state != RQ_DONE) j->req->state = RQ_FAILED;
     }
@@ -504,8 +567,16 @@ extern "C" hf_status hf_server_create(hf_ctx *ctx, int max_inflight, int query_l
     return HF_OK;
 }
 
+namespace {
+void log_stop(hf_server *s);
+}
+
 extern "C" void hf_server_destroy(hf_server *s) {
     if (!s) return;
+    {
+        std::lock_guard<std::mutex> g(s->log_mu);
+        log_stop(s);
+    }
     {
         std::lock_guard<std::mutex> g(s->mu);
         s->stop = true;
@@ -515,6 +586,12 @@ extern "C" void hf_server_destroy(hf_server *s) {
     for (int i = 0; i < s->nsessions.load(); ++i) s->sessions[i].set_current(nullptr);
     cudaDeviceSynchronize();
     free_retired(s);
+    for (int i = 0; i < s->nsessions.load(); ++i) {
+        Session &ss = s->sessions[i];
+        if (!ss.open.exchange(false)) continue;
+        hf_part_drop(ss.s1);
+        hf_part_drop(ss.s2);
+    }
     for (auto st : s->streams)
         if (st) cudaStreamDestroy(st);
     for (auto &L : s->lanes) {
@@ -547,6 +624,8 @@ extern "C" hf_status hf_server_session_open(hf_server *s, const hf_part *s1, con
     const int i = s->nsessions.load();
     if (i >= kMaxSessions) return srv_fail(HF_EINVAL, "hf_server_session_open: more than %d sessions", kMaxSessions);
     Session &ss = s->sessions[i];
+    hf_part_retain(s1);
+    hf_part_retain(s2);
     ss.s1 = s1;
     ss.s2 = s2;
     ss.n = n;
@@ -559,12 +638,31 @@ extern "C" hf_status hf_server_session_open(hf_server *s, const hf_part *s1, con
 
 extern "C" hf_status hf_server_session_close(hf_server *s, int session) {
     if (!s) return srv_fail(HF_EINVAL, "hf_server_session_close: NULL server");
-    std::lock_guard<std::mutex> g(s->mu);
-    Session *ss = session_at(s, session);
-    if (!ss) return srv_fail(HF_EINVAL, "hf_server_session_close: session %d", session);
-    ss->open.store(false);
-    ss->set_current(nullptr);
-    s->stats.sessions--;
+    const hf_part *p1, *p2;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        Session *ss = session_at(s, session);
+        if (!ss) return srv_fail(HF_EINVAL, "hf_server_session_close: session %d", session);
+        ss->open.store(false);
+        ss->set_current(nullptr);
+        s->stats.sessions--;
+        // its unfinished requests fail; queued chunks are dropped, running
+        // ones complete and are discarded
+        for (auto &j : s->queue)
+            if (j->req->session == session) j->superseded = true;
+        for (auto &kv : s->requests) {
+            Request &r = *kv.second;
+            if (r.session != session || (r.state != RQ_QUEUED && r.state != RQ_RUNNING)) continue;
+            r.state = RQ_FAILED;
+            r.error = "session closed";
+            s->stats.failed++;
+        }
+        p1 = ss->s1;
+        p2 = ss->s2;
+    }
+    // the session's references; a build of it in flight holds its own
+    hf_part_drop(p1);
+    hf_part_drop(p2);
     return HF_OK;
 }
 
@@ -778,6 +876,7 @@ extern "C" hf_status hf_server_query(hf_server *s, int session, const float t[3]
     if (st == HF_OK) {
         if (ss) ss->answered++;
         const double us = (t3 - t0) * 1000.0;
+        s->query_hist.add(us);
         {
             std::lock_guard<std::mutex> g(s->lat_mu);
             s->lat_us[s->lat_head] = (float)us;
@@ -868,6 +967,150 @@ extern "C" hf_status hf_server_stats_get(hf_server *s, hf_server_stats *out) {
             for (int c = 0; c < cur->req->nchunks; ++c) resident += cur->get(c) ? 1 : 0;
     }
     out->chunks_resident = resident;
+    return HF_OK;
+}
+
+// --------------------------------------------------------- metrics log
+namespace {
+
+// the period's sample count and quantiles (bin upper edges) from the bins'
+// growth since `prev`, which is advanced
+void hist_period(const LogHist &h, uint32_t *prev, uint64_t *n, const double *qs, double *out, int nq) {
+    uint32_t d[LogHist::kBins];
+    uint64_t tot = 0;
+    for (int i = 0; i < LogHist::kBins; ++i) {
+        const uint32_t c = h.bin[i].load(std::memory_order_relaxed);
+        d[i] = c - prev[i];
+        prev[i] = c;
+        tot += d[i];
+    }
+    *n = tot;
+    for (int k = 0; k < nq; ++k) {
+        const uint64_t want = std::max<uint64_t>(1, (uint64_t)ceil(qs[k] * (double)tot));
+        uint64_t cum = 0;
+        out[k] = 0;
+        for (int i = 0; i < LogHist::kBins && tot; ++i) {
+            cum += d[i];
+            if (cum >= want) {
+                out[k] = LogHist::upper(i);
+                break;
+            }
+        }
+    }
+}
+
+void log_num(FILE *f, const char *key, double v, bool present) {
+    if (present) fprintf(f, "\"%s\": %.6g", key, v);
+    else fprintf(f, "\"%s\": null", key);
+}
+
+void log_line(hf_server *s, MetricsLog &L) {
+    hf_server_stats st;
+    if (hf_server_stats_get(s, &st) != HF_OK) return;
+    const double t = now_ms();
+    FILE *f = L.f;
+    fprintf(f, "{\"t_s\": %.6f, \"period_s\": %.6f", (t - s->t0) * 1e-3, (t - L.t_last) * 1e-3);
+    L.t_last = t;
+    fprintf(f,
+            ", \"submitted\": %lld, \"completed\": %lld, \"failed\": %lld, \"rejected\": %lld, "
+            "\"superseded\": %lld, \"evicted\": %lld, \"queries\": %lld, \"rotations_completed\": %lld, "
+            "\"queued\": %d, \"running\": %d, \"sessions\": %d, \"reserved_bytes\": %zu, \"budget_bytes\": %zu, "
+            "\"chunks_submitted\": %lld, \"chunks_completed\": %lld, \"chunks_resident\": %d",
+            (long long)st.submitted, (long long)st.completed, (long long)st.failed, (long long)st.rejected,
+            (long long)st.superseded, (long long)st.evicted, (long long)st.queries, (long long)st.rotations_completed,
+            st.queued, st.running, st.sessions, st.reserved_bytes, st.budget_bytes, (long long)st.chunks_submitted,
+            (long long)st.chunks_completed, st.chunks_resident);
+    const double qs[3] = {0.5, 0.99, 0.999};
+    double v[3];
+    uint64_t n;
+    hist_period(s->query_hist, L.prev_q, &n, qs, v, 3);
+    const double qmax = s->query_hist.take_max();
+    fprintf(f, ", \"query\": {\"n\": %llu, ", (unsigned long long)n);
+    log_num(f, "p50_us", v[0], n > 0);
+    fprintf(f, ", ");
+    log_num(f, "p99_us", v[1], n > 0);
+    fprintf(f, ", ");
+    log_num(f, "p999_us", v[2], n > 0);
+    fprintf(f, ", ");
+    log_num(f, "max_us", qmax, n > 0);
+    hist_period(s->build_hist, L.prev_b, &n, qs, v, 2);
+    const double bmax = s->build_hist.take_max();
+    fprintf(f, "}, \"build\": {\"n\": %llu, ", (unsigned long long)n);
+    log_num(f, "p50_ms", v[0] * 1e-3, n > 0);
+    fprintf(f, ", ");
+    log_num(f, "p99_ms", v[1] * 1e-3, n > 0);
+    fprintf(f, ", ");
+    log_num(f, "max_ms", bmax * 1e-3, n > 0);
+    fprintf(f, "}, \"session_queries\": [");
+    bool first = true;
+    for (int i = 0; i < s->nsessions.load(std::memory_order_acquire); ++i) {
+        const Session &ss = s->sessions[i];
+        if (!ss.open.load()) continue;
+        fprintf(f, "%s[%d, %lld, %lld]", first ? "" : ", ", i, (long long)ss.answered.load(),
+                (long long)ss.not_ready.load());
+        first = false;
+    }
+    fprintf(f, "]}\n");
+    fflush(f);
+}
+
+void log_run(hf_server *s, MetricsLog *L) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(L->mu);
+    auto next = std::chrono::steady_clock::now();
+    for (;;) {
+        next += std::chrono::milliseconds(L->period_ms);
+        if (L->cv.wait_until(lk, next, [&] { return L->stop; })) break;
+        lk.unlock();
+        log_line(s, *L);
+        lk.lock();
+    }
+    lk.unlock();
+    log_line(s, *L);  // the closing line covers the rest of the last period
+}
+
+// log_mu held
+void log_stop(hf_server *s) {
+    if (!s->log) return;
+    MetricsLog &L = *s->log;
+    {
+        std::lock_guard<std::mutex> g(L.mu);
+        L.stop = true;
+    }
+    L.cv.notify_all();
+    if (L.th.joinable()) L.th.join();
+    fclose(L.f);
+    s->log.reset();
+}
+
+}  // namespace
+
+extern "C" hf_status hf_server_log_open(hf_server *s, const char *path, int period_ms) {
+    if (!s || !path) return srv_fail(HF_EINVAL, "hf_server_log_open: NULL argument");
+    if (period_ms < 10) return srv_fail(HF_EINVAL, "hf_server_log_open: period %d ms (at least 10)", period_ms);
+    std::lock_guard<std::mutex> g(s->log_mu);
+    log_stop(s);
+    FILE *f = fopen(path, "a");
+    if (!f) return srv_fail(HF_EINVAL, "hf_server_log_open: cannot open %s", path);
+    std::unique_ptr<MetricsLog> L(new MetricsLog());
+    L->f = f;
+    L->period_ms = period_ms;
+    L->t_last = now_ms();
+    for (int i = 0; i < LogHist::kBins; ++i) {  // the first period starts now
+        L->prev_q[i] = s->query_hist.bin[i].load();
+        L->prev_b[i] = s->build_hist.bin[i].load();
+    }
+    s->query_hist.take_max();
+    s->build_hist.take_max();
+    L->th = std::thread(log_run, s, L.get());
+    s->log = std::move(L);
+    return HF_OK;
+}
+
+extern "C" hf_status hf_server_log_close(hf_server *s) {
+    if (!s) return srv_fail(HF_EINVAL, "hf_server_log_close: NULL server");
+    std::lock_guard<std::mutex> g(s->log_mu);
+    log_stop(s);
     return HF_OK;
 }
 

@@ -251,3 +251,91 @@ def test_chunks_admitted_as_memory_frees_and_evicted_least_recent_first(hf):
             refused += 1
     assert resident > 0 and refused > 0
     srv.close()
+
+
+def test_closing_a_session_mid_build_leaves_the_others_exact(hf):
+    """A session closed while its builds are queued and running: its
+    requests end failed, its parts stay alive for the build in flight even
+    after the caller drops them, and the other sessions' results are bitwise
+    those of a run without it."""
+    import gc
+    ctx = hf.Context(0)
+    srv = hf.Server(ctx, max_inflight=2, query_lanes=2)
+    keep = make_parts(hf, ctx, 64, 0)
+    other = srv.open(*keep)
+    q = synth.random_quaternions(31, 40)
+    r = srv.submit(other, q)
+    assert srv.wait([r])[r][0] == "done"
+    alone = fields_of(srv, other, (0, 13, 39), 64)
+    cancelled = 0
+    for round_ in range(3):
+        gone = srv.open(*make_parts(hf, ctx, 128, 5 + round_))  # the test keeps no handle to these parts
+        gc.collect()
+        # builds of tens of milliseconds: the close lands while they run or wait
+        doomed = [srv.submit(gone, synth.random_quaternions(40 + round_, 192)) for _ in range(2)]
+        rid = srv.submit(other, q)
+        time.sleep(0.002 * round_)
+        srv.close_session(gone)
+        gc.collect()
+        res = srv.wait(doomed + [rid])
+        assert res[rid][0] == "done"
+        states = [res[d][0] for d in doomed]
+        assert all(x in ("failed", "superseded", "done") for x in states), states
+        cancelled += states.count("failed")
+        assert np.array_equal(fields_of(srv, other, (0, 13, 39), 64), alone)
+    assert cancelled >= 1
+    with pytest.raises(hf.HFError):
+        srv.submit(gone, q)
+    st = srv.stats()
+    assert st["sessions"] == 1
+    srv.close()
+
+
+def test_metrics_log_lines_account_for_every_query_and_build(hf, tmp_path):
+    """The JSON-lines metrics log: one parsable line per period and a last
+    one at close; the per-period query and build counts add up to what the
+    server answered and finished while it was open, the counters only grow,
+    and each period's percentiles are ordered and bound the exact latencies
+    the library recorded."""
+    import json
+    ctx = hf.Context(0)
+    srv = hf.Server(ctx, max_inflight=2, query_lanes=4)
+    a = srv.open(*make_parts(hf, ctx, 64, 8))
+    b = srv.open(*make_parts(hf, ctx, 32, 9))
+    r = [srv.submit(a, synth.random_quaternions(60, 16)), srv.submit(b, synth.random_quaternions(61, 16))]
+    assert all(v[0] == "done" for v in srv.wait(r).values())
+    path = tmp_path / "metrics.jsonl"
+    srv.query_latencies()
+    before = srv.stats()
+    srv.log_open(path, period_ms=50)
+    steps = 400
+    poses = np.stack([np.concatenate([synth.translation_walk(90 + i, steps), synth.quaternion_walk(95 + i, steps)], 1)
+                      for i in range(2)])
+    builds = [srv.submit(a, synth.random_quaternions(64 + i, 24)) for i in range(3)]
+    answered, not_ready, _ = srv.drive_queries([a, b], poses, rate_hz=1000.0)
+    assert srv.wait(builds)
+    lat = srv.query_latencies()
+    time.sleep(0.12)
+    srv.log_close()
+    after = srv.stats()
+    lines = [json.loads(x) for x in path.read_text().splitlines()]
+    assert len(lines) >= 6  # 0.4 s of queries at 50 ms per line, plus the last
+    assert all(y["t_s"] > x["t_s"] for x, y in zip(lines, lines[1:]))
+    for key in ("completed", "queries", "rotations_completed", "submitted"):
+        seq = [x[key] for x in lines]
+        assert seq == sorted(seq) and before[key] <= seq[0] and seq[-1] == after[key], key
+    assert sum(x["query"]["n"] for x in lines) == answered == lat.size
+    assert sum(x["build"]["n"] for x in lines) == after["completed"] - before["completed"]
+    top = 0.0
+    for x in lines:
+        qn = x["query"]
+        if qn["n"]:
+            assert qn["p50_us"] <= qn["p99_us"] <= qn["p999_us"] <= qn["max_us"] * 1.0905
+            top = max(top, qn["max_us"])
+        else:
+            assert qn["p50_us"] is None
+    assert abs(top - float(lat.max())) <= 1e-3 * top + 1e-3
+    last = {s: (ans, nr) for s, ans, nr in lines[-1]["session_queries"]}
+    assert sorted(last) == [a, b]
+    assert sum(v[0] for v in last.values()) >= answered
+    srv.close()
