@@ -291,11 +291,15 @@ def run_ours(args, rank, world, local_rank):
         "resample": n3b + chunk * n3b,
     }
     # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the
-    # tuned pass C kernel (256 threads per CTA) over 32 rotations at 128^3,
-    # scaled to this launch's rotations: the traffic is per rotation (each
-    # reads its own two spectra and writes its own four fields); none for
-    # another launch shape
-    traffic = {"passC": 1.5742e9 * chunk / 32} if n == 128 and not tune_is_pencil(ctx, n) and ctx.tune_tiles(n)[1] == 2 else {}
+    # pass C kernel of this launch shape (tile 5: planes staged by bulk
+    # copies, 256 threads per CTA; tile 2: the same threads with plain loads)
+    # over 32 rotations at 128^3, scaled to this launch's rotations: the
+    # traffic is per rotation (each reads its own two spectra and writes its
+    # own four fields); none for another launch shape
+    captured = {5: 1.5716e9, 2: 1.5742e9}
+    tc_now = ctx.tune_tiles(n)[1]
+    traffic = ({"passC": captured[tc_now] * chunk / 32}
+               if n == 128 and not tune_is_pencil(ctx, n) and tc_now in captured else {})
     hbm_peak, peak_kind = peaks()
     kernels = {}
     for k, (cnt, tot) in prof.items():

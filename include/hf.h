@@ -554,8 +554,12 @@ hf_status hf_tune_get(const hf_ctx *ctx, int n, int *chunk, int *pencil, double 
  * per CTA, 1 = 16; tile_c 0 = the built-in rows per x batch and threads,
  * 1 = 16 rows per x batch, and at N = 128 only 2 = 256 threads per CTA,
  * 3 = that and an L2 prefetch of the block's third input plane, 4 = that
- * and two y-stage items' loads in flight per thread; other than 0 only for
- * N = 64, 96, 128.  set != 0 stores *tile_b / *tile_c (the
+ * and two y-stage items' loads in flight per thread; 5 = each input plane
+ * brought into shared memory by bulk copies, the next plane's rows copied as
+ * the x transform frees them (256 threads at N = 128); 5 is the shape used
+ * at N = 64, 96, 128 when none was chosen, 0 at other N.  Other than 0 only
+ * for N = 64, 96, 128.
+ * set != 0 stores *tile_b / *tile_c (the
  * fields do not change, only their speed), else reads them.  Errors:
  * HF_EINVAL, HF_EUNSUPPORTED. */
 hf_status hf_tune_tiles(hf_ctx *ctx, int n, int set, int *tile_b, int *tile_c);

@@ -874,6 +874,11 @@ int default_chunk(int n) {
     }
 }
 
+// pass C's launch shape when the autotuner has not chosen one: at 64^3,
+// 96^3 and 128^3 the bulk-staged form (tile 5; 256 threads per CTA at 128^3),
+// else the built-in one
+int default_tile_c(int n) { return n >= 64 && n <= 128 ? 5 : 0; }
+
 }  // namespace
 
 // -------------------------------------------------- rotation-set chunking
@@ -1000,6 +1005,7 @@ static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags,
                                                                                              : hf::PREC_FP32;
     fs->spectral = (flags & HF_SPECTRAL) != 0;
     fs->chunk = default_chunk(n);
+    fs->tile_c = default_tile_c(n);
     {
         const Tune &t = ctx->tune[tune_slot(n)];
         const char *ev = getenv("HF_ROT_CHUNK");
@@ -1658,7 +1664,7 @@ extern "C" hf_status hf_tune_tiles(hf_ctx *ctx, int n, int set, int *tile_b, int
     if (!hf::supported_n(n)) return fail(HF_EUNSUPPORTED, "hf_tune_tiles: N=%d not supported", n);
     Tune &t = ctx->tune[tune_slot(n)];
     if (set) {
-        if (*tile_b < 0 || *tile_b > 1 || *tile_c < 0 || *tile_c > 4 || (*tile_c >= 2 && n != 128) ||
+        if (*tile_b < 0 || *tile_b > 1 || *tile_c < 0 || *tile_c > 5 || (*tile_c >= 2 && *tile_c <= 4 && n != 128) ||
             ((*tile_b || *tile_c) && (n < 64 || n > 128)))
             return fail(HF_EINVAL, "hf_tune_tiles: tile_b %d, tile_c %d at N=%d", *tile_b, *tile_c, n);
         if (!t.set) {  // keep the built-in chunk and pipeline
@@ -1670,7 +1676,7 @@ extern "C" hf_status hf_tune_tiles(hf_ctx *ctx, int n, int set, int *tile_b, int
         t.tile_c = *tile_c;
     } else {
         *tile_b = t.set ? t.tile_b : 0;
-        *tile_c = t.set ? t.tile_c : 0;
+        *tile_c = t.set ? t.tile_c : default_tile_c(n);
     }
     return HF_OK;
 }
@@ -1728,10 +1734,10 @@ std::string tune_json_line(const std::string &dev, int n, const Tune &t, const s
     snprintf(buf, sizeof buf,
              "{\"device\": \"%s\", \"n\": %d, \"chunk\": %d, \"pipeline\": \"%s\", \"tile_b\": %d, \"tile_c\": %d, "
              "\"lanes\": %d, \"radix\": \"%s\", \"passB_columns_per_cta\": %d, \"passC_rows_per_x_batch\": %d, "
-             "\"passC_threads\": %d, \"rot_per_s\": %.6g}",
+             "\"passC_threads\": %d, \"passC_staging\": \"%s\", \"rot_per_s\": %.6g}",
              dev.c_str(), n, t.chunk, t.pencil ? "pencil" : "slab", t.tile_b, t.tile_c, t.lanes, tune_radix(n),
              tune_pass_b_columns(n, t.tile_b), tune_pass_c_rows(n, t.tile_c), tune_pass_c_threads(n, t.tile_c),
-             t.rot_per_s);
+             t.tile_c == 5 ? "bulk" : "loads", t.rot_per_s);
     std::string l = buf;
     if (!cands.empty()) {  // every timed candidate: [chunk, pencil, tile_b, tile_c, lanes, rot_per_s]
         l.pop_back();
@@ -1908,10 +1914,9 @@ extern "C" hf_status hf_autotune(hf_ctx *ctx, int n, const char *cache_path, int
         // the launch shapes of passes B and C at the best slab shape: every
         // compiled candidate (tile 0 is the one timed above)
         if (best.set && !best.pencil && n >= 64 && n <= 128) {
-            const int tc_max = n == 128 ? 4 : 1;
             for (int tb = 0; tb <= 1; ++tb)
-                for (int tc = 0; tc <= tc_max; ++tc) {
-                    if (tb == 0 && tc == 0) continue;
+                for (int tc = 0; tc <= 5; ++tc) {
+                    if ((tb == 0 && tc == 0) || (n != 128 && tc >= 2 && tc <= 4)) continue;
                     Tune &t = ctx->tune[tune_slot(n)];
                     t = best;
                     t.tile_b = tb;

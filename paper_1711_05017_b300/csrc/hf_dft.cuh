@@ -36,8 +36,9 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
 }
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
-// multiply by i * s
-__device__ __forceinline__ float2 cmul_is(float2 a, float s) { return make_float2(-a.y * s, a.x * s); }
+// multiply by i * s, as rounded products (never contracted into a following
+// add), so that every kernel that applies the multiplier gives the same bits
+__device__ __forceinline__ float2 cmul_is(float2 a, float s) { return make_float2(__fmul_rn(-a.y, s), __fmul_rn(a.x, s)); }
 
 // ------------------------------------------------ compile-time trigonometry
 // cos / sin of 2*pi*j/R in double, by octant reduction and Taylor series,

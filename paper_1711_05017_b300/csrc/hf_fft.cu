@@ -75,6 +75,57 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+// Bulk copies (the TMA engine's untiled form) into this CTA's shared memory,
+// completing on an mbarrier; both addresses 16-byte aligned, bytes a
+// multiple of 16.  Waits are bounded: a wait that gives up counts itself in
+// g_bulk_timeouts (the blocks that read such a plane wrote invalid output).
+__device__ int g_bulk_timeouts = 0;
+constexpr unsigned long long kBulkWaitNs = 200ull * 1000 * 1000;
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init1(unsigned long long *mbar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\nfence.mbarrier_init.release.cluster;\n" ::"r"(smem_addr(mbar))
+                 : "memory");
+}
+// the arrival that opens a phase expecting `bytes` of copies
+__device__ __forceinline__ void mbar_expect(unsigned long long *mbar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes) : "memory");
+}
+// generic-proxy accesses to shared memory before this point are ordered before
+// the async-proxy writes of copies issued after it (by this thread, after a
+// barrier that covers the other threads' accesses)
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(mbar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long *mbar, unsigned parity) {
+    unsigned ok;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(smem_addr(mbar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// wait for phase `parity` of mbar; on giving up, count it and wait once more
+// (bounded) so that no copy is left writing into the block's shared memory
+__device__ __forceinline__ void mbar_wait_bounded(unsigned long long *mbar, unsigned parity) {
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        const unsigned long long t0 = globaltimer_ns();
+        while (!mbar_test(mbar, parity))
+            if (globaltimer_ns() - t0 > kBulkWaitNs) break;
+        if (mbar_test(mbar, parity)) return;
+        if (attempt == 0 && threadIdx.x == 0) atomicAdd(&g_bulk_timeouts, 1);
+    }
+}
+
 // The rotated resample through the texture units.  The moving grid is held as a
 // 2D float array of stacked z-slices, each (N+1) x (N+1) with the wrapped
 // row y = N and column x = N appended, so slice z spans rows
@@ -233,7 +284,7 @@ __device__ __forceinline__ void passA_body(const float *__restrict__ rho, const 
     __builtin_assume(zu < (1u << 16) && ru < (1u << 16));  // the ranges of the blockIdx they stand for
     const int z = (int)zu, r = (int)ru;
     constexpr int H = PassA<N>::H, HALF = PassA<N>::HALF, NT = PassA<N>::NT;
-    extern __shared__ float2 sm[];
+    extern __shared__ __align__(16) float2 sm[];
     float2 *P = sm;            // [N rows y][H]  (row = N reals = N/2 complex + Nyquist slot)
     float2 *twN = P + N * H;   // exp(-2 pi i j / N)
     float2 *twH = twN + N;     // exp(-2 pi i j / (N/2))
@@ -551,7 +602,7 @@ __device__ __forceinline__ void passB_body(const float2 *__restrict__ X1, const 
     using PB = PassB<N, CWO>;
     constexpr int H = PB::H, R1 = PB::R1, R2 = PB::R2, CW = PB::CW, KPT = PB::KPT;
     constexpr size_t NH = (size_t)N * H;
-    extern __shared__ float2 sm[];
+    extern __shared__ __align__(16) float2 sm[];
     float2 *E = sm;                      // [k1][n2][c], later S's [n2][k1][c]
     float2 *G = sm + (size_t)N * CW;     // Gz's [n2][k1][c]
     float2 *twN = G + (size_t)N * CW;
@@ -699,7 +750,7 @@ __global__ void __launch_bounds__(PassB<N>::NT, 2) passB_torque_kernel(const flo
     constexpr int H = PassB<N>::H, R1 = PassB<N>::R1, R2 = PassB<N>::R2, CW = PassB<N>::CW,
                   KPT = PassB<N>::KPT;
     constexpr size_t NH = (size_t)N * H;
-    extern __shared__ float2 sm[];
+    extern __shared__ __align__(16) float2 sm[];
     float2 *E[3] = {sm, sm + (size_t)N * CW, sm + 2 * (size_t)N * CW};  // E[0] is also the forward exchange
     float2 *twN = sm + 3 * (size_t)N * CW;
     const int c = threadIdx.x % CW, g = threadIdx.x / CW;
@@ -859,12 +910,18 @@ __device__ __forceinline__ void st_keep(float *p, float v, uint64_t pol) {
     asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
 }
 
+// x_pass calls hook(y0) once per row batch, right after the barrier that ends
+// the batch's reads of the plane (the rows it read may then be overwritten)
+struct NoHook {
+    __device__ __forceinline__ void operator()(int) const {}
+};
+
 template <int N, int PAIR, int PW, int RB, int TP, int NT, int ROWS, bool CTW = true, bool KEEP0 = false,
-          bool KEEP1 = false>
+          bool KEEP1 = false, class Hook = NoHook>
 __device__ __forceinline__ void x_pass(const float2 *planeA, const float2 *planeB, int colA, int colB,
                                        float2 *Tb, const float2 *twN,
                                        float *__restrict__ out0, float *__restrict__ out1,
-                                       const TorqueCorr *tc = nullptr) {
+                                       const TorqueCorr *tc = nullptr, const Hook &hook = Hook()) {
     // N = R1 R2 with the longer digit second, so that stage 2 runs with lanes
     // along it: its reads of the row buffer are contiguous and its outputs
     // (x = R2 n1 + n2) go straight to HBM as full 32-byte sectors
@@ -902,6 +959,7 @@ __device__ __forceinline__ void x_pass(const float2 *planeA, const float2 *plane
             }
         }
         __syncthreads();
+        hook(y0);
         // stage 2 (inverse), items (row, n2), lanes along n2: x = R2 n1 + n2
 #pragma unroll 1
         for (int w = threadIdx.x; w < RB * R2; w += NT) {
@@ -958,6 +1016,59 @@ __device__ __forceinline__ void x_pass(const float2 *planeA, const float2 *plane
     }
 }
 
+// The y inverse after stage 1 (its barrier included): the Nyquist column's
+// two steps and stage 2, in place in the plane
+template <int N, int NT>
+__device__ __forceinline__ void y_inverse_tail(float2 *plane, const float2 *twN) {
+    constexpr int HALF = N / 2, R1 = Fact<N>::R1, R2 = Fact<N>::R2, PW = PassC<N>::PW;
+    // Nyquist column, step 1 (warp 0, items k1, in place): slots R2 k1 + k2
+    if (threadIdx.x < R1) {
+        const int k1 = threadIdx.x;
+        float2 *p = plane + (size_t)(R2 * k1) * PW + HALF;
+        float2 v[R2];
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) v[k2] = p[k2 * PW];
+        RegDFT<R2, +1>::run(v);
+#pragma unroll
+        for (int n2 = 0; n2 < R2; ++n2) p[n2 * PW] = n2 ? cmulc(v[n2], twN[n2 * k1]) : v[n2];
+    }
+    // stage 2: items (c, n2); every item is read before any row is written
+    constexpr int ITEMS = HALF * R2, IPT = (ITEMS + NT - 1) / NT;
+    float2 v[IPT][R1];
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+        const int w = threadIdx.x + j * NT;
+        if (w < ITEMS) {
+            const int c = w % HALF, n2 = w / HALF;
+#pragma unroll
+            for (int k1 = 0; k1 < R1; ++k1) v[j][k1] = plane[(n2 * R1 + k1) * PW + c];
+            RegDFT<R1, +1>::run(v[j]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+        const int w = threadIdx.x + j * NT;
+        if (w < ITEMS) {
+            const int c = w % HALF, n2 = w / HALF;
+#pragma unroll
+            for (int n1 = 0; n1 < R1; ++n1) plane[(R2 * n1 + n2) * PW + c] = v[j][n1];
+        }
+    }
+    // Nyquist column, step 2 (warp 1, items n2, in place): natural y = R2 n1 + n2
+    if (threadIdx.x >= 32 && threadIdx.x < 32 + R2) {
+        const int n2 = threadIdx.x - 32;
+        float2 *p = plane + (size_t)n2 * PW + HALF;
+        float2 u[R1];
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) u[k1] = p[k1 * R2 * PW];
+        RegDFT<R1, +1>::run(u);
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1) p[n1 * R2 * PW] = u[n1];
+    }
+    __syncthreads();
+}
+
 // Inverse y transform of one z-plane's H half-spectrum columns: global rows
 // src[s H + c] (ky slot order) -> plane[y PW + c] (natural y).  The N/2 main
 // columns run register-centric (stage 1 straight from HBM, the digit
@@ -1010,52 +1121,56 @@ __device__ __forceinline__ void y_inverse_plane(const float2 *__restrict__ src, 
         plane[threadIdx.x * PW + HALF] = nyq;
     }
     __syncthreads();
-    // Nyquist column, step 1 (warp 0, items k1, in place): slots R2 k1 + k2
-    if (threadIdx.x < R1) {
-        const int k1 = threadIdx.x;
-        float2 *p = plane + (size_t)(R2 * k1) * PW + HALF;
-        float2 v[R2];
-#pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) v[k2] = p[k2 * PW];
-        RegDFT<R2, +1>::run(v);
-#pragma unroll
-        for (int n2 = 0; n2 < R2; ++n2) p[n2 * PW] = n2 ? cmulc(v[n2], twN[n2 * k1]) : v[n2];
-    }
-    // stage 2: items (c, n2); every item is read before any row is written
-    constexpr int ITEMS = HALF * R2, IPT = (ITEMS + NT - 1) / NT;
-    float2 v[IPT][R1];
+    y_inverse_tail<N, NT>(plane, twN);
+}
+
+// The same inverse on a plane that bulk copies bring into shared memory
+// (plane[s PW + c] = src[s H + c], arriving on mbar's phase `parity`):
+// stage 1 reads its items from the plane into registers, and after a barrier
+// writes them back in place.
+template <int N, bool MUL, bool CTW, int NT>
+__device__ __forceinline__ void y_inverse_plane_smem(float2 *plane, const float2 *twN, unsigned long long *mbar,
+                                                     unsigned parity) {
+    constexpr int HALF = N / 2, R1 = Fact<N>::R1, R2 = Fact<N>::R2, PW = PassC<N>::PW;
+    static_assert(PW == N / 2 + 1, "the plane's rows are the source rows");
+    static_assert(NT >= N && NT >= 32 + R2, "one Nyquist value per thread; Nyquist steps on warps 0 and 1");
+    constexpr int ITEMS = HALF * R1, IPT = (ITEMS + NT - 1) / NT;
+    mbar_wait_bounded(mbar, parity);
+    float2 v[IPT][R2];
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
         const int w = threadIdx.x + j * NT;
-        if (w < ITEMS) {
-            const int c = w % HALF, n2 = w / HALF;
+        if (ITEMS % NT == 0 || w < ITEMS) {
+            const int c = w % HALF, k1 = w / HALF;
 #pragma unroll
-            for (int k1 = 0; k1 < R1; ++k1) v[j][k1] = plane[(n2 * R1 + k1) * PW + c];
-            RegDFT<R1, +1>::run(v[j]);
+            for (int k2 = 0; k2 < R2; ++k2) {
+                v[j][k2] = plane[(R2 * k1 + k2) * PW + c];
+                if constexpr (MUL) v[j][k2] = cmul_is(v[j][k2], signed_k_mult<N>(slot_freq<N>(R2 * k1 + k2)));
+            }
+            RegDFT<R2, +1>::run(v[j]);
+        }
+    }
+    if constexpr (MUL) {
+        if (threadIdx.x < N) {  // the Nyquist column: no stage-1 item touches it
+            float2 *q = plane + (size_t)threadIdx.x * PW + HALF;
+            *q = cmul_is(*q, signed_k_mult<N>(slot_freq<N>(threadIdx.x)));
         }
     }
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
         const int w = threadIdx.x + j * NT;
-        if (w < ITEMS) {
-            const int c = w % HALF, n2 = w / HALF;
+        if (ITEMS % NT == 0 || w < ITEMS) {
+            const int c = w % HALF, k1 = w / HALF;
 #pragma unroll
-            for (int n1 = 0; n1 < R1; ++n1) plane[(R2 * n1 + n2) * PW + c] = v[j][n1];
+            for (int n2 = 0; n2 < R2; ++n2) {
+                const float2 t = (CTW && HALF % 32 == 0) ? tw_uniform<N>(n2 * k1) : twN[n2 * k1];
+                plane[(n2 * R1 + k1) * PW + c] = n2 ? cmulc(v[j][n2], t) : v[j][n2];
+            }
         }
     }
-    // Nyquist column, step 2 (warp 1, items n2, in place): natural y = R2 n1 + n2
-    if (threadIdx.x >= 32 && threadIdx.x < 32 + R2) {
-        const int n2 = threadIdx.x - 32;
-        float2 *p = plane + (size_t)n2 * PW + HALF;
-        float2 u[R1];
-#pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1) u[k1] = p[k1 * R2 * PW];
-        RegDFT<R1, +1>::run(u);
-#pragma unroll
-        for (int n1 = 0; n1 < R1; ++n1) p[n1 * R2 * PW] = u[n1];
-    }
     __syncthreads();
+    y_inverse_tail<N, NT>(plane, twN);
 }
 
 // Pass C holds one half-spectrum plane at a time (about 100 KB of shared
@@ -1071,9 +1186,33 @@ __device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// x_pass hook of the bulk-staged pass C: once a row batch of the plane has
+// been read, thread 0 starts the copies of the same rows of the next plane
+// (`src`; ROWSETS 2: the batch read rows y0.. and N/2 + y0..); the first
+// batch opens the mbarrier phase for the whole plane
+template <int N, int RB, int ROWSETS>
+struct RowRefill {
+    float2 *plane;
+    const float2 *src;
+    unsigned long long *mbar;
+    __device__ __forceinline__ void operator()(int y0) const {
+        constexpr int H = N / 2 + 1;
+        constexpr unsigned BYTES = sizeof(float2) * RB * H;
+        static_assert(BYTES % 16 == 0 && (sizeof(float2) * H * RB) % 16 == 0, "16-byte copies");
+        if (threadIdx.x != 0) return;
+        fence_proxy_async_smem();
+        if (y0 == 0) mbar_expect(mbar, (unsigned)(sizeof(float2) * N * H));
+        bulk_g2s(plane + (size_t)y0 * H, src + (size_t)y0 * H, BYTES, mbar);
+        if constexpr (ROWSETS == 2) bulk_g2s(plane + (size_t)(N / 2 + y0) * H, src + (size_t)(N / 2 + y0) * H, BYTES, mbar);
+    }
+};
+
 // YU: y-stage items whose loads a thread keeps in flight; PF: prefetch the
-// block's Gz' plane into L2 when the block starts (it is read third)
-template <int N, bool TQ, int NT = PassC<N>::NT, bool COH = false, int RBO = 0, int YU = 1, bool PF = false>
+// block's Gz' plane into L2 when the block starts (it is read third); BK:
+// bring each input plane into shared memory by bulk copies, the next plane's
+// rows issued as the x pass frees them (one mbarrier, one phase per plane)
+template <int N, bool TQ, int NT = PassC<N>::NT, bool COH = false, int RBO = 0, int YU = 1, bool PF = false,
+          bool BK = false>
 __device__ __forceinline__ void passC_body(const float2 *__restrict__ Y1, const float2 *__restrict__ Y2,
                                            const FieldPtrs &out, const float2 *__restrict__ YT, size_t yt_stride,
                                            unsigned zu, unsigned ru) {
@@ -1081,12 +1220,40 @@ __device__ __forceinline__ void passC_body(const float2 *__restrict__ Y1, const 
     const int z = (int)zu, r = (int)ru;
     using PC = PassC<N, RBO>;
     constexpr int H = PC::H, PW = PC::PW, RB = PC::RB, TP = PC::TP, HALF = N / 2;
-    extern __shared__ float2 sm[];
+    extern __shared__ __align__(16) float2 sm[];
     float2 *plane = sm;                       // [N][PW]
     float2 *Tb = plane + (size_t)N * PW;      // [RB][TP]
     float2 *twN = Tb + (size_t)RB * TP;
     const float2 *s1 = Y1 + ((size_t)r * N + z) * N * H;
     const size_t fo = (size_t)r * out.rot_stride + (size_t)z * N * N;
+    if constexpr (BK) {
+        static_assert(!TQ && !COH && YU == 1 && !PF, "the bulk-staged form of the E/F kernel");
+        static_assert((sizeof(float2) * N * H) % 16 == 0, "whole 16-byte units");
+        // the mbarrier sits after the twiddles (8-byte aligned)
+        unsigned long long *mbar = reinterpret_cast<unsigned long long *>(twN + N);
+        const float2 *s2 = Y2 + ((size_t)r * N + z) * N * H;
+        if (threadIdx.x == 0) {
+            mbar_init1(mbar);
+            mbar_expect(mbar, (unsigned)(sizeof(float2) * N * H));
+            bulk_g2s(plane, s1, (unsigned)(sizeof(float2) * N * H), mbar);
+        }
+        load_tw<N>(twN);
+        __syncthreads();
+        // E + i Fx; its batches refill the plane with S' (for Gy)
+        y_inverse_plane_smem<N, false, true, NT>(plane, twN, mbar, 0);
+        x_pass<N, 0, PW, RB, TP, NT, N, true, false, false>(plane, plane, 0, 0, Tb, twN, out.E + fo, out.Fx + fo,
+                                                            nullptr, RowRefill<N, RB, 1>{plane, s1, mbar});
+        // Fy; its batches refill the plane with Gz'
+        y_inverse_plane_smem<N, true, true, NT>(plane, twN, mbar, 1);
+        x_pass<N, 1, PW, RB, TP, NT, HALF, true, false, false>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN,
+                                                               out.Fy + fo, out.Fy + fo + (size_t)HALF * N, nullptr,
+                                                               RowRefill<N, RB, 2>{plane, s2, mbar});
+        // Fz
+        y_inverse_plane_smem<N, false, true, NT>(plane, twN, mbar, 0);
+        x_pass<N, 1, PW, RB, TP, NT, HALF>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, out.Fz + fo,
+                                           out.Fz + fo + (size_t)HALF * N);
+        return;
+    }
     if constexpr (PF) {
         static_assert((sizeof(float2) * N * H) % 16 == 0, "whole 16-byte units");
         if (threadIdx.x == 0) prefetch_l2(Y2 + ((size_t)r * N + z) * N * H, (unsigned)(sizeof(float2) * N * H));
@@ -1118,13 +1285,19 @@ __device__ __forceinline__ void passC_body(const float2 *__restrict__ Y1, const 
     }
 }
 
-template <int N, bool TQ, int RBO = 0, int NTO = 0, int YU = 1, bool PF = false>
+template <int N, bool TQ, int RBO = 0, int NTO = 0, int YU = 1, bool PF = false, bool BK = false>
 __global__ void __launch_bounds__(PassC<N, RBO, NTO>::NT, PassC<N, RBO, NTO>::MINB) passC_kernel(const float2 *__restrict__ Y1,
                                                                               const float2 *__restrict__ Y2,
                                                                               FieldPtrs out,
                                                                               const float2 *__restrict__ YT,
                                                                               size_t yt_stride) {
-    passC_body<N, TQ, PassC<N, RBO, NTO>::NT, false, RBO, YU, PF>(Y1, Y2, out, YT, yt_stride, blockIdx.x, blockIdx.y);
+    passC_body<N, TQ, PassC<N, RBO, NTO>::NT, false, RBO, YU, PF, BK>(Y1, Y2, out, YT, yt_stride, blockIdx.x,
+                                                                      blockIdx.y);
+}
+// dynamic shared memory of the bulk-staged form: the mbarrier after the twiddles
+template <int N, int RBO = 0, int NTO = 0>
+constexpr size_t passC_bulk_smem() {
+    return PassC<N, RBO, NTO>::smem + 16;
 }
 
 // the stationary moment fields G_a = (u x F)_a / h^3 (F = -h^3 grad rho1)
@@ -1177,7 +1350,7 @@ __global__ void __launch_bounds__(Pencil<N>::NT, Pencil<N>::XMINB) xfwd_kernel(c
                                                              const float *__restrict__ rot9,
                                                              const int *__restrict__ box) {
     constexpr int H = Pencil<N>::H, HALF = Pencil<N>::HALF, RBX = Pencil<N>::RBX, NT = Pencil<N>::NT;
-    extern __shared__ float2 sm[];
+    extern __shared__ __align__(16) float2 sm[];
     float2 *P = sm;               // [RBX][H]
     float2 *twN = P + RBX * H;
     float2 *twH = twN + N;
@@ -1234,7 +1407,7 @@ template <int N>
 __global__ void __launch_bounds__(Pencil<N>::NT) yfwd_kernel(const float2 *__restrict__ Xa,
                                                              float2 *__restrict__ X1) {
     constexpr int H = Pencil<N>::H, CY = Pencil<N>::CY, NCY = Pencil<N>::NCY, NT = Pencil<N>::NT;
-    extern __shared__ float2 sm[];
+    extern __shared__ __align__(16) float2 sm[];
     float2 *T = sm;               // [N][CY]
     float2 *twN = T + N * CY;
     const int z = blockIdx.x / NCY, c0 = (blockIdx.x % NCY) * CY, r = blockIdx.y;
@@ -1264,7 +1437,7 @@ __global__ void __launch_bounds__(Pencil<N>::NT) yinv_kernel(const float2 *__res
                                                              float2 *__restrict__ ZGz) {
     constexpr int H = Pencil<N>::H, CY = Pencil<N>::CY, NCY = Pencil<N>::NCY, NT = Pencil<N>::NT,
                   W3 = 3 * CY;
-    extern __shared__ float2 sm[];
+    extern __shared__ __align__(16) float2 sm[];
     float2 *T = sm;               // [N][3 CY]: S | Gy | Gz
     float2 *twN = T + N * W3;
     const int z = blockIdx.x / NCY, c0 = (blockIdx.x % NCY) * CY, r = blockIdx.y;
@@ -1307,7 +1480,7 @@ __global__ void __launch_bounds__(Pencil<N>::NT) xinv_kernel(const float2 *__res
                                                              const float2 *__restrict__ ZGz, FieldPtrs out) {
     constexpr int H = Pencil<N>::H, RBX = Pencil<N>::RBX, NT = Pencil<N>::NT, PW = Pencil<N>::PW,
                   TP = Pencil<N>::TP;
-    extern __shared__ float2 sm[];
+    extern __shared__ __align__(16) float2 sm[];
     float2 *plane = sm;                    // [RBX][PW]
     float2 *Tb = plane + RBX * PW;         // [RBX][TP]
     float2 *twN = Tb + RBX * TP;
@@ -1406,6 +1579,7 @@ static cudaError_t set_smem_attrs() {
     if constexpr (N >= 64 && N <= 128) {  // the autotuner's tile candidates
         if ((e = cudaFuncSetAttribute(passB_kernel<N, 0, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N, 16>::smem))) return e;
         if ((e = cudaFuncSetAttribute(passC_kernel<N, false, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassC<N, 16>::smem))) return e;
+        if ((e = cudaFuncSetAttribute(passC_kernel<N, false, 0, (N == 128 ? 256 : 0), 1, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)passC_bulk_smem<N, 0, (N == 128 ? 256 : 0)>()))) return e;
         if constexpr (N == 128) {
             if ((e = cudaFuncSetAttribute(passC_kernel<N, false, 0, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassC<N, 0, 256>::smem))) return e;
             if ((e = cudaFuncSetAttribute(passC_kernel<N, false, 0, 256, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassC<N, 0, 256>::smem))) return e;
@@ -1465,10 +1639,15 @@ static cudaError_t launch_passB_spectral(const float2 *table, cudaTextureObject_
         nullptr, R1hat, Y1, Y2, 0.f, SpecSrc{table, os * N, os, tex, table_tex_sc(os * N)}, rot9);
     return cudaGetLastError();
 }
-template <int N, int RBO = 0, int NTO = 0, int YU = 1, bool PF = false>
+template <int N, int RBO = 0, int NTO = 0, int YU = 1, bool PF = false, bool BK = false>
 static cudaError_t launch_passC(const float2 *Y1, const float2 *Y2, FieldPtrs out, int nrot, cudaStream_t st) {
     using PC = PassC<N, RBO, NTO>;
-    passC_kernel<N, false, RBO, NTO, YU, PF><<<dim3(N, nrot), PC::NT, PC::smem, st>>>(Y1, Y2, out, nullptr, 0);
+    if constexpr (BK) {
+        // the bulk copies read whole planes: 16-byte aligned sources
+        if (((uintptr_t)Y1 | (uintptr_t)Y2) % 16) return cudaErrorMisalignedAddress;
+    }
+    passC_kernel<N, false, RBO, NTO, YU, PF, BK>
+        <<<dim3(N, nrot), PC::NT, BK ? passC_bulk_smem<N, RBO, NTO>() : PC::smem, st>>>(Y1, Y2, out, nullptr, 0);
     return cudaGetLastError();
 }
 template <int N>
@@ -1733,6 +1912,13 @@ cudaError_t run_passC(int n, const float2 *Y1, const float2 *Y2, FieldPtrs out, 
         return launch_passC<128, 0, 256, 1, true>(Y1, Y2, out, nrot, st);
     } else if (tile == 4 && n == 128) {  // and two y-stage items' loads in flight
         return launch_passC<128, 0, 256, 2, true>(Y1, Y2, out, nrot, st);
+    } else if (tile == 5) {  // planes staged by bulk copies (256 threads at 128^3)
+        switch (n) {
+            case 64: return launch_passC<64, 0, 0, 1, false, true>(Y1, Y2, out, nrot, st);
+            case 96: return launch_passC<96, 0, 0, 1, false, true>(Y1, Y2, out, nrot, st);
+            case 128: return launch_passC<128, 0, 256, 1, false, true>(Y1, Y2, out, nrot, st);
+            default: break;
+        }
     }
     HF_DISPATCH(n, launch_passC<NN>(Y1, Y2, out, nrot, st));
 }
