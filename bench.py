@@ -1024,9 +1024,18 @@ def run_serving(args, local_rank):
                    "latency_ms_p50": pct(build_lat, 50) if build_lat else None,
                    "latency_ms_p99": pct(build_lat, 99) if build_lat else None},
         "fields_per_s": round((st1["rotations_completed"] - st0["rotations_completed"]) / elapsed, 1),
+        "memory_pool_gb": {"reserved_at_start": round(st0["pool_reserved_bytes"] / 2**30, 2),
+                           "reserved_at_end": round(st1["pool_reserved_bytes"] / 2**30, 2),
+                           "reserved_high": round(st1["pool_reserved_high"] / 2**30, 2)},
+        "hardware_queues": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS", "8 (the default)"),
         "slowest_queries": worst,
         "slow_scheduler_calls": {"n": int(len(slow_c)),
-                                 "max_us": round(float(slow_c[:, 1].max()), 1) if len(slow_c) else 0.0},
+                                 "max_us": round(float(slow_c[:, 1].max()), 1) if len(slow_c) else 0.0,
+                                 "by_kind": {name: {"n": int((slow_c[:, 2] == k).sum()),
+                                                    "max_us": round(float(slow_c[slow_c[:, 2] == k, 1].max()), 1),
+                                                    "p50_us": round(float(np.median(slow_c[slow_c[:, 2] == k, 1])), 1)}
+                                             for k, name in enumerate(("create", "compute", "release"))
+                                             if len(slow_c) and (slow_c[:, 2] == k).any()}},
     }
     srv.close()
     del parts

@@ -390,6 +390,9 @@ typedef struct {
     int64_t chunks_submitted, chunks_completed;
     int chunks_resident;
     size_t chunk_bytes;
+    /* the device's default memory pool, which the builds allocate from: its
+     * reserved bytes now and at their highest */
+    size_t pool_reserved_bytes, pool_reserved_high;
 } hf_server_stats;
 
 /* max_inflight: builds on the device at once (1..16); query_lanes: 1..64. */

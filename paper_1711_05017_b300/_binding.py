@@ -119,7 +119,8 @@ class ServerStats(ctypes.Structure):
                 ("queries", ctypes.c_int64), ("rotations_completed", ctypes.c_int64), ("queued", ctypes.c_int),
                 ("running", ctypes.c_int), ("sessions", ctypes.c_int), ("reserved_bytes", ctypes.c_size_t),
                 ("budget_bytes", ctypes.c_size_t), ("chunks_submitted", ctypes.c_int64),
-                ("chunks_completed", ctypes.c_int64), ("chunks_resident", ctypes.c_int), ("chunk_bytes", ctypes.c_size_t)]
+                ("chunks_completed", ctypes.c_int64), ("chunks_resident", ctypes.c_int), ("chunk_bytes", ctypes.c_size_t),
+                ("pool_reserved_bytes", ctypes.c_size_t), ("pool_reserved_high", ctypes.c_size_t)]
 
 _lib = None
 

@@ -161,6 +161,7 @@ struct hf_fieldset {
     cudaStream_t mem_stream = nullptr;  // non-null: stream-ordered device memory, pageable staging
     std::vector<char> pageable_stage;
     void *h_stage = nullptr;     // staging for the per-call uploads (pinned unless mem_stream)
+    bool stage_owned_pinned = false;  // h_stage is the set's own pinned allocation
     size_t stage_bytes = 0;
     cudaEvent_t stage_done = nullptr;  // the last uploads from h_stage have been consumed
     // the host preparation of the last rotation set (matrices, neighbours,
@@ -955,20 +956,24 @@ static size_t fieldset_bytes(int n, int R, unsigned flags, int chunk, int lanes)
 // intermediates per rotation: 3 half spectra for the slab passes, 5 for the pencil pipeline
 static size_t fields_spectra(bool pencil) { return pencil ? 5 : 3; }
 
+// h_stage_ext: caller-owned pinned staging for the per-compute uploads (used
+// if at least the set's staging bytes; else the set makes its own); lanes:
+// 1 or 2 pipelines, 0 for the context's choice
 static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags, cudaStream_t mem_stream,
-                                      hf_fieldset **out);
+                                      hf_fieldset **out, void *h_stage_ext = nullptr, size_t h_stage_ext_bytes = 0,
+                                      int lanes = 0);
 
 extern "C" hf_status hf_fieldset_create(hf_ctx *ctx, int n, int R, unsigned flags, hf_fieldset **out) {
     return fieldset_create_impl(ctx, n, R, flags, nullptr, out);
 }
 
 hf_status hf_fieldset_create_stream_ordered(hf_ctx *ctx, int n, int R, unsigned flags, cudaStream_t st,
-                                            hf_fieldset **out) {
-    return fieldset_create_impl(ctx, n, R, flags, st, out);
+                                            hf_fieldset **out, void *h_stage, size_t h_stage_bytes, int lanes) {
+    return fieldset_create_impl(ctx, n, R, flags, st, out, h_stage, h_stage_bytes, lanes);
 }
 
 static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags, cudaStream_t mem_stream,
-                                      hf_fieldset **out) {
+                                      hf_fieldset **out, void *h_stage_ext, size_t h_stage_ext_bytes, int lanes) {
     if (!ctx || !out) return fail(HF_EINVAL, "hf_fieldset_create: NULL argument");
     *out = nullptr;
     if (!hf::supported_n(n)) return fail(HF_EUNSUPPORTED, "hf_fieldset_create: N=%d not supported", n);
@@ -1021,6 +1026,7 @@ static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags,
         const char *ev = getenv("HF_LANES");
         const Tune &t = ctx->tune[tune_slot(n)];
         fs->lanes = ev ? ((atoi(ev) == 2) ? 2 : 1) : (t.set && t.lanes == 2 ? 2 : 1);
+        if (lanes == 1 || lanes == 2) fs->lanes = lanes;
     }
     const size_t n3 = (size_t)n * n * n;
     const size_t data_b = (size_t)R * nf * n3 * sizeof(float);
@@ -1040,24 +1046,27 @@ static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags,
         return mem_stream ? hf::dmalloc_async(p, b, mem_stream) : hf::dmalloc(p, b);
     };
     cudaError_t e = dalloc((void **)&fs->data, data_b);
-    for (int l = 0; l < 2; ++l) {
-        if (e == cudaSuccess && l < fs->lanes) e = dalloc((void **)&fs->scratch[l], scr_b);
-
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&fs->lane[l], cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fs->join[l], cudaEventDisableTiming);
+    for (int l = 0; l < fs->lanes; ++l) {
+        if (e == cudaSuccess) e = dalloc((void **)&fs->scratch[l], scr_b);
+        // the pipelines' own streams and events only with two of them
+        if (e == cudaSuccess && fs->lanes == 2) e = cudaStreamCreateWithFlags(&fs->lane[l], cudaStreamNonBlocking);
+        if (e == cudaSuccess && fs->lanes == 2) e = cudaEventCreateWithFlags(&fs->join[l], cudaEventDisableTiming);
     }
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fs->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess && fs->lanes == 2) e = cudaEventCreateWithFlags(&fs->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = dalloc((void **)&fs->d_rot9, (size_t)R * 9 * sizeof(float));
     if (e == cudaSuccess) e = dalloc((void **)&fs->d_quat, (size_t)R * 4 * sizeof(double));
     if (e == cudaSuccess) e = dalloc((void **)&fs->d_nbr, (size_t)R * 6 * sizeof(int));
     if (e == cudaSuccess) e = dalloc((void **)&fs->d_P, (size_t)R * 18 * sizeof(float));
     if (e == cudaSuccess) e = dalloc((void **)&fs->d_P64, (size_t)R * 18 * sizeof(double));
     if (e == cudaSuccess) {
-        if (mem_stream) {
+        if (h_stage_ext && h_stage_ext_bytes >= fs->stage_bytes) {
+            fs->h_stage = h_stage_ext;  // the caller's pinned buffer
+        } else if (mem_stream) {
             fs->pageable_stage.resize(fs->stage_bytes + 64);
             fs->h_stage = fs->pageable_stage.data();
         } else {
             e = hf::hmalloc(&fs->h_stage, fs->stage_bytes);
+            fs->stage_owned_pinned = e == cudaSuccess;
         }
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fs->stage_done, cudaEventDisableTiming);
@@ -1108,7 +1117,7 @@ extern "C" void hf_fieldset_release(hf_fieldset *fs) {
     dfree(fs->d_nbr);
     dfree(fs->d_P);
     dfree(fs->d_P64);
-    if (fs->h_stage && !fs->mem_stream) cudaFreeHost(fs->h_stage);
+    if (fs->stage_owned_pinned) cudaFreeHost(fs->h_stage);
     if (fs->stage_done) cudaEventDestroy(fs->stage_done);
     uncharge(fs->ctx, fs->bytes);
     hf_ctx *c = fs->ctx;

@@ -275,9 +275,13 @@ hf_status hf_set_launch(hf_ctx *ctx, const hf_part *s1, const hf_part *s2, hf_fi
                         const float *d_rot9, const int *d_nbr, const float *d_P, const double *d_P64,
                         cudaStream_t st);
 // a field set whose device memory is allocated and freed in stream order on
-// `st` (no device-wide synchronisation on create or release)
+// `st` (no device-wide synchronisation on create or release); h_stage: a
+// caller-owned pinned buffer for its uploads (used if at least R * 308 bytes;
+// the caller keeps it unused by others until the set's uploads are done),
+// else pageable staging; lanes: 1 or 2 pipelines, 0 for the context's choice
 hf_status hf_fieldset_create_stream_ordered(hf_ctx *ctx, int n, int R, unsigned flags, cudaStream_t st,
-                                            hf_fieldset **out);
+                                            hf_fieldset **out, void *h_stage = nullptr, size_t h_stage_bytes = 0,
+                                            int lanes = 0);
 // checkpoints (hf_api.cu): a computed field set as NPY arrays on an open
 // file, and back (device memory stream-ordered on mem_stream if non-null);
 // the NPY array helpers and the file tag for the server's session files

@@ -211,6 +211,7 @@ struct MetricsLog {
 };
 
 constexpr size_t kLatRing = 1u << 20;
+constexpr size_t kStageBytes = (size_t)4 << 20;  // a build's uploads: 308 bytes per rotation
 constexpr int kMaxSessions = 4096;
 constexpr double kSlowQueryUs = 500.0, kSlowCallUs = 1000.0;
 constexpr double kIdleMs = 20.0;  // a chunk unqueried this long is idle (first to evict)
@@ -232,6 +233,7 @@ struct hf_server {
     std::atomic<int> nsessions{0};
     std::vector<cudaStream_t> streams;
     std::vector<int> stream_busy;
+    std::vector<void *> stage;  // per build stream: pinned staging of a build's uploads (kStageBytes)
     int64_t next_id = 1;
     bool stop = false;
     std::thread sched;
@@ -429,7 +431,11 @@ static void scheduler(hf_server *s) {
         // allocate and launch outside the mutex
         hf_fieldset *fs = nullptr;
         double a = now_ms();
-        hf_status st = hf_fieldset_create_stream_ordered(s->ctx, n, cand->R, cand->req->flags, s->streams[si], &fs);
+        // one pipeline per build (the server runs builds side by side), its
+        // uploads staged in the stream's pinned buffer: a stream takes its
+        // next build only after the last one has completed
+        hf_status st = hf_fieldset_create_stream_ordered(s->ctx, n, cand->R, cand->req->flags, s->streams[si], &fs,
+                                                         s->stage[si], kStageBytes, 1);
         trace_call(s, 0, a, now_ms());
         if (st == HF_EBUDGET) {
             hf_part_drop(p1);
@@ -549,6 +555,9 @@ extern "C" hf_status hf_server_create(hf_ctx *ctx, int max_inflight, int query_l
         e = cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, lo);
         s->streams.push_back(st);
         s->stream_busy.push_back(0);
+        void *h = nullptr;
+        if (e == cudaSuccess) e = cudaHostAlloc(&h, kStageBytes, cudaHostAllocDefault);
+        s->stage.push_back(h);
     }
     s->lanes.resize(query_lanes);
     for (int i = 0; i < query_lanes && e == cudaSuccess; ++i) {
@@ -594,6 +603,8 @@ extern "C" void hf_server_destroy(hf_server *s) {
     }
     for (auto st : s->streams)
         if (st) cudaStreamDestroy(st);
+    for (auto h : s->stage)
+        if (h) cudaFreeHost(h);
     for (auto &L : s->lanes) {
         if (L.st) cudaStreamDestroy(L.st);
         if (L.h_out) cudaFreeHost(L.h_out);
@@ -967,6 +978,16 @@ extern "C" hf_status hf_server_stats_get(hf_server *s, hf_server_stats *out) {
             for (int c = 0; c < cur->req->nchunks; ++c) resident += cur->get(c) ? 1 : 0;
     }
     out->chunks_resident = resident;
+    cudaMemPool_t pool = nullptr;
+    out->pool_reserved_bytes = out->pool_reserved_high = 0;
+    if (cudaDeviceGetDefaultMemPool(&pool, s->device) == cudaSuccess) {
+        unsigned long long v = 0;
+        if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &v) == cudaSuccess)
+            out->pool_reserved_bytes = (size_t)v;
+        if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemHigh, &v) == cudaSuccess)
+            out->pool_reserved_high = (size_t)v;
+    }
+    (void)cudaGetLastError();
     return HF_OK;
 }
 
@@ -1015,11 +1036,12 @@ void log_line(hf_server *s, MetricsLog &L) {
             ", \"submitted\": %lld, \"completed\": %lld, \"failed\": %lld, \"rejected\": %lld, "
             "\"superseded\": %lld, \"evicted\": %lld, \"queries\": %lld, \"rotations_completed\": %lld, "
             "\"queued\": %d, \"running\": %d, \"sessions\": %d, \"reserved_bytes\": %zu, \"budget_bytes\": %zu, "
-            "\"chunks_submitted\": %lld, \"chunks_completed\": %lld, \"chunks_resident\": %d",
+            "\"chunks_submitted\": %lld, \"chunks_completed\": %lld, \"chunks_resident\": %d, "
+            "\"pool_reserved_bytes\": %zu",
             (long long)st.submitted, (long long)st.completed, (long long)st.failed, (long long)st.rejected,
             (long long)st.superseded, (long long)st.evicted, (long long)st.queries, (long long)st.rotations_completed,
             st.queued, st.running, st.sessions, st.reserved_bytes, st.budget_bytes, (long long)st.chunks_submitted,
-            (long long)st.chunks_completed, st.chunks_resident);
+            (long long)st.chunks_completed, st.chunks_resident, st.pool_reserved_bytes);
     const double qs[3] = {0.5, 0.99, 0.999};
     double v[3];
     uint64_t n;
