@@ -569,7 +569,8 @@ hf_status hf_tune_tiles(hf_ctx *ctx, int n, int set, int *tile_b, int *tile_c);
 /* Pipelines a field-set compute at grid n runs (1, or 2 alternating its
  * rotation chunks over two streams so that passes of neighbouring chunks
  * overlap on the device; twice the intermediates).  set != 0 stores *lanes,
- * else reads it.  The HF_LANES environment variable, when set, overrides it.
+ * else reads it.  The HF_LANES environment variable, when set, overrides it;
+ * HF_SPECTRAL sets run one pipeline unless that variable says otherwise.
  * Errors: HF_EINVAL, HF_EUNSUPPORTED. */
 hf_status hf_tune_lanes(hf_ctx *ctx, int n, int set, int *lanes);
 

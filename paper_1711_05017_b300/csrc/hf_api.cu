@@ -1026,6 +1026,10 @@ static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags,
         const char *ev = getenv("HF_LANES");
         const Tune &t = ctx->tune[tune_slot(n)];
         fs->lanes = ev ? ((atoi(ev) == 2) ? 2 : 1) : (t.set && t.lanes == 2 ? 2 : 1);
+        // the tuner times the spatial route; on the spectral route pass B reads
+        // the table through the texture units, and two pipelines' gathers
+        // contend (at os = 2 the build ran at half the rate)
+        if (!ev && (flags & HF_SPECTRAL)) fs->lanes = 1;
         if (lanes == 1 || lanes == 2) fs->lanes = lanes;
     }
     const size_t n3 = (size_t)n * n * n;
