@@ -1227,7 +1227,9 @@ __device__ __forceinline__ void passC_body(const float2 *__restrict__ Y1, const 
     const float2 *s1 = Y1 + ((size_t)r * N + z) * N * H;
     const size_t fo = (size_t)r * out.rot_stride + (size_t)z * N * N;
     if constexpr (BK) {
-        static_assert(!TQ && !COH && YU == 1 && !PF, "the bulk-staged form of the E/F kernel");
+        // (inside the one-launch queue, COH: the thread that issues the copies
+        // has acquired the producers' release and fenced the async proxy)
+        static_assert(!TQ && YU == 1 && !PF, "the bulk-staged form of the E/F kernel");
         static_assert((sizeof(float2) * N * H) % 16 == 0, "whole 16-byte units");
         // the mbarrier sits after the twiddles (8-byte aligned)
         unsigned long long *mbar = reinterpret_cast<unsigned long long *>(twN + N);
@@ -1743,7 +1745,8 @@ __device__ __forceinline__ int ld_relaxed_s32(const int *p) {
 constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
 constexpr size_t kPersistSmem =
     cmax(cmax(cmax(PassA<64>::smem, PassA<96>::smem), cmax(PassA<128>::smem, PassB<64>::smem)),
-         cmax(cmax(PassB<96>::smem, PassB<128>::smem), cmax(PassC<64>::smem, cmax(PassC<96>::smem, PassC<128>::smem))));
+         cmax(cmax(PassB<96>::smem, PassB<128>::smem),
+              cmax(passC_bulk_smem<64>(), cmax(passC_bulk_smem<96>(), passC_bulk_smem<128>()))));
 
 template <int N>
 __device__ __forceinline__ void persist_item(const PersistSeg &g, int local) {
@@ -1755,7 +1758,8 @@ __device__ __forceinline__ void persist_item(const PersistSeg &g, int local) {
         passB_body<N, 0, true>(g.X1, g.R1hat, g.Y1, g.Y2, 0.f, SpecSrc{nullptr, 0, 0}, nullptr, local % BT,
                                local / BT);
     } else {
-        passC_body<N, false, kPersistNT, true>(g.Y1, g.Y2, g.out, nullptr, 0, local % N, local / N);
+        passC_body<N, false, kPersistNT, true, 0, 1, false, true>(g.Y1, g.Y2, g.out, nullptr, 0, local % N,
+                                                                 local / N);
     }
 }
 
@@ -1785,6 +1789,10 @@ __global__ void __launch_bounds__(kPersistNT, 2)
                     __nanosleep(256);
                 }
             }
+            // pass C items read their producers' output by bulk copies (the
+            // async proxy) that this thread issues: order them after the
+            // generic-proxy writes it has just acquired
+            asm volatile("fence.proxy.async.global;" ::: "memory");
         }
         s_item = it;
         s_seg = sg;
