@@ -559,9 +559,9 @@ hf_status hf_tune_get(const hf_ctx *ctx, int n, int *chunk, int *pencil, double 
  * 3 = that and an L2 prefetch of the block's third input plane, 4 = that
  * and two y-stage items' loads in flight per thread; 5 = each input plane
  * brought into shared memory by bulk copies, the next plane's rows copied as
- * the x transform frees them (256 threads at N = 128); 5 is the shape used
- * at N = 64, 96, 128 when none was chosen, 0 at other N.  Other than 0 only
- * for N = 64, 96, 128.
+ * the x transform frees them (256 threads at N = 128), and at N = 128 only
+ * 6 = that with 512 threads; 5 is the shape used at N = 64, 96, 128 when
+ * none was chosen, 0 at other N.  Other than 0 only for N = 64, 96, 128.
  * set != 0 stores *tile_b / *tile_c (the
  * fields do not change, only their speed), else reads them.  Errors:
  * HF_EINVAL, HF_EUNSUPPORTED. */

@@ -1677,7 +1677,7 @@ extern "C" hf_status hf_tune_tiles(hf_ctx *ctx, int n, int set, int *tile_b, int
     if (!hf::supported_n(n)) return fail(HF_EUNSUPPORTED, "hf_tune_tiles: N=%d not supported", n);
     Tune &t = ctx->tune[tune_slot(n)];
     if (set) {
-        if (*tile_b < 0 || *tile_b > 1 || *tile_c < 0 || *tile_c > 5 || (*tile_c >= 2 && *tile_c <= 4 && n != 128) ||
+        if (*tile_b < 0 || *tile_b > 1 || *tile_c < 0 || *tile_c > 6 || (((*tile_c >= 2 && *tile_c <= 4) || *tile_c == 6) && n != 128) ||
             ((*tile_b || *tile_c) && (n < 64 || n > 128)))
             return fail(HF_EINVAL, "hf_tune_tiles: tile_b %d, tile_c %d at N=%d", *tile_b, *tile_c, n);
         if (!t.set) {  // keep the built-in chunk and pipeline
@@ -1738,7 +1738,7 @@ int tune_pass_c_rows(int n, int tile_c) {
     return n == 96 ? 48 : (n >= 64 ? 32 : 16);
 }
 int tune_pass_c_threads(int n, int tile_c) {
-    if (tile_c >= 2 && n == 128) return 256;
+    if (tile_c >= 2 && tile_c <= 5 && n == 128) return 256;
     return n >= 128 ? 512 : (n >= 64 ? 256 : 128);
 }
 
@@ -1750,7 +1750,7 @@ std::string tune_json_line(const std::string &dev, int n, const Tune &t, const s
              "\"passC_threads\": %d, \"passC_staging\": \"%s\", \"rot_per_s\": %.6g}",
              dev.c_str(), n, t.chunk, t.pencil ? "pencil" : "slab", t.tile_b, t.tile_c, t.lanes, tune_radix(n),
              tune_pass_b_columns(n, t.tile_b), tune_pass_c_rows(n, t.tile_c), tune_pass_c_threads(n, t.tile_c),
-             t.tile_c == 5 ? "bulk" : "loads", t.rot_per_s);
+             t.tile_c >= 5 ? "bulk" : "loads", t.rot_per_s);
     std::string l = buf;
     if (!cands.empty()) {  // every timed candidate: [chunk, pencil, tile_b, tile_c, lanes, rot_per_s]
         l.pop_back();
@@ -1928,8 +1928,8 @@ extern "C" hf_status hf_autotune(hf_ctx *ctx, int n, const char *cache_path, int
         // compiled candidate (tile 0 is the one timed above)
         if (best.set && !best.pencil && n >= 64 && n <= 128) {
             for (int tb = 0; tb <= 1; ++tb)
-                for (int tc = 0; tc <= 5; ++tc) {
-                    if ((tb == 0 && tc == 0) || (n != 128 && tc >= 2 && tc <= 4)) continue;
+                for (int tc = 0; tc <= 6; ++tc) {
+                    if ((tb == 0 && tc == 0) || (n != 128 && ((tc >= 2 && tc <= 4) || tc == 6))) continue;
                     Tune &t = ctx->tune[tune_slot(n)];
                     t = best;
                     t.tile_b = tb;

@@ -1586,6 +1586,7 @@ static cudaError_t set_smem_attrs() {
             if ((e = cudaFuncSetAttribute(passC_kernel<N, false, 0, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassC<N, 0, 256>::smem))) return e;
             if ((e = cudaFuncSetAttribute(passC_kernel<N, false, 0, 256, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassC<N, 0, 256>::smem))) return e;
             if ((e = cudaFuncSetAttribute(passC_kernel<N, false, 0, 256, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassC<N, 0, 256>::smem))) return e;
+            if ((e = cudaFuncSetAttribute(passC_kernel<N, false, 0, 0, 1, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)passC_bulk_smem<N>()))) return e;
         }
     }
     if ((e = cudaFuncSetAttribute(passC_kernel<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassC<N>::smem))) return e;
@@ -1927,6 +1928,8 @@ cudaError_t run_passC(int n, const float2 *Y1, const float2 *Y2, FieldPtrs out, 
             case 128: return launch_passC<128, 0, 256, 1, false, true>(Y1, Y2, out, nrot, st);
             default: break;
         }
+    } else if (tile == 6 && n == 128) {  // planes staged by bulk copies, 512 threads per CTA
+        return launch_passC<128, 0, 0, 1, false, true>(Y1, Y2, out, nrot, st);
     }
     HF_DISPATCH(n, launch_passC<NN>(Y1, Y2, out, nrot, st));
 }

@@ -226,7 +226,7 @@ def test_tile_candidates_give_the_same_fields(hf, n):
     q = synth.random_quaternions(61, 10).astype(np.float32)
     base = all_fields(plain(hf, ctx, pair, q, hf.HF_E | hf.HF_F), 10, 4)
     for tb in (0, 1):
-        for tc in ((0, 1, 2, 3, 4, 5) if n == 128 else (0, 1, 5)):
+        for tc in ((0, 1, 2, 3, 4, 5, 6) if n == 128 else (0, 1, 5)):
             ctx.tune_tiles(n, (tb, tc))
             assert ctx.tune_tiles(n) == (tb, tc)
             got = all_fields(plain(hf, ctx, pair, q, hf.HF_E | hf.HF_F), 10, 4)
