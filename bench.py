@@ -204,6 +204,7 @@ def tune_is_pencil(ctx, n):
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_1711_05017_b300 as hf
+    from paper_1711_05017_b300 import _binding as hf_binding
     from paper_1711_05017_b300 import build
 
     build.build()
@@ -482,6 +483,8 @@ def run_ours(args, rank, world, local_rank):
             "two_pipelines": two_lanes,
             "cpu_baseline": cpu,
             "clocks": clk.summary(),
+            # bulk-copy waits that gave up in this run (each would have left its block's output invalid)
+            "bulk_wait_timeouts": int(hf_binding.lib().hf_bulk_timeouts(0)),
             "batch": batch,
             "precision": precision,
             "next_rows": spectral,

@@ -579,6 +579,17 @@ hf_status hf_tune_lanes(hf_ctx *ctx, int n, int set, int *lanes);
  * output: the field set computed with it is invalid); -1 if it cannot be read.
  * Synchronous (reads device memory). */
 int hf_tc_timeouts(int reset);
+/* Number of waits for bulk copies into shared memory (the bulk-staged pass
+ * C) that gave up since the last reset; the blocks behind them wrote invalid
+ * output.  -1 if it cannot be read.  Synchronous. */
+int hf_bulk_timeouts(int reset);
+/* Runs one block that bulk-copies 4 KB into shared memory and waits for it
+ * with the kernels' bounded wait.  plant = 0: HF_OK if the data arrived and
+ * no wait gave up.  plant != 0: the mbarrier expects 16 bytes more than the
+ * copy brings, so the wait runs out (about 0.4 s) and counts itself: returns
+ * HF_ETIMEOUT with *timeouts the waits that gave up (the context stays
+ * usable; reset the counter afterwards).  Errors: HF_EINVAL, HF_ECUDA. */
+hf_status hf_bulk_selftest(int device, int plant, int *timeouts);
 
 /* ---- per-kernel timing (CUDA events on the launching stream) ----
  * While enabled, every kernel launch the context's calls make is bracketed by

@@ -104,6 +104,8 @@ SIGNATURES = {
     "hf_tune_tiles": (_i, [_vp, _i, _i, _ip, _ip]),
     "hf_tune_lanes": (_i, [_vp, _i, _i, _ip]),
     "hf_tc_timeouts": (_i, [_i]),
+    "hf_bulk_timeouts": (_i, [_i]),
+    "hf_bulk_selftest": (_i, [_i, _i, _ip]),
     "hf_part_spectral": (_i, [_vp, _i, _vp]),
     "hf_part_spectral_os": (_i, [_vp]),
     "hf_lowpass_query": (_i, [_vp, _vp, _i, _fp, _fp, _fp]),

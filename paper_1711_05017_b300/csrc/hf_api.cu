@@ -338,6 +338,30 @@ static void ctx_free(hf_ctx *c) {
 extern "C" size_t hf_ctx_budget_bytes(const hf_ctx *c) { return c ? c->budget : 0; }
 
 extern "C" int hf_tc_timeouts(int reset) { return hf::tc_timeouts(reset != 0); }
+extern "C" int hf_bulk_timeouts(int reset) { return hf::bulk_timeouts(reset != 0); }
+
+extern "C" hf_status hf_bulk_selftest(int device, int plant, int *timeouts) {
+    if (!timeouts) return fail(HF_EINVAL, "hf_bulk_selftest: timeouts is NULL");
+    CU(cudaSetDevice(device));
+    const int before = hf::bulk_timeouts(false);
+    if (before < 0) return fail(HF_ECUDA, "hf_bulk_selftest: cannot read the counter");
+    const int nb = hf::bulk_selftest_bytes();
+    std::vector<unsigned char> h(nb), back(nb);
+    for (int i = 0; i < nb; ++i) h[i] = (unsigned char)(i * 37 + 11);
+    void *d = nullptr;
+    CU(hf::dmalloc(&d, 2 * (size_t)nb));
+    cudaError_t e = cudaMemcpy(d, h.data(), nb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset((char *)d + nb, 0, nb);
+    if (e == cudaSuccess) e = hf::run_bulk_selftest(d, (char *)d + nb, plant, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(back.data(), (char *)d + nb, nb, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(HF_ECUDA, "hf_bulk_selftest: %s", cudaGetErrorString(e));
+    *timeouts = hf::bulk_timeouts(false) - before;
+    if (!plant && (*timeouts != 0 || back != h)) return fail(HF_ECUDA, "hf_bulk_selftest: the copy did not arrive");
+    return plant ? (*timeouts > 0 ? HF_ETIMEOUT : fail(HF_ECUDA, "hf_bulk_selftest: the planted wait completed"))
+                 : HF_OK;
+}
 
 extern "C" size_t hf_ctx_reserved_bytes(const hf_ctx *c) {
     if (!c) return 0;

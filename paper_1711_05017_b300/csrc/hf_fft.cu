@@ -1983,4 +1983,44 @@ cudaError_t run_unpermute(int n, const float2 *spec, float2 *out, cudaStream_t s
     HF_DISPATCH_ALL(n, launch_unpermute<NN>(spec, out, st));
 }
 
+// ------------------------------------------------- bulk-copy wait checks
+// The bulk-staged kernels count a wait for their copies that gave up in
+// g_bulk_timeouts.  The self test runs the same copy and bounded wait in one
+// block on a 4 KB buffer: plain, the buffer comes back unchanged; planted,
+// the mbarrier expects 16 bytes more than the copy brings, so the wait runs
+// out (twice its bound) and counts itself, with the copy itself complete.
+int bulk_timeouts(bool reset) {
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_bulk_timeouts, sizeof v) != cudaSuccess) return -1;
+    if (reset) {
+        const int z = 0;
+        if (cudaMemcpyToSymbol(g_bulk_timeouts, &z, sizeof z) != cudaSuccess) return -1;
+    }
+    return v;
+}
+
+constexpr int kSelfTestBytes = 4096;
+
+__global__ void bulk_selftest_kernel(const float4 *__restrict__ src, float4 *__restrict__ dst, int plant) {
+    __shared__ __align__(16) float4 buf[kSelfTestBytes / 16];
+    __shared__ __align__(8) unsigned long long mbar;
+    if (threadIdx.x == 0) {
+        mbar_init1(&mbar);
+        mbar_expect(&mbar, kSelfTestBytes + (plant ? 16u : 0u));
+        fence_proxy_async_smem();
+        bulk_g2s(buf, src, kSelfTestBytes, &mbar);
+    }
+    __syncthreads();
+    mbar_wait_bounded(&mbar, 0);
+    for (int i = threadIdx.x; i < kSelfTestBytes / 16; i += blockDim.x) dst[i] = buf[i];
+}
+
+cudaError_t run_bulk_selftest(const void *src, void *dst, int plant, cudaStream_t st) {
+    if (((uintptr_t)src | (uintptr_t)dst) % 16) return cudaErrorMisalignedAddress;
+    bulk_selftest_kernel<<<1, 128, 0, st>>>(reinterpret_cast<const float4 *>(src), reinterpret_cast<float4 *>(dst),
+                                           plant);
+    return cudaGetLastError();
+}
+int bulk_selftest_bytes() { return kSelfTestBytes; }
+
 }  // namespace hf

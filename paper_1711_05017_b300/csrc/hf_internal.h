@@ -168,6 +168,11 @@ cudaError_t set_tc_attrs();
 // CTAs of the tensor-core stages whose bounded wait for their MMAs gave up
 // (their outputs are invalid); -1 if the counter cannot be read
 int tc_timeouts(bool reset);
+// hf_fft.cu: waits for bulk copies that gave up, and the one-block self test
+// of that bounded wait (plant: the wait cannot complete)
+int bulk_timeouts(bool reset);
+cudaError_t run_bulk_selftest(const void *src, void *dst, int plant, cudaStream_t st);
+int bulk_selftest_bytes();
 cudaError_t run_yinv(int n, const float2 *Y1, const float2 *Y2, float2 *ZS, float2 *ZGy, float2 *ZGz, int nrot,
                      cudaStream_t st);
 cudaError_t run_xinv(int n, const float2 *ZS, const float2 *ZGy, const float2 *ZGz, FieldPtrs out, int nrot,

@@ -194,3 +194,21 @@ def test_each_failed_allocation_is_reported_and_leaves_no_trace(hf, env, name, t
         torch.cuda.synchronize()
         assert ctx.reserved_bytes() == base, (k, ctx.reserved_bytes(), base)
         assert np.array_equal(op(), ref), k
+
+
+def test_bulk_copy_wait_is_bounded_and_reported(hf, env):
+    """The bounded wait of the bulk-staged kernels, in one block: a wait
+    that cannot complete (the mbarrier expects more bytes than the copy
+    brings) gives up after its bound, counts itself and returns; the device
+    stays usable and the next build is exact."""
+    import ctypes
+    from paper_1711_05017_b300 import _binding as B
+    L = B.lib()
+    t = ctypes.c_int(-1)
+    assert L.hf_bulk_selftest(0, 0, ctypes.byref(t)) == B.HF_OK and t.value == 0
+    ref = op_fieldset(hf, env)
+    assert L.hf_bulk_selftest(0, 1, ctypes.byref(t)) == B.HF_ETIMEOUT and t.value == 1
+    assert L.hf_bulk_timeouts(1) >= 1
+    assert L.hf_bulk_timeouts(0) == 0
+    assert np.array_equal(op_fieldset(hf, env), ref)
+    assert L.hf_bulk_timeouts(0) == 0

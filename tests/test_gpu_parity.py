@@ -443,3 +443,10 @@ def test_fieldset_256_matches_single_rotation_path(hf, ctx):
             a, b = host(fs.get(i, f)), host(out[f])
             assert rel_err(a, b) <= 1e-6, (i, f)
     assert np.isfinite(host(fs.get(3, 4))).all()
+
+
+def test_no_bulk_copy_wait_gave_up(hf):
+    """Every bulk-staged pass C block of the tests above saw its planes
+    arrive: no bounded wait ran out."""
+    from paper_1711_05017_b300 import _binding as B
+    assert B.lib().hf_bulk_timeouts(0) == 0
