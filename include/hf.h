@@ -560,8 +560,10 @@ hf_status hf_tune_get(const hf_ctx *ctx, int n, int *chunk, int *pencil, double 
  * and two y-stage items' loads in flight per thread; 5 = each input plane
  * brought into shared memory by bulk copies, the next plane's rows copied as
  * the x transform frees them (256 threads at N = 128), and at N = 128 only
- * 6 = that with 512 threads; 5 is the shape used at N = 64, 96, 128 when
- * none was chosen, 0 at other N.  Other than 0 only for N = 64, 96, 128.
+ * 6 = that with 512 threads and 7 = that with the x inverse's digits in the
+ * other order (16 x 8: the same fields to rounding, not bit for bit); 5 is
+ * the shape used at N = 64, 96, 128 when none was chosen, 0 at other N.
+ * Other than 0 only for N = 64, 96, 128.
  * set != 0 stores *tile_b / *tile_c (the
  * fields do not change, only their speed), else reads them.  Errors:
  * HF_EINVAL, HF_EUNSUPPORTED. */

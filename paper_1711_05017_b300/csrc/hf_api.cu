@@ -1701,7 +1701,7 @@ extern "C" hf_status hf_tune_tiles(hf_ctx *ctx, int n, int set, int *tile_b, int
     if (!hf::supported_n(n)) return fail(HF_EUNSUPPORTED, "hf_tune_tiles: N=%d not supported", n);
     Tune &t = ctx->tune[tune_slot(n)];
     if (set) {
-        if (*tile_b < 0 || *tile_b > 1 || *tile_c < 0 || *tile_c > 6 || (((*tile_c >= 2 && *tile_c <= 4) || *tile_c == 6) && n != 128) ||
+        if (*tile_b < 0 || *tile_b > 1 || *tile_c < 0 || *tile_c > 7 || (((*tile_c >= 2 && *tile_c <= 4) || *tile_c >= 6) && n != 128) ||
             ((*tile_b || *tile_c) && (n < 64 || n > 128)))
             return fail(HF_EINVAL, "hf_tune_tiles: tile_b %d, tile_c %d at N=%d", *tile_b, *tile_c, n);
         if (!t.set) {  // keep the built-in chunk and pipeline
@@ -1753,8 +1753,13 @@ std::string tune_device_key(int device) {
 //     "rot_per_s": 33400},
 //    ...]}
 // It is read back by the key scan below, which accepts the lines it writes.
-const char *tune_radix(int n) {
-    return n == 32 ? "8x4" : n == 64 ? "8x8" : n == 96 ? "12x8" : n == 128 ? "16x8" : "16x16";
+// the transforms' digit orders: the y and z transforms (fixed: they set the
+// intermediates' slot order) and pass C's x inverse (tile 7 at 128^3: 16 x 8)
+std::string tune_radix(int n, int tile_c) {
+    const char *yz = n == 32 ? "8x4" : n == 64 ? "8x8" : n == 96 ? "12x8" : n == 128 ? "16x8" : "16x16";
+    const char *x = n == 32 ? "4x8" : n == 64 ? "8x8" : n == 96 ? "8x12" : n == 128 ? (tile_c == 7 ? "16x8" : "8x16")
+                                                                                      : "16x16";
+    return std::string("yz ") + yz + ", x inverse " + x;
 }
 int tune_pass_b_columns(int n, int tile_b) { return tile_b == 1 && n <= 128 ? 16 : (n >= 256 ? 16 : 32); }
 int tune_pass_c_rows(int n, int tile_c) {
@@ -1762,7 +1767,7 @@ int tune_pass_c_rows(int n, int tile_c) {
     return n == 96 ? 48 : (n >= 64 ? 32 : 16);
 }
 int tune_pass_c_threads(int n, int tile_c) {
-    if (tile_c >= 2 && tile_c <= 5 && n == 128) return 256;
+    if (tile_c >= 2 && tile_c != 6 && n == 128) return 256;
     return n >= 128 ? 512 : (n >= 64 ? 256 : 128);
 }
 
@@ -1772,7 +1777,8 @@ std::string tune_json_line(const std::string &dev, int n, const Tune &t, const s
              "{\"device\": \"%s\", \"n\": %d, \"chunk\": %d, \"pipeline\": \"%s\", \"tile_b\": %d, \"tile_c\": %d, "
              "\"lanes\": %d, \"radix\": \"%s\", \"passB_columns_per_cta\": %d, \"passC_rows_per_x_batch\": %d, "
              "\"passC_threads\": %d, \"passC_staging\": \"%s\", \"rot_per_s\": %.6g}",
-             dev.c_str(), n, t.chunk, t.pencil ? "pencil" : "slab", t.tile_b, t.tile_c, t.lanes, tune_radix(n),
+             dev.c_str(), n, t.chunk, t.pencil ? "pencil" : "slab", t.tile_b, t.tile_c, t.lanes,
+             tune_radix(n, t.tile_c).c_str(),
              tune_pass_b_columns(n, t.tile_b), tune_pass_c_rows(n, t.tile_c), tune_pass_c_threads(n, t.tile_c),
              t.tile_c >= 5 ? "bulk" : "loads", t.rot_per_s);
     std::string l = buf;
@@ -1952,8 +1958,8 @@ extern "C" hf_status hf_autotune(hf_ctx *ctx, int n, const char *cache_path, int
         // compiled candidate (tile 0 is the one timed above)
         if (best.set && !best.pencil && n >= 64 && n <= 128) {
             for (int tb = 0; tb <= 1; ++tb)
-                for (int tc = 0; tc <= 6; ++tc) {
-                    if ((tb == 0 && tc == 0) || (n != 128 && ((tc >= 2 && tc <= 4) || tc == 6))) continue;
+                for (int tc = 0; tc <= 7; ++tc) {
+                    if ((tb == 0 && tc == 0) || (n != 128 && ((tc >= 2 && tc <= 4) || tc >= 6))) continue;
                     Tune &t = ctx->tune[tune_slot(n)];
                     t = best;
                     t.tile_b = tb;

@@ -917,16 +917,18 @@ struct NoHook {
 };
 
 template <int N, int PAIR, int PW, int RB, int TP, int NT, int ROWS, bool CTW = true, bool KEEP0 = false,
-          bool KEEP1 = false, class Hook = NoHook>
+          bool KEEP1 = false, class Hook = NoHook, int XR1 = 0>
 __device__ __forceinline__ void x_pass(const float2 *planeA, const float2 *planeB, int colA, int colB,
                                        float2 *Tb, const float2 *twN,
                                        float *__restrict__ out0, float *__restrict__ out1,
                                        const TorqueCorr *tc = nullptr, const Hook &hook = Hook()) {
-    // N = R1 R2 with the longer digit second, so that stage 2 runs with lanes
-    // along it: its reads of the row buffer are contiguous and its outputs
-    // (x = R2 n1 + n2) go straight to HBM as full 32-byte sectors
-    constexpr int R1 = Fact<N>::R1 < Fact<N>::R2 ? Fact<N>::R1 : Fact<N>::R2;
+    // N = R1 R2, by default with the longer digit second, so that stage 2
+    // runs with lanes along it: its reads of the row buffer are contiguous and
+    // its outputs (x = R2 n1 + n2) go straight to HBM as full 32-byte sectors;
+    // XR1 picks the first digit instead (the autotuner's radix candidate)
+    constexpr int R1 = XR1 ? XR1 : (Fact<N>::R1 < Fact<N>::R2 ? Fact<N>::R1 : Fact<N>::R2);
     constexpr int R2 = N / R1;
+    static_assert(N % R1 == 0 && R2 >= 8, "whole digits; stage 2 writes at least 32-byte runs");
 #pragma unroll 1
     for (int y0 = 0; y0 < ROWS; y0 += RB) {
         // stage 1 (inverse), items (row, k1): Tb[row][R2 k1 + n2] from Z[k1 + R1 k2]
@@ -1212,7 +1214,7 @@ struct RowRefill {
 // bring each input plane into shared memory by bulk copies, the next plane's
 // rows issued as the x pass frees them (one mbarrier, one phase per plane)
 template <int N, bool TQ, int NT = PassC<N>::NT, bool COH = false, int RBO = 0, int YU = 1, bool PF = false,
-          bool BK = false>
+          bool BK = false, int XR1 = 0>
 __device__ __forceinline__ void passC_body(const float2 *__restrict__ Y1, const float2 *__restrict__ Y2,
                                            const FieldPtrs &out, const float2 *__restrict__ YT, size_t yt_stride,
                                            unsigned zu, unsigned ru) {
@@ -1243,17 +1245,17 @@ __device__ __forceinline__ void passC_body(const float2 *__restrict__ Y1, const 
         __syncthreads();
         // E + i Fx; its batches refill the plane with S' (for Gy)
         y_inverse_plane_smem<N, false, true, NT>(plane, twN, mbar, 0);
-        x_pass<N, 0, PW, RB, TP, NT, N, true, false, false>(plane, plane, 0, 0, Tb, twN, out.E + fo, out.Fx + fo,
-                                                            nullptr, RowRefill<N, RB, 1>{plane, s1, mbar});
+        x_pass<N, 0, PW, RB, TP, NT, N, true, false, false, RowRefill<N, RB, 1>, XR1>(
+            plane, plane, 0, 0, Tb, twN, out.E + fo, out.Fx + fo, nullptr, RowRefill<N, RB, 1>{plane, s1, mbar});
         // Fy; its batches refill the plane with Gz'
         y_inverse_plane_smem<N, true, true, NT>(plane, twN, mbar, 1);
-        x_pass<N, 1, PW, RB, TP, NT, HALF, true, false, false>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN,
-                                                               out.Fy + fo, out.Fy + fo + (size_t)HALF * N, nullptr,
-                                                               RowRefill<N, RB, 2>{plane, s2, mbar});
+        x_pass<N, 1, PW, RB, TP, NT, HALF, true, false, false, RowRefill<N, RB, 2>, XR1>(
+            plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, out.Fy + fo, out.Fy + fo + (size_t)HALF * N, nullptr,
+            RowRefill<N, RB, 2>{plane, s2, mbar});
         // Fz
         y_inverse_plane_smem<N, false, true, NT>(plane, twN, mbar, 0);
-        x_pass<N, 1, PW, RB, TP, NT, HALF>(plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, out.Fz + fo,
-                                           out.Fz + fo + (size_t)HALF * N);
+        x_pass<N, 1, PW, RB, TP, NT, HALF, true, false, false, NoHook, XR1>(
+            plane + (size_t)HALF * PW, plane, 0, 0, Tb, twN, out.Fz + fo, out.Fz + fo + (size_t)HALF * N);
         return;
     }
     if constexpr (PF) {
@@ -1287,14 +1289,14 @@ __device__ __forceinline__ void passC_body(const float2 *__restrict__ Y1, const 
     }
 }
 
-template <int N, bool TQ, int RBO = 0, int NTO = 0, int YU = 1, bool PF = false, bool BK = false>
+template <int N, bool TQ, int RBO = 0, int NTO = 0, int YU = 1, bool PF = false, bool BK = false, int XR1 = 0>
 __global__ void __launch_bounds__(PassC<N, RBO, NTO>::NT, PassC<N, RBO, NTO>::MINB) passC_kernel(const float2 *__restrict__ Y1,
                                                                               const float2 *__restrict__ Y2,
                                                                               FieldPtrs out,
                                                                               const float2 *__restrict__ YT,
                                                                               size_t yt_stride) {
-    passC_body<N, TQ, PassC<N, RBO, NTO>::NT, false, RBO, YU, PF, BK>(Y1, Y2, out, YT, yt_stride, blockIdx.x,
-                                                                      blockIdx.y);
+    passC_body<N, TQ, PassC<N, RBO, NTO>::NT, false, RBO, YU, PF, BK, XR1>(Y1, Y2, out, YT, yt_stride, blockIdx.x,
+                                                                           blockIdx.y);
 }
 // dynamic shared memory of the bulk-staged form: the mbarrier after the twiddles
 template <int N, int RBO = 0, int NTO = 0>
@@ -1587,6 +1589,7 @@ static cudaError_t set_smem_attrs() {
             if ((e = cudaFuncSetAttribute(passC_kernel<N, false, 0, 256, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassC<N, 0, 256>::smem))) return e;
             if ((e = cudaFuncSetAttribute(passC_kernel<N, false, 0, 256, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassC<N, 0, 256>::smem))) return e;
             if ((e = cudaFuncSetAttribute(passC_kernel<N, false, 0, 0, 1, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)passC_bulk_smem<N>()))) return e;
+            if ((e = cudaFuncSetAttribute(passC_kernel<N, false, 0, 256, 1, false, true, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)passC_bulk_smem<N, 0, 256>()))) return e;
         }
     }
     if ((e = cudaFuncSetAttribute(passC_kernel<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassC<N>::smem))) return e;
@@ -1642,14 +1645,14 @@ static cudaError_t launch_passB_spectral(const float2 *table, cudaTextureObject_
         nullptr, R1hat, Y1, Y2, 0.f, SpecSrc{table, os * N, os, tex, table_tex_sc(os * N)}, rot9);
     return cudaGetLastError();
 }
-template <int N, int RBO = 0, int NTO = 0, int YU = 1, bool PF = false, bool BK = false>
+template <int N, int RBO = 0, int NTO = 0, int YU = 1, bool PF = false, bool BK = false, int XR1 = 0>
 static cudaError_t launch_passC(const float2 *Y1, const float2 *Y2, FieldPtrs out, int nrot, cudaStream_t st) {
     using PC = PassC<N, RBO, NTO>;
     if constexpr (BK) {
         // the bulk copies read whole planes: 16-byte aligned sources
         if (((uintptr_t)Y1 | (uintptr_t)Y2) % 16) return cudaErrorMisalignedAddress;
     }
-    passC_kernel<N, false, RBO, NTO, YU, PF, BK>
+    passC_kernel<N, false, RBO, NTO, YU, PF, BK, XR1>
         <<<dim3(N, nrot), PC::NT, BK ? passC_bulk_smem<N, RBO, NTO>() : PC::smem, st>>>(Y1, Y2, out, nullptr, 0);
     return cudaGetLastError();
 }
@@ -1930,6 +1933,8 @@ cudaError_t run_passC(int n, const float2 *Y1, const float2 *Y2, FieldPtrs out, 
         }
     } else if (tile == 6 && n == 128) {  // planes staged by bulk copies, 512 threads per CTA
         return launch_passC<128, 0, 0, 1, false, true>(Y1, Y2, out, nrot, st);
+    } else if (tile == 7 && n == 128) {  // as tile 5, the x inverse with radix 16 x 8 (16-point stage 1)
+        return launch_passC<128, 0, 256, 1, false, true, 16>(Y1, Y2, out, nrot, st);
     }
     HF_DISPATCH(n, launch_passC<NN>(Y1, Y2, out, nrot, st));
 }

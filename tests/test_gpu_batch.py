@@ -191,7 +191,7 @@ def test_autotune_choice_cache_and_results(hf, tmp_path):
     doc = json.loads(path.read_text())  # the cache is JSON: one entry per (device, N)
     (ent,) = [e for e in doc["tune"] if e["n"] == 64]
     assert ent["chunk"] == chunk and ent["pipeline"] == ("pencil" if pencil else "slab")
-    assert ent["radix"] == "8x8" and ent["passB_columns_per_cta"] in (16, 32)
+    assert ent["radix"] == "yz 8x8, x inverse 8x8" and ent["passB_columns_per_cta"] in (16, 32)
     assert (ent["tile_b"], ent["tile_c"]) == ctx.tune_tiles(64)
     # a second context reads the cache instead of timing
     ctx2 = hf.Context(0)
@@ -231,6 +231,14 @@ def test_tile_candidates_give_the_same_fields(hf, n):
             assert ctx.tune_tiles(n) == (tb, tc)
             got = all_fields(plain(hf, ctx, pair, q, hf.HF_E | hf.HF_F), 10, 4)
             assert np.array_equal(got, base), (tb, tc)
+    if n == 128:
+        # the x inverse with its digits in the other order: the same sums in
+        # another order, so equal to rounding (and bit for bit run to run)
+        ctx.tune_tiles(n, (0, 7))
+        got = all_fields(plain(hf, ctx, pair, q, hf.HF_E | hf.HF_F), 10, 4)
+        for f in range(4):
+            assert np.abs(got[:, f] - base[:, f]).max() <= 1e-6 * np.abs(base[:, f]).max(), f
+        assert np.array_equal(all_fields(plain(hf, ctx, pair, q, hf.HF_E | hf.HF_F), 10, 4), got)
     with pytest.raises(hf.HFError):
         ctx.tune_tiles(n, (0, 2) if n != 128 else (2, 0))
     # two pipelines alternating chunks on two streams: the same fields
