@@ -25,8 +25,14 @@
 namespace hf {
 
 // ------------------------------------------------------------------ complex
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex additions and subtractions are one paired FP32 instruction each
+// (sm_100 and later: an add on a float2, every component rounded as the
+// scalar operation, so the bits are those of two scalar adds; a + (-b) is
+// a - b exactly, signed zeros included).
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+// the pair (u.x, u.y) times s, one paired instruction
+__device__ __forceinline__ float2 cscale2(float2 u, float s) { return __fmul2_rn(u, make_float2(s, s)); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -132,10 +138,10 @@ __device__ __forceinline__ float2 twiddle_c(float2 x) {
         if constexpr (o == 2) return make_float2(-x.y, x.x);       // * i
         else if constexpr (o == 4) return make_float2(-x.x, -x.y);  // * -1
         else if constexpr (o == 6) return make_float2(x.y, -x.x);   // * -i
-        else if constexpr (o == 1) return make_float2((x.x - x.y) * r, (x.x + x.y) * r);
-        else if constexpr (o == 3) return make_float2(-(x.x + x.y) * r, (x.x - x.y) * r);
-        else if constexpr (o == 5) return make_float2((x.y - x.x) * r, -(x.x + x.y) * r);
-        else return make_float2((x.x + x.y) * r, (x.y - x.x) * r);  // o == 7
+        else if constexpr (o == 1) return cscale2(make_float2(x.x - x.y, x.x + x.y), r);
+        else if constexpr (o == 3) return cscale2(make_float2(-(x.x + x.y), x.x - x.y), r);
+        else if constexpr (o == 5) return cscale2(make_float2(x.y - x.x, -(x.x + x.y)), r);
+        else return cscale2(make_float2(x.x + x.y, x.y - x.x), r);  // o == 7
     } else {
         constexpr float c = (float)ct::trig(m, R, 0);
         constexpr float s = (float)(DIR * ct::trig(m, R, 1));
@@ -168,7 +174,7 @@ struct RegDFT<3, DIR> {
     __device__ __forceinline__ static void run(float2 *x) {
         constexpr float s3 = 0.86602540378443864676f * (float)DIR;
         float2 t = cadd(x[1], x[2]), d = csub(x[1], x[2]);
-        float2 m = make_float2(fmaf(-0.5f, t.x, x[0].x), fmaf(-0.5f, t.y, x[0].y));
+        float2 m = __ffma2_rn(make_float2(-0.5f, -0.5f), t, x[0]);
         float2 r = make_float2(-d.y * s3, d.x * s3);  // i * DIR * (sqrt3/2) * d
         x[0] = cadd(x[0], t);
         x[1] = cadd(m, r);
@@ -181,12 +187,18 @@ struct RegDFT<4, DIR> {
     __device__ __forceinline__ static void run(float2 *x) {
         float2 s02 = cadd(x[0], x[2]), d02 = csub(x[0], x[2]);
         float2 s13 = cadd(x[1], x[3]), d13 = csub(x[1], x[3]);
-        // W = DIR * i
-        float2 wd = DIR > 0 ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);
         x[0] = cadd(s02, s13);
         x[2] = csub(s02, s13);
-        x[1] = cadd(d02, wd);
-        x[3] = csub(d02, wd);
+        // d02 +- W d13 with W = DIR * i, as scalar adds (the swapped pair
+        // would cost moves): the same sums as adding (-d13.y, d13.x) or
+        // (d13.y, -d13.x)
+        if constexpr (DIR > 0) {
+            x[1] = make_float2(d02.x - d13.y, d02.y + d13.x);
+            x[3] = make_float2(d02.x + d13.y, d02.y - d13.x);
+        } else {
+            x[1] = make_float2(d02.x + d13.y, d02.y - d13.x);
+            x[3] = make_float2(d02.x - d13.y, d02.y + d13.x);
+        }
     }
 };
 
