@@ -802,7 +802,7 @@ def run_next_rows(args, local_rank):
     ta = {}
     tref = None
     for name, fl in (("fd_least_squares", hf.HF_T), ("fd_least_squares_f64", hf.HF_T | hf.HF_TORQUE_F64),
-                     ("analytic", hf.HF_TA)):
+                     ("fd_least_squares_compensated", hf.HF_T | hf.HF_TORQUE_C), ("analytic", hf.HF_TA)):
         fs = ctx.fieldset(n, R, hf.HF_E | hf.HF_F | fl)
         fs.compute(p1, p2, q)
         torch.cuda.synchronize()

@@ -87,6 +87,11 @@ typedef void *hf_stream; /* a cudaStream_t */
 #define HF_F 0x2u           /* force field (3 components) per rotation (always held) */
 #define HF_T 0x4u           /* torque field (3 components) per rotation */
 #define HF_TORQUE_F64 0x10u /* torque least-squares product in float64 on the device (over float32 differences) */
+/* Torque least-squares product in compensated float32 (Dot2 of Ogita, Rump
+ * and Oishi over the float64 operator split into two float32 parts): as
+ * accurate as the float64 product before the final rounding to float32, on
+ * the float32 units; an alternative to HF_TORQUE_F64 (both: HF_EINVAL). */
+#define HF_TORQUE_C 0x200u
 /* Precision variant (N = 256 only): the y-axis DFT stages run on the tensor
  * cores as 16 x 16 DFT-matrix GEMMs with operands split into hi + lo parts in
  * BF16 or FP16 and FP32 accumulation; every other stage stays FP32. */
@@ -630,7 +635,7 @@ hf_status hf_fields(hf_ctx *ctx, const hf_part *s1, const hf_part *s2, const flo
 
 /* Torque by least squares over the 6 nearest rotations for explicit
  * buffers: d_E is R x N^3, d_T is R x 3 x N^3, h_quat R x 4.  flags may hold
- * HF_TORQUE_F64.  h_status (R ints, may be NULL) receives 0 or 1 (rank
+ * HF_TORQUE_F64 or HF_TORQUE_C.  h_status (R ints, may be NULL) receives 0 or 1 (rank
  * deficient: NaN torque).  Errors: HF_EINVAL (R < 7 or a rank-deficient
  * rotation), HF_ENOMEM, HF_ECUDA. */
 hf_status hf_torque(hf_ctx *ctx, int n, int R, const float *h_quat, const float *d_E, float *d_T,

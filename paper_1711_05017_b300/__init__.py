@@ -14,7 +14,7 @@ import numpy as np
 from . import _binding as B
 from ._binding import (HF_CKPT_FIELDSET, HF_CKPT_PART, HF_CKPT_SESSION,  # noqa: F401
                        HF_E, HF_F, HF_MOVING, HF_PREC_SPLIT_BF16, HF_PREC_SPLIT_F16, HF_SPECTRAL,
-                       HF_STATIONARY, HF_T, HF_TA, HF_TORQUE_F64, HFError)
+                       HF_STATIONARY, HF_T, HF_TA, HF_TORQUE_C, HF_TORQUE_F64, HFError)
 
 __all__ = ["Context", "Part", "FieldSet", "Batch", "Server", "HFError", "lowpass_query", "lowpass_query_batch",
            "rotation_chunks", "checkpoint_info",

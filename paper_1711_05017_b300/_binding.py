@@ -13,7 +13,7 @@ HF_OK, HF_EINVAL, HF_ENOMEM, HF_EBUDGET, HF_ECUDA, HF_ETIMEOUT, HF_ENOTREADY, HF
 STATUS_NAMES = {0: "HF_OK", 1: "HF_EINVAL", 2: "HF_ENOMEM", 3: "HF_EBUDGET", 4: "HF_ECUDA",
                 5: "HF_ETIMEOUT", 6: "HF_ENOTREADY", 7: "HF_EUNSUPPORTED"}
 HF_STATIONARY, HF_MOVING = 0, 1
-HF_E, HF_F, HF_T, HF_TORQUE_F64 = 0x1, 0x2, 0x4, 0x10
+HF_E, HF_F, HF_T, HF_TORQUE_F64, HF_TORQUE_C = 0x1, 0x2, 0x4, 0x10, 0x200
 HF_PREC_SPLIT_BF16, HF_PREC_SPLIT_F16, HF_SPECTRAL, HF_TA = 0x20, 0x40, 0x80, 0x100
 HF_CKPT_PART, HF_CKPT_FIELDSET, HF_CKPT_SESSION = 1, 2, 3
 

@@ -1006,6 +1006,8 @@ static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags,
     if ((flags & HF_T) && R < 7) return fail(HF_EINVAL, "hf_fieldset_create: torque needs R >= 7 (R=%d)", R);
     if ((flags & HF_T) && (flags & HF_TA))
         return fail(HF_EINVAL, "hf_fieldset_create: HF_T and HF_TA are alternatives");
+    if ((flags & HF_TORQUE_F64) && (flags & HF_TORQUE_C))
+        return fail(HF_EINVAL, "hf_fieldset_create: HF_TORQUE_F64 and HF_TORQUE_C are alternatives");
     if ((flags & HF_TA) && (n > 128 || (flags & HF_SPECTRAL)))
         return fail(HF_EUNSUPPORTED, "hf_fieldset_create: HF_TA needs N <= 128 and the spatial route");
     const unsigned precf = flags & (HF_PREC_SPLIT_BF16 | HF_PREC_SPLIT_F16);
@@ -1242,6 +1244,11 @@ static hf_status check_pair(const hf_part *s1, const hf_part *s2, int n, const c
     return HF_OK;
 }
 
+// the torque product's precision from the flags (hf_internal.h run_torque)
+static int torque_mode(unsigned flags) {
+    return (flags & HF_TORQUE_F64) ? 1 : ((flags & HF_TORQUE_C) ? 2 : 0);
+}
+
 // Host preparation of a rotation set: normalised quaternions, float32
 // matrices and (with torque) the neighbours and float64 least-squares
 // operators.  Returns the number of rank-deficient rotations, or -1 when a
@@ -1318,7 +1325,7 @@ hf_status hf_set_launch(hf_ctx *ctx, const hf_part *s1, const hf_part *s2, hf_fi
     if (fs->flags & HF_T) {
         CU(timed(ctx, kTorque, st, [&] {
             return hf::run_torque(n, R, fs->data, rs, fs->data + (size_t)fs->slot[4] * n3, rs, d_nbr, d_P, d_P64,
-                                  (fs->flags & HF_TORQUE_F64) != 0, st);
+                                  torque_mode(fs->flags), st);
         }));
     }
     return HF_OK;
@@ -1628,6 +1635,8 @@ extern "C" hf_status hf_torque(hf_ctx *ctx, int n, int R, const float *h_quat, c
     if (!ctx || !h_quat || !d_E || !d_T) return fail(HF_EINVAL, "hf_torque: NULL argument");
     if (!hf::supported_n(n)) return fail(HF_EUNSUPPORTED, "hf_torque: N=%d not supported", n);
     if (R < 7) return fail(HF_EINVAL, "hf_torque: R=%d < 7", R);
+    if ((flags & HF_TORQUE_F64) && (flags & HF_TORQUE_C))
+        return fail(HF_EINVAL, "hf_torque: HF_TORQUE_F64 and HF_TORQUE_C are alternatives");
     CU(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
     std::vector<Quat> Q(R);
@@ -1653,7 +1662,7 @@ extern "C" hf_status hf_torque(hf_ctx *ctx, int n, int R, const float *h_quat, c
     const size_t n3 = (size_t)n * n * n;
     if (e == cudaSuccess)
         e = timed(ctx, kTorque, st, [&] {
-            return hf::run_torque(n, R, d_E, n3, d_T, 3 * n3, d_nbr, d_P, d_P64, (flags & HF_TORQUE_F64) != 0, st);
+            return hf::run_torque(n, R, d_E, n3, d_T, 3 * n3, d_nbr, d_P, d_P64, torque_mode(flags), st);
         });
     if (d_nbr) cudaFreeAsync(d_nbr, st);
     if (d_P) cudaFreeAsync(d_P, st);

@@ -182,8 +182,9 @@ cudaError_t run_xinv(int n, const float2 *ZS, const float2 *ZGy, const float2 *Z
 cudaError_t run_splat(int n, const float *pts, const float *sigma, const float *amp, int P, float *grid,
                       cudaStream_t st);
 cudaError_t run_resample(int n, const float *rho, Rot9 rot, float *out, cudaStream_t st);
+// mode: 0 float32 product, 1 float64 product, 2 compensated float32 (float64-class)
 cudaError_t run_torque(int n, int R, const float *E, size_t e_rot_stride, float *T, size_t t_rot_stride,
-                       const int *nbr, const float *P, const double *P64, bool f64, cudaStream_t st);
+                       const int *nbr, const float *P, const double *P64, int mode, cudaStream_t st);
 // query: field f of rotation r at base + r*rot_stride + field_slot[f]*n^3 when
 // field_slot[f] >= 0, else the field reads 0
 struct QueryGeom {

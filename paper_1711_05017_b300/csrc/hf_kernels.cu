@@ -149,7 +149,20 @@ constexpr int kTorqueThreads = 256;
 constexpr int kTorqueVec = 2;  // float4 groups of cells per thread, all loads in flight together
 constexpr int kTorqueTile = kTorqueThreads * 4 * kTorqueVec;
 
-template <bool F64>
+// The 3 x 6 least-squares product T_d = -sum_s P_ds (E_s - E_r) per cell, in
+// one of three precisions (MODE): 0 float32 fma; 1 float64 over the float32
+// differences; 2 compensated float32, as accurate as float64 before the final
+// rounding.  Mode 2 is the dot product Dot2 of Ogita, Rump and Oishi
+// ("Accurate sum and dot product", SIAM J. Sci. Comput. 26, 2005) with the
+// float64 operator split into P = hi + lo (hi its float32 rounding, lo the
+// float32 rounding of the rest, together within 2^-48 of P): each hi b is
+// split exactly into its rounded product and the product's error (one fma),
+// the rounded products are summed with TwoSum (Knuth) keeping every
+// rounding error, and the errors, the lo b terms and the TwoSum errors are
+// summed in float32 beside; the result is the float32 rounding of the two
+// sums' total.  Its float32 arithmetic runs as paired instructions over the
+// (x, y) and (z, w) cells of each float4 group.
+template <int MODE>
 __global__ void __launch_bounds__(kTorqueThreads) torque_kernel(const float *__restrict__ E, size_t es,
                                                                 float *__restrict__ T, size_t ts,
                                                                 const int *__restrict__ nbr,
@@ -158,6 +171,17 @@ __global__ void __launch_bounds__(kTorqueThreads) torque_kernel(const float *__r
                                                                 size_t n3) {
     const int r = blockIdx.x % R;
     const size_t tile = blockIdx.x / R;
+    __shared__ float2 s_hi[18], s_lo[18];
+    if constexpr (MODE == 2) {
+        // the rotation's operator as hi + lo, once per block (18 float64 subtractions)
+        if (threadIdx.x < 18) {
+            const float hi = __ldg(P + 18 * r + threadIdx.x);
+            const float lo = (float)(__ldg(P64 + 18 * r + threadIdx.x) - (double)hi);
+            s_hi[threadIdx.x] = make_float2(hi, hi);
+            s_lo[threadIdx.x] = make_float2(lo, lo);
+        }
+        __syncthreads();
+    }
     // group j of the thread covers cells c0 + 4 (j kTorqueThreads) .. + 3: a
     // warp's accesses stay contiguous for every j
     const size_t c0 = tile * kTorqueTile + (size_t)threadIdx.x * 4;
@@ -181,7 +205,51 @@ __global__ void __launch_bounds__(kTorqueThreads) torque_kernel(const float *__r
         if (!live[j]) continue;
         const size_t c = c0 + (size_t)j * kTorqueThreads * 4;
         float4 g[3];
-        if constexpr (!F64) {
+        if constexpr (MODE == 2) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {  // the float4's (x, y) and (z, w) cells
+                float2 b[6];
+#pragma unroll
+                for (int s = 0; s < 6; ++s) {
+                    const float4 &u = ej[j][s];
+                    const float2 a = h ? make_float2(u.z, u.w) : make_float2(u.x, u.y);
+                    const float2 e0 = h ? make_float2(ei[j].z, ei[j].w) : make_float2(ei[j].x, ei[j].y);
+                    b[s] = __fadd2_rn(a, make_float2(-e0.x, -e0.y));
+                }
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    float2 p = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int s = 0; s < 6; ++s) {
+                        const float2 hi = s_hi[6 * d + s], lo = s_lo[6 * d + s];
+                        const float2 t = __fmul2_rn(hi, b[s]);                                // rounded hi b
+                        const float2 e = __ffma2_rn(hi, b[s], make_float2(-t.x, -t.y));       // its exact error
+                        if (s == 0) {
+                            p = t;
+                            c = __ffma2_rn(lo, b[s], e);
+                        } else {
+                            // TwoSum: p + t = ps + q exactly
+                            const float2 ps = __fadd2_rn(p, t);
+                            const float2 bv = __fadd2_rn(ps, make_float2(-p.x, -p.y));
+                            const float2 av = __fadd2_rn(ps, make_float2(-bv.x, -bv.y));
+                            const float2 q = __fadd2_rn(__fadd2_rn(p, make_float2(-av.x, -av.y)),
+                                                        __fadd2_rn(t, make_float2(-bv.x, -bv.y)));
+                            p = ps;
+                            c = __fadd2_rn(c, __fadd2_rn(q, e));
+                            c = __ffma2_rn(lo, b[s], c);
+                        }
+                    }
+                    const float2 v = __fadd2_rn(p, c);
+                    if (h) {
+                        g[d].z = v.x;
+                        g[d].w = v.y;
+                    } else {
+                        g[d].x = v.x;
+                        g[d].y = v.y;
+                    }
+                }
+            }
+        } else if constexpr (MODE == 0) {
 #pragma unroll
             for (int d = 0; d < 3; ++d) g[d] = make_float4(0, 0, 0, 0);
 #pragma unroll
@@ -371,15 +439,17 @@ cudaError_t run_resample(int n, const float *rho, Rot9 rot, float *out, cudaStre
 }
 
 cudaError_t run_torque(int n, int R, const float *E, size_t e_rot_stride, float *T, size_t t_rot_stride,
-                       const int *nbr, const float *P, const double *P64, bool f64, cudaStream_t st) {
+                       const int *nbr, const float *P, const double *P64, int mode, cudaStream_t st) {
     const size_t n3 = (size_t)n * n * n;
     const size_t tiles = (n3 + kTorqueTile - 1) / kTorqueTile;
     const size_t blocks = tiles * (size_t)R;
     if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
-    if (f64)
-        torque_kernel<true><<<(unsigned)blocks, kTorqueThreads, 0, st>>>(E, e_rot_stride, T, t_rot_stride, nbr, P, P64, R, n3);
+    if (mode == 1)
+        torque_kernel<1><<<(unsigned)blocks, kTorqueThreads, 0, st>>>(E, e_rot_stride, T, t_rot_stride, nbr, P, P64, R, n3);
+    else if (mode == 2)
+        torque_kernel<2><<<(unsigned)blocks, kTorqueThreads, 0, st>>>(E, e_rot_stride, T, t_rot_stride, nbr, P, P64, R, n3);
     else
-        torque_kernel<false><<<(unsigned)blocks, kTorqueThreads, 0, st>>>(E, e_rot_stride, T, t_rot_stride, nbr, P, P64, R, n3);
+        torque_kernel<0><<<(unsigned)blocks, kTorqueThreads, 0, st>>>(E, e_rot_stride, T, t_rot_stride, nbr, P, P64, R, n3);
     return cudaGetLastError();
 }
 

@@ -219,11 +219,24 @@ def test_torque_float64_variant(hf, ctx, small_set):
     n, R = small_set["n"], small_set["R"]
     fs = small_set["fs"]
     E = torch.stack([fs.get(r, 0) for r in range(R)]).contiguous()
-    for flags in (0, hf.HF_TORQUE_F64):
+    got = {}
+    for flags in (0, hf.HF_TORQUE_F64, hf.HF_TORQUE_C):
         T = torch.empty((R, 3, n, n, n), device="cuda")
         st = ctx.torque(n, small_set["q"], E, T, flags=flags)
         assert (st == 0).all()
         assert rel_err(host(T), small_set["T"]) <= TOL
+        got[flags] = host(T).astype(np.float32)
+    # the compensated float32 product is as accurate as the float64 one before
+    # the final rounding: the same float32 results but where the exact value
+    # lies within about 2^-44 of a rounding boundary, and never more than one
+    # float32 step apart
+    a, b = got[hf.HF_TORQUE_C], got[hf.HF_TORQUE_F64]
+    assert np.mean(a == b) >= 0.999
+    step = np.spacing(np.maximum(np.abs(a), np.abs(b)).astype(np.float32))
+    assert (np.abs(a.astype(np.float64) - b.astype(np.float64)) <= step).all()
+    with pytest.raises(hf.HFError):
+        ctx.torque(n, small_set["q"], E, torch.empty((R, 3, n, n, n), device="cuda"),
+                   flags=hf.HF_TORQUE_F64 | hf.HF_TORQUE_C)
 
 
 def test_query_batch_and_single(hf, small_set):
