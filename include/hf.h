@@ -547,9 +547,10 @@ void hf_batch_release(hf_batch *batch);
  * (N = 256: pencil only).  hf_autotune times builds of E and F on synthetic
  * parts for every candidate that fits the budget, keeps the fastest for field
  * sets created afterwards, and, given a cache_path, first looks for a line
- * for this device and N there (and writes one after timing).  Cache lines
- * are text: "<device> <n> <chunk> <pencil> <rotations_per_s>".  Outputs may
- * be NULL.  hf_tune_set fixes the choice by hand (chunk <= 0 restores the
+ * for this device and N there (and writes one after timing).  The cache is
+ * JSON, one entry per (device, N): chunk, pipeline, pass B and C launch
+ * shapes, pipelines, the radix plan, the E+F rate and every timed
+ * candidate.  Outputs may be NULL.  hf_tune_set fixes the choice by hand (chunk <= 0 restores the
  * built-in one); hf_tune_get reads the current choice (rot_per_s 0 when not
  * timed).  The environment variable HF_ROT_CHUNK overrides all of them.
  * Errors: HF_EINVAL, HF_EUNSUPPORTED, HF_ENOMEM (nothing fits), HF_ECUDA. */
