@@ -16,10 +16,11 @@
 namespace hf {
 
 // ------------------------------------------------------------------ splat
-// One CTA per 8x8x8 tile of nodes, one thread per node.  The CTA walks the
-// point list in chunks, keeps (in point order) the points whose cutoff
-// sphere reaches the tile's box, and every thread adds their Gaussians to
-// its node.  Gather form: deterministic, no atomics.
+// One CTA per 8x8x8 tile of nodes; each thread owns the two nodes lz and
+// lz + 4 of its (lx, ly) column.  The CTA walks the point list in chunks,
+// keeps (in point order) the points whose cutoff sphere reaches the tile's
+// box, and every thread adds their Gaussians to its nodes.  Gather form:
+// deterministic, no atomics.
 //
 // A kept point is stored as its offset from the tile centre, taken at its
 // periodic image nearest that centre; a node's own offset from the centre,
@@ -29,8 +30,14 @@ namespace hf {
 // any image, so the node-point distance is one subtraction per axis.  A
 // chunk holding a point with a cutoff too wide for that takes the minimum
 // image per node instead.
+//
+// The two nodes' arithmetic runs as paired FP32 instructions (sm_100 add,
+// multiply and fma on a float2, each half rounded as the scalar operation):
+// the same operations in the same order per node as one node per thread,
+// so the same bits.  The kept points are stored with their offsets negated
+// and duplicated into pairs, so that no pair needs assembling.
 constexpr int kSplatTile = 8;
-constexpr int kSplatThreads = kSplatTile * kSplatTile * kSplatTile;
+constexpr int kSplatThreads = kSplatTile * kSplatTile * kSplatTile / 2;
 
 __device__ __forceinline__ float min_image(float d) { return d - 2.0f * rintf(0.5f * d); }
 
@@ -43,14 +50,17 @@ __device__ __forceinline__ float exp2_neg(float t) {
 }
 
 template <int N>
-__global__ void __launch_bounds__(kSplatThreads, 3) splat_kernel(const float *__restrict__ pts,
+__global__ void __launch_bounds__(kSplatThreads, 6) splat_kernel(const float *__restrict__ pts,
                                                               const float *__restrict__ sigma,
                                                               const float *__restrict__ amp, int P,
                                                               float *__restrict__ grid) {
-    __shared__ float4 cand[kSplatThreads];  // offset from the tile centre (x, y, z), amplitude
-    __shared__ float2 cpar[kSplatThreads];  // cutoff^2, -log2(e) / (2 sigma^2)
+    // kept points: (-x, -x, -y, -y) and (-z, -z, a, a) of the offset from the
+    // tile centre and the amplitude; (c^2, c^2, k, k) with c the cutoff and
+    // k = -log2(e) / (2 sigma^2)
+    __shared__ float4 cxy[kSplatThreads], cza[kSplatThreads], cpar[kSplatThreads];
     __shared__ int warp_cnt[kSplatThreads / 32];
     constexpr int TPA = N / kSplatTile;  // tiles per axis
+    constexpr int HZ = kSplatTile / 2;   // the thread's second node is HZ further along z
     constexpr float kLog2e = 1.4426950408889634f;
     const int t = blockIdx.x;
     const int tx = t % TPA, ty = (t / TPA) % TPA, tz = t / (TPA * TPA);
@@ -65,9 +75,11 @@ __global__ void __launch_bounds__(kSplatThreads, 3) splat_kernel(const float *__
     const float bz = (float)(tz * kSplatTile - N / 2) * h + half;
     const float qx = (float)(2 * lx - (kSplatTile - 1)) * (0.5f * h);
     const float qy = (float)(2 * ly - (kSplatTile - 1)) * (0.5f * h);
-    const float qz = (float)(2 * lz - (kSplatTile - 1)) * (0.5f * h);
+    const float qz0 = (float)(2 * lz - (kSplatTile - 1)) * (0.5f * h);
+    const float qz1 = (float)(2 * (lz + HZ) - (kSplatTile - 1)) * (0.5f * h);
+    const float2 qx2 = make_float2(qx, qx), qy2 = make_float2(qy, qy), qz2 = make_float2(qz0, qz1);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float acc = 0.0f;
+    float2 acc = make_float2(0.0f, 0.0f);
     for (int base = 0; base < P; base += kSplatThreads) {
         const int i = base + threadIdx.x;
         bool keep = false, wide = false;
@@ -97,32 +109,44 @@ __global__ void __launch_bounds__(kSplatThreads, 3) splat_kernel(const float *__
         }
         if (keep) {
             const int pos = off + __popc(m & ((1u << lane) - 1u));
-            cand[pos] = c;
-            cpar[pos] = cp;
+            cxy[pos] = make_float4(-c.x, -c.x, -c.y, -c.y);
+            cza[pos] = make_float4(-c.z, -c.z, c.w, c.w);
+            cpar[pos] = make_float4(cp.x, cp.x, cp.y, cp.y);
         }
         __syncthreads();
         if (!any_wide) {
 #pragma unroll 4
             for (int j = 0; j < total; ++j) {
-                const float4 cj = cand[j];
-                const float2 pj = cpar[j];
-                const float dx = qx - cj.x, dy = qy - cj.y, dz = qz - cj.z;
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                const float g = exp2_neg(r2 * pj.y);
-                acc = fmaf(r2 <= pj.x ? cj.w : 0.0f, g, acc);
+                const float4 a = cxy[j], b = cza[j], pj = cpar[j];
+                const float2 dx = __fadd2_rn(qx2, make_float2(a.x, a.y));
+                const float2 dy = __fadd2_rn(qy2, make_float2(a.z, a.w));
+                const float2 dz = __fadd2_rn(qz2, make_float2(b.x, b.y));
+                const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+                const float2 e = __fmul2_rn(r2, make_float2(pj.z, pj.w));
+                const float2 g = make_float2(exp2_neg(e.x), exp2_neg(e.y));
+                const float2 w = make_float2(r2.x <= pj.x ? b.z : 0.0f, r2.y <= pj.y ? b.w : 0.0f);
+                acc = __ffma2_rn(w, g, acc);
             }
         } else {
             for (int j = 0; j < total; ++j) {
-                const float4 cj = cand[j];
-                const float2 pj = cpar[j];
-                const float dx = min_image(qx - cj.x), dy = min_image(qy - cj.y), dz = min_image(qz - cj.z);
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                if (r2 <= pj.x) acc = fmaf(cj.w, exp2_neg(r2 * pj.y), acc);
+                const float4 a = cxy[j], b = cza[j], pj = cpar[j];
+                const float dx = min_image(qx + a.x), dy = min_image(qy + a.z);
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const float dz = min_image((k ? qz1 : qz0) + b.x);
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    if (r2 <= pj.x) {
+                        const float v = fmaf(b.z, exp2_neg(r2 * pj.z), k ? acc.y : acc.x);
+                        if (k) acc.y = v;
+                        else acc.x = v;
+                    }
+                }
             }
         }
         __syncthreads();
     }
-    grid[((size_t)nz * N + ny) * N + nx] = acc;
+    grid[((size_t)nz * N + ny) * N + nx] = acc.x;
+    grid[((size_t)(nz + HZ) * N + ny) * N + nx] = acc.y;
 }
 
 // --------------------------------------------------------------- resample

@@ -237,6 +237,16 @@ def test_torque_float64_variant(hf, ctx, small_set):
     with pytest.raises(hf.HFError):
         ctx.torque(n, small_set["q"], E, torch.empty((R, 3, n, n, n), device="cuda"),
                    flags=hf.HF_TORQUE_F64 | hf.HF_TORQUE_C)
+    # the same products through a field set's flags
+    p1, p2 = small_set["p"]
+    for flags in (hf.HF_TORQUE_F64, hf.HF_TORQUE_C):
+        fs2 = ctx.fieldset(n, R, hf.HF_E | hf.HF_F | hf.HF_T | flags)
+        fs2.compute(p1, p2, small_set["q"])
+        T2 = np.stack([np.stack([host(fs2.get(r, 4 + d)) for d in range(3)]) for r in range(R)])
+        assert np.array_equal(T2.astype(np.float32), got[flags]), flags
+        fs2.release()
+    with pytest.raises(hf.HFError):
+        ctx.fieldset(n, R, hf.HF_E | hf.HF_F | hf.HF_T | hf.HF_TORQUE_F64 | hf.HF_TORQUE_C)
 
 
 def test_query_batch_and_single(hf, small_set):
