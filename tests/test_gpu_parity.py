@@ -318,11 +318,13 @@ def test_rank_deficient_rotation_set_flags_nan(hf, ctx, small_set):
     angs = np.linspace(-0.6, 0.6, 9)
     q = np.array([[np.cos(a / 2), 0, 0, np.sin(a / 2)] for a in angs], dtype=np.float32)
     p1, p2 = small_set["p"]
-    fs = ctx.fieldset(n, len(q), hf.HF_E | hf.HF_F | hf.HF_T)
-    rc = fs.compute(p1, p2, q, allow_rank_deficient=True)
-    assert rc == 1  # HF_EINVAL after computing everything else
-    assert np.isnan(host(fs.get(0, 4))).all()
-    assert np.isfinite(host(fs.get(0, 0))).all()
+    for prec in (0, hf.HF_TORQUE_F64, hf.HF_TORQUE_C):
+        fs = ctx.fieldset(n, len(q), hf.HF_E | hf.HF_F | hf.HF_T | prec)
+        rc = fs.compute(p1, p2, q, allow_rank_deficient=True)
+        assert rc == 1  # HF_EINVAL after computing everything else
+        assert np.isnan(host(fs.get(0, 4))).all(), prec
+        assert np.isfinite(host(fs.get(0, 0))).all()
+        fs.release()
 
 
 # ------------------------------------------- full-size workload, sampled
