@@ -962,6 +962,7 @@ def run_serving(args, local_rank):
     srv.query_latencies()  # drop the warm-up's
     srv.trace(0)
     srv.trace(1)
+    cg0 = _cgroup_cpu_stat()
     t_start = time.perf_counter()
     for t in th:
         t.start()
@@ -997,8 +998,9 @@ def run_serving(args, local_rank):
         over = [{"kind": ("create", "compute", "release")[int(c[2])], "start_ms": round(c[0], 2),
                  "us": round(c[1], 1)} for c in slow_c if c[0] <= t0q + us / 1e3 and c[0] + c[1] / 1e3 >= t0q]
         worst.append({"start_ms": round(t0q, 2), "us": round(us, 1), "mutex_us": round(row[2], 1),
-                      "lane_wait_us": round(row[3], 1), "launch_sync_us": round(row[4], 1),
-                      "session_n": sess[int(row[5])].n, "overlapping_scheduler_calls": over[:4]})
+                      "lane_wait_us": round(row[3], 1), "launch_us": round(row[4], 1), "sync_us": round(row[5], 1),
+                      "session_n": sess[int(row[6])].n, "involuntary_csw": int(row[7]),
+                      "voluntary_csw": int(row[8]), "overlapping_scheduler_calls": over[:4]})
     per_n = {}
     for sid, s in zip(sids, sess):
         a, nr = srv.session_counts(sid)
@@ -1030,6 +1032,10 @@ def run_serving(args, local_rank):
         "memory_pool_gb": {"reserved_at_start": round(st0["pool_reserved_bytes"] / 2**30, 2),
                            "reserved_at_end": round(st1["pool_reserved_bytes"] / 2**30, 2),
                            "reserved_high": round(st1["pool_reserved_high"] / 2**30, 2)},
+        "field_set_arena": {"gb": round(st1["arena_bytes"] / 2**30, 2),
+                            "free_gb_at_end": round(st1["arena_free_bytes"] / 2**30, 2),
+                            "largest_free_gb_at_end": round(st1["arena_largest_free"] / 2**30, 2),
+                            "refusals": int(st2["arena_refusals"] - st0["arena_refusals"])},
         "hardware_queues": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS", "8 (the default)"),
         "slowest_queries": worst,
         "slow_scheduler_calls": {"n": int(len(slow_c)),
@@ -1040,9 +1046,45 @@ def run_serving(args, local_rank):
                                              for k, name in enumerate(("create", "compute", "release"))
                                              if len(slow_c) and (slow_c[:, 2] == k).any()}},
     }
+    if len(slow_q):
+        inv = slow_q[:, 7] > 0
+        over = slow_q[:, 1] > 1000
+        out["slow_query_causes"] = {
+            "n_over_500us": int(len(slow_q)), "n_over_1ms": int(over.sum()),
+            "with_involuntary_csw": int(inv.sum()), "over_1ms_with_involuntary_csw": int((inv & over).sum()),
+            "launch_us_p50": round(float(np.median(slow_q[:, 4])), 1),
+            "sync_us_p50": round(float(np.median(slow_q[:, 5])), 1),
+            "over_1ms_launch_us_max": round(float(slow_q[over, 4].max()), 1) if over.any() else None,
+            "over_1ms_sync_us_max": round(float(slow_q[over, 5].max()), 1) if over.any() else None}
+    out["host_cpu"] = {"cpus_usable": len(os.sched_getaffinity(0)), "cgroup_cpu": _cgroup_cpu(cg0)}
     srv.close()
     del parts
     return out
+
+
+def _cgroup_cpu_stat():
+    """The process's cgroup CPU quota and throttling counters (cgroup v2 or
+    v1), or None where neither is readable."""
+    for stat, quota in (("/sys/fs/cgroup/cpu.stat", "/sys/fs/cgroup/cpu.max"),
+                        ("/sys/fs/cgroup/cpu/cpu.stat", "/sys/fs/cgroup/cpu/cpu.cfs_quota_us")):
+        try:
+            with open(stat) as f:
+                d = {k: int(v) for k, v in (ln.split() for ln in f if len(ln.split()) == 2)}
+            with open(quota) as f:
+                d["quota"] = f.read().strip()
+            return d
+        except (OSError, ValueError):
+            continue
+    return None
+
+
+def _cgroup_cpu(before):
+    """Throttling during the serving run: the counters' change since `before`."""
+    after = _cgroup_cpu_stat()
+    if not before or not after:
+        return None
+    keys = ("nr_periods", "nr_throttled", "throttled_usec", "throttled_time")
+    return {"quota": after.get("quota"), **{k: after[k] - before[k] for k in keys if k in after and k in before}}
 
 
 # ------------------------------------------------------- reference arm

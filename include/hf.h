@@ -147,6 +147,17 @@ void hf_ctx_destroy(hf_ctx *ctx);
 /* Bytes currently charged against the budget, and the budget (0 = none). */
 size_t hf_ctx_reserved_bytes(const hf_ctx *ctx);
 size_t hf_ctx_budget_bytes(const hf_ctx *ctx);
+/* Load now every kernel of the field builds (all grid sizes, launch shapes and
+ * precision variants), the torque and the pose queries on the context's
+ * device.  CUDA loads device code lazily by default: the first launch of
+ * each kernel loads it, and while the driver loads, other threads' launches
+ * wait (milliseconds).  A latency-bound caller preloads once at start-up;
+ * hf_server_create does.  Loading is per device and idempotent; *loaded (may
+ * be NULL) receives the number of kernels in the modules loaded.  The paper
+ * has no counterpart: this is the runtime around the method.
+ * Errors: HF_EINVAL (null ctx), HF_EUNSUPPORTED (a driver without
+ * per-function loading), HF_ECUDA. */
+hf_status hf_ctx_preload(hf_ctx *ctx, int *loaded);
 
 /* Skeletal density on the N^3 grid (the stand-in for the paper's skeletal
  * density, Section 2.3): rho[n] = sum_i a_i exp(-|x_n - c_i|^2 / (2 sigma_i^2))
@@ -267,7 +278,8 @@ void hf_fieldset_release(hf_fieldset *fs);
  * exact hit, theta < 1e-12, returns that rotation alone); per rotation,
  * periodic trilinear interpolation of each held field at lag u = t/h.
  * out7 = (E, Fx, Fy, Fz, Tx, Ty, Tz); fields not held read 0.  Host in/out;
- * synchronous (runs on an internal high-priority stream).
+ * synchronous (runs on an internal high-priority stream, which is not ordered
+ * after the stream of hf_fieldset_compute: synchronise that stream first).
  * Errors: HF_EINVAL (k_blend outside 1..8 or > R), HF_ENOTREADY, HF_ECUDA. */
 hf_status hf_query(const hf_fieldset *fs, const float t[3], const float q[4], int k_blend,
                    float out7[7]);
@@ -373,18 +385,34 @@ int hf_rotation_chunks(const float *h_quat, int R, int max_build, int halo, int 
  *   - When nothing runs and the head chunk does not fit, a published chunk
  *     is evicted: the least recently queried of those idle for 20 ms, else
  *     the largest.
+ *   - Queries are answered without a kernel launch by a resident query
+ *     kernel: the query posts its request in its lane's mailbox in mapped
+ *     pinned memory and spins until the kernel writes the answer back.  An
+ *     instance of the kernel serves for 10 ms and returns; a server thread
+ *     keeps the next instance queued behind it on a high-priority stream, so
+ *     one always runs (one SM's worth of warps), and destroying the server
+ *     stops it.  A request not answered within 20 ms runs by launch on the
+ *     lane's own stream instead.  Since the kernel always runs, a
+ *     device-wide synchronisation while a server lives (cudaDeviceSynchronize,
+ *     and cudaFree, which implies one) waits for the running and the queued
+ *     instance (up to 20 ms).
+ *     HF_RESIDENT_QUERIES=0 in the environment makes every query launch.
  *   - Queries run on a pool of high-priority lanes (own stream and pinned
  *     mailbox each) against the chunk that owns the query's nearest rotation
  *     (HF_ENOTREADY if that chunk is not resident); they equal the whole
  *     set's answer when the query's k nearest rotations are owned by it.
  *   - Queries take no lock that the scheduler or a submitting thread holds
  *     (the published data is read through atomic shared pointers).
- *   - The builds allocate from the device's default stream-ordered memory
- *     pool, whose release threshold the server sets to keep its reserve; at
- *     creation the server reserves the context's remaining budget in the
- *     pool (up to the free memory less 4 GB), so that builds do not map
- *     memory while queries run (the pool is trimmed when the server is
- *     destroyed).
+ *   - At creation the server allocates the context's remaining budget (up to
+ *     the free memory less 4 GB) as one device arena and carves every build's
+ *     field set from it with host-side bookkeeping (best fit, coalesced on
+ *     free), so that no build maps or unmaps device memory while queries run:
+ *     the driver work of a mapping held up other threads' launches for
+ *     milliseconds.  A chunk that finds no free range of its size is treated
+ *     like one over the budget (eviction, or a wait for a running build).
+ *     Without room for the arena the builds allocate from the device's
+ *     default stream-ordered pool instead (its reserve kept; trimmed when
+ *     the server is destroyed).
  * Request states: 0 queued, 1 running, 2 done, 3 failed, 4 superseded. */
 typedef struct hf_server hf_server;
 typedef struct {
@@ -395,9 +423,17 @@ typedef struct {
     int64_t chunks_submitted, chunks_completed;
     int chunks_resident;
     size_t chunk_bytes;
-    /* the device's default memory pool, which the builds allocate from: its
-     * reserved bytes now and at their highest */
+    /* the device's default memory pool: its reserved bytes now and at their
+     * highest (the builds allocate from it only when the server has no arena) */
     size_t pool_reserved_bytes, pool_reserved_high;
+    /* the server's field-set arena: its size (0: none), free bytes, largest
+     * free range, and the allocations it refused for want of a range */
+    size_t arena_bytes, arena_free_bytes, arena_largest_free;
+    int64_t arena_refusals;
+    /* queries answered by the resident query kernel, those that waited past
+     * its bound and ran by launch instead, and whether it is running now */
+    int64_t resident_queries, resident_timeouts;
+    int resident_live;
 } hf_server_stats;
 
 /* max_inflight: builds on the device at once (1..16); query_lanes: 1..64. */
@@ -459,13 +495,15 @@ hf_status hf_server_session_counts(hf_server *srv, int session, int64_t *answere
  * the last call, oldest first, at most `max` of them (the newest 2^20 are
  * kept); returns how many were written. */
 int hf_server_query_latencies(hf_server *srv, float *h_out_us, int max);
-/* Diagnostics since the last call, oldest first, 6 doubles per row, at most
+/* Diagnostics since the last call, oldest first, 9 doubles per row, at most
  * `max` rows (the newest 4096 are kept); returns the row count.
  *   which 0, queries of 500 us or more: start (ms since hf_server_create),
  *     total us, us spent resolving the session's set (server mutex), waiting
- *     for a lane, and in the lane's launch + synchronise; the session.
+ *     for a lane, in the query kernel's launch call, and in the lane's
+ *     synchronise; the session; the calling thread's involuntary and
+ *     voluntary context switches during the query.
  *   which 1, scheduler calls of 1 ms or more: start (ms), duration (us),
- *     kind (0 field-set create, 1 compute launch, 2 release), 0, 0, 0. */
+ *     kind (0 field-set create, 1 compute launch, 2 release), then zeros. */
 int hf_server_trace(hf_server *srv, int which, double *h_out, int max);
 /* Replay pose trajectories against sessions from native threads, one per
  * session, one query every 1/rate_hz seconds (a haptic device's servo loop):
@@ -476,6 +514,20 @@ int hf_server_trace(hf_server *srv, int which, double *h_out, int max);
 hf_status hf_server_drive_queries(hf_server *srv, int nsess, const int *sessions, const float *h_poses, int steps,
                                   double rate_hz, int k_blend, int64_t *answered, int64_t *not_ready,
                                   int64_t *late);
+
+/* Self-check of the bookkeeping behind the server's field-set arena: `ops`
+ * seeded random allocations (1 byte to a quarter of the region, log-uniform)
+ * and frees on a region of `bytes` at a fictitious address, checking after
+ * every step that live ranges are aligned, disjoint and inside the region,
+ * that free ranges are coalesced, that a release makes the free range the
+ * arena predicted for it, that a free of a freed range is refused,
+ * and that a refusal leaves no range with room; at the end everything is
+ * freed and the region must be one free range again.  Touches no device
+ * memory and needs no GPU.  Returns 0 when every check held, -1 for bad
+ * arguments, else the step (1-based; ops + 1 or + 2 for the final checks)
+ * that failed.  The paper has no counterpart: this is the server's memory
+ * management. */
+int64_t hf_arena_selftest(uint64_t seed, size_t bytes, int ops);
 
 /* ---- a scene's precompute as one CUDA graph ----
  * The offline precompute of Section 4.2 for many part pairs at once, each

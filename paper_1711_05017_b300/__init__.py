@@ -60,6 +60,13 @@ class Context:
     def reserved_bytes(self):
         return B.lib().hf_ctx_reserved_bytes(self.handle)
 
+    def preload(self):
+        """Load every kernel of the builds, torque and queries now (hf_ctx_preload);
+        returns the number of kernels in the loaded modules."""
+        n = ctypes.c_int()
+        B.check(B.lib().hf_ctx_preload(self.handle, ctypes.byref(n)))
+        return n.value
+
     def profile(self, on=True):
         """Bracket every kernel launch of this context with CUDA events."""
         B.check(B.lib().hf_profile_enable(self.handle, 1 if on else 0))
@@ -500,8 +507,8 @@ class Server:
 
     def trace(self, which):
         """Diagnostic rows since the last read (hf_server_trace): which 0 slow
-        queries, 1 slow scheduler calls; an (n, 6) float64 array."""
-        buf = np.zeros((4096, 6), dtype=np.float64)
+        queries, 1 slow scheduler calls; an (n, 9) float64 array."""
+        buf = np.zeros((4096, 9), dtype=np.float64)
         n = B.lib().hf_server_trace(self.handle, int(which), buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 4096)
         return buf[:n].copy()
 

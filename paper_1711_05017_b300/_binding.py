@@ -29,9 +29,11 @@ SIGNATURES = {
     "hf_version": (ctypes.c_char_p, []),
     "hf_last_error": (ctypes.c_char_p, []),
     "hf_inject_alloc_failure": (None, [ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]),
+    "hf_arena_selftest": (ctypes.c_int64, [ctypes.c_uint64, _sz, _i]),
     "hf_ctx_create": (_i, [_i, _sz, ctypes.POINTER(_vp)]),
     "hf_ctx_destroy": (None, [_vp]),
     "hf_ctx_reserved_bytes": (_sz, [_vp]),
+    "hf_ctx_preload": (_i, [_vp, ctypes.POINTER(_i)]),
     "hf_density_build": (_i, [_vp, _i, _vp, _vp, _vp, _i, _vp, _vp]),
     "hf_part_create": (_i, [_vp, _i, _vp, _i, ctypes.POINTER(_vp), _vp]),
     "hf_part_release": (None, [_vp]),
@@ -122,7 +124,11 @@ class ServerStats(ctypes.Structure):
                 ("running", ctypes.c_int), ("sessions", ctypes.c_int), ("reserved_bytes", ctypes.c_size_t),
                 ("budget_bytes", ctypes.c_size_t), ("chunks_submitted", ctypes.c_int64),
                 ("chunks_completed", ctypes.c_int64), ("chunks_resident", ctypes.c_int), ("chunk_bytes", ctypes.c_size_t),
-                ("pool_reserved_bytes", ctypes.c_size_t), ("pool_reserved_high", ctypes.c_size_t)]
+                ("pool_reserved_bytes", ctypes.c_size_t), ("pool_reserved_high", ctypes.c_size_t),
+                ("arena_bytes", ctypes.c_size_t), ("arena_free_bytes", ctypes.c_size_t),
+                ("arena_largest_free", ctypes.c_size_t), ("arena_refusals", ctypes.c_int64),
+                ("resident_queries", ctypes.c_int64), ("resident_timeouts", ctypes.c_int64),
+                ("resident_live", ctypes.c_int)]
 
 _lib = None
 

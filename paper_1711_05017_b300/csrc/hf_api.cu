@@ -1,6 +1,7 @@
 // hf_api.cu -- the C ABI declared in include/hf.h: contexts, parts, field
 // sets, budget accounting, the float64 host set-up of the rotation
 // neighbourhoods for the torque, and the pose-query entry points.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
@@ -10,6 +11,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <mutex>
 #include <new>
 #include <string>
@@ -159,6 +161,8 @@ struct hf_fieldset {
     bool ready = false;
     size_t bytes = 0;
     cudaStream_t mem_stream = nullptr;  // non-null: stream-ordered device memory, pageable staging
+    hf::Arena *arena = nullptr;  // non-null: the device memory is one range of this arena
+    void *arena_block = nullptr;  // that range
     std::vector<char> pageable_stage;
     void *h_stage = nullptr;     // staging for the per-call uploads (pinned unless mem_stream)
     bool stage_owned_pinned = false;  // h_stage is the set's own pinned allocation
@@ -336,6 +340,54 @@ static void ctx_free(hf_ctx *c) {
 }
 
 extern "C" size_t hf_ctx_budget_bytes(const hf_ctx *c) { return c ? c->budget : 0; }
+
+// Driver entry points for loading whole modules: resolved through the runtime
+// (the library does not link the driver library itself).
+namespace {
+struct ModuleLoader {
+    CUresult (*func_get_module)(CUmodule *, CUfunction) = nullptr;
+    CUresult (*module_function_count)(unsigned int *, CUmodule) = nullptr;
+    CUresult (*module_enumerate)(CUfunction *, unsigned int, CUmodule) = nullptr;
+    CUresult (*func_load)(CUfunction) = nullptr;
+    bool ok = false;
+    ModuleLoader() {
+        auto get = [](const char *name, void **fp) {
+            cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+            return cudaGetDriverEntryPointByVersion(name, fp, 12040, cudaEnableDefault, &q) == cudaSuccess &&
+                   q == cudaDriverEntryPointSuccess && *fp;
+        };
+        ok = get("cuFuncGetModule", (void **)&func_get_module) &&
+             get("cuModuleGetFunctionCount", (void **)&module_function_count) &&
+             get("cuModuleEnumerateFunctions", (void **)&module_enumerate) && get("cuFuncLoad", (void **)&func_load);
+        (void)cudaGetLastError();
+    }
+};
+}  // namespace
+
+extern "C" hf_status hf_ctx_preload(hf_ctx *ctx, int *loaded) {
+    if (!ctx) return fail(HF_EINVAL, "hf_ctx_preload: NULL context");
+    if (loaded) *loaded = 0;
+    static ModuleLoader L;
+    if (!L.ok) return fail(HF_EUNSUPPORTED, "hf_ctx_preload: the driver has no per-function loading");
+    CU(cudaSetDevice(ctx->device));
+    int total = 0;
+    for (const void *anchor : {hf::module_anchor_fft(), hf::module_anchor_kernels(), hf::module_anchor_tc()}) {
+        cudaFunction_t f = nullptr;
+        CU(cudaGetFuncBySymbol(&f, anchor));
+        CUmodule mod = nullptr;
+        unsigned int count = 0;
+        if (L.func_get_module(&mod, (CUfunction)f) != CUDA_SUCCESS || L.module_function_count(&count, mod) != CUDA_SUCCESS)
+            return fail(HF_ECUDA, "hf_ctx_preload: the module of a kernel file");
+        std::vector<CUfunction> fns(count);
+        if (count && L.module_enumerate(fns.data(), count, mod) != CUDA_SUCCESS)
+            return fail(HF_ECUDA, "hf_ctx_preload: enumerating a module's kernels");
+        for (CUfunction fn : fns)
+            if (L.func_load(fn) != CUDA_SUCCESS) return fail(HF_ECUDA, "hf_ctx_preload: loading a kernel");
+        total += (int)count;
+    }
+    if (loaded) *loaded = total;
+    return HF_OK;
+}
 
 extern "C" int hf_tc_timeouts(int reset) { return hf::tc_timeouts(reset != 0); }
 extern "C" int hf_bulk_timeouts(int reset) { return hf::bulk_timeouts(reset != 0); }
@@ -982,22 +1034,25 @@ static size_t fields_spectra(bool pencil) { return pencil ? 5 : 3; }
 
 // h_stage_ext: caller-owned pinned staging for the per-compute uploads (used
 // if at least the set's staging bytes; else the set makes its own); lanes:
-// 1 or 2 pipelines, 0 for the context's choice
+// 1 or 2 pipelines, 0 for the context's choice; arena: where the device
+// memory comes from when not null (EBUDGET when no free range fits)
 static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags, cudaStream_t mem_stream,
                                       hf_fieldset **out, void *h_stage_ext = nullptr, size_t h_stage_ext_bytes = 0,
-                                      int lanes = 0);
+                                      int lanes = 0, hf::Arena *arena = nullptr);
 
 extern "C" hf_status hf_fieldset_create(hf_ctx *ctx, int n, int R, unsigned flags, hf_fieldset **out) {
     return fieldset_create_impl(ctx, n, R, flags, nullptr, out);
 }
 
 hf_status hf_fieldset_create_stream_ordered(hf_ctx *ctx, int n, int R, unsigned flags, cudaStream_t st,
-                                            hf_fieldset **out, void *h_stage, size_t h_stage_bytes, int lanes) {
-    return fieldset_create_impl(ctx, n, R, flags, st, out, h_stage, h_stage_bytes, lanes);
+                                            hf_fieldset **out, void *h_stage, size_t h_stage_bytes, int lanes,
+                                            hf::Arena *arena) {
+    return fieldset_create_impl(ctx, n, R, flags, st, out, h_stage, h_stage_bytes, lanes, arena);
 }
 
 static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags, cudaStream_t mem_stream,
-                                      hf_fieldset **out, void *h_stage_ext, size_t h_stage_ext_bytes, int lanes) {
+                                      hf_fieldset **out, void *h_stage_ext, size_t h_stage_ext_bytes, int lanes,
+                                      hf::Arena *arena) {
     if (!ctx || !out) return fail(HF_EINVAL, "hf_fieldset_create: NULL argument");
     *out = nullptr;
     if (!hf::supported_n(n)) return fail(HF_EUNSUPPORTED, "hf_fieldset_create: N=%d not supported", n);
@@ -1072,7 +1127,34 @@ static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags,
         return fail(HF_EBUDGET, "hf_fieldset_create: %zu bytes exceed the budget", b);
     }
     fs->mem_stream = mem_stream;
+    fs->arena = arena;
+    // from an arena: one range for all the set's device arrays, carved in the
+    // order they are allocated below (each on 256 bytes), so that a set frees
+    // one contiguous range
+    bool arena_short = false;
+    size_t carve = 0, carve_end = 0;
+    if (arena) {
+        const size_t a = hf::Arena::kAlign;
+        auto up = [&](size_t b) { return (b + a - 1) / a * a; };
+        size_t total = up(data_b) + fs->lanes * up(scr_b) + up((size_t)R * 9 * sizeof(float)) +
+                       up((size_t)R * 4 * sizeof(double)) + up((size_t)R * 6 * sizeof(int)) +
+                       up((size_t)R * 18 * sizeof(float)) + up((size_t)R * 18 * sizeof(double));
+        if (!hf::alloc_fails()) {  // (an injected failure is an allocation error, not a short arena)
+            fs->arena_block = arena->alloc(total);
+            arena_short = !fs->arena_block;
+        }
+        carve = (size_t)fs->arena_block;
+        carve_end = carve + total;
+    }
     auto dalloc = [&](void **p, size_t b) {
+        if (arena) {
+            if (!fs->arena_block) return cudaErrorMemoryAllocation;
+            const size_t len = (b + hf::Arena::kAlign - 1) / hf::Arena::kAlign * hf::Arena::kAlign;
+            if (carve + len > carve_end) return cudaErrorMemoryAllocation;
+            *p = (void *)carve;
+            carve += len;
+            return cudaSuccess;
+        }
         return mem_stream ? hf::dmalloc_async(p, b, mem_stream) : hf::dmalloc(p, b);
     };
     cudaError_t e = dalloc((void **)&fs->data, data_b);
@@ -1102,6 +1184,8 @@ static hf_status fieldset_create_impl(hf_ctx *ctx, int n, int R, unsigned flags,
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fs->stage_done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         hf_fieldset_release(fs);
+        if (arena_short)  // within the budget, but no free range of the arena is large enough
+            return fail(HF_EBUDGET, "hf_fieldset_create: no free arena range of the size needed");
         return fail(e == cudaErrorMemoryAllocation ? HF_ENOMEM : HF_ECUDA, "hf_fieldset_create: %s",
                     cudaGetErrorString(e));
     }
@@ -1131,7 +1215,7 @@ extern "C" void hf_fieldset_release(hf_fieldset *fs) {
     if (!fs) return;
     cudaSetDevice(fs->ctx->device);
     auto dfree = [&](void *p) {
-        if (!p) return;
+        if (!p || fs->arena) return;  // an arena set frees its one range below
         if (fs->mem_stream) cudaFreeAsync(p, fs->mem_stream);
         else cudaFree(p);
     };
@@ -1147,6 +1231,7 @@ extern "C" void hf_fieldset_release(hf_fieldset *fs) {
     dfree(fs->d_nbr);
     dfree(fs->d_P);
     dfree(fs->d_P64);
+    if (fs->arena_block) fs->arena->release(fs->arena_block);
     if (fs->stage_owned_pinned) cudaFreeHost(fs->h_stage);
     if (fs->stage_done) cudaEventDestroy(fs->stage_done);
     uncharge(fs->ctx, fs->bytes);
@@ -1157,6 +1242,7 @@ extern "C" void hf_fieldset_release(hf_fieldset *fs) {
 
 int hf_ctx_device(const hf_ctx *c) { return c ? c->device : 0; }
 bool hf_fieldset_is_ready(const hf_fieldset *fs) { return fs && fs->ready; }
+const void *hf_fieldset_arena_block(const hf_fieldset *fs) { return fs ? fs->arena_block : nullptr; }
 void hf_fieldset_mark_ready(hf_fieldset *fs) { fs->ready = true; }
 double *hf_fieldset_device_quats(hf_fieldset *fs) { return fs->d_quat; }
 hf::FieldPtrs hf_fieldset_fields(hf_fieldset *fs, int rot) {
@@ -1458,8 +1544,22 @@ extern "C" hf_status hf_query_batch(const hf_fieldset *fs, const float *d_tq, in
 // One pose query: the pose travels as a kernel argument and the kernel
 // writes its 7 results straight into mapped pinned host memory (h_out, whose
 // device alias is d_out), so a query is one launch and one synchronise.
+// A single query's request for the resident query kernel: the checks of
+// hf_query_on_lane, then the set's geometry and the pose.
+hf_status hf_query_request(const hf_fieldset *fs, const float t[3], const float q[4], int k, hf::QueryReq *rq) {
+    if (!fs || !t || !q || !rq) return fail(HF_EINVAL, "hf_query: NULL argument");
+    if (k < 1 || k > 8 || k > fs->R) return fail(HF_EINVAL, "hf_query: k_blend=%d", k);
+    if (!fs->ready) return fail(HF_ENOTREADY, "hf_query: field set not computed");
+    rq->g = query_geom(fs);
+    for (int a = 0; a < 3; ++a) rq->pose.v[a] = t[a];
+    for (int a = 0; a < 4; ++a) rq->pose.v[3 + a] = q[a];
+    rq->n = fs->n;
+    rq->k = k;
+    return HF_OK;
+}
+
 hf_status hf_query_on_lane(const hf_fieldset *fs, const float t[3], const float q[4], int k, float out7[7],
-                           cudaStream_t st, float *h_out, float *d_out) {
+                           cudaStream_t st, float *h_out, float *d_out, double *launched_ms) {
     if (!fs || !t || !q || !out7) return fail(HF_EINVAL, "hf_query: NULL argument");
     if (k < 1 || k > 8 || k > fs->R) return fail(HF_EINVAL, "hf_query: k_blend=%d", k);
     if (!fs->ready) return fail(HF_ENOTREADY, "hf_query: field set not computed");
@@ -1468,6 +1568,8 @@ hf_status hf_query_on_lane(const hf_fieldset *fs, const float t[3], const float 
     for (int a = 0; a < 3; ++a) pose.v[a] = t[a];
     for (int a = 0; a < 4; ++a) pose.v[3 + a] = q[a];
     CU(hf::run_query_one(query_geom(fs), pose, k, d_out, st));
+    if (launched_ms)
+        *launched_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
     CU(cudaStreamSynchronize(st));
     for (int a = 0; a < 7; ++a) out7[a] = ((volatile float *)h_out)[a];
     return HF_OK;

@@ -6,6 +6,8 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <map>
+#include <mutex>
 
 #include <nvtx3/nvToolsExt.h>
 
@@ -200,6 +202,22 @@ struct Pose7 {
 };
 // one query, pose by value, 7 results to `out` (device or mapped host memory)
 cudaError_t run_query_one(const QueryGeom &g, Pose7 pose, int k, float *out, cudaStream_t st);
+// A lane's mailbox of the resident query kernel, in mapped pinned host memory:
+// the host writes g, pose, n, k and then bumps the lane's request number in
+// the mailbox header; the kernel writes out and then done = that number.
+struct QueryReq {
+    QueryGeom g;
+    Pose7 pose;
+    int n, k;
+};
+struct alignas(128) QueryMail {
+    QueryReq rq;
+    float out[8];
+    unsigned done;
+};
+constexpr int kResidentLanesPerBlock = 15;  // + 1 polling warp: 512 threads
+cudaError_t launch_query_resident(QueryMail *mail, unsigned *req, unsigned *served, const unsigned *stop, int lanes,
+                                  unsigned long long life_ns, cudaStream_t st);
 
 // An NVTX range over a library call (a profiler with NVTX support shows the
 // call's kernels under its name; without one the push and pop do nothing).
@@ -209,6 +227,45 @@ struct Range {
     Range(const Range &) = delete;
     Range &operator=(const Range &) = delete;
 };
+
+// A device region handed out by host-side bookkeeping: best-fit over a free
+// list kept sorted by offset and coalesced on every free.  Allocating and
+// freeing are host operations with no CUDA call, so a server whose builds
+// take their field sets from an arena never maps or unmaps device memory
+// while its queries run.  Ranges start on 256 bytes, ranges of 2 MB or more
+// on 2 MB (one large page each).  Thread-safe.  The caller owns the region:
+// reset() adopts [base, base + bytes) with everything free, and the caller
+// frees the region after the last range is released.
+class Arena {
+  public:
+    static constexpr size_t kAlign = 256, kLargeAlign = size_t(2) << 20;
+    void reset(uintptr_t base, size_t bytes);
+    void *alloc(size_t bytes);  // nullptr when no free range fits
+    bool release(void *p);      // false if p is not a live range's start
+    bool owns(const void *p) const;
+    size_t capacity() const;
+    size_t free_bytes() const;
+    size_t largest_free() const;
+    int64_t failures() const;  // allocations refused for want of a range
+    size_t merged_if_released(const void *p) const;  // the free range p's release would make (0: not live)
+    size_t free_range_containing(const void *p) const;  // length of the free range holding p (0: none)
+    bool check() const;        // the invariants (tests)
+    size_t live_count() const;
+
+  private:
+    mutable std::mutex mu_;
+    uintptr_t base_ = 0;
+    size_t size_ = 0, free_ = 0;
+    int64_t failures_ = 0;
+    std::map<size_t, size_t> free_list_;  // offset -> length: disjoint, no two adjacent
+    std::map<size_t, size_t> live_;       // offset -> length
+};
+
+// One kernel of each file whose device code the field builds, the queries and
+// the precision variants use; hf_ctx_preload loads their modules whole.
+const void *module_anchor_fft();
+const void *module_anchor_kernels();
+const void *module_anchor_tc();
 
 // Allocation-failure injection for the error paths' tests (hf_inject_alloc_failure):
 // every device, array and pinned-host allocation the library makes goes
@@ -240,6 +297,11 @@ inline cudaError_t dmalloc_array(cudaArray_t *a, const cudaChannelFormatDesc *fd
     return cudaMallocArray(a, fd, w, h, flags);
 }
 template <class T>
+inline cudaError_t hmalloc_mapped(T **p, size_t b) {
+    if (alloc_fails()) return cudaErrorMemoryAllocation;
+    return cudaHostAlloc((void **)p, b, cudaHostAllocMapped);
+}
+template <class T>
 inline cudaError_t hmalloc(T **p, size_t b) {
     if (alloc_fails()) return cudaErrorMemoryAllocation;
     return cudaMallocHost((void **)p, b);
@@ -261,6 +323,7 @@ void hf_part_retain(const hf_part *p);
 void hf_part_drop(const hf_part *p);
 // whether the set's last compute enqueued all of its work
 bool hf_fieldset_is_ready(const hf_fieldset *fs);
+const void *hf_fieldset_arena_block(const hf_fieldset *fs);  // its arena range, or null
 void hf_fieldset_mark_ready(hf_fieldset *fs);
 double *hf_fieldset_device_quats(hf_fieldset *fs);
 // the E, Fx, Fy, Fz pointers of rotation rot of a set (rot_stride per rotation)
@@ -284,10 +347,12 @@ hf_status hf_set_launch(hf_ctx *ctx, const hf_part *s1, const hf_part *s2, hf_fi
 // `st` (no device-wide synchronisation on create or release); h_stage: a
 // caller-owned pinned buffer for its uploads (used if at least R * 308 bytes;
 // the caller keeps it unused by others until the set's uploads are done),
-// else pageable staging; lanes: 1 or 2 pipelines, 0 for the context's choice
+// else pageable staging; lanes: 1 or 2 pipelines, 0 for the context's choice;
+// arena: when not null the device memory is ranges of it (returned to it on
+// release, with no CUDA call), HF_EBUDGET when no free range fits
 hf_status hf_fieldset_create_stream_ordered(hf_ctx *ctx, int n, int R, unsigned flags, cudaStream_t st,
                                             hf_fieldset **out, void *h_stage = nullptr, size_t h_stage_bytes = 0,
-                                            int lanes = 0);
+                                            int lanes = 0, hf::Arena *arena = nullptr);
 // checkpoints (hf_api.cu): a computed field set as NPY arrays on an open
 // file, and back (device memory stream-ordered on mem_stream if non-null);
 // the NPY array helpers and the file tag for the server's session files
@@ -299,5 +364,10 @@ bool hf_ckpt_read_i64(FILE *f, std::vector<int64_t> &v);
 bool hf_ckpt_read_f32(FILE *f, std::vector<int64_t> &shape, std::vector<float> &v);
 int64_t hf_ckpt_magic();
 int64_t hf_ckpt_version();
+// a single query's request for the resident query kernel (the checks of
+// hf_query); HF_EINVAL / HF_ENOTREADY as hf_query
+hf_status hf_query_request(const hf_fieldset *fs, const float t[3], const float q[4], int k, hf::QueryReq *rq);
+// launched_ms, when not NULL, receives the steady-clock time (ms) at which
+// the query kernel's launch call returned
 hf_status hf_query_on_lane(const hf_fieldset *fs, const float t[3], const float q[4], int k, float out7[7],
-                           cudaStream_t st, float *h_out, float *d_out);
+                           cudaStream_t st, float *h_out, float *d_out, double *launched_ms = nullptr);

@@ -330,8 +330,17 @@ __device__ __forceinline__ bool better(double da, int ia, double db, int ib) {
     return da > db || (da == db && ia < ib);
 }
 
+// Loads of the field sets by the queries: through L1 in a kernel launched
+// after the set was built, at L2 (.cg) in the resident query kernel, which
+// outlives builds that may reuse the addresses of sets it read earlier.
+template <bool CG, class T>
+__device__ __forceinline__ T ld_set(const T *p) {
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
 // One query by one warp: `in` = (t, q), 7 results to `outp`.
-template <int N>
+template <int N, bool CG = false>
 __device__ __forceinline__ void query_warp(const QueryGeom &g, const float *in, int k, float *outp,
                                            float *part) {
     const int lane = threadIdx.x & 31;
@@ -346,7 +355,8 @@ __device__ __forceinline__ void query_warp(const QueryGeom &g, const float *in, 
     for (int s = 0; s < kQueryMaxK; ++s) { bd[s] = -1.0; bi[s] = 0x7fffffff; }
     for (int j = lane; j < g.R; j += 32) {
         const double *qj = g.quats + 4 * (size_t)j;
-        double d = fabs(q[0] * qj[0] + q[1] * qj[1] + q[2] * qj[2] + q[3] * qj[3]);
+        double d = fabs(q[0] * ld_set<CG>(qj) + q[1] * ld_set<CG>(qj + 1) + q[2] * ld_set<CG>(qj + 2) +
+                        q[3] * ld_set<CG>(qj + 3));
         d = fmin(d, 1.0);
         int ij = j;
 #pragma unroll
@@ -405,10 +415,12 @@ __device__ __forceinline__ void query_warp(const QueryGeom &g, const float *in, 
             const float *fb = g.base + (size_t)sel_i[s] * g.rot_stride + (size_t)g.field_slot[f] * n3;
             const float *r00 = fb + ((size_t)z0 * N + y0) * N, *r01 = fb + ((size_t)z0 * N + y1) * N;
             const float *r10 = fb + ((size_t)z1 * N + y0) * N, *r11 = fb + ((size_t)z1 * N + y1) * N;
-            const float c00 = fmaf(ax, r00[x1] - r00[x0], r00[x0]);
-            const float c01 = fmaf(ax, r01[x1] - r01[x0], r01[x0]);
-            const float c10 = fmaf(ax, r10[x1] - r10[x0], r10[x0]);
-            const float c11 = fmaf(ax, r11[x1] - r11[x0], r11[x0]);
+            const float v00 = ld_set<CG>(r00 + x0), v01 = ld_set<CG>(r01 + x0);
+            const float v10 = ld_set<CG>(r10 + x0), v11 = ld_set<CG>(r11 + x0);
+            const float c00 = fmaf(ax, ld_set<CG>(r00 + x1) - v00, v00);
+            const float c01 = fmaf(ax, ld_set<CG>(r01 + x1) - v01, v01);
+            const float c10 = fmaf(ax, ld_set<CG>(r10 + x1) - v10, v10);
+            const float c11 = fmaf(ax, ld_set<CG>(r11 + x1) - v11, v11);
             const float c0 = fmaf(ay, c01 - c00, c00), c1 = fmaf(ay, c11 - c10, c10);
             v = fmaf(az, c1 - c0, c0);
         }
@@ -437,6 +449,121 @@ template <int N>
 __global__ void query_one_kernel(QueryGeom g, Pose7 pose, int k, float *out) {
     __shared__ float part[7 * kQueryMaxK];
     query_warp<N>(g, pose.v, k, out, part);
+}
+
+// The resident query kernel: a query answered without a launch.  The host
+// writes a lane's request (set geometry, pose, k) into the lane's mailbox in
+// mapped pinned memory, then bumps the lane's request number in the mailbox
+// header; warp 0 of the block polls the header, and the warp that serves the
+// lane runs the query and writes the 7 results and the request's number back.
+// An instance serves for `life_ns` of the global timer (or until *stop) and
+// returns: every wait checks that deadline, so no instance outlives it by
+// more than one query.  The host keeps the next instance queued on the same
+// stream behind the running one.  served[] (device memory) carries each
+// lane's last answered request number from one instance to the next.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned ld_acquire_sys(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_sys(unsigned *p, unsigned v) {
+    asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <int N>
+__device__ void query_resident_serve(const QueryReq &r, float *part, float *out) {
+    query_warp<N, true>(r.g, r.pose.v, r.k, out, part);
+}
+
+__global__ void __launch_bounds__(32 * (kResidentLanesPerBlock + 1))
+    query_resident_kernel(QueryMail *mail, unsigned *req, unsigned *served, const unsigned *stop, int lanes,
+                          unsigned long long life_ns, unsigned long long max_polls) {
+    __shared__ volatile unsigned s_pend[kResidentLanesPerBlock];
+    __shared__ volatile int s_quit;
+    __shared__ float part[kResidentLanesPerBlock][7 * kQueryMaxK];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int base = blockIdx.x * kResidentLanesPerBlock;
+    const int nl = min(kResidentLanesPerBlock, lanes - base);
+    if (threadIdx.x < kResidentLanesPerBlock) s_pend[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) s_quit = 0;
+    __syncthreads();
+    const unsigned long long t_end = global_ns() + life_ns;
+    if (warp == 0) {
+        // the poller: lane j watches mailbox base + j
+        unsigned last = lane < nl ? served[base + lane] : 0u;
+        for (unsigned long long it = 0; it < max_polls; ++it) {
+            // warp-uniform: every lane leaves the loop together
+            if (__any_sync(0xffffffffu, global_ns() > t_end || ld_acquire_sys(stop) != 0u)) break;
+            if (lane < nl && s_pend[lane] == 0u) {
+                const unsigned cur = ld_acquire_sys(req + base + lane);
+                if (cur != last) {
+                    last = cur;
+                    s_pend[lane] = cur;
+                    __threadfence_block();
+                }
+            }
+            __syncwarp();
+            __nanosleep(256);
+        }
+        if (lane == 0) s_quit = 1;
+        return;
+    }
+    const int j = warp - 1;  // the lane this warp serves
+    if (j >= nl) return;
+    QueryMail &m = mail[base + j];
+    constexpr int kReqWords = sizeof(QueryReq) / 4;
+    static_assert(sizeof(QueryReq) % 4 == 0 && kReqWords <= 32, "one request word per lane");
+    // bounded by the poller's exit (s_quit); the iteration bound is a second
+    // stop, looser than the poller's since a sleep may end early
+    for (unsigned long long it = 0; it < 8 * max_polls; ++it) {
+        const unsigned p = __shfl_sync(0xffffffffu, s_pend[j], 0);  // warp-uniform
+        if (p != 0u) {
+            __threadfence_block();  // the poller acquired the request's number before publishing it here
+            // the request, one word per lane read past the caches, then gathered
+            const unsigned wv = lane < kReqWords ? __ldcv(reinterpret_cast<const unsigned *>(&m.rq) + lane) : 0u;
+            QueryReq r;
+            unsigned *rw = reinterpret_cast<unsigned *>(&r);
+#pragma unroll
+            for (int w = 0; w < kReqWords; ++w) rw[w] = __shfl_sync(0xffffffffu, wv, w);
+            float *out = m.out;
+            switch (r.n) {
+                case 32: query_resident_serve<32>(r, part[j], out); break;
+                case 64: query_resident_serve<64>(r, part[j], out); break;
+                case 96: query_resident_serve<96>(r, part[j], out); break;
+                case 128: query_resident_serve<128>(r, part[j], out); break;
+                case 256: query_resident_serve<256>(r, part[j], out); break;
+                default:
+                    if (lane < 7) out[lane] = __int_as_float(0x7fc00000);  // NaN: an unsupported size
+            }
+            __threadfence_system();  // each lane's results before the number that publishes them
+            __syncwarp();
+            if (lane == 0) {
+                st_release_sys(&m.done, p);
+                served[base + j] = p;
+                s_pend[j] = 0u;
+            }
+            __syncwarp();
+            continue;
+        }
+        if (__shfl_sync(0xffffffffu, s_quit, 0)) break;
+        __nanosleep(128);
+    }
+}
+
+cudaError_t launch_query_resident(QueryMail *mail, unsigned *req, unsigned *served, const unsigned *stop, int lanes,
+                                  unsigned long long life_ns, cudaStream_t st) {
+    if (lanes <= 0) return cudaErrorInvalidValue;
+    const int blocks = (lanes + kResidentLanesPerBlock - 1) / kResidentLanesPerBlock;
+    // an iteration bound besides the timer: at least 128 ns per poll
+    const unsigned long long max_polls = life_ns / 128 + 1024;
+    query_resident_kernel<<<blocks, 32 * (kResidentLanesPerBlock + 1), 0, st>>>(mail, req, served, stop, lanes,
+                                                                              life_ns, max_polls);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------- launchers
@@ -488,5 +615,10 @@ cudaError_t run_query(const QueryGeom &g, const float *tq, int Q, int k, float *
     HF_DISPATCH_K(g.n, (query_kernel<NN><<<blocks, 32 * kQueryWarps, 0, st>>>(g, tq, Q, k, out)));
     return cudaGetLastError();
 }
+
+// Never launched: its address names this file's device-code module, which
+// hf_ctx_preload loads whole.
+__global__ void module_anchor_kernels_kernel() {}
+const void *module_anchor_kernels() { return (const void *)&module_anchor_kernels_kernel; }
 
 }  // namespace hf

@@ -31,7 +31,9 @@
 #include <stdarg.h>
 #include <stdint.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
+#include <sys/resource.h>
 
 #include <algorithm>
 #include <atomic>
@@ -126,36 +128,49 @@ struct Job {  // one chunk of a request
 // A session's published field data: one set per chunk of one request.  The
 // request (routing tables) is fixed; the slots are atomic shared pointers
 // and the use times atomics, so readers take no lock.
+// The published pointers are std::atomic<std::shared_ptr>: each guards itself
+// with a spin bit held for a reference-count update, so readers of different
+// sessions never share a lock (the free-function atomic_load/atomic_store on
+// a shared_ptr share a small pool of mutexes across all objects).
 struct Published {
     std::shared_ptr<Request> req;
-    std::unique_ptr<std::shared_ptr<SetHolder>[]> chunk;
+    std::unique_ptr<std::atomic<std::shared_ptr<SetHolder>>[]> chunk;
     std::unique_ptr<std::atomic<double>[]> last_use;
     explicit Published(const std::shared_ptr<Request> &r)
-        : req(r), chunk(new std::shared_ptr<SetHolder>[r->nchunks]), last_use(new std::atomic<double>[r->nchunks]) {
+        : req(r),
+          chunk(new std::atomic<std::shared_ptr<SetHolder>>[r->nchunks]),
+          last_use(new std::atomic<double>[r->nchunks]) {
         for (int c = 0; c < r->nchunks; ++c) last_use[c].store(0.0);
     }
-    std::shared_ptr<SetHolder> get(int c) const { return std::atomic_load(&chunk[c]); }
-    void set(int c, std::shared_ptr<SetHolder> h) { std::atomic_store(&chunk[c], std::move(h)); }
+    std::shared_ptr<SetHolder> get(int c) const { return chunk[c].load(); }
+    void set(int c, std::shared_ptr<SetHolder> h) { chunk[c].store(std::move(h)); }
 };
 
 struct Session {
     std::atomic<bool> open{false};
     const hf_part *s1 = nullptr, *s2 = nullptr;  // held while open; fixed once the session is visible
     int n = 0;
-    std::shared_ptr<Published> current_;         // atomic access only
+    std::atomic<std::shared_ptr<Published>> current_;
     std::atomic<int64_t> answered{0}, not_ready{0};
-    std::shared_ptr<Published> current() const { return std::atomic_load(&current_); }
-    void set_current(std::shared_ptr<Published> p) { std::atomic_store(&current_, std::move(p)); }
+    std::shared_ptr<Published> current() const { return current_.load(); }
+    void set_current(std::shared_ptr<Published> p) { current_.store(std::move(p)); }
 };
 
 struct Lane {
     cudaStream_t st = nullptr;
     float *h_out = nullptr, *d_out = nullptr;  // mapped pinned answer mailbox and its device alias
+    // the lane's mailbox of the resident query kernel: the last request number
+    // posted; the set the kernel may still read for it; whether a request
+    // timed out and is still outstanding (the mailbox is then not written
+    // again until the kernel has answered it)
+    unsigned seq = 0;
+    std::shared_ptr<SetHolder> hold;
+    bool outstanding = false;
 };
 
 // fixed-size ring of diagnostic rows (slow queries, slow scheduler calls)
 struct TraceRing {
-    static constexpr int kRows = 4096, kCols = 6;
+    static constexpr int kRows = 4096, kCols = 9;
     std::mutex mu;
     std::vector<double> rows = std::vector<double>((size_t)kRows * kCols);
     int head = 0, count = 0;
@@ -246,12 +261,117 @@ struct hf_server {
     LogHist query_hist, build_hist;  // answered queries (us), finished requests submit -> published (us)
     std::mutex log_mu;               // the metrics log's open and close
     std::unique_ptr<MetricsLog> log;
-    std::mutex lane_mu;
     std::vector<Lane> lanes;
-    std::vector<int> free_lanes;
-    std::condition_variable lane_cv;
+    std::atomic<uint64_t> free_lanes{0};  // bit i: lane i is free (at most 64 lanes)
     TraceRing slow_queries, slow_calls;
+    void *arena_mem = nullptr;  // the field-set arena's device region (null: the pool serves)
+    hf::Arena arena;
+    // the resident query kernel: mapped pinned region of the lanes' request
+    // numbers (256 B), the stop flag (256 B) and the lanes' mailboxes; each
+    // lane's last answered request number on the device; the stream the
+    // instances queue on and the thread that keeps two of them queued
+    char *h_res = nullptr, *d_res = nullptr;
+    unsigned *d_served = nullptr;
+    cudaStream_t res_st = nullptr;
+    std::thread res_keeper;
+    std::atomic<bool> res_live{false}, res_quit{false};
+    std::atomic<int64_t> res_answered{0}, res_timeouts{0};
+    unsigned *h_req() { return reinterpret_cast<unsigned *>(h_res); }
+    unsigned *h_stop() { return reinterpret_cast<unsigned *>(h_res + 256); }
+    hf::QueryMail *h_mail() { return reinterpret_cast<hf::QueryMail *>(h_res + 512); }
 };
+
+// an instance of the resident query kernel serves this long (short, since a
+// device-wide synchronisation, which cudaFree implies, waits for the running
+// and the queued instance); a request not answered within kResidentWaitMs
+// goes to the launch path instead
+constexpr unsigned long long kResidentLifeNs = 10ull * 1000 * 1000;
+constexpr double kResidentWaitMs = 20.0;
+
+static void cpu_relax() {
+#if defined(__x86_64__) || defined(__i386__)
+    __builtin_ia32_pause();
+#endif
+}
+
+// Keeps two instances of the resident query kernel queued on res_st, so that
+// the next one starts on the device as the running one ends, with no launch
+// on the host in between; on stop, raises the stop flag and waits for them.
+static void resident_keeper(hf_server *s) {
+    cudaSetDevice(s->device);
+    constexpr int kRing = 3;
+    cudaEvent_t ev[kRing] = {};
+    bool ok = true;
+    for (auto &e : ev) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    auto *d_req = reinterpret_cast<unsigned *>(s->d_res);
+    auto *d_stop = reinterpret_cast<const unsigned *>(s->d_res + 256);
+    auto *d_mail = reinterpret_cast<hf::QueryMail *>(s->d_res + 512);
+    const int lanes = (int)s->lanes.size();
+    int head = 0, queued = 0;
+    while (ok && !s->res_quit.load()) {
+        if (queued < 2) {
+            const int slot = (head + queued) % kRing;
+            if (hf::launch_query_resident(d_mail, d_req, s->d_served, d_stop, lanes, kResidentLifeNs, s->res_st) !=
+                    cudaSuccess ||
+                cudaEventRecord(ev[slot], s->res_st) != cudaSuccess) {
+                ok = false;
+                break;
+            }
+            ++queued;
+            s->res_live.store(true, std::memory_order_release);
+            continue;
+        }
+        const cudaError_t q = cudaEventQuery(ev[head]);
+        if (q == cudaSuccess) {
+            head = (head + 1) % kRing;
+            --queued;
+            continue;
+        }
+        if (q != cudaErrorNotReady) {
+            ok = false;
+            break;
+        }
+        std::this_thread::sleep_for(std::chrono::milliseconds(2));
+    }
+    s->res_live.store(false, std::memory_order_release);
+    (void)cudaGetLastError();
+    __atomic_store_n(s->h_stop(), 1u, __ATOMIC_RELEASE);  // the running instance ends at its next poll
+    cudaStreamSynchronize(s->res_st);
+    for (auto e : ev)
+        if (e) cudaEventDestroy(e);
+}
+
+// A query through the resident kernel on lane li: post the request, wait
+// (spinning, bounded) for its answer.  *posted receives the time the request
+// was posted.  After kResidentWaitMs the query runs by launch instead, and the
+// lane's mailbox stays untouched until the kernel has answered the request.
+static hf_status resident_query(hf_server *s, int li, Lane &L, const std::shared_ptr<SetHolder> &set,
+                                const float t[3], const float q[4], int k, float out7[7], double *posted) {
+    hf::QueryReq rq;
+    hf_status st = hf_query_request(set->fs, t, q, k, &rq);
+    if (st != HF_OK) return st;
+    hf::QueryMail *m = s->h_mail() + li;
+    m->rq = rq;
+    unsigned seq = L.seq + 1;
+    if (seq == 0) seq = 1;
+    L.seq = seq;
+    L.hold = set;  // the set outlives the kernel's reads of it
+    __atomic_store_n(s->h_req() + li, seq, __ATOMIC_RELEASE);
+    *posted = now_ms();
+    const double give_up = *posted + kResidentWaitMs;
+    for (unsigned spins = 1; __atomic_load_n(&m->done, __ATOMIC_ACQUIRE) != seq; ++spins) {
+        if ((spins & 255u) == 0 && now_ms() > give_up) {
+            L.outstanding = true;
+            s->res_timeouts++;
+            return hf_query_on_lane(set->fs, t, q, k, out7, L.st, L.h_out, L.d_out);
+        }
+        cpu_relax();
+    }
+    for (int a = 0; a < 7; ++a) out7[a] = ((volatile float *)m->out)[a];
+    L.hold.reset();
+    s->res_answered++;
+    return HF_OK;
+}
 
 static Session *session_at(hf_server *s, int session) {
     if (session < 0 || session >= s->nsessions.load(std::memory_order_acquire)) return nullptr;
@@ -262,7 +382,7 @@ static Session *session_at(hf_server *s, int session) {
 static void trace_call(hf_server *s, int kind, double t_start, double t_end) {
     const double us = (t_end - t_start) * 1000.0;
     if (us < kSlowCallUs) return;
-    const double row[TraceRing::kCols] = {t_start - s->t0, us, (double)kind, 0, 0, 0};
+    const double row[TraceRing::kCols] = {t_start - s->t0, us, (double)kind, 0, 0, 0, 0, 0, 0};
     s->slow_calls.put(row);
 }
 
@@ -293,8 +413,11 @@ static bool publish(hf_server *s, const std::shared_ptr<Job> &j) {
 
 // evict one published chunk (server mutex held): the least recently queried
 // idle one; if every resident chunk was queried within kIdleMs, the largest
-// (the fewest sessions lose their data per byte freed)
-static bool evict_one(hf_server *s) {
+// (the fewest sessions lose their data per byte freed).  for_range: the
+// budget had room but the arena had no free range of the size wanted, so
+// among idle (else all) chunks the one whose release makes the largest free
+// range goes first
+static bool evict_one(hf_server *s, bool for_range = false) {
     const double now = now_ms();
     Published *bp = nullptr;
     int bc = -1;
@@ -310,17 +433,20 @@ static bool evict_one(hf_server *s) {
             if (!h) continue;
             const double t = cur->last_use[c].load();
             const bool idle = now - t > kIdleMs;
+            // the size that ranks it: its bytes, or the free range its release makes
+            const size_t sz = for_range ? s->arena.merged_if_released(hf_fieldset_arena_block(h->fs)) : h->bytes;
             bool better;
             if (!bp) better = true;
             else if (idle != b_idle) better = idle;
+            else if (for_range) better = sz > bb || (sz == bb && t < bt);
             else if (idle) better = t < bt;
-            else better = h->bytes > bb || (h->bytes == bb && t < bt);
+            else better = sz > bb || (sz == bb && t < bt);
             if (better) {
                 bp = cur.get();
                 bc = c;
                 b_idle = idle;
                 bt = t;
-                bb = h->bytes;
+                bb = sz;
             }
         }
     }
@@ -430,12 +556,14 @@ static void scheduler(hf_server *s) {
         free_retired(s);
         // allocate and launch outside the mutex
         hf_fieldset *fs = nullptr;
+        const int64_t refusals0 = s->arena.failures();
         double a = now_ms();
         // one pipeline per build (the server runs builds side by side), its
         // uploads staged in the stream's pinned buffer: a stream takes its
         // next build only after the last one has completed
         hf_status st = hf_fieldset_create_stream_ordered(s->ctx, n, cand->R, cand->req->flags, s->streams[si], &fs,
-                                                         s->stage[si], kStageBytes, 1);
+                                                         s->stage[si], kStageBytes, 1,
+                                                         s->arena_mem ? &s->arena : nullptr);
         trace_call(s, 0, a, now_ms());
         if (st == HF_EBUDGET) {
             hf_part_drop(p1);
@@ -444,7 +572,7 @@ static void scheduler(hf_server *s) {
             s->stream_busy[si] = 0;
             if (s->running.empty()) {
                 // nothing in flight will free memory: make room from published chunks
-                if (evict_one(s)) {
+                if (evict_one(s, s->arena.failures() > refusals0)) {
                     s->queue.push_front(cand);  // keep its place; retry once the set is freed
                 } else {
                     cand->req->error = "the chunk cannot fit next to the resident parts";
@@ -522,31 +650,41 @@ extern "C" hf_status hf_server_create(hf_ctx *ctx, int max_inflight, int query_l
     s->t0 = now_ms();
     s->lat_us.resize(kLatRing);  // no allocation on the query path
     cudaGetDevice(&s->device);
-    // the builds allocate stream-ordered from the device's default pool: keep
-    // what it has reserved instead of handing it back at every
-    // synchronisation, so that later builds do not map memory again while
-    // queries launch (the memory is returned when the server is destroyed)
-    cudaMemPool_t pool = nullptr;
-    cudaError_t e = cudaDeviceGetDefaultMemPool(&pool, s->device);
-    if (e == cudaSuccess) {
-        uint64_t keep = UINT64_MAX;
-        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
-    }
-    // and reserve the budget in the pool now: mapping tens of GB on the first
-    // builds took the driver 10+ ms, during which query launches waited
+    // every kernel the builds and queries can launch, loaded now: a kernel
+    // loaded lazily at its first launch held up all query lanes' launches
+    // while the driver loaded it (a driver without per-function loading
+    // keeps lazy loading)
+    (void)hf_ctx_preload(ctx, nullptr);
+    // The builds' field sets come from one device arena of the context's
+    // remaining budget (up to the free memory less 4 GB), carved by host
+    // bookkeeping: a build then maps no memory while queries launch (pool
+    // growth and remapping held up other threads' launches for milliseconds).
+    // Without a budget, or without room for the arena, they allocate
+    // stream-ordered from the device's default pool, which keeps what it has
+    // reserved instead of handing it back at every synchronisation.
+    // The arena holds a quarter more than the budget it serves (HF_ARENA_SLACK,
+    // percent): the budget caps the live field data, and the slack absorbs
+    // the gaps that sets of mixed sizes leave between them.
+    cudaError_t e = cudaSuccess;
     const size_t budget = hf_ctx_budget_bytes(ctx), held = hf_ctx_reserved_bytes(ctx);
     size_t free_b = 0, total_b = 0;
-    if (e == cudaSuccess && budget > held && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+    if (budget > held && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
         const size_t margin = (size_t)4 << 30;
-        const size_t want = std::min(budget - held, free_b > margin ? free_b - margin : 0);
-        cudaStream_t tmp = nullptr;
-        void *blk = nullptr;
-        if (want > 0 && cudaStreamCreateWithFlags(&tmp, cudaStreamNonBlocking) == cudaSuccess) {
-            if (cudaMallocAsync(&blk, want, tmp) == cudaSuccess) cudaFreeAsync(blk, tmp);
-            cudaStreamSynchronize(tmp);
-            cudaStreamDestroy(tmp);
+        const char *ev = getenv("HF_ARENA_SLACK");
+        const long slack = ev ? std::max(0L, std::min(400L, atol(ev))) : 25L;
+        const size_t span = budget - held, with_slack = span + span / 100 * (size_t)slack;
+        const size_t want = std::min(with_slack, free_b > margin ? free_b - margin : 0);
+        if (want > 0 && hf::dmalloc(&s->arena_mem, want) == cudaSuccess) s->arena.reset((uintptr_t)s->arena_mem, want);
+        else s->arena_mem = nullptr;
+        (void)cudaGetLastError();  // an arena that does not fit is not an error: the pool serves
+    }
+    if (!s->arena_mem) {
+        cudaMemPool_t pool = nullptr;
+        e = cudaDeviceGetDefaultMemPool(&pool, s->device);
+        if (e == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;
+            e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
         }
-        (void)cudaGetLastError();  // a reservation that does not fit is not an error
     }
     int lo = 0, hi = 0;
     if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
@@ -565,11 +703,33 @@ extern "C" hf_status hf_server_create(hf_ctx *ctx, int max_inflight, int query_l
         e = cudaStreamCreateWithPriority(&L.st, cudaStreamNonBlocking, hi);
         if (e == cudaSuccess) e = cudaHostAlloc(&L.h_out, 8 * sizeof(float), cudaHostAllocMapped);
         if (e == cudaSuccess) e = cudaHostGetDevicePointer(&L.d_out, L.h_out, 0);
-        s->free_lanes.push_back(i);
+        s->free_lanes.fetch_or(uint64_t(1) << i);
     }
     if (e != cudaSuccess) {
         hf_server_destroy(s);
         return srv_fail(HF_ECUDA, "hf_server_create: %s", cudaGetErrorString(e));
+    }
+    // the resident query kernel (HF_RESIDENT_QUERIES=0: every query by launch);
+    // without its memory or stream the queries launch, which is not an error
+    const char *rev = getenv("HF_RESIDENT_QUERIES");
+    if (!(rev && atoi(rev) == 0)) {
+        const size_t rbytes = 512 + sizeof(hf::QueryMail) * (size_t)query_lanes;
+        void *h = nullptr, *d = nullptr;
+        bool ok = hf::hmalloc_mapped(&h, rbytes) == cudaSuccess;
+        if (ok) {
+            s->h_res = (char *)h;
+            memset(h, 0, rbytes);
+            ok = cudaHostGetDevicePointer(&d, h, 0) == cudaSuccess;
+        }
+        if (ok) {
+            s->d_res = (char *)d;
+            ok = hf::dmalloc(&s->d_served, sizeof(unsigned) * (size_t)query_lanes) == cudaSuccess &&
+                 cudaMemset(s->d_served, 0, sizeof(unsigned) * (size_t)query_lanes) == cudaSuccess &&
+                 cudaStreamCreateWithPriority(&s->res_st, cudaStreamNonBlocking, hi) == cudaSuccess &&
+                 cudaStreamSynchronize(s->res_st) == cudaSuccess;
+        }
+        if (ok) s->res_keeper = std::thread(resident_keeper, s);
+        (void)cudaGetLastError();
     }
     s->sched = std::thread(scheduler, s);
     *out = s;
@@ -592,6 +752,9 @@ extern "C" void hf_server_destroy(hf_server *s) {
     }
     s->cv.notify_all();
     if (s->sched.joinable()) s->sched.join();
+    s->res_quit.store(true);
+    if (s->res_keeper.joinable()) s->res_keeper.join();  // no instance runs after this
+    for (auto &L : s->lanes) L.hold.reset();
     for (int i = 0; i < s->nsessions.load(); ++i) s->sessions[i].set_current(nullptr);
     cudaDeviceSynchronize();
     free_retired(s);
@@ -609,10 +772,17 @@ extern "C" void hf_server_destroy(hf_server *s) {
         if (L.st) cudaStreamDestroy(L.st);
         if (L.h_out) cudaFreeHost(L.h_out);
     }
-    cudaMemPool_t pool = nullptr;
-    if (cudaDeviceGetDefaultMemPool(&pool, s->device) == cudaSuccess) {
-        cudaDeviceSynchronize();
-        cudaMemPoolTrimTo(pool, 0);
+    if (s->res_st) cudaStreamDestroy(s->res_st);
+    if (s->d_served) cudaFree(s->d_served);
+    if (s->h_res) cudaFreeHost(s->h_res);
+    if (s->arena_mem) {
+        cudaFree(s->arena_mem);  // every set carved from it was released above
+    } else {
+        cudaMemPool_t pool = nullptr;
+        if (cudaDeviceGetDefaultMemPool(&pool, s->device) == cudaSuccess) {
+            cudaDeviceSynchronize();
+            cudaMemPoolTrimTo(pool, 0);
+        }
     }
     hf_ctx *c = s->ctx;
     delete s;
@@ -860,6 +1030,8 @@ extern "C" hf_status hf_server_query(hf_server *s, int session, const float t[3]
                                      float out7[7]) {
     if (!s || !t || !q || !out7) return srv_fail(HF_EINVAL, "hf_server_query: NULL argument");
     const double t0 = now_ms();
+    struct rusage ru0;
+    getrusage(RUSAGE_THREAD, &ru0);
     hf_status st = HF_OK;
     std::shared_ptr<SetHolder> set = session_set(s, session, -1, q, nullptr, &st);
     Session *ss = session_at(s, session);
@@ -870,20 +1042,33 @@ extern "C" hf_status hf_server_query(hf_server *s, int session, const float t[3]
     const double t1 = now_ms();
     int li;
     {
-        std::unique_lock<std::mutex> g(s->lane_mu);
-        s->lane_cv.wait(g, [&] { return !s->free_lanes.empty(); });
-        li = s->free_lanes.back();
-        s->free_lanes.pop_back();
+        // take the lowest free lane without a lock; with every lane busy
+        // (more querying threads than lanes) yield until one frees
+        uint64_t m = s->free_lanes.load(std::memory_order_acquire);
+        for (;;) {
+            if (m == 0) {
+                std::this_thread::yield();
+                m = s->free_lanes.load(std::memory_order_acquire);
+                continue;
+            }
+            li = __builtin_ctzll(m);
+            if (s->free_lanes.compare_exchange_weak(m, m & ~(uint64_t(1) << li), std::memory_order_acquire))
+                break;
+        }
     }
     const double t2 = now_ms();
     Lane &L = s->lanes[li];
-    st = hf_query_on_lane(set->fs, t, q, k, out7, L.st, L.h_out, L.d_out);
-    const double t3 = now_ms();
-    {
-        std::lock_guard<std::mutex> g(s->lane_mu);
-        s->free_lanes.push_back(li);
+    double tl = t2;
+    if (L.outstanding && __atomic_load_n(&s->h_mail()[li].done, __ATOMIC_ACQUIRE) == L.seq) {
+        L.outstanding = false;  // the timed-out request has been answered: the mailbox is free
+        L.hold.reset();
     }
-    s->lane_cv.notify_one();
+    if (s->res_live.load(std::memory_order_acquire) && !L.outstanding)
+        st = resident_query(s, li, L, set, t, q, k, out7, &tl);
+    else
+        st = hf_query_on_lane(set->fs, t, q, k, out7, L.st, L.h_out, L.d_out, &tl);
+    const double t3 = now_ms();
+    s->free_lanes.fetch_or(uint64_t(1) << li, std::memory_order_release);
     if (st == HF_OK) {
         if (ss) ss->answered++;
         const double us = (t3 - t0) * 1000.0;
@@ -895,8 +1080,13 @@ extern "C" hf_status hf_server_query(hf_server *s, int session, const float t[3]
             s->lat_count = std::min(s->lat_count + 1, kLatRing);
         }
         if (us >= kSlowQueryUs) {
-            const double row[TraceRing::kCols] = {t0 - s->t0, us, (t1 - t0) * 1e3, (t2 - t1) * 1e3, (t3 - t2) * 1e3,
-                                                  (double)session};
+            // context switches of this thread during the query: involuntary
+            // ones (the OS took the core) apart from voluntary ones (a wait)
+            struct rusage ru1;
+            getrusage(RUSAGE_THREAD, &ru1);
+            const double row[TraceRing::kCols] = {t0 - s->t0, us, (t1 - t0) * 1e3, (t2 - t1) * 1e3, (tl - t2) * 1e3,
+                                                  (t3 - tl) * 1e3, (double)session, (double)(ru1.ru_nivcsw - ru0.ru_nivcsw),
+                                                  (double)(ru1.ru_nvcsw - ru0.ru_nvcsw)};
             s->slow_queries.put(row);
         }
     }
@@ -988,6 +1178,13 @@ extern "C" hf_status hf_server_stats_get(hf_server *s, hf_server_stats *out) {
             out->pool_reserved_high = (size_t)v;
     }
     (void)cudaGetLastError();
+    out->arena_bytes = s->arena.capacity();
+    out->arena_free_bytes = s->arena.free_bytes();
+    out->arena_largest_free = s->arena.largest_free();
+    out->arena_refusals = s->arena.failures();
+    out->resident_queries = s->res_answered.load();
+    out->resident_timeouts = s->res_timeouts.load();
+    out->resident_live = s->res_live.load() ? 1 : 0;
     return HF_OK;
 }
 

@@ -339,3 +339,107 @@ def test_metrics_log_lines_account_for_every_query_and_build(hf, tmp_path):
     assert sorted(last) == [a, b]
     assert sum(v[0] for v in last.values()) >= answered
     srv.close()
+
+
+def test_preload_loads_the_kernel_modules_once(hf):
+    """hf_ctx_preload loads every kernel of the builds, torque and queries;
+    a second call finds the same modules and loads nothing new."""
+    ctx = hf.Context(0)
+    n1 = ctx.preload()
+    n2 = ctx.preload()
+    assert n1 == n2 and n1 > 50
+
+
+def test_budgeted_server_builds_in_its_arena_bitwise(hf):
+    """With a budget the server carves its field sets from one device arena:
+    while sets are resident the arena has less free, the fields are bitwise
+    those of a standalone field-set build of the same rotations, and once
+    every set is evicted and released the arena is one free range again."""
+    from paper_1711_05017_b300 import _binding as B
+    n, R = 64, 24
+    flags = hf.HF_E | hf.HF_F | hf.HF_T
+    one = B.lib().hf_fieldset_bytes(n, R, flags)
+    ctx = hf.Context(0, hbm_budget_bytes=int(3.5 * one) + (64 << 20))
+    p1, p2 = make_parts(hf, ctx, n, 31)
+    srv = hf.Server(ctx, max_inflight=2, query_lanes=2)
+    st0 = srv.stats()
+    assert st0["arena_bytes"] >= 3 * one
+    assert st0["arena_free_bytes"] == st0["arena_bytes"]
+    sid = srv.open(p1, p2)
+    q = synth.random_quaternions(77, R)
+    rid = srv.submit(sid, q, flags)
+    assert srv.wait([rid])[rid][0] == "done"
+    st1 = srv.stats()
+    assert st1["arena_free_bytes"] <= st1["arena_bytes"] - one
+    got = fields_of(srv, sid, (0, 11, 23), n)
+    fs = ctx.fieldset(n, R, flags)
+    fs.compute(p1, p2, q)
+    ref = np.stack([np.stack([fs.get(r, f).cpu().numpy() for f in range(7)]) for r in (0, 11, 23)])
+    assert np.array_equal(got, ref)
+    fs.release()
+    # a second request of the same session replaces the first set, which is
+    # retired and returned to the arena
+    rid2 = srv.submit(sid, synth.random_quaternions(78, R), flags)
+    assert srv.wait([rid2])[rid2][0] == "done"
+    t0 = time.time()
+    while time.time() - t0 < 10 and srv.stats()["arena_free_bytes"] < st1["arena_free_bytes"]:
+        time.sleep(0.01)
+    st2 = srv.stats()
+    assert st2["arena_free_bytes"] == st1["arena_free_bytes"]
+    assert st2["arena_largest_free"] >= st2["arena_free_bytes"] - 2 * one
+    srv.close()
+
+
+def _poses(seed, m):
+    rng = np.random.default_rng(seed)
+    t = rng.uniform(-0.6, 0.6, size=(m, 3)).astype(np.float32)
+    return t, synth.random_quaternions(seed + 1, m).astype(np.float32)
+
+
+@pytest.mark.parametrize("n", [64, 96])
+def test_resident_queries_equal_launched_ones(hf, n, monkeypatch):
+    """Queries answered by the resident query kernel (no launch) equal, bit
+    for bit, those of a launched query kernel on the same field set, from one
+    thread and from several at once; with HF_RESIDENT_QUERIES=0 the server
+    launches every query and gives the same answers."""
+    flags = hf.HF_E | hf.HF_F | hf.HF_T
+    R = 24
+    ctx = hf.Context(0)
+    p1, p2 = make_parts(hf, ctx, n, 41)
+    q = synth.random_quaternions(101, R)
+    fs = ctx.fieldset(n, R, flags)
+    fs.compute(p1, p2, q)
+    import torch
+    torch.cuda.synchronize()  # hf_query runs on its own stream, not ordered after the build
+    t, qq = _poses(7, 120)
+    ks = [1 + (i % 8) for i in range(len(t))]
+    ref = np.stack([fs.query(t[i], qq[i], k=ks[i]) for i in range(len(t))])
+    for resident in (True, False):
+        if not resident:
+            monkeypatch.setenv("HF_RESIDENT_QUERIES", "0")
+        srv = hf.Server(ctx, max_inflight=1, query_lanes=20)  # two blocks of lanes
+        sid = srv.open(p1, p2)
+        rid = srv.submit(sid, q, flags)
+        assert srv.wait([rid])[rid][0] == "done"
+        got = np.stack([srv.query(sid, t[i], qq[i], k=ks[i]) for i in range(len(t))])
+        assert np.array_equal(got, ref), resident
+        outs = {}
+
+        def worker(w):
+            outs[w] = np.stack([srv.query(sid, t[i], qq[i], k=ks[i]) for i in range(w, len(t), 6)])
+
+        th = [threading.Thread(target=worker, args=(w,)) for w in range(6)]
+        for x in th:
+            x.start()
+        for x in th:
+            x.join()
+        for w in range(6):
+            assert np.array_equal(outs[w], ref[w::6]), (resident, w)
+        st = srv.stats()
+        if resident:
+            assert st["resident_live"] == 1
+            assert st["resident_queries"] >= 2 * len(t) and st["resident_timeouts"] == 0
+        else:
+            assert st["resident_live"] == 0 and st["resident_queries"] == 0
+        srv.close()
+    fs.release()
