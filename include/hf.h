@@ -403,8 +403,9 @@ int hf_rotation_chunks(const float *h_quat, int R, int max_build, int halo, int 
  *     set's answer when the query's k nearest rotations are owned by it.
  *   - Queries take no lock that the scheduler or a submitting thread holds
  *     (the published data is read through atomic shared pointers).
- *   - At creation the server allocates the context's remaining budget (up to
- *     the free memory less 4 GB) as one device arena and carves every build's
+ *   - At creation the server allocates the context's remaining budget, plus
+ *     half again for the gaps between sets of mixed sizes (HF_ARENA_SLACK,
+ *     percent; up to the free memory less 4 GB), as one device arena and carves every build's
  *     field set from it with host-side bookkeeping (best fit, coalesced on
  *     free), so that no build maps or unmaps device memory while queries run:
  *     the driver work of a mapping held up other threads' launches for
