@@ -288,6 +288,7 @@ def run_ours(args, rank, world, local_rank):
         "torque": R * n3b + R * 3 * n3b,
         "splat": n3b,
         "passB_fwd": 2 * he,
+        "passA_stationary": n3b + he,
         "query": N_QUERY * 7 * 4 * 2,
         "resample": n3b + chunk * n3b,
     }

@@ -659,7 +659,9 @@ hf_status hf_bulk_selftest(int device, int plant, int *timeouts);
  * summed device time; hf_profile_entry reads kind i (0 <= i < the count
  * returned); hf_profile_reset clears the totals.  Kinds: "splat", "passA",
  * "passB", "passB_fwd", "passC", "torque", "query", "resample", "y_tc"
- * (the tensor-core y stages of the precision variant). */
+ * (the tensor-core y stages of the precision variant), "passA_stationary"
+ * (the x/y transforms of a stationary part's spectrum; "passB_fwd" is its z
+ * transform). */
 hf_status hf_profile_enable(hf_ctx *ctx, int on);
 int hf_profile_read(hf_ctx *ctx);
 hf_status hf_profile_entry(const hf_ctx *ctx, int i, const char **name, long long *launches,

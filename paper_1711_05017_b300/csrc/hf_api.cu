@@ -55,9 +55,11 @@ bool pencil_n(int n) {
     } while (0)
 
 // ------------------------------------------------------------------ handles
-enum ProfKind { kSplat, kPassA, kPassB, kPassBFwd, kPassC, kTorque, kQuery, kResample, kYtc, kProfKinds };
+// (the stationary spectrum's x/y transforms are a kind of their own, so that
+// the rotation passes' averages are the rotation passes' alone)
+enum ProfKind { kSplat, kPassA, kPassB, kPassBFwd, kPassC, kTorque, kQuery, kResample, kYtc, kStatA, kProfKinds };
 static const char *kProfNames[kProfKinds] = {"splat",  "passA", "passB",    "passB_fwd", "passC",
-                                             "torque", "query", "resample", "y_tc"};
+                                             "torque", "query", "resample", "y_tc",      "passA_stationary"};
 
 struct Tune {  // the autotuner's choice for one grid size
     bool set = false;
@@ -464,10 +466,10 @@ static hf_status stationary_spectrum(hf_ctx *c, int n, const float *d_grid, floa
     CU(hf::dmalloc_async(&X1, 2 * he * sizeof(float2), st));
     cudaError_t e;
     if (hf::pencil_n(n)) {
-        e = timed(c, kPassA, st, [&] { return hf::run_xfwd(n, d_grid, X1 + he, 1, st); });
-        if (e == cudaSuccess) e = timed(c, kPassA, st, [&] { return hf::run_yfwd(n, X1 + he, X1, 1, st); });
+        e = timed(c, kStatA, st, [&] { return hf::run_xfwd(n, d_grid, X1 + he, 1, st); });
+        if (e == cudaSuccess) e = timed(c, kStatA, st, [&] { return hf::run_yfwd(n, X1 + he, X1, 1, st); });
     } else {
-        e = timed(c, kPassA, st, [&] { return hf::run_passA_planes(n, d_grid, X1, 1, st); });
+        e = timed(c, kStatA, st, [&] { return hf::run_passA_planes(n, d_grid, X1, 1, st); });
     }
     if (e == cudaSuccess) e = timed(c, kPassBFwd, st, [&] { return hf::run_passB_forward(n, X1, spec, scale, st); });
     const cudaError_t f = cudaFreeAsync(X1, st);
