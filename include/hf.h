@@ -283,6 +283,19 @@ void hf_fieldset_release(hf_fieldset *fs);
  * Errors: HF_EINVAL (k_blend outside 1..8 or > R), HF_ENOTREADY, HF_ECUDA. */
 hf_status hf_query(const hf_fieldset *fs, const float t[3], const float q[4], int k_blend,
                    float out7[7]);
+/* Answer the context's hf_query calls through the resident query kernel
+ * (on != 0) instead of a launch per query, or stop it (on == 0).  A
+ * query then posts its request in a mailbox in mapped pinned memory and
+ * spins until the kernel, which polls that mailbox, writes the answer back;
+ * the answers equal the launched kernel's bit for bit.  An instance of the
+ * kernel serves for 10 ms and a context thread keeps the next one queued, so
+ * one always runs: meanwhile a device-wide synchronisation (including the
+ * one cudaFree implies) waits up to 20 ms.  A query not answered within 20 ms
+ * stops the kernel and runs by launch, and so do the context's later queries.
+ * The paper has no counterpart: this is the runtime around the 1 kHz haptic
+ * loop of Section 4.3.  Errors: HF_EINVAL, HF_ECUDA (the kernel did not
+ * start). */
+hf_status hf_ctx_resident_queries(hf_ctx *ctx, int on);
 
 /* Batched pose query on the caller's stream: d_tq is Q x 7 floats
  * (tx, ty, tz, qw, qx, qy, qz); d_out is Q x 7 floats as in hf_query. */

@@ -60,6 +60,11 @@ class Context:
     def reserved_bytes(self):
         return B.lib().hf_ctx_reserved_bytes(self.handle)
 
+    def resident_queries(self, on=True):
+        """hf_ctx_resident_queries: answer FieldSet.query through the resident
+        query kernel (no launch per query), or stop it."""
+        B.check(B.lib().hf_ctx_resident_queries(self.handle, 1 if on else 0))
+
     def preload(self):
         """Load every kernel of the builds, torque and queries now (hf_ctx_preload);
         returns the number of kernels in the loaded modules."""

@@ -34,6 +34,7 @@ SIGNATURES = {
     "hf_ctx_destroy": (None, [_vp]),
     "hf_ctx_reserved_bytes": (_sz, [_vp]),
     "hf_ctx_preload": (_i, [_vp, ctypes.POINTER(_i)]),
+    "hf_ctx_resident_queries": (_i, [_vp, _i]),
     "hf_density_build": (_i, [_vp, _i, _vp, _vp, _vp, _i, _vp, _vp]),
     "hf_part_create": (_i, [_vp, _i, _vp, _i, ctypes.POINTER(_vp), _vp]),
     "hf_part_release": (None, [_vp]),

@@ -9,7 +9,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libhf.so")
-SOURCES = ["hf_api.cu", "hf_arena.cu", "hf_fft.cu", "hf_kernels.cu", "hf_noalloc.cu", "hf_server.cu", "hf_batch.cu", "hf_tc.cu", "hf_lowpass.cu", "hf_mesh.cu"]
+SOURCES = ["hf_api.cu", "hf_arena.cu", "hf_resident.cu", "hf_fft.cu", "hf_kernels.cu", "hf_noalloc.cu", "hf_server.cu", "hf_batch.cu", "hf_tc.cu", "hf_lowpass.cu", "hf_mesh.cu"]
 HEADERS = ["hf_dft.cuh", "hf_sample.cuh", "hf_spec.cuh", "hf_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++20", "-Xcompiler", "-fPIC", "-I", INCLUDE]

@@ -85,6 +85,9 @@ struct hf_ctx {
     float *h_qout = nullptr;  // mapped pinned 7-float answer mailbox
     float *d_qout = nullptr;  // its device alias
     std::mutex qmu;
+    // hf_query through the resident query kernel when enabled (one lane), under qmu
+    hf::ResidentQueries *res = nullptr;
+    unsigned res_seq = 0;
     // single-pose low-pass scratch (partial sums and the pose counter), under qmu
     double *lp_part = nullptr;
     unsigned *lp_count = nullptr;
@@ -332,6 +335,7 @@ extern "C" void hf_ctx_destroy(hf_ctx *c) { hf_ctx_release(c); }
 
 static void ctx_free(hf_ctx *c) {
     cudaSetDevice(c->device);
+    delete c->res;  // stops its kernel
     if (c->qstream) cudaStreamDestroy(c->qstream);
     if (c->h_qout) cudaFreeHost(c->h_qout);
     if (c->lp_part) cudaFree(c->lp_part);
@@ -1582,7 +1586,37 @@ extern "C" hf_status hf_query(const hf_fieldset *fs, const float t[3], const flo
     hf_ctx *c = fs->ctx;
     std::lock_guard<std::mutex> g(c->qmu);
     CU(cudaSetDevice(c->device));
+    if (c->res && c->res->live()) {
+        hf::QueryReq rq;
+        const hf_status s = hf_query_request(fs, t, q, k, &rq);
+        if (s != HF_OK) return s;
+        if (c->res->query(0, rq, &c->res_seq, out7, 20.0, nullptr)) return HF_OK;
+        // not answered in time: stop the kernel (after which nothing reads the
+        // set) and answer by launch; the context's queries launch from now on
+        delete c->res;
+        c->res = nullptr;
+    }
     return hf_query_on_lane(fs, t, q, k, out7, c->qstream, c->h_qout, c->d_qout);
+}
+
+extern "C" hf_status hf_ctx_resident_queries(hf_ctx *c, int on) {
+    if (!c) return fail(HF_EINVAL, "hf_ctx_resident_queries: NULL context");
+    std::lock_guard<std::mutex> g(c->qmu);
+    CU(cudaSetDevice(c->device));
+    if (on && !c->res) {
+        c->res = new (std::nothrow) hf::ResidentQueries();
+        if (!c->res || !c->res->start(c->device, 1)) {
+            delete c->res;
+            c->res = nullptr;
+            (void)cudaGetLastError();
+            return fail(HF_ECUDA, "hf_ctx_resident_queries: the resident query kernel did not start");
+        }
+        c->res_seq = 0;
+    } else if (!on && c->res) {
+        delete c->res;
+        c->res = nullptr;
+    }
+    return HF_OK;
 }
 
 // ----------------------------------------------------- single-step entries

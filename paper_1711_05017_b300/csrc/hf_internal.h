@@ -8,6 +8,7 @@
 #include <atomic>
 #include <map>
 #include <mutex>
+#include <thread>
 
 #include <nvtx3/nvToolsExt.h>
 
@@ -218,6 +219,42 @@ struct alignas(128) QueryMail {
 constexpr int kResidentLanesPerBlock = 15;  // + 1 polling warp: 512 threads
 cudaError_t launch_query_resident(QueryMail *mail, unsigned *req, unsigned *served, const unsigned *stop, int lanes,
                                   unsigned long long life_ns, cudaStream_t st);
+
+// The resident query kernel's host side (hf_resident.cu): the lanes'
+// mailboxes in mapped pinned memory, each lane's last answered request number
+// on the device, and a thread that keeps two instances of the kernel queued on
+// a high-priority stream (the next starts on the device as the running one
+// ends).  A lane is used by one thread at a time (its owner's lock or lane
+// pool).  While it runs, a device-wide synchronisation waits for the running
+// and the queued instance.
+class ResidentQueries {
+  public:
+    static constexpr unsigned long long kLifeNs = 10ull * 1000 * 1000;  // one instance's service
+    ~ResidentQueries() { stop(); }
+    // allocate and start (false, and nothing left running, on any failure)
+    bool start(int device, int lanes);
+    // stop the keeper; on return no instance runs or is queued
+    void stop();
+    bool live() const { return live_.load(std::memory_order_acquire); }
+    // post a request on `lane` (number *seq + 1, stored back) and spin until
+    // it is answered or wait_ms pass: true with out7 on an answer, false on
+    // timeout (the request may still be read: see answered)
+    bool query(int lane, const QueryReq &rq, unsigned *seq, float out7[7], double wait_ms, double *posted_ms);
+    // whether the request numbered seq on lane has been answered
+    bool answered(int lane, unsigned seq) const;
+
+  private:
+    void keeper();
+    int device_ = 0, lanes_ = 0;
+    char *h_ = nullptr, *d_ = nullptr;  // request numbers (256 B), stop flag (256 B), mailboxes
+    unsigned *d_served_ = nullptr;
+    cudaStream_t st_ = nullptr;
+    std::thread thread_;
+    std::atomic<bool> live_{false}, quit_{false};
+    unsigned *h_req() const { return reinterpret_cast<unsigned *>(h_); }
+    unsigned *h_stop() const { return reinterpret_cast<unsigned *>(h_ + 256); }
+    QueryMail *h_mail() const { return reinterpret_cast<QueryMail *>(h_ + 512); }
+};
 
 // An NVTX range over a library call (a profiler with NVTX support shows the
 // call's kernels under its name; without one the push and pop do nothing).

@@ -339,6 +339,16 @@ __device__ __forceinline__ T ld_set(const T *p) {
     else return *p;
 }
 
+// A double in [-1, 1] as a float by truncation, in integer operations (a
+// float64-to-float32 conversion runs at the float64 rate): within 2^-23 of
+// |x|; values below float's normal range read as zero.
+__device__ __forceinline__ float f32_trunc(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned e = (hi >> 20) & 0x7ffu;
+    if (e < 897u) return 0.0f;
+    return __uint_as_float((hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+}
+
 // One query by one warp: `in` = (t, q), 7 results to `outp`.
 template <int N, bool CG = false>
 __device__ __forceinline__ void query_warp(const QueryGeom &g, const float *in, int k, float *outp,
@@ -348,15 +358,33 @@ __device__ __forceinline__ void query_warp(const QueryGeom &g, const float *in, 
     const double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
 #pragma unroll
     for (int a = 0; a < 4; ++a) q[a] /= qn;
-    // per-lane sorted top-k of (|dot|, index); lanes visit indices in ascending order
+    // The k nearest rotations by |<q, q_j>| (ties to the lower index), ranked
+    // in float64.  A float64 warp instruction takes many times a float32
+    // one, so in the launched kernels a float32 pass first finds the k-th
+    // largest |dot| (K32), and
+    // the float64 ranking then takes only rotations whose float32 |dot| is at
+    // least K32 - 3e-6.  That keeps every rotation the float64 ranking can
+    // select: the float32 |dot| is within 6 2^-24 of the float64 one (unit
+    // quaternions, inputs truncated to float32 within 2^-23, four rounded
+    // fmas), so the float64 k-th largest D >= K32 - 1e-6 and each selected
+    // rotation's float32 |dot| >= D - 1e-6.  The selection, and so the result,
+    // is the same as ranking every rotation in float64.
+    const float qf[4] = {f32_trunc(q[0]), f32_trunc(q[1]), f32_trunc(q[2]), f32_trunc(q[3])};
+    constexpr int kQueryLoads = 4;  // a lane's rotations j = lane + 32 i, loaded kQueryLoads at a time
+    auto dot32 = [&](const double *v) {
+        return fminf(fabsf(fmaf(qf[0], f32_trunc(v[0]),
+                                fmaf(qf[1], f32_trunc(v[1]), fmaf(qf[2], f32_trunc(v[2]), qf[3] * f32_trunc(v[3]))))),
+                     1.0f);
+    };
+    float tk[kQueryMaxK];  // this lane's k largest float32 |dot|, descending
+#pragma unroll
+    for (int s = 0; s < kQueryMaxK; ++s) tk[s] = -1.0f;
     double bd[kQueryMaxK];
     int bi[kQueryMaxK];
 #pragma unroll
     for (int s = 0; s < kQueryMaxK; ++s) { bd[s] = -1.0; bi[s] = 0x7fffffff; }
-    for (int j = lane; j < g.R; j += 32) {
-        const double *qj = g.quats + 4 * (size_t)j;
-        double d = fabs(q[0] * ld_set<CG>(qj) + q[1] * ld_set<CG>(qj + 1) + q[2] * ld_set<CG>(qj + 2) +
-                        q[3] * ld_set<CG>(qj + 3));
+    auto rank64 = [&](const double *v, int j) {  // insert into the lane's float64 top-k
+        double d = fabs(q[0] * v[0] + q[1] * v[1] + q[2] * v[2] + q[3] * v[3]);
         d = fmin(d, 1.0);
         int ij = j;
 #pragma unroll
@@ -367,7 +395,82 @@ __device__ __forceinline__ void query_warp(const QueryGeom &g, const float *in, 
                 bd[s] = d; bi[s] = ij; d = td; ij = ti;
             }
         }
-    }
+    };
+    if constexpr (CG) {
+        // the resident query kernel ranks every rotation in float64, one at a
+        // time: its loads go to L2 (a second pass would pay them again), and
+        // on an SM shared with the builds' float32 kernels the float64 pipe is
+        // the idle one (measured: p50 47 us in serving against 62-68 us with
+        // either float32-first form)
+        for (int j = lane; j < g.R; j += 32) {
+            const double *qj = g.quats + 4 * (size_t)j;
+            const double v[4] = {ld_set<CG>(qj), ld_set<CG>(qj + 1), ld_set<CG>(qj + 2), ld_set<CG>(qj + 3)};
+            rank64(v, j);
+        }
+    } else {
+        for (int j0 = lane; j0 < g.R; j0 += 32 * kQueryLoads) {
+            double qv[kQueryLoads][4];
+#pragma unroll
+            for (int u = 0; u < kQueryLoads; ++u) {
+                const int j = j0 + 32 * u;
+                if (j < g.R) {
+                    const double *qj = g.quats + 4 * (size_t)j;
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) qv[u][a] = ld_set<CG>(qj + a);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kQueryLoads; ++u) {
+                if (j0 + 32 * u >= g.R) break;
+                float df = dot32(qv[u]);
+#pragma unroll
+                for (int s = 0; s < kQueryMaxK; ++s)
+                    if (s < k && df > tk[s]) {
+                        const float t = tk[s];
+                        tk[s] = df;
+                        df = t;
+                    }
+            }
+        }
+        float kth = -1.0f;  // the warp's k-th largest float32 |dot|
+        for (int s = 0; s < k; ++s) {
+            float v = tk[0];
+            int owner = lane;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+                const int oo = __shfl_xor_sync(0xffffffffu, owner, o);
+                if (ov > v || (ov == v && oo < owner)) { v = ov; owner = oo; }
+            }
+            kth = v;
+            if (owner == lane) {
+#pragma unroll
+                for (int t = 0; t < kQueryMaxK - 1; ++t) tk[t] = tk[t + 1];
+                tk[kQueryMaxK - 1] = -1.0f;
+            }
+        }
+        const float tau = kth - 3e-6f;
+        // per-lane sorted top-k of (|dot|, index) over the candidates, in float64;
+        // lanes visit indices in ascending order
+        for (int j0 = lane; j0 < g.R; j0 += 32 * kQueryLoads) {
+            double qv[kQueryLoads][4];
+#pragma unroll
+            for (int u = 0; u < kQueryLoads; ++u) {
+                const int j = j0 + 32 * u;
+                if (j < g.R) {
+                    const double *qj = g.quats + 4 * (size_t)j;
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) qv[u][a] = ld_set<CG>(qj + a);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kQueryLoads; ++u) {
+                const int j = j0 + 32 * u;
+                if (j >= g.R) break;
+                if (dot32(qv[u]) >= tau) rank64(qv[u], j);
+            }
+        }
+    }  // two passes
     // warp merge: k rounds of arg-best over the lanes' list heads
     double sel_d[kQueryMaxK];
     int sel_i[kQueryMaxK];
@@ -389,15 +492,21 @@ __device__ __forceinline__ void query_warp(const QueryGeom &g, const float *in, 
             bi[kQueryMaxK - 1] = 0x7fffffff;
         }
     }
-    // weights 1/theta, theta = 2 acos(|dot|)
+    // weights 1/theta, theta = 2 acos(|dot|): lane s < k computes the s-th
+    // theta, the others none (a float64 warp instruction costs per active lane)
+    double th = 1.0;
+#pragma unroll
+    for (int s = 0; s < kQueryMaxK; ++s)
+        if (s == lane && s < k) th = 2.0 * acos(sel_d[s]);
     double w[kQueryMaxK];
     int used = k;
-    if (2.0 * acos(sel_d[0]) < 1e-12) {
+    if (__shfl_sync(0xffffffffu, th < 1e-12 ? 1 : 0, 0)) {
         used = 1;
         w[0] = 1.0;
     } else {
+        const double wl = lane < k ? 1.0 / th : 0.0;
         double sw = 0.0;
-        for (int s = 0; s < k; ++s) { w[s] = 1.0 / (2.0 * acos(sel_d[s])); sw += w[s]; }
+        for (int s = 0; s < k; ++s) { w[s] = __shfl_sync(0xffffffffu, wl, s); sw += w[s]; }
         for (int s = 0; s < k; ++s) w[s] /= sw;
     }
     // trilinear per (field, rotation) pair at lag u = t / h
@@ -476,11 +585,11 @@ __device__ __forceinline__ void st_release_sys(unsigned *p, unsigned v) {
 }
 
 template <int N>
-__device__ void query_resident_serve(const QueryReq &r, float *part, float *out) {
+__device__ __noinline__ void query_resident_serve(const QueryReq &r, float *part, float *out) {
     query_warp<N, true>(r.g, r.pose.v, r.k, out, part);
 }
 
-__global__ void __launch_bounds__(32 * (kResidentLanesPerBlock + 1))
+__global__ void __launch_bounds__(32 * (kResidentLanesPerBlock + 1), 1)
     query_resident_kernel(QueryMail *mail, unsigned *req, unsigned *served, const unsigned *stop, int lanes,
                           unsigned long long life_ns, unsigned long long max_polls) {
     __shared__ volatile unsigned s_pend[kResidentLanesPerBlock];

@@ -266,80 +266,14 @@ struct hf_server {
     TraceRing slow_queries, slow_calls;
     void *arena_mem = nullptr;  // the field-set arena's device region (null: the pool serves)
     hf::Arena arena;
-    // the resident query kernel: mapped pinned region of the lanes' request
-    // numbers (256 B), the stop flag (256 B) and the lanes' mailboxes; each
-    // lane's last answered request number on the device; the stream the
-    // instances queue on and the thread that keeps two of them queued
-    char *h_res = nullptr, *d_res = nullptr;
-    unsigned *d_served = nullptr;
-    cudaStream_t res_st = nullptr;
-    std::thread res_keeper;
-    std::atomic<bool> res_live{false}, res_quit{false};
+    // the resident query kernel (its host side) and what it has answered
+    hf::ResidentQueries res;
     std::atomic<int64_t> res_answered{0}, res_timeouts{0};
-    unsigned *h_req() { return reinterpret_cast<unsigned *>(h_res); }
-    unsigned *h_stop() { return reinterpret_cast<unsigned *>(h_res + 256); }
-    hf::QueryMail *h_mail() { return reinterpret_cast<hf::QueryMail *>(h_res + 512); }
 };
 
-// an instance of the resident query kernel serves this long (short, since a
-// device-wide synchronisation, which cudaFree implies, waits for the running
-// and the queued instance); a request not answered within kResidentWaitMs
-// goes to the launch path instead
-constexpr unsigned long long kResidentLifeNs = 10ull * 1000 * 1000;
+// a request not answered by the resident query kernel within this long goes
+// to the launch path instead
 constexpr double kResidentWaitMs = 20.0;
-
-static void cpu_relax() {
-#if defined(__x86_64__) || defined(__i386__)
-    __builtin_ia32_pause();
-#endif
-}
-
-// Keeps two instances of the resident query kernel queued on res_st, so that
-// the next one starts on the device as the running one ends, with no launch
-// on the host in between; on stop, raises the stop flag and waits for them.
-static void resident_keeper(hf_server *s) {
-    cudaSetDevice(s->device);
-    constexpr int kRing = 3;
-    cudaEvent_t ev[kRing] = {};
-    bool ok = true;
-    for (auto &e : ev) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
-    auto *d_req = reinterpret_cast<unsigned *>(s->d_res);
-    auto *d_stop = reinterpret_cast<const unsigned *>(s->d_res + 256);
-    auto *d_mail = reinterpret_cast<hf::QueryMail *>(s->d_res + 512);
-    const int lanes = (int)s->lanes.size();
-    int head = 0, queued = 0;
-    while (ok && !s->res_quit.load()) {
-        if (queued < 2) {
-            const int slot = (head + queued) % kRing;
-            if (hf::launch_query_resident(d_mail, d_req, s->d_served, d_stop, lanes, kResidentLifeNs, s->res_st) !=
-                    cudaSuccess ||
-                cudaEventRecord(ev[slot], s->res_st) != cudaSuccess) {
-                ok = false;
-                break;
-            }
-            ++queued;
-            s->res_live.store(true, std::memory_order_release);
-            continue;
-        }
-        const cudaError_t q = cudaEventQuery(ev[head]);
-        if (q == cudaSuccess) {
-            head = (head + 1) % kRing;
-            --queued;
-            continue;
-        }
-        if (q != cudaErrorNotReady) {
-            ok = false;
-            break;
-        }
-        std::this_thread::sleep_for(std::chrono::milliseconds(2));
-    }
-    s->res_live.store(false, std::memory_order_release);
-    (void)cudaGetLastError();
-    __atomic_store_n(s->h_stop(), 1u, __ATOMIC_RELEASE);  // the running instance ends at its next poll
-    cudaStreamSynchronize(s->res_st);
-    for (auto e : ev)
-        if (e) cudaEventDestroy(e);
-}
 
 // A query through the resident kernel on lane li: post the request, wait
 // (spinning, bounded) for its answer.  *posted receives the time the request
@@ -350,24 +284,12 @@ static hf_status resident_query(hf_server *s, int li, Lane &L, const std::shared
     hf::QueryReq rq;
     hf_status st = hf_query_request(set->fs, t, q, k, &rq);
     if (st != HF_OK) return st;
-    hf::QueryMail *m = s->h_mail() + li;
-    m->rq = rq;
-    unsigned seq = L.seq + 1;
-    if (seq == 0) seq = 1;
-    L.seq = seq;
     L.hold = set;  // the set outlives the kernel's reads of it
-    __atomic_store_n(s->h_req() + li, seq, __ATOMIC_RELEASE);
-    *posted = now_ms();
-    const double give_up = *posted + kResidentWaitMs;
-    for (unsigned spins = 1; __atomic_load_n(&m->done, __ATOMIC_ACQUIRE) != seq; ++spins) {
-        if ((spins & 255u) == 0 && now_ms() > give_up) {
-            L.outstanding = true;
-            s->res_timeouts++;
-            return hf_query_on_lane(set->fs, t, q, k, out7, L.st, L.h_out, L.d_out);
-        }
-        cpu_relax();
+    if (!s->res.query(li, rq, &L.seq, out7, kResidentWaitMs, posted)) {
+        L.outstanding = true;
+        s->res_timeouts++;
+        return hf_query_on_lane(set->fs, t, q, k, out7, L.st, L.h_out, L.d_out);
     }
-    for (int a = 0; a < 7; ++a) out7[a] = ((volatile float *)m->out)[a];
     L.hold.reset();
     s->res_answered++;
     return HF_OK;
@@ -713,25 +635,8 @@ extern "C" hf_status hf_server_create(hf_ctx *ctx, int max_inflight, int query_l
     // the resident query kernel (HF_RESIDENT_QUERIES=0: every query by launch);
     // without its memory or stream the queries launch, which is not an error
     const char *rev = getenv("HF_RESIDENT_QUERIES");
-    if (!(rev && atoi(rev) == 0)) {
-        const size_t rbytes = 512 + sizeof(hf::QueryMail) * (size_t)query_lanes;
-        void *h = nullptr, *d = nullptr;
-        bool ok = hf::hmalloc_mapped(&h, rbytes) == cudaSuccess;
-        if (ok) {
-            s->h_res = (char *)h;
-            memset(h, 0, rbytes);
-            ok = cudaHostGetDevicePointer(&d, h, 0) == cudaSuccess;
-        }
-        if (ok) {
-            s->d_res = (char *)d;
-            ok = hf::dmalloc(&s->d_served, sizeof(unsigned) * (size_t)query_lanes) == cudaSuccess &&
-                 cudaMemset(s->d_served, 0, sizeof(unsigned) * (size_t)query_lanes) == cudaSuccess &&
-                 cudaStreamCreateWithPriority(&s->res_st, cudaStreamNonBlocking, hi) == cudaSuccess &&
-                 cudaStreamSynchronize(s->res_st) == cudaSuccess;
-        }
-        if (ok) s->res_keeper = std::thread(resident_keeper, s);
-        (void)cudaGetLastError();
-    }
+    if (!(rev && atoi(rev) == 0)) (void)s->res.start(s->device, query_lanes);
+    (void)cudaGetLastError();
     s->sched = std::thread(scheduler, s);
     *out = s;
     return HF_OK;
@@ -753,8 +658,7 @@ extern "C" void hf_server_destroy(hf_server *s) {
     }
     s->cv.notify_all();
     if (s->sched.joinable()) s->sched.join();
-    s->res_quit.store(true);
-    if (s->res_keeper.joinable()) s->res_keeper.join();  // no instance runs after this
+    s->res.stop();  // no instance runs after this
     for (auto &L : s->lanes) L.hold.reset();
     for (int i = 0; i < s->nsessions.load(); ++i) s->sessions[i].set_current(nullptr);
     cudaDeviceSynchronize();
@@ -773,9 +677,7 @@ extern "C" void hf_server_destroy(hf_server *s) {
         if (L.st) cudaStreamDestroy(L.st);
         if (L.h_out) cudaFreeHost(L.h_out);
     }
-    if (s->res_st) cudaStreamDestroy(s->res_st);
-    if (s->d_served) cudaFree(s->d_served);
-    if (s->h_res) cudaFreeHost(s->h_res);
+
     if (s->arena_mem) {
         cudaFree(s->arena_mem);  // every set carved from it was released above
     } else {
@@ -1060,11 +962,11 @@ extern "C" hf_status hf_server_query(hf_server *s, int session, const float t[3]
     const double t2 = now_ms();
     Lane &L = s->lanes[li];
     double tl = t2;
-    if (L.outstanding && __atomic_load_n(&s->h_mail()[li].done, __ATOMIC_ACQUIRE) == L.seq) {
+    if (L.outstanding && s->res.answered(li, L.seq)) {
         L.outstanding = false;  // the timed-out request has been answered: the mailbox is free
         L.hold.reset();
     }
-    if (s->res_live.load(std::memory_order_acquire) && !L.outstanding)
+    if (s->res.live() && !L.outstanding)
         st = resident_query(s, li, L, set, t, q, k, out7, &tl);
     else
         st = hf_query_on_lane(set->fs, t, q, k, out7, L.st, L.h_out, L.d_out, &tl);
@@ -1185,7 +1087,7 @@ extern "C" hf_status hf_server_stats_get(hf_server *s, hf_server_stats *out) {
     out->arena_refusals = s->arena.failures();
     out->resident_queries = s->res_answered.load();
     out->resident_timeouts = s->res_timeouts.load();
-    out->resident_live = s->res_live.load() ? 1 : 0;
+    out->resident_live = s->res.live() ? 1 : 0;
     return HF_OK;
 }
 

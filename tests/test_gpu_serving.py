@@ -443,3 +443,34 @@ def test_resident_queries_equal_launched_ones(hf, n, monkeypatch):
             assert st["resident_live"] == 0 and st["resident_queries"] == 0
         srv.close()
     fs.release()
+
+
+def test_context_resident_queries_equal_launched_ones(hf):
+    """hf_ctx_resident_queries: FieldSet.query through the resident query
+    kernel gives the launched kernel's answers bit for bit; turning it off
+    and on again (twice on is a no-op) keeps them."""
+    import torch
+    flags = hf.HF_E | hf.HF_F | hf.HF_T
+    n, R = 64, 24
+    ctx = hf.Context(0)
+    p1, p2 = make_parts(hf, ctx, n, 43)
+    q = synth.random_quaternions(103, R)
+    fs = ctx.fieldset(n, R, flags)
+    fs.compute(p1, p2, q)
+    torch.cuda.synchronize()
+    t, qq = _poses(9, 100)
+    ks = [1 + (i % 8) for i in range(len(t))]
+
+    def run():
+        return np.stack([fs.query(t[i], qq[i], k=ks[i]) for i in range(len(t))])
+
+    ref = run()
+    ctx.resident_queries(True)
+    ctx.resident_queries(True)
+    assert np.array_equal(run(), ref)
+    ctx.resident_queries(False)
+    assert np.array_equal(run(), ref)
+    ctx.resident_queries(True)
+    assert np.array_equal(run(), ref)
+    ctx.resident_queries(False)
+    fs.release()
