@@ -292,9 +292,11 @@ hf_status hf_query(const hf_fieldset *fs, const float t[3], const float q[4], in
  * one always runs: meanwhile a device-wide synchronisation (including the
  * one cudaFree implies) waits up to 20 ms.  A query not answered within 20 ms
  * stops the kernel and runs by launch, and so do the context's later queries.
- * The paper has no counterpart: this is the runtime around the 1 kHz haptic
- * loop of Section 4.3.  Errors: HF_EINVAL, HF_ECUDA (the kernel did not
- * start). */
+ * On an idle device a launched query is as fast (the launched kernel ranks
+ * in float32 first); the resident kernel avoids the launches that builds
+ * running beside the queries can hold up for milliseconds.  The paper has
+ * no counterpart: this is the runtime around the 1 kHz haptic loop of
+ * Section 4.3.  Errors: HF_EINVAL, HF_ECUDA (the kernel did not start). */
 hf_status hf_ctx_resident_queries(hf_ctx *ctx, int on);
 
 /* Batched pose query on the caller's stream: d_tq is Q x 7 floats
