@@ -475,3 +475,72 @@ def test_no_bulk_copy_wait_gave_up(hf):
     arrive: no bounded wait ran out."""
     from paper_1711_05017_b300 import _binding as B
     assert B.lib().hf_bulk_timeouts(0) == 0
+
+
+def test_query_selection_near_ties(hf, tmp_path):
+    """The pose query's choice of the k nearest rotations, exactly as the
+    oracle ranks them, where the float32 pass of the launched kernels cannot
+    tell rotations apart: clusters of rotations 2e-4 to 1e-3 rad apart, exact
+    duplicates (ties go to the lower index), and a query at a stored rotation
+    (an exact hit).  A set whose energy field of rotation j is the constant
+    j + 1 (written as a checkpoint with numpy) makes every answer the weighted
+    sum of the chosen indices; the launched query, the batched one and the
+    resident one are compared with the oracle's blend of the same fields.
+    (No query sits exactly on a clustered rotation: there one ulp of |dot|,
+    from the two sides normalising the quaternions in different rounding
+    orders, decides the exact-hit rule and moves the 1/theta blend by up to
+    5e-3; exact member rotations are tested apart from clusters.)"""
+    import torch
+    from scipy.spatial.transform import Rotation
+    n = 32
+    rng = np.random.default_rng(7)
+    base = synth.random_quaternions(70, 8)
+    quats = []
+    for b in base:
+        quats.append(b)
+        for ang in (2e-4, 5e-4, 1e-3):
+            ax = rng.normal(size=3)
+            dq = Rotation.from_rotvec(ax / np.linalg.norm(ax) * ang).as_quat()  # x, y, z, w
+            r = Rotation.from_quat([b[1], b[2], b[3], b[0]]) * Rotation.from_quat(dq)
+            x, y, z, w = r.as_quat()
+            quats.append([w, x, y, z])
+    quats += [quats[1], quats[5], quats[2]]  # exact duplicates at higher indices
+    q32 = np.asarray(quats, dtype=np.float32)
+    R = len(q32)
+    fields = np.zeros((R, 4, n, n, n), dtype=np.float32)
+    for j in range(R):
+        fields[j, 0] = j + 1.0
+    path = tmp_path / "ties.hfc"
+    with open(path, "wb") as f:
+        np.lib.format.write_array(f, np.array([0x31504B4348465348, 1, hf.HF_CKPT_FIELDSET, n, R, hf.HF_E | hf.HF_F, 4,
+                                                0, 1, 2, 3, -1, -1, -1, 0, 0], dtype=np.int64))
+        np.lib.format.write_array(f, q32)
+        np.lib.format.write_array(f, fields)
+    ctx = hf.Context(0)
+    fs = hf.FieldSet.load(ctx, path)
+    torch.cuda.synchronize()
+    # queries: near each cluster (inside the float32 ambiguity), and at stored rotations
+    poses = []
+    for i, b in enumerate(base):
+        for ang in (1e-4, 3e-4, 2e-3):
+            ax = rng.normal(size=3)
+            dq = Rotation.from_rotvec(ax / np.linalg.norm(ax) * ang).as_quat()
+            r = Rotation.from_quat([b[1], b[2], b[3], b[0]]) * Rotation.from_quat(dq)
+            x, y, z, w = r.as_quat()
+            poses.append((rng.uniform(-0.9, 0.9, 3).astype(np.float32), np.array([w, x, y, z], dtype=np.float32)))
+    f64 = fields[:, :1].astype(np.float64)
+    ks = (1, 2, 4, 5, 8)
+    tq = cuda(np.stack([np.concatenate([t, qq]) for t, qq in poses]))
+    qn = norm_quats(q32)
+    for k in ks:
+        ref = np.array([oracle.query(qn, f64, t.astype(np.float64), qq.astype(np.float64), k)[0]
+                        for t, qq in poses])
+        one = np.array([fs.query(t, qq, k=k)[0] for t, qq in poses])
+        bat = fs.query_batch(tq, k=k)[:, 0].cpu().numpy()
+        assert np.abs(one - ref).max() <= 1e-5 * np.abs(ref).max(), k
+        assert np.array_equal(one, bat), k
+        ctx.resident_queries(True)
+        res = np.array([fs.query(t, qq, k=k)[0] for t, qq in poses])
+        ctx.resident_queries(False)
+        assert np.array_equal(one, res), k
+    fs.release()
