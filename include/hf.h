@@ -514,10 +514,11 @@ int hf_server_query_latencies(hf_server *srv, float *h_out_us, int max);
 /* Diagnostics since the last call, oldest first, 9 doubles per row, at most
  * `max` rows (the newest 4096 are kept); returns the row count.
  *   which 0, queries of 500 us or more: start (ms since hf_server_create),
- *     total us, us spent resolving the session's set (server mutex), waiting
- *     for a lane, in the query kernel's launch call, and in the lane's
- *     synchronise; the session; the calling thread's involuntary and
- *     voluntary context switches during the query.
+ *     total us, us spent resolving the session's set, waiting for a lane,
+ *     posting the request to the resident query kernel (or, on the launch
+ *     path, in the query kernel's launch call), and waiting for the answer
+ *     (or in the lane's synchronise); the session; the calling thread's
+ *     involuntary and voluntary context switches during the query.
  *   which 1, scheduler calls of 1 ms or more: start (ms), duration (us),
  *     kind (0 field-set create, 1 compute launch, 2 release), then zeros. */
 int hf_server_trace(hf_server *srv, int which, double *h_out, int max);
